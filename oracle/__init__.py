@@ -1,0 +1,226 @@
+"""CPU FP64 oracle for the implicit electron / potential JFNK solve.
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package. The CUDA product path
+never does, and the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, IEEE double, one column per
+OpenMP thread); this module compiles it with gcc on first use and marshals
+numpy arrays through ctypes. Every function follows Sec. 3.2 and Algorithm 2
+of arXiv:1904.08510 as documented in ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, MAX_NEWTON, MAX_KRYLOV, LINESEARCH_FAIL, NONFINITE, BAD_INPUT = range(6)
+BC_ABSORBING, BC_ZERO_GRADIENT = 0, 1
+
+# physical constants (SI, CODATA 2018) as used by oracle.c
+E_CHARGE = 1.602176634e-19
+K_B = 1.380649e-23
+EPS0 = 8.8541878128e-12
+
+
+class Params(C.Structure):
+    _fields_ = [("eps_F", C.c_double), ("eps_X", C.c_double), ("gamma", C.c_double),
+                ("mobility", C.c_double), ("ls_alpha", C.c_double), ("eps_r", C.c_double),
+                ("restart_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int),
+                ("max_linesearch", C.c_int), ("bc_electron", C.c_int), ("precond", C.c_int)]
+
+
+class _Batch(C.Structure):
+    _fields_ = [("ncol", C.c_int64), ("col_off", C.c_void_p), ("length", C.c_void_p),
+                ("dt", C.c_void_p), ("v_left", C.c_void_p), ("v_right", C.c_void_p),
+                ("ne_old", C.c_void_p), ("phi_old", C.c_void_p), ("n_species", C.c_int),
+                ("valence", C.c_void_p), ("n_ion", C.c_void_p), ("T", C.c_void_p),
+                ("u_adv", C.c_void_p), ("i_re", C.c_void_p)]
+
+
+def default_params(**kw) -> Params:
+    """Defaults: eps_F = 1e-10, gamma = 1e-4 (Table 1), mobility 0.4 m^2/(V s)
+    (Sec. 2.2), GMRES(30), 50 Newton steps, 200 Krylov iterations per step,
+    20 line-search halvings, absorbing electrodes, recast Schur preconditioner."""
+    p = dict(eps_F=1e-10, eps_X=0.0, gamma=1e-4, mobility=0.4, ls_alpha=1e-4, eps_r=1.0,
+             restart_m=30, max_newton=50, max_krylov=200, max_linesearch=20,
+             bc_electron=BC_ABSORBING, precond=1)
+    p.update(kw)
+    return Params(**p)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (gcc, -O2, OpenMP)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            os.makedirs(_BUILD, exist_ok=True)
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.POINTER(Params)
+        B = C.POINTER(_Batch)
+        vp = C.c_void_p
+        L.or_bern.restype = C.c_double
+        L.or_bern.argtypes = [C.c_double]
+        L.or_bern_deriv.restype = C.c_double
+        L.or_bern_deriv.argtypes = [C.c_double]
+        L.or_residual_batch.argtypes = [P, B, vp, vp, vp, vp]
+        L.or_jacobian_batch.argtypes = [P, B, vp, vp, vp, vp, vp]
+        L.or_prec_apply_col.argtypes = [P, B, C.c_int64, vp, vp, vp, vp, vp, vp]
+        L.or_solve_batch.argtypes = [P, B, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
+        L.or_thomas.argtypes = [C.c_int, vp, vp, vp, vp, vp, vp]
+        L.or_gmres_dense.restype = C.c_int
+        L.or_gmres_dense.argtypes = [C.c_int, vp, vp, vp, C.c_int, C.c_double, C.c_int,
+                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.or_max_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class _Keep:
+    """Holds the contiguous copies referenced by a ctypes batch struct."""
+
+    def __init__(self, batch):
+        self.col_off = np.ascontiguousarray(batch.col_off, dtype=np.int64)
+        self.length = _f64(batch.length)
+        self.dt = _f64(batch.dt)
+        self.v_left = _f64(batch.v_left)
+        self.v_right = _f64(batch.v_right)
+        self.ne_old = _f64(batch.ne_old)
+        self.phi_old = _f64(batch.phi_old)
+        self.n_ion = _f64(np.atleast_2d(batch.n_ion))
+        self.valence = np.ascontiguousarray(batch.valence, dtype=np.int32)
+        self.T = _f64(batch.T)
+        self.u_adv = None if batch.u_adv is None else _f64(batch.u_adv)
+        self.i_re = None if batch.i_re is None else _f64(batch.i_re)
+        self.s = _Batch(self.col_off.shape[0] - 1, _ptr(self.col_off), _ptr(self.length),
+                        _ptr(self.dt), _ptr(self.v_left), _ptr(self.v_right),
+                        _ptr(self.ne_old), _ptr(self.phi_old), self.n_ion.shape[0],
+                        _ptr(self.valence), _ptr(self.n_ion), _ptr(self.T),
+                        _ptr(self.u_adv), _ptr(self.i_re))
+
+
+def bern(x: float) -> float:
+    """B(x) = x / (e^x - 1) as evaluated by the oracle."""
+    return lib().or_bern(float(x))
+
+
+def bern_deriv(x: float) -> float:
+    return lib().or_bern_deriv(float(x))
+
+
+def residual(batch, ne, phi, params: Params | None = None):
+    """F(X) of Eq. nls for every column: returns (F_e, F_phi), each [cells]."""
+    P = params or default_params()
+    k = _Keep(batch)
+    ne, phi = _f64(ne), _f64(phi)
+    Fe = np.zeros(batch.ncells)
+    Fp = np.zeros(batch.ncells)
+    lib().or_residual_batch(C.byref(P), C.byref(k.s), _ptr(ne), _ptr(phi), _ptr(Fe), _ptr(Fp))
+    return Fe, Fp
+
+
+def jacobian_blocks(batch, ne, phi, params: Params | None = None):
+    """Analytic tridiagonal blocks (A, B, L), each an array [3, cells] of
+    (sub, diag, sup); C = dF_phi/dn = -I (Eq. linear_nls)."""
+    P = params or default_params()
+    k = _Keep(batch)
+    ne, phi = _f64(ne), _f64(phi)
+    n = batch.ncells
+    A = np.zeros((3, n))
+    B = np.zeros((3, n))
+    Lm = np.zeros((3, n))
+    lib().or_jacobian_batch(C.byref(P), C.byref(k.s), _ptr(ne), _ptr(phi), _ptr(A), _ptr(B),
+                            _ptr(Lm))
+    return A, B, Lm
+
+
+def prec_apply(batch, c, ne, phi, v1, v2, params: Params | None = None):
+    """Recast Schur preconditioner (Eq. prec_recast) of column c built at X, applied
+    to (v1, v2) in unscaled units."""
+    P = params or default_params()
+    k = _Keep(batch)
+    ne, phi, v1, v2 = _f64(ne), _f64(phi), _f64(v1), _f64(v2)
+    x1 = np.zeros_like(v1)
+    x2 = np.zeros_like(v2)
+    lib().or_prec_apply_col(C.byref(P), C.byref(k.s), int(c), _ptr(ne), _ptr(phi), _ptr(v1),
+                            _ptr(v2), _ptr(x1), _ptr(x2))
+    return x1, x2
+
+
+def thomas(sub, dia, sup, d):
+    sub, dia, sup, d = _f64(sub), _f64(dia), _f64(sup), _f64(d)
+    n = d.shape[0]
+    x = np.zeros(n)
+    w = np.zeros(2 * n)
+    lib().or_thomas(n, _ptr(sub), _ptr(dia), _ptr(sup), _ptr(d), _ptr(x), _ptr(w))
+    return x
+
+
+def gmres_dense(M, b, m, tol, maxit):
+    """The oracle's GMRES routine on a dense operator (no preconditioner)."""
+    M = _f64(M)
+    b = _f64(b)
+    n = b.shape[0]
+    x = np.zeros(n)
+    it = C.c_int(0)
+    est = C.c_double(0)
+    conv = lib().or_gmres_dense(n, _ptr(M), _ptr(b), _ptr(x), int(m), float(tol), int(maxit),
+                                C.byref(it), C.byref(est))
+    return x, bool(conv), it.value, est.value
+
+
+def solve(batch, params: Params | None = None, *, guess=None, threads: int = 0):
+    """JFNK (Algorithm 2) on every column. Returns a dict with ne, phi, status,
+    newton_it, krylov_it, res_evals, final_res."""
+    P = params or default_params()
+    k = _Keep(batch)
+    n = batch.ncells
+    ncol = batch.ncol
+    ne = np.zeros(n)
+    phi = np.zeros(n)
+    status = np.zeros(ncol, dtype=np.int32)
+    newton = np.zeros(ncol, dtype=np.int32)
+    krylov = np.zeros(ncol, dtype=np.int32)
+    evals = np.zeros(ncol, dtype=np.int32)
+    fres = np.zeros(ncol)
+    g_ne = g_phi = None
+    if guess is not None:
+        g_ne, g_phi = _f64(guess[0]), _f64(guess[1])
+    lib().or_solve_batch(C.byref(P), C.byref(k.s), _ptr(g_ne), _ptr(g_phi), _ptr(ne), _ptr(phi),
+                         _ptr(status), _ptr(newton), _ptr(krylov), _ptr(evals), _ptr(fres),
+                         int(threads))
+    return dict(ne=ne, phi=phi, status=status, newton_it=newton, krylov_it=krylov,
+                res_evals=evals, final_res=fres)
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
