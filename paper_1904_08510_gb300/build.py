@@ -1,0 +1,97 @@
+"""Compile the CUDA library libsdcef.so for sm_103a (in-tree, no cmake).
+
+The solver kernel is instantiated once per (threads per column, Krylov
+precision) pair in its own translation unit; the units compile in parallel
+and are linked with the host-side C ABI into one shared library.
+"""
+from __future__ import annotations
+
+import hashlib
+import os
+import shutil
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libsdcef.so")
+INCLUDE = os.path.join(ROOT, "include")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+INSTANCES = [(tpb, kr) for kr in ("double", "float") for tpb in (32, 64, 128, 256)]
+
+
+def _nvcc() -> str:
+    for c in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libsdcef.so")
+
+
+def _sources():
+    out = []
+    for d in (CSRC, INCLUDE):
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".cu", ".cuh", ".h")):
+                out.append(os.path.join(d, f))
+    return out
+
+
+def _digest() -> str:
+    h = hashlib.sha256()
+    for p in _sources():
+        h.update(p.encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Build (or reuse) libsdcef.so; returns its path."""
+    os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "libsdcef.stamp")
+    dig = _digest()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
+        return LIB
+    nvcc = _nvcc()
+    jobs = []
+    for tpb, kr in INSTANCES:
+        obj = os.path.join(BUILD, f"kern_{tpb}_{kr}.o")
+        cmd = [nvcc, *ARCH, *FLAGS, f"-DSDCEF_TPB={tpb}", f"-DSDCEF_KR={kr}"]
+        if (tpb, kr) == INSTANCES[0]:
+            cmd.append("-DSDCEF_WITH_ORDER")
+        cmd += ["-c", os.path.join(CSRC, "kern_inst.cu"), "-o", obj]
+        jobs.append((obj, cmd))
+    host_obj = os.path.join(BUILD, "sdcef_host.o")
+    jobs.append((host_obj, [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, "sdcef.cu"), "-o", host_obj]))
+
+    def run(job):
+        obj, cmd = job
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {obj}:\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    workers = max(1, min(len(jobs), os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        objs = list(ex.map(run, jobs))
+    tmp = LIB + f".{os.getpid()}.tmp"
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(dig)
+    return LIB
+
+
+if __name__ == "__main__":
+    import sys
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,17 @@
+// Explicit instantiation of the solver kernel for one (threads per column,
+// Krylov precision) pair, selected with -DSDCEF_TPB=... -DSDCEF_KR=...; the
+// order kernel is built in the TU compiled with -DSDCEF_WITH_ORDER.
+#define SDCEF_KERNEL_TU
+#include "solver.cuh"
+
+namespace sdcef_impl {
+template cudaError_t launch_t<SDCEF_TPB, SDCEF_KR>(const KArgs&, int, size_t, cudaStream_t);
+template int occupancy_t<SDCEF_TPB, SDCEF_KR>(size_t);
+#ifdef SDCEF_WITH_ORDER
+cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int shift, int* order,
+                         cudaStream_t st) {
+  order_kernel<<<1, 1024, nbins * sizeof(int), st>>>(col_off, ncol, nbins, shift, order);
+  return cudaGetLastError();
+}
+#endif
+}  // namespace sdcef_impl

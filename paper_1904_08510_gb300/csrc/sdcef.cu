@@ -1,0 +1,456 @@
+// C ABI of the batched JFNK solver (host side): argument validation,
+// workspace ownership, launch configuration and the host-buffer entry point.
+// The kernels are in solver.cuh / kern_inst.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sdcef.h"
+#include "solver.cuh"
+
+using namespace sdcef_impl;
+
+namespace {
+thread_local std::string g_err;
+int set_err(int code, const std::string& m) {
+  g_err = m;
+  return code;
+}
+}  // namespace
+
+// ============================================================================
+// Host side
+// ============================================================================
+struct sdcef_ctx {
+  sdcef_params p;
+  int64_t max_cols, max_cells;
+  int max_col_cells;
+  int m_cap;
+  cudaStream_t stream;
+  int device, sms;
+  char* ws;
+  size_t ws_bytes;
+  int nslots;
+  int* queue;     // 1 int
+  int* order;     // max_cols ints
+  int launches;
+  // host-call staging
+  char* stage;
+  size_t stage_bytes;
+};
+
+namespace {
+
+int tpb_for(const sdcef_params& p, int max_col_cells) {
+  if (p.threads_per_column) return p.threads_per_column;
+  (void)max_col_cells;
+  return 128;
+}
+
+size_t smem_bytes(int tpb, int m, size_t kr) {
+  const int nw = tpb / 32;
+  size_t d = (size_t)(nw + 1) * 40 + 4 * tpb + (m + 1) * m + (m + 1) + 3 * m + m + 2;
+  return d * sizeof(double) + 12 * (size_t)tpb * kr + 64;
+}
+
+int check_params(const sdcef_params* p, int m_cap) {
+  if (!p) return set_err(SDCEF_ERR_INVALID, "params is NULL");
+  if (!(p->eps_F > 0.0) || !(p->gamma > 0.0 && p->gamma < 1.0) || !(p->mobility > 0.0) ||
+      !(p->ls_alpha >= 0.0 && p->ls_alpha < 1.0) || !(p->eps_r > 0.0) || !(p->eps_X >= 0.0))
+    return set_err(SDCEF_ERR_INVALID, "params: eps_F, gamma, mobility, ls_alpha, eps_r out of range");
+  if (p->restart_m < 1 || p->restart_m > SDCEF_MAX_RESTART || (m_cap > 0 && p->restart_m > m_cap))
+    return set_err(SDCEF_ERR_INVALID, "params: restart_m out of range");
+  if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0)
+    return set_err(SDCEF_ERR_INVALID, "params: iteration caps out of range");
+  if (p->precision != SDCEF_FP64 && p->precision != SDCEF_MIXED)
+    return set_err(SDCEF_ERR_INVALID, "params: precision");
+  if (p->precond != SDCEF_PREC_EXACT && p->precond != SDCEF_PREC_RECAST &&
+      p->precond != SDCEF_PREC_NONE)
+    return set_err(SDCEF_ERR_INVALID, "params: precond");
+  if (p->bc_electron != SDCEF_BC_ABSORBING && p->bc_electron != SDCEF_BC_ZERO_GRADIENT)
+    return set_err(SDCEF_ERR_INVALID, "params: bc_electron");
+  int t = p->threads_per_column;
+  if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256)
+    return set_err(SDCEF_ERR_INVALID, "params: threads_per_column must be 0, 32, 64, 128 or 256");
+  return SDCEF_SUCCESS;
+}
+
+template <typename KR>
+cudaError_t launch_kr(int tpb, const KArgs& a, int grid, size_t smem, cudaStream_t st) {
+  switch (tpb) {
+    case 32: return launch_t<32, KR>(a, grid, smem, st);
+    case 64: return launch_t<64, KR>(a, grid, smem, st);
+    case 128: return launch_t<128, KR>(a, grid, smem, st);
+    case 256: return launch_t<256, KR>(a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename KR>
+int occupancy_kr(int tpb, size_t smem) {
+  switch (tpb) {
+    case 32: return occupancy_t<32, KR>(smem);
+    case 64: return occupancy_t<64, KR>(smem);
+    case 128: return occupancy_t<128, KR>(smem);
+    case 256: return occupancy_t<256, KR>(smem);
+  }
+  return 1;
+}
+
+int validate_batch(const sdcef_ctx* ctx, const sdcef_batch* b, bool need_solve_inputs) {
+  if (!b) return set_err(SDCEF_ERR_INVALID, "batch is NULL");
+  if (b->ncol < 0) return set_err(SDCEF_ERR_INVALID, "batch: ncol < 0");
+  if (b->ncol > ctx->max_cols) return set_err(SDCEF_ERR_CAPACITY, "batch: ncol exceeds max_cols");
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (!b->col_off || !b->length || !b->dt || !b->v_left || !b->v_right || !b->T)
+    return set_err(SDCEF_ERR_INVALID, "batch: required pointer is NULL");
+  if (need_solve_inputs && (!b->ne_old || !b->phi_old))
+    return set_err(SDCEF_ERR_INVALID, "batch: ne_old / phi_old is NULL");
+  if (b->n_species < 0 || b->n_species > SDCEF_MAX_SPECIES)
+    return set_err(SDCEF_ERR_INVALID, "batch: n_species out of range");
+  if (b->n_species > 0 && (!b->valence || !b->n_ion))
+    return set_err(SDCEF_ERR_INVALID, "batch: valence / n_ion is NULL");
+  return SDCEF_SUCCESS;
+}
+
+// Fill kernel args shared by all modes.
+KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb, size_t kr) {
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ncol = b->ncol;
+  a.col_off = b->col_off;
+  a.length = b->length;
+  a.dt = b->dt;
+  a.vl = b->v_left;
+  a.vr = b->v_right;
+  a.ne_old = b->ne_old;
+  a.phi_old = b->phi_old;
+  a.nsp = b->n_species;
+  for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
+  a.n_ion = b->n_ion;
+  a.T = b->T;
+  a.u = b->u_adv;
+  a.ire = b->i_re;
+  a.ne_g = b->ne_guess;
+  a.phi_g = b->phi_guess;
+  a.ws = ctx->ws;
+  const int kmax = (ctx->max_col_cells + tpb - 1) / tpb;
+  a.kmax = kmax;
+  a.PL = (size_t)kmax * tpb;
+  a.slot_bytes = kr == 8 ? slot_bytes_for<double>(a.PL, ctx->m_cap, tpb)
+                         : slot_bytes_for<float>(a.PL, ctx->m_cap, tpb);
+  a.max_col_cells = ctx->max_col_cells;
+  a.queue = ctx->queue;
+  const sdcef_params& p = ctx->p;
+  a.p.eps_F = p.eps_F;
+  a.p.eps_X = p.eps_X;
+  a.p.gamma = p.gamma;
+  a.p.mu = p.mobility;
+  a.p.ls_alpha = p.ls_alpha;
+  a.p.kap = kEps0 * p.eps_r / kQe;
+  a.p.m = ctx->m_cap;   // plane layout uses the capacity; iteration uses restart_m
+  a.p.max_newton = p.max_newton;
+  a.p.max_krylov = p.max_krylov;
+  a.p.max_ls = p.max_linesearch;
+  a.p.bc = p.bc_electron;
+  a.p.precond = p.precond;
+  return a;
+}
+
+int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
+  const bool fp32 = ctx->p.precision == SDCEF_MIXED;
+  const size_t kr = fp32 ? 4 : 8;
+  // restart length used by the iteration (planes are laid out for m_cap)
+  const int m_run = ctx->p.restart_m;
+  a.p.m = m_run;
+  const size_t smem = smem_bytes(tpb, m_run, kr);
+  // slot layout must use the same m as the device code: recompute with m_run
+  a.slot_bytes = fp32 ? slot_bytes_for<float>(a.PL, m_run, tpb) : slot_bytes_for<double>(a.PL, m_run, tpb);
+  int per_sm = fp32 ? occupancy_kr<float>(tpb, smem) : occupancy_kr<double>(tpb, smem);
+  int64_t slots_fit = (int64_t)(ctx->ws_bytes / a.slot_bytes);
+  int grid = (int)std::min<int64_t>({(int64_t)per_sm * ctx->sms, a.ncol, slots_fit});
+  if (grid < 1) return set_err(SDCEF_ERR_CAPACITY, "workspace too small for one column slot");
+  cudaError_t e = cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  ctx->launches = 0;
+  if (a.mode == MODE_SOLVE && a.ncol > 1) {
+    int shift = 4;
+    while ((ctx->max_col_cells >> shift) + 1 > 4096) ++shift;
+    const int nbins = (ctx->max_col_cells >> shift) + 1;
+    e = launch_order(a.col_off, a.ncol, nbins, shift, ctx->order, ctx->stream);
+    if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+    a.order = ctx->order;
+    ++ctx->launches;
+  }
+  e = fp32 ? launch_kr<float>(tpb, a, grid, smem, ctx->stream)
+           : launch_kr<double>(tpb, a, grid, smem, ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  ++ctx->launches;
+  return SDCEF_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sdcef_default_params(sdcef_params* p) {
+  if (!p) return;
+  p->eps_F = 1e-10;
+  p->eps_X = 0.0;
+  p->gamma = 1e-4;
+  p->mobility = 0.4;
+  p->ls_alpha = 1e-4;
+  p->eps_r = 1.0;
+  p->restart_m = 8;
+  p->max_newton = 50;
+  p->max_krylov = 200;
+  p->max_linesearch = 20;
+  p->precision = SDCEF_FP64;
+  p->precond = SDCEF_PREC_EXACT;
+  p->bc_electron = SDCEF_BC_ABSORBING;
+  p->threads_per_column = 0;
+}
+
+const char* sdcef_last_error(void) { return g_err.c_str(); }
+
+int sdcef_create(sdcef_ctx** out, const sdcef_params* p, int64_t max_cols, int64_t max_cells,
+                 int max_col_cells, void* stream) {
+  if (!out) return set_err(SDCEF_ERR_INVALID, "out is NULL");
+  int rc = check_params(p, 0);
+  if (rc) return rc;
+  if (max_cols < 1 || max_cells < 2 || max_col_cells < 2 || max_col_cells > (1 << 20) ||
+      (int64_t)max_col_cells > max_cells)
+    return set_err(SDCEF_ERR_INVALID, "create: sizes out of range");
+  sdcef_ctx* c = new sdcef_ctx();
+  memset(c, 0, sizeof(*c));
+  c->p = *p;
+  c->max_cols = max_cols;
+  c->max_cells = max_cells;
+  c->max_col_cells = max_col_cells;
+  c->m_cap = p->restart_m;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  // workspace: enough slots for the widest configuration at 2 CTAs per SM
+  // (FP64 planes, smallest thread count gives the largest per-slot size)
+  size_t best = 0;
+  for (int tpb : {32, 64, 128, 256}) {
+    const size_t PL = (size_t)((max_col_cells + tpb - 1) / tpb) * tpb;
+    best = std::max(best, slot_bytes_for<double>(PL, c->m_cap, tpb));
+  }
+  int64_t nslots = std::min<int64_t>((int64_t)c->sms * 4, max_cols);
+  c->nslots = (int)nslots;
+  c->ws_bytes = best * (size_t)nslots;
+  e = cudaMalloc((void**)&c->ws, c->ws_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->queue, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->order, sizeof(int) * (size_t)max_cols);
+  if (e != cudaSuccess) {
+    if (c->ws) cudaFree(c->ws);
+    if (c->queue) cudaFree(c->queue);
+    if (c->order) cudaFree(c->order);
+    delete c;
+    return set_err(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
+  }
+  *out = c;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_set_params(sdcef_ctx* ctx, const sdcef_params* p) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = check_params(p, ctx->m_cap);
+  if (rc) return rc;
+  ctx->p = *p;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_destroy(sdcef_ctx* ctx) {
+  if (!ctx) return SDCEF_SUCCESS;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->ws);
+  cudaFree(ctx->queue);
+  cudaFree(ctx->order);
+  if (ctx->stage) cudaFree(ctx->stage);
+  delete ctx;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_last_launch_count(const sdcef_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, b, true);
+  if (rc) return rc;
+  if (b->ncol == 0) { ctx->launches = 0; return SDCEF_SUCCESS; }
+  if (!out || !out->ne_out || !out->phi_out) return set_err(SDCEF_ERR_INVALID, "result: ne_out / phi_out is NULL");
+  const int tpb = tpb_for(ctx->p, ctx->max_col_cells);
+  const size_t kr = ctx->p.precision == SDCEF_MIXED ? 4 : 8;
+  KArgs a = base_args(ctx, b, tpb, kr);
+  a.mode = MODE_SOLVE;
+  a.ne_out = out->ne_out;
+  a.phi_out = out->phi_out;
+  a.status = out->status;
+  a.newton_it = out->newton_it;
+  a.krylov_it = out->krylov_it;
+  a.res_evals = out->res_evals;
+  a.final_res = out->final_res;
+  return run(ctx, a, tpb);
+}
+
+int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne, const double* phi,
+                         double* F_e, double* F_phi) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, b, false);
+  if (rc) return rc;
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (!ne || !phi || !F_e || !F_phi) return set_err(SDCEF_ERR_INVALID, "residual: NULL array");
+  const int tpb = tpb_for(ctx->p, ctx->max_col_cells);
+  const size_t kr = ctx->p.precision == SDCEF_MIXED ? 4 : 8;
+  KArgs a = base_args(ctx, b, tpb, kr);
+  // set-up reads ne_old / phi_old; point them at X when absent
+  if (!a.ne_old) a.ne_old = ne;
+  if (!a.phi_old) a.phi_old = phi;
+  a.mode = MODE_RESIDUAL;
+  a.x_ne = ne;
+  a.x_phi = phi;
+  a.o1 = F_e;
+  a.o2 = F_phi;
+  return run(ctx, a, tpb);
+}
+
+int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
+                              const double* phi, const double* r_e, const double* r_phi,
+                              double* x_e, double* x_phi) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, b, true);
+  if (rc) return rc;
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (!ne || !phi || !r_e || !r_phi || !x_e || !x_phi)
+    return set_err(SDCEF_ERR_INVALID, "precond: NULL array");
+  const int tpb = tpb_for(ctx->p, ctx->max_col_cells);
+  const size_t kr = ctx->p.precision == SDCEF_MIXED ? 4 : 8;
+  KArgs a = base_args(ctx, b, tpb, kr);
+  a.mode = MODE_PRECOND;
+  a.x_ne = ne;
+  a.x_phi = phi;
+  a.r_e = r_e;
+  a.r_phi = r_phi;
+  a.o1 = x_e;
+  a.o2 = x_phi;
+  return run(ctx, a, tpb);
+}
+
+int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_result* ho) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, hb, true);
+  if (rc) return rc;
+  if (!ho || !ho->ne_out || !ho->phi_out) return set_err(SDCEF_ERR_INVALID, "result: ne_out / phi_out is NULL");
+  const int64_t ncol = hb->ncol;
+  if (ncol == 0) return SDCEF_SUCCESS;
+  const int64_t cells = hb->col_off[ncol];
+  if (cells > ctx->max_cells || cells < 0) return set_err(SDCEF_ERR_CAPACITY, "batch: cells exceed max_cells");
+  const int nsp = hb->n_species;
+  // staging layout (bytes)
+  struct Item { const void* src; void* dst_host; size_t bytes; };
+  size_t need = 0;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t c8 = (size_t)cells * 8, n8 = (size_t)ncol * 8, n4 = (size_t)ncol * 4;
+  size_t o_off = need; need += al((size_t)(ncol + 1) * 8);
+  size_t o_len = need; need += al(n8);
+  size_t o_dt = need; need += al(n8);
+  size_t o_vl = need; need += al(n8);
+  size_t o_vr = need; need += al(n8);
+  size_t o_ne = need; need += al(c8);
+  size_t o_ph = need; need += al(c8);
+  size_t o_ion = need; need += al(c8 * (size_t)std::max(nsp, 1));
+  size_t o_T = need; need += al(c8);
+  size_t o_u = need; if (hb->u_adv) need += al(c8);
+  size_t o_ir = need; if (hb->i_re) need += al(c8);
+  size_t o_ng = need; if (hb->ne_guess) need += al(c8);
+  size_t o_pg = need; if (hb->phi_guess) need += al(c8);
+  size_t o_neo = need; need += al(c8);
+  size_t o_pho = need; need += al(c8);
+  size_t o_st = need; need += al(n4);
+  size_t o_nt = need; need += al(n4);
+  size_t o_kt = need; need += al(n4);
+  size_t o_re = need; need += al(n4);
+  size_t o_fr = need; need += al(n8);
+  if (need > ctx->stage_bytes) {
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    // sized for the context capacity so later calls never reallocate
+    size_t cap = need * 2;
+    cudaError_t e = cudaMalloc((void**)&ctx->stage, cap);
+    if (e != cudaSuccess) return set_err(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
+    ctx->stage_bytes = cap;
+  }
+  char* d = ctx->stage;
+  cudaStream_t st = ctx->stream;
+  auto h2d = [&](size_t o, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(d + o, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = h2d(o_off, hb->col_off, (size_t)(ncol + 1) * 8);
+  if (e == cudaSuccess) e = h2d(o_len, hb->length, n8);
+  if (e == cudaSuccess) e = h2d(o_dt, hb->dt, n8);
+  if (e == cudaSuccess) e = h2d(o_vl, hb->v_left, n8);
+  if (e == cudaSuccess) e = h2d(o_vr, hb->v_right, n8);
+  if (e == cudaSuccess) e = h2d(o_ne, hb->ne_old, c8);
+  if (e == cudaSuccess) e = h2d(o_ph, hb->phi_old, c8);
+  if (e == cudaSuccess && nsp > 0) e = h2d(o_ion, hb->n_ion, c8 * nsp);
+  if (e == cudaSuccess) e = h2d(o_T, hb->T, c8);
+  if (e == cudaSuccess && hb->u_adv) e = h2d(o_u, hb->u_adv, c8);
+  if (e == cudaSuccess && hb->i_re) e = h2d(o_ir, hb->i_re, c8);
+  if (e == cudaSuccess && hb->ne_guess) e = h2d(o_ng, hb->ne_guess, c8);
+  if (e == cudaSuccess && hb->phi_guess) e = h2d(o_pg, hb->phi_guess, c8);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  sdcef_batch db = *hb;
+  db.col_off = (const int64_t*)(d + o_off);
+  db.length = (const double*)(d + o_len);
+  db.dt = (const double*)(d + o_dt);
+  db.v_left = (const double*)(d + o_vl);
+  db.v_right = (const double*)(d + o_vr);
+  db.ne_old = (const double*)(d + o_ne);
+  db.phi_old = (const double*)(d + o_ph);
+  db.n_ion = nsp > 0 ? (const double*)(d + o_ion) : nullptr;
+  db.T = (const double*)(d + o_T);
+  db.rho = nullptr;
+  db.u_adv = hb->u_adv ? (const double*)(d + o_u) : nullptr;
+  db.i_re = hb->i_re ? (const double*)(d + o_ir) : nullptr;
+  db.ne_guess = hb->ne_guess ? (const double*)(d + o_ng) : nullptr;
+  db.phi_guess = hb->phi_guess ? (const double*)(d + o_pg) : nullptr;
+  sdcef_result dr;
+  dr.ne_out = (double*)(d + o_neo);
+  dr.phi_out = (double*)(d + o_pho);
+  dr.status = (int*)(d + o_st);
+  dr.newton_it = (int*)(d + o_nt);
+  dr.krylov_it = (int*)(d + o_kt);
+  dr.res_evals = (int*)(d + o_re);
+  dr.final_res = (double*)(d + o_fr);
+  rc = sdcef_solve_batch(ctx, &db, &dr);
+  if (rc) return rc;
+  auto d2h = [&](void* dst, size_t o, size_t bytes) {
+    return dst ? cudaMemcpyAsync(dst, d + o, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+  };
+  e = d2h(ho->ne_out, o_neo, c8);
+  if (e == cudaSuccess) e = d2h(ho->phi_out, o_pho, c8);
+  if (e == cudaSuccess) e = d2h(ho->status, o_st, n4);
+  if (e == cudaSuccess) e = d2h(ho->newton_it, o_nt, n4);
+  if (e == cudaSuccess) e = d2h(ho->krylov_it, o_kt, n4);
+  if (e == cudaSuccess) e = d2h(ho->res_evals, o_re, n4);
+  if (e == cudaSuccess) e = d2h(ho->final_res, o_fr, n8);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  return SDCEF_SUCCESS;
+}
+
+}  // extern "C"

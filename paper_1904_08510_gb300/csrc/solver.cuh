@@ -1,0 +1,1139 @@
+// Device code of the batched JFNK solver: kernel arguments, workspace layout,
+// residual (Eq. nls), finite-difference Jacobian-vector product
+// (Eq. jf_dfapprox), preconditioner factorisation/application (Eq. prec,
+// Eq. prec_recast), right-preconditioned GMRES and the Newton driver of
+// Algorithm 2. Kernel templates are instantiated in kern_inst.cu, one
+// translation unit per (threads per column, Krylov precision).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/sdcef.h"
+#include "blockalg.cuh"
+
+namespace sdcef_impl {
+using namespace sdcef;
+
+// SI constants (CODATA 2018)
+constexpr double kQe = 1.602176634e-19;
+constexpr double kKb = 1.380649e-23;
+constexpr double kEps0 = 8.8541878128e-12;
+// lambda_FD = eps_mach^(1/3) for IEEE double (Eq. jf_dfapprox)
+constexpr double kLambdaFD = 6.0554544523933395e-06;
+
+
+// --------------------------------------------------------------------------
+// Kernel arguments
+// --------------------------------------------------------------------------
+struct DevParams {
+  double eps_F, eps_X, gamma, mu, ls_alpha, kap;   // kap = eps0 eps_r / e
+  int m, max_newton, max_krylov, max_ls, bc, precond;
+};
+
+enum { MODE_SOLVE = 0, MODE_RESIDUAL = 1, MODE_PRECOND = 2 };
+
+struct KArgs {
+  int64_t ncol;
+  const int64_t* col_off;
+  const double *length, *dt, *vl, *vr, *ne_old, *phi_old;
+  int nsp;
+  int val[SDCEF_MAX_SPECIES];
+  const double *n_ion, *T, *u, *ire, *ne_g, *phi_g;
+  double *ne_out, *phi_out;
+  int *status, *newton_it, *krylov_it, *res_evals;
+  double* final_res;
+  // workspace
+  char* ws;
+  size_t slot_bytes;
+  size_t PL;          // elements per plane (kmax * TPB)
+  int kmax;           // rows per thread capacity
+  int max_col_cells;
+  int* queue;
+  const int* order;
+  DevParams p;
+  int mode;
+  // test modes: state X, residual-space vector r, outputs
+  const double *x_ne, *x_phi, *r_e, *r_phi;
+  double *o1, *o2;
+};
+
+// FP64 planes of a slot
+enum {
+  PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_HD, PD_UF,
+  PD_FACE0,               // 4 planes: face derivative set 0 (a0, a1, b0, b1), scaled
+  PD_FACE1 = PD_FACE0 + 4,
+  PD_COUNT = PD_FACE1 + 4
+};
+// Krylov planes (type KR): V[(m+1)*2], W[2], Z[2], XH[2], T[2]
+// Factor planes (type KR): 20
+constexpr int kFactorPlanes = 20;
+constexpr int kScalPerThread = 80;
+
+template <typename KR>
+__host__ __device__ inline size_t slot_bytes_for(size_t PL, int m, int tpb) {
+  size_t b = (size_t)PD_COUNT * PL * sizeof(double);
+  b += (size_t)(2 * (m + 1) + 8 + kFactorPlanes) * PL * sizeof(KR);
+  b += (size_t)kScalPerThread * tpb * sizeof(KR);
+  return (b + 255) & ~(size_t)255;
+}
+
+
+// Launch / occupancy entry points, one instantiation per kernel TU.
+template <int TPB, typename KR>
+cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st);
+template <int TPB, typename KR>
+int occupancy_t(size_t smem);
+cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int shift, int* order,
+                         cudaStream_t st);
+
+#ifdef SDCEF_KERNEL_TU
+// --------------------------------------------------------------------------
+// Block reductions
+// --------------------------------------------------------------------------
+template <int TPB>
+__device__ __forceinline__ void block_reduce(double* v, int nv, bool is_max, double* red) {
+  constexpr int NW = TPB / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < nv; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = is_max ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) red[w * 40 + k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double x = red[threadIdx.x];
+    for (int q = 1; q < NW; ++q) {
+      double y = red[q * 40 + threadIdx.x];
+      x = is_max ? fmax(x, y) : x + y;
+    }
+    red[NW * 40 + threadIdx.x] = x;
+  }
+  __syncthreads();
+  for (int k = 0; k < nv; ++k) v[k] = red[NW * 40 + k];
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// Bernoulli function of the Scharfetter-Gummel flux. For a = |Pe| >= 0:
+// b = B(a) = a / (e^a - 1) and the derivative B'(a) = (1 - a - b) / (e^a - 1).
+// B(-a) = a + B(a) and B'(-a) = -1 - B'(a) give the other branch without
+// cancellation, so one expm1 and one division serve both.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void bern_pos(double a, double* b, double* db) {
+  if (a < 1e-3) {
+    double a2 = a * a;
+    *b = 1.0 - 0.5 * a + a2 * (1.0 / 12.0) - a2 * a2 * (1.0 / 720.0);
+    *db = -0.5 + a * (1.0 / 6.0) - a * a2 * (1.0 / 180.0);
+  } else {
+    double E = expm1(a);
+    double iE = 1.0 / E;
+    *b = a * iE;
+    *db = (1.0 - a - *b) * iE;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Per-CTA column context (shared memory) and per-thread geometry
+// --------------------------------------------------------------------------
+struct ColShared {
+  int64_t col, off;
+  int N, K, tact, bad;
+  double h, inv_h, dt, vl, vr, g0, ubl, ubr;
+  double sn, sp, sFe, sFp;
+  double vL[2], vR[2];      // electrode-face electron velocities of face sets 0/1
+  double xnorm;
+  int flag;
+  double gam, beta0;
+  int conv, stop;
+  double scal[8];
+};
+
+struct Geo {
+  int tid, kt, t0, N, K, tact;
+};
+
+template <int TPB, typename KR>
+struct Slot {
+  double* d;    // FP64 planes
+  KR* k;        // Krylov planes
+  KR* f;        // factor planes
+  KR* s;        // per-thread scalars
+  size_t PL;
+  int m;
+  __device__ double* pd(int i) const { return d + (size_t)i * PL; }
+  __device__ KR* V(int i, int comp) const { return k + (size_t)(2 * i + comp) * PL; }
+  __device__ KR* W(int comp) const { return k + (size_t)(2 * (m + 1) + comp) * PL; }
+  __device__ KR* Z(int comp) const { return k + (size_t)(2 * (m + 1) + 2 + comp) * PL; }
+  __device__ KR* XH(int comp) const { return k + (size_t)(2 * (m + 1) + 4 + comp) * PL; }
+  __device__ KR* T(int comp) const { return k + (size_t)(2 * (m + 1) + 6 + comp) * PL; }
+};
+
+template <int TPB, typename KR>
+__device__ Slot<TPB, KR> make_slot(const KArgs& a, int slot) {
+  Slot<TPB, KR> s;
+  char* base = a.ws + (size_t)slot * a.slot_bytes;
+  s.PL = a.PL;
+  s.m = a.p.m;
+  s.d = (double*)base;
+  s.k = (KR*)(base + (size_t)PD_COUNT * a.PL * sizeof(double));
+  s.f = s.k + (size_t)(2 * (a.p.m + 1) + 8) * a.PL;
+  s.s = s.f + (size_t)kFactorPlanes * a.PL;
+  return s;
+}
+
+__device__ __forceinline__ size_t ix(int j, int tid, int TPB) { return (size_t)j * TPB + tid; }
+
+// --------------------------------------------------------------------------
+// Residual F(X) of Eq. nls on (n, psi), phi = phi_ref + psi.
+// State of local row j: n = nb[j] + cn * dn[j], psi = pb[j] + cp * dp[j]
+// (dn/dp may be null). Output modes:
+//   OUT_F:   write F to (fe_o, fp_o), face derivative set `fs`, electrode
+//            velocities; returns raw max|F_e|, max|F_phi|, sum F_e^2, sum F_phi^2
+//   OUT_JVP: w = (F - F_ref) / (eps S_F) into Krylov planes (we, wp)
+// --------------------------------------------------------------------------
+enum { OUT_F = 0, OUT_JVP = 1 };
+
+template <int TPB, typename KR>
+__device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR>& S,
+                         const double* nb, const double* pb, const KR* dn, const KR* dp,
+                         double cn, double cp, int out_mode, double* fe_o, double* fp_o, int fs,
+                         const double* fe_ref, const double* fp_ref, KR* we, KR* wp, double ieps,
+                         double* halo, double* red, double* norms) {
+  const int tid = g.tid, kt = g.kt, N = g.N;
+  const double ih = cs.inv_h, dt = cs.dt, g0 = cs.g0, mu = a.p.mu, kap = a.p.kap;
+  const double r = dt * ih;
+  const double* FEX = S.pd(PD_FEX);
+  const double* FPHI = S.pd(PD_FPHI);
+  const double* DH = S.pd(PD_DH);
+  const double* HD = S.pd(PD_HD);
+  const double* UF = a.u ? S.pd(PD_UF) : nullptr;
+  double* face = S.pd(PD_FACE0 + 4 * fs);
+  auto st_n = [&](int j) {
+    double v = nb[ix(j, tid, TPB)];
+    if (dn) v = fma(cn, (double)dn[ix(j, tid, TPB)], v);
+    return v;
+  };
+  auto st_p = [&](int j) {
+    double v = pb[ix(j, tid, TPB)];
+    if (dp) v = fma(cp, (double)dp[ix(j, tid, TPB)], v);
+    return v;
+  };
+  // 1. halo: first and last cell state of each thread
+  if (kt > 0) {
+    halo[0 * TPB + tid] = st_n(0);
+    halo[1 * TPB + tid] = st_p(0);
+    halo[2 * TPB + tid] = st_n(kt - 1);
+    halo[3 * TPB + tid] = st_p(kt - 1);
+  }
+  __syncthreads();
+  double mxe = 0.0, mxp = 0.0, sse = 0.0, ssp = 0.0;
+  double gam_left = 0.0, d_left = 0.0;   // left-face values of row 0 (thread 0 only)
+  double pend_e = 0.0, pend_p = 0.0;     // row-0 partial residuals
+  double gam_prev = 0.0, d_prev = 0.0, last_gam = 0.0, last_d = 0.0;
+  if (kt > 0) {
+    double n_i = st_n(0), p_i = st_p(0);
+    if (g.t0 == 0) {
+      // left electrode face: G_L - g0 = (9 psi_0 - psi_1) / (3h)
+      double p1 = kt >= 2 ? st_p(1) : halo[1 * TPB + tid + 1];
+      double dL = (9.0 * p_i - p1) * (ih / 3.0);
+      double vL = cs.ubl + mu * (g0 + dL);
+      bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0;
+      gam_left = act ? vL * n_i : 0.0;
+      d_left = dL;
+      if (out_mode == OUT_F) cs.vL[fs] = vL;
+    }
+    for (int j = 0; j < kt; ++j) {
+      const int i = g.t0 + j;
+      double n_n, p_n, gam, dd;
+      if (i < N - 1) {
+        n_n = (j + 1 < kt) ? st_n(j + 1) : halo[0 * TPB + tid + 1];
+        p_n = (j + 1 < kt) ? st_p(j + 1) : halo[1 * TPB + tid + 1];
+        dd = (p_n - p_i) * ih;
+        double v = (UF ? UF[ix(j, tid, TPB)] : 0.0) + mu * (g0 + dd);
+        double Pe = v * HD[ix(j, tid, TPB)];
+        double aa = fabs(Pe), b, db;
+        bern_pos(aa, &b, &db);
+        double Bp, Bm, dBp, dBm;   // B(Pe), B(-Pe) and derivatives
+        if (Pe >= 0.0) { Bp = b; Bm = aa + b; dBp = db; dBm = -1.0 - db; }
+        else { Bm = b; Bp = aa + b; dBm = db; dBp = -1.0 - db; }
+        const double dh = DH[ix(j, tid, TPB)];
+        gam = dh * (Bm * n_i - Bp * n_n);
+        if (out_mode == OUT_F) {
+          // r dGam/dn_i, r dGam/dn_{i+1}, r dGam/dpsi_i, r dGam/dpsi_{i+1} (unscaled)
+          double dg_n0 = dh * Bm, dg_n1 = -dh * Bp;
+          double dg_p1 = mu * ih * (-dBm * n_i - dBp * n_n);
+          face[0 * a.PL + ix(j, tid, TPB)] = r * dg_n0;
+          face[1 * a.PL + ix(j, tid, TPB)] = r * dg_n1;
+          face[2 * a.PL + ix(j, tid, TPB)] = -r * dg_p1;
+          face[3 * a.PL + ix(j, tid, TPB)] = r * dg_p1;
+        }
+      } else {
+        // right electrode face: G_R - g0 = (-9 psi_{N-1} + psi_{N-2}) / (3h)
+        double pm = (j >= 1) ? st_p(j - 1) : halo[3 * TPB + tid - 1];
+        dd = (-9.0 * p_i + pm) * (ih / 3.0);
+        double vR = cs.ubr + mu * (g0 + dd);
+        bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0;
+        gam = act ? vR * n_i : 0.0;
+        if (out_mode == OUT_F) cs.vR[fs] = vR;
+        n_n = 0.0;
+        p_n = 0.0;
+      }
+      const double fex = FEX[ix(j, tid, TPB)], fph = FPHI[ix(j, tid, TPB)];
+      double Fe, Fp;
+      if (j == 0) {
+        Fe = -n_i + fex - r * gam;     // + r * gam_left later
+        Fp = -n_i + fph + kap * ih * dd;
+        pend_e = Fe;
+        pend_p = Fp;
+      } else {
+        Fe = -n_i + fex - r * (gam - gam_prev);
+        Fp = -n_i + fph + kap * ih * (dd - d_prev);
+        if (out_mode == OUT_F) {
+          fe_o[ix(j, tid, TPB)] = Fe;
+          fp_o[ix(j, tid, TPB)] = Fp;
+          mxe = fmax(mxe, fabs(Fe));
+          mxp = fmax(mxp, fabs(Fp));
+          sse += Fe * Fe;
+          ssp += Fp * Fp;
+        } else {
+          we[ix(j, tid, TPB)] = (KR)((Fe - fe_ref[ix(j, tid, TPB)]) * ieps / cs.sFe);
+          wp[ix(j, tid, TPB)] = (KR)((Fp - fp_ref[ix(j, tid, TPB)]) * ieps / cs.sFp);
+        }
+      }
+      gam_prev = gam;
+      d_prev = dd;
+      n_i = n_n;
+      p_i = p_n;
+    }
+    last_gam = gam_prev;
+    last_d = d_prev;
+  }
+  __syncthreads();   // halo reads done
+  if (kt > 0) {
+    halo[0 * TPB + tid] = last_gam;
+    halo[1 * TPB + tid] = last_d;
+  }
+  __syncthreads();
+  if (kt > 0) {
+    if (g.t0 > 0) {
+      gam_left = halo[0 * TPB + tid - 1];
+      d_left = halo[1 * TPB + tid - 1];
+    }
+    double Fe = pend_e + r * gam_left;
+    double Fp = pend_p - kap * ih * d_left;
+    if (out_mode == OUT_F) {
+      fe_o[ix(0, tid, TPB)] = Fe;
+      fp_o[ix(0, tid, TPB)] = Fp;
+      mxe = fmax(mxe, fabs(Fe));
+      mxp = fmax(mxp, fabs(Fp));
+      sse += Fe * Fe;
+      ssp += Fp * Fp;
+    } else {
+      we[ix(0, tid, TPB)] = (KR)((Fe - fe_ref[ix(0, tid, TPB)]) * ieps / cs.sFe);
+      wp[ix(0, tid, TPB)] = (KR)((Fp - fp_ref[ix(0, tid, TPB)]) * ieps / cs.sFp);
+    }
+  }
+  if (out_mode == OUT_F) {
+    double mx[2] = {mxe, mxp};
+    // NaN-propagating max: fmax drops NaN, so fold non-finite into +inf
+    if (!(mx[0] <= 1.79e308)) mx[0] = INFINITY;
+    if (!(mx[1] <= 1.79e308)) mx[1] = INFINITY;
+    block_reduce<TPB>(mx, 2, true, red);
+    double ss[2] = {sse, ssp};
+    block_reduce<TPB>(ss, 2, false, red);
+    norms[0] = mx[0];
+    norms[1] = mx[1];
+    norms[2] = ss[0];
+    norms[3] = ss[1];
+  } else {
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// Scaled Jacobian row blocks (Eq. linear_nls), built from the stored face
+// derivatives of face set fs. Unknown order per cell: (n, psi).
+//   A = dF_e/dn, B = dF_e/dpsi, C = dF_phi/dn = -I, L = dF_phi/dpsi,
+// scaled: Ahat = A s_n/s_Fe, Bhat = B s_phi/s_Fe, Chat = -s_n/s_Fphi, Lhat = L s_phi/s_Fphi.
+// --------------------------------------------------------------------------
+struct RowJ {
+  double As, Ad, Au, Bs, Bd, Bu, Ls, Ld, Lu, C;
+};
+
+template <int TPB, typename KR>
+__device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColShared& cs,
+                                        const Slot<TPB, KR>& S, int fs, int j,
+                                        const double* lf /*left face (a0,a1,b0,b1)*/, double n_i,
+                                        double n_0, double n_last) {
+  (void)n_i;
+  const double* face = S.pd(PD_FACE0 + 4 * fs);
+  const int i = g.t0 + j, N = g.N;
+  const double ih = cs.inv_h, r = cs.dt * ih, mu = a.p.mu;
+  const double sl = cs.sp / cs.sFp;
+  const double kh2 = a.p.kap * ih * ih * sl;
+  RowJ R;
+  R.As = R.Au = R.Bs = R.Bu = 0.0;
+  R.Ad = -cs.sn / cs.sFe;
+  R.Bd = 0.0;
+  R.C = -cs.sn / cs.sFp;
+  const double sa = cs.sn / cs.sFe, sb = cs.sp / cs.sFe;
+  // right face (row i carries -r Gam_{i+1/2})
+  if (i < N - 1) {
+    R.Ad -= face[0 * a.PL + ix(j, g.tid, TPB)] * sa;
+    R.Au -= face[1 * a.PL + ix(j, g.tid, TPB)] * sa;
+    R.Bd -= face[2 * a.PL + ix(j, g.tid, TPB)] * sb;
+    R.Bu -= face[3 * a.PL + ix(j, g.tid, TPB)] * sb;
+  } else {
+    double vR = cs.vR[fs];
+    if (a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0) {
+      R.Ad -= r * vR * cs.sn / cs.sFe;
+      R.Bd -= r * n_last * mu * (-3.0 * ih) * cs.sp / cs.sFe;
+      R.Bs -= r * n_last * mu * (ih / 3.0) * cs.sp / cs.sFe;
+    }
+  }
+  // left face (row i carries +r Gam_{i-1/2})
+  if (i > 0) {
+    R.As += lf[0] * sa;
+    R.Ad += lf[1] * sa;
+    R.Bs += lf[2] * sb;
+    R.Bd += lf[3] * sb;
+  } else {
+    double vL = cs.vL[fs];
+    if (a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0) {
+      R.Ad += r * vL * cs.sn / cs.sFe;
+      R.Bd += r * n_0 * mu * (3.0 * ih) * cs.sp / cs.sFe;
+      R.Bu += r * n_0 * mu * (-ih / 3.0) * cs.sp / cs.sFe;
+    }
+  }
+  // Poisson stencil with the second-order electrode closure
+  if (i == 0) {
+    R.Ls = 0.0;
+    R.Ld = -4.0 * kh2;
+    R.Lu = (4.0 / 3.0) * kh2;
+  } else if (i == N - 1) {
+    R.Ls = (4.0 / 3.0) * kh2;
+    R.Ld = -4.0 * kh2;
+    R.Lu = 0.0;
+  } else {
+    R.Ls = kh2;
+    R.Ld = -2.0 * kh2;
+    R.Lu = kh2;
+  }
+  return R;
+}
+
+// --------------------------------------------------------------------------
+// Preconditioner: factorisation and application (scaled units).
+// --------------------------------------------------------------------------
+template <int TPB, typename KR>
+__device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR>& S,
+                            int fs, KR* sh, double* halo, bool* bad) {
+  const int tid = g.tid, kt = g.kt;
+  // left-face derivatives of each thread's first row = previous thread's last face
+  if (kt > 0) {
+    const double* face = S.pd(PD_FACE0 + 4 * fs);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) halo[q * TPB + tid] = face[q * a.PL + ix(kt - 1, tid, TPB)];
+  }
+  __syncthreads();
+  double lf0[4] = {0, 0, 0, 0};
+  if (kt > 0 && tid > 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lf0[q] = halo[q * TPB + tid - 1];
+  }
+  const double* NP = S.pd(PD_N);
+  const double n0 = (g.t0 == 0 && kt > 0) ? NP[ix(0, tid, TPB)] : 0.0;
+  const double nlast = (kt > 0 && g.t0 + kt == g.N) ? NP[ix(kt - 1, tid, TPB)] : 0.0;
+  const double* face = S.pd(PD_FACE0 + 4 * fs);
+  auto lface = [&](int j, double* lf) {
+    if (j == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lf[q] = lf0[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lf[q] = face[q * a.PL + ix(j - 1, tid, TPB)];
+    }
+  };
+  if (a.p.precond == SDCEF_PREC_EXACT) {
+    Planes<2, KR, TPB> F{S.f, S.PL};
+    Scal<2, KR, TPB> Sc{S.s};
+    auto rowf = [&](int j, Mat<2, KR>& M, Mat<2, KR>& D, Mat<2, KR>& U) {
+      double lf[4];
+      lface(j, lf);
+      RowJ R = jac_row<TPB, KR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      M.a[0] = (KR)R.As; M.a[1] = (KR)R.Bs; M.a[2] = KR(0); M.a[3] = (KR)R.Ls;
+      D.a[0] = (KR)R.Ad; D.a[1] = (KR)R.Bd; D.a[2] = (KR)R.C; D.a[3] = (KR)R.Ld;
+      U.a[0] = (KR)R.Au; U.a[1] = (KR)R.Bu; U.a[2] = KR(0); U.a[3] = (KR)R.Lu;
+    };
+    part_factor<2, KR, TPB>(F, Sc, kt, tid, g.tact, rowf, sh, bad);
+  } else if (a.p.precond == SDCEF_PREC_RECAST) {
+    // system 1: Ahat; system 2: S~hat = Lhat - (s_Fe/s_Fphi) Bhat; Bhat kept for the matvec
+    Planes<1, KR, TPB> F1{S.f, S.PL};
+    Planes<1, KR, TPB> F2{S.f + 5 * S.PL, S.PL};
+    KR* Bpl = S.f + 10 * S.PL;   // 3 planes: sub, dia, sup
+    Scal<1, KR, TPB> S1{S.s};
+    Scal<1, KR, TPB> S2{S.s + 40 * TPB};
+    const double rho = cs.sFe / cs.sFp;
+    auto row1 = [&](int j, Mat<1, KR>& M, Mat<1, KR>& D, Mat<1, KR>& U) {
+      double lf[4];
+      lface(j, lf);
+      RowJ R = jac_row<TPB, KR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      M.a[0] = (KR)R.As; D.a[0] = (KR)R.Ad; U.a[0] = (KR)R.Au;
+      Bpl[0 * S.PL + ix(j, tid, TPB)] = (KR)R.Bs;
+      Bpl[1 * S.PL + ix(j, tid, TPB)] = (KR)R.Bd;
+      Bpl[2 * S.PL + ix(j, tid, TPB)] = (KR)R.Bu;
+    };
+    part_factor<1, KR, TPB>(F1, S1, kt, tid, g.tact, row1, sh, bad);
+    auto row2 = [&](int j, Mat<1, KR>& M, Mat<1, KR>& D, Mat<1, KR>& U) {
+      double lf[4];
+      lface(j, lf);
+      RowJ R = jac_row<TPB, KR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      M.a[0] = (KR)(R.Ls - rho * R.Bs);
+      D.a[0] = (KR)(R.Ld - rho * R.Bd);
+      U.a[0] = (KR)(R.Lu - rho * R.Bu);
+    };
+    part_factor<1, KR, TPB>(F2, S2, kt, tid, g.tact, row2, sh, bad);
+  }
+  __syncthreads();
+}
+
+// z = Mhat^{-1} r (scaled units); in/out are Krylov planes (2 components each).
+// Returns ||z||_2^2 (block-reduced) if want_norm.
+template <int TPB, typename KR>
+__device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const ColShared& cs,
+                             const Slot<TPB, KR>& S, KR* re, KR* rp, KR* ze, KR* zp, KR* sh,
+                             double* red, bool want_norm) {
+  const int tid = g.tid, kt = g.kt;
+  if (a.p.precond == SDCEF_PREC_EXACT) {
+    Planes<2, KR, TPB> F{S.f, S.PL};
+    Scal<2, KR, TPB> Sc{S.s};
+    KR* rin[2] = {re, rp};
+    KR* out[2] = {ze, zp};
+    part_solve<2, KR, TPB>(F, Sc, rin, out, kt, tid, g.tact, sh);
+  } else if (a.p.precond == SDCEF_PREC_RECAST) {
+    Planes<1, KR, TPB> F1{S.f, S.PL};
+    Planes<1, KR, TPB> F2{S.f + 5 * S.PL, S.PL};
+    const KR* Bpl = S.f + 10 * S.PL;
+    Scal<1, KR, TPB> S1{S.s};
+    Scal<1, KR, TPB> S2{S.s + 40 * TPB};
+    const KR cfac = (KR)(cs.sn / cs.sFp);   // -Chat
+    // z1 = Ahat^{-1} r_e (into ze)
+    {
+      KR* rin[1] = {re};
+      KR* out[1] = {ze};
+      part_solve<1, KR, TPB>(F1, S1, rin, out, kt, tid, g.tact, sh);
+    }
+    // z2 = S~^{-1} (r_phi - Chat z1) (into zp)
+    for (int j = 0; j < kt; ++j) zp[ix(j, tid, TPB)] = rp[ix(j, tid, TPB)] + cfac * ze[ix(j, tid, TPB)];
+    {
+      KR* rin[1] = {zp};
+      KR* out[1] = {zp};
+      part_solve<1, KR, TPB>(F2, S2, rin, out, kt, tid, g.tact, sh);
+    }
+    // t = Bhat z2 (tridiagonal matvec with halo), then x1 = z1 - Ahat^{-1} t
+    KR* tpl = S.T(0);
+    {
+      KR* hb = sh;
+      if (kt > 0) {
+        hb[tid] = zp[ix(0, tid, TPB)];
+        hb[TPB + tid] = zp[ix(kt - 1, tid, TPB)];
+      }
+      __syncthreads();
+      for (int j = 0; j < kt; ++j) {
+        const int i = g.t0 + j;
+        KR zc = zp[ix(j, tid, TPB)];
+        KR zl = (i == 0) ? KR(0) : (j > 0 ? zp[ix(j - 1, tid, TPB)] : hb[TPB + tid - 1]);
+        KR zr = (i == g.N - 1) ? KR(0) : (j + 1 < kt ? zp[ix(j + 1, tid, TPB)] : hb[tid + 1]);
+        tpl[ix(j, tid, TPB)] = Bpl[0 * S.PL + ix(j, tid, TPB)] * zl +
+                               Bpl[1 * S.PL + ix(j, tid, TPB)] * zc +
+                               Bpl[2 * S.PL + ix(j, tid, TPB)] * zr;
+      }
+      __syncthreads();
+    }
+    {
+      KR* rin[1] = {tpl};
+      KR* out[1] = {tpl};
+      part_solve<1, KR, TPB>(F1, S1, rin, out, kt, tid, g.tact, sh);
+    }
+    for (int j = 0; j < kt; ++j) ze[ix(j, tid, TPB)] = ze[ix(j, tid, TPB)] - tpl[ix(j, tid, TPB)];
+  } else {
+    for (int j = 0; j < kt; ++j) {
+      ze[ix(j, tid, TPB)] = re[ix(j, tid, TPB)];
+      zp[ix(j, tid, TPB)] = rp[ix(j, tid, TPB)];
+    }
+  }
+  double nz = 0.0;
+  if (want_norm) {
+    double s = 0.0;
+    for (int j = 0; j < kt; ++j) {
+      double x = ze[ix(j, tid, TPB)], y = zp[ix(j, tid, TPB)];
+      s += x * x + y * y;
+    }
+    block_reduce<TPB>(&s, 1, false, red);
+    nz = s;
+  } else {
+    __syncthreads();
+  }
+  return nz;
+}
+
+// --------------------------------------------------------------------------
+// Column set-up: inputs into the slot, scaling, initial state.
+// Returns false if the column is rejected (BAD_INPUT).
+// --------------------------------------------------------------------------
+template <int TPB, typename KR>
+__device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs, const Slot<TPB, KR>& S,
+                             double* halo, double* red) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int64_t off = a.col_off[cs.col];
+    int64_t N = a.col_off[cs.col + 1] - off;
+    cs.off = off;
+    int bad = 0;
+    if (N < 2 || N > a.max_col_cells) bad = 1;
+    double L = a.length[cs.col], dt = a.dt[cs.col];
+    if (!(L > 0.0) || !isfinite(L) || !(dt > 0.0) || !isfinite(dt)) bad = 1;
+    double vl = a.vl[cs.col], vr = a.vr[cs.col];
+    if (!isfinite(vl) || !isfinite(vr)) bad = 1;
+    int Ni = bad ? 2 : (int)N;
+    cs.N = Ni;
+    cs.K = (Ni + TPB - 1) / TPB;
+    cs.tact = (Ni + cs.K - 1) / cs.K;
+    cs.h = L / Ni;
+    cs.inv_h = 1.0 / cs.h;
+    cs.dt = dt;
+    cs.vl = vl;
+    cs.vr = vr;
+    cs.g0 = (vr - vl) / (Ni * cs.h);
+    cs.bad = bad;
+    cs.N = bad ? 0 : Ni;
+  }
+  __syncthreads();
+  if (cs.bad) return false;
+  g.tid = tid;
+  g.N = cs.N;
+  g.K = cs.K;
+  g.tact = cs.tact;
+  g.t0 = tid * g.K;
+  g.kt = max(0, min(g.K, g.N - g.t0));
+  const int64_t off = cs.off;
+  const int64_t ncell_tot = a.col_off[a.ncol];
+  double* NP = S.pd(PD_N);
+  double* PP = S.pd(PD_PSI);
+  double* FEX = S.pd(PD_FEX);
+  double* FPHI = S.pd(PD_FPHI);
+  double* DH = S.pd(PD_DH);
+  double* HD = S.pd(PD_HD);
+  double* UF = S.pd(PD_UF);
+  const double mu = a.p.mu;
+  int bad = 0;
+  double m_n = 0.0, m_fphi = 0.0, m_phi = 0.0, m_fe = 0.0;
+  // D at this thread's first cell, for the neighbour's last face
+  for (int j = 0; j < g.kt; ++j) {
+    const int64_t gi = off + g.t0 + j;
+    double T = a.T[gi];
+    if (!(T > 0.0) || !isfinite(T)) bad = 1;
+    double D = mu * kKb * T / kQe;
+    if (j == 0) halo[tid] = D;
+    if (a.u && j == 0) halo[TPB + tid] = a.u[gi];
+    double neo = a.ne_old[gi], pho = a.phi_old[gi];
+    double fe = neo + (a.ire ? cs.dt * a.ire[gi] : 0.0);
+    double q = 0.0;
+    for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * ncell_tot + gi];
+    double n0 = a.ne_g ? a.ne_g[gi] : neo;
+    double p0 = a.phi_g ? a.phi_g[gi] : pho;
+    if (!isfinite(neo) || !isfinite(pho) || !isfinite(fe) || !isfinite(q) || !isfinite(n0) ||
+        !isfinite(p0))
+      bad = 1;
+    FEX[ix(j, tid, TPB)] = fe;
+    FPHI[ix(j, tid, TPB)] = q;
+    const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+    NP[ix(j, tid, TPB)] = n0;
+    PP[ix(j, tid, TPB)] = p0 - pref;
+    // face D (right face) stored temporarily as D_i; fixed below
+    DH[ix(j, tid, TPB)] = D;
+    if (a.u) UF[ix(j, tid, TPB)] = a.u[gi];
+    m_n = fmax(m_n, fabs(neo));
+    m_fphi = fmax(m_fphi, fabs(q));
+    m_phi = fmax(m_phi, fabs(pho));
+    m_fe = fmax(m_fe, fabs(fe));
+  }
+  __syncthreads();
+  for (int j = 0; j < g.kt; ++j) {
+    const int i = g.t0 + j;
+    if (i < g.N - 1) {
+      double Dn = (j + 1 < g.kt) ? DH[ix(j + 1, tid, TPB)] : halo[tid + 1];
+      double Df = 0.5 * (DH[ix(j, tid, TPB)] + Dn);
+      if (a.u) {
+        double un = (j + 1 < g.kt) ? UF[ix(j + 1, tid, TPB)] : halo[TPB + tid + 1];
+        UF[ix(j, tid, TPB)] = 0.5 * (UF[ix(j, tid, TPB)] + un);
+      }
+      DH[ix(j, tid, TPB)] = Df * cs.inv_h;
+      HD[ix(j, tid, TPB)] = cs.h / Df;
+    }
+  }
+  if (tid == 0) cs.ubl = a.u ? a.u[off] : 0.0;
+  if (g.kt > 0 && g.t0 + g.kt == g.N) cs.ubr = a.u ? a.u[off + g.N - 1] : 0.0;
+  double mx[5] = {m_n, m_fphi, m_phi, m_fe, (double)bad};
+  block_reduce<TPB>(mx, 5, true, red);
+  if (mx[4] != 0.0) return false;
+  if (tid == 0) {
+    cs.sn = fmax(fmax(mx[0], mx[1]), 1.0);
+    cs.sp = fmax(fmax(mx[2], fmax(fabs(cs.vl), fabs(cs.vr))), 1.0);
+    cs.scal[0] = mx[3];
+    cs.scal[1] = mx[1];
+  }
+  __syncthreads();
+  return true;
+}
+
+// --------------------------------------------------------------------------
+// The persistent solver kernel.
+// --------------------------------------------------------------------------
+template <int TPB, typename KR>
+__global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ColShared cs;
+  constexpr int NW = TPB / 32;
+  double* red = (double*)smem_raw;                          // (NW+1) * 40
+  double* halo = red + (NW + 1) * 40;                       // 4 * TPB
+  double* Hm = halo + 4 * TPB;                              // (m+1) * m Hessenberg
+  const int m = a.p.m;
+  double* gv = Hm + (m + 1) * m;                            // m+1
+  double* cs_ = gv + (m + 1);                               // m
+  double* sn_ = cs_ + m;                                    // m
+  double* yv = sn_ + m;                                     // m
+  double* hv = yv + m;                                      // m+2 scratch
+  KR* sh = (KR*)(hv + m + 2);                               // 12 * TPB (PCR / exchange)
+  const int tid = threadIdx.x;
+  Slot<TPB, KR> S = make_slot<TPB, KR>(a, blockIdx.x);
+
+  for (;;) {
+    if (tid == 0) {
+      int q = atomicAdd(a.queue, 1);
+      cs.col = (q < a.ncol) ? (a.order ? a.order[q] : q) : -1;
+    }
+    __syncthreads();
+    if (cs.col < 0) break;
+    Geo g;
+    bool ok = column_setup<TPB, KR>(a, g, cs, S, halo, red);
+    const int64_t col = cs.col;
+    if (!ok) {
+      if (tid == 0) {
+        if (a.mode == MODE_SOLVE) {
+          if (a.status) a.status[col] = SDCEF_STATUS_BAD_INPUT;
+          if (a.newton_it) a.newton_it[col] = 0;
+          if (a.krylov_it) a.krylov_it[col] = 0;
+          if (a.res_evals) a.res_evals[col] = 0;
+          if (a.final_res) a.final_res[col] = NAN;
+        }
+      }
+      // copy the start state through so outputs are defined
+      int64_t off = a.col_off[col], N = a.col_off[col + 1] - off;
+      if (a.mode == MODE_SOLVE)
+        for (int64_t i = tid; i < N; i += TPB) {
+          double n0 = a.ne_g ? a.ne_g[off + i] : a.ne_old[off + i];
+          double p0 = a.phi_g ? a.phi_g[off + i] : a.phi_old[off + i];
+          a.ne_out[off + i] = n0;
+          a.phi_out[off + i] = p0;
+        }
+      __syncthreads();
+      continue;
+    }
+    const int kt = g.kt;
+    const int64_t off = cs.off;
+    double* NP = S.pd(PD_N);
+    double* PP = S.pd(PD_PSI);
+    double norms[4];
+    int res_evals = 0;
+
+    // ---- test modes -------------------------------------------------------
+    if (a.mode == MODE_RESIDUAL) {
+      for (int j = 0; j < kt; ++j) {
+        const int64_t gi = off + g.t0 + j;
+        const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+        NP[ix(j, tid, TPB)] = a.x_ne[gi];
+        PP[ix(j, tid, TPB)] = a.x_phi[gi] - pref;
+      }
+      if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; }
+      __syncthreads();
+      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+                        S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
+      for (int j = 0; j < kt; ++j) {
+        const int64_t gi = off + g.t0 + j;
+        a.o1[gi] = S.pd(PD_FE0)[ix(j, tid, TPB)];
+        a.o2[gi] = S.pd(PD_FP0)[ix(j, tid, TPB)];
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // scaling: typical values at the plain start X^n (Eq. newton_sc, Algorithm 2
+    // first line), whatever the Newton start is
+    const bool start_differs = (a.mode == MODE_PRECOND) || a.ne_g || a.phi_g;
+    if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; }
+    if (start_differs) {
+      double* tn = S.pd(PD_FE1);
+      double* tp = S.pd(PD_FP1);
+      for (int j = 0; j < kt; ++j) {
+        const int64_t gi = off + g.t0 + j;
+        const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+        tn[ix(j, tid, TPB)] = a.ne_old[gi];
+        tp[ix(j, tid, TPB)] = a.phi_old[gi] - pref;
+      }
+      __syncthreads();
+      residual<TPB, KR>(a, g, cs, S, tn, tp, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+                        S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
+    } else {
+      __syncthreads();
+      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+                        S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
+    }
+    ++res_evals;
+    if (tid == 0) {
+      cs.sFe = fmax(fmax(norms[0], cs.scal[0]), 1e-12 * cs.sn);
+      cs.sFp = fmax(fmax(norms[1], cs.scal[1]), 1e-12 * cs.sn);
+      if (!(cs.sFe <= 1.79e308)) cs.sFe = 1.0;
+      if (!(cs.sFp <= 1.79e308)) cs.sFp = 1.0;
+    }
+    if (start_differs) {
+      if (a.mode == MODE_PRECOND) {
+        for (int j = 0; j < kt; ++j) {
+          const int64_t gi = off + g.t0 + j;
+          const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+          NP[ix(j, tid, TPB)] = a.x_ne[gi];
+          PP[ix(j, tid, TPB)] = a.x_phi[gi] - pref;
+        }
+      }
+      __syncthreads();
+      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+                        S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
+      ++res_evals;
+    }
+    __syncthreads();
+    int cur = 0;   // current F / face set
+    bool bad = false;
+
+    if (a.mode == MODE_PRECOND) {
+      prec_factor<TPB, KR>(a, g, cs, S, cur, sh, halo, &bad);
+      // r (physical) -> rhat = r / S_F -> z = Mhat^{-1} rhat -> x = S_X z
+      KR* re = S.W(0);
+      KR* rp = S.W(1);
+      for (int j = 0; j < kt; ++j) {
+        const int64_t gi = off + g.t0 + j;
+        re[ix(j, tid, TPB)] = (KR)(a.r_e[gi] / cs.sFe);
+        rp[ix(j, tid, TPB)] = (KR)(a.r_phi[gi] / cs.sFp);
+      }
+      __syncthreads();
+      prec_apply<TPB, KR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
+      for (int j = 0; j < kt; ++j) {
+        const int64_t gi = off + g.t0 + j;
+        a.o1[gi] = (double)S.Z(0)[ix(j, tid, TPB)] * cs.sn;
+        a.o2[gi] = (double)S.Z(1)[ix(j, tid, TPB)] * cs.sp;
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // ---- Newton loop (Algorithm 2) ---------------------------------------
+    auto scaled_inf = [&](const double* nr) { return fmax(nr[0] / cs.sFe, nr[1] / cs.sFp); };
+    auto scaled_two = [&](const double* nr) {
+      return sqrt(nr[2] / (cs.sFe * cs.sFe) + nr[3] / (cs.sFp * cs.sFp));
+    };
+    double fninf = scaled_inf(norms), fn2 = scaled_two(norms);
+    int status = SDCEF_STATUS_MAX_NEWTON, newton = 0, krylov = 0;
+    const double gam = a.p.gamma;
+    for (int l = 0;; ++l) {
+      if (!(fninf <= 1.79e308)) { status = SDCEF_STATUS_NONFINITE; break; }
+      if (fninf < a.p.eps_F) { status = SDCEF_STATUS_OK; break; }
+      if (l >= a.p.max_newton) { status = SDCEF_STATUS_MAX_NEWTON; break; }
+      // preconditioner at X^(l) and ||S_X^{-1} X||_2 (X = (n, phi))
+      prec_factor<TPB, KR>(a, g, cs, S, cur, sh, halo, &bad);
+      {
+        double s = 0.0;
+        for (int j = 0; j < kt; ++j) {
+          const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+          double xn = NP[ix(j, tid, TPB)] / cs.sn;
+          double xp = (PP[ix(j, tid, TPB)] + pref) / cs.sp;
+          s += xn * xn + xp * xp;
+        }
+        double v[2] = {s, bad ? 1.0 : 0.0};
+        block_reduce<TPB>(v, 2, false, red);
+        if (tid == 0) cs.xnorm = sqrt(v[0]);
+        if (v[1] != 0.0) { status = SDCEF_STATUS_NONFINITE; break; }
+      }
+      const double* Fe = S.pd(PD_FE0 + 2 * cur);
+      const double* Fp = S.pd(PD_FP0 + 2 * cur);
+      // ---- GMRES(m), right-preconditioned: Jhat Mhat^{-1} y = -Fhat --------
+      // x-hat accumulates sum y_i V_i; delta-hat = Mhat^{-1} x-hat.
+      KR* XHe = S.XH(0);
+      KR* XHp = S.XH(1);
+      for (int j = 0; j < kt; ++j) { XHe[ix(j, tid, TPB)] = KR(0); XHp[ix(j, tid, TPB)] = KR(0); }
+      double beta = fn2;                 // ||Fhat||_2
+      const double beta0 = fn2;
+      int its = 0;
+      bool converged = (beta0 == 0.0);
+      // V0 = -Fhat / beta
+      if (!converged) {
+        for (int j = 0; j < kt; ++j) {
+          S.V(0, 0)[ix(j, tid, TPB)] = (KR)(-Fe[ix(j, tid, TPB)] / (cs.sFe * beta));
+          S.V(0, 1)[ix(j, tid, TPB)] = (KR)(-Fp[ix(j, tid, TPB)] / (cs.sFp * beta));
+        }
+      }
+      __syncthreads();
+      while (!converged && its < a.p.max_krylov) {
+        if (tid == 0) {
+          for (int q = 0; q <= m; ++q) gv[q] = 0.0;
+          gv[0] = beta;
+        }
+        __syncthreads();
+        int kdim = 0;
+        for (int jj = 0; jj < m && its < a.p.max_krylov; ++jj) {
+          // z = Mhat^{-1} V_jj, w = Jhat z
+          double zz = prec_apply<TPB, KR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.Z(0), S.Z(1), sh,
+                                          red, true);
+          double zn = sqrt(zz);
+          double eps = kLambdaFD * (kLambdaFD + cs.xnorm / zn);
+          if (!(zn > 0.0)) eps = 1.0;
+          residual<TPB, KR>(a, g, cs, S, NP, PP, S.Z(0), S.Z(1), eps * cs.sn, eps * cs.sp, OUT_JVP,
+                            nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1), 1.0 / eps, halo, red,
+                            norms);
+          ++res_evals;
+          ++its;
+          // CGS with one re-orthogonalisation
+          double hcur[34];
+          for (int q = 0; q <= jj; ++q) hcur[q] = 0.0;
+          for (int pass = 0; pass < 2; ++pass) {
+            double d[34];
+            for (int q = 0; q <= jj; ++q) d[q] = 0.0;
+            for (int j = 0; j < kt; ++j) {
+              double we = S.W(0)[ix(j, tid, TPB)], wp = S.W(1)[ix(j, tid, TPB)];
+              for (int q = 0; q <= jj; ++q)
+                d[q] += (double)S.V(q, 0)[ix(j, tid, TPB)] * we +
+                        (double)S.V(q, 1)[ix(j, tid, TPB)] * wp;
+            }
+            block_reduce<TPB>(d, jj + 1, false, red);
+            for (int j = 0; j < kt; ++j) {
+              double we = S.W(0)[ix(j, tid, TPB)], wp = S.W(1)[ix(j, tid, TPB)];
+              for (int q = 0; q <= jj; ++q) {
+                we -= d[q] * (double)S.V(q, 0)[ix(j, tid, TPB)];
+                wp -= d[q] * (double)S.V(q, 1)[ix(j, tid, TPB)];
+              }
+              S.W(0)[ix(j, tid, TPB)] = (KR)we;
+              S.W(1)[ix(j, tid, TPB)] = (KR)wp;
+            }
+            for (int q = 0; q <= jj; ++q) hcur[q] += d[q];
+          }
+          double wn = 0.0;
+          for (int j = 0; j < kt; ++j) {
+            double we = S.W(0)[ix(j, tid, TPB)], wp = S.W(1)[ix(j, tid, TPB)];
+            wn += we * we + wp * wp;
+          }
+          block_reduce<TPB>(&wn, 1, false, red);
+          double hn = sqrt(wn);
+          if (tid == 0) {
+            for (int q = 0; q <= jj; ++q) Hm[q * m + jj] = hcur[q];
+            Hm[(jj + 1) * m + jj] = hn;
+            for (int q = 0; q < jj; ++q) {
+              double x0 = Hm[q * m + jj], x1 = Hm[(q + 1) * m + jj];
+              Hm[q * m + jj] = cs_[q] * x0 + sn_[q] * x1;
+              Hm[(q + 1) * m + jj] = -sn_[q] * x0 + cs_[q] * x1;
+            }
+            double x0 = Hm[jj * m + jj], x1 = Hm[(jj + 1) * m + jj];
+            double rho = hypot(x0, x1);
+            cs_[jj] = rho == 0.0 ? 1.0 : x0 / rho;
+            sn_[jj] = rho == 0.0 ? 0.0 : x1 / rho;
+            Hm[jj * m + jj] = rho;
+            Hm[(jj + 1) * m + jj] = 0.0;
+            gv[jj + 1] = -sn_[jj] * gv[jj];
+            gv[jj] = cs_[jj] * gv[jj];
+            double est = fabs(gv[jj + 1]);
+            cs.conv = (est <= gam * beta0 || !(hn > 0.0) || !isfinite(est)) ? 1 : 0;
+            if (!isfinite(est)) cs.conv = 2;
+          }
+          __syncthreads();
+          kdim = jj + 1;
+          const int cv = cs.conv;
+          if (cv == 2) { bad = true; break; }
+          if (cv) { converged = true; break; }
+          if (jj + 1 < m) {
+            const double ihn = 1.0 / hn;
+            for (int j = 0; j < kt; ++j) {
+              S.V(jj + 1, 0)[ix(j, tid, TPB)] = (KR)((double)S.W(0)[ix(j, tid, TPB)] * ihn);
+              S.V(jj + 1, 1)[ix(j, tid, TPB)] = (KR)((double)S.W(1)[ix(j, tid, TPB)] * ihn);
+            }
+          }
+          __syncthreads();
+        }
+        if (bad) break;
+        // y = H^{-1} g, x-hat += V y
+        if (tid == 0) {
+          for (int q = kdim - 1; q >= 0; --q) {
+            double s = gv[q];
+            for (int p2 = q + 1; p2 < kdim; ++p2) s -= Hm[q * m + p2] * yv[p2];
+            yv[q] = Hm[q * m + q] != 0.0 ? s / Hm[q * m + q] : 0.0;
+          }
+        }
+        __syncthreads();
+        for (int j = 0; j < kt; ++j) {
+          double xe = XHe[ix(j, tid, TPB)], xp = XHp[ix(j, tid, TPB)];
+          for (int q = 0; q < kdim; ++q) {
+            xe += yv[q] * (double)S.V(q, 0)[ix(j, tid, TPB)];
+            xp += yv[q] * (double)S.V(q, 1)[ix(j, tid, TPB)];
+          }
+          XHe[ix(j, tid, TPB)] = (KR)xe;
+          XHp[ix(j, tid, TPB)] = (KR)xp;
+        }
+        __syncthreads();
+        if (converged || its >= a.p.max_krylov) break;
+        // restart: r = -Fhat - Jhat Mhat^{-1} x-hat
+        double zz = prec_apply<TPB, KR>(a, g, cs, S, XHe, XHp, S.Z(0), S.Z(1), sh, red, true);
+        double zn = sqrt(zz);
+        double eps = (zn > 0.0) ? kLambdaFD * (kLambdaFD + cs.xnorm / zn) : 1.0;
+        residual<TPB, KR>(a, g, cs, S, NP, PP, S.Z(0), S.Z(1), eps * cs.sn, eps * cs.sp, OUT_JVP,
+                          nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1), 1.0 / eps, halo, red, norms);
+        ++res_evals;
+        ++its;
+        double rs = 0.0;
+        for (int j = 0; j < kt; ++j) {
+          double re = -Fe[ix(j, tid, TPB)] / cs.sFe - (double)S.W(0)[ix(j, tid, TPB)];
+          double rp = -Fp[ix(j, tid, TPB)] / cs.sFp - (double)S.W(1)[ix(j, tid, TPB)];
+          S.W(0)[ix(j, tid, TPB)] = (KR)re;
+          S.W(1)[ix(j, tid, TPB)] = (KR)rp;
+          rs += re * re + rp * rp;
+        }
+        block_reduce<TPB>(&rs, 1, false, red);
+        beta = sqrt(rs);
+        if (beta <= gam * beta0) { converged = true; break; }
+        const double ib = 1.0 / beta;
+        for (int j = 0; j < kt; ++j) {
+          S.V(0, 0)[ix(j, tid, TPB)] = (KR)((double)S.W(0)[ix(j, tid, TPB)] * ib);
+          S.V(0, 1)[ix(j, tid, TPB)] = (KR)((double)S.W(1)[ix(j, tid, TPB)] * ib);
+        }
+        __syncthreads();
+      }
+      krylov += its;
+      if (bad) { status = SDCEF_STATUS_NONFINITE; break; }
+      // delta-hat = Mhat^{-1} x-hat  (into Z)
+      prec_apply<TPB, KR>(a, g, cs, S, XHe, XHp, S.Z(0), S.Z(1), sh, red, false);
+      // ---- backtracking line search ----------------------------------------
+      double lam = 1.0;
+      bool accepted = false;
+      const int nxt = 1 - cur;
+      double tnorm[4];
+      for (int t = 0; t <= a.p.max_ls; ++t) {
+        residual<TPB, KR>(a, g, cs, S, NP, PP, S.Z(0), S.Z(1), lam * cs.sn, lam * cs.sp, OUT_F,
+                          S.pd(PD_FE0 + 2 * nxt), S.pd(PD_FP0 + 2 * nxt), nxt, nullptr, nullptr,
+                          nullptr, nullptr, 0, halo, red, tnorm);
+        ++res_evals;
+        double t2 = scaled_two(tnorm);
+        if (t2 <= 1.79e308 && t2 <= (1.0 - a.p.ls_alpha * lam * (1.0 - gam)) * fn2) {
+          accepted = true;
+          break;
+        }
+        if (t < a.p.max_ls) lam *= 0.5;
+      }
+      if (!accepted) {
+        status = converged ? SDCEF_STATUS_LINESEARCH_FAIL : SDCEF_STATUS_MAX_KRYLOV;
+        break;
+      }
+      // X += lam S_X delta-hat; step size for the eps_X test
+      double smax = 0.0;
+      for (int j = 0; j < kt; ++j) {
+        double dn = (double)S.Z(0)[ix(j, tid, TPB)], dp = (double)S.Z(1)[ix(j, tid, TPB)];
+        NP[ix(j, tid, TPB)] = fma(lam * cs.sn, dn, NP[ix(j, tid, TPB)]);
+        PP[ix(j, tid, TPB)] = fma(lam * cs.sp, dp, PP[ix(j, tid, TPB)]);
+        smax = fmax(smax, fmax(fabs(dn), fabs(dp)));
+      }
+      cur = nxt;
+      fninf = scaled_inf(tnorm);
+      fn2 = scaled_two(tnorm);
+      ++newton;
+      if (a.p.eps_X > 0.0) {
+        block_reduce<TPB>(&smax, 1, true, red);
+        if (lam * smax < a.p.eps_X && fninf >= a.p.eps_F) { status = SDCEF_STATUS_OK; break; }
+      } else {
+        __syncthreads();
+      }
+    }
+    // ---- outputs ----------------------------------------------------------
+    for (int j = 0; j < kt; ++j) {
+      const int64_t gi = off + g.t0 + j;
+      const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+      a.ne_out[gi] = NP[ix(j, tid, TPB)];
+      a.phi_out[gi] = pref + PP[ix(j, tid, TPB)];
+    }
+    if (tid == 0) {
+      if (a.status) a.status[col] = status;
+      if (a.newton_it) a.newton_it[col] = newton;
+      if (a.krylov_it) a.krylov_it[col] = krylov;
+      if (a.res_evals) a.res_evals[col] = res_evals;
+      if (a.final_res) a.final_res[col] = fninf;
+    }
+    __syncthreads();
+  }
+}
+
+#ifdef SDCEF_WITH_ORDER
+// Longest-first order of the columns (counting sort on length, descending).
+__global__ void order_kernel(const int64_t* col_off, int64_t ncol, int nbins, int shift,
+                             int* order) {
+  extern __shared__ int sh_hist[];
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh_hist[b] = 0;
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+    int64_t n = col_off[c + 1] - col_off[c];
+    long long nn = n < 0 ? 0 : (long long)n;
+    long long bb = nn >> shift;
+    int b = (int)(bb < nbins - 1 ? bb : nbins - 1);
+    atomicAdd(&sh_hist[nbins - 1 - b], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int b = 0; b < nbins; ++b) {
+      int c = sh_hist[b];
+      sh_hist[b] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+    int64_t n = col_off[c + 1] - col_off[c];
+    long long nn = n < 0 ? 0 : (long long)n;
+    long long bb = nn >> shift;
+    int b = (int)(bb < nbins - 1 ? bb : nbins - 1);
+    int pos = atomicAdd(&sh_hist[nbins - 1 - b], 1);
+    order[pos] = (int)c;
+  }
+}
+
+
+
+#endif  // SDCEF_WITH_ORDER
+
+template <int TPB, typename KR>
+cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
+  auto k = jfnk_kernel<TPB, KR>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, TPB, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int TPB, typename KR>
+int occupancy_t(size_t smem) {
+  int nb = 0;
+  auto k = jfnk_kernel<TPB, KR>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, TPB, smem) != cudaSuccess) return 1;
+  return nb < 1 ? 1 : nb;
+}
+#endif  // SDCEF_KERNEL_TU
+
+}  // namespace sdcef_impl

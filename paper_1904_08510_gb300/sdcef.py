@@ -1,0 +1,253 @@
+"""Python binding of the sdcef C ABI (include/sdcef.h): argument marshalling only.
+
+Every step of the solve runs in libsdcef.so; this module converts torch CUDA
+tensors into the plain pointers of the C structs and raises when the
+library is missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsdcef.so")
+
+SUCCESS = 0
+ERR_INVALID, ERR_CUDA, ERR_CAPACITY, ERR_NOMEM = -1, -2, -3, -4
+STATUS_OK, STATUS_MAX_NEWTON, STATUS_MAX_KRYLOV, STATUS_LINESEARCH_FAIL, \
+    STATUS_NONFINITE, STATUS_BAD_INPUT = range(6)
+FP64, MIXED = 0, 1
+PREC_EXACT, PREC_RECAST, PREC_NONE = 0, 1, 2
+BC_ABSORBING, BC_ZERO_GRADIENT = 0, 1
+MAX_RESTART = 32
+MAX_SPECIES = 16
+
+# every function declared in include/sdcef.h
+EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_params",
+           "sdcef_solve_batch", "sdcef_solve_batch_host", "sdcef_residual_batch",
+           "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count")
+
+
+class Params(C.Structure):
+    _fields_ = [("eps_F", C.c_double), ("eps_X", C.c_double), ("gamma", C.c_double),
+                ("mobility", C.c_double), ("ls_alpha", C.c_double), ("eps_r", C.c_double),
+                ("restart_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int),
+                ("max_linesearch", C.c_int), ("precision", C.c_int), ("precond", C.c_int),
+                ("bc_electron", C.c_int), ("threads_per_column", C.c_int)]
+
+
+class BatchC(C.Structure):
+    _fields_ = [("ncol", C.c_int64), ("col_off", C.c_void_p), ("length", C.c_void_p),
+                ("dt", C.c_void_p), ("v_left", C.c_void_p), ("v_right", C.c_void_p),
+                ("ne_old", C.c_void_p), ("phi_old", C.c_void_p), ("n_species", C.c_int),
+                ("valence", C.c_void_p), ("n_ion", C.c_void_p), ("T", C.c_void_p),
+                ("rho", C.c_void_p), ("u_adv", C.c_void_p), ("i_re", C.c_void_p),
+                ("ne_guess", C.c_void_p), ("phi_guess", C.c_void_p)]
+
+
+class ResultC(C.Structure):
+    _fields_ = [("ne_out", C.c_void_p), ("phi_out", C.c_void_p), ("status", C.c_void_p),
+                ("newton_it", C.c_void_p), ("krylov_it", C.c_void_p), ("res_evals", C.c_void_p),
+                ("final_res", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsdcef.so (built by paper_1904_08510_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsdcef.so not found at {LIB_PATH}; run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER(Params)
+        B = C.POINTER(BatchC)
+        R = C.POINTER(ResultC)
+        vp = C.c_void_p
+        L.sdcef_default_params.argtypes = [P]
+        L.sdcef_default_params.restype = None
+        L.sdcef_create.argtypes = [C.POINTER(vp), P, C.c_int64, C.c_int64, C.c_int, vp]
+        L.sdcef_destroy.argtypes = [vp]
+        L.sdcef_set_params.argtypes = [vp, P]
+        L.sdcef_solve_batch.argtypes = [vp, B, R]
+        L.sdcef_solve_batch_host.argtypes = [vp, B, R]
+        L.sdcef_residual_batch.argtypes = [vp, B, vp, vp, vp, vp]
+        L.sdcef_precond_apply_batch.argtypes = [vp, B, vp, vp, vp, vp, vp, vp]
+        L.sdcef_last_error.restype = C.c_char_p
+        L.sdcef_last_error.argtypes = []
+        L.sdcef_last_launch_count.argtypes = [vp]
+        for f in ("sdcef_create", "sdcef_destroy", "sdcef_set_params", "sdcef_solve_batch",
+                  "sdcef_solve_batch_host", "sdcef_residual_batch", "sdcef_precond_apply_batch",
+                  "sdcef_last_launch_count"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class SdcefError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sdcef error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != SUCCESS:
+        raise SdcefError(rc, lib().sdcef_last_error().decode())
+    return rc
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().sdcef_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class DeviceBatch:
+    """A workload.Batch resident on the GPU (torch tensors) plus its C struct."""
+    ncol: int
+    ncells: int
+    tensors: dict
+    valence: np.ndarray
+
+    @classmethod
+    def from_host(cls, b, device="cuda", guess=None):
+        import torch
+        t = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a)).to(device)
+        ts = dict(col_off=t(b.col_off.astype(np.int64)), length=t(b.length), dt=t(b.dt),
+                  v_left=t(b.v_left), v_right=t(b.v_right), ne_old=t(b.ne_old),
+                  phi_old=t(b.phi_old), n_ion=t(np.atleast_2d(b.n_ion)), T=t(b.T),
+                  rho=t(b.rho), u_adv=t(b.u_adv), i_re=t(b.i_re),
+                  ne_guess=None if guess is None else t(guess[0]),
+                  phi_guess=None if guess is None else t(guess[1]))
+        return cls(b.ncol, b.ncells, ts, np.ascontiguousarray(b.valence, dtype=np.int32))
+
+    def cstruct(self) -> BatchC:
+        ts = self.tensors
+        return BatchC(self.ncol, _ptr(ts["col_off"]), _ptr(ts["length"]), _ptr(ts["dt"]),
+                      _ptr(ts["v_left"]), _ptr(ts["v_right"]), _ptr(ts["ne_old"]),
+                      _ptr(ts["phi_old"]), int(self.valence.shape[0]),
+                      self.valence.ctypes.data, _ptr(ts["n_ion"]), _ptr(ts["T"]),
+                      _ptr(ts["rho"]), _ptr(ts["u_adv"]), _ptr(ts["i_re"]),
+                      _ptr(ts["ne_guess"]), _ptr(ts["phi_guess"]))
+
+    def with_guess(self, ne, phi) -> "DeviceBatch":
+        ts = dict(self.tensors, ne_guess=ne, phi_guess=phi)
+        return DeviceBatch(self.ncol, self.ncells, ts, self.valence)
+
+
+class Solver:
+    """Owns one sdcef context (workspace sized at construction)."""
+
+    def __init__(self, params: Params | None = None, *, max_cols: int, max_cells: int,
+                 max_col_cells: int, stream=None):
+        import torch
+        self.params = params or default_params()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().sdcef_create(C.byref(h), C.byref(self.params), int(max_cols),
+                                  int(max_cells), int(max_col_cells),
+                                  C.c_void_p(stream.cuda_stream)))
+        self.h = h
+        self.max_cols, self.max_cells = max_cols, max_cells
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sdcef_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p: Params):
+        _check(lib().sdcef_set_params(self.h, C.byref(p)))
+        self.params = p
+
+    def launches(self) -> int:
+        return int(lib().sdcef_last_launch_count(self.h))
+
+    def alloc_result(self, db: DeviceBatch):
+        import torch
+        dev = db.tensors["ne_old"].device
+        return dict(ne=torch.empty(db.ncells, dtype=torch.float64, device=dev),
+                    phi=torch.empty(db.ncells, dtype=torch.float64, device=dev),
+                    status=torch.empty(db.ncol, dtype=torch.int32, device=dev),
+                    newton_it=torch.empty(db.ncol, dtype=torch.int32, device=dev),
+                    krylov_it=torch.empty(db.ncol, dtype=torch.int32, device=dev),
+                    res_evals=torch.empty(db.ncol, dtype=torch.int32, device=dev),
+                    final_res=torch.empty(db.ncol, dtype=torch.float64, device=dev))
+
+    def solve(self, db: DeviceBatch, out: dict | None = None) -> dict:
+        """sdcef_solve_batch on device tensors; asynchronous on the solver stream."""
+        out = out or self.alloc_result(db)
+        bs = db.cstruct()
+        rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), _ptr(out["status"]),
+                     _ptr(out["newton_it"]), _ptr(out["krylov_it"]), _ptr(out["res_evals"]),
+                     _ptr(out["final_res"]))
+        _check(lib().sdcef_solve_batch(self.h, C.byref(bs), C.byref(rs)))
+        return out
+
+    def solve_host(self, b, out: dict | None = None, guess=None) -> dict:
+        """sdcef_solve_batch_host: numpy (or pinned torch) host arrays in and out."""
+        keep = []
+
+        def h(a, dt=np.float64):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                keep.append(a)
+                return a.data_ptr()
+            arr = np.ascontiguousarray(a, dtype=dt)
+            keep.append(arr)
+            return arr.ctypes.data
+        val = np.ascontiguousarray(b.valence, dtype=np.int32)
+        bs = BatchC(b.ncol, h(b.col_off, np.int64), h(b.length), h(b.dt), h(b.v_left),
+                    h(b.v_right), h(b.ne_old), h(b.phi_old), int(val.shape[0]), val.ctypes.data,
+                    h(np.atleast_2d(b.n_ion) if not hasattr(b.n_ion, "data_ptr") else b.n_ion),
+                    h(b.T), None, h(b.u_adv), h(b.i_re),
+                    h(None if guess is None else guess[0]), h(None if guess is None else guess[1]))
+        if out is None:
+            out = dict(ne=np.empty(b.ncells), phi=np.empty(b.ncells),
+                       status=np.empty(b.ncol, np.int32), newton_it=np.empty(b.ncol, np.int32),
+                       krylov_it=np.empty(b.ncol, np.int32), res_evals=np.empty(b.ncol, np.int32),
+                       final_res=np.empty(b.ncol))
+        rs = ResultC(*[h(out[k], None) if k in out else None for k in
+                       ("ne", "phi", "status", "newton_it", "krylov_it", "res_evals", "final_res")])
+        _check(lib().sdcef_solve_batch_host(self.h, C.byref(bs), C.byref(rs)))
+        return out
+
+    def residual(self, db: DeviceBatch, ne, phi):
+        import torch
+        Fe = torch.empty_like(ne)
+        Fp = torch.empty_like(phi)
+        bs = db.cstruct()
+        _check(lib().sdcef_residual_batch(self.h, C.byref(bs), _ptr(ne), _ptr(phi), _ptr(Fe),
+                                          _ptr(Fp)))
+        return Fe, Fp
+
+    def precond_apply(self, db: DeviceBatch, ne, phi, r_e, r_phi):
+        import torch
+        xe = torch.empty_like(r_e)
+        xp = torch.empty_like(r_phi)
+        bs = db.cstruct()
+        _check(lib().sdcef_precond_apply_batch(self.h, C.byref(bs), _ptr(ne), _ptr(phi),
+                                               _ptr(r_e), _ptr(r_phi), _ptr(xe), _ptr(xp)))
+        return xe, xp
