@@ -181,6 +181,38 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const do
                               const double* phi, const double* r_e, const double* r_phi,
                               double* x_e, double* x_phi);
 
+/* Allocation-free solve. The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc when they solve, for example an
+ * application whose device memory is handed out entirely by its own arena
+ * allocator, or a time-stepping code that forbids allocation after start-up so
+ * that its memory footprint stays fixed. It needs no context: it runs the same
+ * solver kernel as sdcef_solve_batch, with its workspace (column slots, work
+ * queue, column order) in one file-scope device array of
+ * SDCEF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Arguments: p as for sdcef_create (validated the same way); batch and out as
+ * for sdcef_solve_batch (device pointers); max_col_cells bounds the longest
+ * column of the batch (cells of a longer column are reported as
+ * SDCEF_STATUS_BAD_INPUT); stream is a cudaStream_t (NULL = legacy default).
+ * Limits: ncol <= SDCEF_NOALLOC_MAX_COLS and max_col_cells <=
+ * SDCEF_NOALLOC_MAX_COL_CELLS, else SDCEF_ERR_CAPACITY with a message; fewer
+ * columns run concurrently than with a context (as many slots as fit in the
+ * array), so throughput is lower.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture. Every call on a device shares the one array and
+ * leaves its contents behind (the call itself zeroes the work-queue counter,
+ * the only part that must start at zero): calls that overlap on the GPU, on
+ * different streams or threads, race and give wrong results. Enqueued on
+ * `stream`; does not synchronise. */
+#define SDCEF_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+#define SDCEF_NOALLOC_MAX_COLS 65536
+#define SDCEF_NOALLOC_MAX_COL_CELLS 4096
+int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batch* batch,
+                              const sdcef_result* out, int max_col_cells, void* stream);
+
 /* Message of the last error on this thread (static storage). */
 const char* sdcef_last_error(void);
 

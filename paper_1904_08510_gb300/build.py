@@ -66,8 +66,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd.append("-DSDCEF_WITH_ORDER")
         cmd += ["-c", os.path.join(CSRC, "kern_inst.cu"), "-o", obj]
         jobs.append((obj, cmd))
-    host_obj = os.path.join(BUILD, "sdcef_host.o")
-    jobs.append((host_obj, [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, "sdcef.cu"), "-o", host_obj]))
+    for src in ("sdcef.cu", "noalloc.cu"):
+        obj = os.path.join(BUILD, src.replace(".cu", "_host.o"))
+        jobs.append((obj, [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]))
 
     def run(job):
         obj, cmd = job

@@ -196,6 +196,12 @@ int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
 
 }  // namespace
 
+// Shared with the allocation-free entry point (noalloc.cu).
+namespace sdcef_impl {
+int report_error(int code, const char* msg) { return set_err(code, msg); }
+int validate_params(const sdcef_params* p) { return check_params(p, 0); }
+}  // namespace sdcef_impl
+
 extern "C" {
 
 void sdcef_default_params(sdcef_params* p) {

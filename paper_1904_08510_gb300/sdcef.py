@@ -28,7 +28,11 @@ MAX_SPECIES = 16
 # every function declared in include/sdcef.h
 EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_params",
            "sdcef_solve_batch", "sdcef_solve_batch_host", "sdcef_residual_batch",
-           "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count")
+           "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count",
+           "sdcef_solve_batch_noalloc")
+NOALLOC_SCRATCH_BYTES = 32 << 20
+NOALLOC_MAX_COLS = 65536
+NOALLOC_MAX_COL_CELLS = 4096
 
 
 class Params(C.Structure):
@@ -81,9 +85,10 @@ def lib():
         L.sdcef_last_error.restype = C.c_char_p
         L.sdcef_last_error.argtypes = []
         L.sdcef_last_launch_count.argtypes = [vp]
+        L.sdcef_solve_batch_noalloc.argtypes = [P, B, R, C.c_int, vp]
         for f in ("sdcef_create", "sdcef_destroy", "sdcef_set_params", "sdcef_solve_batch",
                   "sdcef_solve_batch_host", "sdcef_residual_batch", "sdcef_precond_apply_batch",
-                  "sdcef_last_launch_count"):
+                  "sdcef_last_launch_count", "sdcef_solve_batch_noalloc"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -251,3 +256,18 @@ class Solver:
         _check(lib().sdcef_precond_apply_batch(self.h, C.byref(bs), _ptr(ne), _ptr(phi),
                                                _ptr(r_e), _ptr(r_phi), _ptr(xe), _ptr(xp)))
         return xe, xp
+
+
+def solve_noalloc(params: Params, db: DeviceBatch, out: dict, max_col_cells: int, stream=None):
+    """sdcef_solve_batch_noalloc: the solve without a context, its workspace in the
+    library's fixed device scratch array (for callers that cannot allocate)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    bs = db.cstruct()
+    rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), _ptr(out["status"]),
+                 _ptr(out["newton_it"]), _ptr(out["krylov_it"]), _ptr(out["res_evals"]),
+                 _ptr(out["final_res"]))
+    _check(lib().sdcef_solve_batch_noalloc(C.byref(params), C.byref(bs), C.byref(rs),
+                                           int(max_col_cells), C.c_void_p(stream.cuda_stream)))
+    return out
