@@ -226,7 +226,7 @@ def main():
     prec = S.MIXED if args.precision == "mixed" else S.FP64
     pc = S.PREC_EXACT if args.precond == "exact" else S.PREC_RECAST
     params = S.default_params(precision=prec, precond=pc,
-                              restart_m=30 if pc == S.PREC_RECAST else 8)
+                              restart_m=30 if pc == S.PREC_RECAST else (16 if prec == S.MIXED else 8))
     solver = S.Solver(params, max_cols=b.ncol, max_cells=b.ncells,
                       max_col_cells=int(lengths.max()))
     db = S.DeviceBatch.from_host(b, dev)
@@ -323,6 +323,7 @@ def main():
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "solve_stats": {"status_ok": int((st == 0).sum()), "ncol": int(b.ncol),
+                            "status_hist": np.bincount(st, minlength=6).tolist(),
                             "newton_mean": float(nw.mean()), "krylov_mean": float(kr.mean()),
                             "res_evals_mean": float(re.mean()), "final_res_max": float(fr.max()),
                             "step_ms": ms}}

@@ -59,7 +59,7 @@ struct KArgs {
 
 // FP64 planes of a slot
 enum {
-  PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_HD, PD_UF,
+  PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_HD, PD_UF, PD_PREF,
   PD_FACE0,               // 4 planes: face derivative set 0 (a0, a1, b0, b1), scaled
   PD_FACE1 = PD_FACE0 + 4,
   PD_COUNT = PD_FACE1 + 4
@@ -144,6 +144,8 @@ struct ColShared {
   int N, K, tact, bad;
   double h, inv_h, dt, vl, vr, g0, ubl, ubr;
   double sn, sp, sFe, sFp;
+  // reciprocals / ratios of the scales, set once per column
+  double isn, isp, isFe, isFp, r_a, r_b, r_c, r_l, r_rho;
   double vL[2], vR[2];      // electrode-face electron velocities of face sets 0/1
   double xnorm;
   int flag;
@@ -206,6 +208,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
   const int tid = g.tid, kt = g.kt, N = g.N;
   const double ih = cs.inv_h, dt = cs.dt, g0 = cs.g0, mu = a.p.mu, kap = a.p.kap;
   const double r = dt * ih;
+  const double ie_e = ieps * cs.isFe, ie_p = ieps * cs.isFp;   // JVP output scaling
   const double* FEX = S.pd(PD_FEX);
   const double* FPHI = S.pd(PD_FPHI);
   const double* DH = S.pd(PD_DH);
@@ -239,7 +242,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
     if (g.t0 == 0) {
       // left electrode face: G_L - g0 = (9 psi_0 - psi_1) / (3h)
       double p1 = kt >= 2 ? st_p(1) : halo[1 * TPB + tid + 1];
-      double dL = (9.0 * p_i - p1) * (ih / 3.0);
+      double dL = (9.0 * p_i - p1) * (ih * (1.0 / 3.0));
       double vL = cs.ubl + mu * (g0 + dL);
       bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0;
       gam_left = act ? vL * n_i : 0.0;
@@ -274,7 +277,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
       } else {
         // right electrode face: G_R - g0 = (-9 psi_{N-1} + psi_{N-2}) / (3h)
         double pm = (j >= 1) ? st_p(j - 1) : halo[3 * TPB + tid - 1];
-        dd = (-9.0 * p_i + pm) * (ih / 3.0);
+        dd = (-9.0 * p_i + pm) * (ih * (1.0 / 3.0));
         double vR = cs.ubr + mu * (g0 + dd);
         bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0;
         gam = act ? vR * n_i : 0.0;
@@ -300,8 +303,8 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
           sse += Fe * Fe;
           ssp += Fp * Fp;
         } else {
-          we[ix(j, tid, TPB)] = (KR)((Fe - fe_ref[ix(j, tid, TPB)]) * ieps / cs.sFe);
-          wp[ix(j, tid, TPB)] = (KR)((Fp - fp_ref[ix(j, tid, TPB)]) * ieps / cs.sFp);
+          we[ix(j, tid, TPB)] = (KR)((Fe - fe_ref[ix(j, tid, TPB)]) * ie_e);
+          wp[ix(j, tid, TPB)] = (KR)((Fp - fp_ref[ix(j, tid, TPB)]) * ie_p);
         }
       }
       gam_prev = gam;
@@ -333,8 +336,8 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
       sse += Fe * Fe;
       ssp += Fp * Fp;
     } else {
-      we[ix(0, tid, TPB)] = (KR)((Fe - fe_ref[ix(0, tid, TPB)]) * ieps / cs.sFe);
-      wp[ix(0, tid, TPB)] = (KR)((Fp - fp_ref[ix(0, tid, TPB)]) * ieps / cs.sFp);
+      we[ix(0, tid, TPB)] = (KR)((Fe - fe_ref[ix(0, tid, TPB)]) * ie_e);
+      wp[ix(0, tid, TPB)] = (KR)((Fp - fp_ref[ix(0, tid, TPB)]) * ie_p);
     }
   }
   if (out_mode == OUT_F) {
@@ -373,14 +376,14 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   const double* face = S.pd(PD_FACE0 + 4 * fs);
   const int i = g.t0 + j, N = g.N;
   const double ih = cs.inv_h, r = cs.dt * ih, mu = a.p.mu;
-  const double sl = cs.sp / cs.sFp;
+  const double sl = cs.r_l;
   const double kh2 = a.p.kap * ih * ih * sl;
   RowJ R;
   R.As = R.Au = R.Bs = R.Bu = 0.0;
-  R.Ad = -cs.sn / cs.sFe;
+  const double sa = cs.r_a, sb = cs.r_b;
+  R.Ad = -sa;
   R.Bd = 0.0;
-  R.C = -cs.sn / cs.sFp;
-  const double sa = cs.sn / cs.sFe, sb = cs.sp / cs.sFe;
+  R.C = -cs.r_c;
   // right face (row i carries -r Gam_{i+1/2})
   if (i < N - 1) {
     R.Ad -= face[0 * a.PL + ix(j, g.tid, TPB)] * sa;
@@ -390,9 +393,9 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   } else {
     double vR = cs.vR[fs];
     if (a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0) {
-      R.Ad -= r * vR * cs.sn / cs.sFe;
-      R.Bd -= r * n_last * mu * (-3.0 * ih) * cs.sp / cs.sFe;
-      R.Bs -= r * n_last * mu * (ih / 3.0) * cs.sp / cs.sFe;
+      R.Ad -= r * vR * sa;
+      R.Bd -= r * n_last * mu * (-3.0 * ih) * sb;
+      R.Bs -= r * n_last * mu * (ih * (1.0 / 3.0)) * sb;
     }
   }
   // left face (row i carries +r Gam_{i-1/2})
@@ -404,9 +407,9 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   } else {
     double vL = cs.vL[fs];
     if (a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0) {
-      R.Ad += r * vL * cs.sn / cs.sFe;
-      R.Bd += r * n_0 * mu * (3.0 * ih) * cs.sp / cs.sFe;
-      R.Bu += r * n_0 * mu * (-ih / 3.0) * cs.sp / cs.sFe;
+      R.Ad += r * vL * sa;
+      R.Bd += r * n_0 * mu * (3.0 * ih) * sb;
+      R.Bu += r * n_0 * mu * (-ih * (1.0 / 3.0)) * sb;
     }
   }
   // Poisson stencil with the second-order electrode closure
@@ -477,7 +480,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     KR* Bpl = S.f + 10 * S.PL;   // 3 planes: sub, dia, sup
     Scal<1, KR, TPB> S1{S.s};
     Scal<1, KR, TPB> S2{S.s + 40 * TPB};
-    const double rho = cs.sFe / cs.sFp;
+    const double rho = cs.r_rho;
     auto row1 = [&](int j, Mat<1, KR>& M, Mat<1, KR>& D, Mat<1, KR>& U) {
       double lf[4];
       lface(j, lf);
@@ -520,7 +523,7 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const Co
     const KR* Bpl = S.f + 10 * S.PL;
     Scal<1, KR, TPB> S1{S.s};
     Scal<1, KR, TPB> S2{S.s + 40 * TPB};
-    const KR cfac = (KR)(cs.sn / cs.sFp);   // -Chat
+    const KR cfac = (KR)cs.r_c;   // -Chat
     // z1 = Ahat^{-1} r_e (into ze)
     {
       KR* rin[1] = {re};
@@ -637,7 +640,7 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
     const int64_t gi = off + g.t0 + j;
     double T = a.T[gi];
     if (!(T > 0.0) || !isfinite(T)) bad = 1;
-    double D = mu * kKb * T / kQe;
+    double D = mu * (kKb / kQe) * T;
     if (j == 0) halo[tid] = D;
     if (a.u && j == 0) halo[TPB + tid] = a.u[gi];
     double neo = a.ne_old[gi], pho = a.phi_old[gi];
@@ -652,6 +655,7 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
     FEX[ix(j, tid, TPB)] = fe;
     FPHI[ix(j, tid, TPB)] = q;
     const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+    S.pd(PD_PREF)[ix(j, tid, TPB)] = pref;
     NP[ix(j, tid, TPB)] = n0;
     PP[ix(j, tid, TPB)] = p0 - pref;
     // face D (right face) stored temporarily as D_i; fixed below
@@ -755,7 +759,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     if (a.mode == MODE_RESIDUAL) {
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
-        const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+        const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
         NP[ix(j, tid, TPB)] = a.x_ne[gi];
         PP[ix(j, tid, TPB)] = a.x_phi[gi] - pref;
       }
@@ -781,7 +785,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       double* tp = S.pd(PD_FP1);
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
-        const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+        const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
         tn[ix(j, tid, TPB)] = a.ne_old[gi];
         tp[ix(j, tid, TPB)] = a.phi_old[gi] - pref;
       }
@@ -799,12 +803,21 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       cs.sFp = fmax(fmax(norms[1], cs.scal[1]), 1e-12 * cs.sn);
       if (!(cs.sFe <= 1.79e308)) cs.sFe = 1.0;
       if (!(cs.sFp <= 1.79e308)) cs.sFp = 1.0;
+      cs.isn = 1.0 / cs.sn;
+      cs.isp = 1.0 / cs.sp;
+      cs.isFe = 1.0 / cs.sFe;
+      cs.isFp = 1.0 / cs.sFp;
+      cs.r_a = cs.sn / cs.sFe;
+      cs.r_b = cs.sp / cs.sFe;
+      cs.r_c = cs.sn / cs.sFp;
+      cs.r_l = cs.sp / cs.sFp;
+      cs.r_rho = cs.sFe / cs.sFp;
     }
     if (start_differs) {
       if (a.mode == MODE_PRECOND) {
         for (int j = 0; j < kt; ++j) {
           const int64_t gi = off + g.t0 + j;
-          const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+          const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
           NP[ix(j, tid, TPB)] = a.x_ne[gi];
           PP[ix(j, tid, TPB)] = a.x_phi[gi] - pref;
         }
@@ -825,8 +838,8 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       KR* rp = S.W(1);
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
-        re[ix(j, tid, TPB)] = (KR)(a.r_e[gi] / cs.sFe);
-        rp[ix(j, tid, TPB)] = (KR)(a.r_phi[gi] / cs.sFp);
+        re[ix(j, tid, TPB)] = (KR)(a.r_e[gi] * cs.isFe);
+        rp[ix(j, tid, TPB)] = (KR)(a.r_phi[gi] * cs.isFp);
       }
       __syncthreads();
       prec_apply<TPB, KR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
@@ -856,9 +869,9 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       {
         double s = 0.0;
         for (int j = 0; j < kt; ++j) {
-          const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
-          double xn = NP[ix(j, tid, TPB)] / cs.sn;
-          double xp = (PP[ix(j, tid, TPB)] + pref) / cs.sp;
+          const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
+          double xn = NP[ix(j, tid, TPB)] * cs.isn;
+          double xp = (PP[ix(j, tid, TPB)] + pref) * cs.isp;
           s += xn * xn + xp * xp;
         }
         double v[2] = {s, bad ? 1.0 : 0.0};
@@ -879,9 +892,10 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       bool converged = (beta0 == 0.0);
       // V0 = -Fhat / beta
       if (!converged) {
+        const double ve = -cs.isFe / beta, vp = -cs.isFp / beta;
         for (int j = 0; j < kt; ++j) {
-          S.V(0, 0)[ix(j, tid, TPB)] = (KR)(-Fe[ix(j, tid, TPB)] / (cs.sFe * beta));
-          S.V(0, 1)[ix(j, tid, TPB)] = (KR)(-Fp[ix(j, tid, TPB)] / (cs.sFp * beta));
+          S.V(0, 0)[ix(j, tid, TPB)] = (KR)(Fe[ix(j, tid, TPB)] * ve);
+          S.V(0, 1)[ix(j, tid, TPB)] = (KR)(Fp[ix(j, tid, TPB)] * vp);
         }
       }
       __syncthreads();
@@ -1000,8 +1014,8 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         ++its;
         double rs = 0.0;
         for (int j = 0; j < kt; ++j) {
-          double re = -Fe[ix(j, tid, TPB)] / cs.sFe - (double)S.W(0)[ix(j, tid, TPB)];
-          double rp = -Fp[ix(j, tid, TPB)] / cs.sFp - (double)S.W(1)[ix(j, tid, TPB)];
+          double re = -Fe[ix(j, tid, TPB)] * cs.isFe - (double)S.W(0)[ix(j, tid, TPB)];
+          double rp = -Fp[ix(j, tid, TPB)] * cs.isFp - (double)S.W(1)[ix(j, tid, TPB)];
           S.W(0)[ix(j, tid, TPB)] = (KR)re;
           S.W(1)[ix(j, tid, TPB)] = (KR)rp;
           rs += re * re + rp * rp;
@@ -1063,7 +1077,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     // ---- outputs ----------------------------------------------------------
     for (int j = 0; j < kt; ++j) {
       const int64_t gi = off + g.t0 + j;
-      const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+      const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
       a.ne_out[gi] = NP[ix(j, tid, TPB)];
       a.phi_out[gi] = pref + PP[ix(j, tid, TPB)];
     }
