@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tpc", type=int, default=0, help="threads per column (0 = library default)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the unbatched / learned / SDC-sweep comparison legs")
+    ap.add_argument("--sdc-ncol", type=int, default=16384)
     return ap.parse_args()
 
 
@@ -225,11 +229,14 @@ def main():
     lengths = b.lengths()
     prec = S.MIXED if args.precision == "mixed" else S.FP64
     pc = S.PREC_EXACT if args.precond == "exact" else S.PREC_RECAST
-    params = S.default_params(precision=prec, precond=pc,
+    params = S.default_params(precision=prec, precond=pc, threads_per_column=args.tpc,
                               restart_m=30 if pc == S.PREC_RECAST else (16 if prec == S.MIXED else 8))
     solver = S.Solver(params, max_cols=b.ncol, max_cells=b.ncells,
                       max_col_cells=int(lengths.max()))
     db = S.DeviceBatch.from_host(b, dev)
+    tuned = None
+    if args.tpc == 0:
+        tuned = solver.autotune(db, reps=1)   # before warm-up and timing
     out = solver.alloc_result(db)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -292,6 +299,9 @@ def main():
         e2e = {"value": b.ncol * ws * args.steps / sum(e2e_t), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    extra = None
+    if not args.no_extras and ws == 1:
+        extra = extras(args, S, b, db, solver, params, dev)
     if rank != 0:
         return 0
     peaks, peak_kind = load_peaks()
@@ -318,10 +328,12 @@ def main():
             "data": "synthetic (seeded profiles; the paper's flame data is not available)",
             "config": {"workload": WORKLOAD, "ncol": b.ncol, "cells": int(b.ncells),
                        "precision": args.precision, "precond": args.precond, "eps_F": 1e-10,
+                       "threads_per_column": (tuned[0] if tuned else args.tpc),
+                       "autotune_ms": (tuned[1] if tuned else None),
                        "l2": "flushed between steps (256 MB write); inputs 5 x 8 B x cells > L2",
                        "parallelism": f"replicas x{ws}"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "comparisons": extra,
             "solve_stats": {"status_ok": int((st == 0).sum()), "ncol": int(b.ncol),
                             "status_hist": np.bincount(st, minlength=6).tolist(),
                             "newton_mean": float(nw.mean()), "krylov_mean": float(kr.mean()),
@@ -329,6 +341,99 @@ def main():
                             "step_ms": ms}}
     print(json.dumps(line))
     return 0
+
+
+def extras(args, S, b, db, solver, params, dev):
+    """Comparison legs reported beside the headline (not part of `value`)."""
+    import torch
+    from paper_1904_08510_gb300 import learned as Lrn
+    from paper_1904_08510_gb300.workload import sdc_batch
+    res = {}
+    # plain unbatched FP64 JFNK: one column per launch, looped over a prefix
+    m = min(64, b.ncol)
+    cols = [S.DeviceBatch.from_host(b.column(c), dev) for c in range(m)]
+    one = S.Solver(params, max_cols=1, max_cells=int(b.lengths()[:m].max()),
+                   max_col_cells=int(b.lengths()[:m].max()))
+    outs = [one.alloc_result(c) for c in cols]
+    for c, o in zip(cols[:4], outs[:4]):
+        one.solve(c, o)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for c, o in zip(cols, outs):
+        one.solve(c, o)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    res["plain_unbatched_fp64"] = {"value": m / t, "unit": "column-solves/s", "columns": m,
+                                   "launches_per_column": 2}
+    one.close()
+    # learned initial guess (weights trained by the library's own kernels)
+    if os.path.exists(Lrn.WEIGHTS):
+        mlp = S.MLP(b.ncells)
+        mlp.set_params(Lrn.load())
+        out = solver.alloc_result(db)
+        ne_g = torch.empty(b.ncells, dtype=torch.float64, device=dev)
+        ph_g = torch.empty(b.ncells, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            mlp.guess(db, ne_g, ph_g, components=S.GUESS_NE)
+            solver.solve(db.with_guess(ne_g, ph_g), out)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(args.steps, 3)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mlp.guess(db, ne_g, ph_g, components=S.GUESS_NE)
+            solver.solve(db.with_guess(ne_g, ph_g), out)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        nw = out["newton_it"].cpu().numpy()
+        st = out["status"].cpu().numpy()
+        res["learned_guess_fp64"] = {"value": b.ncol / float(np.median(times)), "unit": "column-solves/s",
+                                     "newton_mean": float(nw.mean()), "status_ok": int((st == 0).sum()),
+                                     "krylov_mean": float(out["krylov_it"].float().mean().item()),
+                                     "components": "n_e increment"}
+        mlp.close()
+    # SDC electric sweep: k_max = 4 solves per MISDC step, ion-CFL time step
+    sb = sdc_batch(args.sdc_ncol, 5_000_000, n_cells=1024)
+    sdb = S.DeviceBatch.from_host(sb, dev)
+    st_ = torch.cuda.Stream()
+    ssolver = S.Solver(params, max_cols=sb.ncol, max_cells=sb.ncells, max_col_cells=1024, stream=st_)
+    sout = ssolver.alloc_result(sdb)
+    work = torch.empty_like(sdb.tensors["n_ion"])
+    with torch.cuda.stream(st_):
+        ssolver.sdc_sweep(sdb, 4, work=work, out=sout)
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st_)
+        ssolver.sdc_sweep(sdb, 4, work=work, out=sout)
+        e1.record(st_)
+        torch.cuda.synchronize()
+        te.append(e0.elapsed_time(e1) / 1e3)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st_):
+        ssolver.sdc_sweep(sdb, 4, work=work, out=sout)
+    g.replay()
+    torch.cuda.synchronize()
+    tg = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st_)
+        g.replay()
+        e1.record(st_)
+        torch.cuda.synchronize()
+        tg.append(e0.elapsed_time(e1) / 1e3)
+    sst = sout["status"].cpu().numpy()
+    res["sdc_sweep_fp64"] = {"columns": sb.ncol, "cells_per_column": 1024, "k_max": 4,
+                             "ms_per_sweep_eager": 1e3 * min(te), "ms_per_sweep_graph": 1e3 * min(tg),
+                             "column_solves_per_s_graph": 4 * sb.ncol / min(tg),
+                             "status_ok_last_iteration": int((sst == 0).sum()),
+                             "newton_mean_last_iteration": float(sout["newton_it"].float().mean().item())}
+    ssolver.close()
+    return res
 
 
 class _HostView:

@@ -181,6 +181,39 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const do
                               const double* phi, const double* r_e, const double* r_phi,
                               double* x_e, double* x_phi);
 
+/* Autotuner: times sdcef_solve_batch on this batch with 32, 64, 128 and 256
+ * threads per column (one warm-up and `reps` timed solves each, CUDA events on
+ * the context stream), keeps the fastest as the context's threads_per_column
+ * and returns it in *tpb_out (ms_out, if not NULL, receives the 4 mean times).
+ * Synchronises the stream; call it before any stream capture. Not part of the
+ * paper (the paper solves one 1D problem at a time). */
+int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef_result* out, int reps,
+                   int* tpb_out, float* ms_out);
+
+/* Provisional charged species of an SDC iteration: the electric-drift part of
+ * the provisional rho Y~ that Algorithm 1 hands to the electric solve (the
+ * effective ion velocity U_ef,m = U - nu_m kappa_m grad(phi) of Sec. 3.1 with
+ * U = 0; advection, diffusion and reactions of the ions are outside this
+ * library). One explicit first-order upwind step of length dt per column:
+ *   n~_i = n_i - (dt/h) (Phi_{i+1/2} - Phi_{i-1/2}),  Phi = w n_upwind,
+ *   w = -nu kappa_ion dphi/dx at the face (second-order one-sided gradient at
+ *   the electrodes, which absorb outgoing ions and emit none).
+ * Stable for kappa_ion |E| dt / h <= 1. Reads batch->n_ion and the potential
+ * phi ([cells]); writes n_ion_out ([n_species][cells], device). */
+int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* phi,
+                           double kappa_ion, double* n_ion_out);
+
+/* The electric part of one MISDC time step (Algorithm 1, SDC iterations
+ * k = 1..k_max; the paper uses k_max = 4, Table 1): for each k the provisional
+ * ions are advanced from batch->n_ion in the field of the previous iterate
+ * (phi^n for k = 1) and Eq. nls is solved from the previous iterate (from
+ * X^n, or batch->ne_guess / phi_guess, for k = 1). n_ion_work is caller-owned
+ * device scratch of [n_species][cells]. The results of the last iteration are
+ * written to out; enqueued on the context stream with no allocation and no
+ * synchronisation, so the sweep can be captured in a CUDA graph. */
+int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* batch, int k_max, double kappa_ion,
+                    double* n_ion_work, const sdcef_result* out);
+
 /* Allocation-free solve. The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc when they solve, for example an
  * application whose device memory is handed out entirely by its own arena
@@ -212,6 +245,59 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const do
 #define SDCEF_NOALLOC_MAX_COL_CELLS 4096
 int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batch* batch,
                               const sdcef_result* out, int max_col_cells, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned Newton initial guess. Not part of the paper: a small MLP predicts,
+ * from local stencil features of the plain start X^n, the scaled increment to
+ * the converged solution; Algorithm 2 then starts from X^n + S_X y and still
+ * decides convergence with its own residual test, so the guess changes only
+ * the iteration count, never the accepted root.
+ *   features of cell i: for stencil offsets -2..2 (indices mirrored at the
+ *   column ends) n_e^n/s_n, phi^n/s_phi, f_phi/s_n, T/2000 K, E h/s_phi with
+ *   E h = -(phi_{k+1} - phi_{k-1})/2; 25 values zero-padded to 32, BF16,
+ *   row-major [cells][32]; s_n, s_phi are the per-column scales of Eq. newton_sc.
+ *   network: y = W3 silu(W2 silu(W1 x + b1) + b2) + b3 (32 -> 128 -> 128 -> 2),
+ *   BF16 weights and activations on the tensor cores, FP32 accumulation.
+ *   parameters: FP32 flat array of SDCEF_MLP_NPARAM values, in order
+ *   W1[128][32], b1[128], W2[128][128], b2[128], W3[2][128], b3[2].
+ *   training: mean-squared error against y* = ((n* - n^n)/s_n, (phi* - phi^n)/s_phi),
+ *   Adam (beta 0.9 / 0.999, eps 1e-8) on the FP32 master parameters.
+ * All array arguments are device pointers; calls are enqueued on the stream
+ * given to sdcef_mlp_create (set/get_params synchronise it). */
+#define SDCEF_MLP_NPARAM 20994
+typedef struct sdcef_mlp sdcef_mlp;
+/* Allocate parameters, Adam state and activation buffers for up to max_rows cells. */
+int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream);
+int sdcef_mlp_destroy(sdcef_mlp* mlp);
+/* Copy SDCEF_MLP_NPARAM FP32 parameters from HOST memory; resets the Adam state. */
+int sdcef_mlp_set_params(sdcef_mlp* mlp, const float* params_host);
+/* Copy the FP32 parameters to HOST memory. */
+int sdcef_mlp_get_params(sdcef_mlp* mlp, float* params_host);
+/* Features of every cell of the batch into X_bf16 ([cells][32] bfloat16). */
+int sdcef_mlp_features(sdcef_mlp* mlp, const sdcef_batch* batch, void* X_bf16);
+/* Training targets y* ([cells][2] FP32) from converged (ne_star, phi_star). */
+int sdcef_mlp_targets(sdcef_mlp* mlp, const sdcef_batch* batch, const double* ne_star,
+                      const double* phi_star, float* targets);
+/* Network output Y ([n][2] FP32) for n feature rows (n <= max_rows). */
+int sdcef_mlp_forward(sdcef_mlp* mlp, const void* X_bf16, int64_t n, float* Y);
+/* Gradient of the mean-squared loss over n rows (no update): grads
+ * [SDCEF_MLP_NPARAM] FP32 and loss [1] FP32, both device pointers (may be NULL). */
+int sdcef_mlp_grad(sdcef_mlp* mlp, const void* X_bf16, const float* targets, int64_t n,
+                   float* grads, float* loss);
+/* One Adam step on n rows with learning rate lr; loss [1] FP32 device (may be NULL). */
+int sdcef_mlp_train_step(sdcef_mlp* mlp, const void* X_bf16, const float* targets, int64_t n,
+                         float lr, float* loss);
+/* Newton start for every cell of the batch: features, network, and
+ * X^n + S_X y written to ne_guess / phi_guess ([cells] FP64). ncells is the
+ * batch's total cell count (<= max_rows). components selects which predicted
+ * increments are applied (SDCEF_GUESS_NE | SDCEF_GUESS_PHI); an increment not
+ * selected leaves that field at its plain start value. */
+#define SDCEF_GUESS_NE 1
+#define SDCEF_GUESS_PHI 2
+int sdcef_mlp_guess(sdcef_mlp* mlp, const sdcef_batch* batch, int64_t ncells, int components,
+                    double* ne_guess, double* phi_guess);
+/* Kernel launches enqueued by the last forward / grad / train_step / guess call. */
+int sdcef_mlp_last_launch_count(const sdcef_mlp* mlp);
 
 /* Message of the last error on this thread (static storage). */
 const char* sdcef_last_error(void);

@@ -93,6 +93,7 @@ def lib():
         L.or_gmres_dense.argtypes = [C.c_int, vp, vp, vp, C.c_int, C.c_double, C.c_int,
                                      C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.or_max_threads.restype = C.c_int
+        L.or_ion_update_batch.argtypes = [B, vp, C.c_double, vp]
         _lib = L
     return _lib
 
@@ -224,3 +225,34 @@ def solve(batch, params: Params | None = None, *, guess=None, threads: int = 0):
 
 def max_threads() -> int:
     return int(lib().or_max_threads())
+
+
+def ion_update(batch, phi, kappa_ion=4e-3):
+    """Provisional ion densities after one explicit upwind drift step in the field
+    of phi ([n_species, cells])."""
+    k = _Keep(batch)
+    phi = _f64(phi)
+    out = np.zeros_like(k.n_ion)
+    lib().or_ion_update_batch(C.byref(k.s), _ptr(phi), float(kappa_ion), _ptr(out))
+    return out
+
+
+def sdc_sweep(batch, k_max=4, kappa_ion=4e-3, params: Params | None = None, guess=None):
+    """The electric part of one MISDC step (Algorithm 1): for k = 1..k_max the
+    provisional ions are advanced from n_ion^n in the field of the previous
+    iterate and the implicit electron/potential system is solved from the
+    previous iterate (X^0 = X^n, or the given guess for k = 1)."""
+    from copy import copy
+    P = params or default_params()
+    ne, phi = batch.ne_old.copy(), batch.phi_old.copy()
+    start = guess
+    hist = []
+    for k in range(k_max):
+        bk = copy(batch)
+        bk.n_ion = ion_update(batch, phi, kappa_ion)
+        g = start if start is not None else ((ne, phi) if k > 0 else None)
+        r = solve(bk, P, guess=g)
+        ne, phi = r["ne"], r["phi"]
+        start = None
+        hist.append(r)
+    return ne, phi, hist

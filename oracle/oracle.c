@@ -807,6 +807,48 @@ void or_solve_batch(const or_params* P, const or_batch* b, const double* ne_gues
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Provisional charged species between SDC iterations (Algorithm 1 calls the */
+/* electric solve with provisional ion fields; only their electric drift is  */
+/* modelled here): explicit first-order upwind update of each species,       */
+/*   n~_i = n_i - (dt/h) (Phi_{i+1/2} - Phi_{i-1/2}),                         */
+/*   Phi = w n_upwind, w = nu kappa_ion E_face (Eq. for U_ef,m with U = 0),   */
+/* E_face = -dphi/dx at interior faces and from the quadratic electrode      */
+/* stencil at the electrodes, which absorb outgoing ions and emit none.      */
+/* ------------------------------------------------------------------------ */
+void or_ion_update_batch(const or_batch* b, const double* phi, double kappa_ion,
+                         double* n_out) {
+  int64_t ncells = b->col_off[b->ncol];
+  for (int64_t c = 0; c < b->ncol; ++c) {
+    int64_t a = b->col_off[c];
+    int n = (int)(b->col_off[c + 1] - a);
+    if (n < 2) continue;
+    double h = b->length[c] / n, dt = b->dt[c];
+    const double* p = phi + a;
+    double GL = (-8.0 * b->v_left[c] + 9.0 * p[0] - p[1]) / (3.0 * h);
+    double GR = (8.0 * b->v_right[c] - 9.0 * p[n - 1] + p[n - 2]) / (3.0 * h);
+    for (int s = 0; s < b->n_species; ++s) {
+      const double* ni = b->n_ion + s * ncells + a;
+      double* no = n_out + s * ncells + a;
+      double nu = (double)b->valence[s];
+      double wl = -nu * kappa_ion * GL;          /* drift velocity at x = 0 */
+      double flux_prev = wl < 0.0 ? wl * ni[0] : 0.0;
+      for (int i = 0; i < n; ++i) {
+        double flux_next;
+        if (i == n - 1) {
+          double wr = -nu * kappa_ion * GR;
+          flux_next = wr > 0.0 ? wr * ni[n - 1] : 0.0;
+        } else {
+          double w = -nu * kappa_ion * (p[i + 1] - p[i]) / h;
+          flux_next = w * (w > 0.0 ? ni[i] : ni[i + 1]);
+        }
+        no[i] = ni[i] - (dt / h) * (flux_next - flux_prev);
+        flux_prev = flux_next;
+      }
+    }
+  }
+}
+
 int or_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd.append("-DSDCEF_WITH_ORDER")
         cmd += ["-c", os.path.join(CSRC, "kern_inst.cu"), "-o", obj]
         jobs.append((obj, cmd))
-    for src in ("sdcef.cu", "noalloc.cu"):
+    for src in ("sdcef.cu", "noalloc.cu", "mlp.cu"):
         obj = os.path.join(BUILD, src.replace(".cu", "_host.o"))
         jobs.append((obj, [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]))
 

@@ -13,5 +13,9 @@ cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int sh
   order_kernel<<<1, 1024, nbins * sizeof(int), st>>>(col_off, ncol, nbins, shift, order);
   return cudaGetLastError();
 }
+cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st) {
+  ion_update_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
 #endif
 }  // namespace sdcef_impl

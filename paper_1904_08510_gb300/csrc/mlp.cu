@@ -1,0 +1,621 @@
+// Learned Newton initial guess: feature extraction, a BF16 tensor-core GEMM
+// (mma.sync m16n8k16, FP32 accumulation) with fused bias/SiLU epilogues, the
+// MSE loss, backpropagation, Adam and the guess assembly. The network maps the
+// 5-cell stencil features of a cell to the scaled Newton increment
+// ((n* - n^n)/s_n, (phi* - phi^n)/s_phi); the JFNK of Algorithm 2 then starts
+// from X^n + S_X y instead of X^n and still decides convergence.
+//
+// Shapes: 32 (25 features, zero-padded) -> 128 -> 128 -> 2, SiLU activations.
+// Parameters (FP32 master copy, flat): W1[128][32], b1[128], W2[128][128],
+// b2[128], W3[2][128], b3[2]; BF16 copies of W1, W2, W3 feed the tensor cores.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "../../include/sdcef.h"
+
+namespace sdcef_impl {
+int report_error(int code, const char* msg);
+}
+using sdcef_impl::report_error;
+
+namespace {
+
+constexpr int kIn = 32, kFeat = 25, kHid = 128, kOut = 2;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
+              kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kOut * kHid,
+              kNParam = kOffB3 + kOut;
+static_assert(kNParam == SDCEF_MLP_NPARAM, "parameter count");
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+// --------------------------------------------------------------------------
+// Features: one CTA per column (block max-reductions for s_n, s_phi).
+// --------------------------------------------------------------------------
+struct FeatArgs {
+  int64_t ncol;
+  const int64_t* col_off;
+  const double *v_left, *v_right, *ne, *phi, *n_ion, *T;
+  int nsp;
+  int val[SDCEF_MAX_SPECIES];
+  __nv_bfloat16* X;     // [cells][32]
+  // optional targets / guess
+  const double *ne_star, *phi_star;
+  float* Tgt;           // [cells][2]
+  const float* Y;       // [cells][2] network output (guess mode)
+  double *ne_g, *phi_g;
+  int mode;             // 0 features, 1 targets, 2 guess
+  int comps;            // guess: bit 0 applies the n_e increment, bit 1 the phi increment
+};
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = sh[0];
+  for (int q = 1; q < nw; ++q) r = fmax(r, sh[q]);
+  return r;
+}
+
+__global__ void feat_kernel(FeatArgs a) {
+  __shared__ double sh[32];
+  const int64_t c = blockIdx.x;
+  if (c >= a.ncol) return;
+  const int64_t off = a.col_off[c];
+  const int N = (int)(a.col_off[c + 1] - off);
+  const int64_t cells = a.col_off[a.ncol];
+  auto fphi = [&](int i) {
+    double q = 0.0;
+    for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * cells + off + i];
+    return q;
+  };
+  double mn = 0.0, mq = 0.0, mp = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    mn = fmax(mn, fabs(a.ne[off + i]));
+    mq = fmax(mq, fabs(fphi(i)));
+    mp = fmax(mp, fabs(a.phi[off + i]));
+  }
+  mn = block_max(mn, sh);
+  mq = block_max(mq, sh);
+  mp = block_max(mp, sh);
+  const double sn = fmax(fmax(mn, mq), 1.0);
+  const double sp = fmax(fmax(mp, fmax(fabs(a.v_left[c]), fabs(a.v_right[c]))), 1.0);
+  const double isn = 1.0 / sn, isp = 1.0 / sp;
+  if (N < 1) return;
+  auto mir = [&](int j) {
+    if (j < 0) j = -j - 1;
+    if (j >= N) j = 2 * N - 1 - j;
+    return min(max(j, 0), N - 1);
+  };
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int64_t gi = off + i;
+    if (a.mode == 0) {
+      __nv_bfloat16* x = a.X + gi * kIn;
+      for (int o = -2; o <= 2; ++o) {
+        int k = mir(i + o), kp = mir(k + 1), km = mir(k - 1);
+        int base = 5 * (o + 2);
+        x[base + 0] = __float2bfloat16((float)(a.ne[off + k] * isn));
+        x[base + 1] = __float2bfloat16((float)(a.phi[off + k] * isp));
+        x[base + 2] = __float2bfloat16((float)(fphi(k) * isn));
+        x[base + 3] = __float2bfloat16((float)(a.T[off + k] * (1.0 / 2000.0)));
+        x[base + 4] = __float2bfloat16((float)(-(a.phi[off + kp] - a.phi[off + km]) * 0.5 * isp));
+      }
+      for (int f = kFeat; f < kIn; ++f) x[f] = __float2bfloat16(0.0f);
+    } else if (a.mode == 1) {
+      a.Tgt[gi * 2 + 0] = (float)((a.ne_star[gi] - a.ne[gi]) * isn);
+      a.Tgt[gi * 2 + 1] = (float)((a.phi_star[gi] - a.phi[gi]) * isp);
+    } else {
+      a.ne_g[gi] = a.ne[gi] + ((a.comps & 1) ? sn * (double)a.Y[gi * 2 + 0] : 0.0);
+      a.phi_g[gi] = a.phi[gi] + ((a.comps & 2) ? sp * (double)a.Y[gi * 2 + 1] : 0.0);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// BF16 GEMM on the tensor cores: C[m][n] = sum_k A(m,k) B(k,n),
+// A(m,k) = transA ? A[k*lda+m] : A[m*lda+k], B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n].
+// 64x64 CTA tile, 32-deep K slab, 4 warps of 32x32, mma.sync m16n8k16.
+// Epilogues: 0 store/accumulate FP32 C; 1 Z = acc + bias (FP32, optional)
+// and H = silu(Z) (BF16); 2 dZ = acc * silu'(Zin) (BF16) with the column sums
+// of dZ added to colsum; 3 C = acc + bias (FP32).
+// --------------------------------------------------------------------------
+struct GemmArgs {
+  int M, N, K;
+  const __nv_bfloat16* A;
+  int lda, transA;
+  const __nv_bfloat16* B;
+  int ldb, transB;
+  float* C;
+  int ldc, atomic;
+  int kchunk;
+  int epi;
+  const float* bias;
+  __nv_bfloat16* H;
+  int ldh;
+  const float* Zin;
+  int ldz;
+  float* colsum;
+};
+
+constexpr int BM = 64, BN = 64, BK = 32, PADK = BK + 8;
+
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 sA[BM][PADK];
+  __shared__ __align__(16) __nv_bfloat16 sB[BN][PADK];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    // load A tile -> sA[m][k], B tile -> sB[n][k]
+    for (int e = tid; e < BM * BK; e += 128) {
+      int mm, kk;
+      if (g.transA) { kk = e / BM; mm = e % BM; } else { mm = e / BK; kk = e % BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      __nv_bfloat16 v = zero;
+      if (gm < g.M && gk < kend)
+        v = g.transA ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
+      sA[mm][kk] = v;
+    }
+    for (int e = tid; e < BN * BK; e += 128) {
+      int nn, kk;
+      if (g.transB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      __nv_bfloat16 v = zero;
+      if (gn < g.N && gk < kend)
+        v = g.transB ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
+      sB[nn][kk] = v;
+    }
+    __syncthreads();
+    const int gr = lane >> 2, tc = (lane & 3) * 2;
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + gr;
+        af[i][0] = *(const uint32_t*)&sA[r][ks + tc];
+        af[i][1] = *(const uint32_t*)&sA[r + 8][ks + tc];
+        af[i][2] = *(const uint32_t*)&sA[r][ks + tc + 8];
+        af[i][3] = *(const uint32_t*)&sA[r + 8][ks + tc + 8];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + j * 8 + gr;
+        bfr[j][0] = *(const uint32_t*)&sB[c][ks + tc];
+        bfr[j][1] = *(const uint32_t*)&sB[c][ks + tc + 8];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
+    }
+    __syncthreads();
+  }
+  // epilogue
+  const int gr = lane >> 2, tc = (lane & 3) * 2;
+  float cs[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = m0 + wm + i * 16 + gr + (q >> 1) * 8;
+        const int col = n0 + wn + j * 8 + tc + (q & 1);
+        if (row >= g.M || col >= g.N) continue;
+        float v = acc[i][j][q];
+        if (g.epi == 0) {
+          float* p = g.C + (size_t)row * g.ldc + col;
+          if (g.atomic) atomicAdd(p, v); else *p = v;
+        } else if (g.epi == 1) {
+          float z = v + g.bias[col];
+          if (g.C) g.C[(size_t)row * g.ldc + col] = z;
+          g.H[(size_t)row * g.ldh + col] = __float2bfloat16(silu(z));
+        } else if (g.epi == 2) {
+          float dz = v * silu_grad(g.Zin[(size_t)row * g.ldz + col]);
+          g.H[(size_t)row * g.ldh + col] = __float2bfloat16(dz);
+          cs[j][q & 1] += dz;
+        } else {
+          g.C[(size_t)row * g.ldc + col] = v + g.bias[col];
+        }
+      }
+  if (g.epi == 2) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float v = cs[j][q];
+        // lanes sharing a column: same lane & 3
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        const int col = n0 + wn + j * 8 + tc + q;
+        if (gr == 0 && col < g.N) atomicAdd(&g.colsum[col], v);
+      }
+  }
+}
+
+// MSE loss: dY = 2 (Y - T) / (2 n) (BF16 for the backward GEMMs), loss and
+// the bias gradient of the output layer accumulated with atomics.
+__global__ void loss_kernel(const float* Y, const float* T, int64_t n, __nv_bfloat16* dY,
+                            float* loss, float* gb3) {
+  float l = 0.0f, g0 = 0.0f, g1 = 0.0f;
+  const float sc = 1.0f / (float)n;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    float d0 = Y[2 * s] - T[2 * s], d1 = Y[2 * s + 1] - T[2 * s + 1];
+    l += d0 * d0 + d1 * d1;
+    float e0 = d0 * sc, e1 = d1 * sc;   // 2 d / (2 n)
+    dY[2 * s] = __float2bfloat16(e0);
+    dY[2 * s + 1] = __float2bfloat16(e1);
+    g0 += e0;
+    g1 += e1;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    l += __shfl_xor_sync(0xffffffffu, l, o);
+    g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+    g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(loss, l * 0.5f * sc);
+    atomicAdd(&gb3[0], g0);
+    atomicAdd(&gb3[1], g1);
+  }
+}
+
+// Adam (Kingma & Ba 2015) with bias correction; refreshes the BF16 weight
+// copies and clears the gradient for the next step.
+__global__ void adam_kernel(float* p, float* g, float* m, float* v, int n, float lr, float b1,
+                            float b2, float eps, float c1, float c2, __nv_bfloat16* w1,
+                            __nv_bfloat16* w2, __nv_bfloat16* w3) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.0f - b1) * gi;
+    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    g[i] = 0.0f;
+    if (i >= kOffW1 && i < kOffB1) w1[i - kOffW1] = __float2bfloat16(pi);
+    else if (i >= kOffW2 && i < kOffB2) w2[i - kOffW2] = __float2bfloat16(pi);
+    else if (i >= kOffW3 && i < kOffB3) w3[i - kOffW3] = __float2bfloat16(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* p, __nv_bfloat16* w1, __nv_bfloat16* w2,
+                               __nv_bfloat16* w3) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNParam; i += gridDim.x * blockDim.x) {
+    if (i >= kOffW1 && i < kOffB1) w1[i - kOffW1] = __float2bfloat16(p[i]);
+    else if (i >= kOffW2 && i < kOffB2) w2[i - kOffW2] = __float2bfloat16(p[i]);
+    else if (i >= kOffW3 && i < kOffB3) w3[i - kOffW3] = __float2bfloat16(p[i]);
+  }
+}
+
+}  // namespace
+
+// ============================================================================
+struct sdcef_mlp {
+  int64_t max_rows;
+  cudaStream_t st;
+  float *p, *g, *m, *v;                 // FP32 parameters, gradients, Adam moments
+  __nv_bfloat16 *w1, *w2, *w3;          // BF16 weight copies
+  float *Z1, *Z2, *Y, *loss;            // activations (FP32)
+  __nv_bfloat16 *H1, *H2, *dY, *dZ2, *dZ1, *X;   // BF16 activations / features
+  int step;
+  int launches;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e)); }
+
+cudaError_t gemm(sdcef_mlp* h, GemmArgs g) {
+  int splits = 1;
+  g.kchunk = ((g.K + BK - 1) / BK) * BK;
+  if (g.epi == 0 && g.atomic) {
+    // split K across CTAs so that the long sample dimension fills the GPU
+    const int tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+    splits = std::max(1, std::min(1024, 608 / std::max(tiles, 1)));
+    int kc = (g.K + splits - 1) / splits;
+    g.kchunk = ((kc + BK - 1) / BK) * BK;
+    splits = (g.K + g.kchunk - 1) / g.kchunk;
+  }
+  // M (the sample dimension of the layer GEMMs) on grid.x, whose limit is 2^31 - 1
+  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, splits);
+  gemm_bf16_kernel<<<grid, 128, 0, h->st>>>(g);
+  ++h->launches;
+  return cudaGetLastError();
+}
+
+GemmArgs ga() {
+  GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  return g;
+}
+
+// forward through the three layers for n rows of X; fills Z1, H1, Z2, H2, Y
+cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n, bool keep_z) {
+  GemmArgs g = ga();
+  g.M = (int)n; g.N = kHid; g.K = kIn;
+  g.A = X; g.lda = kIn; g.B = h->w1; g.ldb = kIn; g.transB = 1;
+  g.epi = 1; g.bias = h->p + kOffB1; g.C = keep_z ? h->Z1 : nullptr; g.ldc = kHid;
+  g.H = h->H1; g.ldh = kHid;
+  cudaError_t e = gemm(h, g);
+  if (e != cudaSuccess) return e;
+  g = ga();
+  g.M = (int)n; g.N = kHid; g.K = kHid;
+  g.A = h->H1; g.lda = kHid; g.B = h->w2; g.ldb = kHid; g.transB = 1;
+  g.epi = 1; g.bias = h->p + kOffB2; g.C = keep_z ? h->Z2 : nullptr; g.ldc = kHid;
+  g.H = h->H2; g.ldh = kHid;
+  e = gemm(h, g);
+  if (e != cudaSuccess) return e;
+  g = ga();
+  g.M = (int)n; g.N = kOut; g.K = kHid;
+  g.A = h->H2; g.lda = kHid; g.B = h->w3; g.ldb = kHid; g.transB = 1;
+  g.epi = 3; g.bias = h->p + kOffB3; g.C = h->Y; g.ldc = kOut;
+  return gemm(h, g);
+}
+
+// gradients of the mean-squared loss over n rows into h->g (accumulated)
+cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t n) {
+  int nb = (int)std::min<int64_t>(1216, (n + 255) / 256);
+  loss_kernel<<<std::max(nb, 1), 256, 0, h->st>>>(h->Y, T, n, h->dY, h->loss, h->g + kOffB3);
+  ++h->launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // gW3 = dY^T H2
+  GemmArgs g = ga();
+  g.M = kOut; g.N = kHid; g.K = (int)n;
+  g.A = h->dY; g.lda = kOut; g.transA = 1; g.B = h->H2; g.ldb = kHid;
+  g.C = h->g + kOffW3; g.ldc = kHid; g.atomic = 1; g.epi = 0;
+  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  // dZ2 = (dY W3) * silu'(Z2); gb2 += colsum
+  g = ga();
+  g.M = (int)n; g.N = kHid; g.K = kOut;
+  g.A = h->dY; g.lda = kOut; g.B = h->w3; g.ldb = kHid;
+  g.epi = 2; g.Zin = h->Z2; g.ldz = kHid; g.H = h->dZ2; g.ldh = kHid; g.colsum = h->g + kOffB2;
+  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  // gW2 = dZ2^T H1
+  g = ga();
+  g.M = kHid; g.N = kHid; g.K = (int)n;
+  g.A = h->dZ2; g.lda = kHid; g.transA = 1; g.B = h->H1; g.ldb = kHid;
+  g.C = h->g + kOffW2; g.ldc = kHid; g.atomic = 1;
+  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  // dZ1 = (dZ2 W2) * silu'(Z1); gb1 += colsum
+  g = ga();
+  g.M = (int)n; g.N = kHid; g.K = kHid;
+  g.A = h->dZ2; g.lda = kHid; g.B = h->w2; g.ldb = kHid;
+  g.epi = 2; g.Zin = h->Z1; g.ldz = kHid; g.H = h->dZ1; g.ldh = kHid; g.colsum = h->g + kOffB1;
+  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  // gW1 = dZ1^T X
+  g = ga();
+  g.M = kHid; g.N = kIn; g.K = (int)n;
+  g.A = h->dZ1; g.lda = kHid; g.transA = 1; g.B = X; g.ldb = kIn;
+  g.C = h->g + kOffW1; g.ldc = kIn; g.atomic = 1;
+  return gemm(h, g);
+}
+
+FeatArgs feat_args(const sdcef_batch* b) {
+  FeatArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ncol = b->ncol;
+  a.col_off = b->col_off;
+  a.v_left = b->v_left;
+  a.v_right = b->v_right;
+  a.ne = b->ne_old;
+  a.phi = b->phi_old;
+  a.n_ion = b->n_ion;
+  a.T = b->T;
+  a.nsp = b->n_species;
+  for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
+  return a;
+}
+
+int check_batch(const sdcef_batch* b) {
+  if (!b || b->ncol < 0) return report_error(SDCEF_ERR_INVALID, "mlp: batch is NULL or ncol < 0");
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (!b->col_off || !b->v_left || !b->v_right || !b->ne_old || !b->phi_old || !b->T)
+    return report_error(SDCEF_ERR_INVALID, "mlp: required batch pointer is NULL");
+  if (b->n_species < 0 || b->n_species > SDCEF_MAX_SPECIES || (b->n_species > 0 && (!b->valence || !b->n_ion)))
+    return report_error(SDCEF_ERR_INVALID, "mlp: ion species arguments");
+  return SDCEF_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
+  if (!out || max_rows < 1) return report_error(SDCEF_ERR_INVALID, "mlp_create: bad arguments");
+  sdcef_mlp* h = new sdcef_mlp();
+  memset(h, 0, sizeof(*h));
+  h->max_rows = max_rows;
+  h->st = (cudaStream_t)stream;
+  const size_t R = (size_t)max_rows;
+  struct Alloc { void** p; size_t bytes; } al[] = {
+      {(void**)&h->p, kNParam * 4}, {(void**)&h->g, kNParam * 4}, {(void**)&h->m, kNParam * 4},
+      {(void**)&h->v, kNParam * 4}, {(void**)&h->w1, kHid * kIn * 2}, {(void**)&h->w2, kHid * kHid * 2},
+      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->Z1, R * kHid * 4}, {(void**)&h->Z2, R * kHid * 4},
+      {(void**)&h->Y, R * kOut * 4}, {(void**)&h->loss, 64}, {(void**)&h->H1, R * kHid * 2},
+      {(void**)&h->H2, R * kHid * 2}, {(void**)&h->dY, R * kOut * 2}, {(void**)&h->dZ2, R * kHid * 2},
+      {(void**)&h->dZ1, R * kHid * 2}, {(void**)&h->X, R * kIn * 2}};
+  for (auto& a : al) {
+    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    if (e == cudaSuccess) e = cudaMemset(*a.p, 0, a.bytes);
+    if (e != cudaSuccess) {
+      for (auto& b : al) if (*b.p) cudaFree(*b.p);
+      delete h;
+      return report_error(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
+    }
+  }
+  *out = h;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_mlp_destroy(sdcef_mlp* h) {
+  if (!h) return SDCEF_SUCCESS;
+  cudaStreamSynchronize(h->st);
+  void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->Z1, h->Z2, h->Y, h->loss,
+                h->H1, h->H2, h->dY, h->dZ2, h->dZ1, h->X};
+  for (void* p : ps) cudaFree(p);
+  delete h;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_mlp_set_params(sdcef_mlp* h, const float* params_host) {
+  if (!h || !params_host) return report_error(SDCEF_ERR_INVALID, "mlp_set_params: NULL");
+  cudaError_t e = cudaMemcpyAsync(h->p, params_host, kNParam * 4, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->m, 0, kNParam * 4, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->v, 0, kNParam * 4, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->g, 0, kNParam * 4, h->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  to_bf16_kernel<<<64, 256, 0, h->st>>>(h->p, h->w1, h->w2, h->w3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->step = 0;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_mlp_get_params(sdcef_mlp* h, float* params_host) {
+  if (!h || !params_host) return report_error(SDCEF_ERR_INVALID, "mlp_get_params: NULL");
+  cudaError_t e = cudaMemcpyAsync(params_host, h->p, kNParam * 4, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
+}
+
+int sdcef_mlp_features(sdcef_mlp* h, const sdcef_batch* b, void* X_bf16) {
+  if (!h || !X_bf16) return report_error(SDCEF_ERR_INVALID, "mlp_features: NULL");
+  int rc = check_batch(b);
+  if (rc || b->ncol == 0) return rc;
+  FeatArgs a = feat_args(b);
+  a.X = (__nv_bfloat16*)X_bf16;
+  a.mode = 0;
+  feat_kernel<<<(unsigned)b->ncol, 128, 0, h->st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
+}
+
+int sdcef_mlp_targets(sdcef_mlp* h, const sdcef_batch* b, const double* ne_star,
+                      const double* phi_star, float* targets) {
+  if (!h || !ne_star || !phi_star || !targets) return report_error(SDCEF_ERR_INVALID, "mlp_targets: NULL");
+  int rc = check_batch(b);
+  if (rc || b->ncol == 0) return rc;
+  FeatArgs a = feat_args(b);
+  a.ne_star = ne_star;
+  a.phi_star = phi_star;
+  a.Tgt = targets;
+  a.mode = 1;
+  feat_kernel<<<(unsigned)b->ncol, 128, 0, h->st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
+}
+
+int sdcef_mlp_forward(sdcef_mlp* h, const void* X_bf16, int64_t n, float* Y) {
+  if (!h || !X_bf16 || n < 0) return report_error(SDCEF_ERR_INVALID, "mlp_forward: bad arguments");
+  if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_forward: n exceeds max_rows");
+  if (n == 0) return SDCEF_SUCCESS;
+  h->launches = 0;
+  cudaError_t e = forward(h, (const __nv_bfloat16*)X_bf16, n, false);
+  if (e == cudaSuccess && Y)
+    e = cudaMemcpyAsync(Y, h->Y, (size_t)n * kOut * 4, cudaMemcpyDeviceToDevice, h->st);
+  return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
+}
+
+int sdcef_mlp_grad(sdcef_mlp* h, const void* X_bf16, const float* T, int64_t n, float* grads,
+                   float* loss) {
+  if (!h || !X_bf16 || !T || n < 1) return report_error(SDCEF_ERR_INVALID, "mlp_grad: bad arguments");
+  if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_grad: n exceeds max_rows");
+  h->launches = 0;
+  cudaError_t e = cudaMemsetAsync(h->g, 0, kNParam * 4, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->loss, 0, 4, h->st);
+  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, n, true);
+  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, T, n);
+  if (e == cudaSuccess && grads)
+    e = cudaMemcpyAsync(grads, h->g, kNParam * 4, cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, h->loss, 4, cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->g, 0, kNParam * 4, h->st);
+  return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
+}
+
+int sdcef_mlp_train_step(sdcef_mlp* h, const void* X_bf16, const float* T, int64_t n, float lr,
+                         float* loss) {
+  if (!h || !X_bf16 || !T || n < 1 || !(lr > 0.0f))
+    return report_error(SDCEF_ERR_INVALID, "mlp_train_step: bad arguments");
+  if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_train_step: n exceeds max_rows");
+  h->launches = 0;
+  cudaError_t e = cudaMemsetAsync(h->loss, 0, 4, h->st);
+  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, n, true);
+  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, T, n);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - powf(b1, (float)h->step), c2 = 1.0f - powf(b2, (float)h->step);
+  adam_kernel<<<64, 256, 0, h->st>>>(h->p, h->g, h->m, h->v, kNParam, lr, b1, b2, 1e-8f, c1, c2,
+                                      h->w1, h->w2, h->w3);
+  ++h->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  if (loss) e = cudaMemcpyAsync(loss, h->loss, 4, cudaMemcpyDeviceToDevice, h->st);
+  return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
+}
+
+int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int components,
+                    double* ne_guess, double* phi_guess) {
+  if (!h || !ne_guess || !phi_guess || ncells < 0 || components < 0 || components > 3)
+    return report_error(SDCEF_ERR_INVALID, "mlp_guess: bad arguments");
+  if (ncells > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
+  int rc = check_batch(b);
+  if (rc || b->ncol == 0) return rc;
+  h->launches = 0;
+  FeatArgs a = feat_args(b);
+  a.X = h->X;
+  a.mode = 0;
+  feat_kernel<<<(unsigned)b->ncol, 128, 0, h->st>>>(a);
+  ++h->launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = forward(h, h->X, ncells, false);
+  if (e != cudaSuccess) return cuda_fail(e);
+  a.mode = 2;
+  a.comps = components;
+  a.Y = h->Y;
+  a.ne_g = ne_guess;
+  a.phi_g = phi_guess;
+  feat_kernel<<<(unsigned)b->ncol, 128, 0, h->st>>>(a);
+  ++h->launches;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
+}
+
+int sdcef_mlp_last_launch_count(const sdcef_mlp* h) { return h ? h->launches : 0; }
+
+}  // extern "C"

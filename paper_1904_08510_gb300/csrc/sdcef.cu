@@ -311,6 +311,104 @@ int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* 
   return run(ctx, a, tpb);
 }
 
+int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out, int reps,
+                   int* tpb_out, float* ms_out) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  if (reps < 1 || reps > 100) return set_err(SDCEF_ERR_INVALID, "autotune: reps out of range");
+  const int cands[4] = {32, 64, 128, 256};
+  const sdcef_params saved = ctx->p;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  int best = 0;
+  float best_ms = 0.0f;
+  int rc = SDCEF_SUCCESS;
+  for (int ci = 0; ci < 4 && rc == SDCEF_SUCCESS; ++ci) {
+    ctx->p.threads_per_column = cands[ci];
+    rc = sdcef_solve_batch(ctx, b, out);   // warm-up (also loads the kernel)
+    if (rc) break;
+    float tot = 0.0f;
+    for (int r = 0; r < reps && rc == SDCEF_SUCCESS; ++r) {
+      e = cudaEventRecord(e0, ctx->stream);
+      if (e == cudaSuccess) rc = sdcef_solve_batch(ctx, b, out);
+      if (e == cudaSuccess && rc == SDCEF_SUCCESS) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess && rc == SDCEF_SUCCESS) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess && rc == SDCEF_SUCCESS) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) rc = set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+      tot += ms;
+    }
+    if (rc == SDCEF_SUCCESS) {
+      const float ms = tot / reps;
+      if (ms_out) ms_out[ci] = ms;
+      if (best == 0 || ms < best_ms) { best = cands[ci]; best_ms = ms; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->p = saved;
+  if (rc) return rc;
+  ctx->p.threads_per_column = best;
+  if (tpb_out) *tpb_out = best;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* phi,
+                           double kappa_ion, double* n_ion_out) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, b, false);
+  if (rc) return rc;
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (!phi || !n_ion_out || !(kappa_ion >= 0.0)) return set_err(SDCEF_ERR_INVALID, "ion_update: bad arguments");
+  if (b->n_species == 0) return SDCEF_SUCCESS;
+  IonArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ncol = b->ncol;
+  a.col_off = b->col_off;
+  a.length = b->length;
+  a.dt = b->dt;
+  a.vl = b->v_left;
+  a.vr = b->v_right;
+  a.phi = phi;
+  a.n_in = b->n_ion;
+  a.n_out = n_ion_out;
+  a.nsp = b->n_species;
+  for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
+  a.kappa = kappa_ion;
+  cudaError_t e = launch_ion_update(a, ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kappa_ion,
+                    double* n_ion_work, const sdcef_result* out) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, b, true);
+  if (rc) return rc;
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (k_max < 1 || k_max > 64 || !n_ion_work || !(kappa_ion >= 0.0))
+    return set_err(SDCEF_ERR_INVALID, "sdc_sweep: bad arguments");
+  if (!out || !out->ne_out || !out->phi_out) return set_err(SDCEF_ERR_INVALID, "result: ne_out / phi_out is NULL");
+  int launches = 0;
+  for (int k = 0; k < k_max; ++k) {
+    const double* phi_field = (k == 0) ? b->phi_old : out->phi_out;
+    rc = sdcef_ion_update_batch(ctx, b, phi_field, kappa_ion, n_ion_work);
+    if (rc) return rc;
+    sdcef_batch bk = *b;
+    bk.n_ion = b->n_species > 0 ? n_ion_work : b->n_ion;
+    if (k > 0) {
+      bk.ne_guess = out->ne_out;
+      bk.phi_guess = out->phi_out;
+    }
+    rc = sdcef_solve_batch(ctx, &bk, out);
+    if (rc) return rc;
+    launches += ctx->launches + (b->n_species > 0 ? 1 : 0);
+  }
+  ctx->launches = launches;
+  return SDCEF_SUCCESS;
+}
+
 int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne, const double* phi,
                          double* F_e, double* F_phi) {
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");

@@ -86,6 +86,18 @@ int occupancy_t(size_t smem);
 cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int shift, int* order,
                          cudaStream_t st);
 
+// Provisional charged species of one SDC iteration (electric drift only).
+struct IonArgs {
+  int64_t ncol;
+  const int64_t* col_off;
+  const double *length, *dt, *vl, *vr, *phi, *n_in;
+  double* n_out;
+  int nsp;
+  int val[SDCEF_MAX_SPECIES];
+  double kappa;
+};
+cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st);
+
 #ifdef SDCEF_KERNEL_TU
 // --------------------------------------------------------------------------
 // Block reductions
@@ -1127,6 +1139,46 @@ __global__ void order_kernel(const int64_t* col_off, int64_t ncol, int nbins, in
 }
 
 
+
+// n~_i = n_i - (dt/h) (Phi_{i+1/2} - Phi_{i-1/2}), Phi = w n_upwind with the
+// drift velocity w = nu kappa E at the face (E = -dphi/dx; the electrode faces
+// use the second-order one-sided gradient); electrodes absorb outgoing ions
+// and emit none. One CTA per column.
+__global__ void ion_update_kernel(IonArgs a) {
+  const int64_t c = blockIdx.x;
+  if (c >= a.ncol) return;
+  const int64_t off = a.col_off[c];
+  const int N = (int)(a.col_off[c + 1] - off);
+  if (N < 2) return;
+  const int64_t cells = a.col_off[a.ncol];
+  const double h = a.length[c] / N, ih = 1.0 / h, r = a.dt[c] * ih;
+  const double* p = a.phi + off;
+  const double GL = (-8.0 * a.vl[c] + 9.0 * p[0] - p[1]) * (ih * (1.0 / 3.0));
+  const double GR = (8.0 * a.vr[c] - 9.0 * p[N - 1] + p[N - 2]) * (ih * (1.0 / 3.0));
+  for (int s = 0; s < a.nsp; ++s) {
+    const double* ni = a.n_in + (int64_t)s * cells + off;
+    double* no = a.n_out + (int64_t)s * cells + off;
+    const double nk = (double)a.val[s] * a.kappa;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      double fl, fr;
+      if (i == 0) {
+        double w = -nk * GL;
+        fl = w < 0.0 ? w * ni[0] : 0.0;
+      } else {
+        double w = -nk * (p[i] - p[i - 1]) * ih;
+        fl = w * (w > 0.0 ? ni[i - 1] : ni[i]);
+      }
+      if (i == N - 1) {
+        double w = -nk * GR;
+        fr = w > 0.0 ? w * ni[N - 1] : 0.0;
+      } else {
+        double w = -nk * (p[i + 1] - p[i]) * ih;
+        fr = w * (w > 0.0 ? ni[i] : ni[i + 1]);
+      }
+      no[i] = ni[i] - r * (fr - fl);
+    }
+  }
+}
 
 #endif  // SDCEF_WITH_ORDER
 

@@ -1,0 +1,165 @@
+"""Training and evaluation of the learned Newton initial guess.
+
+Data: converged solves of seeded single-flame columns (256 cells, the profile
+family of workload.make_batch(kind="single")), solved by the batched FP64 JFNK
+on the GPU; features and targets are produced by the library's own kernels
+(sdcef_mlp_features / sdcef_mlp_targets). Training runs the library's BF16
+forward/backward kernels and its Adam step. Evaluation solves held-out columns
+with and without the guess and compares Newton and GMRES iteration counts.
+"""
+from __future__ import annotations
+
+import os
+import time
+
+import numpy as np
+
+from . import sdcef as S
+from .workload import make_batch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(HERE, "data", "mlp_weights.npz")
+
+
+def init_params(seed=0):
+    """He-style initial parameters, flat FP32 in the order of the C ABI."""
+    rng = np.random.default_rng(seed)
+    p = dict(W1=rng.standard_normal((128, 32)) * np.sqrt(2.0 / 25),
+             b1=np.zeros(128),
+             W2=rng.standard_normal((128, 128)) * np.sqrt(2.0 / 128),
+             b2=np.zeros(128),
+             W3=rng.standard_normal((2, 128)) * np.sqrt(1.0 / 128) * 0.1,
+             b3=np.zeros(2))
+    p["W1"][:, 25:] = 0.0
+    return S.pack_params(p).astype(np.float32)
+
+
+def generate(ncol: int, seed: int, *, n_cells=256, n_range=None, chunk=8192, device="cuda:0",
+             eps_F=1e-10):
+    """Solve ncol seeded columns on the GPU; return (features bf16 [cells,32],
+    targets f32 [cells,2]) device tensors and the solve statistics."""
+    import torch
+    Xs, Ts, stats = [], [], []
+    mlp = S.MLP(1, )
+    for c0 in range(0, ncol, chunk):
+        n = min(chunk, ncol - c0)
+        b = make_batch("single", n, seed + c0, n_cells=None if n_range else n_cells, n_range=n_range)
+        db = S.DeviceBatch.from_host(b, device)
+        solver = S.Solver(S.default_params(eps_F=eps_F), max_cols=n, max_cells=b.ncells,
+                          max_col_cells=int(b.lengths().max()))
+        out = solver.solve(db)
+        X = mlp.features(db)
+        T = mlp.targets(db, out["ne"], out["phi"])
+        ok = out["status"] == S.STATUS_OK
+        torch.cuda.synchronize()
+        Xs.append(X)
+        Ts.append(T)
+        stats.append(int(ok.sum().item()))
+        solver.close()
+    mlp.close()
+    return torch.cat(Xs), torch.cat(Ts), sum(stats)
+
+
+def train(X, T, *, steps: int, batch: int = 32768, lr: float = 2e-3, lr_end: float = 1e-4,
+          seed: int = 0, params=None, log_every: int = 0):
+    """Adam on contiguous random windows of (X, T); cosine learning-rate decay.
+    Returns (mlp handle with the trained parameters, loss history)."""
+    import torch
+    rows = X.shape[0]
+    batch = min(batch, rows)
+    mlp = S.MLP(batch)
+    mlp.set_params(init_params(seed) if params is None else params)
+    rng = np.random.default_rng(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    hist = []
+    for it in range(steps):
+        o = int(rng.integers(0, rows - batch + 1))
+        a = lr_end + 0.5 * (lr - lr_end) * (1 + np.cos(np.pi * it / max(steps - 1, 1)))
+        mlp.train_step(X[o:o + batch], T[o:o + batch], a, loss)
+        if log_every and (it % log_every == 0 or it == steps - 1):
+            torch.cuda.synchronize()
+            hist.append((it, float(loss.item())))
+    torch.cuda.synchronize()
+    return mlp, hist
+
+
+def evaluate(params, ncol: int, seed: int, *, n_range=(512, 2048), device="cuda:0", reps=3,
+             variants=(("learned", 1),)):
+    """Held-out solves with and without the learned guess (FP64 batched JFNK).
+    variants: (name, components) pairs; components = 1 applies the predicted
+    n_e increment only, 3 applies n_e and phi."""
+    import torch
+    b = make_batch("single", ncol, seed, n_range=n_range)
+    db = S.DeviceBatch.from_host(b, device)
+    solver = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells,
+                      max_col_cells=int(b.lengths().max()))
+    mlp = S.MLP(b.ncells)
+    mlp.set_params(params)
+    res = {}
+    comps = dict(variants)
+    for name in ("plain",) + tuple(comps):
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if name != "plain":
+                ne, phi = mlp.guess(db, components=comps[name])
+                out = solver.solve(db.with_guess(ne, phi))
+            else:
+                out = solver.solve(db)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        st = out["status"].cpu().numpy()
+        nw = out["newton_it"].cpu().numpy()
+        kr = out["krylov_it"].cpu().numpy()
+        res[name] = dict(ms=float(np.median(times)), status_ok=int((st == 0).sum()),
+                         newton_mean=float(nw.mean()), newton_p50=float(np.median(nw)),
+                         newton_p99=float(np.percentile(nw, 99)), krylov_mean=float(kr.mean()),
+                         solves_per_s=b.ncol / (np.median(times) / 1e3),
+                         ne=out["ne"].cpu().numpy(), phi=out["phi"].cpu().numpy())
+    solver.close()
+    mlp.close()
+    return b, res
+
+
+def save(params, path=WEIGHTS, meta=None):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, params=np.asarray(params, dtype=np.float32), meta=np.array(repr(meta or {})))
+
+
+def load(path=WEIGHTS):
+    with np.load(path) as z:
+        return z["params"].astype(np.float32)
+
+
+def main():
+    """Train on converged single-flame solves and report held-out gains."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--ncol", type=int, default=200_000)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--batch", type=int, default=32768)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--eval-ncol", type=int, default=4096)
+    ap.add_argument("--out", default=WEIGHTS)
+    args = ap.parse_args()
+    t0 = time.perf_counter()
+    X, T, nok = generate(args.ncol, 1_000_000)
+    t1 = time.perf_counter()
+    mlp, hist = train(X, T, steps=args.steps, batch=args.batch, lr=args.lr, log_every=500)
+    t2 = time.perf_counter()
+    params = mlp.get_params()
+    save(params, args.out, dict(ncol=args.ncol, steps=args.steps, batch=args.batch, lr=args.lr))
+    b, res = evaluate(params, args.eval_ncol, 2_000_000,
+                      variants=(("learned_ne", 1), ("learned_ne_phi", 3)))
+    summary = dict(train_columns=args.ncol, train_samples=int(X.shape[0]), converged=nok,
+                   data_s=t1 - t0, train_s=t2 - t1, loss=hist,
+                   eval={k: {kk: vv for kk, vv in v.items() if kk not in ("ne", "phi")}
+                         for k, v in res.items()})
+    print(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()

@@ -29,7 +29,14 @@ MAX_SPECIES = 16
 EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_params",
            "sdcef_solve_batch", "sdcef_solve_batch_host", "sdcef_residual_batch",
            "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count",
-           "sdcef_solve_batch_noalloc")
+           "sdcef_solve_batch_noalloc", "sdcef_ion_update_batch", "sdcef_sdc_sweep",
+           "sdcef_autotune",
+           "sdcef_mlp_create", "sdcef_mlp_destroy",
+           "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
+           "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
+           "sdcef_mlp_guess", "sdcef_mlp_last_launch_count")
+MLP_NPARAM = 20994
+GUESS_NE, GUESS_PHI = 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NOALLOC_MAX_COLS = 65536
 NOALLOC_MAX_COL_CELLS = 4096
@@ -86,6 +93,29 @@ def lib():
         L.sdcef_last_error.argtypes = []
         L.sdcef_last_launch_count.argtypes = [vp]
         L.sdcef_solve_batch_noalloc.argtypes = [P, B, R, C.c_int, vp]
+        L.sdcef_ion_update_batch.argtypes = [vp, B, vp, C.c_double, vp]
+        L.sdcef_sdc_sweep.argtypes = [vp, B, C.c_int, C.c_double, vp, R]
+        L.sdcef_ion_update_batch.restype = C.c_int
+        L.sdcef_autotune.argtypes = [vp, B, R, C.c_int, C.POINTER(C.c_int), vp]
+        L.sdcef_autotune.restype = C.c_int
+        L.sdcef_sdc_sweep.restype = C.c_int
+        i64 = C.c_int64
+        L.sdcef_mlp_create.argtypes = [C.POINTER(vp), i64, vp]
+        L.sdcef_mlp_destroy.argtypes = [vp]
+        L.sdcef_mlp_set_params.argtypes = [vp, vp]
+        L.sdcef_mlp_get_params.argtypes = [vp, vp]
+        L.sdcef_mlp_features.argtypes = [vp, B, vp]
+        L.sdcef_mlp_targets.argtypes = [vp, B, vp, vp, vp]
+        L.sdcef_mlp_forward.argtypes = [vp, vp, i64, vp]
+        L.sdcef_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.sdcef_mlp_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp]
+        L.sdcef_mlp_guess.argtypes = [vp, B, i64, C.c_int, vp, vp]
+        L.sdcef_mlp_last_launch_count.argtypes = [vp]
+        for f in ("sdcef_mlp_create", "sdcef_mlp_destroy", "sdcef_mlp_set_params",
+                  "sdcef_mlp_get_params", "sdcef_mlp_features", "sdcef_mlp_targets",
+                  "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
+                  "sdcef_mlp_guess", "sdcef_mlp_last_launch_count"):
+            getattr(L, f).restype = C.c_int
         for f in ("sdcef_create", "sdcef_destroy", "sdcef_set_params", "sdcef_solve_batch",
                   "sdcef_solve_batch_host", "sdcef_residual_batch", "sdcef_precond_apply_batch",
                   "sdcef_last_launch_count", "sdcef_solve_batch_noalloc"):
@@ -239,6 +269,40 @@ class Solver:
         _check(lib().sdcef_solve_batch_host(self.h, C.byref(bs), C.byref(rs)))
         return out
 
+    def autotune(self, db: DeviceBatch, reps: int = 2):
+        """sdcef_autotune: pick threads per column for this batch by timing."""
+        out = self.alloc_result(db)
+        bs = db.cstruct()
+        rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), None, None, None, None, None)
+        tpb = C.c_int(0)
+        ms = (C.c_float * 4)()
+        _check(lib().sdcef_autotune(self.h, C.byref(bs), C.byref(rs), int(reps), C.byref(tpb),
+                                    C.cast(ms, C.c_void_p)))
+        self.params.threads_per_column = tpb.value
+        return tpb.value, {t: float(m) for t, m in zip((32, 64, 128, 256), ms)}
+
+    def ion_update(self, db: DeviceBatch, phi, kappa_ion: float = 4e-3):
+        import torch
+        out = torch.empty_like(db.tensors["n_ion"])
+        bs = db.cstruct()
+        _check(lib().sdcef_ion_update_batch(self.h, C.byref(bs), _ptr(phi), float(kappa_ion),
+                                            _ptr(out)))
+        return out
+
+    def sdc_sweep(self, db: DeviceBatch, k_max: int = 4, kappa_ion: float = 4e-3,
+                  work=None, out: dict | None = None) -> dict:
+        """sdcef_sdc_sweep: k_max SDC iterations of the electric solve."""
+        import torch
+        out = out or self.alloc_result(db)
+        work = torch.empty_like(db.tensors["n_ion"]) if work is None else work
+        bs = db.cstruct()
+        rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), _ptr(out["status"]),
+                     _ptr(out["newton_it"]), _ptr(out["krylov_it"]), _ptr(out["res_evals"]),
+                     _ptr(out["final_res"]))
+        _check(lib().sdcef_sdc_sweep(self.h, C.byref(bs), int(k_max), float(kappa_ion),
+                                     _ptr(work), C.byref(rs)))
+        return out
+
     def residual(self, db: DeviceBatch, ne, phi):
         import torch
         Fe = torch.empty_like(ne)
@@ -270,4 +334,101 @@ def solve_noalloc(params: Params, db: DeviceBatch, out: dict, max_col_cells: int
                  _ptr(out["final_res"]))
     _check(lib().sdcef_solve_batch_noalloc(C.byref(params), C.byref(bs), C.byref(rs),
                                            int(max_col_cells), C.c_void_p(stream.cuda_stream)))
+    return out
+
+
+class MLP:
+    """The learned Newton initial guess (sdcef_mlp_* of include/sdcef.h)."""
+
+    def __init__(self, max_rows: int, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().sdcef_mlp_create(C.byref(h), int(max_rows), C.c_void_p(stream.cuda_stream)))
+        self.h = h
+        self.max_rows = int(max_rows)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sdcef_mlp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat: np.ndarray):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.shape == (MLP_NPARAM,)
+        _check(lib().sdcef_mlp_set_params(self.h, a.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(MLP_NPARAM, dtype=np.float32)
+        _check(lib().sdcef_mlp_get_params(self.h, a.ctypes.data))
+        return a
+
+    def launches(self) -> int:
+        return int(lib().sdcef_mlp_last_launch_count(self.h))
+
+    def features(self, db: DeviceBatch):
+        import torch
+        X = torch.empty((db.ncells, 32), dtype=torch.bfloat16, device=db.tensors["ne_old"].device)
+        bs = db.cstruct()
+        _check(lib().sdcef_mlp_features(self.h, C.byref(bs), _ptr(X)))
+        return X
+
+    def targets(self, db: DeviceBatch, ne_star, phi_star):
+        import torch
+        T = torch.empty((db.ncells, 2), dtype=torch.float32, device=ne_star.device)
+        bs = db.cstruct()
+        _check(lib().sdcef_mlp_targets(self.h, C.byref(bs), _ptr(ne_star), _ptr(phi_star), _ptr(T)))
+        return T
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _check(lib().sdcef_mlp_forward(self.h, _ptr(X), int(X.shape[0]), _ptr(Y)))
+        return Y
+
+    def grad(self, X, T):
+        import torch
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib().sdcef_mlp_grad(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(g), _ptr(loss)))
+        return g, loss
+
+    def train_step(self, X, T, lr: float, loss=None):
+        _check(lib().sdcef_mlp_train_step(self.h, _ptr(X), _ptr(T), int(X.shape[0]),
+                                          float(lr), _ptr(loss)))
+
+    def guess(self, db: DeviceBatch, ne=None, phi=None, components: int = 3):
+        import torch
+        dev = db.tensors["ne_old"].device
+        ne = torch.empty(db.ncells, dtype=torch.float64, device=dev) if ne is None else ne
+        phi = torch.empty(db.ncells, dtype=torch.float64, device=dev) if phi is None else phi
+        bs = db.cstruct()
+        _check(lib().sdcef_mlp_guess(self.h, C.byref(bs), int(db.ncells), int(components),
+                                     _ptr(ne), _ptr(phi)))
+        return ne, phi
+
+
+def pack_params(p: dict) -> np.ndarray:
+    """Flatten {W1, b1, W2, b2, W3, b3} in the order of the C ABI."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+def unpack_params(flat) -> dict:
+    flat = np.asarray(flat, dtype=np.float64)
+    shapes = (("W1", (128, 32)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+              ("W3", (2, 128)), ("b3", (2,)))
+    out, o = {}, 0
+    for k, sh in shapes:
+        n = int(np.prod(sh))
+        out[k] = flat[o:o + n].reshape(sh).copy()
+        o += n
     return out

@@ -111,7 +111,7 @@ def make_batch(kind: str, ncol: int, seed: int, *, n_cells=None, n_range=None,
     """Draw ``ncol`` columns of one of the synthetic profile families.
 
     kind = "single": flame at 5 mm, ion peak 1e16 * U(0.5, 1.5), V_R ~ U(-300, 300),
-                     n_cells cells per column (default 256).
+                     n_cells cells per column (default 256), or cells ~ U{n_range}.
     kind = "ragged": cells ~ U{n_range} (default 128..2048), flame ~ U(3, 7) mm,
                      ion peak log-uniform in [1e15, 1e17], V_R ~ U(-500, 500).
     """
@@ -119,7 +119,10 @@ def make_batch(kind: str, ncol: int, seed: int, *, n_cells=None, n_range=None,
     for c in range(ncol):
         rng = np.random.Generator(np.random.PCG64(seed + c))
         if kind == "single":
-            n = 256 if n_cells is None else int(n_cells)
+            if n_range is not None and n_cells is None:
+                n = int(rng.integers(n_range[0], n_range[1] + 1))
+            else:
+                n = 256 if n_cells is None else int(n_cells)
             amp = 1e16 * rng.uniform(0.5, 1.5)
             v_right = rng.uniform(-300.0, 300.0)
             x_f = 0.005
@@ -160,3 +163,19 @@ def uniform_batch(ncol: int, n: int, *, ne: float, n_ion: float, T: float, v_lef
         ne_old=np.full(ncol * n, ne), phi_old=rep(phi), n_ion=np.full((1, ncol * n), n_ion),
         valence=np.array([1], dtype=np.int32), T=np.full(ncol * n, T),
         rho=np.full(ncol * n, P0 * W_MIX / (R_U * T)), meta={"kind": "uniform"})
+
+
+KAPPA_ION = 4e-3   # m^2/(V s): H3O+ mobility implied by the relaxation-time table (Sec. 4.4)
+
+
+def sdc_batch(ncol: int, seed: int, *, n_cells: int = 1024, cfl: float = 0.5,
+              kappa_ion: float = KAPPA_ION) -> Batch:
+    """Columns of the "ragged" profile family with a fixed cell count and a time
+    step set by the ion drift CFL: dt = cfl h / (kappa_ion |V_R - V_L| / L),
+    the constant-CFL stepping of the paper's runs (Sec. 4.2)."""
+    b = make_batch("ragged", ncol, seed, n_cells=n_cells)
+    h = b.length / n_cells
+    e = np.maximum(np.abs(b.v_right - b.v_left) / b.length, 1e3)
+    b.dt = cfl * h / (kappa_ion * e)
+    b.meta.update(kind="sdc", cfl=cfl, kappa_ion=kappa_ion)
+    return b

@@ -1,0 +1,148 @@
+"""GPU kernels of the learned initial guess against the FP64 numpy oracle.
+
+BF16 bar: features match the oracle rounded to bfloat16 to one BF16 ulp; the
+network output and every parameter gradient match the oracle evaluated on the
+same BF16-rounded weights and inputs to 2e-2 relative (BF16 activations and
+operands carry 8 significant bits; accumulation is FP32).
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_1904_08510_gb300.workload import make_batch
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1904_08510_gb300 import sdcef as S  # noqa: E402
+from paper_1904_08510_gb300 import learned as Lrn  # noqa: E402
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return "cuda:0"
+
+
+def rounded_params(seed=3):
+    p = M.init_params(seed)
+    rng = np.random.default_rng(seed)
+    for k in ("b1", "b2", "b3"):
+        p[k] = 0.1 * rng.standard_normal(p[k].shape)
+    p["W1"][:, 25:] = 0.0
+    flat = S.pack_params(p).astype(np.float32)
+    q = S.unpack_params(flat.astype(np.float64))
+    for k in ("W1", "W2", "W3"):
+        q[k] = M.bf16_round(q[k])
+    return flat, q
+
+
+def test_features_match_oracle():
+    d = dev()
+    b = make_batch("ragged", 5, 31, n_range=(3, 300))
+    db = S.DeviceBatch.from_host(b, d)
+    mlp = S.MLP(16)
+    X = mlp.features(db).float().cpu().numpy()
+    ref = M.bf16_round(M.features(b))
+    tol = 2.0 ** -7 * np.abs(ref) + 1e-30
+    assert np.all(np.abs(X - ref) <= tol)
+
+
+def test_targets_and_guess_round_trip():
+    d = dev()
+    b = make_batch("ragged", 4, 8, n_range=(20, 200))
+    db = S.DeviceBatch.from_host(b, d)
+    rng = np.random.default_rng(0)
+    ne = b.ne_old * (1 + 0.2 * rng.standard_normal(b.ncells))
+    phi = b.phi_old + 3 * rng.standard_normal(b.ncells)
+    mlp = S.MLP(16)
+    T = mlp.targets(db, torch.as_tensor(ne, device=d), torch.as_tensor(phi, device=d))
+    ref = M.targets(b, ne, phi)
+    np.testing.assert_allclose(T.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
+
+
+def test_forward_matches_oracle_on_bf16_weights():
+    d = dev()
+    flat, q = rounded_params()
+    rng = np.random.default_rng(1)
+    n = 1000
+    Xh = M.bf16_round(rng.standard_normal((n, 32)))
+    Xh[:, 25:] = 0.0
+    mlp = S.MLP(n)
+    mlp.set_params(flat)
+    X = torch.as_tensor(Xh, dtype=torch.float32, device=d).to(torch.bfloat16)
+    Y = mlp.forward(X).cpu().numpy()
+    Yr, _ = M.forward(q, Xh)
+    assert np.linalg.norm(Y - Yr) <= 2e-2 * np.linalg.norm(Yr)
+
+
+@pytest.mark.parametrize("n", [37, 700])
+def test_gradients_match_fp64_backprop(n):
+    d = dev()
+    flat, q = rounded_params(5)
+    rng = np.random.default_rng(n)
+    Xh = M.bf16_round(rng.standard_normal((n, 32)))
+    Xh[:, 25:] = 0.0
+    Th = rng.standard_normal((n, 2))
+    mlp = S.MLP(n)
+    mlp.set_params(flat)
+    X = torch.as_tensor(Xh, dtype=torch.float32, device=d).to(torch.bfloat16)
+    T = torch.as_tensor(Th, dtype=torch.float32, device=d)
+    g, loss = mlp.grad(X, T)
+    g = S.unpack_params(g.cpu().numpy())
+    Y, cache = M.forward(q, Xh)
+    lr, dY = M.mse(Y, Th)
+    gr = M.backward(q, cache, dY)
+    assert float(loss.item()) == pytest.approx(lr, rel=2e-2)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a, r = g[k], gr[k]
+        if k == "W1":
+            a, r = a[:, :25], r[:, :25]
+        assert np.linalg.norm(a - r) <= 2e-2 * np.linalg.norm(r), k
+
+
+def test_adam_step_matches_oracle():
+    d = dev()
+    flat, q = rounded_params(7)
+    rng = np.random.default_rng(2)
+    n = 256
+    Xh = M.bf16_round(rng.standard_normal((n, 32)))
+    Xh[:, 25:] = 0.0
+    Th = rng.standard_normal((n, 2))
+    mlp = S.MLP(n)
+    mlp.set_params(flat)
+    X = torch.as_tensor(Xh, dtype=torch.float32, device=d).to(torch.bfloat16)
+    T = torch.as_tensor(Th, dtype=torch.float32, device=d)
+    mlp.train_step(X, T, 1e-3)
+    got = S.unpack_params(mlp.get_params())
+    p0 = S.unpack_params(flat.astype(np.float64))
+    # first Adam step moves every parameter with a non-negligible gradient by ~lr
+    Y, cache = M.forward(q, Xh)
+    _, dY = M.mse(Y, Th)
+    gr = M.backward(q, cache, dY)
+    for k in ("W2", "b2", "W3"):
+        big = np.abs(gr[k]) > 1e-3 * np.abs(gr[k]).max()
+        step = (p0[k] - got[k])[big]
+        np.testing.assert_allclose(np.abs(step), 1e-3, rtol=2e-2)
+        assert np.mean(np.sign(step) == np.sign(gr[k][big])) > 0.97
+
+
+def test_training_reduces_loss_and_newton_iterations():
+    """A short training run on converged solves lowers the loss and the Newton
+    iterations of held-out columns (what the learned guess is for). The
+    predicted n_e increment is applied; phi starts at phi^n (the predicted phi
+    increment is too coarse for the exponential Scharfetter-Gummel fluxes)."""
+    dev()
+    X, T, nok = Lrn.generate(2048, 3_000_000)
+    mlp, hist = Lrn.train(X, T, steps=1500, batch=16384, lr=2e-3, log_every=100)
+    assert hist[-1][1] < 0.5 * hist[0][1], hist
+    params = mlp.get_params()
+    b, res = Lrn.evaluate(params, 128, 4_000_000, n_range=(256, 1024), reps=1,
+                          variants=(("learned", S.GUESS_NE),))
+    assert res["plain"]["status_ok"] == b.ncol and res["learned"]["status_ok"] == b.ncol
+    assert res["learned"]["newton_mean"] < res["plain"]["newton_mean"], res
+    # the guess changes the start, not the root
+    for c in range(b.ncol):
+        s = slice(b.col_off[c], b.col_off[c + 1])
+        e = np.abs(res["learned"]["ne"][s] - res["plain"]["ne"][s]).max() / np.abs(res["plain"]["ne"][s]).max()
+        assert e < 1e-8

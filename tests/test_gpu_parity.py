@@ -327,3 +327,19 @@ def test_outputs_may_alias_inputs():
     s.solve(db, out)
     torch.cuda.synchronize()
     assert torch.equal(out["ne"], ref["ne"]) and torch.equal(out["phi"], ref["phi"])
+
+
+def test_autotune_picks_a_candidate_and_keeps_results():
+    d = dev()
+    b = make_batch("ragged", 40, 321, n_range=(64, 700))
+    s = solver_for(b)
+    db = S.DeviceBatch.from_host(b, d)
+    ref = s.solve(db)
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    tpb, ms = s.autotune(db, reps=1)
+    assert tpb in (32, 64, 128, 256) and ms[tpb] == min(ms.values())
+    out = s.solve(db)
+    torch.cuda.synchronize()
+    assert (out["status"].cpu().numpy() == ref["status"]).all()
+    assert colerr(b, out["ne"].cpu().numpy(), ref["ne"]).max() <= 1e-9

@@ -1,0 +1,80 @@
+"""GPU parity of the SDC electric sweep (provisional ions + k_max solves)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1904_08510_gb300.workload import make_batch, sdc_batch
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1904_08510_gb300 import sdcef as S  # noqa: E402
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return "cuda:0"
+
+
+def colerr(b, a, ref):
+    return np.array([np.abs(a[s] - ref[s]).max() / max(np.abs(ref[s]).max(), 1e-300)
+                     for s in (slice(b.col_off[c], b.col_off[c + 1]) for c in range(b.ncol))])
+
+
+def test_ion_update_matches_oracle():
+    d = dev()
+    b = make_batch("ragged", 7, 91, n_range=(2, 500))
+    b.n_ion = np.vstack([b.n_ion, 0.3 * b.n_ion])
+    b.valence = np.array([1, -1], dtype=np.int32)
+    rng = np.random.default_rng(4)
+    phi = b.phi_old + 20 * rng.standard_normal(b.ncells)
+    s = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells,
+                 max_col_cells=int(b.lengths().max()))
+    db = S.DeviceBatch.from_host(b, d)
+    out = s.ion_update(db, torch.as_tensor(phi, device=d), 4e-3)
+    torch.cuda.synchronize()
+    ref = O.ion_update(b, phi, 4e-3)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("precond", [S.PREC_EXACT, S.PREC_RECAST])
+def test_sdc_sweep_matches_oracle(precond):
+    d = dev()
+    b = sdc_batch(12, 777, n_cells=256)
+    P = S.default_params(eps_F=1e-12, precond=precond, restart_m=30 if precond == S.PREC_RECAST else 8)
+    s = S.Solver(P, max_cols=b.ncol, max_cells=b.ncells, max_col_cells=256)
+    db = S.DeviceBatch.from_host(b, d)
+    out = s.sdc_sweep(db, k_max=4)
+    torch.cuda.synchronize()
+    ne_r, phi_r, hist = O.sdc_sweep(b, 4, 4e-3, O.default_params(precond=2, eps_F=1e-12))
+    assert all((h["status"] == 0).all() for h in hist)
+    assert (out["status"].cpu().numpy() == S.STATUS_OK).all()
+    assert colerr(b, out["ne"].cpu().numpy(), ne_r).max() <= 1e-9
+    assert colerr(b, out["phi"].cpu().numpy(), phi_r).max() <= 1e-9
+
+
+def test_sdc_sweep_graph_replay_matches_eager():
+    d = dev()
+    b = sdc_batch(64, 31, n_cells=512)
+    s = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells, max_col_cells=512)
+    db = S.DeviceBatch.from_host(b, d)
+    eager = s.sdc_sweep(db, k_max=4)
+    torch.cuda.synchronize()
+    eager = {k: v.clone() for k, v in eager.items()}
+    out = s.alloc_result(db)
+    work = torch.empty_like(db.tensors["n_ion"])
+    stream = torch.cuda.Stream()
+    s2 = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells, max_col_cells=512,
+                  stream=stream)
+    s2.sdc_sweep(db, k_max=4, work=work, out=out)     # first call outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        s2.sdc_sweep(db, k_max=4, work=work, out=out)
+    for v in out.values():
+        v.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out["ne"], eager["ne"]) and torch.equal(out["phi"], eager["phi"])
+    assert torch.equal(out["status"], eager["status"])

@@ -387,3 +387,43 @@ def test_plasma_charge_relaxation_rate():
     D = 0.4 * O.K_B * 300.0 / O.E_CHARGE
     k = 2 * np.pi / L
     assert amp == pytest.approx(1.0 / (1.0 + dt / tau + dt * D * k * k), rel=0.01)
+
+
+# --------------------------------------------------------------------------
+# Provisional ions between SDC iterations (electric drift, upwind)
+# --------------------------------------------------------------------------
+def test_ion_update_conserves_and_shifts():
+    """Uniform field, CFL = 1, ions confined away from the electrodes: the upwind
+    step is an exact one-cell shift and the total is conserved."""
+    from paper_1904_08510_gb300.workload import uniform_batch
+    n, L, V = 64, 0.01, -200.0      # phi decreasing to the right? E = -dphi/dx = -V/L > 0 for V < 0
+    b = uniform_batch(1, n, ne=0.0, n_ion=0.0, T=1000.0, v_left=0.0, v_right=V, dt=1.0)
+    kappa = 4e-3
+    h = L / n
+    w = kappa * (-V / L)            # drift velocity of a positive ion
+    b.dt[:] = h / w                  # CFL = 1
+    prof = np.exp(-0.5 * ((np.arange(n) - 20) / 3.0) ** 2)
+    b.n_ion[0, :] = prof
+    out = O.ion_update(b, b.phi_old, kappa)[0]
+    np.testing.assert_allclose(out[1:], prof[:-1], rtol=1e-10, atol=1e-14)
+    assert out.sum() == pytest.approx(prof.sum() - prof[-1], rel=1e-12)
+
+
+def test_ion_update_telescopes_with_absorbing_electrodes():
+    b = make_batch("ragged", 3, 17, n_range=(40, 90))
+    rng = np.random.default_rng(3)
+    phi = b.phi_old + 30 * rng.standard_normal(b.ncells)
+    out = O.ion_update(b, phi, 4e-3)[0]
+    for c in range(b.ncol):
+        s = slice(b.col_off[c], b.col_off[c + 1])
+        n = s.stop - s.start
+        h = b.length[c] / n
+        # interior fluxes cancel; the electrodes only remove ions (no emission)
+        assert np.sum(out[s]) <= np.sum(b.n_ion[0, s]) * (1 + 1e-12)
+        # the change equals the boundary outflow
+        dt = b.dt[c]
+        GL = (-8 * b.v_left[c] + 9 * phi[s][0] - phi[s][1]) / (3 * h)
+        GR = (8 * b.v_right[c] - 9 * phi[s][-1] + phi[s][-2]) / (3 * h)
+        wl, wr = -4e-3 * GL, -4e-3 * GR
+        outflow = (max(wr, 0) * b.n_ion[0, s][-1] - min(wl, 0) * b.n_ion[0, s][0]) * dt / h
+        assert np.sum(b.n_ion[0, s]) - np.sum(out[s]) == pytest.approx(outflow, rel=1e-9, abs=1e-9 * np.sum(b.n_ion[0, s]))
