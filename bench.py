@@ -58,11 +58,7 @@ def parse():
     return ap.parse_args()
 
 
-def dist_info():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+from paper_1904_08510_gb300.replicas import dist_info, job_throughput, max_over_ranks, shard_seed  # noqa: E402
 
 
 def load_peaks():
@@ -225,7 +221,7 @@ def main():
     from paper_1904_08510_gb300 import sdcef as S
     from paper_1904_08510_gb300.workload import make_batch
     # weak scaling: each rank solves its own batch (independent columns, no exchange)
-    b = make_batch("ragged", args.ncol, args.seed + rank * args.ncol)
+    b = make_batch("ragged", args.ncol, shard_seed(args.seed, rank, args.ncol))
     lengths = b.lengths()
     prec = S.MIXED if args.precision == "mixed" else S.FP64
     pc = S.PREC_EXACT if args.precond == "exact" else S.PREC_RECAST
@@ -263,13 +259,8 @@ def main():
             ev[i][1].record(stream)
         barrier()
     ms = [a.elapsed_time(bb) for a, bb in ev]
-    tot_ms = float(sum(ms))
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = b.ncol * ws * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(float(sum(ms)), device=dev)
+    value = job_throughput(b.ncol, ws, args.steps, tot_ms / 1e3)
     st = out["status"].cpu().numpy()
     nw = out["newton_it"].cpu().numpy()
     kr = out["krylov_it"].cpu().numpy()
@@ -416,14 +407,16 @@ def extras(args, S, b, db, solver, params, dev):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=st_):
         ssolver.sdc_sweep(sdb, 4, work=work, out=sout)
-    g.replay()
+    with torch.cuda.stream(st_):
+        g.replay()
     torch.cuda.synchronize()
     tg = []
     for _ in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st_)
-        g.replay()
-        e1.record(st_)
+        with torch.cuda.stream(st_):
+            e0.record(st_)
+            g.replay()
+            e1.record(st_)
         torch.cuda.synchronize()
         tg.append(e0.elapsed_time(e1) / 1e3)
     sst = sout["status"].cpu().numpy()

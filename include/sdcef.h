@@ -96,6 +96,9 @@ typedef struct {
   int precond;        /* SDCEF_PREC_EXACT | SDCEF_PREC_RECAST | SDCEF_PREC_NONE       */
   int bc_electron;    /* SDCEF_BC_ABSORBING | SDCEF_BC_ZERO_GRADIENT                  */
   int threads_per_column; /* 0 = chosen per column length; else 32, 64, 128 or 256    */
+  int guess_newton_cap; /* Newton steps allowed from a supplied start (ne_guess /
+                           phi_guess) before that column restarts from the plain
+                           start X^n with the remaining budget; 0 = never restart  */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -137,7 +140,8 @@ typedef struct {
 /* Fill p with the defaults: eps_F 1e-10, eps_X 0, gamma 1e-4 (Table 1),
  * mobility 0.4 (Sec. 2.2), ls_alpha 1e-4, eps_r 1, restart 8, 50 Newton
  * steps, 200 Krylov iterations per step, 20 halvings, FP64, exact Schur
- * preconditioner, absorbing electrodes, automatic threads per column. */
+ * preconditioner, absorbing electrodes, automatic threads per column, and a
+ * supplied start judged after 12 Newton steps. */
 void sdcef_default_params(sdcef_params* p);
 
 /* Create a solver context. max_cols, max_cells and max_col_cells bound every

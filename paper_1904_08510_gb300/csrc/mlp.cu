@@ -263,6 +263,187 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
   }
 }
 
+// --------------------------------------------------------------------------
+// Fused guess: features -> 3 layers -> X^n + S_X y, one pass per column.
+// Persistent CTAs (4 warps) keep the BF16 weights in shared memory; each warp
+// takes 16 cells, builds their features straight into mma.sync A fragments,
+// and chains the layers in registers: the FP32 accumulators of two adjacent
+// m16n8 tiles hold exactly the A fragment of the next layer's k16 block.
+// --------------------------------------------------------------------------
+struct GuessArgs {
+  FeatArgs f;
+  const float* p;                  // FP32 parameters (biases read from here)
+  const __nv_bfloat16 *w1, *w2, *w3;
+  int* queue;
+  float* stage;                    // [cells][5] per-cell feature values (FP32)
+};
+
+constexpr int W1S = kIn + 8, W2S = kHid + 8;   // padded smem row strides (bf16)
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 sW1[kHid * W1S];
+  __shared__ __align__(16) __nv_bfloat16 sW2[kHid * W2S];
+  __shared__ __align__(16) __nv_bfloat16 sW3[8 * W2S];
+  __shared__ float sb1[kHid], sb2[kHid], sb3[2];
+  __shared__ double red[8];
+  __shared__ int s_col;
+  const FeatArgs& a = g.f;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < kHid * kIn; e += 128) sW1[(e / kIn) * W1S + e % kIn] = g.w1[e];
+  for (int e = tid; e < kHid * kHid; e += 128) sW2[(e / kHid) * W2S + e % kHid] = g.w2[e];
+  for (int e = tid; e < 8 * kHid; e += 128)
+    sW3[(e / kHid) * W2S + e % kHid] = (e / kHid) < kOut ? g.w3[e] : __float2bfloat16(0.0f);
+  for (int e = tid; e < kHid; e += 128) { sb1[e] = g.p[kOffB1 + e]; sb2[e] = g.p[kOffB2 + e]; }
+  if (tid < 2) sb3[tid] = g.p[kOffB3 + tid];
+  const int64_t cells = a.col_off[a.ncol];
+  const int gr = lane >> 2, tc = (lane & 3) * 2;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_col = atomicAdd(g.queue, 1);
+    __syncthreads();
+    const int64_t c = s_col;
+    if (c >= a.ncol) break;
+    const int64_t off = a.col_off[c];
+    const int N = (int)(a.col_off[c + 1] - off);
+    auto fphi = [&](int i) {
+      double q = 0.0;
+      for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * cells + off + i];
+      return q;
+    };
+    double mn = 0.0, mq = 0.0, mp = 0.0;
+    for (int i = tid; i < N; i += 128) {
+      mn = fmax(mn, fabs(a.ne[off + i]));
+      mq = fmax(mq, fabs(fphi(i)));
+      mp = fmax(mp, fabs(a.phi[off + i]));
+    }
+    double mx[3] = {mn, mq, mp};
+    for (int k = 0; k < 3; ++k) {
+      double v = mx[k];
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) red[warp] = v;
+      __syncthreads();
+      mx[k] = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+      __syncthreads();
+    }
+    const double sn = fmax(fmax(mx[0], mx[1]), 1.0);
+    const double sp = fmax(fmax(mx[2], fmax(fabs(a.v_left[c]), fabs(a.v_right[c]))), 1.0);
+    const double isn = 1.0 / sn, isp = 1.0 / sp;
+    if (N < 1) continue;
+    auto mir = [&](int j) {
+      if (j < 0) j = -j - 1;
+      if (j >= N) j = 2 * N - 1 - j;
+      return min(max(j, 0), N - 1);
+    };
+    // stage the five per-cell values once (the only FP64 work per cell); the
+    // stencil gather below reads them back in FP32
+    float* st = g.stage + off * 5;
+    for (int i = tid; i < N; i += 128) {
+      // mirrored neighbours: index -1 -> 0, index N -> N-1
+      const int kp = (i + 1 < N) ? i + 1 : N - 1;
+      const int km = (i >= 1) ? i - 1 : 0;
+      st[i * 5 + 0] = (float)(a.ne[off + i] * isn);
+      st[i * 5 + 1] = (float)(a.phi[off + i] * isp);
+      st[i * 5 + 2] = (float)(fphi(i) * isn);
+      st[i * 5 + 3] = (float)(a.T[off + i] * (1.0 / 2000.0));
+      st[i * 5 + 4] = (float)(-(a.phi[off + kp] - a.phi[off + km]) * 0.5 * isp);
+    }
+    __syncthreads();
+    // feature f (0..31) of cell i: stencil offset f/5 - 2, quantity f%5
+    auto feat = [&](int i, int f) -> float {
+      if (f >= kFeat) return 0.0f;
+      const int k = mir(i + f / 5 - 2);
+      return __bfloat162float(__float2bfloat16(st[k * 5 + f % 5]));
+    };
+    for (int r0 = warp * 16; r0 < N; r0 += 64) {
+      const int ra = min(r0 + gr, N - 1), rb = min(r0 + gr + 8, N - 1);
+      // layer 1 A fragments (K = 32: two k16 blocks)
+      uint32_t a1[2][4];
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        const int k0 = kb * 16 + tc;
+        a1[kb][0] = pack_bf16(feat(ra, k0), feat(ra, k0 + 1));
+        a1[kb][1] = pack_bf16(feat(rb, k0), feat(rb, k0 + 1));
+        a1[kb][2] = pack_bf16(feat(ra, k0 + 8), feat(ra, k0 + 9));
+        a1[kb][3] = pack_bf16(feat(rb, k0 + 8), feat(rb, k0 + 9));
+      }
+      float acc[16][4];
+#pragma unroll
+      for (int nt = 0; nt < 16; ++nt) {
+        acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb) {
+          uint32_t b[2];
+          const __nv_bfloat16* w = sW1 + (nt * 8 + gr) * W1S + kb * 16 + tc;
+          b[0] = *(const uint32_t*)w;
+          b[1] = *(const uint32_t*)(w + 8);
+          mma16816(acc[nt], a1[kb], b);
+        }
+      }
+      // bias + SiLU -> layer 2 A fragments (K = 128: eight k16 blocks)
+      uint32_t a2[8][4];
+#pragma unroll
+      for (int kb = 0; kb < 8; ++kb) {
+        const int n0 = 2 * kb, n1 = 2 * kb + 1;
+        const float b00 = sb1[n0 * 8 + tc], b01 = sb1[n0 * 8 + tc + 1];
+        const float b10 = sb1[n1 * 8 + tc], b11 = sb1[n1 * 8 + tc + 1];
+        a2[kb][0] = pack_bf16(silu(acc[n0][0] + b00), silu(acc[n0][1] + b01));
+        a2[kb][1] = pack_bf16(silu(acc[n0][2] + b00), silu(acc[n0][3] + b01));
+        a2[kb][2] = pack_bf16(silu(acc[n1][0] + b10), silu(acc[n1][1] + b11));
+        a2[kb][3] = pack_bf16(silu(acc[n1][2] + b10), silu(acc[n1][3] + b11));
+      }
+#pragma unroll
+      for (int nt = 0; nt < 16; ++nt) {
+        acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+#pragma unroll
+        for (int kb = 0; kb < 8; ++kb) {
+          uint32_t b[2];
+          const __nv_bfloat16* w = sW2 + (nt * 8 + gr) * W2S + kb * 16 + tc;
+          b[0] = *(const uint32_t*)w;
+          b[1] = *(const uint32_t*)(w + 8);
+          mma16816(acc[nt], a2[kb], b);
+        }
+      }
+#pragma unroll
+      for (int kb = 0; kb < 8; ++kb) {
+        const int n0 = 2 * kb, n1 = 2 * kb + 1;
+        const float b00 = sb2[n0 * 8 + tc], b01 = sb2[n0 * 8 + tc + 1];
+        const float b10 = sb2[n1 * 8 + tc], b11 = sb2[n1 * 8 + tc + 1];
+        a2[kb][0] = pack_bf16(silu(acc[n0][0] + b00), silu(acc[n0][1] + b01));
+        a2[kb][1] = pack_bf16(silu(acc[n0][2] + b00), silu(acc[n0][3] + b01));
+        a2[kb][2] = pack_bf16(silu(acc[n1][0] + b10), silu(acc[n1][1] + b11));
+        a2[kb][3] = pack_bf16(silu(acc[n1][2] + b10), silu(acc[n1][3] + b11));
+      }
+      // layer 3: N = 2 padded to one n8 tile
+      float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int kb = 0; kb < 8; ++kb) {
+        uint32_t b[2];
+        const __nv_bfloat16* w = sW3 + gr * W2S + kb * 16 + tc;
+        b[0] = *(const uint32_t*)w;
+        b[1] = *(const uint32_t*)(w + 8);
+        mma16816(y, a2[kb], b);
+      }
+      if (tc == 0) {   // lanes holding output columns 0 (n_e) and 1 (phi)
+        const int rows[2] = {r0 + gr, r0 + gr + 8};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = rows[h];
+          if (i >= N) continue;
+          const float yn = y[2 * h] + sb3[0], yp = y[2 * h + 1] + sb3[1];
+          const int64_t gi = off + i;
+          a.ne_g[gi] = a.ne[gi] + ((a.comps & 1) ? sn * (double)yn : 0.0);
+          a.phi_g[gi] = a.phi[gi] + ((a.comps & 2) ? sp * (double)yp : 0.0);
+        }
+      }
+    }
+  }
+}
+
 // MSE loss: dY = 2 (Y - T) / (2 n) (BF16 for the backward GEMMs), loss and
 // the bias gradient of the output layer accumulated with atomics.
 __global__ void loss_kernel(const float* Y, const float* T, int64_t n, __nv_bfloat16* dY,
@@ -592,25 +773,30 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
                     double* ne_guess, double* phi_guess) {
   if (!h || !ne_guess || !phi_guess || ncells < 0 || components < 0 || components > 3)
     return report_error(SDCEF_ERR_INVALID, "mlp_guess: bad arguments");
-  if (ncells > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
   int rc = check_batch(b);
   if (rc || b->ncol == 0) return rc;
   h->launches = 0;
-  FeatArgs a = feat_args(b);
-  a.X = h->X;
-  a.mode = 0;
-  feat_kernel<<<(unsigned)b->ncol, 128, 0, h->st>>>(a);
-  ++h->launches;
-  cudaError_t e = cudaGetLastError();
+  GuessArgs g;
+  memset(&g, 0, sizeof(g));
+  g.f = feat_args(b);
+  g.f.comps = components;
+  g.f.ne_g = ne_guess;
+  g.f.phi_g = phi_guess;
+  g.p = h->p;
+  g.w1 = h->w1;
+  g.w2 = h->w2;
+  g.w3 = h->w3;
+  g.queue = (int*)h->loss + 4;   // spare words of the loss buffer
+  if (ncells * 5 > h->max_rows * (kIn / 2))
+    return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
+  g.stage = (float*)h->X;        // [cells][5] FP32 inside the [max_rows][32] BF16 buffer
+  cudaError_t e = cudaMemsetAsync(g.queue, 0, sizeof(int), h->st);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = forward(h, h->X, ncells, false);
-  if (e != cudaSuccess) return cuda_fail(e);
-  a.mode = 2;
-  a.comps = components;
-  a.Y = h->Y;
-  a.ne_g = ne_guess;
-  a.phi_g = phi_guess;
-  feat_kernel<<<(unsigned)b->ncol, 128, 0, h->st>>>(a);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(b->ncol, (int64_t)std::max(sms, 1) * 4);
+  guess_fused_kernel<<<grid, 128, 0, h->st>>>(g);
   ++h->launches;
   e = cudaGetLastError();
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);

@@ -167,6 +167,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.p.max_ls = p->max_linesearch;
   a.p.bc = p->bc_electron;
   a.p.precond = p->precond;
+  a.p.guess_cap = p->guess_newton_cap;
   a.mode = MODE_SOLVE;
 
   cudaStream_t st = (cudaStream_t)stream;

@@ -28,6 +28,7 @@ constexpr double kLambdaFD = 6.0554544523933395e-06;
 struct DevParams {
   double eps_F, eps_X, gamma, mu, ls_alpha, kap;   // kap = eps0 eps_r / e
   int m, max_newton, max_krylov, max_ls, bc, precond;
+  int guess_cap;   // Newton steps from a supplied start before restarting from X^n (0 = never)
 };
 
 enum { MODE_SOLVE = 0, MODE_RESIDUAL = 1, MODE_PRECOND = 2 };
@@ -64,7 +65,7 @@ enum {
   PD_FACE1 = PD_FACE0 + 4,
   PD_COUNT = PD_FACE1 + 4
 };
-// Krylov planes (type KR): V[(m+1)*2], W[2], Z[2], XH[2], T[2]
+// Krylov planes (type KR): V[(m+1)*2], W[2], Z[2], XH[2], T[2], ZK[m*2]
 // Factor planes (type KR): 20
 constexpr int kFactorPlanes = 20;
 constexpr int kScalPerThread = 80;
@@ -72,7 +73,7 @@ constexpr int kScalPerThread = 80;
 template <typename KR>
 __host__ __device__ inline size_t slot_bytes_for(size_t PL, int m, int tpb) {
   size_t b = (size_t)PD_COUNT * PL * sizeof(double);
-  b += (size_t)(2 * (m + 1) + 8 + kFactorPlanes) * PL * sizeof(KR);
+  b += (size_t)(2 * (m + 1) + 8 + 2 * m + kFactorPlanes) * PL * sizeof(KR);
   b += (size_t)kScalPerThread * tpb * sizeof(KR);
   return (b + 255) & ~(size_t)255;
 }
@@ -184,6 +185,8 @@ struct Slot {
   __device__ KR* Z(int comp) const { return k + (size_t)(2 * (m + 1) + 2 + comp) * PL; }
   __device__ KR* XH(int comp) const { return k + (size_t)(2 * (m + 1) + 4 + comp) * PL; }
   __device__ KR* T(int comp) const { return k + (size_t)(2 * (m + 1) + 6 + comp) * PL; }
+  // Mhat^{-1} V_i of the current GMRES cycle (flexible-GMRES storage)
+  __device__ KR* ZK(int i, int comp) const { return k + (size_t)(2 * (m + 1) + 8 + 2 * i + comp) * PL; }
 };
 
 template <int TPB, typename KR>
@@ -194,7 +197,7 @@ __device__ Slot<TPB, KR> make_slot(const KArgs& a, int slot) {
   s.m = a.p.m;
   s.d = (double*)base;
   s.k = (KR*)(base + (size_t)PD_COUNT * a.PL * sizeof(double));
-  s.f = s.k + (size_t)(2 * (a.p.m + 1) + 8) * a.PL;
+  s.f = s.k + (size_t)(2 * (a.p.m + 1) + 8 + 2 * a.p.m) * a.PL;
   s.s = s.f + (size_t)kFactorPlanes * a.PL;
   return s;
 }
@@ -872,10 +875,17 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     double fninf = scaled_inf(norms), fn2 = scaled_two(norms);
     int status = SDCEF_STATUS_MAX_NEWTON, newton = 0, krylov = 0;
     const double gam = a.p.gamma;
+    // A supplied start is judged by the Newton iteration itself: if it has not
+    // converged within guess_cap steps, the column restarts from X^n.
+    const bool guessed = (a.ne_g || a.phi_g) && a.p.guess_cap > 0;
+    for (int attempt = 0; attempt < (guessed ? 2 : 1); ++attempt) {
+    const int cap = (guessed && attempt == 0) ? min(a.p.guess_cap, a.p.max_newton)
+                                              : a.p.max_newton - newton;
+    status = SDCEF_STATUS_MAX_NEWTON;
     for (int l = 0;; ++l) {
       if (!(fninf <= 1.79e308)) { status = SDCEF_STATUS_NONFINITE; break; }
       if (fninf < a.p.eps_F) { status = SDCEF_STATUS_OK; break; }
-      if (l >= a.p.max_newton) { status = SDCEF_STATUS_MAX_NEWTON; break; }
+      if (l >= cap) { status = SDCEF_STATUS_MAX_NEWTON; break; }
       // preconditioner at X^(l) and ||S_X^{-1} X||_2 (X = (n, phi))
       prec_factor<TPB, KR>(a, g, cs, S, cur, sh, halo, &bad);
       {
@@ -894,7 +904,9 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       const double* Fe = S.pd(PD_FE0 + 2 * cur);
       const double* Fp = S.pd(PD_FP0 + 2 * cur);
       // ---- GMRES(m), right-preconditioned: Jhat Mhat^{-1} y = -Fhat --------
-      // x-hat accumulates sum y_i V_i; delta-hat = Mhat^{-1} x-hat.
+      // With the fixed preconditioner the correction Mhat^{-1} V y is accumulated
+      // from the stored z_i = Mhat^{-1} V_i (flexible-GMRES storage), which saves
+      // the final preconditioner application.
       KR* XHe = S.XH(0);
       KR* XHp = S.XH(1);
       for (int j = 0; j < kt; ++j) { XHe[ix(j, tid, TPB)] = KR(0); XHp[ix(j, tid, TPB)] = KR(0); }
@@ -919,15 +931,15 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         __syncthreads();
         int kdim = 0;
         for (int jj = 0; jj < m && its < a.p.max_krylov; ++jj) {
-          // z = Mhat^{-1} V_jj, w = Jhat z
-          double zz = prec_apply<TPB, KR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.Z(0), S.Z(1), sh,
-                                          red, true);
+          // z_jj = Mhat^{-1} V_jj (kept), w = Jhat z_jj
+          double zz = prec_apply<TPB, KR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
+                                          S.ZK(jj, 1), sh, red, true);
           double zn = sqrt(zz);
           double eps = kLambdaFD * (kLambdaFD + cs.xnorm / zn);
           if (!(zn > 0.0)) eps = 1.0;
-          residual<TPB, KR>(a, g, cs, S, NP, PP, S.Z(0), S.Z(1), eps * cs.sn, eps * cs.sp, OUT_JVP,
-                            nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1), 1.0 / eps, halo, red,
-                            norms);
+          residual<TPB, KR>(a, g, cs, S, NP, PP, S.ZK(jj, 0), S.ZK(jj, 1), eps * cs.sn,
+                            eps * cs.sp, OUT_JVP, nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1),
+                            1.0 / eps, halo, red, norms);
           ++res_evals;
           ++its;
           // CGS with one re-orthogonalisation
@@ -996,7 +1008,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           __syncthreads();
         }
         if (bad) break;
-        // y = H^{-1} g, x-hat += V y
+        // y = H^{-1} g; the correction delta-hat += sum_q y_q z_q
         if (tid == 0) {
           for (int q = kdim - 1; q >= 0; --q) {
             double s = gv[q];
@@ -1005,22 +1017,24 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           }
         }
         __syncthreads();
+        double dd = 0.0;
         for (int j = 0; j < kt; ++j) {
           double xe = XHe[ix(j, tid, TPB)], xp = XHp[ix(j, tid, TPB)];
           for (int q = 0; q < kdim; ++q) {
-            xe += yv[q] * (double)S.V(q, 0)[ix(j, tid, TPB)];
-            xp += yv[q] * (double)S.V(q, 1)[ix(j, tid, TPB)];
+            xe += yv[q] * (double)S.ZK(q, 0)[ix(j, tid, TPB)];
+            xp += yv[q] * (double)S.ZK(q, 1)[ix(j, tid, TPB)];
           }
           XHe[ix(j, tid, TPB)] = (KR)xe;
           XHp[ix(j, tid, TPB)] = (KR)xp;
+          dd += xe * xe + xp * xp;
         }
         __syncthreads();
         if (converged || its >= a.p.max_krylov) break;
-        // restart: r = -Fhat - Jhat Mhat^{-1} x-hat
-        double zz = prec_apply<TPB, KR>(a, g, cs, S, XHe, XHp, S.Z(0), S.Z(1), sh, red, true);
-        double zn = sqrt(zz);
+        // restart: r = -Fhat - Jhat delta-hat
+        block_reduce<TPB>(&dd, 1, false, red);
+        double zn = sqrt(dd);
         double eps = (zn > 0.0) ? kLambdaFD * (kLambdaFD + cs.xnorm / zn) : 1.0;
-        residual<TPB, KR>(a, g, cs, S, NP, PP, S.Z(0), S.Z(1), eps * cs.sn, eps * cs.sp, OUT_JVP,
+        residual<TPB, KR>(a, g, cs, S, NP, PP, XHe, XHp, eps * cs.sn, eps * cs.sp, OUT_JVP,
                           nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1), 1.0 / eps, halo, red, norms);
         ++res_evals;
         ++its;
@@ -1044,15 +1058,14 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       }
       krylov += its;
       if (bad) { status = SDCEF_STATUS_NONFINITE; break; }
-      // delta-hat = Mhat^{-1} x-hat  (into Z)
-      prec_apply<TPB, KR>(a, g, cs, S, XHe, XHp, S.Z(0), S.Z(1), sh, red, false);
+      // delta-hat is in XH (sum of y_q Mhat^{-1} V_q over the cycles)
       // ---- backtracking line search ----------------------------------------
       double lam = 1.0;
       bool accepted = false;
       const int nxt = 1 - cur;
       double tnorm[4];
       for (int t = 0; t <= a.p.max_ls; ++t) {
-        residual<TPB, KR>(a, g, cs, S, NP, PP, S.Z(0), S.Z(1), lam * cs.sn, lam * cs.sp, OUT_F,
+        residual<TPB, KR>(a, g, cs, S, NP, PP, XHe, XHp, lam * cs.sn, lam * cs.sp, OUT_F,
                           S.pd(PD_FE0 + 2 * nxt), S.pd(PD_FP0 + 2 * nxt), nxt, nullptr, nullptr,
                           nullptr, nullptr, 0, halo, red, tnorm);
         ++res_evals;
@@ -1070,7 +1083,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       // X += lam S_X delta-hat; step size for the eps_X test
       double smax = 0.0;
       for (int j = 0; j < kt; ++j) {
-        double dn = (double)S.Z(0)[ix(j, tid, TPB)], dp = (double)S.Z(1)[ix(j, tid, TPB)];
+        double dn = (double)XHe[ix(j, tid, TPB)], dp = (double)XHp[ix(j, tid, TPB)];
         NP[ix(j, tid, TPB)] = fma(lam * cs.sn, dn, NP[ix(j, tid, TPB)]);
         PP[ix(j, tid, TPB)] = fma(lam * cs.sp, dp, PP[ix(j, tid, TPB)]);
         smax = fmax(smax, fmax(fabs(dn), fabs(dp)));
@@ -1086,6 +1099,22 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         __syncthreads();
       }
     }
+    if (status == SDCEF_STATUS_OK || !guessed || attempt == 1) break;
+    // restart from the plain start X^n
+    for (int j = 0; j < kt; ++j) {
+      const int64_t gi = off + g.t0 + j;
+      NP[ix(j, tid, TPB)] = a.ne_old[gi];
+      PP[ix(j, tid, TPB)] = a.phi_old[gi] - S.pd(PD_PREF)[ix(j, tid, TPB)];
+    }
+    cur = 0;
+    bad = false;
+    __syncthreads();
+    residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+                      S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
+    ++res_evals;
+    fninf = scaled_inf(norms);
+    fn2 = scaled_two(norms);
+    }   // attempts
     // ---- outputs ----------------------------------------------------------
     for (int j = 0; j < kt; ++j) {
       const int64_t gi = off + g.t0 + j;

@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("mobility", C.c_double), ("ls_alpha", C.c_double), ("eps_r", C.c_double),
                 ("restart_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int),
                 ("max_linesearch", C.c_int), ("precision", C.c_int), ("precond", C.c_int),
-                ("bc_electron", C.c_int), ("threads_per_column", C.c_int)]
+                ("bc_electron", C.c_int), ("threads_per_column", C.c_int),
+                ("guess_newton_cap", C.c_int)]
 
 
 class BatchC(C.Structure):

@@ -146,3 +146,26 @@ def test_training_reduces_loss_and_newton_iterations():
         s = slice(b.col_off[c], b.col_off[c + 1])
         e = np.abs(res["learned"]["ne"][s] - res["plain"]["ne"][s]).max() / np.abs(res["plain"]["ne"][s]).max()
         assert e < 1e-8
+
+
+@pytest.mark.parametrize("components", [S.GUESS_NE, S.GUESS_NE | S.GUESS_PHI])
+def test_fused_guess_matches_oracle_network(components):
+    d = dev()
+    flat, q = rounded_params(11)
+    b = make_batch("ragged", 9, 55, n_range=(2, 700))
+    db = S.DeviceBatch.from_host(b, d)
+    mlp = S.MLP(b.ncells)
+    mlp.set_params(flat)
+    ne, phi = mlp.guess(db, components=components)
+    ne, phi = ne.cpu().numpy(), phi.cpu().numpy()
+    Y, _ = M.forward(q, M.bf16_round(M.features(b)))
+    sn, sp = M.column_scales(b)
+    for c in range(b.ncol):
+        s = slice(b.col_off[c], b.col_off[c + 1])
+        yn = (ne[s] - b.ne_old[s]) / sn[c]
+        assert np.linalg.norm(yn - Y[s, 0]) <= 2e-2 * np.linalg.norm(Y[s, 0]) + 1e-6
+        if components & S.GUESS_PHI:
+            yp = (phi[s] - b.phi_old[s]) / sp[c]
+            assert np.linalg.norm(yp - Y[s, 1]) <= 2e-2 * np.linalg.norm(Y[s, 1]) + 1e-6
+        else:
+            assert np.array_equal(phi[s], b.phi_old[s])
