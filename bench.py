@@ -123,6 +123,30 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def kernel_digest():
+    """Digest of the solver kernel sources (ties an ncu capture to the code it measured)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("solver.cuh", "blockalg.cuh", "kern_inst.cu"):
+        with open(os.path.join(ROOT, "paper_1904_08510_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(ncells):
+    """DRAM bytes per launch of the solver kernel from the committed ncu summary, if it
+    was taken on the current kernel sources (else None), scaled to this batch's cells."""
+    path = os.path.join(ROOT, "profiles", "jfnk_kernel_counters.json")
+    try:
+        with open(path) as f:
+            c = json.load(f)
+    except Exception:
+        return None
+    if c.get("kernel_digest") != kernel_digest():
+        return None
+    return float(c["dram_bytes_per_launch"]) * ncells / float(c["cells"])
+
+
 def algorithmic_model(lengths, newton, krylov, res_evals, precond, kr_bytes):
     """Algorithmic FP64 flops and streaming-model bytes of the solve (per batch).
 
@@ -304,7 +328,7 @@ def main():
     achieved_tf = flops / t_launch / 1e12
     hbm_gbs = sbytes / t_launch / 1e9
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_peak, "traffic": None,
+                "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(b.ncells),
                 "kernel": "jfnk_kernel (persistent solver)",
                 "peak_source": "FP64 FMA pipe, 2 DFMA/clk/SM x 152 SM x max SM clock",
                 "streaming_model": {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

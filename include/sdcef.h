@@ -99,6 +99,9 @@ typedef struct {
   int guess_newton_cap; /* Newton steps allowed from a supplied start (ne_guess /
                            phi_guess) before that column restarts from the plain
                            start X^n with the remaining budget; 0 = never restart  */
+  double guess_reject_ratio; /* a supplied start whose scaled residual 2-norm exceeds
+                           this multiple of the plain start's is replaced by X^n
+                           before the first Newton step; 0 = never                  */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -141,7 +144,8 @@ typedef struct {
  * mobility 0.4 (Sec. 2.2), ls_alpha 1e-4, eps_r 1, restart 8, 50 Newton
  * steps, 200 Krylov iterations per step, 20 halvings, FP64, exact Schur
  * preconditioner, absorbing electrodes, automatic threads per column, and a
- * supplied start judged after 12 Newton steps. */
+ * supplied start rejected if its residual is over 30x the plain start's and
+ * judged after 16 Newton steps. */
 void sdcef_default_params(sdcef_params* p);
 
 /* Create a solver context. max_cols, max_cells and max_col_cells bound every

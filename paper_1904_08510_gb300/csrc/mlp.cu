@@ -31,9 +31,11 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
               kNParam = kOffB3 + kOut;
 static_assert(kNParam == SDCEF_MLP_NPARAM, "parameter count");
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU and its derivative with the hardware exponential and fast division (the
+// result feeds BF16 activations, whose rounding is far coarser).
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z) {
-  float s = 1.0f / (1.0f + __expf(-z));
+  float s = __fdividef(1.0f, 1.0f + __expf(-z));
   return s * (1.0f + z * (1.0f - s));
 }
 
@@ -302,6 +304,16 @@ __global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
   if (tid < 2) sb3[tid] = g.p[kOffB3 + tid];
   const int64_t cells = a.col_off[a.ncol];
   const int gr = lane >> 2, tc = (lane & 3) * 2;
+  // this lane's feature columns: k = kb*16 + tc + {0, 1, 8, 9}
+  int fo[8], fq[8];
+#pragma unroll
+  for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = kb * 16 + tc + (u & 1) + (u >> 1) * 8;
+      fo[4 * kb + u] = f / 5 - 2;
+      fq[4 * kb + u] = f < kFeat ? f % 5 : -1;
+    }
   for (;;) {
     __syncthreads();
     if (tid == 0) s_col = atomicAdd(g.queue, 1);
@@ -353,11 +365,13 @@ __global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
       st[i * 5 + 4] = (float)(-(a.phi[off + kp] - a.phi[off + km]) * 0.5 * isp);
     }
     __syncthreads();
-    // feature f (0..31) of cell i: stencil offset f/5 - 2, quantity f%5
-    auto feat = [&](int i, int f) -> float {
-      if (f >= kFeat) return 0.0f;
-      const int k = mir(i + f / 5 - 2);
-      return __bfloat162float(__float2bfloat16(st[k * 5 + f % 5]));
+    // feature f of cell i is quantity f%5 of stencil cell i + f/5 - 2; each lane
+    // owns the same 8 feature columns for every tile, so their (offset,
+    // quantity) pairs are computed once
+    auto feat = [&](int i, int fo, int fq) -> float {
+      if (fq < 0) return 0.0f;
+      const int k = mir(i + fo);
+      return __bfloat162float(__float2bfloat16(st[k * 5 + fq]));
     };
     for (int r0 = warp * 16; r0 < N; r0 += 64) {
       const int ra = min(r0 + gr, N - 1), rb = min(r0 + gr + 8, N - 1);
@@ -365,11 +379,12 @@ __global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
       uint32_t a1[2][4];
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
-        const int k0 = kb * 16 + tc;
-        a1[kb][0] = pack_bf16(feat(ra, k0), feat(ra, k0 + 1));
-        a1[kb][1] = pack_bf16(feat(rb, k0), feat(rb, k0 + 1));
-        a1[kb][2] = pack_bf16(feat(ra, k0 + 8), feat(ra, k0 + 9));
-        a1[kb][3] = pack_bf16(feat(rb, k0 + 8), feat(rb, k0 + 9));
+        const int* o = fo + 4 * kb;
+        const int* q = fq + 4 * kb;
+        a1[kb][0] = pack_bf16(feat(ra, o[0], q[0]), feat(ra, o[1], q[1]));
+        a1[kb][1] = pack_bf16(feat(rb, o[0], q[0]), feat(rb, o[1], q[1]));
+        a1[kb][2] = pack_bf16(feat(ra, o[2], q[2]), feat(ra, o[3], q[3]));
+        a1[kb][3] = pack_bf16(feat(rb, o[2], q[2]), feat(rb, o[3], q[3]));
       }
       float acc[16][4];
 #pragma unroll

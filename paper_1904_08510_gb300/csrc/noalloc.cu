@@ -168,6 +168,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.p.bc = p->bc_electron;
   a.p.precond = p->precond;
   a.p.guess_cap = p->guess_newton_cap;
+  a.p.guess_ratio = p->guess_reject_ratio;
   a.mode = MODE_SOLVE;
 
   cudaStream_t st = (cudaStream_t)stream;

@@ -65,7 +65,8 @@ int check_params(const sdcef_params* p, int m_cap) {
     return set_err(SDCEF_ERR_INVALID, "params: eps_F, gamma, mobility, ls_alpha, eps_r out of range");
   if (p->restart_m < 1 || p->restart_m > SDCEF_MAX_RESTART || (m_cap > 0 && p->restart_m > m_cap))
     return set_err(SDCEF_ERR_INVALID, "params: restart_m out of range");
-  if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0 || p->guess_newton_cap < 0)
+  if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0 || p->guess_newton_cap < 0 ||
+      !(p->guess_reject_ratio >= 0.0))
     return set_err(SDCEF_ERR_INVALID, "params: iteration caps out of range");
   if (p->precision != SDCEF_FP64 && p->precision != SDCEF_MIXED)
     return set_err(SDCEF_ERR_INVALID, "params: precision");
@@ -160,6 +161,7 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb, size_t kr) {
   a.p.bc = p.bc_electron;
   a.p.precond = p.precond;
   a.p.guess_cap = p.guess_newton_cap;
+  a.p.guess_ratio = p.guess_reject_ratio;
   return a;
 }
 
@@ -221,7 +223,8 @@ void sdcef_default_params(sdcef_params* p) {
   p->precond = SDCEF_PREC_EXACT;
   p->bc_electron = SDCEF_BC_ABSORBING;
   p->threads_per_column = 0;
-  p->guess_newton_cap = 12;
+  p->guess_newton_cap = 16;
+  p->guess_reject_ratio = 30.0;
 }
 
 const char* sdcef_last_error(void) { return g_err.c_str(); }

@@ -29,6 +29,7 @@ struct DevParams {
   double eps_F, eps_X, gamma, mu, ls_alpha, kap;   // kap = eps0 eps_r / e
   int m, max_newton, max_krylov, max_ls, bc, precond;
   int guess_cap;   // Newton steps from a supplied start before restarting from X^n (0 = never)
+  double guess_ratio;   // reject a supplied start with ||Fhat|| > ratio ||Fhat(X^n)|| (0 = never)
 };
 
 enum { MODE_SOLVE = 0, MODE_RESIDUAL = 1, MODE_PRECOND = 2 };
@@ -136,8 +137,13 @@ __device__ __forceinline__ void block_reduce(double* v, int nv, bool is_max, dou
 // B(-a) = a + B(a) and B'(-a) = -1 - B'(a) give the other branch without
 // cancellation, so one expm1 and one division serve both.
 // --------------------------------------------------------------------------
+// Order tests on non-negative doubles run on the integer pipe: for x, y >= 0 the
+// IEEE bit patterns order like the values (NaN patterns sort above +inf).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+constexpr long long kBits1em3 = 0x3F50624DD2F1A9FCLL;   // bit pattern of 1e-3
+
 __device__ __forceinline__ void bern_pos(double a, double* b, double* db) {
-  if (a < 1e-3) {
+  if (dbits(a) < kBits1em3) {
     double a2 = a * a;
     *b = 1.0 - 0.5 * a + a2 * (1.0 / 12.0) - a2 * a2 * (1.0 / 720.0);
     *db = -0.5 + a * (1.0 / 6.0) - a * a2 * (1.0 / 180.0);
@@ -248,7 +254,9 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
     halo[3 * TPB + tid] = st_p(kt - 1);
   }
   __syncthreads();
-  double mxe = 0.0, mxp = 0.0, sse = 0.0, ssp = 0.0;
+  long long mxe = 0, mxp = 0;   // bit patterns of max |F_e|, max |F_phi|
+  double sse = 0.0, ssp = 0.0;
+  constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL;
   double gam_left = 0.0, d_left = 0.0;   // left-face values of row 0 (thread 0 only)
   double pend_e = 0.0, pend_p = 0.0;     // row-0 partial residuals
   double gam_prev = 0.0, d_prev = 0.0, last_gam = 0.0, last_d = 0.0;
@@ -276,7 +284,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         double aa = fabs(Pe), b, db;
         bern_pos(aa, &b, &db);
         double Bp, Bm, dBp, dBm;   // B(Pe), B(-Pe) and derivatives
-        if (Pe >= 0.0) { Bp = b; Bm = aa + b; dBp = db; dBm = -1.0 - db; }
+        if (dbits(Pe) >= 0) { Bp = b; Bm = aa + b; dBp = db; dBm = -1.0 - db; }   // sign bit clear
         else { Bm = b; Bp = aa + b; dBm = db; dBp = -1.0 - db; }
         const double dh = DH[ix(j, tid, TPB)];
         gam = dh * (Bm * n_i - Bp * n_n);
@@ -313,8 +321,8 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         if (out_mode == OUT_F) {
           fe_o[ix(j, tid, TPB)] = Fe;
           fp_o[ix(j, tid, TPB)] = Fp;
-          mxe = fmax(mxe, fabs(Fe));
-          mxp = fmax(mxp, fabs(Fp));
+          mxe = max(mxe, dbits(Fe) & kAbs);
+          mxp = max(mxp, dbits(Fp) & kAbs);
           sse += Fe * Fe;
           ssp += Fp * Fp;
         } else {
@@ -346,8 +354,8 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
     if (out_mode == OUT_F) {
       fe_o[ix(0, tid, TPB)] = Fe;
       fp_o[ix(0, tid, TPB)] = Fp;
-      mxe = fmax(mxe, fabs(Fe));
-      mxp = fmax(mxp, fabs(Fp));
+      mxe = max(mxe, dbits(Fe) & kAbs);
+      mxp = max(mxp, dbits(Fp) & kAbs);
       sse += Fe * Fe;
       ssp += Fp * Fp;
     } else {
@@ -356,7 +364,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
     }
   }
   if (out_mode == OUT_F) {
-    double mx[2] = {mxe, mxp};
+    double mx[2] = {__longlong_as_double(mxe), __longlong_as_double(mxp)};
     // NaN-propagating max: fmax drops NaN, so fold non-finite into +inf
     if (!(mx[0] <= 1.79e308)) mx[0] = INFINITY;
     if (!(mx[1] <= 1.79e308)) mx[1] = INFINITY;
@@ -813,6 +821,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
     }
     ++res_evals;
+    double norms_n[4] = {norms[0], norms[1], norms[2], norms[3]};   // F at X^n
     if (tid == 0) {
       cs.sFe = fmax(fmax(norms[0], cs.scal[0]), 1e-12 * cs.sn);
       cs.sFp = fmax(fmax(norms[1], cs.scal[1]), 1e-12 * cs.sn);
@@ -875,10 +884,32 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     double fninf = scaled_inf(norms), fn2 = scaled_two(norms);
     int status = SDCEF_STATUS_MAX_NEWTON, newton = 0, krylov = 0;
     const double gam = a.p.gamma;
-    // A supplied start is judged by the Newton iteration itself: if it has not
-    // converged within guess_cap steps, the column restarts from X^n.
-    const bool guessed = (a.ne_g || a.phi_g) && a.p.guess_cap > 0;
-    for (int attempt = 0; attempt < (guessed ? 2 : 1); ++attempt) {
+    // A supplied start is judged twice: before the first Newton step (its scaled
+    // residual against the plain start's) and by the iteration itself (if it
+    // has not converged within guess_cap steps). A rejected start is replaced by
+    // X^n, which then gets the remaining Newton budget.
+    const bool supplied = a.ne_g || a.phi_g;
+    const bool guessed = supplied && a.p.guess_cap > 0;
+    const bool reject = supplied && a.p.guess_ratio > 0.0 &&
+                        !(fn2 <= a.p.guess_ratio * scaled_two(norms_n));
+    const int n_att = (guessed || reject) ? 2 : 1;
+    for (int attempt = reject ? 1 : 0; attempt < n_att; ++attempt) {
+    if (attempt == 1) {
+      // restart from the plain start X^n
+      for (int j = 0; j < kt; ++j) {
+        const int64_t gi = off + g.t0 + j;
+        NP[ix(j, tid, TPB)] = a.ne_old[gi];
+        PP[ix(j, tid, TPB)] = a.phi_old[gi] - S.pd(PD_PREF)[ix(j, tid, TPB)];
+      }
+      cur = 0;
+      bad = false;
+      __syncthreads();
+      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+                        S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
+      ++res_evals;
+      fninf = scaled_inf(norms);
+      fn2 = scaled_two(norms);
+    }
     const int cap = (guessed && attempt == 0) ? min(a.p.guess_cap, a.p.max_newton)
                                               : a.p.max_newton - newton;
     status = SDCEF_STATUS_MAX_NEWTON;
@@ -1100,20 +1131,6 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       }
     }
     if (status == SDCEF_STATUS_OK || !guessed || attempt == 1) break;
-    // restart from the plain start X^n
-    for (int j = 0; j < kt; ++j) {
-      const int64_t gi = off + g.t0 + j;
-      NP[ix(j, tid, TPB)] = a.ne_old[gi];
-      PP[ix(j, tid, TPB)] = a.phi_old[gi] - S.pd(PD_PREF)[ix(j, tid, TPB)];
-    }
-    cur = 0;
-    bad = false;
-    __syncthreads();
-    residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
-                      S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
-    ++res_evals;
-    fninf = scaled_inf(norms);
-    fn2 = scaled_two(norms);
     }   // attempts
     // ---- outputs ----------------------------------------------------------
     for (int j = 0; j < kt; ++j) {

@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("restart_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int),
                 ("max_linesearch", C.c_int), ("precision", C.c_int), ("precond", C.c_int),
                 ("bc_electron", C.c_int), ("threads_per_column", C.c_int),
-                ("guess_newton_cap", C.c_int)]
+                ("guess_newton_cap", C.c_int), ("guess_reject_ratio", C.c_double)]
 
 
 class BatchC(C.Structure):
