@@ -133,16 +133,17 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(ncells):
+def ncu_traffic(ncells, tpc):
     """DRAM bytes per launch of the solver kernel from the committed ncu summary, if it
-    was taken on the current kernel sources (else None), scaled to this batch's cells."""
+    was taken on the current kernel sources and launch shape (else None), scaled to
+    this batch's cells."""
     path = os.path.join(ROOT, "profiles", "jfnk_kernel_counters.json")
     try:
         with open(path) as f:
             c = json.load(f)
     except Exception:
         return None
-    if c.get("kernel_digest") != kernel_digest():
+    if c.get("kernel_digest") != kernel_digest() or int(c.get("threads_per_column", -1)) != tpc:
         return None
     return float(c["dram_bytes_per_launch"]) * ncells / float(c["cells"])
 
@@ -328,7 +329,7 @@ def main():
     achieved_tf = flops / t_launch / 1e12
     hbm_gbs = sbytes / t_launch / 1e9
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(b.ncells),
+                "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(b.ncells, tuned[0] if tuned else args.tpc),
                 "kernel": "jfnk_kernel (persistent solver)",
                 "peak_source": "FP64 FMA pipe, 2 DFMA/clk/SM x 152 SM x max SM clock",
                 "streaming_model": {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -144,17 +144,25 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--eval-ncol", type=int, default=4096)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--train-cells", default="256",
+                    help="cells per training column: an integer, or lo:hi for U{lo..hi}")
     args = ap.parse_args()
     t0 = time.perf_counter()
-    X, T, nok = generate(args.ncol, 1_000_000)
+    if ":" in args.train_cells:
+        lo, hi = (int(v) for v in args.train_cells.split(":"))
+        X, T, nok = generate(args.ncol, 1_000_000, n_range=(lo, hi))
+    else:
+        X, T, nok = generate(args.ncol, 1_000_000, n_cells=int(args.train_cells))
     t1 = time.perf_counter()
     mlp, hist = train(X, T, steps=args.steps, batch=args.batch, lr=args.lr, log_every=500)
     t2 = time.perf_counter()
     params = mlp.get_params()
-    save(params, args.out, dict(ncol=args.ncol, steps=args.steps, batch=args.batch, lr=args.lr))
+    save(params, args.out, dict(ncol=args.ncol, steps=args.steps, batch=args.batch, lr=args.lr,
+                                train_cells=args.train_cells))
     b, res = evaluate(params, args.eval_ncol, 2_000_000,
                       variants=(("learned_ne", 1), ("learned_ne_phi", 3)))
-    summary = dict(train_columns=args.ncol, train_samples=int(X.shape[0]), converged=nok,
+    summary = dict(train_columns=args.ncol, train_cells=args.train_cells,
+                   train_samples=int(X.shape[0]), converged=nok,
                    data_s=t1 - t0, train_s=t2 - t1, loss=hist,
                    eval={k: {kk: vv for kk, vv in v.items() if kk not in ("ne", "phi")}
                          for k, v in res.items()})
