@@ -1,8 +1,9 @@
 """Training and evaluation of the learned Newton initial guess.
 
-Data: converged solves of seeded single-flame columns (256 cells, the profile
-family of workload.make_batch(kind="single")), solved by the batched FP64 JFNK
-on the GPU; features and targets are produced by the library's own kernels
+Data: converged solves of seeded single-flame columns (the profile family of
+workload.make_batch(kind="single"); a fixed cell count or cell counts drawn
+uniformly from a range, --train-cells), solved by the batched FP64 JFNK on the
+GPU; features and targets are produced by the library's own kernels
 (sdcef_mlp_features / sdcef_mlp_targets). Training runs the library's BF16
 forward/backward kernels and its Adam step. Evaluation solves held-out columns
 with and without the guess and compares Newton and GMRES iteration counts.
