@@ -11,10 +11,22 @@
 // X_L and to the chunk's own separator X_R):
 //     x_j = y_j + P_j X_L + Q_j X_R .
 // Substituting into the separator rows gives a block-tridiagonal system with
-// one unknown per thread, solved by parallel cyclic reduction (PCR) in shared
-// memory. The factorisation (matrix-only work) is done once per Newton step;
-// each solve then costs a forward/backward sweep, log2(threads) PCR levels on
-// the right-hand side only, and the spike reconstruction.
+// one unknown per active thread. It is reduced by cyclic reduction (CR, half
+// of the rows eliminated per level, compact thread mapping) until at most 32
+// rows remain, which warp 0 solves by parallel cyclic reduction (PCR) with
+// register shuffles; CR back-substitution then recovers the eliminated rows.
+// The factorisation (matrix-only work) is done once per Newton step; each
+// solve then costs a forward/backward sweep, the CR/PCR passes on the
+// right-hand side only, and the spike reconstruction.
+//
+// Cost model. On this part every FP64 warp instruction occupies the FP64 pipe
+// for the same time whatever the number of active lanes, so the reduced solve
+// is organised to keep the number of FP64 warp instructions small: CR touches
+// T/2 + T/4 + ... rows on compact lanes, and the PCR tail runs on one warp,
+// where PCR over all T rows would issue log2(T) levels on every warp. Products
+// with the coupling blocks skip their structural zeros (the lower-left entry
+// of the 2x2 off-diagonal blocks of Eq. linear_nls is zero because
+// dF_phi/dn is diagonal) and every multiply-accumulate is one FMA chain.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -50,45 +62,68 @@ __device__ __forceinline__ Vec<NB, R> vzero() {
   for (int k = 0; k < NB; ++k) v.a[k] = R(0);
   return v;
 }
-template <int NB, typename R>
-__device__ __forceinline__ Mat<NB, R> mmul(const Mat<NB, R>& x, const Mat<NB, R>& y) {
+
+// Block product with optional accumulator and sign, skipping structural zeros:
+//   r = (ACC ? acc : 0) + SG * x y,
+// XU / YU: x / y is upper triangular (entries below the diagonal are zero and
+// are never read). The first term of an entry without accumulator is a plain
+// multiply; the rest are FMAs.
+template <int SG, bool ACC, bool XU, bool YU, int NB, typename R>
+__device__ __forceinline__ Mat<NB, R> mprod(const Mat<NB, R>& acc, const Mat<NB, R>& x,
+                                            const Mat<NB, R>& y) {
   Mat<NB, R> r;
 #pragma unroll
   for (int i = 0; i < NB; ++i)
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      R s = R(0);
+      R s = ACC ? acc.a[i * NB + j] : R(0);
+      bool first = !ACC;
 #pragma unroll
-      for (int k = 0; k < NB; ++k) s = fma(x.a[i * NB + k], y.a[k * NB + j], s);
+      for (int k = 0; k < NB; ++k) {
+        if ((XU && i > k) || (YU && k > j)) continue;
+        const R xv = SG > 0 ? x.a[i * NB + k] : -x.a[i * NB + k];
+        if (first) {
+          s = xv * y.a[k * NB + j];
+          first = false;
+        } else {
+          s = fma(xv, y.a[k * NB + j], s);
+        }
+      }
       r.a[i * NB + j] = s;
     }
   return r;
 }
 template <int NB, typename R>
-__device__ __forceinline__ Vec<NB, R> mvec(const Mat<NB, R>& x, const Vec<NB, R>& v) {
+__device__ __forceinline__ Mat<NB, R> mmul(const Mat<NB, R>& x, const Mat<NB, R>& y) {
+  return mprod<1, false, false, false>(x, x, y);
+}
+// r = (ACC ? acc : 0) + SG * x v (x upper triangular if XU)
+template <int SG, bool ACC, bool XU, int NB, typename R>
+__device__ __forceinline__ Vec<NB, R> vprod(const Vec<NB, R>& acc, const Mat<NB, R>& x,
+                                            const Vec<NB, R>& v) {
   Vec<NB, R> r;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
-    R s = R(0);
+    R s = ACC ? acc.a[i] : R(0);
+    bool first = !ACC;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) s = fma(x.a[i * NB + k], v.a[k], s);
+    for (int k = 0; k < NB; ++k) {
+      if (XU && i > k) continue;
+      const R xv = SG > 0 ? x.a[i * NB + k] : -x.a[i * NB + k];
+      if (first) {
+        s = xv * v.a[k];
+        first = false;
+      } else {
+        s = fma(xv, v.a[k], s);
+      }
+    }
     r.a[i] = s;
   }
   return r;
 }
 template <int NB, typename R>
-__device__ __forceinline__ Mat<NB, R> madd(const Mat<NB, R>& x, const Mat<NB, R>& y) {
-  Mat<NB, R> r;
-#pragma unroll
-  for (int k = 0; k < NB * NB; ++k) r.a[k] = x.a[k] + y.a[k];
-  return r;
-}
-template <int NB, typename R>
-__device__ __forceinline__ Mat<NB, R> msub(const Mat<NB, R>& x, const Mat<NB, R>& y) {
-  Mat<NB, R> r;
-#pragma unroll
-  for (int k = 0; k < NB * NB; ++k) r.a[k] = x.a[k] - y.a[k];
-  return r;
+__device__ __forceinline__ Vec<NB, R> mvec(const Mat<NB, R>& x, const Vec<NB, R>& v) {
+  return vprod<1, false, false>(v, x, v);
 }
 template <int NB, typename R>
 __device__ __forceinline__ Mat<NB, R> mneg(const Mat<NB, R>& x) {
@@ -97,43 +132,34 @@ __device__ __forceinline__ Mat<NB, R> mneg(const Mat<NB, R>& x) {
   for (int k = 0; k < NB * NB; ++k) r.a[k] = -x.a[k];
   return r;
 }
-template <int NB, typename R>
-__device__ __forceinline__ Vec<NB, R> vsub(const Vec<NB, R>& x, const Vec<NB, R>& y) {
-  Vec<NB, R> r;
-#pragma unroll
-  for (int k = 0; k < NB; ++k) r.a[k] = x.a[k] - y.a[k];
-  return r;
+
+// Pivot checks on the bit patterns (integer pipe): zero or non-finite.
+__device__ __forceinline__ bool bad_pivot(double det, double inv) {
+  const long long d = __double_as_longlong(det), v = __double_as_longlong(inv);
+  return (d & 0x7FFFFFFFFFFFFFFFLL) == 0 || (v & 0x7FF0000000000000LL) == 0x7FF0000000000000LL;
 }
-template <int NB, typename R>
-__device__ __forceinline__ Vec<NB, R> vadd(const Vec<NB, R>& x, const Vec<NB, R>& y) {
-  Vec<NB, R> r;
-#pragma unroll
-  for (int k = 0; k < NB; ++k) r.a[k] = x.a[k] + y.a[k];
-  return r;
+__device__ __forceinline__ bool bad_pivot(float det, float inv) {
+  const int d = __float_as_int(det), v = __float_as_int(inv);
+  return (d & 0x7FFFFFFF) == 0 || (v & 0x7F800000) == 0x7F800000;
 }
-// Inverse; *bad is set when the pivot is zero or not finite.
-__device__ __forceinline__ Mat<1, double> minv(const Mat<1, double>& x, bool* bad) {
-  Mat<1, double> r;
-  r.a[0] = 1.0 / x.a[0];
-  if (!(x.a[0] != 0.0) || !isfinite(r.a[0])) *bad = true;
-  return r;
-}
-__device__ __forceinline__ Mat<1, float> minv(const Mat<1, float>& x, bool* bad) {
-  Mat<1, float> r;
-  r.a[0] = 1.0f / x.a[0];
-  if (!(x.a[0] != 0.0f) || !isfinite(r.a[0])) *bad = true;
+// Inverse; *bad is set when the pivot is zero or the inverse not finite.
+template <typename R>
+__device__ __forceinline__ Mat<1, R> minv(const Mat<1, R>& x, bool* bad) {
+  Mat<1, R> r;
+  r.a[0] = R(1) / x.a[0];
+  if (bad_pivot(x.a[0], r.a[0])) *bad = true;
   return r;
 }
 template <typename R>
 __device__ __forceinline__ Mat<2, R> minv(const Mat<2, R>& x, bool* bad) {
-  R det = x.a[0] * x.a[3] - x.a[1] * x.a[2];
-  R id = R(1) / det;
+  const R det = fma(x.a[0], x.a[3], -(x.a[1] * x.a[2]));
+  const R id = R(1) / det;
   Mat<2, R> r;
   r.a[0] = x.a[3] * id;
   r.a[1] = -x.a[1] * id;
   r.a[2] = -x.a[2] * id;
   r.a[3] = x.a[0] * id;
-  if (!(det != R(0)) || !isfinite(id)) *bad = true;
+  if (bad_pivot(det, id)) *bad = true;
   return r;
 }
 
@@ -170,26 +196,218 @@ struct Scal {
   }
 };
 
+// Reduced-system levels: CR while more than 32 rows remain (at most 3 levels
+// for TPB <= 256), then PCR on at most 32 rows (at most 5 levels).
+constexpr int kMaxCR = 3, kMaxPCR = 5;
+
 // Factor planes per interior row: Winv, G = Winv M, Cp = Winv U, P, Q.
 template <int NB> struct FIdx {
-  static constexpr int WINV = 0, G = NB * NB, CP = 2 * NB * NB, P = 3 * NB * NB,
-                       Q = 4 * NB * NB, NPLANES = 5 * NB * NB;
-  // per-thread scalars: Me, Ue, Binv, then per PCR level alpha, gamma
-  static constexpr int ME = 0, UE = NB * NB, BINV = 2 * NB * NB, LVL = 3 * NB * NB;
-  static __host__ __device__ constexpr int nscal(int levels) { return 3 * NB * NB + 2 * NB * NB * levels; }
+  static constexpr int NN = NB * NB;
+  static constexpr int WINV = 0, G = NN, CP = 2 * NN, P = 3 * NN, Q = 4 * NN, NPLANES = 5 * NN;
+  // per-thread scalars: separator row blocks Me, Ue; final PCR pivot inverse;
+  // per CR level: eliminated row (Binv, A, C) and surviving row (alpha, gamma);
+  // per PCR level: (alpha, gamma)
+  static constexpr int ME = 0, UE = NN, BINV = 2 * NN, CR0 = 3 * NN, CRSTEP = 5 * NN,
+                       PCR0 = CR0 + kMaxCR * CRSTEP, NSCAL = PCR0 + 2 * NN * kMaxPCR;
 };
 
-// Number of PCR levels for a reduced system of `tact` unknowns.
-__device__ __forceinline__ int pcr_levels(int tact) {
-  int l = 0;
-  while ((1 << l) < tact) ++l;
-  return l;
+// Shuffle a block from lane - s (up) or lane + s (down) within a full warp.
+template <int NB, typename R>
+__device__ __forceinline__ Mat<NB, R> shfl_up_m(const Mat<NB, R>& x, int s) {
+  Mat<NB, R> r;
+#pragma unroll
+  for (int k = 0; k < NB * NB; ++k) r.a[k] = __shfl_up_sync(0xffffffffu, x.a[k], s);
+  return r;
+}
+template <int NB, typename R>
+__device__ __forceinline__ Mat<NB, R> shfl_down_m(const Mat<NB, R>& x, int s) {
+  Mat<NB, R> r;
+#pragma unroll
+  for (int k = 0; k < NB * NB; ++k) r.a[k] = __shfl_down_sync(0xffffffffu, x.a[k], s);
+  return r;
+}
+
+// Factorise the reduced system Ab_t X_{t-1} + Bb_t X_t + Cb_t X_{t+1} = rb_t
+// (t < T; Ab_0 = 0 and Cb_{T-1} = 0). All threads call it; sh must hold
+// 3 * NB * NB * TPB values of R.
+template <int NB, typename R, int TPB>
+__device__ void red_factor(Scal<NB, R, TPB> S, int tid, int T, const Mat<NB, R>& Ab,
+                           const Mat<NB, R>& Bb, const Mat<NB, R>& Cb, R* sh, bool* bad) {
+  using FI = FIdx<NB>;
+  constexpr int NN = NB * NB;
+  R* sA = sh;
+  R* sB = sh + NN * TPB;
+  R* sC = sh + 2 * NN * TPB;
+  auto ld = [&](const R* b, int i) {
+    Mat<NB, R> m;
+#pragma unroll
+    for (int k = 0; k < NN; ++k) m.a[k] = b[k * TPB + i];
+    return m;
+  };
+  auto st = [&](R* b, int i, const Mat<NB, R>& m) {
+#pragma unroll
+    for (int k = 0; k < NN; ++k) b[k * TPB + i] = m.a[k];
+  };
+  if (tid < T) {
+    st(sA, tid, Ab);
+    st(sB, tid, Bb);
+    st(sC, tid, Cb);
+  }
+  __syncthreads();
+  int n = T, l = 0;
+  for (; n > 32; ++l, n >>= 1) {
+    const int ne = (n + 1) >> 1, ns = n >> 1;
+    const int base = FI::CR0 + FI::CRSTEP * l;
+    // rows q = 2t leave the system: invert their pivot in place (only the
+    // surviving neighbours read it, after the barrier)
+    if (tid < ne) {
+      const int q = 2 * tid;
+      const Mat<NB, R> Bi = minv(ld(sB, q), bad);
+      st(sB, q, Bi);
+      S.stm(base, tid, Bi);
+      S.stm(base + NN, tid, ld(sA, q));
+      S.stm(base + 2 * NN, tid, ld(sC, q));
+    }
+    __syncthreads();
+    Mat<NB, R> An = mzero<NB, R>(), Bn = mident<NB, R>(), Cn = mzero<NB, R>();
+    if (tid < ns) {
+      const int q = 2 * tid + 1;   // q - 1 >= 0 always exists
+      const Mat<NB, R> al = mprod<-1, false, false, false>(Ab, ld(sA, q), ld(sB, q - 1));
+      Bn = mprod<1, true, false, false>(ld(sB, q), al, ld(sC, q - 1));
+      An = mmul(al, ld(sA, q - 1));
+      Mat<NB, R> ga = mzero<NB, R>();
+      if (q + 1 < n) {
+        ga = mprod<-1, false, false, false>(Ab, ld(sC, q), ld(sB, q + 1));
+        Bn = mprod<1, true, false, false>(Bn, ga, ld(sA, q + 1));
+        Cn = mmul(ga, ld(sC, q + 1));
+      }
+      S.stm(base + 3 * NN, tid, al);
+      S.stm(base + 4 * NN, tid, ga);
+    }
+    __syncthreads();
+    if (tid < ns) {
+      st(sA, tid, An);
+      st(sB, tid, Bn);
+      st(sC, tid, Cn);
+    }
+    __syncthreads();
+  }
+  // PCR on the remaining n <= 32 rows in warp 0; lanes >= n are identity rows
+  if (tid < 32) {
+    Mat<NB, R> A = mzero<NB, R>(), B = mident<NB, R>(), C = mzero<NB, R>();
+    if (tid < n) {
+      A = ld(sA, tid);
+      B = ld(sB, tid);
+      C = ld(sC, tid);
+    }
+    int k = 0;
+    for (int s = 1; s < n; s <<= 1, ++k) {
+      Mat<NB, R> Al = shfl_up_m(A, s), Bl = shfl_up_m(B, s), Cl = shfl_up_m(C, s);
+      Mat<NB, R> Ar = shfl_down_m(A, s), Br = shfl_down_m(B, s), Cr = shfl_down_m(C, s);
+      if (tid < s) {
+        Al = mzero<NB, R>();
+        Bl = mident<NB, R>();
+        Cl = mzero<NB, R>();
+      }
+      if (tid + s >= n) {
+        Ar = mzero<NB, R>();
+        Br = mident<NB, R>();
+        Cr = mzero<NB, R>();
+      }
+      const Mat<NB, R> al = mprod<-1, false, false, false>(A, A, minv(Bl, bad));
+      const Mat<NB, R> ga = mprod<-1, false, false, false>(C, C, minv(Br, bad));
+      B = mprod<1, true, false, false>(mprod<1, true, false, false>(B, al, Cl), ga, Ar);
+      A = mmul(al, Al);
+      C = mmul(ga, Cr);
+      if (tid < n) {
+        S.stm(FI::PCR0 + 2 * NN * k, tid, al);
+        S.stm(FI::PCR0 + 2 * NN * k + NN, tid, ga);
+      }
+    }
+    if (tid < n) S.stm(FI::BINV, tid, minv(B, bad));
+  }
+  __syncthreads();   // sh is free again
+}
+
+// Solve the factorised reduced system for rb (thread t < T holds rb_t).
+// sr must hold 2 * NB * TPB values of R. On return (after a barrier) the
+// solution X_t of every row sits at sr[k * T + t], k < NB.
+template <int NB, typename R, int TPB>
+__device__ void red_solve(Scal<NB, R, TPB> S, int tid, int T, const Vec<NB, R>& rb, R* sr) {
+  using FI = FIdx<NB>;
+  constexpr int NN = NB * NB;
+  // level l occupies sr[o_l + k * n_l + i], o_l = NB * (T + T/2 + ... ) before it
+  auto ld = [&](int o, int n, int i) {
+    Vec<NB, R> v;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) v.a[k] = sr[o + k * n + i];
+    return v;
+  };
+  auto st = [&](int o, int n, int i, const Vec<NB, R>& v) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) sr[o + k * n + i] = v.a[k];
+  };
+  if (tid < T) st(0, T, tid, rb);
+  __syncthreads();
+  int n = T, l = 0, o = 0;
+  for (; n > 32; ++l) {
+    const int ns = n >> 1;
+    const int base = FI::CR0 + FI::CRSTEP * l;
+    if (tid < ns) {
+      const int q = 2 * tid + 1;
+      Vec<NB, R> r = vprod<1, true, false>(ld(o, n, q), S.ldm(base + 3 * NN, tid), ld(o, n, q - 1));
+      if (q + 1 < n) r = vprod<1, true, false>(r, S.ldm(base + 4 * NN, tid), ld(o, n, q + 1));
+      st(o + NB * n, ns, tid, r);
+    }
+    __syncthreads();
+    o += NB * n;
+    n = ns;
+  }
+  const int L = l;
+  if (tid < 32) {
+    Vec<NB, R> r = vzero<NB, R>();
+    if (tid < n) r = ld(o, n, tid);
+    int k = 0;
+    for (int s = 1; s < n; s <<= 1, ++k) {
+      Vec<NB, R> rl, rr;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        rl.a[c] = __shfl_up_sync(0xffffffffu, r.a[c], s);
+        rr.a[c] = __shfl_down_sync(0xffffffffu, r.a[c], s);
+      }
+      if (tid < n) {
+        if (tid >= s) r = vprod<1, true, false>(r, S.ldm(FI::PCR0 + 2 * NN * k, tid), rl);
+        if (tid + s < n) r = vprod<1, true, false>(r, S.ldm(FI::PCR0 + 2 * NN * k + NN, tid), rr);
+      }
+    }
+    if (tid < n) st(o, n, tid, mvec(S.ldm(FI::BINV, tid), r));
+  }
+  __syncthreads();
+  // CR back-substitution, coarsest level first
+  for (l = L - 1; l >= 0; --l) {
+    const int nl = T >> l, ns = nl >> 1, ne = (nl + 1) >> 1;
+    o -= NB * nl;
+    const int o1 = o + NB * nl;
+    const int base = FI::CR0 + FI::CRSTEP * l;
+    Vec<NB, R> xs = vzero<NB, R>();
+    if (tid < ns) xs = ld(o1, ns, tid);
+    if (tid < ne) {
+      const int q = 2 * tid;
+      Vec<NB, R> r = ld(o, nl, q);
+      if (tid >= 1) r = vprod<-1, true, false>(r, S.ldm(base + NN, tid), ld(o1, ns, tid - 1));
+      if (tid < ns) r = vprod<-1, true, false>(r, S.ldm(base + 2 * NN, tid), xs);
+      st(o, nl, q, mvec(S.ldm(base, tid), r));
+    }
+    if (tid < ns) st(o, nl, 2 * tid + 1, xs);
+    __syncthreads();
+  }
 }
 
 // Factorise the column's block-tridiagonal matrix. rowf(j, M, D, U) yields the
-// blocks of the thread's local row j (M couples row-1, U couples row+1).
-// sh must hold TPB * 3 * NB * NB values of R. All threads of the CTA call it.
-template <int NB, typename R, int TPB, class RowF>
+// blocks of the thread's local row j (M couples row-1, U couples row+1); UT
+// states that M and U are upper triangular. sh must hold TPB * 3 * NB * NB
+// values of R. All threads of the CTA call it.
+template <int NB, typename R, int TPB, bool UT, class RowF>
 __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, int tid,
                             int tact, RowF rowf, R* sh, bool* bad) {
   using FI = FIdx<NB>;
@@ -202,11 +420,11 @@ __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, in
     for (int j = 0; j < m; ++j) {
       Mat<NB, R> M, D, U;
       rowf(j, M, D, U);
-      Mat<NB, R> W = (j == 0) ? D : msub(D, mmul(M, Cp_prev));
-      Mat<NB, R> Wi = minv(W, bad);
-      Mat<NB, R> G = mmul(Wi, M);
-      Mat<NB, R> Cp = mmul(Wi, U);
-      Mat<NB, R> Pg = (j == 0) ? mneg(G) : mneg(mmul(G, Pg_prev));
+      const Mat<NB, R> W = (j == 0) ? D : mprod<-1, true, UT, false>(D, M, Cp_prev);
+      const Mat<NB, R> Wi = minv(W, bad);
+      const Mat<NB, R> G = mprod<1, false, false, UT>(Wi, Wi, M);
+      const Mat<NB, R> Cp = mprod<1, false, false, UT>(Wi, Wi, U);
+      const Mat<NB, R> Pg = (j == 0) ? mneg(G) : mprod<-1, false, false, false>(G, G, Pg_prev);
       F.stm(FI::WINV, j, tid, Wi);
       F.stm(FI::G, j, tid, G);
       F.stm(FI::CP, j, tid, Cp);
@@ -222,9 +440,9 @@ __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, in
       Qlast = Qn;
       F.stm(FI::Q, m - 1, tid, Qn);
       for (int j = m - 2; j >= 0; --j) {
-        Mat<NB, R> Cp = F.ldm(FI::CP, j, tid);
-        Mat<NB, R> Pj = msub(F.ldm(FI::P, j, tid), mmul(Cp, Pn));
-        Mat<NB, R> Qj = mneg(mmul(Cp, Qn));
+        const Mat<NB, R> Cp = F.ldm(FI::CP, j, tid);
+        const Mat<NB, R> Pj = mprod<-1, true, false, false>(F.ldm(FI::P, j, tid), Cp, Pn);
+        const Mat<NB, R> Qj = mprod<-1, false, false, false>(Cp, Cp, Qn);
         F.stm(FI::P, j, tid, Pj);
         F.stm(FI::Q, j, tid, Qj);
         Pn = Pj;
@@ -257,56 +475,21 @@ __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, in
   // reduced row: Abar X_{t-1} + Bbar X_t + Cbar X_{t+1} = rbar
   Mat<NB, R> Ab = mzero<NB, R>(), Bb = mident<NB, R>(), Cb = mzero<NB, R>();
   if (kt > 0) {
-    Ab = mmul(Me, Plast);
-    Bb = madd(madd(De, mmul(Me, Qlast)), mmul(Ue, Pn1));
-    Cb = mmul(Ue, Qn1);
+    Ab = mprod<1, false, UT, false>(Me, Me, Plast);
+    Bb = mprod<1, true, UT, false>(mprod<1, true, UT, false>(De, Me, Qlast), Ue, Pn1);
+    Cb = mprod<1, false, UT, false>(Ue, Ue, Qn1);
   }
-  const int L = pcr_levels(tact);
-  for (int l = 0; l < L; ++l) {
-    const int s = 1 << l;
-#pragma unroll
-    for (int k = 0; k < NN; ++k) {
-      sh[k * TPB + tid] = Ab.a[k];
-      sh[(NN + k) * TPB + tid] = Bb.a[k];
-      sh[(2 * NN + k) * TPB + tid] = Cb.a[k];
-    }
-    __syncthreads();
-    Mat<NB, R> Al, Bl, Cl, Ar, Br, Cr;
-    const bool hl = tid - s >= 0, hr = tid + s < TPB;
-#pragma unroll
-    for (int k = 0; k < NN; ++k) {
-      Al.a[k] = hl ? sh[k * TPB + tid - s] : R(0);
-      Bl.a[k] = hl ? sh[(NN + k) * TPB + tid - s] : R(k % (NB + 1) == 0);
-      Cl.a[k] = hl ? sh[(2 * NN + k) * TPB + tid - s] : R(0);
-      Ar.a[k] = hr ? sh[k * TPB + tid + s] : R(0);
-      Br.a[k] = hr ? sh[(NN + k) * TPB + tid + s] : R(k % (NB + 1) == 0);
-      Cr.a[k] = hr ? sh[(2 * NN + k) * TPB + tid + s] : R(0);
-    }
-    __syncthreads();
-    Mat<NB, R> al = hl ? mneg(mmul(Ab, minv(Bl, bad))) : mzero<NB, R>();
-    Mat<NB, R> ga = hr ? mneg(mmul(Cb, minv(Br, bad))) : mzero<NB, R>();
-    Mat<NB, R> Bn = Bb;
-    if (hl) Bn = madd(Bn, mmul(al, Cl));
-    if (hr) Bn = madd(Bn, mmul(ga, Ar));
-    Ab = hl ? mmul(al, Al) : mzero<NB, R>();
-    Cb = hr ? mmul(ga, Cr) : mzero<NB, R>();
-    Bb = Bn;
-    S.stm(FI::LVL + 2 * NN * l, tid, al);
-    S.stm(FI::LVL + 2 * NN * l + NN, tid, ga);
-  }
-  S.stm(FI::BINV, tid, minv(Bb, bad));
+  red_factor<NB, R, TPB>(S, tid, tact, Ab, Bb, Cb, sh, bad);
 }
 
 // Solve with the factors of part_factor. rhs and out are NB planes each
 // (row j of thread t at j*TPB + t); out may alias rhs. sh must hold
-// 2 * TPB * NB values of R.
-template <int NB, typename R, int TPB>
+// 3 * TPB * NB values of R. UT as for part_factor.
+template <int NB, typename R, int TPB, bool UT>
 __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, R* const* rhs,
                            R* const* out, int kt, int tid, int tact, R* sh) {
   using FI = FIdx<NB>;
   const int m = kt - 1;
-  const size_t PL = F.PL;
-  (void)PL;
   auto ldv = [&](R* const* pl, int j) {
     Vec<NB, R> v;
 #pragma unroll
@@ -322,9 +505,8 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, R* const* r
     rsep = ldv(rhs, m);
     Vec<NB, R> g = vzero<NB, R>();
     for (int j = 0; j < m; ++j) {
-      Vec<NB, R> r = ldv(rhs, j);
-      Vec<NB, R> gn = mvec(F.ldm(FI::WINV, j, tid), r);
-      if (j > 0) gn = vsub(gn, mvec(F.ldm(FI::G, j, tid), g));
+      Vec<NB, R> gn = mvec(F.ldm(FI::WINV, j, tid), ldv(rhs, j));
+      if (j > 0) gn = vprod<-1, true, false>(gn, F.ldm(FI::G, j, tid), g);
       stv(out, j, gn);
       g = gn;
     }
@@ -332,7 +514,7 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, R* const* r
       Vec<NB, R> yn = g;
       ylast = yn;
       for (int j = m - 2; j >= 0; --j) {
-        Vec<NB, R> yj = vsub(ldv(out, j), mvec(F.ldm(FI::CP, j, tid), yn));
+        const Vec<NB, R> yj = vprod<-1, true, false>(ldv(out, j), F.ldm(FI::CP, j, tid), yn);
         stv(out, j, yj);
         yn = yj;
       }
@@ -349,44 +531,22 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, R* const* r
   }
   Vec<NB, R> rb = vzero<NB, R>();
   if (kt > 0) {
-    rb = vsub(vsub(rsep, mvec(S.ldm(FI::ME, tid), ylast)), mvec(S.ldm(FI::UE, tid), ynext));
+    rb = vprod<-1, true, UT>(vprod<-1, true, UT>(rsep, S.ldm(FI::ME, tid), ylast),
+                             S.ldm(FI::UE, tid), ynext);
   }
-  const int L = pcr_levels(tact);
-  constexpr int NN = NB * NB;
-  for (int l = 0; l < L; ++l) {
-    const int s = 1 << l;
-    R* buf = sh + ((l + 1) & 1) * (NB * TPB);   // level 0 uses buffer 1 (buffer 0 held y)
-#pragma unroll
-    for (int k = 0; k < NB; ++k) buf[k * TPB + tid] = rb.a[k];
-    __syncthreads();
-    Vec<NB, R> rl = vzero<NB, R>(), rr = vzero<NB, R>();
-    if (tid - s >= 0) {
-#pragma unroll
-      for (int k = 0; k < NB; ++k) rl.a[k] = buf[k * TPB + tid - s];
-    }
-    if (tid + s < TPB) {
-#pragma unroll
-      for (int k = 0; k < NB; ++k) rr.a[k] = buf[k * TPB + tid + s];
-    }
-    Mat<NB, R> al = S.ldm(FI::LVL + 2 * NN * l, tid);
-    Mat<NB, R> ga = S.ldm(FI::LVL + 2 * NN * l + NN, tid);
-    rb = vadd(rb, vadd(mvec(al, rl), mvec(ga, rr)));
-  }
-  Vec<NB, R> xsep = mvec(S.ldm(FI::BINV, tid), rb);
-  R* xb = sh + ((L + 1) & 1) * (NB * TPB);
-  __syncthreads();   // everyone done reading the last PCR buffer
-#pragma unroll
-  for (int k = 0; k < NB; ++k) xb[k * TPB + tid] = xsep.a[k];
-  __syncthreads();
+  R* sr = sh + NB * TPB;
+  red_solve<NB, R, TPB>(S, tid, tact, rb, sr);
   if (kt > 0) {
-    Vec<NB, R> xl = vzero<NB, R>();
+    Vec<NB, R> xsep, xl = vzero<NB, R>();
+#pragma unroll
+    for (int k = 0; k < NB; ++k) xsep.a[k] = sr[k * tact + tid];
     if (tid > 0) {
 #pragma unroll
-      for (int k = 0; k < NB; ++k) xl.a[k] = xb[k * TPB + tid - 1];
+      for (int k = 0; k < NB; ++k) xl.a[k] = sr[k * tact + tid - 1];
     }
     for (int j = 0; j < m; ++j) {
-      Vec<NB, R> xj = vadd(ldv(out, j),
-                           vadd(mvec(F.ldm(FI::P, j, tid), xl), mvec(F.ldm(FI::Q, j, tid), xsep)));
+      Vec<NB, R> xj = vprod<1, true, false>(ldv(out, j), F.ldm(FI::P, j, tid), xl);
+      xj = vprod<1, true, false>(xj, F.ldm(FI::Q, j, tid), xsep);
       stv(out, j, xj);
     }
     stv(out, m, xsep);

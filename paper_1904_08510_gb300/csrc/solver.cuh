@@ -69,7 +69,7 @@ enum {
 // Krylov planes (type KR): V[(m+1)*2], W[2], Z[2], XH[2], T[2], ZK[m*2]
 // Factor planes (type KR): 20
 constexpr int kFactorPlanes = 20;
-constexpr int kScalPerThread = 80;
+constexpr int kScalPerThread = FIdx<2>::NSCAL;   // >= 2 * FIdx<1>::NSCAL for the recast form
 
 template <typename KR>
 __host__ __device__ inline size_t slot_bytes_for(size_t PL, int m, int tpb) {
@@ -495,14 +495,14 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
       D.a[0] = (KR)R.Ad; D.a[1] = (KR)R.Bd; D.a[2] = (KR)R.C; D.a[3] = (KR)R.Ld;
       U.a[0] = (KR)R.Au; U.a[1] = (KR)R.Bu; U.a[2] = KR(0); U.a[3] = (KR)R.Lu;
     };
-    part_factor<2, KR, TPB>(F, Sc, kt, tid, g.tact, rowf, sh, bad);
+    part_factor<2, KR, TPB, true>(F, Sc, kt, tid, g.tact, rowf, sh, bad);
   } else if (a.p.precond == SDCEF_PREC_RECAST) {
     // system 1: Ahat; system 2: S~hat = Lhat - (s_Fe/s_Fphi) Bhat; Bhat kept for the matvec
     Planes<1, KR, TPB> F1{S.f, S.PL};
     Planes<1, KR, TPB> F2{S.f + 5 * S.PL, S.PL};
     KR* Bpl = S.f + 10 * S.PL;   // 3 planes: sub, dia, sup
     Scal<1, KR, TPB> S1{S.s};
-    Scal<1, KR, TPB> S2{S.s + 40 * TPB};
+    Scal<1, KR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
     const double rho = cs.r_rho;
     auto row1 = [&](int j, Mat<1, KR>& M, Mat<1, KR>& D, Mat<1, KR>& U) {
       double lf[4];
@@ -513,7 +513,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
       Bpl[1 * S.PL + ix(j, tid, TPB)] = (KR)R.Bd;
       Bpl[2 * S.PL + ix(j, tid, TPB)] = (KR)R.Bu;
     };
-    part_factor<1, KR, TPB>(F1, S1, kt, tid, g.tact, row1, sh, bad);
+    part_factor<1, KR, TPB, false>(F1, S1, kt, tid, g.tact, row1, sh, bad);
     auto row2 = [&](int j, Mat<1, KR>& M, Mat<1, KR>& D, Mat<1, KR>& U) {
       double lf[4];
       lface(j, lf);
@@ -522,7 +522,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
       D.a[0] = (KR)(R.Ld - rho * R.Bd);
       U.a[0] = (KR)(R.Lu - rho * R.Bu);
     };
-    part_factor<1, KR, TPB>(F2, S2, kt, tid, g.tact, row2, sh, bad);
+    part_factor<1, KR, TPB, false>(F2, S2, kt, tid, g.tact, row2, sh, bad);
   }
   __syncthreads();
 }
@@ -539,26 +539,26 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const Co
     Scal<2, KR, TPB> Sc{S.s};
     KR* rin[2] = {re, rp};
     KR* out[2] = {ze, zp};
-    part_solve<2, KR, TPB>(F, Sc, rin, out, kt, tid, g.tact, sh);
+    part_solve<2, KR, TPB, true>(F, Sc, rin, out, kt, tid, g.tact, sh);
   } else if (a.p.precond == SDCEF_PREC_RECAST) {
     Planes<1, KR, TPB> F1{S.f, S.PL};
     Planes<1, KR, TPB> F2{S.f + 5 * S.PL, S.PL};
     const KR* Bpl = S.f + 10 * S.PL;
     Scal<1, KR, TPB> S1{S.s};
-    Scal<1, KR, TPB> S2{S.s + 40 * TPB};
+    Scal<1, KR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
     const KR cfac = (KR)cs.r_c;   // -Chat
     // z1 = Ahat^{-1} r_e (into ze)
     {
       KR* rin[1] = {re};
       KR* out[1] = {ze};
-      part_solve<1, KR, TPB>(F1, S1, rin, out, kt, tid, g.tact, sh);
+      part_solve<1, KR, TPB, false>(F1, S1, rin, out, kt, tid, g.tact, sh);
     }
     // z2 = S~^{-1} (r_phi - Chat z1) (into zp)
     for (int j = 0; j < kt; ++j) zp[ix(j, tid, TPB)] = rp[ix(j, tid, TPB)] + cfac * ze[ix(j, tid, TPB)];
     {
       KR* rin[1] = {zp};
       KR* out[1] = {zp};
-      part_solve<1, KR, TPB>(F2, S2, rin, out, kt, tid, g.tact, sh);
+      part_solve<1, KR, TPB, false>(F2, S2, rin, out, kt, tid, g.tact, sh);
     }
     // t = Bhat z2 (tridiagonal matvec with halo), then x1 = z1 - Ahat^{-1} t
     KR* tpl = S.T(0);
@@ -583,7 +583,7 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const Co
     {
       KR* rin[1] = {tpl};
       KR* out[1] = {tpl};
-      part_solve<1, KR, TPB>(F1, S1, rin, out, kt, tid, g.tact, sh);
+      part_solve<1, KR, TPB, false>(F1, S1, rin, out, kt, tid, g.tact, sh);
     }
     for (int j = 0; j < kt; ++j) ze[ix(j, tid, TPB)] = ze[ix(j, tid, TPB)] - tpl[ix(j, tid, TPB)];
   } else {
