@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ncol", type=int, default=4096)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_df"])
     ap.add_argument("--precond", default="exact", choices=["exact", "recast"])
     ap.add_argument("--seed", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -248,7 +248,7 @@ def main():
     # weak scaling: each rank solves its own batch (independent columns, no exchange)
     b = make_batch("ragged", args.ncol, shard_seed(args.seed, rank, args.ncol))
     lengths = b.lengths()
-    prec = S.MIXED if args.precision == "mixed" else S.FP64
+    prec = {"fp64": S.FP64, "mixed": S.MIXED, "mixed_df": S.MIXED_DF}[args.precision]
     pc = S.PREC_EXACT if args.precond == "exact" else S.PREC_RECAST
     params = S.default_params(precision=prec, precond=pc, threads_per_column=args.tpc,
                               restart_m=30 if pc == S.PREC_RECAST else (16 if prec == S.MIXED else 8))
@@ -340,7 +340,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == S.FP64 else "f64+f32",
+            "dtype": {S.FP64: "f64", S.MIXED: "f64+f32", S.MIXED_DF: "f64+f32x2"}[prec],
             "data": "synthetic (seeded profiles; the paper's flame data is not available)",
             "config": {"workload": WORKLOAD, "ncol": b.ncol, "cells": int(b.ncells),
                        "precision": args.precision, "precond": args.precond, "eps_F": 1e-10,
@@ -413,27 +413,51 @@ def extras(args, S, b, db, solver, params, dev):
     res["plain_unbatched_fp64"] = {"value": m / t, "unit": "column-solves/s", "columns": m,
                                    "launches_per_column": 2}
     one.close()
-    # config 3: the 256-cell batch in mixed precision, error against the FP64 GPU path
+    # config 3: the 256-cell batch in the mixed modes (FP32 and double-float
+    # preconditioner), error against the FP64 GPU path; then the double-float
+    # mode on the headline workload
     b3 = make_batch("single", 4096, 1)
     db3 = S.DeviceBatch.from_host(b3, dev)
     s64 = S.Solver(params, max_cols=b3.ncol, max_cells=b3.ncells, max_col_cells=256)
-    pm = S.default_params(precision=S.MIXED, restart_m=16)
-    s32 = S.Solver(pm, max_cols=b3.ncol, max_cells=b3.ncells, max_col_cells=256)
     t64, o64 = _timed(lambda: s64.solve(db3))
-    t32, o32 = _timed(lambda: s32.solve(db3))
-    ok = (o64["status"] == 0) & (o32["status"] == 0)
-    okc = ok.cpu().numpy()
-    en = _colerr(b3, o32["ne"].cpu().numpy(), o64["ne"].cpu().numpy())[okc]
-    ep = _colerr(b3, o32["phi"].cpu().numpy(), o64["phi"].cpu().numpy())[okc]
-    res["config3_mixed_vs_fp64"] = {
-        "columns": b3.ncol, "cells": 256, "fp64_value": b3.ncol / t64, "mixed_value": b3.ncol / t32,
-        "unit": "column-solves/s", "fp64_status_ok": int((o64["status"] == 0).sum().item()),
-        "mixed_status_ok": int((o32["status"] == 0).sum().item()),
-        "mixed_err_vs_fp64_ne": {"max": float(en.max()), "median": float(np.median(en))},
-        "mixed_err_vs_fp64_phi": {"max": float(ep.max()), "median": float(np.median(ep))},
-        "note": "the FP64 GPU path itself matches the CPU oracle to 1e-9 (tests/test_gpu_parity.py)"}
+    res["config3_mixed_vs_fp64"] = {"columns": b3.ncol, "cells": 256, "unit": "column-solves/s",
+                                    "fp64_value": b3.ncol / t64,
+                                    "fp64_status_ok": int((o64["status"] == 0).sum().item())}
+    for name, prec, m in (("mixed", S.MIXED, 16), ("mixed_df", S.MIXED_DF, 8)):
+        sm = S.Solver(S.default_params(precision=prec, restart_m=m), max_cols=b3.ncol,
+                      max_cells=b3.ncells, max_col_cells=256)
+        tm, om = _timed(lambda: sm.solve(db3))
+        okc = ((o64["status"] == 0) & (om["status"] == 0)).cpu().numpy()
+        en = _colerr(b3, om["ne"].cpu().numpy(), o64["ne"].cpu().numpy())[okc]
+        ep = _colerr(b3, om["phi"].cpu().numpy(), o64["phi"].cpu().numpy())[okc]
+        res["config3_mixed_vs_fp64"].update({
+            f"{name}_value": b3.ncol / tm, f"{name}_status_ok": int((om["status"] == 0).sum().item()),
+            f"{name}_krylov_mean": float(om["krylov_it"].float().mean().item()),
+            f"{name}_err_vs_fp64_ne": {"max": float(en.max()), "median": float(np.median(en))},
+            f"{name}_err_vs_fp64_phi": {"max": float(ep.max()), "median": float(np.median(ep))}})
+        sm.close()
+    res["config3_mixed_vs_fp64"]["note"] = ("the FP64 GPU path itself matches the CPU oracle to 1e-9 "
+                                            "(tests/test_gpu_parity.py)")
     s64.close()
-    s32.close()
+    if args.precision == "fp64":
+        pdf = S.default_params(precision=S.MIXED_DF, precond=params.precond, restart_m=8,
+                               threads_per_column=params.threads_per_column)
+        sdf = S.Solver(pdf, max_cols=b.ncol, max_cells=b.ncells, max_col_cells=int(b.lengths().max()))
+        if not pdf.threads_per_column:
+            sdf.autotune(db, reps=1)
+        o_ref = solver.solve(db)
+        tdf, odf = _timed(lambda: sdf.solve(db))
+        okc = ((o_ref["status"] == 0) & (odf["status"] == 0)).cpu().numpy()
+        en = _colerr(b, odf["ne"].cpu().numpy(), o_ref["ne"].cpu().numpy())[okc]
+        ep = _colerr(b, odf["phi"].cpu().numpy(), o_ref["phi"].cpu().numpy())[okc]
+        res["headline_workload_mixed_df"] = {
+            "value": b.ncol / tdf, "unit": "column-solves/s",
+            "status_ok": int((odf["status"] == 0).sum().item()),
+            "newton_mean": float(odf["newton_it"].float().mean().item()),
+            "krylov_mean": float(odf["krylov_it"].float().mean().item()),
+            "err_vs_fp64_ne": {"max": float(en.max()), "median": float(np.median(en))},
+            "err_vs_fp64_phi": {"max": float(ep.max()), "median": float(np.median(ep))}}
+        sdf.close()
     # config 4: learned initial guess on held-out columns (512-2048 cells)
     if os.path.exists(Lrn.WEIGHTS):
         b4 = make_batch("single", 4096, 2_000_000, n_range=(512, 2048))

@@ -66,6 +66,11 @@ extern "C" {
 #define SDCEF_MIXED 1      /* GMRES basis, Arnoldi and preconditioner in FP32;
                               residuals, JVP differencing, Newton update and the
                               stopping test in FP64                                */
+#define SDCEF_MIXED_DF 2   /* preconditioner (factorisation and solves) in
+                              double-float arithmetic (pairs of FP32 numbers,
+                              ~48-bit significand, FP32 exponent range); GMRES
+                              basis, Arnoldi, residuals, JVP, Newton update and
+                              the stopping test in FP64                            */
 
 /* preconditioner (Sec. 3.2) */
 #define SDCEF_PREC_EXACT 0   /* Eq. prec with the exact Schur complement:
@@ -92,7 +97,7 @@ typedef struct {
   int max_newton;     /* Newton iteration cap                                         */
   int max_krylov;     /* GMRES iteration cap per Newton step                          */
   int max_linesearch; /* line-search halvings before LINESEARCH_FAIL                  */
-  int precision;      /* SDCEF_FP64 | SDCEF_MIXED                                     */
+  int precision;      /* SDCEF_FP64 | SDCEF_MIXED | SDCEF_MIXED_DF                    */
   int precond;        /* SDCEF_PREC_EXACT | SDCEF_PREC_RECAST | SDCEF_PREC_NONE       */
   int bc_electron;    /* SDCEF_BC_ABSORBING | SDCEF_BC_ZERO_GRADIENT                  */
   int threads_per_column; /* 0 = chosen per column length; else 32, 64, 128 or 256    */

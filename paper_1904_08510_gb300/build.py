@@ -21,7 +21,10 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
-INSTANCES = [(tpb, kr) for kr in ("double", "float") for tpb in (32, 64, 128, 256)]
+# (threads per column, Krylov type, preconditioner type) of each kernel instance
+INSTANCES = [(tpb, kr, pr) for kr, pr in (("double", "double"), ("float", "float"),
+                                          ("double", "sdcef::dfloat"))
+             for tpb in (32, 64, 128, 256)]
 
 
 def _nvcc() -> str:
@@ -59,10 +62,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     jobs = []
-    for tpb, kr in INSTANCES:
-        obj = os.path.join(BUILD, f"kern_{tpb}_{kr}.o")
-        cmd = [nvcc, *ARCH, *FLAGS, f"-DSDCEF_TPB={tpb}", f"-DSDCEF_KR={kr}"]
-        if (tpb, kr) == INSTANCES[0]:
+    for tpb, kr, pr in INSTANCES:
+        obj = os.path.join(BUILD, f"kern_{tpb}_{kr}_{pr.split(':')[-1]}.o")
+        cmd = [nvcc, *ARCH, *FLAGS, f"-DSDCEF_TPB={tpb}", f"-DSDCEF_KR={kr}", f"-DSDCEF_PR={pr}"]
+        if (tpb, kr, pr) == INSTANCES[0]:
             cmd.append("-DSDCEF_WITH_ORDER")
         cmd += ["-c", os.path.join(CSRC, "kern_inst.cu"), "-o", obj]
         jobs.append((obj, cmd))

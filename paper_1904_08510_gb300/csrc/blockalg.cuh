@@ -30,7 +30,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
+
 namespace sdcef {
+using ::fma;
 
 template <int NB, typename R>
 struct Mat {
@@ -216,14 +219,14 @@ template <int NB, typename R>
 __device__ __forceinline__ Mat<NB, R> shfl_up_m(const Mat<NB, R>& x, int s) {
   Mat<NB, R> r;
 #pragma unroll
-  for (int k = 0; k < NB * NB; ++k) r.a[k] = __shfl_up_sync(0xffffffffu, x.a[k], s);
+  for (int k = 0; k < NB * NB; ++k) r.a[k] = shfl_up_v(x.a[k], s);
   return r;
 }
 template <int NB, typename R>
 __device__ __forceinline__ Mat<NB, R> shfl_down_m(const Mat<NB, R>& x, int s) {
   Mat<NB, R> r;
 #pragma unroll
-  for (int k = 0; k < NB * NB; ++k) r.a[k] = __shfl_down_sync(0xffffffffu, x.a[k], s);
+  for (int k = 0; k < NB * NB; ++k) r.a[k] = shfl_down_v(x.a[k], s);
   return r;
 }
 
@@ -372,8 +375,8 @@ __device__ void red_solve(Scal<NB, R, TPB> S, int tid, int T, const Vec<NB, R>& 
       Vec<NB, R> rl, rr;
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        rl.a[c] = __shfl_up_sync(0xffffffffu, r.a[c], s);
-        rr.a[c] = __shfl_down_sync(0xffffffffu, r.a[c], s);
+        rl.a[c] = shfl_up_v(r.a[c], s);
+        rr.a[c] = shfl_down_v(r.a[c], s);
       }
       if (tid < n) {
         if (tid >= s) r = vprod<1, true, false>(r, S.ldm(FI::PCR0 + 2 * NN * k, tid), rl);
@@ -482,40 +485,51 @@ __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, in
   red_factor<NB, R, TPB>(S, tid, tact, Ab, Bb, Cb, sh, bad);
 }
 
-// Solve with the factors of part_factor. rhs and out are NB planes each
-// (row j of thread t at j*TPB + t); out may alias rhs. sh must hold
-// 3 * TPB * NB values of R. UT as for part_factor.
-template <int NB, typename R, int TPB, bool UT>
-__device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, R* const* rhs,
-                           R* const* out, int kt, int tid, int tact, R* sh) {
+// Solve with the factors of part_factor. rhs and out are NB planes each of the
+// caller's type IO (row j of thread t at j*TPB + t); scr are NB planes of R
+// for the intermediate sweeps (scr may alias out when IO is R; out may alias
+// rhs). sh must hold 3 * TPB * NB values of R. UT as for part_factor.
+template <int NB, typename R, typename IO, int TPB, bool UT>
+__device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* rhs,
+                           IO* const* out, R* const* scr, int kt, int tid, int tact, R* sh) {
   using FI = FIdx<NB>;
   const int m = kt - 1;
-  auto ldv = [&](R* const* pl, int j) {
+  auto ldin = [&](int j) {
     Vec<NB, R> v;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) v.a[k] = pl[k][(size_t)j * TPB + tid];
+    for (int k = 0; k < NB; ++k) v.a[k] = conv<R>(rhs[k][(size_t)j * TPB + tid]);
     return v;
   };
-  auto stv = [&](R* const* pl, int j, const Vec<NB, R>& v) {
+  auto lds = [&](int j) {
+    Vec<NB, R> v;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) pl[k][(size_t)j * TPB + tid] = v.a[k];
+    for (int k = 0; k < NB; ++k) v.a[k] = scr[k][(size_t)j * TPB + tid];
+    return v;
+  };
+  auto sts = [&](int j, const Vec<NB, R>& v) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) scr[k][(size_t)j * TPB + tid] = v.a[k];
+  };
+  auto stout = [&](int j, const Vec<NB, R>& v) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) out[k][(size_t)j * TPB + tid] = conv<IO>(v.a[k]);
   };
   Vec<NB, R> yfirst = vzero<NB, R>(), ylast = vzero<NB, R>(), rsep = vzero<NB, R>();
   if (kt > 0) {
-    rsep = ldv(rhs, m);
+    rsep = ldin(m);
     Vec<NB, R> g = vzero<NB, R>();
     for (int j = 0; j < m; ++j) {
-      Vec<NB, R> gn = mvec(F.ldm(FI::WINV, j, tid), ldv(rhs, j));
+      Vec<NB, R> gn = mvec(F.ldm(FI::WINV, j, tid), ldin(j));
       if (j > 0) gn = vprod<-1, true, false>(gn, F.ldm(FI::G, j, tid), g);
-      stv(out, j, gn);
+      sts(j, gn);
       g = gn;
     }
     if (m > 0) {
       Vec<NB, R> yn = g;
       ylast = yn;
       for (int j = m - 2; j >= 0; --j) {
-        const Vec<NB, R> yj = vprod<-1, true, false>(ldv(out, j), F.ldm(FI::CP, j, tid), yn);
-        stv(out, j, yj);
+        const Vec<NB, R> yj = vprod<-1, true, false>(lds(j), F.ldm(FI::CP, j, tid), yn);
+        sts(j, yj);
         yn = yj;
       }
       yfirst = yn;
@@ -545,11 +559,11 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, R* const* r
       for (int k = 0; k < NB; ++k) xl.a[k] = sr[k * tact + tid - 1];
     }
     for (int j = 0; j < m; ++j) {
-      Vec<NB, R> xj = vprod<1, true, false>(ldv(out, j), F.ldm(FI::P, j, tid), xl);
+      Vec<NB, R> xj = vprod<1, true, false>(lds(j), F.ldm(FI::P, j, tid), xl);
       xj = vprod<1, true, false>(xj, F.ldm(FI::Q, j, tid), xsep);
-      stv(out, j, xj);
+      stout(j, xj);
     }
-    stv(out, m, xsep);
+    stout(m, xsep);
   }
   __syncthreads();   // the caller may reuse sh
 }

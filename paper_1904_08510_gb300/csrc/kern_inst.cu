@@ -1,12 +1,13 @@
 // Explicit instantiation of the solver kernel for one (threads per column,
-// Krylov precision) pair, selected with -DSDCEF_TPB=... -DSDCEF_KR=...; the
-// order kernel is built in the TU compiled with -DSDCEF_WITH_ORDER.
+// Krylov type, preconditioner type) triple, selected with -DSDCEF_TPB=...
+// -DSDCEF_KR=... -DSDCEF_PR=...; the order kernel is built in the TU compiled
+// with -DSDCEF_WITH_ORDER.
 #define SDCEF_KERNEL_TU
 #include "solver.cuh"
 
 namespace sdcef_impl {
-template cudaError_t launch_t<SDCEF_TPB, SDCEF_KR>(const KArgs&, int, size_t, cudaStream_t);
-template int occupancy_t<SDCEF_TPB, SDCEF_KR>(size_t);
+template cudaError_t launch_t<SDCEF_TPB, SDCEF_KR, SDCEF_PR>(const KArgs&, int, size_t, cudaStream_t);
+template int occupancy_t<SDCEF_TPB, SDCEF_KR, SDCEF_PR>(size_t);
 #ifdef SDCEF_WITH_ORDER
 cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int shift, int* order,
                          cudaStream_t st) {

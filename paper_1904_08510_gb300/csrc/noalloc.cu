@@ -61,27 +61,6 @@ int scratch_for_current_device(unsigned char** ptr, int* sms) {
   return SDCEF_SUCCESS;
 }
 
-template <typename KR>
-cudaError_t launch_kr_na(int tpb, const KArgs& a, int grid, size_t smem, cudaStream_t st) {
-  switch (tpb) {
-    case 32: return launch_t<32, KR>(a, grid, smem, st);
-    case 64: return launch_t<64, KR>(a, grid, smem, st);
-    case 128: return launch_t<128, KR>(a, grid, smem, st);
-    case 256: return launch_t<256, KR>(a, grid, smem, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename KR>
-int occupancy_kr_na(int tpb, size_t smem) {
-  switch (tpb) {
-    case 32: return occupancy_t<32, KR>(smem);
-    case 64: return occupancy_t<64, KR>(smem);
-    case 128: return occupancy_t<128, KR>(smem);
-    case 256: return occupancy_t<256, KR>(smem);
-  }
-  return 1;
-}
 
 }  // namespace
 
@@ -113,11 +92,11 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   if (rc) return rc;
 
   const int tpb = p->threads_per_column ? p->threads_per_column : 128;
-  const bool fp32 = p->precision == SDCEF_MIXED;
+  const int prec = p->precision;
   const int m = p->restart_m;
   const int kmax = (max_col_cells + tpb - 1) / tpb;
   const size_t PL = (size_t)kmax * tpb;
-  const size_t slot = fp32 ? slot_bytes_for<float>(PL, m, tpb) : slot_bytes_for<double>(PL, m, tpb);
+  const size_t slot = slot_bytes_prec(prec, PL, m, tpb);
   const size_t avail = SDCEF_NOALLOC_SCRATCH_BYTES - kHeaderAligned;
   const int64_t nslots = (int64_t)(avail / slot);
   if (nslots < 1)
@@ -172,11 +151,8 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.mode = MODE_SOLVE;
 
   cudaStream_t st = (cudaStream_t)stream;
-  const int nw = tpb / 32;
-  const size_t kr = fp32 ? 4 : 8;
-  const size_t smem = ((size_t)(nw + 1) * 40 + 4 * tpb + (m + 1) * m + (m + 1) + 3 * m + m + 2) *
-                          sizeof(double) + 12 * (size_t)tpb * kr + 64;
-  const int per_sm = fp32 ? occupancy_kr_na<float>(tpb, smem) : occupancy_kr_na<double>(tpb, smem);
+  const size_t smem = smem_bytes_prec(prec, tpb, m);
+  const int per_sm = occupancy_prec(prec, tpb, smem);
   const int grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, a.ncol, nslots});
   // the queue counter must start at zero; everything else a call reads it writes first
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
@@ -189,7 +165,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
     if (e != cudaSuccess) return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
     a.order = order;
   }
-  e = fp32 ? launch_kr_na<float>(tpb, a, grid, smem, st) : launch_kr_na<double>(tpb, a, grid, smem, st);
+  e = launch_prec(prec, tpb, a, grid, smem, st);
   if (e != cudaSuccess) return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
   return SDCEF_SUCCESS;
 }

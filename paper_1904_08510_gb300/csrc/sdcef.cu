@@ -52,11 +52,6 @@ int tpb_for(const sdcef_params& p, int max_col_cells) {
   return 128;
 }
 
-size_t smem_bytes(int tpb, int m, size_t kr) {
-  const int nw = tpb / 32;
-  size_t d = (size_t)(nw + 1) * 40 + 4 * tpb + (m + 1) * m + (m + 1) + 3 * m + m + 2;
-  return d * sizeof(double) + 12 * (size_t)tpb * kr + 64;
-}
 
 int check_params(const sdcef_params* p, int m_cap) {
   if (!p) return set_err(SDCEF_ERR_INVALID, "params is NULL");
@@ -68,7 +63,7 @@ int check_params(const sdcef_params* p, int m_cap) {
   if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0 || p->guess_newton_cap < 0 ||
       !(p->guess_reject_ratio >= 0.0))
     return set_err(SDCEF_ERR_INVALID, "params: iteration caps out of range");
-  if (p->precision != SDCEF_FP64 && p->precision != SDCEF_MIXED)
+  if (p->precision != SDCEF_FP64 && p->precision != SDCEF_MIXED && p->precision != SDCEF_MIXED_DF)
     return set_err(SDCEF_ERR_INVALID, "params: precision");
   if (p->precond != SDCEF_PREC_EXACT && p->precond != SDCEF_PREC_RECAST &&
       p->precond != SDCEF_PREC_NONE)
@@ -79,28 +74,6 @@ int check_params(const sdcef_params* p, int m_cap) {
   if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256)
     return set_err(SDCEF_ERR_INVALID, "params: threads_per_column must be 0, 32, 64, 128 or 256");
   return SDCEF_SUCCESS;
-}
-
-template <typename KR>
-cudaError_t launch_kr(int tpb, const KArgs& a, int grid, size_t smem, cudaStream_t st) {
-  switch (tpb) {
-    case 32: return launch_t<32, KR>(a, grid, smem, st);
-    case 64: return launch_t<64, KR>(a, grid, smem, st);
-    case 128: return launch_t<128, KR>(a, grid, smem, st);
-    case 256: return launch_t<256, KR>(a, grid, smem, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename KR>
-int occupancy_kr(int tpb, size_t smem) {
-  switch (tpb) {
-    case 32: return occupancy_t<32, KR>(smem);
-    case 64: return occupancy_t<64, KR>(smem);
-    case 128: return occupancy_t<128, KR>(smem);
-    case 256: return occupancy_t<256, KR>(smem);
-  }
-  return 1;
 }
 
 int validate_batch(const sdcef_ctx* ctx, const sdcef_batch* b, bool need_solve_inputs) {
@@ -120,7 +93,7 @@ int validate_batch(const sdcef_ctx* ctx, const sdcef_batch* b, bool need_solve_i
 }
 
 // Fill kernel args shared by all modes.
-KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb, size_t kr) {
+KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb) {
   KArgs a;
   memset(&a, 0, sizeof(a));
   a.ncol = b->ncol;
@@ -143,8 +116,7 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb, size_t kr) {
   const int kmax = (ctx->max_col_cells + tpb - 1) / tpb;
   a.kmax = kmax;
   a.PL = (size_t)kmax * tpb;
-  a.slot_bytes = kr == 8 ? slot_bytes_for<double>(a.PL, ctx->m_cap, tpb)
-                         : slot_bytes_for<float>(a.PL, ctx->m_cap, tpb);
+  a.slot_bytes = slot_bytes_prec(ctx->p.precision, a.PL, ctx->m_cap, tpb);
   a.max_col_cells = ctx->max_col_cells;
   a.queue = ctx->queue;
   const sdcef_params& p = ctx->p;
@@ -166,15 +138,14 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb, size_t kr) {
 }
 
 int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
-  const bool fp32 = ctx->p.precision == SDCEF_MIXED;
-  const size_t kr = fp32 ? 4 : 8;
+  const int prec = ctx->p.precision;
   // restart length used by the iteration (planes are laid out for m_cap)
   const int m_run = ctx->p.restart_m;
   a.p.m = m_run;
-  const size_t smem = smem_bytes(tpb, m_run, kr);
+  const size_t smem = smem_bytes_prec(prec, tpb, m_run);
   // slot layout must use the same m as the device code: recompute with m_run
-  a.slot_bytes = fp32 ? slot_bytes_for<float>(a.PL, m_run, tpb) : slot_bytes_for<double>(a.PL, m_run, tpb);
-  int per_sm = fp32 ? occupancy_kr<float>(tpb, smem) : occupancy_kr<double>(tpb, smem);
+  a.slot_bytes = slot_bytes_prec(prec, a.PL, m_run, tpb);
+  int per_sm = occupancy_prec(prec, tpb, smem);
   int64_t slots_fit = (int64_t)(ctx->ws_bytes / a.slot_bytes);
   int grid = (int)std::min<int64_t>({(int64_t)per_sm * ctx->sms, a.ncol, slots_fit});
   if (grid < 1) return set_err(SDCEF_ERR_CAPACITY, "workspace too small for one column slot");
@@ -190,8 +161,7 @@ int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
     a.order = ctx->order;
     ++ctx->launches;
   }
-  e = fp32 ? launch_kr<float>(tpb, a, grid, smem, ctx->stream)
-           : launch_kr<double>(tpb, a, grid, smem, ctx->stream);
+  e = launch_prec(prec, tpb, a, grid, smem, ctx->stream);
   if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
   ++ctx->launches;
   return SDCEF_SUCCESS;
@@ -256,7 +226,7 @@ int sdcef_create(sdcef_ctx** out, const sdcef_params* p, int64_t max_cols, int64
   size_t best = 0;
   for (int tpb : {32, 64, 128, 256}) {
     const size_t PL = (size_t)((max_col_cells + tpb - 1) / tpb) * tpb;
-    best = std::max(best, slot_bytes_for<double>(PL, c->m_cap, tpb));
+    best = std::max(best, slot_bytes_for<double, double>(PL, c->m_cap, tpb));
   }
   int64_t nslots = std::min<int64_t>((int64_t)c->sms * 4, max_cols);
   c->nslots = (int)nslots;
@@ -303,8 +273,7 @@ int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* 
   if (b->ncol == 0) { ctx->launches = 0; return SDCEF_SUCCESS; }
   if (!out || !out->ne_out || !out->phi_out) return set_err(SDCEF_ERR_INVALID, "result: ne_out / phi_out is NULL");
   const int tpb = tpb_for(ctx->p, ctx->max_col_cells);
-  const size_t kr = ctx->p.precision == SDCEF_MIXED ? 4 : 8;
-  KArgs a = base_args(ctx, b, tpb, kr);
+  KArgs a = base_args(ctx, b, tpb);
   a.mode = MODE_SOLVE;
   a.ne_out = out->ne_out;
   a.phi_out = out->phi_out;
@@ -422,8 +391,7 @@ int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
   if (b->ncol == 0) return SDCEF_SUCCESS;
   if (!ne || !phi || !F_e || !F_phi) return set_err(SDCEF_ERR_INVALID, "residual: NULL array");
   const int tpb = tpb_for(ctx->p, ctx->max_col_cells);
-  const size_t kr = ctx->p.precision == SDCEF_MIXED ? 4 : 8;
-  KArgs a = base_args(ctx, b, tpb, kr);
+  KArgs a = base_args(ctx, b, tpb);
   // set-up reads ne_old / phi_old; point them at X when absent
   if (!a.ne_old) a.ne_old = ne;
   if (!a.phi_old) a.phi_old = phi;
@@ -445,8 +413,7 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double
   if (!ne || !phi || !r_e || !r_phi || !x_e || !x_phi)
     return set_err(SDCEF_ERR_INVALID, "precond: NULL array");
   const int tpb = tpb_for(ctx->p, ctx->max_col_cells);
-  const size_t kr = ctx->p.precision == SDCEF_MIXED ? 4 : 8;
-  KArgs a = base_args(ctx, b, tpb, kr);
+  KArgs a = base_args(ctx, b, tpb);
   a.mode = MODE_PRECOND;
   a.x_ne = ne;
   a.x_phi = phi;

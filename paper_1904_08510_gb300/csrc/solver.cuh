@@ -67,24 +67,82 @@ enum {
   PD_COUNT = PD_FACE1 + 4
 };
 // Krylov planes (type KR): V[(m+1)*2], W[2], Z[2], XH[2], T[2], ZK[m*2]
-// Factor planes (type KR): 20
-constexpr int kFactorPlanes = 20;
+// Preconditioner planes (type PR): 20 factor planes + 2 scratch planes for the
+// forward/backward sweeps of a solve; per-thread scalars (type PR).
+constexpr int kFactorPlanes = 22;
+constexpr int kScrPlane = 20;
 constexpr int kScalPerThread = FIdx<2>::NSCAL;   // >= 2 * FIdx<1>::NSCAL for the recast form
 
-template <typename KR>
+template <typename KR, typename PR>
 __host__ __device__ inline size_t slot_bytes_for(size_t PL, int m, int tpb) {
   size_t b = (size_t)PD_COUNT * PL * sizeof(double);
-  b += (size_t)(2 * (m + 1) + 8 + 2 * m + kFactorPlanes) * PL * sizeof(KR);
-  b += (size_t)kScalPerThread * tpb * sizeof(KR);
+  b += (size_t)(2 * (m + 1) + 8 + 2 * m) * PL * sizeof(KR);
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)kFactorPlanes * PL * sizeof(PR);
+  b += (size_t)kScalPerThread * tpb * sizeof(PR);
   return (b + 255) & ~(size_t)255;
+}
+// Dynamic shared memory of the solver kernel: reduction scratch, halo,
+// Hessenberg / Givens state (FP64) and the block-solver exchange area (PR).
+inline size_t smem_bytes_for(int tpb, int m, size_t pr_bytes) {
+  const int nw = tpb / 32;
+  size_t d = (size_t)(nw + 1) * 40 + 4 * tpb + (m + 1) * m + (m + 1) + 3 * m + m + 2;
+  return d * sizeof(double) + 12 * (size_t)tpb * pr_bytes + 64;
 }
 
 
 // Launch / occupancy entry points, one instantiation per kernel TU.
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st);
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 int occupancy_t(size_t smem);
+
+// Precision modes as (Krylov type KR, preconditioner type PR):
+//   SDCEF_FP64 (double, double), SDCEF_MIXED (float, float),
+//   SDCEF_MIXED_DF (double, dfloat).
+inline size_t slot_bytes_prec(int precision, size_t PL, int m, int tpb) {
+  if (precision == SDCEF_MIXED) return slot_bytes_for<float, float>(PL, m, tpb);
+  if (precision == SDCEF_MIXED_DF) return slot_bytes_for<double, dfloat>(PL, m, tpb);
+  return slot_bytes_for<double, double>(PL, m, tpb);
+}
+inline size_t smem_bytes_prec(int precision, int tpb, int m) {
+  return smem_bytes_for(tpb, m, precision == SDCEF_MIXED ? sizeof(float) : 8);
+}
+#ifndef SDCEF_KERNEL_TU
+// Host dispatch (host translation units only: in a kernel unit these bodies
+// would instantiate every kernel).
+template <typename KR, typename PR>
+inline cudaError_t launch_tpb(int tpb, const KArgs& a, int grid, size_t smem, cudaStream_t st) {
+  switch (tpb) {
+    case 32: return launch_t<32, KR, PR>(a, grid, smem, st);
+    case 64: return launch_t<64, KR, PR>(a, grid, smem, st);
+    case 128: return launch_t<128, KR, PR>(a, grid, smem, st);
+    case 256: return launch_t<256, KR, PR>(a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+template <typename KR, typename PR>
+inline int occupancy_tpb(int tpb, size_t smem) {
+  switch (tpb) {
+    case 32: return occupancy_t<32, KR, PR>(smem);
+    case 64: return occupancy_t<64, KR, PR>(smem);
+    case 128: return occupancy_t<128, KR, PR>(smem);
+    case 256: return occupancy_t<256, KR, PR>(smem);
+  }
+  return 1;
+}
+inline cudaError_t launch_prec(int precision, int tpb, const KArgs& a, int grid, size_t smem,
+                               cudaStream_t st) {
+  if (precision == SDCEF_MIXED) return launch_tpb<float, float>(tpb, a, grid, smem, st);
+  if (precision == SDCEF_MIXED_DF) return launch_tpb<double, dfloat>(tpb, a, grid, smem, st);
+  return launch_tpb<double, double>(tpb, a, grid, smem, st);
+}
+inline int occupancy_prec(int precision, int tpb, size_t smem) {
+  if (precision == SDCEF_MIXED) return occupancy_tpb<float, float>(tpb, smem);
+  if (precision == SDCEF_MIXED_DF) return occupancy_tpb<double, dfloat>(tpb, smem);
+  return occupancy_tpb<double, double>(tpb, smem);
+}
+#endif  // SDCEF_KERNEL_TU
 cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int shift, int* order,
                          cudaStream_t st);
 
@@ -177,12 +235,12 @@ struct Geo {
   int tid, kt, t0, N, K, tact;
 };
 
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 struct Slot {
   double* d;    // FP64 planes
   KR* k;        // Krylov planes
-  KR* f;        // factor planes
-  KR* s;        // per-thread scalars
+  PR* f;        // preconditioner planes
+  PR* s;        // per-thread scalars
   size_t PL;
   int m;
   __device__ double* pd(int i) const { return d + (size_t)i * PL; }
@@ -195,15 +253,18 @@ struct Slot {
   __device__ KR* ZK(int i, int comp) const { return k + (size_t)(2 * (m + 1) + 8 + 2 * i + comp) * PL; }
 };
 
-template <int TPB, typename KR>
-__device__ Slot<TPB, KR> make_slot(const KArgs& a, int slot) {
-  Slot<TPB, KR> s;
+template <int TPB, typename KR, typename PR>
+__device__ Slot<TPB, KR, PR> make_slot(const KArgs& a, int slot) {
+  Slot<TPB, KR, PR> s;
   char* base = a.ws + (size_t)slot * a.slot_bytes;
   s.PL = a.PL;
   s.m = a.p.m;
   s.d = (double*)base;
   s.k = (KR*)(base + (size_t)PD_COUNT * a.PL * sizeof(double));
-  s.f = s.k + (size_t)(2 * (a.p.m + 1) + 8 + 2 * a.p.m) * a.PL;
+  size_t kb = (size_t)PD_COUNT * a.PL * sizeof(double) +
+              (size_t)(2 * (a.p.m + 1) + 8 + 2 * a.p.m) * a.PL * sizeof(KR);
+  kb = (kb + 15) & ~(size_t)15;
+  s.f = (PR*)(base + kb);
   s.s = s.f + (size_t)kFactorPlanes * a.PL;
   return s;
 }
@@ -220,8 +281,8 @@ __device__ __forceinline__ size_t ix(int j, int tid, int TPB) { return (size_t)j
 // --------------------------------------------------------------------------
 enum { OUT_F = 0, OUT_JVP = 1 };
 
-template <int TPB, typename KR>
-__device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR>& S,
+template <int TPB, typename KR, typename PR>
+__device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
                          const double* nb, const double* pb, const KR* dn, const KR* dp,
                          double cn, double cp, int out_mode, double* fe_o, double* fp_o, int fs,
                          const double* fe_ref, const double* fp_ref, KR* we, KR* wp, double ieps,
@@ -390,9 +451,9 @@ struct RowJ {
   double As, Ad, Au, Bs, Bd, Bu, Ls, Ld, Lu, C;
 };
 
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColShared& cs,
-                                        const Slot<TPB, KR>& S, int fs, int j,
+                                        const Slot<TPB, KR, PR>& S, int fs, int j,
                                         const double* lf /*left face (a0,a1,b0,b1)*/, double n_i,
                                         double n_0, double n_last) {
   (void)n_i;
@@ -455,9 +516,9 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
 // --------------------------------------------------------------------------
 // Preconditioner: factorisation and application (scaled units).
 // --------------------------------------------------------------------------
-template <int TPB, typename KR>
-__device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR>& S,
-                            int fs, KR* sh, double* halo, bool* bad) {
+template <int TPB, typename KR, typename PR>
+__device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
+                            int fs, PR* sh, double* halo, bool* bad) {
   const int tid = g.tid, kt = g.kt;
   // left-face derivatives of each thread's first row = previous thread's last face
   if (kt > 0) {
@@ -485,85 +546,87 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     }
   };
   if (a.p.precond == SDCEF_PREC_EXACT) {
-    Planes<2, KR, TPB> F{S.f, S.PL};
-    Scal<2, KR, TPB> Sc{S.s};
-    auto rowf = [&](int j, Mat<2, KR>& M, Mat<2, KR>& D, Mat<2, KR>& U) {
+    Planes<2, PR, TPB> F{S.f, S.PL};
+    Scal<2, PR, TPB> Sc{S.s};
+    auto rowf = [&](int j, Mat<2, PR>& M, Mat<2, PR>& D, Mat<2, PR>& U) {
       double lf[4];
       lface(j, lf);
-      RowJ R = jac_row<TPB, KR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
-      M.a[0] = (KR)R.As; M.a[1] = (KR)R.Bs; M.a[2] = KR(0); M.a[3] = (KR)R.Ls;
-      D.a[0] = (KR)R.Ad; D.a[1] = (KR)R.Bd; D.a[2] = (KR)R.C; D.a[3] = (KR)R.Ld;
-      U.a[0] = (KR)R.Au; U.a[1] = (KR)R.Bu; U.a[2] = KR(0); U.a[3] = (KR)R.Lu;
+      RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      M.a[0] = conv<PR>(R.As); M.a[1] = conv<PR>(R.Bs); M.a[2] = PR(0); M.a[3] = conv<PR>(R.Ls);
+      D.a[0] = conv<PR>(R.Ad); D.a[1] = conv<PR>(R.Bd); D.a[2] = conv<PR>(R.C); D.a[3] = conv<PR>(R.Ld);
+      U.a[0] = conv<PR>(R.Au); U.a[1] = conv<PR>(R.Bu); U.a[2] = PR(0); U.a[3] = conv<PR>(R.Lu);
     };
-    part_factor<2, KR, TPB, true>(F, Sc, kt, tid, g.tact, rowf, sh, bad);
+    part_factor<2, PR, TPB, true>(F, Sc, kt, tid, g.tact, rowf, sh, bad);
   } else if (a.p.precond == SDCEF_PREC_RECAST) {
     // system 1: Ahat; system 2: S~hat = Lhat - (s_Fe/s_Fphi) Bhat; Bhat kept for the matvec
-    Planes<1, KR, TPB> F1{S.f, S.PL};
-    Planes<1, KR, TPB> F2{S.f + 5 * S.PL, S.PL};
-    KR* Bpl = S.f + 10 * S.PL;   // 3 planes: sub, dia, sup
-    Scal<1, KR, TPB> S1{S.s};
-    Scal<1, KR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
+    Planes<1, PR, TPB> F1{S.f, S.PL};
+    Planes<1, PR, TPB> F2{S.f + 5 * S.PL, S.PL};
+    PR* Bpl = S.f + 10 * S.PL;   // 3 planes: sub, dia, sup
+    Scal<1, PR, TPB> S1{S.s};
+    Scal<1, PR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
     const double rho = cs.r_rho;
-    auto row1 = [&](int j, Mat<1, KR>& M, Mat<1, KR>& D, Mat<1, KR>& U) {
+    auto row1 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
       double lf[4];
       lface(j, lf);
-      RowJ R = jac_row<TPB, KR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
-      M.a[0] = (KR)R.As; D.a[0] = (KR)R.Ad; U.a[0] = (KR)R.Au;
-      Bpl[0 * S.PL + ix(j, tid, TPB)] = (KR)R.Bs;
-      Bpl[1 * S.PL + ix(j, tid, TPB)] = (KR)R.Bd;
-      Bpl[2 * S.PL + ix(j, tid, TPB)] = (KR)R.Bu;
+      RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      M.a[0] = conv<PR>(R.As); D.a[0] = conv<PR>(R.Ad); U.a[0] = conv<PR>(R.Au);
+      Bpl[0 * S.PL + ix(j, tid, TPB)] = conv<PR>(R.Bs);
+      Bpl[1 * S.PL + ix(j, tid, TPB)] = conv<PR>(R.Bd);
+      Bpl[2 * S.PL + ix(j, tid, TPB)] = conv<PR>(R.Bu);
     };
-    part_factor<1, KR, TPB, false>(F1, S1, kt, tid, g.tact, row1, sh, bad);
-    auto row2 = [&](int j, Mat<1, KR>& M, Mat<1, KR>& D, Mat<1, KR>& U) {
+    part_factor<1, PR, TPB, false>(F1, S1, kt, tid, g.tact, row1, sh, bad);
+    auto row2 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
       double lf[4];
       lface(j, lf);
-      RowJ R = jac_row<TPB, KR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
-      M.a[0] = (KR)(R.Ls - rho * R.Bs);
-      D.a[0] = (KR)(R.Ld - rho * R.Bd);
-      U.a[0] = (KR)(R.Lu - rho * R.Bu);
+      RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      M.a[0] = conv<PR>(R.Ls - rho * R.Bs);
+      D.a[0] = conv<PR>(R.Ld - rho * R.Bd);
+      U.a[0] = conv<PR>(R.Lu - rho * R.Bu);
     };
-    part_factor<1, KR, TPB, false>(F2, S2, kt, tid, g.tact, row2, sh, bad);
+    part_factor<1, PR, TPB, false>(F2, S2, kt, tid, g.tact, row2, sh, bad);
   }
   __syncthreads();
 }
 
 // z = Mhat^{-1} r (scaled units); in/out are Krylov planes (2 components each).
 // Returns ||z||_2^2 (block-reduced) if want_norm.
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const ColShared& cs,
-                             const Slot<TPB, KR>& S, KR* re, KR* rp, KR* ze, KR* zp, KR* sh,
+                             const Slot<TPB, KR, PR>& S, KR* re, KR* rp, KR* ze, KR* zp, PR* sh,
                              double* red, bool want_norm) {
   const int tid = g.tid, kt = g.kt;
   if (a.p.precond == SDCEF_PREC_EXACT) {
-    Planes<2, KR, TPB> F{S.f, S.PL};
-    Scal<2, KR, TPB> Sc{S.s};
+    Planes<2, PR, TPB> F{S.f, S.PL};
+    Scal<2, PR, TPB> Sc{S.s};
     KR* rin[2] = {re, rp};
     KR* out[2] = {ze, zp};
-    part_solve<2, KR, TPB, true>(F, Sc, rin, out, kt, tid, g.tact, sh);
+    PR* scr[2] = {S.f + (size_t)kScrPlane * S.PL, S.f + (size_t)(kScrPlane + 1) * S.PL};
+    part_solve<2, PR, KR, TPB, true>(F, Sc, rin, out, scr, kt, tid, g.tact, sh);
   } else if (a.p.precond == SDCEF_PREC_RECAST) {
-    Planes<1, KR, TPB> F1{S.f, S.PL};
-    Planes<1, KR, TPB> F2{S.f + 5 * S.PL, S.PL};
-    const KR* Bpl = S.f + 10 * S.PL;
-    Scal<1, KR, TPB> S1{S.s};
-    Scal<1, KR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
+    Planes<1, PR, TPB> F1{S.f, S.PL};
+    Planes<1, PR, TPB> F2{S.f + 5 * S.PL, S.PL};
+    const PR* Bpl = S.f + 10 * S.PL;
+    PR* scr[1] = {S.f + (size_t)kScrPlane * S.PL};
+    Scal<1, PR, TPB> S1{S.s};
+    Scal<1, PR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
     const KR cfac = (KR)cs.r_c;   // -Chat
     // z1 = Ahat^{-1} r_e (into ze)
     {
       KR* rin[1] = {re};
       KR* out[1] = {ze};
-      part_solve<1, KR, TPB, false>(F1, S1, rin, out, kt, tid, g.tact, sh);
+      part_solve<1, PR, KR, TPB, false>(F1, S1, rin, out, scr, kt, tid, g.tact, sh);
     }
     // z2 = S~^{-1} (r_phi - Chat z1) (into zp)
     for (int j = 0; j < kt; ++j) zp[ix(j, tid, TPB)] = rp[ix(j, tid, TPB)] + cfac * ze[ix(j, tid, TPB)];
     {
       KR* rin[1] = {zp};
       KR* out[1] = {zp};
-      part_solve<1, KR, TPB, false>(F2, S2, rin, out, kt, tid, g.tact, sh);
+      part_solve<1, PR, KR, TPB, false>(F2, S2, rin, out, scr, kt, tid, g.tact, sh);
     }
     // t = Bhat z2 (tridiagonal matvec with halo), then x1 = z1 - Ahat^{-1} t
     KR* tpl = S.T(0);
     {
-      KR* hb = sh;
+      KR* hb = reinterpret_cast<KR*>(sh);
       if (kt > 0) {
         hb[tid] = zp[ix(0, tid, TPB)];
         hb[TPB + tid] = zp[ix(kt - 1, tid, TPB)];
@@ -574,16 +637,16 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const Co
         KR zc = zp[ix(j, tid, TPB)];
         KR zl = (i == 0) ? KR(0) : (j > 0 ? zp[ix(j - 1, tid, TPB)] : hb[TPB + tid - 1]);
         KR zr = (i == g.N - 1) ? KR(0) : (j + 1 < kt ? zp[ix(j + 1, tid, TPB)] : hb[tid + 1]);
-        tpl[ix(j, tid, TPB)] = Bpl[0 * S.PL + ix(j, tid, TPB)] * zl +
-                               Bpl[1 * S.PL + ix(j, tid, TPB)] * zc +
-                               Bpl[2 * S.PL + ix(j, tid, TPB)] * zr;
+        tpl[ix(j, tid, TPB)] = conv<KR>(Bpl[0 * S.PL + ix(j, tid, TPB)]) * zl +
+                               conv<KR>(Bpl[1 * S.PL + ix(j, tid, TPB)]) * zc +
+                               conv<KR>(Bpl[2 * S.PL + ix(j, tid, TPB)]) * zr;
       }
       __syncthreads();
     }
     {
       KR* rin[1] = {tpl};
       KR* out[1] = {tpl};
-      part_solve<1, KR, TPB, false>(F1, S1, rin, out, kt, tid, g.tact, sh);
+      part_solve<1, PR, KR, TPB, false>(F1, S1, rin, out, scr, kt, tid, g.tact, sh);
     }
     for (int j = 0; j < kt; ++j) ze[ix(j, tid, TPB)] = ze[ix(j, tid, TPB)] - tpl[ix(j, tid, TPB)];
   } else {
@@ -611,8 +674,8 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const Co
 // Column set-up: inputs into the slot, scaling, initial state.
 // Returns false if the column is rejected (BAD_INPUT).
 // --------------------------------------------------------------------------
-template <int TPB, typename KR>
-__device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs, const Slot<TPB, KR>& S,
+template <int TPB, typename KR, typename PR>
+__device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
                              double* halo, double* red) {
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -721,7 +784,7 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
 // --------------------------------------------------------------------------
 // The persistent solver kernel.
 // --------------------------------------------------------------------------
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ColShared cs;
@@ -735,9 +798,9 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
   double* sn_ = cs_ + m;                                    // m
   double* yv = sn_ + m;                                     // m
   double* hv = yv + m;                                      // m+2 scratch
-  KR* sh = (KR*)(hv + m + 2);                               // 12 * TPB (PCR / exchange)
+  PR* sh = (PR*)(hv + m + 2);                               // 12 * TPB (PCR / exchange)
   const int tid = threadIdx.x;
-  Slot<TPB, KR> S = make_slot<TPB, KR>(a, blockIdx.x);
+  Slot<TPB, KR, PR> S = make_slot<TPB, KR, PR>(a, blockIdx.x);
 
   for (;;) {
     if (tid == 0) {
@@ -747,7 +810,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     __syncthreads();
     if (cs.col < 0) break;
     Geo g;
-    bool ok = column_setup<TPB, KR>(a, g, cs, S, halo, red);
+    bool ok = column_setup<TPB, KR, PR>(a, g, cs, S, halo, red);
     const int64_t col = cs.col;
     if (!ok) {
       if (tid == 0) {
@@ -788,7 +851,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       }
       if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; }
       __syncthreads();
-      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
@@ -813,11 +876,11 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         tp[ix(j, tid, TPB)] = a.phi_old[gi] - pref;
       }
       __syncthreads();
-      residual<TPB, KR>(a, g, cs, S, tn, tp, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR>(a, g, cs, S, tn, tp, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
     } else {
       __syncthreads();
-      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
     }
     ++res_evals;
@@ -847,7 +910,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         }
       }
       __syncthreads();
-      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       ++res_evals;
     }
@@ -856,7 +919,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     bool bad = false;
 
     if (a.mode == MODE_PRECOND) {
-      prec_factor<TPB, KR>(a, g, cs, S, cur, sh, halo, &bad);
+      prec_factor<TPB, KR, PR>(a, g, cs, S, cur, sh, halo, &bad);
       // r (physical) -> rhat = r / S_F -> z = Mhat^{-1} rhat -> x = S_X z
       KR* re = S.W(0);
       KR* rp = S.W(1);
@@ -866,7 +929,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         rp[ix(j, tid, TPB)] = (KR)(a.r_phi[gi] * cs.isFp);
       }
       __syncthreads();
-      prec_apply<TPB, KR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
+      prec_apply<TPB, KR, PR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
         a.o1[gi] = (double)S.Z(0)[ix(j, tid, TPB)] * cs.sn;
@@ -904,7 +967,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       cur = 0;
       bad = false;
       __syncthreads();
-      residual<TPB, KR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       ++res_evals;
       fninf = scaled_inf(norms);
@@ -918,7 +981,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       if (fninf < a.p.eps_F) { status = SDCEF_STATUS_OK; break; }
       if (l >= cap) { status = SDCEF_STATUS_MAX_NEWTON; break; }
       // preconditioner at X^(l) and ||S_X^{-1} X||_2 (X = (n, phi))
-      prec_factor<TPB, KR>(a, g, cs, S, cur, sh, halo, &bad);
+      prec_factor<TPB, KR, PR>(a, g, cs, S, cur, sh, halo, &bad);
       {
         double s = 0.0;
         for (int j = 0; j < kt; ++j) {
@@ -963,12 +1026,12 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         int kdim = 0;
         for (int jj = 0; jj < m && its < a.p.max_krylov; ++jj) {
           // z_jj = Mhat^{-1} V_jj (kept), w = Jhat z_jj
-          double zz = prec_apply<TPB, KR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
+          double zz = prec_apply<TPB, KR, PR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
                                           S.ZK(jj, 1), sh, red, true);
           double zn = sqrt(zz);
           double eps = kLambdaFD * (kLambdaFD + cs.xnorm / zn);
           if (!(zn > 0.0)) eps = 1.0;
-          residual<TPB, KR>(a, g, cs, S, NP, PP, S.ZK(jj, 0), S.ZK(jj, 1), eps * cs.sn,
+          residual<TPB, KR, PR>(a, g, cs, S, NP, PP, S.ZK(jj, 0), S.ZK(jj, 1), eps * cs.sn,
                             eps * cs.sp, OUT_JVP, nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1),
                             1.0 / eps, halo, red, norms);
           ++res_evals;
@@ -1065,7 +1128,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         block_reduce<TPB>(&dd, 1, false, red);
         double zn = sqrt(dd);
         double eps = (zn > 0.0) ? kLambdaFD * (kLambdaFD + cs.xnorm / zn) : 1.0;
-        residual<TPB, KR>(a, g, cs, S, NP, PP, XHe, XHp, eps * cs.sn, eps * cs.sp, OUT_JVP,
+        residual<TPB, KR, PR>(a, g, cs, S, NP, PP, XHe, XHp, eps * cs.sn, eps * cs.sp, OUT_JVP,
                           nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1), 1.0 / eps, halo, red, norms);
         ++res_evals;
         ++its;
@@ -1096,7 +1159,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       const int nxt = 1 - cur;
       double tnorm[4];
       for (int t = 0; t <= a.p.max_ls; ++t) {
-        residual<TPB, KR>(a, g, cs, S, NP, PP, XHe, XHp, lam * cs.sn, lam * cs.sp, OUT_F,
+        residual<TPB, KR, PR>(a, g, cs, S, NP, PP, XHe, XHp, lam * cs.sn, lam * cs.sp, OUT_F,
                           S.pd(PD_FE0 + 2 * nxt), S.pd(PD_FP0 + 2 * nxt), nxt, nullptr, nullptr,
                           nullptr, nullptr, 0, halo, red, tnorm);
         ++res_evals;
@@ -1228,19 +1291,19 @@ __global__ void ion_update_kernel(IonArgs a) {
 
 #endif  // SDCEF_WITH_ORDER
 
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
-  auto k = jfnk_kernel<TPB, KR>;
+  auto k = jfnk_kernel<TPB, KR, PR>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, TPB, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int TPB, typename KR>
+template <int TPB, typename KR, typename PR>
 int occupancy_t(size_t smem) {
   int nb = 0;
-  auto k = jfnk_kernel<TPB, KR>;
+  auto k = jfnk_kernel<TPB, KR, PR>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, TPB, smem) != cudaSuccess) return 1;

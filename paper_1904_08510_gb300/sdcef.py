@@ -19,7 +19,7 @@ SUCCESS = 0
 ERR_INVALID, ERR_CUDA, ERR_CAPACITY, ERR_NOMEM = -1, -2, -3, -4
 STATUS_OK, STATUS_MAX_NEWTON, STATUS_MAX_KRYLOV, STATUS_LINESEARCH_FAIL, \
     STATUS_NONFINITE, STATUS_BAD_INPUT = range(6)
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_DF = 0, 1, 2
 PREC_EXACT, PREC_RECAST, PREC_NONE = 0, 1, 2
 BC_ABSORBING, BC_ZERO_GRADIENT = 0, 1
 MAX_RESTART = 32
