@@ -127,7 +127,7 @@ def kernel_digest():
     """Digest of the solver kernel sources (ties an ncu capture to the code it measured)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("solver.cuh", "blockalg.cuh", "kern_inst.cu"):
+    for f in ("solver.cuh", "blockalg.cuh", "dfloat.cuh", "kern_inst.cu"):
         with open(os.path.join(ROOT, "paper_1904_08510_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
