@@ -151,8 +151,10 @@ def ncu_traffic(ncells, tpc):
 def algorithmic_model(lengths, newton, krylov, res_evals, precond, kr_bytes):
     """Algorithmic FP64 flops and streaming-model bytes of the solve (per batch).
 
-    Per cell: a residual evaluation ~ 40 FP64 flops + one expm1 and one
-    reciprocal per face (counted as 50 + 16 flop-equivalents); a block
+    Per cell: a residual evaluation ~ 40 FP64 flops + one e^x - 1 and one
+    reciprocal per face (counted as 26 + 9 flop-equivalents: 13 and ~4.5
+    FMA-class operations), 75 in all, inside the 60-80 per cell per residual
+    of the path's scope analysis; a block
     factorisation ~ 120 flops per Newton step; a preconditioner application
     ~ 40 flops (exact form) or 30 (recast); Arnoldi CGS2 with a basis of p
     vectors ~ 8 (p+1) flops per iteration. Streaming-model bytes per cell
@@ -166,7 +168,7 @@ def algorithmic_model(lengths, newton, krylov, res_evals, precond, kr_bytes):
     it_per = np.where(nw > 0, kr / np.maximum(nw, 1), 0.0)
     p_mean = 0.5 * it_per + 1.0
     pa = 40.0 if precond == "exact" else 30.0
-    flop_cell = res * 106.0 + nw * 120.0 + (kr + nw) * 2 * pa + kr * 8.0 * (p_mean + 1) * 2
+    flop_cell = res * 75.0 + nw * 120.0 + (kr + nw) * 2 * pa + kr * 8.0 * (p_mean + 1) * 2
     s = float(kr_bytes)
     byte_cell = 56.0 + res * 56.0 + nw * (40 + 18 * s) + kr * (40 + 19 * s + 4 * s * (p_mean + 1)) + 48 * nw
     return float(np.sum(flop_cell * N)), float(np.sum(byte_cell * N))
@@ -478,11 +480,9 @@ def extras(args, S, b, db, solver, params, dev):
         tg, _ = _timed(lambda: mlp.guess(db4, ne_g, ph_g, components=S.GUESS_NE))
         res["config4_learned_guess"] = {
             "columns": b4.ncol, "cells": "512-2048",
-            "plain": {"value": b4.ncol / tp, "newton_mean": float(op["newton_it"].float().mean().item()),
-                      "krylov_mean": float(op["krylov_it"].float().mean().item()),
+            "plain": {"value": b4.ncol / tp, **_iterations(op),
                       "status_ok": int((op["status"] == 0).sum().item())},
-            "learned": {"value": b4.ncol / tl, "newton_mean": float(ol["newton_it"].float().mean().item()),
-                        "krylov_mean": float(ol["krylov_it"].float().mean().item()),
+            "learned": {"value": b4.ncol / tl, **_iterations(ol),
                         "status_ok": int((ol["status"] == 0).sum().item()),
                         "guess_kernel_ms": 1e3 * tg},
             "unit": "column-solves/s", "components": "n_e increment"}
@@ -508,8 +508,52 @@ def extras(args, S, b, db, solver, params, dev):
         "column_solves_per_s_graph": 4 * sb.ncol / tg,
         "status_ok_last_iteration": int((sst == 0).sum()),
         "newton_mean_last_iteration": float(sout["newton_it"].float().mean().item())}
+    # the same sweep with the double-float preconditioner and the learned Newton
+    # start of the first SDC iteration: guess kernel + 4 solves in one CUDA graph
+    if os.path.exists(Lrn.WEIGHTS):
+        pdf = S.default_params(precision=S.MIXED_DF, restart_m=8,
+                               threads_per_column=params.threads_per_column)
+        dsolver = S.Solver(pdf, max_cols=sb.ncol, max_cells=sb.ncells, max_col_cells=1024, stream=st_)
+        mlp5 = S.MLP(sb.ncells, stream=st_)
+        mlp5.set_params(Lrn.load())
+        g_ne = torch.empty(sb.ncells, dtype=torch.float64, device=dev)
+        g_ph = torch.empty_like(g_ne)
+        gdb = sdb.with_guess(g_ne, g_ph)
+        dout = dsolver.alloc_result(sdb)
+
+        def mixed_learned():
+            mlp5.guess(sdb, g_ne, g_ph, components=S.GUESS_NE)
+            return dsolver.sdc_sweep(gdb, 4, work=work, out=dout)
+        with torch.cuda.stream(st_):
+            tme, _ = _timed(mixed_learned, reps=2)
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2, stream=st_):
+                mixed_learned()
+            tmg, _ = _timed(lambda: g2.replay(), reps=2)
+        okc = ((sout["status"] == 0) & (dout["status"] == 0)).cpu().numpy()
+        en = _colerr(sb, dout["ne"].cpu().numpy(), sout["ne"].cpu().numpy())[okc]
+        ep = _colerr(sb, dout["phi"].cpu().numpy(), sout["phi"].cpu().numpy())[okc]
+        res["config5_sdc_sweep_mixed_df_learned"] = {
+            "ms_per_sweep_eager": 1e3 * tme, "ms_per_sweep_graph": 1e3 * tmg,
+            "column_solves_per_s_graph": 4 * sb.ncol / tmg, "speedup_vs_fp64_graph": tg / tmg,
+            "status_ok_last_iteration": int((dout["status"] == 0).sum().item()),
+            "newton_mean_last_iteration": float(dout["newton_it"].float().mean().item()),
+            "err_vs_fp64_sweep_ne": {"max": float(en.max()), "median": float(np.median(en))},
+            "err_vs_fp64_sweep_phi": {"max": float(ep.max()), "median": float(np.median(ep))}}
+        mlp5.close()
+        dsolver.close()
     ssolver.close()
     return res
+
+
+def _iterations(o):
+    """Mean, median and 99th percentile of the Newton and GMRES iteration counts."""
+    out = {}
+    for k, name in (("newton_it", "newton"), ("krylov_it", "krylov")):
+        v = o[k].float().cpu().numpy()
+        out.update({f"{name}_mean": float(v.mean()), f"{name}_p50": float(np.median(v)),
+                    f"{name}_p99": float(np.percentile(v, 99))})
+    return out
 
 
 class _HostView:

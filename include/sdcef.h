@@ -185,6 +185,14 @@ int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef
 int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* ne,
                          const double* phi, double* F_e, double* F_phi);
 
+/* The Bernoulli function of the Scharfetter-Gummel electron flux (Sec. 3.1),
+ * B(x) = x / (e^x - 1), and its derivative B'(x), evaluated exactly as the
+ * residual kernel evaluates them (series for |x| < 1e-3, otherwise a
+ * table-driven e^|x| - 1 and B(-a) = a + B(a)). x, b, db: device arrays of n
+ * doubles; b and db are written. Enqueued on the context stream. Returns
+ * SDCEF_ERR_INVALID for NULL arrays or n < 0. */
+int sdcef_bernoulli_batch(sdcef_ctx* ctx, const double* x, double* b, double* db, int64_t n);
+
 /* Apply the configured preconditioner, built at X = (ne, phi), to the
  * residual-space vector (r_e, r_phi) in physical (unscaled) units:
  * x = P^-1 r with P^-1 from Eq. prec (SDCEF_PREC_EXACT: x = J^-1 r) or

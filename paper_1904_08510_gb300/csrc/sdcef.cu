@@ -328,6 +328,15 @@ int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out
   return SDCEF_SUCCESS;
 }
 
+int sdcef_bernoulli_batch(sdcef_ctx* ctx, const double* x, double* b, double* db, int64_t n) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  if (n < 0 || (n > 0 && (!x || !b || !db))) return set_err(SDCEF_ERR_INVALID, "bernoulli: bad arguments");
+  if (n == 0) return SDCEF_SUCCESS;
+  cudaError_t e = launch_bernoulli(x, b, db, n, ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  return SDCEF_SUCCESS;
+}
+
 int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* phi,
                            double kappa_ion, double* n_ion_out) {
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");

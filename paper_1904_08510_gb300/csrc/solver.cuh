@@ -10,6 +10,7 @@
 
 #include "../../include/sdcef.h"
 #include "blockalg.cuh"
+#include "expm1_table.cuh"
 
 namespace sdcef_impl {
 using namespace sdcef;
@@ -61,7 +62,9 @@ struct KArgs {
 
 // FP64 planes of a slot
 enum {
-  PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_HD, PD_UF, PD_PREF,
+  // PD_MUHD: mu h / D_f per face; PD_PE0: (u_f + mu g0) h / D_f, the face Peclet number
+  // at dpsi/dx = 0, so that Pe = PD_PE0 + PD_MUHD dpsi/dx is one FMA
+  PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_MUHD, PD_PE0, PD_PREF,
   PD_FACE0,               // 4 planes: face derivative set 0 (a0, a1, b0, b1), scaled
   PD_FACE1 = PD_FACE0 + 4,
   PD_COUNT = PD_FACE1 + 4
@@ -157,6 +160,8 @@ struct IonArgs {
   double kappa;
 };
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st);
+// B(x) and B'(x) of the Scharfetter-Gummel flux, as the residual evaluates them.
+cudaError_t launch_bernoulli(const double* x, double* b, double* db, int64_t n, cudaStream_t st);
 
 #ifdef SDCEF_KERNEL_TU
 // --------------------------------------------------------------------------
@@ -200,16 +205,51 @@ __device__ __forceinline__ void block_reduce(double* v, int nv, bool is_max, dou
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 constexpr long long kBits1em3 = 0x3F50624DD2F1A9FCLL;   // bit pattern of 1e-3
 
+// e^a - 1 for a >= 1e-3 (+inf for a >= 709 and for NaN), FP64, after the
+// table-driven method of P. T. P. Tang (ACM TOMS 15, 1989, for exp; ACM TOMS
+// 18, 1992, for expm1):
+//   k = round(64 a / ln 2) = 64 M + j,  r = a - k ln2/64 (|r| <= ln2/128),
+//   e^a = 2^M 2^(j/64) e^r,  e^r - 1 = p(r) = r + r^2 (1/2 + r/6 + r^2/24
+//   + r^3/120 + r^4/720)  (Taylor; truncation below 3e-20 on |r| <= ln2/128),
+//   e^a - 1 = (2^M T_hi - 1) + 2^M (T_lo + T_hi p),  2^(j/64) = T_hi + T_lo.
+// k comes from the shifter trick (a * 64/ln2 + 1.5 2^52 rounds to an integer
+// held in the low bits) and 2^M from the exponent bits, so the whole
+// evaluation is 13 FP64 operations (CUDA's expm1 measured ~18 FP64-pipe
+// instructions). Error below 1.4 ulp over [1e-3, 709] against a long-double
+// reference; for a in [709, inf) the Bernoulli function underflows
+// (a / (e^a - 1) < 1e-305) and +inf gives B = 0.
+__device__ __forceinline__ double expm1_pos(double a) {
+  constexpr long long kBits709 = 0x4086280000000000LL;   // bit pattern of 709.0
+  if (dbits(a) >= kBits709) return __longlong_as_double(0x7FF0000000000000LL);
+  constexpr double kShift = 0x1.8p52;
+  const double t = fma(a, kExpInvL, kShift);
+  const int k = __double2loint(t);
+  const double kd = t - kShift;
+  double r = fma(-kd, kExpL1, a);
+  r = fma(-kd, kExpL2, r);
+  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(r * r, q, r);
+  const double2 T = __ldg(&kExp2Tab[k & 63]);
+  const double u = fma(T.x, p, T.y);
+  const double s = __longlong_as_double((long long)((k >> 6) + 1023) << 52);
+  return fma(s, u, fma(s, T.x, -1.0));
+}
+
+// DERIV = false skips B'(a): the finite-difference JVP needs fluxes only.
+template <bool DERIV>
 __device__ __forceinline__ void bern_pos(double a, double* b, double* db) {
   if (dbits(a) < kBits1em3) {
     double a2 = a * a;
     *b = 1.0 - 0.5 * a + a2 * (1.0 / 12.0) - a2 * a2 * (1.0 / 720.0);
-    *db = -0.5 + a * (1.0 / 6.0) - a * a2 * (1.0 / 180.0);
+    if (DERIV) *db = -0.5 + a * (1.0 / 6.0) - a * a2 * (1.0 / 180.0);
   } else {
-    double E = expm1(a);
+    double E = expm1_pos(a);
     double iE = 1.0 / E;
     *b = a * iE;
-    *db = (1.0 - a - *b) * iE;
+    if (DERIV) *db = (1.0 - a - *b) * iE;
   }
 }
 
@@ -294,8 +334,8 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
   const double* FEX = S.pd(PD_FEX);
   const double* FPHI = S.pd(PD_FPHI);
   const double* DH = S.pd(PD_DH);
-  const double* HD = S.pd(PD_HD);
-  const double* UF = a.u ? S.pd(PD_UF) : nullptr;
+  const double* MUHD = S.pd(PD_MUHD);
+  const double* PE0 = S.pd(PD_PE0);
   double* face = S.pd(PD_FACE0 + 4 * fs);
   auto st_n = [&](int j) {
     double v = nb[ix(j, tid, TPB)];
@@ -340,16 +380,17 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         n_n = (j + 1 < kt) ? st_n(j + 1) : halo[0 * TPB + tid + 1];
         p_n = (j + 1 < kt) ? st_p(j + 1) : halo[1 * TPB + tid + 1];
         dd = (p_n - p_i) * ih;
-        double v = (UF ? UF[ix(j, tid, TPB)] : 0.0) + mu * (g0 + dd);
-        double Pe = v * HD[ix(j, tid, TPB)];
-        double aa = fabs(Pe), b, db;
-        bern_pos(aa, &b, &db);
-        double Bp, Bm, dBp, dBm;   // B(Pe), B(-Pe) and derivatives
-        if (dbits(Pe) >= 0) { Bp = b; Bm = aa + b; dBp = db; dBm = -1.0 - db; }   // sign bit clear
-        else { Bm = b; Bp = aa + b; dBm = db; dBp = -1.0 - db; }
+        // Pe = (u_f + mu (g0 + dpsi/dx)) h / D_f
+        const double Pe = fma(MUHD[ix(j, tid, TPB)], dd, PE0[ix(j, tid, TPB)]);
+        double aa = fabs(Pe), b, db = 0.0;
+        if (out_mode == OUT_F) bern_pos<true>(aa, &b, &db);   // CTA-uniform branch
+        else bern_pos<false>(aa, &b, &db);
+        const bool pos = dbits(Pe) >= 0;   // sign bit clear
+        const double Bp = pos ? b : aa + b, Bm = pos ? aa + b : b;   // B(Pe), B(-Pe)
         const double dh = DH[ix(j, tid, TPB)];
         gam = dh * (Bm * n_i - Bp * n_n);
         if (out_mode == OUT_F) {
+          const double dBp = pos ? db : -1.0 - db, dBm = pos ? -1.0 - db : db;
           // r dGam/dn_i, r dGam/dn_{i+1}, r dGam/dpsi_i, r dGam/dpsi_{i+1} (unscaled)
           double dg_n0 = dh * Bm, dg_n1 = -dh * Bp;
           double dg_p1 = mu * ih * (-dBm * n_i - dBp * n_n);
@@ -716,8 +757,8 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
   double* FEX = S.pd(PD_FEX);
   double* FPHI = S.pd(PD_FPHI);
   double* DH = S.pd(PD_DH);
-  double* HD = S.pd(PD_HD);
-  double* UF = S.pd(PD_UF);
+  double* MUHD = S.pd(PD_MUHD);
+  double* UF = S.pd(PD_PE0);   // cell velocities first, then the face Peclet offsets
   const double mu = a.p.mu;
   int bad = 0;
   double m_n = 0.0, m_fphi = 0.0, m_phi = 0.0, m_fe = 0.0;
@@ -758,12 +799,15 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
     if (i < g.N - 1) {
       double Dn = (j + 1 < g.kt) ? DH[ix(j + 1, tid, TPB)] : halo[tid + 1];
       double Df = 0.5 * (DH[ix(j, tid, TPB)] + Dn);
+      double uf = 0.0;
       if (a.u) {
         double un = (j + 1 < g.kt) ? UF[ix(j + 1, tid, TPB)] : halo[TPB + tid + 1];
-        UF[ix(j, tid, TPB)] = 0.5 * (UF[ix(j, tid, TPB)] + un);
+        uf = 0.5 * (UF[ix(j, tid, TPB)] + un);
       }
+      const double hd = cs.h / Df;
       DH[ix(j, tid, TPB)] = Df * cs.inv_h;
-      HD[ix(j, tid, TPB)] = cs.h / Df;
+      MUHD[ix(j, tid, TPB)] = mu * hd;
+      UF[ix(j, tid, TPB)] = (uf + mu * cs.g0) * hd;
     }
   }
   if (tid == 0) cs.ubl = a.u ? a.u[off] : 0.0;
@@ -1111,6 +1155,8 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           }
         }
         __syncthreads();
+        // ||delta-hat||^2 is needed only by a restart (its FD epsilon)
+        const bool restart = !(converged || its >= a.p.max_krylov);
         double dd = 0.0;
         for (int j = 0; j < kt; ++j) {
           double xe = XHe[ix(j, tid, TPB)], xp = XHp[ix(j, tid, TPB)];
@@ -1120,10 +1166,10 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           }
           XHe[ix(j, tid, TPB)] = (KR)xe;
           XHp[ix(j, tid, TPB)] = (KR)xp;
-          dd += xe * xe + xp * xp;
+          if (restart) dd += xe * xe + xp * xp;
         }
         __syncthreads();
-        if (converged || its >= a.p.max_krylov) break;
+        if (!restart) break;
         // restart: r = -Fhat - Jhat delta-hat
         block_reduce<TPB>(&dd, 1, false, red);
         double zn = sqrt(dd);
@@ -1180,7 +1226,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         double dn = (double)XHe[ix(j, tid, TPB)], dp = (double)XHp[ix(j, tid, TPB)];
         NP[ix(j, tid, TPB)] = fma(lam * cs.sn, dn, NP[ix(j, tid, TPB)]);
         PP[ix(j, tid, TPB)] = fma(lam * cs.sp, dp, PP[ix(j, tid, TPB)]);
-        smax = fmax(smax, fmax(fabs(dn), fabs(dp)));
+        if (a.p.eps_X > 0.0) smax = fmax(smax, fmax(fabs(dn), fabs(dp)));
       }
       cur = nxt;
       fninf = scaled_inf(tnorm);
@@ -1286,6 +1332,20 @@ __global__ void ion_update_kernel(IonArgs a) {
       }
       no[i] = ni[i] - r * (fr - fl);
     }
+  }
+}
+
+// B(x) = x / (e^x - 1) and B'(x) for any sign of x, through bern_pos and
+// B(-a) = a + B(a), B'(-a) = -1 - B'(a), exactly as the residual forms them.
+__global__ void bernoulli_kernel(const double* x, double* b, double* db, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i], aa = fabs(v);
+    double bp, dbp;
+    bern_pos<true>(aa, &bp, &dbp);
+    const bool pos = dbits(v) >= 0;
+    b[i] = pos ? bp : aa + bp;
+    db[i] = pos ? dbp : -1.0 - dbp;
   }
 }
 

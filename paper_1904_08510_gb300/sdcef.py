@@ -30,7 +30,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_solve_batch", "sdcef_solve_batch_host", "sdcef_residual_batch",
            "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count",
            "sdcef_solve_batch_noalloc", "sdcef_ion_update_batch", "sdcef_sdc_sweep",
-           "sdcef_autotune",
+           "sdcef_autotune", "sdcef_bernoulli_batch",
            "sdcef_mlp_create", "sdcef_mlp_destroy",
            "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
@@ -89,6 +89,8 @@ def lib():
         L.sdcef_solve_batch.argtypes = [vp, B, R]
         L.sdcef_solve_batch_host.argtypes = [vp, B, R]
         L.sdcef_residual_batch.argtypes = [vp, B, vp, vp, vp, vp]
+        L.sdcef_bernoulli_batch.argtypes = [vp, vp, vp, vp, C.c_int64]
+        L.sdcef_bernoulli_batch.restype = C.c_int
         L.sdcef_precond_apply_batch.argtypes = [vp, B, vp, vp, vp, vp, vp, vp]
         L.sdcef_last_error.restype = C.c_char_p
         L.sdcef_last_error.argtypes = []
@@ -312,6 +314,15 @@ class Solver:
         _check(lib().sdcef_residual_batch(self.h, C.byref(bs), _ptr(ne), _ptr(phi), _ptr(Fe),
                                           _ptr(Fp)))
         return Fe, Fp
+
+    def bernoulli(self, x):
+        """sdcef_bernoulli_batch: B(x) = x / (e^x - 1) and B'(x) as the residual
+        kernel evaluates them (x: FP64 device tensor)."""
+        import torch
+        b = torch.empty_like(x)
+        db = torch.empty_like(x)
+        _check(lib().sdcef_bernoulli_batch(self.h, _ptr(x), _ptr(b), _ptr(db), int(x.numel())))
+        return b, db
 
     def precond_apply(self, db: DeviceBatch, ne, phi, r_e, r_phi):
         import torch
