@@ -190,9 +190,16 @@ def cpu_baseline(batch, seconds, precond):
     t0 = time.perf_counter()
     r = O.solve(sub, P, threads=threads)
     el = time.perf_counter() - t0
+    # one core: a prefix sized to about 2 s from the all-core rate
+    m1 = int(min(m, max(min(m, 8), 2.0 * m / (el * threads))))
+    t0 = time.perf_counter()
+    O.solve(batch.subset(range(m1)), P, threads=1)
+    el1 = time.perf_counter() - t0
     return {"value": m / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "value_1core": m1 / el1,
             "sample": f"first {m} of {batch.ncol} columns ({int(sub.ncells)} cells), "
-                      f"{el:.1f} s on {threads} threads, status OK {int((r['status'] == 0).sum())}/{m}"}
+                      f"{el:.1f} s on {threads} threads, status OK {int((r['status'] == 0).sum())}/{m}; "
+                      f"1 core: first {m1} columns, {el1:.2f} s"}
 
 
 def run_reference(args):

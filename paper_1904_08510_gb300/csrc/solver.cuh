@@ -269,6 +269,8 @@ struct ColShared {
   double gam, beta0;
   int conv, stop;
   double scal[8];
+  double pref0, dpref;                  // phi_ref at cell i: pref0 + dpref * i
+  double vald[SDCEF_MAX_SPECIES];       // ion valences as doubles
 };
 
 struct Geo {
@@ -739,6 +741,9 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
     cs.vl = vl;
     cs.vr = vr;
     cs.g0 = (vr - vl) / (Ni * cs.h);
+    cs.dpref = (vr - vl) / Ni;
+    cs.pref0 = fma(0.5, cs.dpref, vl);
+    for (int sp = 0; sp < a.nsp; ++sp) cs.vald[sp] = (double)a.val[sp];
     cs.bad = bad;
     cs.N = bad ? 0 : Ni;
   }
@@ -760,38 +765,42 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
   double* MUHD = S.pd(PD_MUHD);
   double* UF = S.pd(PD_PE0);   // cell velocities first, then the face Peclet offsets
   const double mu = a.p.mu;
+  // finiteness tests and maxima of |x| on the bit patterns (integer pipe):
+  // |x| orders like its bit pattern, and NaN/Inf have the all-ones exponent
+  constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL, kExp = 0x7FF0000000000000LL;
+  auto nonfinite = [&](double x) { return (dbits(x) & kExp) == kExp; };
   int bad = 0;
-  double m_n = 0.0, m_fphi = 0.0, m_phi = 0.0, m_fe = 0.0;
+  long long m_n = 0, m_fphi = 0, m_phi = 0, m_fe = 0;
   // D at this thread's first cell, for the neighbour's last face
   for (int j = 0; j < g.kt; ++j) {
     const int64_t gi = off + g.t0 + j;
     double T = a.T[gi];
-    if (!(T > 0.0) || !isfinite(T)) bad = 1;
+    if (dbits(T) <= 0 || nonfinite(T)) bad = 1;   // T <= 0 (incl. -0), NaN or Inf
     double D = mu * (kKb / kQe) * T;
     if (j == 0) halo[tid] = D;
     if (a.u && j == 0) halo[TPB + tid] = a.u[gi];
     double neo = a.ne_old[gi], pho = a.phi_old[gi];
     double fe = neo + (a.ire ? cs.dt * a.ire[gi] : 0.0);
     double q = 0.0;
-    for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * ncell_tot + gi];
+    for (int s = 0; s < a.nsp; ++s) q = fma(cs.vald[s], a.n_ion[(int64_t)s * ncell_tot + gi], q);
     double n0 = a.ne_g ? a.ne_g[gi] : neo;
     double p0 = a.phi_g ? a.phi_g[gi] : pho;
-    if (!isfinite(neo) || !isfinite(pho) || !isfinite(fe) || !isfinite(q) || !isfinite(n0) ||
-        !isfinite(p0))
+    if (nonfinite(neo) || nonfinite(pho) || nonfinite(fe) || nonfinite(q) || nonfinite(n0) ||
+        nonfinite(p0))
       bad = 1;
     FEX[ix(j, tid, TPB)] = fe;
     FPHI[ix(j, tid, TPB)] = q;
-    const double pref = cs.vl + (cs.vr - cs.vl) * (g.t0 + j + 0.5) / g.N;
+    const double pref = fma(cs.dpref, (double)(g.t0 + j), cs.pref0);
     S.pd(PD_PREF)[ix(j, tid, TPB)] = pref;
     NP[ix(j, tid, TPB)] = n0;
     PP[ix(j, tid, TPB)] = p0 - pref;
     // face D (right face) stored temporarily as D_i; fixed below
     DH[ix(j, tid, TPB)] = D;
     if (a.u) UF[ix(j, tid, TPB)] = a.u[gi];
-    m_n = fmax(m_n, fabs(neo));
-    m_fphi = fmax(m_fphi, fabs(q));
-    m_phi = fmax(m_phi, fabs(pho));
-    m_fe = fmax(m_fe, fabs(fe));
+    m_n = max(m_n, dbits(neo) & kAbs);
+    m_fphi = max(m_fphi, dbits(q) & kAbs);
+    m_phi = max(m_phi, dbits(pho) & kAbs);
+    m_fe = max(m_fe, dbits(fe) & kAbs);
   }
   __syncthreads();
   for (int j = 0; j < g.kt; ++j) {
@@ -812,7 +821,8 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
   }
   if (tid == 0) cs.ubl = a.u ? a.u[off] : 0.0;
   if (g.kt > 0 && g.t0 + g.kt == g.N) cs.ubr = a.u ? a.u[off + g.N - 1] : 0.0;
-  double mx[5] = {m_n, m_fphi, m_phi, m_fe, (double)bad};
+  double mx[5] = {__longlong_as_double(m_n), __longlong_as_double(m_fphi), __longlong_as_double(m_phi),
+                  __longlong_as_double(m_fe), (double)bad};
   block_reduce<TPB>(mx, 5, true, red);
   if (mx[4] != 0.0) return false;
   if (tid == 0) {

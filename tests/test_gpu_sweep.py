@@ -38,11 +38,15 @@ def test_ion_update_matches_oracle():
     np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("precond", [S.PREC_EXACT, S.PREC_RECAST])
-def test_sdc_sweep_matches_oracle(precond):
+@pytest.mark.parametrize("precond,precision", [(S.PREC_EXACT, S.FP64), (S.PREC_RECAST, S.FP64),
+                                               (S.PREC_EXACT, S.MIXED_DF)])
+def test_sdc_sweep_matches_oracle(precond, precision):
+    """Every SDC iteration's solve at the FP64 bar; the double-float
+    preconditioner mode reaches the same roots."""
     d = dev()
     b = sdc_batch(12, 777, n_cells=256)
-    P = S.default_params(eps_F=1e-12, precond=precond, restart_m=30 if precond == S.PREC_RECAST else 8)
+    P = S.default_params(eps_F=1e-12, precond=precond, precision=precision,
+                         restart_m=30 if precond == S.PREC_RECAST else 8)
     s = S.Solver(P, max_cols=b.ncol, max_cells=b.ncells, max_col_cells=256)
     db = S.DeviceBatch.from_host(b, d)
     out = s.sdc_sweep(db, k_max=4)
@@ -54,10 +58,12 @@ def test_sdc_sweep_matches_oracle(precond):
     assert colerr(b, out["phi"].cpu().numpy(), phi_r).max() <= 1e-9
 
 
-def test_sdc_sweep_graph_replay_matches_eager():
+@pytest.mark.parametrize("precision", [S.FP64, S.MIXED_DF])
+def test_sdc_sweep_graph_replay_matches_eager(precision):
     d = dev()
     b = sdc_batch(64, 31, n_cells=512)
-    s = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells, max_col_cells=512)
+    s = S.Solver(S.default_params(precision=precision), max_cols=b.ncol, max_cells=b.ncells,
+                 max_col_cells=512)
     db = S.DeviceBatch.from_host(b, d)
     eager = s.sdc_sweep(db, k_max=4)
     torch.cuda.synchronize()
@@ -65,8 +71,8 @@ def test_sdc_sweep_graph_replay_matches_eager():
     out = s.alloc_result(db)
     work = torch.empty_like(db.tensors["n_ion"])
     stream = torch.cuda.Stream()
-    s2 = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells, max_col_cells=512,
-                  stream=stream)
+    s2 = S.Solver(S.default_params(precision=precision), max_cols=b.ncol, max_cells=b.ncells,
+                  max_col_cells=512, stream=stream)
     s2.sdc_sweep(db, k_max=4, work=work, out=out)     # first call outside capture
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
