@@ -270,6 +270,8 @@ struct ColShared {
   int conv, stop;
   double scal[8];
   double pref0, dpref;                  // phi_ref at cell i: pref0 + dpref * i
+  // scaled Poisson stencil of the Jacobian rows: kap/h^2 s_phi/s_Fphi and multiples
+  double kh2, m2kh2, m4kh2, kh2_43;
   double vald[SDCEF_MAX_SPECIES];       // ion valences as doubles
 };
 
@@ -503,8 +505,6 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   const double* face = S.pd(PD_FACE0 + 4 * fs);
   const int i = g.t0 + j, N = g.N;
   const double ih = cs.inv_h, r = cs.dt * ih, mu = a.p.mu;
-  const double sl = cs.r_l;
-  const double kh2 = a.p.kap * ih * ih * sl;
   RowJ R;
   R.As = R.Au = R.Bs = R.Bu = 0.0;
   const double sa = cs.r_a, sb = cs.r_b;
@@ -542,16 +542,16 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   // Poisson stencil with the second-order electrode closure
   if (i == 0) {
     R.Ls = 0.0;
-    R.Ld = -4.0 * kh2;
-    R.Lu = (4.0 / 3.0) * kh2;
+    R.Ld = cs.m4kh2;
+    R.Lu = cs.kh2_43;
   } else if (i == N - 1) {
-    R.Ls = (4.0 / 3.0) * kh2;
-    R.Ld = -4.0 * kh2;
+    R.Ls = cs.kh2_43;
+    R.Ld = cs.m4kh2;
     R.Lu = 0.0;
   } else {
-    R.Ls = kh2;
-    R.Ld = -2.0 * kh2;
-    R.Lu = kh2;
+    R.Ls = cs.kh2;
+    R.Ld = cs.m2kh2;
+    R.Lu = cs.kh2;
   }
   return R;
 }
@@ -953,6 +953,10 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       cs.r_c = cs.sn / cs.sFp;
       cs.r_l = cs.sp / cs.sFp;
       cs.r_rho = cs.sFe / cs.sFp;
+      cs.kh2 = a.p.kap * cs.inv_h * cs.inv_h * cs.r_l;
+      cs.m2kh2 = -2.0 * cs.kh2;
+      cs.m4kh2 = -4.0 * cs.kh2;
+      cs.kh2_43 = (4.0 / 3.0) * cs.kh2;
     }
     if (start_differs) {
       if (a.mode == MODE_PRECOND) {
