@@ -471,6 +471,38 @@ def extras(args, S, b, db, solver, params, dev):
             "err_vs_fp64_ne": {"max": float(en.max()), "median": float(np.median(en))},
             "err_vs_fp64_phi": {"max": float(ep.max()), "median": float(np.median(ep))}}
         sdf.close()
+    # learned Newton start on the headline workload, with the network trained on
+    # the same (ragged) profile family from disjoint seeds; timed including the
+    # guess kernel, plain FP64 and with the double-float preconditioner
+    if args.precision == "fp64" and os.path.exists(Lrn.WEIGHTS_RAGGED):
+        mlp = S.MLP(b.ncells)
+        mlp.set_params(Lrn.load(Lrn.WEIGHTS_RAGGED))
+        ne_g = torch.empty(b.ncells, dtype=torch.float64, device=dev)
+        ph_g = torch.empty_like(ne_g)
+        gdb = db.with_guess(ne_g, ph_g)
+        o_ref = solver.solve(db)
+        legs = {}
+        for name, prec in (("headline_workload_learned", S.FP64),
+                           ("headline_workload_mixed_df_learned", S.MIXED_DF)):
+            sl = S.Solver(S.default_params(precision=prec, precond=params.precond, restart_m=8,
+                                           threads_per_column=params.threads_per_column),
+                          max_cols=b.ncol, max_cells=b.ncells, max_col_cells=int(b.lengths().max()))
+            ol_ = sl.alloc_result(db)
+
+            def learned(sl=sl, ol_=ol_):
+                mlp.guess(db, ne_g, ph_g, components=S.GUESS_NE)
+                return sl.solve(gdb, ol_)
+            tl, ol = _timed(learned)
+            okc = ((o_ref["status"] == 0) & (ol["status"] == 0)).cpu().numpy()
+            en = _colerr(b, ol["ne"].cpu().numpy(), o_ref["ne"].cpu().numpy())[okc]
+            ep = _colerr(b, ol["phi"].cpu().numpy(), o_ref["phi"].cpu().numpy())[okc]
+            res[name] = {"value": b.ncol / tl, "unit": "column-solves/s",
+                         "status_ok": int((ol["status"] == 0).sum().item()), **_iterations(ol),
+                         "err_vs_plain_fp64_ne": {"max": float(en.max()), "median": float(np.median(en))},
+                         "err_vs_plain_fp64_phi": {"max": float(ep.max()), "median": float(np.median(ep))}}
+            sl.close()
+        res["headline_workload_plain_iterations"] = _iterations(o_ref)
+        mlp.close()
     # config 4: learned initial guess on held-out columns (512-2048 cells)
     if os.path.exists(Lrn.WEIGHTS):
         b4 = make_batch("single", 4096, 2_000_000, n_range=(512, 2048))

@@ -1,9 +1,10 @@
 """Training and evaluation of the learned Newton initial guess.
 
-Data: converged solves of seeded single-flame columns (the profile family of
-workload.make_batch(kind="single"); a fixed cell count or cell counts drawn
-uniformly from a range, --train-cells), solved by the batched FP64 JFNK on the
-GPU; features and targets are produced by the library's own kernels
+Data: converged solves of seeded columns of one profile family (--family):
+the single-flame family of workload.make_batch(kind="single") with a fixed cell
+count or cell counts drawn uniformly from a range (--train-cells), or the ragged
+family of the benchmark workload (kind="ragged", training seeds disjoint from
+the benchmark's), solved by the batched FP64 JFNK on the GPU; features and targets are produced by the library's own kernels
 (sdcef_mlp_features / sdcef_mlp_targets). Training runs the library's BF16
 forward/backward kernels and its Adam step. Evaluation solves held-out columns
 with and without the guess and compares Newton and GMRES iteration counts.
@@ -19,7 +20,8 @@ from . import sdcef as S
 from .workload import make_batch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-WEIGHTS = os.path.join(HERE, "data", "mlp_weights.npz")
+WEIGHTS = os.path.join(HERE, "data", "mlp_weights.npz")                 # single-flame family
+WEIGHTS_RAGGED = os.path.join(HERE, "data", "mlp_weights_ragged.npz")   # ragged (bench) family
 
 
 def init_params(seed=0):
@@ -35,16 +37,22 @@ def init_params(seed=0):
     return S.pack_params(p).astype(np.float32)
 
 
-def generate(ncol: int, seed: int, *, n_cells=256, n_range=None, chunk=8192, device="cuda:0",
-             eps_F=1e-10):
-    """Solve ncol seeded columns on the GPU; return (features bf16 [cells,32],
-    targets f32 [cells,2]) device tensors and the solve statistics."""
+def generate(ncol: int, seed: int, *, kind="single", n_cells=256, n_range=None, chunk=8192,
+             device="cuda:0", eps_F=1e-10):
+    """Solve ncol seeded columns of profile family `kind` on the GPU; return
+    (features bf16 [cells,32], targets f32 [cells,2]) device tensors and the
+    number of converged solves. For kind="ragged" the cell counts follow the
+    family's own draw unless n_range is given."""
     import torch
     Xs, Ts, stats = [], [], []
     mlp = S.MLP(1, )
     for c0 in range(0, ncol, chunk):
         n = min(chunk, ncol - c0)
-        b = make_batch("single", n, seed + c0, n_cells=None if n_range else n_cells, n_range=n_range)
+        if kind == "ragged":
+            b = make_batch("ragged", n, seed + c0, n_range=n_range)
+        else:
+            b = make_batch("single", n, seed + c0, n_cells=None if n_range else n_cells,
+                           n_range=n_range)
         db = S.DeviceBatch.from_host(b, device)
         solver = S.Solver(S.default_params(eps_F=eps_F), max_cols=n, max_cells=b.ncells,
                           max_col_cells=int(b.lengths().max()))
@@ -84,13 +92,13 @@ def train(X, T, *, steps: int, batch: int = 32768, lr: float = 2e-3, lr_end: flo
     return mlp, hist
 
 
-def evaluate(params, ncol: int, seed: int, *, n_range=(512, 2048), device="cuda:0", reps=3,
-             variants=(("learned", 1),)):
+def evaluate(params, ncol: int, seed: int, *, kind="single", n_range=(512, 2048), device="cuda:0",
+             reps=3, variants=(("learned", 1),)):
     """Held-out solves with and without the learned guess (FP64 batched JFNK).
     variants: (name, components) pairs; components = 1 applies the predicted
     n_e increment only, 3 applies n_e and phi."""
     import torch
-    b = make_batch("single", ncol, seed, n_range=n_range)
+    b = make_batch(kind, ncol, seed, n_range=n_range)
     db = S.DeviceBatch.from_host(b, device)
     solver = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells,
                       max_col_cells=int(b.lengths().max()))
@@ -147,9 +155,14 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--train-cells", default="256",
                     help="cells per training column: an integer, or lo:hi for U{lo..hi}")
+    ap.add_argument("--family", default="single", choices=["single", "ragged"],
+                    help="profile family of the training and evaluation columns")
     args = ap.parse_args()
     t0 = time.perf_counter()
-    if ":" in args.train_cells:
+    if args.family == "ragged":
+        # training seeds 3e6 + i, disjoint from the evaluation / benchmark seeds 2e6 + i
+        X, T, nok = generate(args.ncol, 3_000_000, kind="ragged")
+    elif ":" in args.train_cells:
         lo, hi = (int(v) for v in args.train_cells.split(":"))
         X, T, nok = generate(args.ncol, 1_000_000, n_range=(lo, hi))
     else:
@@ -159,10 +172,11 @@ def main():
     t2 = time.perf_counter()
     params = mlp.get_params()
     save(params, args.out, dict(ncol=args.ncol, steps=args.steps, batch=args.batch, lr=args.lr,
-                                train_cells=args.train_cells))
-    b, res = evaluate(params, args.eval_ncol, 2_000_000,
+                                train_cells=args.train_cells, family=args.family))
+    b, res = evaluate(params, args.eval_ncol, 2_000_000, kind=args.family,
+                      n_range=None if args.family == "ragged" else (512, 2048),
                       variants=(("learned_ne", 1), ("learned_ne_phi", 3)))
-    summary = dict(train_columns=args.ncol, train_cells=args.train_cells,
+    summary = dict(family=args.family, train_columns=args.ncol, train_cells=args.train_cells,
                    train_samples=int(X.shape[0]), converged=nok,
                    data_s=t1 - t0, train_s=t2 - t1, loss=hist,
                    eval={k: {kk: vv for kk, vv in v.items() if kk not in ("ne", "phi")}
