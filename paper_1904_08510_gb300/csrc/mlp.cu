@@ -1,6 +1,7 @@
 // Learned Newton initial guess: feature extraction, a BF16 tensor-core GEMM
-// (mma.sync m16n8k16, FP32 accumulation) with fused bias/SiLU epilogues, the
-// MSE loss, backpropagation, Adam and the guess assembly. The network maps the
+// for training (mma.sync m16n8k16, FP32 accumulation) with fused bias/SiLU
+// epilogues, the MSE loss, backpropagation, Adam, and the fused inference
+// kernel on the tcgen05 tensor cores (mlp_tc.cuh) that assembles the guess. The network maps the
 // 5-cell stencil features of a cell to the scaled Newton increment
 // ((n* - n^n)/s_n, (phi* - phi^n)/s_phi); the JFNK of Algorithm 2 then starts
 // from X^n + S_X y instead of X^n and still decides convergence.
@@ -17,6 +18,7 @@
 #include <string>
 
 #include "../../include/sdcef.h"
+#include "mlp_tc.cuh"
 
 namespace sdcef_impl {
 int report_error(int code, const char* msg);
@@ -276,11 +278,9 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
 }
 
 // --------------------------------------------------------------------------
-// Fused guess: features -> 3 layers -> X^n + S_X y, one pass per column.
-// Persistent CTAs (4 warps) keep the BF16 weights in shared memory; each warp
-// takes 16 cells, builds their features straight into mma.sync A fragments,
-// and chains the layers in registers: the FP32 accumulators of two adjacent
-// m16n8 tiles hold exactly the A fragment of the next layer's k16 block.
+// Fused guess: features -> 3 layers -> X^n + S_X y, one pass per column, on
+// the tcgen05 tensor cores (BF16 operands in shared memory, FP32 accumulators
+// in tensor memory); the kernel's organisation is described in mlp_tc.cuh.
 // --------------------------------------------------------------------------
 struct GuessArgs {
   FeatArgs f;
@@ -288,48 +288,125 @@ struct GuessArgs {
   const __nv_bfloat16 *w1, *w2, *w3;
   int* queue;
   float* stage;                    // [cells][5] per-cell feature values (FP32)
+  int* err;                        // set when a tensor-core wait times out
 };
-
-constexpr int W1S = kIn + 8, W2S = kHid + 8;   // padded smem row strides (bf16)
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-__global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 sW1[kHid * W1S];
-  __shared__ __align__(16) __nv_bfloat16 sW2[kHid * W2S];
-  __shared__ __align__(16) __nv_bfloat16 sW3[8 * W2S];
-  __shared__ float sb1[kHid], sb2[kHid], sb3[2];
-  __shared__ double red[8];
-  __shared__ int s_col;
-  const FeatArgs& a = g.f;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < kHid * kIn; e += 128) sW1[(e / kIn) * W1S + e % kIn] = g.w1[e];
-  for (int e = tid; e < kHid * kHid; e += 128) sW2[(e / kHid) * W2S + e % kHid] = g.w2[e];
-  for (int e = tid; e < 8 * kHid; e += 128)
-    sW3[(e / kHid) * W2S + e % kHid] = (e / kHid) < kOut ? g.w3[e] : __float2bfloat16(0.0f);
-  for (int e = tid; e < kHid; e += 128) { sb1[e] = g.p[kOffB1 + e]; sb2[e] = g.p[kOffB2 + e]; }
-  if (tid < 2) sb3[tid] = g.p[kOffB3 + tid];
-  const int64_t cells = a.col_off[a.ncol];
-  const int gr = lane >> 2, tc = (lane & 3) * 2;
-  // this lane's feature columns: k = kb*16 + tc + {0, 1, 8, 9}
-  int fo[8], fq[8];
+// TMEM lane -> bias + SiLU -> BF16 row of the next layer's A operand
+__device__ __forceinline__ void tc_epilogue(uint32_t taddr, const float* bias, unsigned char* A,
+                                            int row) {
+#pragma unroll 1
+  for (int ch = 0; ch < 4; ++ch) {
+    float v[32];
+    tc::ld32(taddr + ch * 32, v);
 #pragma unroll
-  for (int kb = 0; kb < 2; ++kb)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int f = kb * 16 + tc + (u & 1) + (u >> 1) * 8;
-      fo[4 * kb + u] = f / 5 - 2;
-      fq[4 * kb + u] = f < kFeat ? f % 5 : -1;
+    for (int q = 0; q < 4; ++q) {
+      const int k0 = ch * 32 + q * 8;
+      uint4 w;
+      w.x = pack_bf16(silu_fast(v[q * 8 + 0] + bias[k0 + 0]), silu_fast(v[q * 8 + 1] + bias[k0 + 1]));
+      w.y = pack_bf16(silu_fast(v[q * 8 + 2] + bias[k0 + 2]), silu_fast(v[q * 8 + 3] + bias[k0 + 3]));
+      w.z = pack_bf16(silu_fast(v[q * 8 + 4] + bias[k0 + 4]), silu_fast(v[q * 8 + 5] + bias[k0 + 5]));
+      w.w = pack_bf16(silu_fast(v[q * 8 + 6] + bias[k0 + 6]), silu_fast(v[q * 8 + 7] + bias[k0 + 7]));
+      *reinterpret_cast<uint4*>(A + tc::cm_off(row, k0, kHid / 8)) = w;
     }
+  }
+}
+
+__global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* sW1 = tc_smem;
+  unsigned char* sW2 = sW1 + tc::kW1Bytes;
+  unsigned char* sW3 = sW2 + tc::kW2Bytes;
+  float* sb = reinterpret_cast<float*>(sW3 + tc::kW3Bytes + 2 * tc::kABytes);   // b1, b2, b3
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ double red_s[2][4];
+  __shared__ int col_s[2];
+  const FeatArgs& a = g.f;
+  const int tid = threadIdx.x;
+  // weights in the core-matrix layout; W3 padded with zero rows to N = 16
+  for (int e = tid; e < kHid * kIn; e += 256)
+    *reinterpret_cast<__nv_bfloat16*>(sW1 + tc::cm_off(e / kIn, e % kIn, kIn / 8)) = g.w1[e];
+  for (int e = tid; e < kHid * kHid; e += 256)
+    *reinterpret_cast<__nv_bfloat16*>(sW2 + tc::cm_off(e / kHid, e % kHid, kHid / 8)) = g.w2[e];
+  for (int e = tid; e < 16 * kHid; e += 256) {
+    const int n = e / kHid;
+    *reinterpret_cast<__nv_bfloat16*>(sW3 + tc::cm_off(n, e % kHid, kHid / 8)) =
+        n < kOut ? g.w3[e] : __float2bfloat16(0.0f);
+  }
+  for (int e = tid; e < kHid; e += 256) {
+    sb[e] = g.p[kOffB1 + e];
+    sb[kHid + e] = g.p[kOffB2 + e];
+  }
+  if (tid < kOut) sb[2 * kHid + tid] = g.p[kOffB3 + tid];
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc::saddr(&tmem_base)),
+                 "n"(tc::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[1])) : "memory");
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  // ---- this warpgroup's worker ----
+  const int wg = tid >> 7, t = tid & 127, lane = t & 31, lw = t >> 5;
+  const int barid = 1 + wg;                       // named barrier of the worker (0 is the CTA's)
+  unsigned char* sA = sW3 + tc::kW3Bytes + wg * tc::kABytes;
+  double* red = red_s[wg];
+  const uint32_t s_mbar = tc::saddr(&mbar[wg]);
+  const uint32_t tm = tmem_base;
+  const uint32_t dcol = tm + 128u * (uint32_t)wg;                     // accumulator columns
+  const uint32_t lane_addr = dcol + ((uint32_t)(lw * 32) << 16);     // TMEM lane of row t
+  const uint32_t aA = tc::saddr(sA), aW1 = tc::saddr(sW1), aW2 = tc::saddr(sW2),
+                 aW3 = tc::saddr(sW3);
+  constexpr uint32_t kId1 = tc::idesc_bf16(128, 128), kId3 = tc::idesc_bf16(128, 16);
+  const int64_t cells = a.col_off[a.ncol];
+  uint32_t phase = 0;
+  bool failed = false;
+  // the worker's first thread issues a layer once the A operand is published;
+  // everyone waits, and the outcome is made uniform over the worker
+  auto run_layer = [&](int layer) -> bool {
+    tc::fence_async_smem();
+    tc::fence_before();
+    tc::bar(barid, 128);
+    if (t == 0) {
+      tc::fence_after();
+      if (layer == 1) {
+#pragma unroll
+        for (int k = 0; k < kIn / 16; ++k)
+          tc::mma(dcol, tc::smem_desc(aA + k * 256, 128, (kIn / 8) * 128),
+                  tc::smem_desc(aW1 + k * 256, 128, (kIn / 8) * 128), kId1, k > 0);
+      } else {
+        const uint32_t b = layer == 2 ? aW2 : aW3;
+#pragma unroll
+        for (int k = 0; k < kHid / 16; ++k)
+          tc::mma(dcol, tc::smem_desc(aA + k * 256, 128, (kHid / 8) * 128),
+                  tc::smem_desc(b + k * 256, 128, (kHid / 8) * 128), layer == 2 ? kId1 : kId3,
+                  k > 0);
+      }
+      tc::commit(s_mbar);
+    }
+    const bool ok = tc::wait_phase(s_mbar, phase);
+    phase ^= 1u;
+    const bool bad = tc::bar_or(barid, 128, !ok);
+    tc::fence_after();
+    return !bad;
+  };
   for (;;) {
-    __syncthreads();
-    if (tid == 0) s_col = atomicAdd(g.queue, 1);
-    __syncthreads();
-    const int64_t c = s_col;
-    if (c >= a.ncol) break;
+    tc::bar(barid, 128);
+    if (t == 0) col_s[wg] = atomicAdd(g.queue, 1);
+    tc::bar(barid, 128);
+    const int64_t c = col_s[wg];
+    if (c >= a.ncol || failed) break;
     const int64_t off = a.col_off[c];
     const int N = (int)(a.col_off[c + 1] - off);
     auto fphi = [&](int i) {
@@ -338,7 +415,7 @@ __global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
       return q;
     };
     double mn = 0.0, mq = 0.0, mp = 0.0;
-    for (int i = tid; i < N; i += 128) {
+    for (int i = t; i < N; i += 128) {
       mn = fmax(mn, fabs(a.ne[off + i]));
       mq = fmax(mq, fabs(fphi(i)));
       mp = fmax(mp, fabs(a.phi[off + i]));
@@ -347,10 +424,10 @@ __global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
     for (int k = 0; k < 3; ++k) {
       double v = mx[k];
       for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0) red[warp] = v;
-      __syncthreads();
+      if (lane == 0) red[lw] = v;
+      tc::bar(barid, 128);
       mx[k] = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
-      __syncthreads();
+      tc::bar(barid, 128);
     }
     const double sn = fmax(fmax(mx[0], mx[1]), 1.0);
     const double sp = fmax(fmax(mx[2], fmax(fabs(a.v_left[c]), fabs(a.v_right[c]))), 1.0);
@@ -361,11 +438,9 @@ __global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
       if (j >= N) j = 2 * N - 1 - j;
       return min(max(j, 0), N - 1);
     };
-    // stage the five per-cell values once (the only FP64 work per cell); the
-    // stencil gather below reads them back in FP32
+    // the five per-cell values of the features, staged once in FP32
     float* st = g.stage + off * 5;
-    for (int i = tid; i < N; i += 128) {
-      // mirrored neighbours: index -1 -> 0, index N -> N-1
+    for (int i = t; i < N; i += 128) {
       const int kp = (i + 1 < N) ? i + 1 : N - 1;
       const int km = (i >= 1) ? i - 1 : 0;
       st[i * 5 + 0] = (float)(a.ne[off + i] * isn);
@@ -374,99 +449,60 @@ __global__ void __launch_bounds__(128) guess_fused_kernel(GuessArgs g) {
       st[i * 5 + 3] = (float)(a.T[off + i] * (1.0 / 2000.0));
       st[i * 5 + 4] = (float)(-(a.phi[off + kp] - a.phi[off + km]) * 0.5 * isp);
     }
-    __syncthreads();
-    // feature f of cell i is quantity f%5 of stencil cell i + f/5 - 2; each lane
-    // owns the same 8 feature columns for every tile, so their (offset,
-    // quantity) pairs are computed once
-    auto feat = [&](int i, int fo, int fq) -> float {
-      if (fq < 0) return 0.0f;
-      const int k = mir(i + fo);
-      return __bfloat162float(__float2bfloat16(st[k * 5 + fq]));
-    };
-    for (int r0 = warp * 16; r0 < N; r0 += 64) {
-      const int ra = min(r0 + gr, N - 1), rb = min(r0 + gr + 8, N - 1);
-      // layer 1 A fragments (K = 32: two k16 blocks)
-      uint32_t a1[2][4];
+    tc::bar(barid, 128);
+    for (int r0 = 0; r0 < N; r0 += tc::kTile) {
+      // row t of A: the 25 stencil features of cell i (f = 5 o + q: quantity q
+      // of cell i + o - 2), zero-padded to K = 32
+      const int i = min(r0 + t, N - 1);
 #pragma unroll
-      for (int kb = 0; kb < 2; ++kb) {
-        const int* o = fo + 4 * kb;
-        const int* q = fq + 4 * kb;
-        a1[kb][0] = pack_bf16(feat(ra, o[0], q[0]), feat(ra, o[1], q[1]));
-        a1[kb][1] = pack_bf16(feat(rb, o[0], q[0]), feat(rb, o[1], q[1]));
-        a1[kb][2] = pack_bf16(feat(ra, o[2], q[2]), feat(ra, o[3], q[3]));
-        a1[kb][3] = pack_bf16(feat(rb, o[2], q[2]), feat(rb, o[3], q[3]));
-      }
-      float acc[16][4];
+      for (int ch = 0; ch < kIn / 8; ++ch) {
+        float f8[8];
 #pragma unroll
-      for (int nt = 0; nt < 16; ++nt) {
-        acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-#pragma unroll
-        for (int kb = 0; kb < 2; ++kb) {
-          uint32_t b[2];
-          const __nv_bfloat16* w = sW1 + (nt * 8 + gr) * W1S + kb * 16 + tc;
-          b[0] = *(const uint32_t*)w;
-          b[1] = *(const uint32_t*)(w + 8);
-          mma16816(acc[nt], a1[kb], b);
+        for (int u = 0; u < 8; ++u) {
+          const int f = ch * 8 + u;
+          f8[u] = f < kFeat ? st[mir(i + f / 5 - 2) * 5 + f % 5] : 0.0f;
         }
+        uint4 w;
+        w.x = pack_bf16(f8[0], f8[1]);
+        w.y = pack_bf16(f8[2], f8[3]);
+        w.z = pack_bf16(f8[4], f8[5]);
+        w.w = pack_bf16(f8[6], f8[7]);
+        *reinterpret_cast<uint4*>(sA + tc::cm_off(t, ch * 8, kIn / 8)) = w;
       }
-      // bias + SiLU -> layer 2 A fragments (K = 128: eight k16 blocks)
-      uint32_t a2[8][4];
-#pragma unroll
-      for (int kb = 0; kb < 8; ++kb) {
-        const int n0 = 2 * kb, n1 = 2 * kb + 1;
-        const float b00 = sb1[n0 * 8 + tc], b01 = sb1[n0 * 8 + tc + 1];
-        const float b10 = sb1[n1 * 8 + tc], b11 = sb1[n1 * 8 + tc + 1];
-        a2[kb][0] = pack_bf16(silu_fast(acc[n0][0] + b00), silu_fast(acc[n0][1] + b01));
-        a2[kb][1] = pack_bf16(silu_fast(acc[n0][2] + b00), silu_fast(acc[n0][3] + b01));
-        a2[kb][2] = pack_bf16(silu_fast(acc[n1][0] + b10), silu_fast(acc[n1][1] + b11));
-        a2[kb][3] = pack_bf16(silu_fast(acc[n1][2] + b10), silu_fast(acc[n1][3] + b11));
+      bool ok = run_layer(1);
+      if (ok) {
+        tc_epilogue(lane_addr, sb, sA, t);
+        ok = run_layer(2);
       }
-#pragma unroll
-      for (int nt = 0; nt < 16; ++nt) {
-        acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-#pragma unroll
-        for (int kb = 0; kb < 8; ++kb) {
-          uint32_t b[2];
-          const __nv_bfloat16* w = sW2 + (nt * 8 + gr) * W2S + kb * 16 + tc;
-          b[0] = *(const uint32_t*)w;
-          b[1] = *(const uint32_t*)(w + 8);
-          mma16816(acc[nt], a2[kb], b);
-        }
+      if (ok) {
+        tc_epilogue(lane_addr, sb + kHid, sA, t);
+        ok = run_layer(3);
       }
-#pragma unroll
-      for (int kb = 0; kb < 8; ++kb) {
-        const int n0 = 2 * kb, n1 = 2 * kb + 1;
-        const float b00 = sb2[n0 * 8 + tc], b01 = sb2[n0 * 8 + tc + 1];
-        const float b10 = sb2[n1 * 8 + tc], b11 = sb2[n1 * 8 + tc + 1];
-        a2[kb][0] = pack_bf16(silu_fast(acc[n0][0] + b00), silu_fast(acc[n0][1] + b01));
-        a2[kb][1] = pack_bf16(silu_fast(acc[n0][2] + b00), silu_fast(acc[n0][3] + b01));
-        a2[kb][2] = pack_bf16(silu_fast(acc[n1][0] + b10), silu_fast(acc[n1][1] + b11));
-        a2[kb][3] = pack_bf16(silu_fast(acc[n1][2] + b10), silu_fast(acc[n1][3] + b11));
+      float y[2] = {NAN, NAN};
+      if (ok) tc::ld2(lane_addr, y);
+      const int row = r0 + t;
+      if (row < N) {
+        const int64_t gi = off + row;
+        const float yn = y[0] + sb[2 * kHid], yp = y[1] + sb[2 * kHid + 1];
+        a.ne_g[gi] = a.ne[gi] + ((a.comps & 1) ? sn * (double)yn : (ok ? 0.0 : (double)NAN));
+        a.phi_g[gi] = a.phi[gi] + ((a.comps & 2) ? sp * (double)yp : 0.0);
       }
-      // layer 3: N = 2 padded to one n8 tile
-      float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int kb = 0; kb < 8; ++kb) {
-        uint32_t b[2];
-        const __nv_bfloat16* w = sW3 + gr * W2S + kb * 16 + tc;
-        b[0] = *(const uint32_t*)w;
-        b[1] = *(const uint32_t*)(w + 8);
-        mma16816(y, a2[kb], b);
-      }
-      if (tc == 0) {   // lanes holding output columns 0 (n_e) and 1 (phi)
-        const int rows[2] = {r0 + gr, r0 + gr + 8};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int i = rows[h];
-          if (i >= N) continue;
-          const float yn = y[2 * h] + sb3[0], yp = y[2 * h + 1] + sb3[1];
-          const int64_t gi = off + i;
-          a.ne_g[gi] = a.ne[gi] + ((a.comps & 1) ? sn * (double)yn : 0.0);
-          a.phi_g[gi] = a.phi[gi] + ((a.comps & 2) ? sp * (double)yp : 0.0);
-        }
+      // the next tile's layer 1 overwrites these TMEM columns after the barrier
+      tc::fence_before();
+      if (!ok) {
+        failed = true;
+        if (t == 0) atomicExch(g.err, 1);
+        // an MMA may still be in flight: one more bounded wait before TMEM is freed
+        tc::wait_phase(s_mbar, phase ^ 1u);
+        break;
       }
     }
   }
+  tc::fence_before();
+  __syncthreads();
+  if (tid < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm),
+                 "n"(tc::kTmemCols));
 }
 
 // MSE loss: dY = 2 (Y - T) / (2 n) (BF16 for the backward GEMMs), loss and
@@ -812,16 +848,21 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
   g.w2 = h->w2;
   g.w3 = h->w3;
   g.queue = (int*)h->loss + 4;   // spare words of the loss buffer
+  g.err = (int*)h->loss + 5;
   if (ncells * 5 > h->max_rows * (kIn / 2))
     return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
   g.stage = (float*)h->X;        // [cells][5] FP32 inside the [max_rows][32] BF16 buffer
-  cudaError_t e = cudaMemsetAsync(g.queue, 0, sizeof(int), h->st);
+  cudaError_t e = cudaMemsetAsync(g.queue, 0, 2 * sizeof(int), h->st);
   if (e != cudaSuccess) return cuda_fail(e);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)std::min<int64_t>(b->ncol, (int64_t)std::max(sms, 1) * 4);
-  guess_fused_kernel<<<grid, 128, 0, h->st>>>(g);
+  // two CTAs (four column workers) per SM: 2 x 256 TMEM columns fill the SM's tensor memory
+  const int grid = (int)std::min<int64_t>((b->ncol + 1) / 2, (int64_t)std::max(sms, 1) * 2);
+  e = cudaFuncSetAttribute(guess_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc::kSmemBytes);
+  if (e != cudaSuccess) return cuda_fail(e);
+  guess_tc_kernel<<<grid, 256, tc::kSmemBytes, h->st>>>(g);
   ++h->launches;
   e = cudaGetLastError();
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
