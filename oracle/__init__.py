@@ -38,7 +38,12 @@ class Params(C.Structure):
     _fields_ = [("eps_F", C.c_double), ("eps_X", C.c_double), ("gamma", C.c_double),
                 ("mobility", C.c_double), ("ls_alpha", C.c_double), ("eps_r", C.c_double),
                 ("restart_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int),
-                ("max_linesearch", C.c_int), ("bc_electron", C.c_int), ("precond", C.c_int)]
+                ("max_linesearch", C.c_int), ("bc_electron", C.c_int), ("precond", C.c_int),
+                ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
+                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int)]
+
+PREC_NONE, PREC_RECAST, PREC_EXACT, PREC_MG = 0, 1, 2, 3
+MG_OPERATOR, MG_LINEAR = 0, 1
 
 
 class _Batch(C.Structure):
@@ -52,10 +57,13 @@ class _Batch(C.Structure):
 def default_params(**kw) -> Params:
     """Defaults: eps_F = 1e-10, gamma = 1e-4 (Table 1), mobility 0.4 m^2/(V s)
     (Sec. 2.2), GMRES(30), 50 Newton steps, 200 Krylov iterations per step,
-    20 line-search halvings, absorbing electrodes, recast Schur preconditioner."""
+    20 line-search halvings, absorbing electrodes, recast Schur preconditioner;
+    with precond=PREC_MG its blocks are solved by V-cycles to gamma_MG = 1e-4
+    (Sec. 4.2), at most 100 per block solve."""
     p = dict(eps_F=1e-10, eps_X=0.0, gamma=1e-4, mobility=0.4, ls_alpha=1e-4, eps_r=1.0,
              restart_m=30, max_newton=50, max_krylov=200, max_linesearch=20,
-             bc_electron=BC_ABSORBING, precond=1)
+             bc_electron=BC_ABSORBING, precond=PREC_RECAST, mg_gamma_A=1e-4, mg_gamma_S=1e-4,
+             mg_max_cycles=100, mg_transfer=MG_OPERATOR)
     p.update(kw)
     return Params(**p)
 
@@ -86,8 +94,13 @@ def lib():
         L.or_bern_deriv.argtypes = [C.c_double]
         L.or_residual_batch.argtypes = [P, B, vp, vp, vp, vp]
         L.or_jacobian_batch.argtypes = [P, B, vp, vp, vp, vp, vp]
-        L.or_prec_apply_col.argtypes = [P, B, C.c_int64, vp, vp, vp, vp, vp, vp]
-        L.or_solve_batch.argtypes = [P, B, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
+        L.or_prec_apply_col.argtypes = [P, B, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+        L.or_solve_batch.argtypes = [P, B, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
+        L.or_mg_solve_tri.restype = C.c_int
+        L.or_mg_solve_tri.argtypes = [C.c_int, vp, vp, vp, vp, vp, C.c_double, C.c_int, C.c_int]
+        L.or_mg_hierarchy.restype = C.c_int
+        L.or_mg_hierarchy.argtypes = [C.c_int, vp, vp, vp, C.c_int, vp, vp]
+        L.or_mg_transfers.argtypes = [C.c_int, vp, vp, vp, C.c_int, vp, vp]
         L.or_thomas.argtypes = [C.c_int, vp, vp, vp, vp, vp, vp]
         L.or_gmres_dense.restype = C.c_int
         L.or_gmres_dense.argtypes = [C.c_int, vp, vp, vp, C.c_int, C.c_double, C.c_int,
@@ -164,17 +177,55 @@ def jacobian_blocks(batch, ne, phi, params: Params | None = None):
     return A, B, Lm
 
 
-def prec_apply(batch, c, ne, phi, v1, v2, params: Params | None = None):
-    """Recast Schur preconditioner (Eq. prec_recast) of column c built at X, applied
-    to (v1, v2) in unscaled units."""
+def prec_apply(batch, c, ne, phi, v1, v2, params: Params | None = None, *,
+               return_cycles: bool = False):
+    """Preconditioner params.precond (recast Schur form of Eq. prec_recast by
+    default) of column c built at X, applied to (v1, v2) in unscaled units. With
+    return_cycles, also the V-cycles the multigrid block solves took."""
     P = params or default_params()
     k = _Keep(batch)
     ne, phi, v1, v2 = _f64(ne), _f64(phi), _f64(v1), _f64(v2)
     x1 = np.zeros_like(v1)
     x2 = np.zeros_like(v2)
+    cyc = C.c_int(0)
     lib().or_prec_apply_col(C.byref(P), C.byref(k.s), int(c), _ptr(ne), _ptr(phi), _ptr(v1),
-                            _ptr(v2), _ptr(x1), _ptr(x2))
-    return x1, x2
+                            _ptr(v2), _ptr(x1), _ptr(x2), C.addressof(cyc))
+    return (x1, x2, cyc.value) if return_cycles else (x1, x2)
+
+
+def mg_solve_tri(sub, dia, sup, b, gamma, max_cycles=100, transfer=MG_OPERATOR):
+    """Multigrid V-cycles (Sec. 4.2) on one tridiagonal system from x = 0 until
+    ||b - T x||_2 <= gamma ||b||_2 (or no progress); returns (x, cycles)."""
+    sub, dia, sup, b = _f64(sub), _f64(dia), _f64(sup), _f64(b)
+    x = np.zeros_like(b)
+    k = lib().or_mg_solve_tri(b.shape[0], _ptr(sub), _ptr(dia), _ptr(sup), _ptr(b), _ptr(x),
+                              float(gamma), int(max_cycles), int(transfer))
+    return x, int(k)
+
+
+def mg_hierarchy(sub, dia, sup, transfer=MG_OPERATOR):
+    """The multigrid levels of a tridiagonal matrix: a list of (sub, dia, sup)."""
+    sub, dia, sup = _f64(sub), _f64(dia), _f64(sup)
+    n = sub.shape[0]
+    sizes = np.zeros(64, dtype=np.int32)
+    out = np.zeros(3 * 2 * n + 64)
+    nl = lib().or_mg_hierarchy(n, _ptr(sub), _ptr(dia), _ptr(sup), int(transfer), _ptr(sizes),
+                               _ptr(out))
+    levels, o = [], 0
+    for m in sizes[:nl]:
+        levels.append((out[o:o + m].copy(), out[o + m:o + 2 * m].copy(), out[o + 2 * m:o + 3 * m].copy()))
+        o += 3 * m
+    return levels
+
+
+def mg_transfers(sub, dia, sup, transfer=MG_OPERATOR):
+    """Dense prolongation P (n x n/2) and restriction R (n/2 x n) of the finest level."""
+    sub, dia, sup = _f64(sub), _f64(dia), _f64(sup)
+    n = sub.shape[0]
+    P = np.zeros((n, n // 2))
+    R = np.zeros((n // 2, n))
+    lib().or_mg_transfers(n, _ptr(sub), _ptr(dia), _ptr(sup), int(transfer), _ptr(P), _ptr(R))
+    return P, R
 
 
 def thomas(sub, dia, sup, d):
@@ -201,7 +252,8 @@ def gmres_dense(M, b, m, tol, maxit):
 
 def solve(batch, params: Params | None = None, *, guess=None, threads: int = 0):
     """JFNK (Algorithm 2) on every column. Returns a dict with ne, phi, status,
-    newton_it, krylov_it, res_evals, final_res."""
+    newton_it, krylov_it, res_evals, final_res and mg_cycles (V-cycles of the
+    multigrid block solves, precond=PREC_MG)."""
     P = params or default_params()
     k = _Keep(batch)
     n = batch.ncells
@@ -213,14 +265,15 @@ def solve(batch, params: Params | None = None, *, guess=None, threads: int = 0):
     krylov = np.zeros(ncol, dtype=np.int32)
     evals = np.zeros(ncol, dtype=np.int32)
     fres = np.zeros(ncol)
+    mgc = np.zeros(ncol, dtype=np.int32)
     g_ne = g_phi = None
     if guess is not None:
         g_ne, g_phi = _f64(guess[0]), _f64(guess[1])
     lib().or_solve_batch(C.byref(P), C.byref(k.s), _ptr(g_ne), _ptr(g_phi), _ptr(ne), _ptr(phi),
                          _ptr(status), _ptr(newton), _ptr(krylov), _ptr(evals), _ptr(fres),
-                         int(threads))
+                         _ptr(mgc), int(threads))
     return dict(ne=ne, phi=phi, status=status, newton_it=newton, krylov_it=krylov,
-                res_evals=evals, final_res=fres)
+                res_evals=evals, final_res=fres, mg_cycles=mgc)
 
 
 def max_threads() -> int:

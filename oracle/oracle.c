@@ -46,7 +46,9 @@
  *   block-tridiagonal in (n_i, phi_i) and is solved by block elimination) or
  *   the recast form (Eq. prec_recast) with the approximate Schur complement
  *   S~ = L + I_e dt D_r, its blocks solved exactly by the Thomas algorithm (the
- *   paper's own 1D choice, Sec. 4.2); backtracking
+ *   paper's own 1D choice for the exact reference, Sec. 4.2) or by multigrid
+ *   V-cycles to a tolerance gamma_MG (Sec. 4.2: red-black Gauss-Seidel, two
+ *   relaxations down and up every level); backtracking
  *   line search with sufficient decrease ||F(X + lam dX)|| <= (1 - alpha lam
  *   (1 - gamma)) ||F(X)|| (halving; the printed condition is garbled).
  *
@@ -74,11 +76,18 @@ typedef struct {
   int restart_m, max_newton, max_krylov, max_linesearch;
   int bc_electron;
   int precond;          /* 1: recast Schur P~ (Eq. prec_recast); 2: exact Schur
-                           (Eq. prec, P^-1 = J^-1); 0: none */
+                           (Eq. prec, P^-1 = J^-1); 0: none; 3: recast Schur P~
+                           with its two blocks solved by multigrid V-cycles */
+  double mg_gamma_A;    /* precond 3: V-cycle tolerance of the (dt D_f - I) block;
+                           <= 0 solves that block exactly (Thomas) */
+  double mg_gamma_S;    /* precond 3: V-cycle tolerance of the S~ block; <= 0: exact */
+  int mg_max_cycles;    /* precond 3: V-cycles per block solve at most */
+  int mg_transfer;      /* precond 3: 0 operator-dependent, 1 linear (see below) */
 } or_params;
 
 typedef struct {
   int status, newton_it, krylov_it, res_evals, ls_halvings, krylov_capped;
+  int mg_cycles;        /* V-cycles of all multigrid block solves (precond 3) */
   double final_res, first_res;
 } or_stats;
 
@@ -290,11 +299,269 @@ static void tri_matvec(int n, or_tri T, const double* x, double* y) {
 /* tridiagonal in the cell-interleaved unknowns (n_i, phi_i), so J^{-1} v is */
 /* computed by block Gaussian elimination (block Thomas) on 2x2 blocks.      */
 /* ------------------------------------------------------------------------ */
+/* ------------------------------------------------------------------------ */
+/* Geometric multigrid for one tridiagonal block (Sec. 4.2): standard       */
+/* V-cycles with two red-black Gauss-Seidel relaxations on every level going */
+/* down and two going up, repeated from x = 0 until                          */
+/* ||b - T x||_2 <= gamma_MG ||b||_2, a cycle cap, or a cycle that does not  */
+/* lower the residual (that cycle is undone).                                */
+/* The paper names these ingredients but not the grid transfers; readings:   */
+/*  - coarse unknown I sits on fine unknown 2I+1, n_c = floor(n_f / 2); the  */
+/*    even ("red", relaxed first) unknowns are the fine-only ones;           */
+/*  - transfer OR_MG_OPERATOR (default): operator-dependent interpolation    */
+/*    and restriction of black-box multigrid (Dendy): a fine-only unknown i  */
+/*    takes -T[i][k] / T[i][i] of its coarse neighbour on fine k (P), and    */
+/*    passes -T[k][i] / T[i][i] of its residual to it (R, from T^T);         */
+/*    coarse unknowns are injected both ways. The electron block is an       */
+/*    upwind-dominated M-matrix (cell Peclet numbers up to ~20, drift CFL    */
+/*    in the thousands), on which linear transfers give coarse operators of  */
+/*    the wrong sign pattern and the V-cycle diverges; these transfers keep  */
+/*    the coarse operator the Schur complement onto the coarse unknowns;     */
+/*  - transfer OR_MG_LINEAR: the textbook linear interpolation (mean of the  */
+/*    two coarse neighbours, half of the one neighbour at an end) and        */
+/*    R = P^T;                                                               */
+/*  - coarse operator R T P (Galerkin; tridiagonal again);                   */
+/*  - coarsening stops at OR_MG_COARSE unknowns or fewer, solved by Thomas.  */
+/* ------------------------------------------------------------------------ */
+#define OR_MG_COARSE 8
+#define OR_MG_MAXLEV 40
+enum { OR_MG_OPERATOR = 0, OR_MG_LINEAR = 1 };
+
+typedef struct { int n; double *sub, *dia, *sup, *x, *b, *r; } or_mg_level;
 typedef struct {
-  int n, mode;       /* mode 1: recast, 2: exact */
+  int nlev, transfer;
+  or_mg_level lev[OR_MG_MAXLEV];
+  double* mem;
+  double* xp;        /* iterate before the current cycle */
+  double work[2 * OR_MG_COARSE];
+} or_mg;
+
+static double tri_at(const or_mg_level* L, int i, int k) {
+  if (i < 0 || i >= L->n || k < 0 || k >= L->n) return 0.0;
+  if (k == i - 1) return L->sub[i];
+  if (k == i) return L->dia[i];
+  if (k == i + 1) return L->sup[i];
+  return 0.0;
+}
+
+/* fine unknown of coarse unknown J */
+static int fine_of(int J) { return 2 * J + 1; }
+
+/* P[i][J]: prolongation from level F (n_c = F->n / 2 coarse unknowns) */
+static double mg_p(const or_mg_level* F, int transfer, int i, int J) {
+  int nc = F->n / 2;
+  if (i < 0 || i >= F->n || J < 0 || J >= nc) return 0.0;
+  if (i & 1) return J == (i - 1) / 2 ? 1.0 : 0.0;
+  int k = fine_of(J);
+  if (k != i - 1 && k != i + 1) return 0.0;
+  return transfer == OR_MG_LINEAR ? 0.5 : -tri_at(F, i, k) / F->dia[i];
+}
+
+/* R[J][i]: restriction to level F's coarse unknowns */
+static double mg_r(const or_mg_level* F, int transfer, int J, int i) {
+  int nc = F->n / 2;
+  if (i < 0 || i >= F->n || J < 0 || J >= nc) return 0.0;
+  if (i & 1) return J == (i - 1) / 2 ? 1.0 : 0.0;
+  int k = fine_of(J);
+  if (k != i - 1 && k != i + 1) return 0.0;
+  return transfer == OR_MG_LINEAR ? 0.5 : -tri_at(F, k, i) / F->dia[i];
+}
+
+/* (R T P)[I][J] = sum_i sum_k R[I][i] T[i][k] P[k][J]; R[I][i] vanishes
+ * outside i = 2I .. 2I+2 and T[i][k] outside k = i-1 .. i+1. */
+static double galerkin_entry(const or_mg_level* F, int transfer, int I, int J) {
+  double s = 0.0;
+  for (int i = 2 * I; i <= 2 * I + 2; ++i) {
+    double r = mg_r(F, transfer, I, i);
+    if (r == 0.0) continue;
+    for (int k = i - 1; k <= i + 1; ++k) {
+      double p = mg_p(F, transfer, k, J);
+      if (p == 0.0) continue;
+      s += r * tri_at(F, i, k) * p;
+    }
+  }
+  return s;
+}
+
+static void or_mg_init(or_mg* M, int n, int transfer) {
+  int tot = 0;
+  for (int m = n;; m /= 2) { tot += m; if (m <= OR_MG_COARSE) break; }
+  M->mem = (double*)malloc(sizeof(double) * (6 * (size_t)tot + n));
+  M->nlev = 0;
+  M->transfer = transfer;
+  double* p = M->mem;
+  for (int m = n;; m /= 2) {
+    or_mg_level* L = &M->lev[M->nlev++];
+    L->n = m;
+    L->sub = p; L->dia = p + m; L->sup = p + 2 * m; L->x = p + 3 * m; L->b = p + 4 * m;
+    L->r = p + 5 * m;
+    p += 6 * m;
+    if (m <= OR_MG_COARSE) break;
+  }
+  M->xp = p;
+}
+
+static void or_mg_free(or_mg* M) { free(M->mem); M->mem = NULL; }
+
+/* Level 0 = T; level l+1 = R T_l P. */
+static void or_mg_setup(or_mg* M, const double* sub, const double* dia, const double* sup) {
+  or_mg_level* L0 = &M->lev[0];
+  memcpy(L0->sub, sub, sizeof(double) * L0->n);
+  memcpy(L0->dia, dia, sizeof(double) * L0->n);
+  memcpy(L0->sup, sup, sizeof(double) * L0->n);
+  L0->sub[0] = 0.0;
+  L0->sup[L0->n - 1] = 0.0;
+  for (int l = 0; l + 1 < M->nlev; ++l) {
+    const or_mg_level* F = &M->lev[l];
+    or_mg_level* Cg = &M->lev[l + 1];
+    for (int I = 0; I < Cg->n; ++I) {
+      Cg->sub[I] = I > 0 ? galerkin_entry(F, M->transfer, I, I - 1) : 0.0;
+      Cg->dia[I] = galerkin_entry(F, M->transfer, I, I);
+      Cg->sup[I] = I + 1 < Cg->n ? galerkin_entry(F, M->transfer, I, I + 1) : 0.0;
+    }
+  }
+}
+
+/* One red-black Gauss-Seidel relaxation of T x = b. */
+static void rbgs(const or_mg_level* L, double* x, const double* b) {
+  for (int colour = 0; colour < 2; ++colour)
+    for (int i = colour; i < L->n; i += 2) {
+      double s = b[i];
+      if (i > 0) s -= L->sub[i] * x[i - 1];
+      if (i + 1 < L->n) s -= L->sup[i] * x[i + 1];
+      x[i] = s / L->dia[i];
+    }
+}
+
+static void tri_residual(const or_mg_level* L, const double* x, const double* b, double* r) {
+  for (int i = 0; i < L->n; ++i) {
+    double s = L->dia[i] * x[i];
+    if (i > 0) s += L->sub[i] * x[i - 1];
+    if (i + 1 < L->n) s += L->sup[i] * x[i + 1];
+    r[i] = b[i] - s;
+  }
+}
+
+/* One V-cycle on level l: improves lev[l].x for the right-hand side lev[l].b. */
+static void vcycle(or_mg* M, int l) {
+  or_mg_level* F = &M->lev[l];
+  if (l == M->nlev - 1) {
+    or_thomas(F->n, F->sub, F->dia, F->sup, F->b, F->x, M->work);
+    return;
+  }
+  or_mg_level* Cg = &M->lev[l + 1];
+  rbgs(F, F->x, F->b);
+  rbgs(F, F->x, F->b);
+  tri_residual(F, F->x, F->b, F->r);
+  for (int I = 0; I < Cg->n; ++I) {             /* b_c = R r */
+    double s = 0.0;
+    for (int i = 2 * I; i <= 2 * I + 2 && i < F->n; ++i) s += mg_r(F, M->transfer, I, i) * F->r[i];
+    Cg->b[I] = s;
+    Cg->x[I] = 0.0;
+  }
+  vcycle(M, l + 1);
+  for (int i = 0; i < F->n; ++i) {              /* x += P x_c */
+    double s = 0.0;
+    for (int J = i / 2 - 1; J <= i / 2; ++J)
+      if (J >= 0 && J < Cg->n) s += mg_p(F, M->transfer, i, J) * Cg->x[J];
+    F->x[i] += s;
+  }
+  rbgs(F, F->x, F->b);
+  rbgs(F, F->x, F->b);
+}
+
+/* x = T^{-1} b by V-cycles; returns the cycles run. */
+static int or_mg_solve(or_mg* M, const double* b, double* x, double gamma, int max_cycles) {
+  or_mg_level* L = &M->lev[0];
+  const int n = L->n;
+  double nb = 0.0;
+  for (int i = 0; i < n; ++i) { L->b[i] = b[i]; L->x[i] = 0.0; nb += b[i] * b[i]; }
+  nb = sqrt(nb);
+  double prev = nb;
+  int k = 0;
+  while (nb > 0.0 && k < max_cycles) {
+    memcpy(M->xp, L->x, sizeof(double) * n);
+    vcycle(M, 0);
+    ++k;
+    tri_residual(L, L->x, L->b, L->r);
+    double rr = 0.0;
+    for (int i = 0; i < n; ++i) rr += L->r[i] * L->r[i];
+    rr = sqrt(rr);
+    if (!(rr < prev)) {                  /* no progress (rounding floor or divergence) */
+      memcpy(L->x, M->xp, sizeof(double) * n);
+      break;
+    }
+    prev = rr;
+    if (rr <= gamma * nb) break;
+  }
+  memcpy(x, L->x, sizeof(double) * n);
+  return k;
+}
+
+/* Stand-alone multigrid solve of one tridiagonal system (tests). */
+int or_mg_solve_tri(int n, const double* sub, const double* dia, const double* sup,
+                    const double* b, double* x, double gamma, int max_cycles, int transfer) {
+  or_mg M;
+  or_mg_init(&M, n, transfer);
+  or_mg_setup(&M, sub, dia, sup);
+  int k = or_mg_solve(&M, b, x, gamma, max_cycles);
+  or_mg_free(&M);
+  return k;
+}
+
+/* The level hierarchy of one tridiagonal matrix: number of levels, and each
+ * level's size and three diagonals packed back to back into out (tests). */
+int or_mg_hierarchy(int n, const double* sub, const double* dia, const double* sup,
+                    int transfer, int* sizes, double* out) {
+  or_mg M;
+  or_mg_init(&M, n, transfer);
+  or_mg_setup(&M, sub, dia, sup);
+  size_t o = 0;
+  for (int l = 0; l < M.nlev; ++l) {
+    const or_mg_level* L = &M.lev[l];
+    sizes[l] = L->n;
+    memcpy(out + o, L->sub, sizeof(double) * L->n); o += L->n;
+    memcpy(out + o, L->dia, sizeof(double) * L->n); o += L->n;
+    memcpy(out + o, L->sup, sizeof(double) * L->n); o += L->n;
+  }
+  int nl = M.nlev;
+  or_mg_free(&M);
+  return nl;
+}
+
+/* Dense P (nf x nf/2) and R (nf/2 x nf) of the finest transfer of T (tests). */
+void or_mg_transfers(int n, const double* sub, const double* dia, const double* sup,
+                     int transfer, double* P, double* R) {
+  or_mg_level F = {n, (double*)sub, (double*)dia, (double*)sup, NULL, NULL, NULL};
+  int nc = n / 2;
+  for (int i = 0; i < n; ++i)
+    for (int J = 0; J < nc; ++J) {
+      P[(size_t)i * nc + J] = mg_p(&F, transfer, i, J);
+      R[(size_t)J * n + i] = mg_r(&F, transfer, J, i);
+    }
+}
+
+typedef struct {
+  int n, mode;       /* mode 1: recast, 2: exact, 3: recast with multigrid blocks */
   or_tri A, B, L, S;
   double* work;      /* 4n (recast) or 12n (exact) */
+  or_mg *mgA, *mgS;  /* mode 3: hierarchies of A and S~ (NULL: that block exact) */
+  double gA, gS;
+  int max_cycles;
+  int* cycles;       /* mode 3: V-cycle counter */
 } or_prec;
+
+/* x = A^{-1} v (blk 0) or S~^{-1} v (blk 1): Thomas, or V-cycles in mode 3. */
+static void blk_solve(const or_prec* P, int blk, const double* v, double* x, double* tw) {
+  or_mg* M = blk == 0 ? P->mgA : P->mgS;
+  if (P->mode == 3 && M) {
+    int k = or_mg_solve(M, v, x, blk == 0 ? P->gA : P->gS, P->max_cycles);
+    if (P->cycles) *P->cycles += k;
+    return;
+  }
+  const or_tri* T = blk == 0 ? &P->A : &P->S;
+  or_thomas(P->n, T->sub, T->dia, T->sup, v, x, tw);
+}
 
 void or_prec_recast_apply(const or_prec* P, const double* v1, const double* v2,
                           double* x1, double* x2) {
@@ -302,11 +569,11 @@ void or_prec_recast_apply(const or_prec* P, const double* v1, const double* v2,
   double* z1 = P->work;
   double* t = P->work + n;
   double* tw = P->work + 2 * n;
-  or_thomas(n, P->A.sub, P->A.dia, P->A.sup, v1, z1, tw);
+  blk_solve(P, 0, v1, z1, tw);
   for (int i = 0; i < n; ++i) t[i] = v2[i] + z1[i];            /* v2 - C z1 */
-  or_thomas(n, P->S.sub, P->S.dia, P->S.sup, t, x2, tw);       /* z2 */
+  blk_solve(P, 1, t, x2, tw);                                  /* z2 */
   tri_matvec(n, P->B, x2, t);                                  /* B z2 */
-  or_thomas(n, P->A.sub, P->A.dia, P->A.sup, t, x1, tw);       /* A^{-1} B z2 */
+  blk_solve(P, 0, t, x1, tw);                                  /* A^{-1} B z2 */
   for (int i = 0; i < n; ++i) x1[i] = z1[i] - x1[i];
 }
 
@@ -461,6 +728,92 @@ int or_gmres(int n, or_op_fn op, void* ctx, const double* b, double* x,
   return converged;
 }
 
+/* Flexible GMRES (Saad 1993) for J x = b with a right preconditioner M^{-1}
+ * that may differ between applications (the multigrid block solves of
+ * precond 3 stop at a tolerance, so M^{-1} is not a fixed linear map): each
+ * z_j = M^{-1} v_j is kept and x = Z y, so the residual the Givens estimate
+ * tracks is that of the returned x. Restarts from the true residual b - J x.
+ * For a fixed M^{-1} it produces the iterates of or_gmres on J M^{-1}. */
+int or_fgmres(int n, or_op_fn jop, or_op_fn prec, void* ctx, const double* b, double* x,
+              int m, double tol, int maxit, int* iters, double* res_est) {
+  double* V = (double*)malloc(sizeof(double) * (size_t)n * (m + 1));
+  double* Z = (double*)malloc(sizeof(double) * (size_t)n * m);
+  double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));
+  double* cs = (double*)malloc(sizeof(double) * m);
+  double* sn = (double*)malloc(sizeof(double) * m);
+  double* g = (double*)malloc(sizeof(double) * (m + 1));
+  double* y = (double*)malloc(sizeof(double) * m);
+  double* r = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  int total = 0, converged = 0;
+  for (int i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; }
+  double beta0 = sqrt(dot(n, b, b));
+  double beta = beta0;
+  double est = beta0;
+  if (beta0 == 0.0) converged = 1;
+  while (!converged && total < maxit) {
+    for (int i = 0; i < n; ++i) V[i] = r[i] / beta;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m && total < maxit; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      prec(ctx, vj, zj);
+      jop(ctx, zj, w);
+      ++total;
+      for (int i = 0; i <= j; ++i) {          /* modified Gram-Schmidt */
+        double* vi = V + (size_t)i * n;
+        double hij = dot(n, w, vi);
+        H[i * m + j] = hij;
+        for (int q = 0; q < n; ++q) w[q] -= hij * vi[q];
+      }
+      double hn = sqrt(dot(n, w, w));
+      H[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double a = H[i * m + j], bb = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[j * m + j], bb = H[(j + 1) * m + j];
+      double rho = hypot(a, bb);
+      cs[j] = rho == 0.0 ? 1.0 : a / rho;
+      sn[j] = rho == 0.0 ? 0.0 : bb / rho;
+      H[j * m + j] = rho;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      est = fabs(g[j + 1]);
+      if (est <= tol * beta0 || hn == 0.0) { converged = 1; break; }
+      double* vn = V + (size_t)(j + 1) * n;
+      for (int q = 0; q < n; ++q) vn[q] = w[q] / hn;
+    }
+    /* back substitution of the k x k triangle, x += Z y */
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < k; ++q) s -= H[i * m + q] * y[q];
+      y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+    }
+    for (int i = 0; i < k; ++i) {
+      const double* zi = Z + (size_t)i * n;
+      for (int q = 0; q < n; ++q) x[q] += y[i] * zi[q];
+    }
+    if (converged || total >= maxit) break;
+    /* restart from the true residual r = b - J x */
+    jop(ctx, x, w);
+    ++total;
+    for (int q = 0; q < n; ++q) r[q] = b[q] - w[q];
+    beta = sqrt(dot(n, r, r));
+    est = beta;
+    if (beta <= tol * beta0) { converged = 1; break; }
+  }
+  if (iters) *iters = total;
+  if (res_est) *res_est = beta0 > 0.0 ? est / beta0 : 0.0;
+  free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y); free(r); free(w);
+  return converged;
+}
+
 /* Dense-operator GMRES (test hook: pins GMRES against dense linear algebra). */
 typedef struct { int n; const double* M; } dense_ctx;
 static void dense_op(void* ctx, const double* v, double* w) {
@@ -525,6 +878,9 @@ static void jf_prec(jf_ctx* j, const double* r, double* out) {
   or_prec_apply(&j->prec, j->u1, j->u2, out, out + n);
   for (int i = 0; i < n; ++i) { out[i] /= j->sn; out[n + i] /= j->sp; }
 }
+
+static void jf_jvp_op(void* ctx, const double* v, double* w) { jf_jvp((jf_ctx*)ctx, v, w); }
+static void jf_prec_op(void* ctx, const double* v, double* w) { jf_prec((jf_ctx*)ctx, v, w); }
 
 /* Right-preconditioned operator y -> Jhat Mhat^{-1} y. */
 static void jf_op(void* ctx, const double* v, double* w) {
@@ -607,6 +963,15 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
          L = {tri + 6 * n, tri + 7 * n, tri + 8 * n}, S = {Sd, Sd + n, Sd + 2 * n};
   J.prec.n = n; J.prec.mode = P->precond; J.prec.A = A; J.prec.B = B; J.prec.L = L;
   J.prec.S = S; J.prec.work = pw;
+  or_mg mgA, mgS;
+  J.prec.mgA = J.prec.mgS = NULL;
+  J.prec.gA = P->mg_gamma_A; J.prec.gS = P->mg_gamma_S;
+  J.prec.max_cycles = P->mg_max_cycles;
+  J.prec.cycles = &st->mg_cycles;
+  if (P->precond == 3) {
+    if (P->mg_gamma_A > 0.0) { or_mg_init(&mgA, n, P->mg_transfer); J.prec.mgA = &mgA; }
+    if (P->mg_gamma_S > 0.0) { or_mg_init(&mgS, n, P->mg_transfer); J.prec.mgS = &mgS; }
+  }
 
   double fn2;
   double fninf = scaled_norms(n, Fe, Fp, sFe, sFp, &fn2);
@@ -624,6 +989,8 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
       S.dia[i] = L.dia[i] - B.dia[i];
       S.sup[i] = L.sup[i] - B.sup[i];
     }
+    if (J.prec.mgA) or_mg_setup(J.prec.mgA, A.sub, A.dia, A.sup);
+    if (J.prec.mgS) or_mg_setup(J.prec.mgS, S.sub, S.dia, S.sup);
     double xs = 0.0;
     for (int i = 0; i < n; ++i) xs += (ne[i] / sn) * (ne[i] / sn) + (phin[i] / sp) * (phin[i] / sp);
     J.xnorm = sqrt(xs);
@@ -634,9 +1001,16 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
     for (int i = 0; i < n; ++i) { rhs[i] = -Fe[i] / sFe; rhs[n + i] = -Fp[i] / sFp; }
     int its = 0;
     double est = 0.0;
-    int conv = or_gmres(2 * n, jf_op, &J, rhs, y, P->restart_m, P->gamma, P->max_krylov,
-                        &its, &est);
-    jf_prec(&J, y, dX);
+    int conv;
+    if (P->precond == 3) {
+      /* multigrid block solves to a tolerance: a varying preconditioner */
+      conv = or_fgmres(2 * n, jf_jvp_op, jf_prec_op, &J, rhs, dX, P->restart_m, P->gamma,
+                       P->max_krylov, &its, &est);
+    } else {
+      conv = or_gmres(2 * n, jf_op, &J, rhs, y, P->restart_m, P->gamma, P->max_krylov,
+                      &its, &est);
+      jf_prec(&J, y, dX);
+    }
     st->krylov_it += its;
     if (!conv) st->krylov_capped++;
     /* backtracking line search */
@@ -672,6 +1046,8 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
   }
   for (int i = 0; i < n; ++i) phi[i] = phi_ref(c, i) + psi[i];
   st->final_res = fninf;
+  if (J.prec.mgA) or_mg_free(J.prec.mgA);
+  if (J.prec.mgS) or_mg_free(J.prec.mgS);
   free(buf);
 }
 
@@ -749,10 +1125,10 @@ void or_jacobian_batch(const or_params* P, const or_batch* b, const double* ne,
   }
 }
 
-/* Apply the recast preconditioner of one column built at (ne, phi). */
+/* Apply the preconditioner (P->precond) of one column built at (ne, phi). */
 void or_prec_apply_col(const or_params* P, const or_batch* b, int64_t c, const double* ne,
                        const double* phi, const double* v1, const double* v2, double* x1,
-                       double* x2) {
+                       double* x2, int* cycles /* precond 3: V-cycles used, or NULL */) {
   int n = (int)(b->col_off[c + 1] - b->col_off[c]);
   double* tmp = (double*)malloc(sizeof(double) * 19 * n);
   or_col col;
@@ -768,8 +1144,19 @@ void or_prec_apply_col(const or_params* P, const or_batch* b, int64_t c, const d
     S.sup[i] = L.sup[i] - B.sup[i];
   }
   double* w = (double*)malloc(sizeof(double) * 12 * n);
-  or_prec pr = {n, P->precond == 2 ? 2 : 1, A, B, L, S, w};
+  or_prec pr = {n, P->precond == 2 ? 2 : (P->precond == 3 ? 3 : 1), A, B, L, S, w,
+                NULL, NULL, P->mg_gamma_A, P->mg_gamma_S, P->mg_max_cycles, cycles};
+  or_mg mgA, mgS;
+  if (pr.mode == 3 && P->mg_gamma_A > 0.0) {
+    or_mg_init(&mgA, n, P->mg_transfer); or_mg_setup(&mgA, A.sub, A.dia, A.sup); pr.mgA = &mgA;
+  }
+  if (pr.mode == 3 && P->mg_gamma_S > 0.0) {
+    or_mg_init(&mgS, n, P->mg_transfer); or_mg_setup(&mgS, S.sub, S.dia, S.sup); pr.mgS = &mgS;
+  }
+  if (cycles) *cycles = 0;
   or_prec_apply(&pr, v1, v2, x1, x2);
+  if (pr.mgA) or_mg_free(&mgA);
+  if (pr.mgS) or_mg_free(&mgS);
   free(w);
   free(tmp);
 }
@@ -777,7 +1164,7 @@ void or_prec_apply_col(const or_params* P, const or_batch* b, int64_t c, const d
 void or_solve_batch(const or_params* P, const or_batch* b, const double* ne_guess,
                     const double* phi_guess, double* ne_out, double* phi_out, int* status,
                     int* newton_it, int* krylov_it, int* res_evals, double* final_res,
-                    int nthreads) {
+                    int* mg_cycles, int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -804,6 +1191,7 @@ void or_solve_batch(const or_params* P, const or_batch* b, const double* ne_gues
     if (krylov_it) krylov_it[c] = st.krylov_it;
     if (res_evals) res_evals[c] = st.res_evals;
     if (final_res) final_res[c] = st.final_res;
+    if (mg_cycles) mg_cycles[c] = st.mg_cycles;
   }
 }
 
