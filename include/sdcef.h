@@ -79,6 +79,19 @@ extern "C" {
 #define SDCEF_PREC_RECAST 1  /* Eq. prec_recast: three tridiagonal solves with the
                                 approximate Schur complement S~ = L + I_e dt D_r   */
 #define SDCEF_PREC_NONE 2    /* no preconditioner (diagnostics)                    */
+#define SDCEF_PREC_MG 3      /* Eq. prec_recast with the (dt D_f - I) and S~ blocks
+                                solved by geometric multigrid V-cycles to the
+                                tolerances mg_gamma_A / mg_gamma_S (Sec. 4.2:
+                                two red-black Gauss-Seidel relaxations going down
+                                and up every level); SDCEF_FP64 precision only    */
+
+/* multigrid grid transfers (SDCEF_PREC_MG; the paper does not name them) */
+#define SDCEF_MG_OPERATOR 0  /* operator-dependent (black-box multigrid): a fine-only
+                                unknown i interpolates -T[i][k]/T[i][i] from its
+                                coarse neighbour k and restricts with -T[k][i]/T[i][i];
+                                coarse operator R T P                               */
+#define SDCEF_MG_LINEAR 1    /* linear interpolation (1/2, 1/2), R = P^T, coarse
+                                operator R T P                                      */
 
 /* electron boundary condition at the electrodes (the paper states none) */
 #define SDCEF_BC_ABSORBING 0      /* drift outflow only, no emission, no diffusion */
@@ -100,13 +113,21 @@ typedef struct {
   int precision;      /* SDCEF_FP64 | SDCEF_MIXED | SDCEF_MIXED_DF                    */
   int precond;        /* SDCEF_PREC_EXACT | SDCEF_PREC_RECAST | SDCEF_PREC_NONE       */
   int bc_electron;    /* SDCEF_BC_ABSORBING | SDCEF_BC_ZERO_GRADIENT                  */
-  int threads_per_column; /* 0 = chosen per column length; else 32, 64, 128 or 256    */
+  int threads_per_column; /* 0 = chosen per column length; else 32, 64, 128 or 256;
+                             SDCEF_PREC_MG always runs 128                         */
   int guess_newton_cap; /* Newton steps allowed from a supplied start (ne_guess /
                            phi_guess) before that column restarts from the plain
                            start X^n with the remaining budget; 0 = never restart  */
   double guess_reject_ratio; /* a supplied start whose scaled residual 2-norm exceeds
                            this multiple of the plain start's is replaced by X^n
                            before the first Newton step; 0 = never                  */
+  double mg_gamma_A;  /* SDCEF_PREC_MG: V-cycles of the (dt D_f - I) block stop at
+                         ||b - A x||_2 <= mg_gamma_A ||b||_2 (Sec. 4.2: gamma_MG);
+                         <= 0 solves that block exactly (partitioned Thomas)    */
+  double mg_gamma_S;  /* SDCEF_PREC_MG: the same for the S~ block                 */
+  int mg_max_cycles;  /* SDCEF_PREC_MG: V-cycles per block solve, 1..1000; a cycle
+                         that does not lower the residual also ends the solve  */
+  int mg_transfer;    /* SDCEF_PREC_MG: SDCEF_MG_OPERATOR | SDCEF_MG_LINEAR       */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -143,6 +164,8 @@ typedef struct {
   int* krylov_it;     /* [ncol] GMRES iterations (operator applications)      */
   int* res_evals;     /* [ncol] residual evaluations                          */
   double* final_res;  /* [ncol] ||S_F^-1 F||_inf at exit                      */
+  int* mg_cycles;     /* [ncol] V-cycles of all multigrid block solves
+                         (SDCEF_PREC_MG; 0 otherwise)                         */
 } sdcef_result;
 
 /* Fill p with the defaults: eps_F 1e-10, eps_X 0, gamma 1e-4 (Table 1),
@@ -150,7 +173,9 @@ typedef struct {
  * steps, 200 Krylov iterations per step, 20 halvings, FP64, exact Schur
  * preconditioner, absorbing electrodes, automatic threads per column, and a
  * supplied start rejected if its residual is over 30x the plain start's and
- * judged after 16 Newton steps. */
+ * judged after 16 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
+ * blocks (the optimum of Sec. 4.2), at most 50 V-cycles per block solve and
+ * operator-dependent transfers. */
 void sdcef_default_params(sdcef_params* p);
 
 /* Create a solver context. max_cols, max_cells and max_col_cells bound every
@@ -196,11 +221,13 @@ int sdcef_bernoulli_batch(sdcef_ctx* ctx, const double* x, double* b, double* db
 /* Apply the configured preconditioner, built at X = (ne, phi), to the
  * residual-space vector (r_e, r_phi) in physical (unscaled) units:
  * x = P^-1 r with P^-1 from Eq. prec (SDCEF_PREC_EXACT: x = J^-1 r) or
- * Eq. prec_recast (SDCEF_PREC_RECAST), using the precision of the context.
- * Device pointers, [cells] each. Enqueued on the context stream. */
+ * Eq. prec_recast (SDCEF_PREC_RECAST; SDCEF_PREC_MG with multigrid block
+ * solves), using the precision of the context. Device pointers, [cells] each;
+ * mg_cycles ([ncol], may be NULL) receives the V-cycles of each column's
+ * multigrid block solves. Enqueued on the context stream. */
 int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* ne,
                               const double* phi, const double* r_e, const double* r_phi,
-                              double* x_e, double* x_phi);
+                              double* x_e, double* x_phi, int* mg_cycles);
 
 /* Autotuner: times sdcef_solve_batch on this batch with 32, 64, 128 and 256
  * threads per column (one warm-up and `reps` timed solves each, CUDA events on

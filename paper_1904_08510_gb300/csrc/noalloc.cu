@@ -91,12 +91,13 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   rc = scratch_for_current_device(&base, &sms);
   if (rc) return rc;
 
-  const int tpb = p->threads_per_column ? p->threads_per_column : 128;
+  const int tpb = p->precond == SDCEF_PREC_MG ? kMgTPB
+                  : (p->threads_per_column ? p->threads_per_column : 128);
   const int prec = p->precision;
   const int m = p->restart_m;
   const int kmax = (max_col_cells + tpb - 1) / tpb;
   const size_t PL = (size_t)kmax * tpb;
-  const size_t slot = slot_bytes_prec(prec, PL, m, tpb);
+  const size_t slot = slot_bytes_prec(prec, PL, m, tpb, p->precond);
   const size_t avail = SDCEF_NOALLOC_SCRATCH_BYTES - kHeaderAligned;
   const int64_t nslots = (int64_t)(avail / slot);
   if (nslots < 1)
@@ -126,6 +127,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.newton_it = out->newton_it;
   a.krylov_it = out->krylov_it;
   a.res_evals = out->res_evals;
+  a.mg_cycles = out->mg_cycles;
   a.final_res = out->final_res;
   a.queue = (int*)base;                        // bytes [0, 4): work-queue counter
   int* order = (int*)(base + 256);             // SDCEF_NOALLOC_MAX_COLS ints
@@ -148,11 +150,15 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.p.precond = p->precond;
   a.p.guess_cap = p->guess_newton_cap;
   a.p.guess_ratio = p->guess_reject_ratio;
+  a.p.mg_gA = p->mg_gamma_A;
+  a.p.mg_gS = p->mg_gamma_S;
+  a.p.mg_maxc = p->mg_max_cycles;
+  a.p.mg_transfer = p->mg_transfer;
   a.mode = MODE_SOLVE;
 
   cudaStream_t st = (cudaStream_t)stream;
   const size_t smem = smem_bytes_prec(prec, tpb, m);
-  const int per_sm = occupancy_prec(prec, tpb, smem);
+  const int per_sm = occupancy_prec(prec, tpb, smem, p->precond);
   const int grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, a.ncol, nslots});
   // the queue counter must start at zero; everything else a call reads it writes first
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);

@@ -47,6 +47,7 @@ struct sdcef_ctx {
 namespace {
 
 int tpb_for(const sdcef_params& p, int max_col_cells) {
+  if (p.precond == SDCEF_PREC_MG) return kMgTPB;   // the multigrid kernel's fixed width
   if (p.threads_per_column) return p.threads_per_column;
   (void)max_col_cells;
   return 128;
@@ -66,8 +67,19 @@ int check_params(const sdcef_params* p, int m_cap) {
   if (p->precision != SDCEF_FP64 && p->precision != SDCEF_MIXED && p->precision != SDCEF_MIXED_DF)
     return set_err(SDCEF_ERR_INVALID, "params: precision");
   if (p->precond != SDCEF_PREC_EXACT && p->precond != SDCEF_PREC_RECAST &&
-      p->precond != SDCEF_PREC_NONE)
+      p->precond != SDCEF_PREC_NONE && p->precond != SDCEF_PREC_MG)
     return set_err(SDCEF_ERR_INVALID, "params: precond");
+  if (p->precond == SDCEF_PREC_MG) {
+    if (p->precision != SDCEF_FP64)
+      return set_err(SDCEF_ERR_INVALID, "params: the multigrid preconditioner needs precision FP64");
+    if (!std::isfinite(p->mg_gamma_A) || !std::isfinite(p->mg_gamma_S) || p->mg_gamma_A >= 1.0 ||
+        p->mg_gamma_S >= 1.0)
+      return set_err(SDCEF_ERR_INVALID, "params: mg_gamma_A / mg_gamma_S");
+    if (p->mg_max_cycles < 1 || p->mg_max_cycles > 1000)
+      return set_err(SDCEF_ERR_INVALID, "params: mg_max_cycles");
+    if (p->mg_transfer != SDCEF_MG_OPERATOR && p->mg_transfer != SDCEF_MG_LINEAR)
+      return set_err(SDCEF_ERR_INVALID, "params: mg_transfer");
+  }
   if (p->bc_electron != SDCEF_BC_ABSORBING && p->bc_electron != SDCEF_BC_ZERO_GRADIENT)
     return set_err(SDCEF_ERR_INVALID, "params: bc_electron");
   int t = p->threads_per_column;
@@ -116,7 +128,7 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb) {
   const int kmax = (ctx->max_col_cells + tpb - 1) / tpb;
   a.kmax = kmax;
   a.PL = (size_t)kmax * tpb;
-  a.slot_bytes = slot_bytes_prec(ctx->p.precision, a.PL, ctx->m_cap, tpb);
+  a.slot_bytes = slot_bytes_prec(ctx->p.precision, a.PL, ctx->m_cap, tpb, ctx->p.precond);
   a.max_col_cells = ctx->max_col_cells;
   a.queue = ctx->queue;
   const sdcef_params& p = ctx->p;
@@ -134,6 +146,10 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb) {
   a.p.precond = p.precond;
   a.p.guess_cap = p.guess_newton_cap;
   a.p.guess_ratio = p.guess_reject_ratio;
+  a.p.mg_gA = p.mg_gamma_A;
+  a.p.mg_gS = p.mg_gamma_S;
+  a.p.mg_maxc = p.mg_max_cycles;
+  a.p.mg_transfer = p.mg_transfer;
   return a;
 }
 
@@ -144,8 +160,8 @@ int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
   a.p.m = m_run;
   const size_t smem = smem_bytes_prec(prec, tpb, m_run);
   // slot layout must use the same m as the device code: recompute with m_run
-  a.slot_bytes = slot_bytes_prec(prec, a.PL, m_run, tpb);
-  int per_sm = occupancy_prec(prec, tpb, smem);
+  a.slot_bytes = slot_bytes_prec(prec, a.PL, m_run, tpb, ctx->p.precond);
+  int per_sm = occupancy_prec(prec, tpb, smem, ctx->p.precond);
   int64_t slots_fit = (int64_t)(ctx->ws_bytes / a.slot_bytes);
   int grid = (int)std::min<int64_t>({(int64_t)per_sm * ctx->sms, a.ncol, slots_fit});
   if (grid < 1) return set_err(SDCEF_ERR_CAPACITY, "workspace too small for one column slot");
@@ -191,6 +207,10 @@ void sdcef_default_params(sdcef_params* p) {
   p->max_linesearch = 20;
   p->precision = SDCEF_FP64;
   p->precond = SDCEF_PREC_EXACT;
+  p->mg_gamma_A = 1e-4;
+  p->mg_gamma_S = 1e-4;
+  p->mg_max_cycles = 50;
+  p->mg_transfer = SDCEF_MG_OPERATOR;
   p->bc_electron = SDCEF_BC_ABSORBING;
   p->threads_per_column = 0;
   p->guess_newton_cap = 16;
@@ -226,7 +246,7 @@ int sdcef_create(sdcef_ctx** out, const sdcef_params* p, int64_t max_cols, int64
   size_t best = 0;
   for (int tpb : {32, 64, 128, 256}) {
     const size_t PL = (size_t)((max_col_cells + tpb - 1) / tpb) * tpb;
-    best = std::max(best, slot_bytes_for<double, double>(PL, c->m_cap, tpb));
+    best = std::max(best, slot_bytes_prec(SDCEF_FP64, PL, c->m_cap, tpb, p->precond));
   }
   int64_t nslots = std::min<int64_t>((int64_t)c->sms * 4, max_cols);
   c->nslots = (int)nslots;
@@ -281,6 +301,7 @@ int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* 
   a.newton_it = out->newton_it;
   a.krylov_it = out->krylov_it;
   a.res_evals = out->res_evals;
+  a.mg_cycles = out->mg_cycles;
   a.final_res = out->final_res;
   return run(ctx, a, tpb);
 }
@@ -414,7 +435,7 @@ int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
 
 int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
                               const double* phi, const double* r_e, const double* r_phi,
-                              double* x_e, double* x_phi) {
+                              double* x_e, double* x_phi, int* mg_cycles) {
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, true);
   if (rc) return rc;
@@ -430,6 +451,7 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double
   a.r_phi = r_phi;
   a.o1 = x_e;
   a.o2 = x_phi;
+  a.mg_cycles = mg_cycles;
   return run(ctx, a, tpb);
 }
 
@@ -468,6 +490,7 @@ int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_re
   size_t o_kt = need; need += al(n4);
   size_t o_re = need; need += al(n4);
   size_t o_fr = need; need += al(n8);
+  size_t o_mg = need; need += al(n4);
   if (need > ctx->stage_bytes) {
     if (ctx->stage) cudaFree(ctx->stage);
     ctx->stage = nullptr;
@@ -521,6 +544,7 @@ int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_re
   dr.krylov_it = (int*)(d + o_kt);
   dr.res_evals = (int*)(d + o_re);
   dr.final_res = (double*)(d + o_fr);
+  dr.mg_cycles = (int*)(d + o_mg);
   rc = sdcef_solve_batch(ctx, &db, &dr);
   if (rc) return rc;
   auto d2h = [&](void* dst, size_t o, size_t bytes) {
@@ -533,6 +557,7 @@ int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_re
   if (e == cudaSuccess) e = d2h(ho->krylov_it, o_kt, n4);
   if (e == cudaSuccess) e = d2h(ho->res_evals, o_re, n4);
   if (e == cudaSuccess) e = d2h(ho->final_res, o_fr, n8);
+  if (e == cudaSuccess) e = d2h(ho->mg_cycles, o_mg, n4);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
   return SDCEF_SUCCESS;

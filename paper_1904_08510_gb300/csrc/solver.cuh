@@ -7,10 +7,12 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/sdcef.h"
 #include "blockalg.cuh"
 #include "expm1_table.cuh"
+#include "mg.cuh"
 
 namespace sdcef_impl {
 using namespace sdcef;
@@ -31,6 +33,8 @@ struct DevParams {
   int m, max_newton, max_krylov, max_ls, bc, precond;
   int guess_cap;   // Newton steps from a supplied start before restarting from X^n (0 = never)
   double guess_ratio;   // reject a supplied start with ||Fhat|| > ratio ||Fhat(X^n)|| (0 = never)
+  double mg_gA, mg_gS;  // multigrid tolerances of the two blocks (<= 0: exact block solve)
+  int mg_maxc, mg_transfer;
 };
 
 enum { MODE_SOLVE = 0, MODE_RESIDUAL = 1, MODE_PRECOND = 2 };
@@ -43,7 +47,7 @@ struct KArgs {
   int val[SDCEF_MAX_SPECIES];
   const double *n_ion, *T, *u, *ire, *ne_g, *phi_g;
   double *ne_out, *phi_out;
-  int *status, *newton_it, *krylov_it, *res_evals;
+  int *status, *newton_it, *krylov_it, *res_evals, *mg_cycles;
   double* final_res;
   // workspace
   char* ws;
@@ -99,14 +103,20 @@ template <int TPB, typename KR, typename PR>
 cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st);
 template <int TPB, typename KR, typename PR>
 int occupancy_t(size_t smem);
+// the multigrid preconditioner runs in its own FP64 kernel instantiation
+constexpr int kMgTPB = 128;
+cudaError_t launch_mg(const KArgs& a, int grid, size_t smem, cudaStream_t st);
+int occupancy_mg(size_t smem);
 
 // Precision modes as (Krylov type KR, preconditioner type PR):
 //   SDCEF_FP64 (double, double), SDCEF_MIXED (float, float),
 //   SDCEF_MIXED_DF (double, dfloat).
-inline size_t slot_bytes_prec(int precision, size_t PL, int m, int tpb) {
+// The multigrid preconditioner (FP64 only) appends its region to the slot.
+inline size_t slot_bytes_prec(int precision, size_t PL, int m, int tpb, int precond) {
   if (precision == SDCEF_MIXED) return slot_bytes_for<float, float>(PL, m, tpb);
   if (precision == SDCEF_MIXED_DF) return slot_bytes_for<double, dfloat>(PL, m, tpb);
-  return slot_bytes_for<double, double>(PL, m, tpb);
+  const size_t mg = precond == SDCEF_PREC_MG ? mg_region_doubles(PL) * sizeof(double) : 0;
+  return slot_bytes_for<double, double>(PL, m, tpb) + mg;
 }
 inline size_t smem_bytes_prec(int precision, int tpb, int m) {
   return smem_bytes_for(tpb, m, precision == SDCEF_MIXED ? sizeof(float) : 8);
@@ -136,11 +146,13 @@ inline int occupancy_tpb(int tpb, size_t smem) {
 }
 inline cudaError_t launch_prec(int precision, int tpb, const KArgs& a, int grid, size_t smem,
                                cudaStream_t st) {
+  if (a.p.precond == SDCEF_PREC_MG) return launch_mg(a, grid, smem, st);
   if (precision == SDCEF_MIXED) return launch_tpb<float, float>(tpb, a, grid, smem, st);
   if (precision == SDCEF_MIXED_DF) return launch_tpb<double, dfloat>(tpb, a, grid, smem, st);
   return launch_tpb<double, double>(tpb, a, grid, smem, st);
 }
-inline int occupancy_prec(int precision, int tpb, size_t smem) {
+inline int occupancy_prec(int precision, int tpb, size_t smem, int precond) {
+  if (precond == SDCEF_PREC_MG) return occupancy_mg(smem);
   if (precision == SDCEF_MIXED) return occupancy_tpb<float, float>(tpb, smem);
   if (precision == SDCEF_MIXED_DF) return occupancy_tpb<double, dfloat>(tpb, smem);
   return occupancy_tpb<double, double>(tpb, smem);
@@ -273,6 +285,7 @@ struct ColShared {
   // scaled Poisson stencil of the Jacobian rows: kap/h^2 s_phi/s_Fphi and multiples
   double kh2, m2kh2, m4kh2, kh2_43;
   double vald[SDCEF_MAX_SPECIES];       // ion valences as doubles
+  int mgc;                              // V-cycles of this column's multigrid block solves
 };
 
 struct Geo {
@@ -314,6 +327,12 @@ __device__ Slot<TPB, KR, PR> make_slot(const KArgs& a, int slot) {
 }
 
 __device__ __forceinline__ size_t ix(int j, int tid, int TPB) { return (size_t)j * TPB + tid; }
+
+// The multigrid region follows the slot's planes (SDCEF_PREC_MG only).
+template <int TPB, typename KR, typename PR>
+__device__ __forceinline__ MgArea mg_slot_area(const Slot<TPB, KR, PR>& S) {
+  return mg_area((double*)((char*)S.d + slot_bytes_for<KR, PR>(S.PL, S.m, TPB)), S.PL);
+}
 
 // --------------------------------------------------------------------------
 // Residual F(X) of Eq. nls on (n, psi), phi = phi_ref + psi.
@@ -559,7 +578,7 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
 // --------------------------------------------------------------------------
 // Preconditioner: factorisation and application (scaled units).
 // --------------------------------------------------------------------------
-template <int TPB, typename KR, typename PR>
+template <int TPB, typename KR, typename PR, bool MG>
 __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
                             int fs, PR* sh, double* halo, bool* bad) {
   const int tid = g.tid, kt = g.kt;
@@ -627,14 +646,102 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
       U.a[0] = conv<PR>(R.Lu - rho * R.Bu);
     };
     part_factor<1, PR, TPB, false>(F2, S2, kt, tid, g.tact, row2, sh, bad);
+  } else if (a.p.precond == SDCEF_PREC_MG) {
+    if constexpr (MG && std::is_same<KR, double>::value && std::is_same<PR, double>::value) {
+      // level 0 of both blocks in natural row order (Ahat, S~hat = Lhat - rho Bhat),
+      // Bhat kept for the matvec as in the recast form
+      const MgArea M = mg_slot_area(S);
+      PR* Bpl = S.f + 10 * S.PL;
+      const double rho = cs.r_rho;
+      for (int j = 0; j < kt; ++j) {
+        double lf[4];
+        lface(j, lf);
+        RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+        const int i = g.t0 + j;
+        M.op[0].sub[i] = R.As;
+        M.op[0].dia[i] = R.Ad;
+        M.op[0].sup[i] = R.Au;
+        M.op[1].sub[i] = R.Ls - rho * R.Bs;
+        M.op[1].dia[i] = R.Ld - rho * R.Bd;
+        M.op[1].sup[i] = R.Lu - rho * R.Bu;
+        Bpl[0 * S.PL + ix(j, tid, TPB)] = R.Bs;
+        Bpl[1 * S.PL + ix(j, tid, TPB)] = R.Bd;
+        Bpl[2 * S.PL + ix(j, tid, TPB)] = R.Bu;
+      }
+      __syncthreads();
+      for (int blk = 0; blk < 2; ++blk) {
+        const MgOp& T = M.op[blk];
+        if ((blk == 0 ? a.p.mg_gA : a.p.mg_gS) > 0.0) {
+          mg_build<TPB>(T, g.N, a.p.mg_transfer, bad);
+        } else {
+          // this block is solved exactly: partitioned Thomas factorisation
+          Planes<1, PR, TPB> F{S.f + (size_t)(5 * blk) * S.PL, S.PL};
+          Scal<1, PR, TPB> Sc{S.s + (size_t)blk * FIdx<1>::NSCAL * TPB};
+          auto row = [&](int j, Mat<1, PR>& Ml, Mat<1, PR>& D, Mat<1, PR>& U) {
+            const int i = g.t0 + j;
+            Ml.a[0] = T.sub[i];
+            D.a[0] = T.dia[i];
+            U.a[0] = T.sup[i];
+          };
+          part_factor<1, PR, TPB, false>(F, Sc, kt, tid, g.tact, row, sh, bad);
+        }
+      }
+    }
   }
   __syncthreads();
 }
 
+// x = T^{-1} r for block blk of the multigrid area by V-cycles (Sec. 4.2) from
+// x = 0 until ||r - T x||_2 <= gamma_MG ||r||_2, the cycle cap, or a cycle that
+// does not lower the residual (undone). in/out in the Krylov plane layout (may
+// alias). Returns the cycles run; uniform over the CTA.
+template <int TPB>
+__device__ __noinline__ int mg_solve(const KArgs& a, const Geo& g, const MgArea& M, int blk,
+                                     const double* in, double* out, double* red) {
+  const int tid = g.tid, kt = g.kt, N = g.N;
+  const MgOp& T = M.op[blk];
+  const double gam = blk == 0 ? a.p.mg_gA : a.p.mg_gS;
+  double s = 0.0;
+  for (int j = 0; j < kt; ++j) {
+    const double v = in[ix(j, tid, TPB)];
+    M.b[g.t0 + j] = v;
+    M.x[g.t0 + j] = 0.0;
+    s = fma(v, v, s);
+  }
+  block_reduce<TPB>(&s, 1, false, red);
+  const double nb2 = s;
+  const double tol2 = gam * gam * nb2;
+  const MgLev F0 = mg_lev(T, 0, N);
+  double prev = nb2;
+  int k = 0;
+  while (nb2 > 0.0 && k < a.p.mg_maxc) {
+    for (int i = tid; i < N; i += TPB) M.xp[i] = M.x[i];
+    __syncthreads();
+    mg_vcycle<TPB>(T, N, M.x, M.b, a.p.mg_transfer);
+    ++k;
+    double r2 = 0.0;
+    for (int i = tid; i < N; i += TPB) {
+      const double r = mg_res(F0, M.x, M.b, i);
+      r2 = fma(r, r, r2);
+    }
+    block_reduce<TPB>(&r2, 1, false, red);
+    if (!(r2 < prev)) {
+      for (int i = tid; i < N; i += TPB) M.x[i] = M.xp[i];
+      __syncthreads();
+      break;
+    }
+    prev = r2;
+    if (r2 <= tol2) break;
+  }
+  for (int j = 0; j < kt; ++j) out[ix(j, tid, TPB)] = M.x[g.t0 + j];
+  __syncthreads();
+  return k;
+}
+
 // z = Mhat^{-1} r (scaled units); in/out are Krylov planes (2 components each).
 // Returns ||z||_2^2 (block-reduced) if want_norm.
-template <int TPB, typename KR, typename PR>
-__device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const ColShared& cs,
+template <int TPB, typename KR, typename PR, bool MG>
+__device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShared& cs,
                              const Slot<TPB, KR, PR>& S, KR* re, KR* rp, KR* ze, KR* zp, PR* sh,
                              double* red, bool want_norm) {
   const int tid = g.tid, kt = g.kt;
@@ -692,6 +799,52 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, const Co
       part_solve<1, PR, KR, TPB, false>(F1, S1, rin, out, scr, kt, tid, g.tact, sh);
     }
     for (int j = 0; j < kt; ++j) ze[ix(j, tid, TPB)] = ze[ix(j, tid, TPB)] - tpl[ix(j, tid, TPB)];
+  } else if (a.p.precond == SDCEF_PREC_MG) {
+    if constexpr (MG && std::is_same<KR, double>::value && std::is_same<PR, double>::value) {
+      // Eq. prec_recast as in the recast form, each block solve by V-cycles
+      // (or exactly, where that block's tolerance is <= 0)
+      const MgArea M = mg_slot_area(S);
+      const PR* Bpl = S.f + 10 * S.PL;
+      PR* scr[1] = {S.f + (size_t)kScrPlane * S.PL};
+      auto blk_solve = [&](int blk, KR* rin_, KR* out_) {
+        if ((blk == 0 ? a.p.mg_gA : a.p.mg_gS) > 0.0) {
+          const int k = mg_solve<TPB>(a, g, M, blk, rin_, out_, red);
+          if (tid == 0) cs.mgc += k;
+        } else {
+          Planes<1, PR, TPB> F{S.f + (size_t)(5 * blk) * S.PL, S.PL};
+          Scal<1, PR, TPB> Sc{S.s + (size_t)blk * FIdx<1>::NSCAL * TPB};
+          KR* rin[1] = {rin_};
+          KR* out[1] = {out_};
+          part_solve<1, PR, KR, TPB, false>(F, Sc, rin, out, scr, kt, tid, g.tact, sh);
+        }
+      };
+      const KR cfac = (KR)cs.r_c;   // -Chat
+      blk_solve(0, re, ze);                                   // z1 = Ahat^{-1} r_e
+      for (int j = 0; j < kt; ++j) zp[ix(j, tid, TPB)] = rp[ix(j, tid, TPB)] + cfac * ze[ix(j, tid, TPB)];
+      __syncthreads();
+      blk_solve(1, zp, zp);                                   // z2 = S~^{-1}(r_phi - Chat z1)
+      KR* tpl = S.T(0);
+      {
+        KR* hb = reinterpret_cast<KR*>(sh);
+        if (kt > 0) {
+          hb[tid] = zp[ix(0, tid, TPB)];
+          hb[TPB + tid] = zp[ix(kt - 1, tid, TPB)];
+        }
+        __syncthreads();
+        for (int j = 0; j < kt; ++j) {
+          const int i = g.t0 + j;
+          KR zc = zp[ix(j, tid, TPB)];
+          KR zl = (i == 0) ? KR(0) : (j > 0 ? zp[ix(j - 1, tid, TPB)] : hb[TPB + tid - 1]);
+          KR zr = (i == g.N - 1) ? KR(0) : (j + 1 < kt ? zp[ix(j + 1, tid, TPB)] : hb[tid + 1]);
+          tpl[ix(j, tid, TPB)] = Bpl[0 * S.PL + ix(j, tid, TPB)] * zl +
+                                 Bpl[1 * S.PL + ix(j, tid, TPB)] * zc +
+                                 Bpl[2 * S.PL + ix(j, tid, TPB)] * zr;
+        }
+        __syncthreads();
+      }
+      blk_solve(0, tpl, tpl);                                 // Ahat^{-1} Bhat z2
+      for (int j = 0; j < kt; ++j) ze[ix(j, tid, TPB)] = ze[ix(j, tid, TPB)] - tpl[ix(j, tid, TPB)];
+    }
   } else {
     for (int j = 0; j < kt; ++j) {
       ze[ix(j, tid, TPB)] = re[ix(j, tid, TPB)];
@@ -746,6 +899,7 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
     for (int sp = 0; sp < a.nsp; ++sp) cs.vald[sp] = (double)a.val[sp];
     cs.bad = bad;
     cs.N = bad ? 0 : Ni;
+    cs.mgc = 0;
   }
   __syncthreads();
   if (cs.bad) return false;
@@ -838,7 +992,9 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
 // --------------------------------------------------------------------------
 // The persistent solver kernel.
 // --------------------------------------------------------------------------
-template <int TPB, typename KR, typename PR>
+// MG = true: the instantiation that carries the multigrid preconditioner
+// (SDCEF_PREC_MG); the others compile without it.
+template <int TPB, typename KR, typename PR, bool MG>
 __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ColShared cs;
@@ -873,6 +1029,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           if (a.newton_it) a.newton_it[col] = 0;
           if (a.krylov_it) a.krylov_it[col] = 0;
           if (a.res_evals) a.res_evals[col] = 0;
+          if (a.mg_cycles) a.mg_cycles[col] = 0;
           if (a.final_res) a.final_res[col] = NAN;
         }
       }
@@ -977,7 +1134,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     bool bad = false;
 
     if (a.mode == MODE_PRECOND) {
-      prec_factor<TPB, KR, PR>(a, g, cs, S, cur, sh, halo, &bad);
+      prec_factor<TPB, KR, PR, MG>(a, g, cs, S, cur, sh, halo, &bad);
       // r (physical) -> rhat = r / S_F -> z = Mhat^{-1} rhat -> x = S_X z
       KR* re = S.W(0);
       KR* rp = S.W(1);
@@ -987,12 +1144,13 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         rp[ix(j, tid, TPB)] = (KR)(a.r_phi[gi] * cs.isFp);
       }
       __syncthreads();
-      prec_apply<TPB, KR, PR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
+      prec_apply<TPB, KR, PR, MG>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
         a.o1[gi] = (double)S.Z(0)[ix(j, tid, TPB)] * cs.sn;
         a.o2[gi] = (double)S.Z(1)[ix(j, tid, TPB)] * cs.sp;
       }
+      if (tid == 0 && a.mg_cycles) a.mg_cycles[col] = cs.mgc;
       __syncthreads();
       continue;
     }
@@ -1039,7 +1197,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       if (fninf < a.p.eps_F) { status = SDCEF_STATUS_OK; break; }
       if (l >= cap) { status = SDCEF_STATUS_MAX_NEWTON; break; }
       // preconditioner at X^(l) and ||S_X^{-1} X||_2 (X = (n, phi))
-      prec_factor<TPB, KR, PR>(a, g, cs, S, cur, sh, halo, &bad);
+      prec_factor<TPB, KR, PR, MG>(a, g, cs, S, cur, sh, halo, &bad);
       {
         double s = 0.0;
         for (int j = 0; j < kt; ++j) {
@@ -1084,7 +1242,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         int kdim = 0;
         for (int jj = 0; jj < m && its < a.p.max_krylov; ++jj) {
           // z_jj = Mhat^{-1} V_jj (kept), w = Jhat z_jj
-          double zz = prec_apply<TPB, KR, PR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
+          double zz = prec_apply<TPB, KR, PR, MG>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
                                           S.ZK(jj, 1), sh, red, true);
           double zn = sqrt(zz);
           double eps = kLambdaFD * (kLambdaFD + cs.xnorm / zn);
@@ -1267,6 +1425,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       if (a.newton_it) a.newton_it[col] = newton;
       if (a.krylov_it) a.krylov_it[col] = krylov;
       if (a.res_evals) a.res_evals[col] = res_evals;
+      if (a.mg_cycles) a.mg_cycles[col] = cs.mgc;
       if (a.final_res) a.final_res[col] = fninf;
     }
     __syncthreads();
@@ -1367,7 +1526,7 @@ __global__ void bernoulli_kernel(const double* x, double* b, double* db, int64_t
 
 template <int TPB, typename KR, typename PR>
 cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
-  auto k = jfnk_kernel<TPB, KR, PR>;
+  auto k = jfnk_kernel<TPB, KR, PR, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, TPB, smem, st>>>(a);
@@ -1377,12 +1536,31 @@ cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
 template <int TPB, typename KR, typename PR>
 int occupancy_t(size_t smem) {
   int nb = 0;
-  auto k = jfnk_kernel<TPB, KR, PR>;
+  auto k = jfnk_kernel<TPB, KR, PR, false>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, TPB, smem) != cudaSuccess) return 1;
   return nb < 1 ? 1 : nb;
 }
+
+#ifdef SDCEF_MG
+// The multigrid instantiation: FP64, kMgTPB threads per column.
+inline cudaError_t launch_mg_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
+  auto k = jfnk_kernel<kMgTPB, double, double, true>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kMgTPB, smem, st>>>(a);
+  return cudaGetLastError();
+}
+inline int occupancy_mg_t(size_t smem) {
+  int nb = 0;
+  auto k = jfnk_kernel<kMgTPB, double, double, true>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kMgTPB, smem) != cudaSuccess) return 1;
+  return nb < 1 ? 1 : nb;
+}
+#endif  // SDCEF_MG
 #endif  // SDCEF_KERNEL_TU
 
 }  // namespace sdcef_impl

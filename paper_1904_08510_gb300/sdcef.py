@@ -20,7 +20,8 @@ ERR_INVALID, ERR_CUDA, ERR_CAPACITY, ERR_NOMEM = -1, -2, -3, -4
 STATUS_OK, STATUS_MAX_NEWTON, STATUS_MAX_KRYLOV, STATUS_LINESEARCH_FAIL, \
     STATUS_NONFINITE, STATUS_BAD_INPUT = range(6)
 FP64, MIXED, MIXED_DF = 0, 1, 2
-PREC_EXACT, PREC_RECAST, PREC_NONE = 0, 1, 2
+PREC_EXACT, PREC_RECAST, PREC_NONE, PREC_MG = 0, 1, 2, 3
+MG_OPERATOR, MG_LINEAR = 0, 1
 BC_ABSORBING, BC_ZERO_GRADIENT = 0, 1
 MAX_RESTART = 32
 MAX_SPECIES = 16
@@ -48,7 +49,9 @@ class Params(C.Structure):
                 ("restart_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int),
                 ("max_linesearch", C.c_int), ("precision", C.c_int), ("precond", C.c_int),
                 ("bc_electron", C.c_int), ("threads_per_column", C.c_int),
-                ("guess_newton_cap", C.c_int), ("guess_reject_ratio", C.c_double)]
+                ("guess_newton_cap", C.c_int), ("guess_reject_ratio", C.c_double),
+                ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
+                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int)]
 
 
 class BatchC(C.Structure):
@@ -63,7 +66,7 @@ class BatchC(C.Structure):
 class ResultC(C.Structure):
     _fields_ = [("ne_out", C.c_void_p), ("phi_out", C.c_void_p), ("status", C.c_void_p),
                 ("newton_it", C.c_void_p), ("krylov_it", C.c_void_p), ("res_evals", C.c_void_p),
-                ("final_res", C.c_void_p)]
+                ("final_res", C.c_void_p), ("mg_cycles", C.c_void_p)]
 
 
 _lib = None
@@ -91,7 +94,7 @@ def lib():
         L.sdcef_residual_batch.argtypes = [vp, B, vp, vp, vp, vp]
         L.sdcef_bernoulli_batch.argtypes = [vp, vp, vp, vp, C.c_int64]
         L.sdcef_bernoulli_batch.restype = C.c_int
-        L.sdcef_precond_apply_batch.argtypes = [vp, B, vp, vp, vp, vp, vp, vp]
+        L.sdcef_precond_apply_batch.argtypes = [vp, B, vp, vp, vp, vp, vp, vp, vp]
         L.sdcef_last_error.restype = C.c_char_p
         L.sdcef_last_error.argtypes = []
         L.sdcef_last_launch_count.argtypes = [vp]
@@ -231,7 +234,8 @@ class Solver:
                     newton_it=torch.empty(db.ncol, dtype=torch.int32, device=dev),
                     krylov_it=torch.empty(db.ncol, dtype=torch.int32, device=dev),
                     res_evals=torch.empty(db.ncol, dtype=torch.int32, device=dev),
-                    final_res=torch.empty(db.ncol, dtype=torch.float64, device=dev))
+                    final_res=torch.empty(db.ncol, dtype=torch.float64, device=dev),
+                    mg_cycles=torch.empty(db.ncol, dtype=torch.int32, device=dev))
 
     def solve(self, db: DeviceBatch, out: dict | None = None) -> dict:
         """sdcef_solve_batch on device tensors; asynchronous on the solver stream."""
@@ -239,7 +243,7 @@ class Solver:
         bs = db.cstruct()
         rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), _ptr(out["status"]),
                      _ptr(out["newton_it"]), _ptr(out["krylov_it"]), _ptr(out["res_evals"]),
-                     _ptr(out["final_res"]))
+                     _ptr(out["final_res"]), _ptr(out.get("mg_cycles")))
         _check(lib().sdcef_solve_batch(self.h, C.byref(bs), C.byref(rs)))
         return out
 
@@ -324,14 +328,18 @@ class Solver:
         _check(lib().sdcef_bernoulli_batch(self.h, _ptr(x), _ptr(b), _ptr(db), int(x.numel())))
         return b, db
 
-    def precond_apply(self, db: DeviceBatch, ne, phi, r_e, r_phi):
+    def precond_apply(self, db: DeviceBatch, ne, phi, r_e, r_phi, *, return_cycles=False):
+        """x = P^-1 r (physical units) of the configured preconditioner built at
+        (ne, phi); with return_cycles also the V-cycles per column (PREC_MG)."""
         import torch
         xe = torch.empty_like(r_e)
         xp = torch.empty_like(r_phi)
+        cyc = torch.zeros(db.ncol, dtype=torch.int32, device=r_e.device)
         bs = db.cstruct()
         _check(lib().sdcef_precond_apply_batch(self.h, C.byref(bs), _ptr(ne), _ptr(phi),
-                                               _ptr(r_e), _ptr(r_phi), _ptr(xe), _ptr(xp)))
-        return xe, xp
+                                               _ptr(r_e), _ptr(r_phi), _ptr(xe), _ptr(xp),
+                                               _ptr(cyc)))
+        return (xe, xp, cyc) if return_cycles else (xe, xp)
 
 
 def solve_noalloc(params: Params, db: DeviceBatch, out: dict, max_col_cells: int, stream=None):
@@ -343,7 +351,7 @@ def solve_noalloc(params: Params, db: DeviceBatch, out: dict, max_col_cells: int
     bs = db.cstruct()
     rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), _ptr(out["status"]),
                  _ptr(out["newton_it"]), _ptr(out["krylov_it"]), _ptr(out["res_evals"]),
-                 _ptr(out["final_res"]))
+                 _ptr(out["final_res"]), _ptr(out.get("mg_cycles")))
     _check(lib().sdcef_solve_batch_noalloc(C.byref(params), C.byref(bs), C.byref(rs),
                                            int(max_col_cells), C.c_void_p(stream.cuda_stream)))
     return out
