@@ -586,7 +586,96 @@ def extras(args, S, b, db, solver, params, dev):
         mlp5.close()
         dsolver.close()
     ssolver.close()
+    res["multigrid_block_solver"] = mg_study(S, dev)
     return res
+
+
+def _dv_batch(make_batch, ncol, seed, dv, n_cells=512):
+    """The paper's n_x = 512 flame columns with the electrode potential
+    difference fixed at dv and the time step of a constant ion-drift CFL of 0.5
+    (gas velocity 0.4 m/s plus the ion drift kappa_ion dv / L), so that dt
+    shrinks as dv grows."""
+    from paper_1904_08510_gb300.workload import KAPPA_ION, L_DOMAIN
+    h = L_DOMAIN / n_cells
+    dt = 0.5 * h / (0.4 + KAPPA_ION * dv / L_DOMAIN)
+    b = make_batch("single", ncol, seed, n_cells=n_cells, dt=dt)
+    b.v_right[:] = dv
+    x = (np.arange(n_cells) + 0.5) * h
+    b.phi_old = np.tile(dv * x / L_DOMAIN, ncol)
+    return b, dt
+
+
+def mg_study(S, dev):
+    """The multigrid block solver (SDCEF_PREC_MG) and the preconditioner studies
+    of Sec. 4.2: GMRES iterations and V-cycles against the V-cycle tolerance
+    gamma_MG, one block inexact while the other is solved exactly; and the
+    recast preconditioner against none over dv = 0..1000 V."""
+    import torch
+    from paper_1904_08510_gb300.workload import make_batch
+    out = {"workload": "1024 columns x 512 cells (single-flame family), V_R = dv, "
+                       "dt from an ion-drift CFL of 0.5"}
+
+    def run(b, db, **kw):
+        p = S.default_params(**kw)
+        sv = S.Solver(p, max_cols=b.ncol, max_cells=b.ncells, max_col_cells=int(b.lengths().max()))
+        t, o = _timed(lambda: sv.solve(db), reps=2)
+        nw = o["newton_it"].float()
+        kr = o["krylov_it"].float()
+        r = {"status_ok": int((o["status"] == 0).sum().item()),
+             "newton_mean": float(nw.mean().item()),
+             "krylov_per_newton": float((kr.sum() / nw.sum().clamp(min=1)).item()),
+             "ms": 1e3 * t, "column_solves_per_s": b.ncol / t}
+        if p.precond == S.PREC_MG:
+            r["vcycles_per_column"] = float(o["mg_cycles"].float().mean().item())
+        sv.close()
+        return r, o
+
+    # gamma_MG study at dv = 100 V
+    b, dt = _dv_batch(make_batch, 1024, 7_000_000, 100.0)
+    db = S.DeviceBatch.from_host(b, dev)
+    exact, oref = run(b, db, precond=S.PREC_RECAST)
+    study = {"dv_V": 100.0, "dt_s": dt, "recast_exact_blocks": exact}
+    rows = []
+    for g in (1e-1, 1e-2, 1e-3, 1e-4, 1e-6, 1e-8):
+        row = {"gamma_MG": g}
+        row["S_linear_A_exact"], _ = run(b, db, precond=S.PREC_MG, mg_transfer=S.MG_LINEAR,
+                                         mg_gamma_A=0.0, mg_gamma_S=g)
+        row["A_operator_S_exact"], _ = run(b, db, precond=S.PREC_MG, mg_transfer=S.MG_OPERATOR,
+                                           mg_gamma_A=g, mg_gamma_S=0.0)
+        row["both_operator"], o = run(b, db, precond=S.PREC_MG, mg_transfer=S.MG_OPERATOR,
+                                      mg_gamma_A=g, mg_gamma_S=g)
+        ok = ((o["status"] == 0) & (oref["status"] == 0)).cpu().numpy()
+        row["both_operator"]["max_root_diff_vs_exact_ne"] = float(
+            _colerr(b, o["ne"].cpu().numpy(), oref["ne"].cpu().numpy())[ok].max()) if ok.any() else None
+        rows.append(row)
+    study["rows"] = rows
+    lin_a, _ = run(b, db, precond=S.PREC_MG, mg_transfer=S.MG_LINEAR, mg_gamma_A=1e-4,
+                   mg_gamma_S=1e-4)
+    study["A_linear_transfers_gamma_1e-4"] = lin_a
+    out["gamma_MG_study"] = study
+    # recast preconditioner against none, dv = 0 .. 1000 V (128 columns each):
+    # GMRES(32) iterations to gamma = 1e-4 on the first Newton system (one
+    # Newton step, at most 5000 iterations)
+    pre = []
+    cap = 5000
+    for dv in (0.0, 10.0, 50.0, 100.0, 500.0, 1000.0):
+        bq, dtq = _dv_batch(make_batch, 128, 7_100_000, dv)
+        dbq = S.DeviceBatch.from_host(bq, dev)
+        row = {"dv_V": dv, "dt_s": dtq}
+        for name, pc in (("recast", S.PREC_RECAST), ("none", S.PREC_NONE)):
+            p = S.default_params(precond=pc, restart_m=32, max_newton=1, max_krylov=cap)
+            sv = S.Solver(p, max_cols=bq.ncol, max_cells=bq.ncells, max_col_cells=512)
+            o = sv.solve(dbq)
+            torch.cuda.synchronize()
+            k = o["krylov_it"].cpu().numpy()
+            row[name] = {"krylov_mean": float(k.mean()), "krylov_max": int(k.max()),
+                         "converged_columns": int((k < cap).sum())}
+            sv.close()
+        row["ratio_none_over_recast"] = row["none"]["krylov_mean"] / max(row["recast"]["krylov_mean"], 1e-30)
+        pre.append(row)
+    out["with_without_preconditioner_first_newton_system"] = {"gmres": "GMRES(32), gamma 1e-4",
+                                                               "cap": cap, "rows": pre}
+    return out
 
 
 def _iterations(o):
