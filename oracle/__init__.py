@@ -107,6 +107,7 @@ def lib():
                                      C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.or_max_threads.restype = C.c_int
         L.or_ion_update_batch.argtypes = [B, vp, C.c_double, vp]
+        L.or_current_batch.argtypes = [P, B, vp, vp, C.c_double, vp, vp]
         _lib = L
     return _lib
 
@@ -288,6 +289,19 @@ def ion_update(batch, phi, kappa_ion=4e-3):
     out = np.zeros_like(k.n_ion)
     lib().or_ion_update_batch(C.byref(k.s), _ptr(phi), float(kappa_ion), _ptr(out))
     return out
+
+
+def current(batch, ne, phi, kappa_ion=4e-3, params: Params | None = None):
+    """Charge flux density through every face (Sec. 4.4): (J+, J-) [A/m^2], each
+    [cells + ncol], the N + 1 faces of column c starting at col_off[c] + c."""
+    P = params or default_params()
+    k = _Keep(batch)
+    ne, phi = _f64(ne), _f64(phi)
+    jp = np.zeros(batch.ncells + batch.ncol)
+    jn = np.zeros_like(jp)
+    lib().or_current_batch(C.byref(P), C.byref(k.s), _ptr(ne), _ptr(phi), float(kappa_ion),
+                           _ptr(jp), _ptr(jn))
+    return jp, jn
 
 
 def sdc_sweep(batch, k_max=4, kappa_ion=4e-3, params: Params | None = None, guess=None):

@@ -1237,6 +1237,82 @@ void or_ion_update_batch(const or_batch* b, const double* phi, double kappa_ion,
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Charge flux through every face (Sec. 4.4, i-V curves): J_m = nu_m e       */
+/* Gamma_m with Gamma_m the number flux of species m, J+ the sum over the    */
+/* positive ions, J- over the negative ions and the electrons, J = J+ + J-.  */
+/*   electrons: the Scharfetter-Gummel flux of the residual (Eq. nls), the    */
+/*     electrode faces by the column's electron boundary condition;          */
+/*   ions: drift with the effective velocity U_ef,m = U + nu_m kappa E        */
+/*     (E = -dphi/dx) carrying the upwind cell value, plus diffusion          */
+/*     -D_m dn_m/dx with D_m = kappa k_B T / (|nu_m| e) (Einstein), the face  */
+/*     value the mean of the two cells; at an electrode only an outgoing     */
+/*     drift flux (absorbing, as in the provisional update).                 */
+/* Faces of column c: [col_off[c] + c, col_off[c+1] + c], N + 1 of them,     */
+/* face 0 on the left electrode.                                              */
+/* ------------------------------------------------------------------------ */
+void or_current_batch(const or_params* P, const or_batch* b, const double* ne,
+                      const double* phi, double kappa_ion, double* j_pos, double* j_neg) {
+  int64_t ncells = b->col_off[b->ncol];
+  for (int64_t c = 0; c < b->ncol; ++c) {
+    int64_t a = b->col_off[c];
+    int n = (int)(b->col_off[c + 1] - a);
+    int64_t f0 = a + c;
+    for (int f = 0; f <= n; ++f) { j_pos[f0 + f] = 0.0; j_neg[f0 + f] = 0.0; }
+    if (n < 2) continue;
+    double* tmp = (double*)malloc(sizeof(double) * 3 * n);
+    or_col col;
+    build_col(P, b, c, &col, tmp, tmp + n, tmp + 2 * n);
+    const double h = col.h, mu = col.mu;
+    const double* p = phi + a;
+    const double* x = ne + a;
+    const double* U = col.U;
+    double GL = (-8.0 * col.vl + 9.0 * p[0] - p[1]) / (3.0 * h);
+    double GR = (8.0 * col.vr - 9.0 * p[n - 1] + p[n - 2]) / (3.0 * h);
+    /* electrons */
+    for (int f = 0; f <= n; ++f) {
+      double gam;
+      if (f == 0 || f == n) {
+        double v = f == 0 ? (U ? U[0] : 0.0) + mu * GL : (U ? U[n - 1] : 0.0) + mu * GR;
+        double ned = f == 0 ? x[0] : x[n - 1];
+        int out = f == 0 ? v < 0.0 : v > 0.0;
+        gam = (col.bc == OR_BC_ZERO_GRADIENT || out) ? v * ned : 0.0;
+      } else {
+        int i = f - 1;
+        double Df = 0.5 * (col.D[i] + col.D[i + 1]);
+        double v = face_u(&col, i) + mu * (p[i + 1] - p[i]) / h;
+        double Pe = v * h / Df;
+        gam = (Df / h) * (or_bern(-Pe) * x[i] - or_bern(Pe) * x[i + 1]);
+      }
+      j_neg[f0 + f] += -OR_E * gam;
+    }
+    /* ions */
+    for (int s = 0; s < b->n_species; ++s) {
+      const double* ni = b->n_ion + s * ncells + a;
+      double nu = (double)b->valence[s];
+      if (nu == 0.0) continue;
+      double* J = nu > 0.0 ? j_pos : j_neg;
+      for (int f = 0; f <= n; ++f) {
+        double gam;
+        if (f == 0 || f == n) {
+          double E = f == 0 ? -GL : -GR;
+          double w = (f == 0 ? (U ? U[0] : 0.0) : (U ? U[n - 1] : 0.0)) + nu * kappa_ion * E;
+          int out = f == 0 ? w < 0.0 : w > 0.0;
+          gam = out ? w * (f == 0 ? ni[0] : ni[n - 1]) : 0.0;
+        } else {
+          int i = f - 1;
+          double E = -(p[i + 1] - p[i]) / h;
+          double w = face_u(&col, i) + nu * kappa_ion * E;
+          double Di = 0.5 * (b->T[a + i] + b->T[a + i + 1]) * kappa_ion * OR_KB / (fabs(nu) * OR_E);
+          gam = w * (w > 0.0 ? ni[i] : ni[i + 1]) - Di * (ni[i + 1] - ni[i]) / h;
+        }
+        J[f0 + f] += nu * OR_E * gam;
+      }
+    }
+    free(tmp);
+  }
+}
+
 int or_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
