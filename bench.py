@@ -587,17 +587,50 @@ def extras(args, S, b, db, solver, params, dev):
         dsolver.close()
     ssolver.close()
     res["multigrid_block_solver"] = mg_study(S, dev)
+    res["current_iv_sweep"] = iv_sweep(S, dev)
     return res
+
+
+def iv_sweep(S, dev):
+    """Charge flux (Sec. 4.4) after one implicit electric step over a sweep of
+    the applied voltage: J = J+ + J- at both electrodes and its mean over the
+    interior faces, i = J S with the burner cross-section S = 7.04 cm^2 of the
+    paper's i-V comparison (synthetic columns: no chemistry, no steady state,
+    no experimental comparison)."""
+    import torch
+    from paper_1904_08510_gb300.workload import make_batch
+    s_expe = 7.04e-4                      # m^2
+    rows = []
+    kt = []
+    for dv in (-1000.0, -500.0, -250.0, -100.0, -50.0, 0.0, 50.0, 100.0, 250.0, 500.0, 1000.0):
+        b, dt = _dv_batch(make_batch, 256, 7_200_000, dv)
+        db = S.DeviceBatch.from_host(b, dev)
+        sv = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells, max_col_cells=512)
+        o = sv.solve(db)
+        t, (jp, jn) = _timed(lambda: sv.current(db, o["ne"], o["phi"]), reps=3)
+        kt.append(t)
+        J = (jp + jn).cpu().numpy().reshape(b.ncol, 513)
+        ok = (o["status"] == 0).cpu().numpy()
+        rows.append({"dv_V": dv, "dt_s": dt, "status_ok": int(ok.sum()),
+                     "i_left_uA": float(J[ok, 0].mean() * s_expe * 1e6),
+                     "i_right_uA": float(J[ok, -1].mean() * s_expe * 1e6),
+                     "i_interior_mean_uA": float(J[ok, 1:-1].mean() * s_expe * 1e6)})
+        sv.close()
+    return {"workload": "256 columns x 512 cells per voltage (single-flame family), dt from an "
+                        "ion-drift CFL of 0.5, one implicit step from X^n",
+            "cross_section_m2": s_expe, "rows": rows,
+            "current_kernel_us": 1e6 * float(np.median(kt)),
+            "current_kernel_faces": 256 * 513}
 
 
 def _dv_batch(make_batch, ncol, seed, dv, n_cells=512):
     """The paper's n_x = 512 flame columns with the electrode potential
     difference fixed at dv and the time step of a constant ion-drift CFL of 0.5
-    (gas velocity 0.4 m/s plus the ion drift kappa_ion dv / L), so that dt
-    shrinks as dv grows."""
+    (gas velocity 0.4 m/s plus the ion drift kappa_ion |dv| / L), so that dt
+    shrinks as |dv| grows."""
     from paper_1904_08510_gb300.workload import KAPPA_ION, L_DOMAIN
     h = L_DOMAIN / n_cells
-    dt = 0.5 * h / (0.4 + KAPPA_ION * dv / L_DOMAIN)
+    dt = 0.5 * h / (0.4 + KAPPA_ION * abs(dv) / L_DOMAIN)
     b = make_batch("single", ncol, seed, n_cells=n_cells, dt=dt)
     b.v_right[:] = dv
     x = (np.arange(n_cells) + 0.5) * h

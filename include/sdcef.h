@@ -251,6 +251,22 @@ int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef_result*
 int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* phi,
                            double kappa_ion, double* n_ion_out);
 
+/* Charge flux density through every face (Sec. 4.4, the current of the i-V
+ * curves): J_m = nu_m e Gamma_m summed into J+ (positive ions) and J-
+ * (negative ions and electrons), J = J+ + J- [A/m^2]; the current through a
+ * cross-section S is i = J S. Electrons carry the Scharfetter-Gummel flux of
+ * the residual (electrode faces by the context's electron boundary
+ * condition); each ion species drifts with U + nu_m kappa_ion E (E =
+ * -dphi/dx, upwind cell value) and diffuses with D_m = kappa_ion k_B T /
+ * (|nu_m| e) (face mean of T); an electrode passes only outgoing ion drift.
+ * ne, phi: the state [cells] (device); ions from batch->n_ion; j_pos, j_neg:
+ * [cells + ncol] device outputs, the N + 1 faces of column c at offsets
+ * col_off[c] + c .. col_off[c+1] + c (face 0 on the x = 0 electrode).
+ * Enqueued on the context stream. Returns SDCEF_ERR_INVALID for NULL arrays
+ * or a negative / non-finite kappa_ion. */
+int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* ne,
+                        const double* phi, double kappa_ion, double* j_pos, double* j_neg);
+
 /* The electric part of one MISDC time step (Algorithm 1, SDC iterations
  * k = 1..k_max; the paper uses k_max = 4, Table 1): for each k the provisional
  * ions are advanced from batch->n_ion in the field of the previous iterate

@@ -27,6 +27,10 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st) {
   ion_update_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
+cudaError_t launch_current(const CurrentArgs& a, cudaStream_t st) {
+  current_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
 cudaError_t launch_bernoulli(const double* x, double* b, double* db, int64_t n, cudaStream_t st) {
   const int64_t blocks = (n + 255) / 256;
   bernoulli_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(x, b, db, n);

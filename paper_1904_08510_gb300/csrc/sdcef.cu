@@ -385,6 +385,40 @@ int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* p
   return SDCEF_SUCCESS;
 }
 
+int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
+                        const double* phi, double kappa_ion, double* j_pos, double* j_neg) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, b, false);
+  if (rc) return rc;
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (!ne || !phi || !j_pos || !j_neg || !(kappa_ion >= 0.0) || !std::isfinite(kappa_ion))
+    return set_err(SDCEF_ERR_INVALID, "current: bad arguments");
+  if (b->ncol > 0x7fffffff) return set_err(SDCEF_ERR_INVALID, "current: too many columns");
+  CurrentArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ncol = b->ncol;
+  a.col_off = b->col_off;
+  a.length = b->length;
+  a.vl = b->v_left;
+  a.vr = b->v_right;
+  a.T = b->T;
+  a.u = b->u_adv;
+  a.ne = ne;
+  a.phi = phi;
+  a.n_ion = b->n_ion;
+  a.jp = j_pos;
+  a.jn = j_neg;
+  a.nsp = b->n_species;
+  for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
+  a.kappa = kappa_ion;
+  a.mu = ctx->p.mobility;
+  a.bc = ctx->p.bc_electron;
+  cudaError_t e = launch_current(a, ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  ctx->launches = 1;
+  return SDCEF_SUCCESS;
+}
+
 int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kappa_ion,
                     double* n_ion_work, const sdcef_result* out) {
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");

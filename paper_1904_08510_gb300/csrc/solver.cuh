@@ -172,6 +172,18 @@ struct IonArgs {
   double kappa;
 };
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st);
+
+// Charge flux through every face of every column (Sec. 4.4).
+struct CurrentArgs {
+  int64_t ncol;
+  const int64_t* col_off;
+  const double *length, *vl, *vr, *T, *u, *ne, *phi, *n_ion;
+  double *jp, *jn;
+  int nsp, bc;
+  int val[SDCEF_MAX_SPECIES];
+  double kappa, mu;
+};
+cudaError_t launch_current(const CurrentArgs& a, cudaStream_t st);
 // B(x) and B'(x) of the Scharfetter-Gummel flux, as the residual evaluates them.
 cudaError_t launch_bernoulli(const double* x, double* b, double* db, int64_t n, cudaStream_t st);
 
@@ -1505,6 +1517,82 @@ __global__ void ion_update_kernel(IonArgs a) {
       }
       no[i] = ni[i] - r * (fr - fl);
     }
+  }
+}
+
+// Charge flux J = J+ + J- through the N + 1 faces of a column (Sec. 4.4):
+// J_m = nu_m e Gamma_m, Gamma_m the number flux. Electrons: the
+// Scharfetter-Gummel flux of the residual (electrode faces by the electron
+// boundary condition). Ions: drift with U + nu_m kappa E (E = -dphi/dx) on the
+// upwind cell value plus diffusion -D_m dn/dx, D_m = kappa k_B T / (|nu_m| e)
+// with the face mean of T; at an electrode only outgoing drift. One CTA per
+// column, one thread per face; faces of column c start at col_off[c] + c.
+__global__ void current_kernel(CurrentArgs a) {
+  const int64_t c = blockIdx.x;
+  if (c >= a.ncol) return;
+  const int64_t off = a.col_off[c];
+  const int N = (int)(a.col_off[c + 1] - off);
+  const int64_t f0 = off + c;
+  if (N < 2) {
+    for (int f = threadIdx.x; f <= N; f += blockDim.x) {
+      a.jp[f0 + f] = 0.0;
+      a.jn[f0 + f] = 0.0;
+    }
+    return;
+  }
+  const int64_t cells = a.col_off[a.ncol];
+  const double h = a.length[c] / N, ih = 1.0 / h, mu = a.mu;
+  const double* p = a.phi + off;
+  const double* x = a.ne + off;
+  const double* T = a.T + off;
+  const double* U = a.u ? a.u + off : nullptr;
+  const double GL = (-8.0 * a.vl[c] + 9.0 * p[0] - p[1]) / (3.0 * h);
+  const double GR = (8.0 * a.vr[c] - 9.0 * p[N - 1] + p[N - 2]) / (3.0 * h);
+  const double kbe = kKb / kQe;
+  for (int f = threadIdx.x; f <= N; f += blockDim.x) {
+    double jp = 0.0, jn = 0.0;
+    const bool edge = (f == 0 || f == N);
+    const int i = f - 1;   // interior face between cells i and i + 1
+    double gam;            // electrons
+    if (edge) {
+      const double v = (U ? U[f == 0 ? 0 : N - 1] : 0.0) + mu * (f == 0 ? GL : GR);
+      const double ned = f == 0 ? x[0] : x[N - 1];
+      const bool out = f == 0 ? v < 0.0 : v > 0.0;
+      gam = (a.bc == SDCEF_BC_ZERO_GRADIENT || out) ? v * ned : 0.0;
+    } else {
+      const double Df = 0.5 * (mu * kbe * T[i] + mu * kbe * T[i + 1]);
+      const double uf = U ? 0.5 * (U[i] + U[i + 1]) : 0.0;
+      const double v = uf + mu * (p[i + 1] - p[i]) * ih;
+      const double Pe = v * h / Df;
+      const double aa = fabs(Pe);
+      double bb, dbb;
+      bern_pos<false>(aa, &bb, &dbb);
+      const double bpos = Pe >= 0.0 ? bb : aa + bb;    // B(Pe)
+      const double bneg = Pe >= 0.0 ? aa + bb : bb;    // B(-Pe)
+      gam = (Df * ih) * (bneg * x[i] - bpos * x[i + 1]);
+    }
+    jn -= kQe * gam;
+    for (int s = 0; s < a.nsp; ++s) {
+      const double nu = (double)a.val[s];
+      if (nu == 0.0) continue;
+      const double* ni = a.n_ion + (int64_t)s * cells + off;
+      double g;
+      if (edge) {
+        const double E = f == 0 ? -GL : -GR;
+        const double w = (U ? U[f == 0 ? 0 : N - 1] : 0.0) + nu * a.kappa * E;
+        const bool out = f == 0 ? w < 0.0 : w > 0.0;
+        g = out ? w * (f == 0 ? ni[0] : ni[N - 1]) : 0.0;
+      } else {
+        const double E = -(p[i + 1] - p[i]) * ih;
+        const double w = (U ? 0.5 * (U[i] + U[i + 1]) : 0.0) + nu * a.kappa * E;
+        const double Di = 0.5 * (T[i] + T[i + 1]) * a.kappa * kKb / (fabs(nu) * kQe);
+        g = w * (w > 0.0 ? ni[i] : ni[i + 1]) - Di * (ni[i + 1] - ni[i]) * ih;
+      }
+      if (nu > 0.0) jp += nu * kQe * g;
+      else jn += nu * kQe * g;
+    }
+    a.jp[f0 + f] = jp;
+    a.jn[f0 + f] = jn;
   }
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_solve_batch", "sdcef_solve_batch_host", "sdcef_residual_batch",
            "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count",
            "sdcef_solve_batch_noalloc", "sdcef_ion_update_batch", "sdcef_sdc_sweep",
-           "sdcef_autotune", "sdcef_bernoulli_batch",
+           "sdcef_autotune", "sdcef_bernoulli_batch", "sdcef_current_batch",
            "sdcef_mlp_create", "sdcef_mlp_destroy",
            "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
@@ -100,6 +100,7 @@ def lib():
         L.sdcef_last_launch_count.argtypes = [vp]
         L.sdcef_solve_batch_noalloc.argtypes = [P, B, R, C.c_int, vp]
         L.sdcef_ion_update_batch.argtypes = [vp, B, vp, C.c_double, vp]
+        L.sdcef_current_batch.argtypes = [vp, B, vp, vp, C.c_double, vp, vp]
         L.sdcef_sdc_sweep.argtypes = [vp, B, C.c_int, C.c_double, vp, R]
         L.sdcef_ion_update_batch.restype = C.c_int
         L.sdcef_autotune.argtypes = [vp, B, R, C.c_int, C.POINTER(C.c_int), vp]
@@ -295,6 +296,17 @@ class Solver:
         _check(lib().sdcef_ion_update_batch(self.h, C.byref(bs), _ptr(phi), float(kappa_ion),
                                             _ptr(out)))
         return out
+
+    def current(self, db: DeviceBatch, ne, phi, kappa_ion: float = 4e-3):
+        """sdcef_current_batch: (J+, J-) [A/m^2] through every face, [cells + ncol]
+        each; the N + 1 faces of column c start at col_off[c] + c."""
+        import torch
+        jp = torch.empty(db.ncells + db.ncol, dtype=torch.float64, device=ne.device)
+        jn = torch.empty_like(jp)
+        bs = db.cstruct()
+        _check(lib().sdcef_current_batch(self.h, C.byref(bs), _ptr(ne), _ptr(phi),
+                                         float(kappa_ion), _ptr(jp), _ptr(jn)))
+        return jp, jn
 
     def sdc_sweep(self, db: DeviceBatch, k_max: int = 4, kappa_ion: float = 4e-3,
                   work=None, out: dict | None = None) -> dict:
