@@ -108,6 +108,7 @@ def lib():
         L.or_max_threads.restype = C.c_int
         L.or_ion_update_batch.argtypes = [B, vp, C.c_double, vp]
         L.or_current_batch.argtypes = [P, B, vp, vp, C.c_double, vp, vp]
+        L.or_ion_provisional_batch.argtypes = [B, vp, vp, C.c_double, vp]
         _lib = L
     return _lib
 
@@ -288,6 +289,18 @@ def ion_update(batch, phi, kappa_ion=4e-3):
     phi = _f64(phi)
     out = np.zeros_like(k.n_ion)
     lib().or_ion_update_batch(C.byref(k.s), _ptr(phi), float(kappa_ion), _ptr(out))
+    return out
+
+
+def ion_provisional(batch, phi, n_prev=None, kappa_ion=4e-3):
+    """Provisional ion densities of an SDC iteration with second-order Godunov
+    drift/advection, implicit diffusion and the SDC diffusion correction
+    against the previous iterate n_prev ([n_species, cells]; None = n^n)."""
+    k = _Keep(batch)
+    phi = _f64(phi)
+    npv = None if n_prev is None else _f64(np.atleast_2d(n_prev))
+    out = np.zeros_like(k.n_ion)
+    lib().or_ion_provisional_batch(C.byref(k.s), _ptr(phi), _ptr(npv), float(kappa_ion), _ptr(out))
     return out
 
 

@@ -1238,6 +1238,99 @@ void or_ion_update_batch(const or_batch* b, const double* phi, double kappa_ion,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Provisional charged species of an SDC iteration with the transport of     */
+/* Sec. 3.1 and Algorithm 1: for each species m                               */
+/*   n~ = n^n + dt [A^{n+1/2} + (D n^n - D n^(k)) / 2 + D n~],                */
+/* i.e. one implicit diffusion solve                                          */
+/*   (I - dt D) n~ = n^n + dt A^{n+1/2} + (dt / 2)(D n^n - D n^(k)),          */
+/* n^(k) the previous SDC iterate (n^n at the first iteration, where the      */
+/* correction vanishes); no reactions (the columns carry no chemistry).       */
+/*  A: advection with the effective velocity w = U_f + nu kappa E_f          */
+/*     (E = -dphi/dx of the current potential), by a second-order Godunov     */
+/*     (MUSCL) scheme: the face state is the upwind cell value extrapolated   */
+/*     to the face and to t^{n+1/2} along the characteristic,                 */
+/*       n_{i+1/2} = n_i + (1 - w dt/h) s_i / 2        (w >= 0)               */
+/*                 = n_{i+1} - (1 + w dt/h) s_{i+1} / 2 (w < 0),              */
+/*     s the monotonized-central limited difference of n^n (0 in the end      */
+/*     cells); electrodes pass the outgoing drift of the edge cell only.      */
+/*  D: (D n)_i = [D_{i+1/2}(n_{i+1} - n_i) - D_{i-1/2}(n_i - n_{i-1})] / h^2,  */
+/*     D = kappa k_B T_f / (|nu| e) (Einstein, T_f the face mean), no         */
+/*     diffusive flux through the electrodes.                                 */
+/* ------------------------------------------------------------------------ */
+static double mc_slope(double dm, double dp) {
+  if (dm * dp <= 0.0) return 0.0;
+  double a = fabs(dm), b = fabs(dp), c = 0.5 * fabs(dm + dp);
+  double m = 2.0 * a < 2.0 * b ? 2.0 * a : 2.0 * b;
+  if (c < m) m = c;
+  return dm > 0.0 ? m : -m;
+}
+
+void or_ion_provisional_batch(const or_batch* b, const double* phi, const double* n_prev,
+                              double kappa_ion, double* n_out) {
+  int64_t ncells = b->col_off[b->ncol];
+  for (int64_t c = 0; c < b->ncol; ++c) {
+    int64_t a = b->col_off[c];
+    int n = (int)(b->col_off[c + 1] - a);
+    if (n < 2) {
+      for (int s = 0; s < b->n_species; ++s)
+        for (int i = 0; i < n; ++i) n_out[s * ncells + a + i] = b->n_ion[s * ncells + a + i];
+      continue;
+    }
+    double h = b->length[c] / n, dt = b->dt[c];
+    const double* p = phi + a;
+    const double* T = b->T + a;
+    const double* U = b->u_adv ? b->u_adv + a : NULL;
+    double GL = (-8.0 * b->v_left[c] + 9.0 * p[0] - p[1]) / (3.0 * h);
+    double GR = (8.0 * b->v_right[c] - 9.0 * p[n - 1] + p[n - 2]) / (3.0 * h);
+    double* F = (double*)malloc(sizeof(double) * (n + 1));      /* advective face fluxes */
+    double* Df = (double*)malloc(sizeof(double) * (n + 1));     /* face diffusivities    */
+    double* sl = (double*)malloc(sizeof(double) * n);
+    double* rhs = (double*)malloc(sizeof(double) * n);
+    double* sub = (double*)malloc(sizeof(double) * n);
+    double* dia = (double*)malloc(sizeof(double) * n);
+    double* sup = (double*)malloc(sizeof(double) * n);
+    double* work = (double*)malloc(sizeof(double) * 2 * n);
+    for (int s = 0; s < b->n_species; ++s) {
+      const double* n0 = b->n_ion + s * ncells + a;
+      const double* nk = n_prev ? n_prev + s * ncells + a : n0;
+      double* no = n_out + s * ncells + a;
+      double nu = (double)b->valence[s];
+      double Dc = nu != 0.0 ? kappa_ion * OR_KB / (fabs(nu) * OR_E) : 0.0;
+      for (int i = 0; i < n; ++i)
+        sl[i] = (i == 0 || i == n - 1) ? 0.0 : mc_slope(n0[i] - n0[i - 1], n0[i + 1] - n0[i]);
+      for (int f = 0; f <= n; ++f) {
+        if (f == 0 || f == n) {
+          double w = (U ? U[f == 0 ? 0 : n - 1] : 0.0) + nu * kappa_ion * (f == 0 ? -GL : -GR);
+          int out = f == 0 ? w < 0.0 : w > 0.0;
+          F[f] = out ? w * (f == 0 ? n0[0] : n0[n - 1]) : 0.0;
+          Df[f] = 0.0;
+        } else {
+          int i = f - 1;
+          double w = (U ? 0.5 * (U[i] + U[i + 1]) : 0.0) - nu * kappa_ion * (p[i + 1] - p[i]) / h;
+          double cfl = w * dt / h;
+          double nf = w >= 0.0 ? n0[i] + 0.5 * (1.0 - cfl) * sl[i]
+                               : n0[i + 1] - 0.5 * (1.0 + cfl) * sl[i + 1];
+          F[f] = w * nf;
+          Df[f] = Dc * 0.5 * (T[i] + T[i + 1]);
+        }
+      }
+      for (int i = 0; i < n; ++i) {
+        double dn0 = (Df[i + 1] * ((i + 1 < n ? n0[i + 1] : n0[i]) - n0[i]) -
+                      Df[i] * (n0[i] - (i > 0 ? n0[i - 1] : n0[i]))) / (h * h);
+        double dnk = (Df[i + 1] * ((i + 1 < n ? nk[i + 1] : nk[i]) - nk[i]) -
+                      Df[i] * (nk[i] - (i > 0 ? nk[i - 1] : nk[i]))) / (h * h);
+        rhs[i] = n0[i] - (dt / h) * (F[i + 1] - F[i]) + 0.5 * dt * (dn0 - dnk);
+        sub[i] = -dt * Df[i] / (h * h);
+        sup[i] = -dt * Df[i + 1] / (h * h);
+        dia[i] = 1.0 - sub[i] - sup[i];
+      }
+      or_thomas(n, sub, dia, sup, rhs, no, work);
+    }
+    free(F); free(Df); free(sl); free(rhs); free(sub); free(dia); free(sup); free(work);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Charge flux through every face (Sec. 4.4, i-V curves): J_m = nu_m e       */
 /* Gamma_m with Gamma_m the number flux of species m, J+ the sum over the    */
 /* positive ions, J- over the negative ions and the electrons, J = J+ + J-.  */
