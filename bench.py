@@ -537,7 +537,7 @@ def extras(args, S, b, db, solver, params, dev):
     st_ = torch.cuda.Stream()
     ssolver = S.Solver(params, max_cols=sb.ncol, max_cells=sb.ncells, max_col_cells=1024, stream=st_)
     sout = ssolver.alloc_result(sdb)
-    work = torch.empty_like(sdb.tensors["n_ion"])
+    work = ssolver.sweep_work(sdb)
     with torch.cuda.stream(st_):
         te, _ = _timed(lambda: ssolver.sdc_sweep(sdb, 4, work=work, out=sout), reps=2)
         g = torch.cuda.CUDAGraph()

@@ -93,6 +93,12 @@ extern "C" {
 #define SDCEF_MG_LINEAR 1    /* linear interpolation (1/2, 1/2), R = P^T, coarse
                                 operator R T P                                      */
 
+/* provisional charged species between SDC iterations (sdcef_sdc_sweep) */
+#define SDCEF_ION_DRIFT_UPWIND 0  /* electric drift only, first-order upwind, explicit */
+#define SDCEF_ION_GODUNOV 1       /* the transport of Sec. 3.1 / Algorithm 1: effective-
+                                     velocity advection by a second-order Godunov scheme,
+                                     implicit diffusion, SDC diffusion correction      */
+
 /* electron boundary condition at the electrodes (the paper states none) */
 #define SDCEF_BC_ABSORBING 0      /* drift outflow only, no emission, no diffusion */
 #define SDCEF_BC_ZERO_GRADIENT 1  /* boundary flux v n_edge in both directions     */
@@ -128,6 +134,8 @@ typedef struct {
   int mg_max_cycles;  /* SDCEF_PREC_MG: V-cycles per block solve, 1..1000; a cycle
                          that does not lower the residual also ends the solve  */
   int mg_transfer;    /* SDCEF_PREC_MG: SDCEF_MG_OPERATOR | SDCEF_MG_LINEAR       */
+  int ion_scheme;     /* provisional ions of sdcef_sdc_sweep: SDCEF_ION_GODUNOV |
+                         SDCEF_ION_DRIFT_UPWIND                                 */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -175,7 +183,8 @@ typedef struct {
  * supplied start rejected if its residual is over 30x the plain start's and
  * judged after 16 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
  * blocks (the optimum of Sec. 4.2), at most 50 V-cycles per block solve and
- * operator-dependent transfers. */
+ * operator-dependent transfers; the paper's ion transport in the SDC sweep
+ * (SDCEF_ION_GODUNOV). */
 void sdcef_default_params(sdcef_params* p);
 
 /* Create a solver context. max_cols, max_cells and max_col_cells bound every
@@ -251,6 +260,23 @@ int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef_result*
 int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* phi,
                            double kappa_ion, double* n_ion_out);
 
+/* Provisional charged species of an SDC iteration with the paper's transport
+ * (Sec. 3.1, Algorithm 1; SDCEF_ION_GODUNOV): for each species
+ *   (I - dt D) n~ = n^n + dt A^{n+1/2} + (dt/2)(D n^n - D n^(k)),
+ * A the advection with the effective velocity U_ef,m = U + nu_m kappa_ion E
+ * (E = -dphi/dx of phi) by a second-order Godunov (MUSCL) scheme: the face
+ * state is the upwind cell value extrapolated to the face and to t^{n+1/2}
+ * with its monotonized-central limited difference; electrodes pass outgoing
+ * drift only. D: diffusion with D_m = kappa_ion k_B T / (|nu_m| e), no flux
+ * through the electrodes. n^(k) = n_prev ([n_species][cells], NULL: n^n, the
+ * first SDC iteration, where the correction vanishes). No reactions (the
+ * columns carry no chemistry). n^n = batch->n_ion; scratch: [cells] device
+ * doubles; n_ion_out: [n_species][cells] device (may not alias n^n or
+ * n_prev). Enqueued on the context stream. */
+int sdcef_ion_provisional_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* phi,
+                                const double* n_prev, double kappa_ion, double* scratch,
+                                double* n_ion_out);
+
 /* Charge flux density through every face (Sec. 4.4, the current of the i-V
  * curves): J_m = nu_m e Gamma_m summed into J+ (positive ions) and J-
  * (negative ions and electrons), J = J+ + J- [A/m^2]; the current through a
@@ -271,8 +297,13 @@ int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* 
  * k = 1..k_max; the paper uses k_max = 4, Table 1): for each k the provisional
  * ions are advanced from batch->n_ion in the field of the previous iterate
  * (phi^n for k = 1) and Eq. nls is solved from the previous iterate (from
- * X^n, or batch->ne_guess / phi_guess, for k = 1). n_ion_work is caller-owned
- * device scratch of [n_species][cells]. The results of the last iteration are
+ * X^n, or batch->ne_guess / phi_guess, for k = 1). The provisional ions come
+ * from sdcef_ion_provisional_batch (params ion_scheme SDCEF_ION_GODUNOV, with
+ * the previous iteration's provisional ions as n^(k)) or from
+ * sdcef_ion_update_batch (SDCEF_ION_DRIFT_UPWIND). n_ion_work is caller-owned
+ * device scratch of (2 n_species + 1) x max_cells doubles (Godunov; max_cells
+ * of sdcef_create: the library does not read the cell count on the host) or
+ * n_species x cells (drift-only). The results of the last iteration are
  * written to out; enqueued on the context stream with no allocation and no
  * synchronisation, so the sweep can be captured in a CUDA graph. */
 int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* batch, int k_max, double kappa_ion,

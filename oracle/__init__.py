@@ -317,19 +317,27 @@ def current(batch, ne, phi, kappa_ion=4e-3, params: Params | None = None):
     return jp, jn
 
 
-def sdc_sweep(batch, k_max=4, kappa_ion=4e-3, params: Params | None = None, guess=None):
+def sdc_sweep(batch, k_max=4, kappa_ion=4e-3, params: Params | None = None, guess=None,
+              scheme="godunov"):
     """The electric part of one MISDC step (Algorithm 1): for k = 1..k_max the
     provisional ions are advanced from n_ion^n in the field of the previous
-    iterate and the implicit electron/potential system is solved from the
-    previous iterate (X^0 = X^n, or the given guess for k = 1)."""
+    iterate (scheme "godunov": ion_provisional with the previous iteration's
+    provisional ions as n^(k); "drift": ion_update) and the implicit
+    electron/potential system is solved from the previous iterate (X^0 = X^n,
+    or the given guess for k = 1)."""
     from copy import copy
     P = params or default_params()
     ne, phi = batch.ne_old.copy(), batch.phi_old.copy()
     start = guess
     hist = []
+    prev = None
     for k in range(k_max):
         bk = copy(batch)
-        bk.n_ion = ion_update(batch, phi, kappa_ion)
+        if scheme == "godunov":
+            bk.n_ion = ion_provisional(batch, phi, prev, kappa_ion)
+            prev = bk.n_ion
+        else:
+            bk.n_ion = ion_update(batch, phi, kappa_ion)
         g = start if start is not None else ((ne, phi) if k > 0 else None)
         r = solve(bk, P, guess=g)
         ne, phi = r["ne"], r["phi"]

@@ -27,6 +27,10 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st) {
   ion_update_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
+cudaError_t launch_ion_provisional(const IonProvArgs& a, cudaStream_t st) {
+  ion_provisional_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
 cudaError_t launch_current(const CurrentArgs& a, cudaStream_t st) {
   current_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
   return cudaGetLastError();

@@ -80,6 +80,8 @@ int check_params(const sdcef_params* p, int m_cap) {
     if (p->mg_transfer != SDCEF_MG_OPERATOR && p->mg_transfer != SDCEF_MG_LINEAR)
       return set_err(SDCEF_ERR_INVALID, "params: mg_transfer");
   }
+  if (p->ion_scheme != SDCEF_ION_GODUNOV && p->ion_scheme != SDCEF_ION_DRIFT_UPWIND)
+    return set_err(SDCEF_ERR_INVALID, "params: ion_scheme");
   if (p->bc_electron != SDCEF_BC_ABSORBING && p->bc_electron != SDCEF_BC_ZERO_GRADIENT)
     return set_err(SDCEF_ERR_INVALID, "params: bc_electron");
   int t = p->threads_per_column;
@@ -211,6 +213,7 @@ void sdcef_default_params(sdcef_params* p) {
   p->mg_gamma_S = 1e-4;
   p->mg_max_cycles = 50;
   p->mg_transfer = SDCEF_MG_OPERATOR;
+  p->ion_scheme = SDCEF_ION_GODUNOV;
   p->bc_electron = SDCEF_BC_ABSORBING;
   p->threads_per_column = 0;
   p->guess_newton_cap = 16;
@@ -385,6 +388,42 @@ int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* p
   return SDCEF_SUCCESS;
 }
 
+int sdcef_ion_provisional_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* phi,
+                                const double* n_prev, double kappa_ion, double* scratch,
+                                double* n_ion_out) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = validate_batch(ctx, b, false);
+  if (rc) return rc;
+  if (b->ncol == 0) return SDCEF_SUCCESS;
+  if (!phi || !n_ion_out || !scratch || !(kappa_ion >= 0.0) || !std::isfinite(kappa_ion))
+    return set_err(SDCEF_ERR_INVALID, "ion_provisional: bad arguments");
+  if (b->n_species == 0) return SDCEF_SUCCESS;
+  if (n_ion_out == b->n_ion || (n_prev && n_ion_out == n_prev))
+    return set_err(SDCEF_ERR_INVALID, "ion_provisional: n_ion_out aliases an input");
+  if (b->ncol > 0x7fffffff) return set_err(SDCEF_ERR_INVALID, "ion_provisional: too many columns");
+  IonProvArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ncol = b->ncol;
+  a.col_off = b->col_off;
+  a.length = b->length;
+  a.dt = b->dt;
+  a.vl = b->v_left;
+  a.vr = b->v_right;
+  a.T = b->T;
+  a.u = b->u_adv;
+  a.phi = phi;
+  a.n0 = b->n_ion;
+  a.nk = n_prev;
+  a.n_out = n_ion_out;
+  a.scratch = scratch;
+  a.nsp = b->n_species;
+  for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
+  a.kappa = kappa_ion;
+  cudaError_t e = launch_ion_provisional(a, ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  return SDCEF_SUCCESS;
+}
+
 int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
                         const double* phi, double kappa_ion, double* j_pos, double* j_neg) {
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
@@ -429,12 +468,23 @@ int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kapp
     return set_err(SDCEF_ERR_INVALID, "sdc_sweep: bad arguments");
   if (!out || !out->ne_out || !out->phi_out) return set_err(SDCEF_ERR_INVALID, "result: ne_out / phi_out is NULL");
   int launches = 0;
+  const bool godunov = ctx->p.ion_scheme == SDCEF_ION_GODUNOV;
+  // buffer stride from the context capacity: the cell count lives on the device
+  const size_t plane = (size_t)b->n_species * (size_t)ctx->max_cells;
   for (int k = 0; k < k_max; ++k) {
     const double* phi_field = (k == 0) ? b->phi_old : out->phi_out;
-    rc = sdcef_ion_update_batch(ctx, b, phi_field, kappa_ion, n_ion_work);
+    // Godunov: provisional ions ping-pong between two halves of the work
+    // buffer (the previous iteration's are n^(k)); the Thomas scratch follows
+    double* prov = godunov ? n_ion_work + (size_t)(k & 1) * plane : n_ion_work;
+    if (godunov)
+      rc = sdcef_ion_provisional_batch(ctx, b, phi_field,
+                                       k == 0 ? nullptr : n_ion_work + (size_t)((k - 1) & 1) * plane,
+                                       kappa_ion, n_ion_work + 2 * plane, prov);
+    else
+      rc = sdcef_ion_update_batch(ctx, b, phi_field, kappa_ion, prov);
     if (rc) return rc;
     sdcef_batch bk = *b;
-    bk.n_ion = b->n_species > 0 ? n_ion_work : b->n_ion;
+    bk.n_ion = b->n_species > 0 ? prov : b->n_ion;
     if (k > 0) {
       bk.ne_guess = out->ne_out;
       bk.phi_guess = out->phi_out;

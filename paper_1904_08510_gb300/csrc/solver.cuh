@@ -173,6 +173,19 @@ struct IonArgs {
 };
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st);
 
+// Provisional ions with the paper's transport (second-order Godunov
+// advection, implicit diffusion, SDC diffusion correction).
+struct IonProvArgs {
+  int64_t ncol;
+  const int64_t* col_off;
+  const double *length, *dt, *vl, *vr, *T, *u, *phi, *n0, *nk;
+  double *n_out, *scratch;
+  int nsp;
+  int val[SDCEF_MAX_SPECIES];
+  double kappa;
+};
+cudaError_t launch_ion_provisional(const IonProvArgs& a, cudaStream_t st);
+
 // Charge flux through every face of every column (Sec. 4.4).
 struct CurrentArgs {
   int64_t ncol;
@@ -1517,6 +1530,92 @@ __global__ void ion_update_kernel(IonArgs a) {
       }
       no[i] = ni[i] - r * (fr - fl);
     }
+  }
+}
+
+// Provisional ion densities of an SDC iteration (Sec. 3.1, Algorithm 1), per
+// species: (I - dt D) n~ = n^n - (dt/h)(F_{i+1/2} - F_{i-1/2}) + (dt/2)(D n^n
+// - D n^(k)). F = w n_face with the effective velocity w = U_f + nu kappa E_f
+// and the second-order Godunov (MUSCL) face state: the upwind cell value
+// extrapolated by (1 -+ w dt/h)/2 times its monotonized-central limited
+// difference (zero in the end cells); electrodes pass the outgoing drift of
+// the edge cell only. D: Einstein diffusivity kappa k_B T_f / (|nu| e), no
+// flux through the electrodes. One CTA per column: the right-hand side with
+// thread-strided cells, then the tridiagonal solve by Thomas on one thread
+// (eliminated super-diagonal in scratch, right-hand side in place).
+__device__ __forceinline__ double mc_limited(double dm, double dp) {
+  if (dm * dp <= 0.0) return 0.0;
+  double m = fmin(2.0 * fabs(dm), 2.0 * fabs(dp));
+  m = fmin(m, 0.5 * fabs(dm + dp));
+  return dm > 0.0 ? m : -m;
+}
+
+__global__ void ion_provisional_kernel(IonProvArgs a) {
+  const int64_t c = blockIdx.x;
+  if (c >= a.ncol) return;
+  const int64_t off = a.col_off[c];
+  const int N = (int)(a.col_off[c + 1] - off);
+  const int64_t cells = a.col_off[a.ncol];
+  if (N < 2) {
+    for (int s = 0; s < a.nsp; ++s)
+      for (int i = threadIdx.x; i < N; i += blockDim.x)
+        a.n_out[(int64_t)s * cells + off + i] = a.n0[(int64_t)s * cells + off + i];
+    return;
+  }
+  const double h = a.length[c] / N, dt = a.dt[c];
+  const double* p = a.phi + off;
+  const double* T = a.T + off;
+  const double* U = a.u ? a.u + off : nullptr;
+  const double GL = (-8.0 * a.vl[c] + 9.0 * p[0] - p[1]) / (3.0 * h);
+  const double GR = (8.0 * a.vr[c] - 9.0 * p[N - 1] + p[N - 2]) / (3.0 * h);
+  double* cp = a.scratch + off;
+  for (int s = 0; s < a.nsp; ++s) {
+    const double* n0 = a.n0 + (int64_t)s * cells + off;
+    const double* nk = a.nk ? a.nk + (int64_t)s * cells + off : n0;
+    double* out = a.n_out + (int64_t)s * cells + off;
+    const double nu = (double)a.val[s];
+    const double Dc = nu != 0.0 ? a.kappa * kKb / (fabs(nu) * kQe) : 0.0;
+    auto slope = [&](int i) {
+      return (i == 0 || i == N - 1) ? 0.0 : mc_limited(n0[i] - n0[i - 1], n0[i + 1] - n0[i]);
+    };
+    auto flux = [&](int f) {
+      if (f == 0 || f == N) {
+        const double w = (U ? U[f == 0 ? 0 : N - 1] : 0.0) + nu * a.kappa * (f == 0 ? -GL : -GR);
+        const bool out_ = f == 0 ? w < 0.0 : w > 0.0;
+        return out_ ? w * (f == 0 ? n0[0] : n0[N - 1]) : 0.0;
+      }
+      const int i = f - 1;
+      const double w = (U ? 0.5 * (U[i] + U[i + 1]) : 0.0) - nu * a.kappa * (p[i + 1] - p[i]) / h;
+      const double cfl = w * dt / h;
+      const double nf = w >= 0.0 ? n0[i] + 0.5 * (1.0 - cfl) * slope(i)
+                                 : n0[i + 1] - 0.5 * (1.0 + cfl) * slope(i + 1);
+      return w * nf;
+    };
+    auto dface = [&](int f) { return (f == 0 || f == N) ? 0.0 : Dc * 0.5 * (T[f - 1] + T[f]); };
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double Dl = dface(i), Dr = dface(i + 1);
+      const double dn0 = (Dr * ((i + 1 < N ? n0[i + 1] : n0[i]) - n0[i]) -
+                          Dl * (n0[i] - (i > 0 ? n0[i - 1] : n0[i]))) / (h * h);
+      const double dnk = (Dr * ((i + 1 < N ? nk[i + 1] : nk[i]) - nk[i]) -
+                          Dl * (nk[i] - (i > 0 ? nk[i - 1] : nk[i]))) / (h * h);
+      out[i] = n0[i] - (dt / h) * (flux(i + 1) - flux(i)) + 0.5 * dt * (dn0 - dnk);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sub = 0.0, sup = -dt * dface(1) / (h * h);
+      double piv = 1.0 - sub - sup;
+      cp[0] = sup / piv;
+      out[0] = out[0] / piv;
+      for (int i = 1; i < N; ++i) {
+        sub = -dt * dface(i) / (h * h);
+        sup = -dt * dface(i + 1) / (h * h);
+        piv = (1.0 - sub - sup) - sub * cp[i - 1];
+        cp[i] = sup / piv;
+        out[i] = (out[i] - sub * out[i - 1]) / piv;
+      }
+      for (int i = N - 2; i >= 0; --i) out[i] = out[i] - cp[i] * out[i + 1];
+    }
+    __syncthreads();
   }
 }
 

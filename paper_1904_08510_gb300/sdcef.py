@@ -22,6 +22,7 @@ STATUS_OK, STATUS_MAX_NEWTON, STATUS_MAX_KRYLOV, STATUS_LINESEARCH_FAIL, \
 FP64, MIXED, MIXED_DF = 0, 1, 2
 PREC_EXACT, PREC_RECAST, PREC_NONE, PREC_MG = 0, 1, 2, 3
 MG_OPERATOR, MG_LINEAR = 0, 1
+ION_DRIFT_UPWIND, ION_GODUNOV = 0, 1
 BC_ABSORBING, BC_ZERO_GRADIENT = 0, 1
 MAX_RESTART = 32
 MAX_SPECIES = 16
@@ -32,6 +33,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count",
            "sdcef_solve_batch_noalloc", "sdcef_ion_update_batch", "sdcef_sdc_sweep",
            "sdcef_autotune", "sdcef_bernoulli_batch", "sdcef_current_batch",
+           "sdcef_ion_provisional_batch",
            "sdcef_mlp_create", "sdcef_mlp_destroy",
            "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
@@ -51,7 +53,7 @@ class Params(C.Structure):
                 ("bc_electron", C.c_int), ("threads_per_column", C.c_int),
                 ("guess_newton_cap", C.c_int), ("guess_reject_ratio", C.c_double),
                 ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
-                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int)]
+                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int), ("ion_scheme", C.c_int)]
 
 
 class BatchC(C.Structure):
@@ -101,6 +103,7 @@ def lib():
         L.sdcef_solve_batch_noalloc.argtypes = [P, B, R, C.c_int, vp]
         L.sdcef_ion_update_batch.argtypes = [vp, B, vp, C.c_double, vp]
         L.sdcef_current_batch.argtypes = [vp, B, vp, vp, C.c_double, vp, vp]
+        L.sdcef_ion_provisional_batch.argtypes = [vp, B, vp, vp, C.c_double, vp, vp]
         L.sdcef_sdc_sweep.argtypes = [vp, B, C.c_int, C.c_double, vp, R]
         L.sdcef_ion_update_batch.restype = C.c_int
         L.sdcef_autotune.argtypes = [vp, B, R, C.c_int, C.POINTER(C.c_int), vp]
@@ -308,12 +311,31 @@ class Solver:
                                          float(kappa_ion), _ptr(jp), _ptr(jn)))
         return jp, jn
 
+    def sweep_work(self, db: DeviceBatch):
+        """Device scratch of sdcef_sdc_sweep for this context's ion scheme:
+        (2 n_species + 1) x max_cells doubles (Godunov) or n_species x cells."""
+        import torch
+        nsp = int(db.tensors["n_ion"].shape[0]) if db.tensors["n_ion"].dim() > 1 else 1
+        n = (2 * nsp + 1) * self.max_cells if self.params.ion_scheme == ION_GODUNOV else nsp * db.ncells
+        return torch.empty(n, dtype=torch.float64, device=db.tensors["ne_old"].device)
+
+    def ion_provisional(self, db: DeviceBatch, phi, n_prev=None, kappa_ion: float = 4e-3):
+        """sdcef_ion_provisional_batch: provisional ions with the paper's
+        transport; n_prev = the previous SDC iterate (None: n^n)."""
+        import torch
+        out = torch.empty_like(db.tensors["n_ion"])
+        scratch = torch.empty(db.ncells, dtype=torch.float64, device=phi.device)
+        bs = db.cstruct()
+        _check(lib().sdcef_ion_provisional_batch(self.h, C.byref(bs), _ptr(phi), _ptr(n_prev),
+                                                 float(kappa_ion), _ptr(scratch), _ptr(out)))
+        return out
+
     def sdc_sweep(self, db: DeviceBatch, k_max: int = 4, kappa_ion: float = 4e-3,
                   work=None, out: dict | None = None) -> dict:
-        """sdcef_sdc_sweep: k_max SDC iterations of the electric solve."""
-        import torch
+        """sdcef_sdc_sweep: k_max SDC iterations of the electric solve; work, if
+        given, as sized by sweep_work."""
         out = out or self.alloc_result(db)
-        work = torch.empty_like(db.tensors["n_ion"]) if work is None else work
+        work = self.sweep_work(db) if work is None else work
         bs = db.cstruct()
         rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), _ptr(out["status"]),
                      _ptr(out["newton_it"]), _ptr(out["krylov_it"]), _ptr(out["res_evals"]),
