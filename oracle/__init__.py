@@ -40,10 +40,14 @@ class Params(C.Structure):
                 ("restart_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int),
                 ("max_linesearch", C.c_int), ("bc_electron", C.c_int), ("precond", C.c_int),
                 ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
-                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int)]
+                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int),
+                ("transport", C.c_int), ("tab_mu", C.c_void_p), ("tab_D", C.c_void_p),
+                ("tab_nc", C.c_int), ("tab_nx", C.c_int), ("tab_en_max", C.c_double),
+                ("T_in", C.c_double), ("T_max", C.c_double), ("gas_molar_mass", C.c_double)]
 
 PREC_NONE, PREC_RECAST, PREC_EXACT, PREC_MG = 0, 1, 2, 3
 MG_OPERATOR, MG_LINEAR = 0, 1
+TRANSPORT_CONSTANT, TRANSPORT_TABLE = 0, 1
 
 
 class _Batch(C.Structure):
@@ -51,7 +55,7 @@ class _Batch(C.Structure):
                 ("dt", C.c_void_p), ("v_left", C.c_void_p), ("v_right", C.c_void_p),
                 ("ne_old", C.c_void_p), ("phi_old", C.c_void_p), ("n_species", C.c_int),
                 ("valence", C.c_void_p), ("n_ion", C.c_void_p), ("T", C.c_void_p),
-                ("u_adv", C.c_void_p), ("i_re", C.c_void_p)]
+                ("u_adv", C.c_void_p), ("i_re", C.c_void_p), ("rho", C.c_void_p)]
 
 
 def default_params(**kw) -> Params:
@@ -63,9 +67,34 @@ def default_params(**kw) -> Params:
     p = dict(eps_F=1e-10, eps_X=0.0, gamma=1e-4, mobility=0.4, ls_alpha=1e-4, eps_r=1.0,
              restart_m=30, max_newton=50, max_krylov=200, max_linesearch=20,
              bc_electron=BC_ABSORBING, precond=PREC_RECAST, mg_gamma_A=1e-4, mg_gamma_S=1e-4,
-             mg_max_cycles=100, mg_transfer=MG_OPERATOR)
+             mg_max_cycles=100, mg_transfer=MG_OPERATOR, transport=TRANSPORT_CONSTANT,
+             gas_molar_mass=0.028, T_in=300.0, T_max=2000.0)
+    table = kw.pop("table", None)
     p.update(kw)
-    return Params(**p)
+    P = Params(**p)
+    if table is not None:
+        set_table(P, table)
+    return P
+
+
+def tab_lookup(t, en_max, c, x):
+    """The oracle's bilinear table interpolation at (c, E/N = x Td)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    return lib().or_tab_lookup(_ptr(t), t.shape[0], t.shape[1], float(en_max), float(c), float(x))
+
+
+def set_table(P, table):
+    """Point P at a transport table (dict mu, D [nc, nx] arrays, en_max_td,
+    T_in, T_max) and switch P to TRANSPORT_TABLE. The arrays are kept alive on P."""
+    mu = np.ascontiguousarray(table["mu"], dtype=np.float64)
+    D = np.ascontiguousarray(table["D"], dtype=np.float64)
+    P._keep = (mu, D)
+    P.transport = TRANSPORT_TABLE
+    P.tab_mu, P.tab_D = mu.ctypes.data, D.ctypes.data
+    P.tab_nc, P.tab_nx = mu.shape
+    P.tab_en_max = float(table["en_max_td"])
+    P.T_in, P.T_max = float(table["T_in"]), float(table["T_max"])
+    return P
 
 
 def build(force: bool = False) -> str:
@@ -108,6 +137,8 @@ def lib():
         L.or_max_threads.restype = C.c_int
         L.or_ion_update_batch.argtypes = [B, vp, C.c_double, vp]
         L.or_current_batch.argtypes = [P, B, vp, vp, C.c_double, vp, vp]
+        L.or_tab_lookup.restype = C.c_double
+        L.or_tab_lookup.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]
         L.or_ion_provisional_batch.argtypes = [B, vp, vp, C.c_double, vp]
         _lib = L
     return _lib
@@ -137,11 +168,12 @@ class _Keep:
         self.T = _f64(batch.T)
         self.u_adv = None if batch.u_adv is None else _f64(batch.u_adv)
         self.i_re = None if batch.i_re is None else _f64(batch.i_re)
+        self.rho = None if getattr(batch, "rho", None) is None else _f64(batch.rho)
         self.s = _Batch(self.col_off.shape[0] - 1, _ptr(self.col_off), _ptr(self.length),
                         _ptr(self.dt), _ptr(self.v_left), _ptr(self.v_right),
                         _ptr(self.ne_old), _ptr(self.phi_old), self.n_ion.shape[0],
                         _ptr(self.valence), _ptr(self.n_ion), _ptr(self.T),
-                        _ptr(self.u_adv), _ptr(self.i_re))
+                        _ptr(self.u_adv), _ptr(self.i_re), _ptr(self.rho))
 
 
 def bern(x: float) -> float:

@@ -83,6 +83,15 @@ typedef struct {
   double mg_gamma_S;    /* precond 3: V-cycle tolerance of the S~ block; <= 0: exact */
   int mg_max_cycles;    /* precond 3: V-cycles per block solve at most */
   int mg_transfer;      /* precond 3: 0 operator-dependent, 1 linear (see below) */
+  /* electron transport: 0 constant mobility with Einstein D; 1 tables of mu and D
+     over the progress variable c and the reduced field E/N (Sec. 2.2) */
+  int transport;
+  const double *tab_mu, *tab_D;   /* [tab_nc][tab_nx], row c_k = k/(nc-1), column
+                                     E/N = j tab_en_max/(nx-1) Td */
+  int tab_nc, tab_nx;
+  double tab_en_max;              /* Td (1 Td = 1e-21 V m^2) */
+  double T_in, T_max;             /* c = (T - T_in) / (T_max - T_in), clamped to [0, 1] */
+  double gas_molar_mass;          /* kg/mol: N = rho N_A / W */
 } or_params;
 
 typedef struct {
@@ -97,7 +106,54 @@ typedef struct {
   double h, dt, vl, vr, mu, eps_r;
   int bc;
   const double *fe, *fphi, *D, *U;   /* U may be NULL (no advection) */
+  /* transport tables (NULL: constant mu, D per cell) and, for them, the
+     progress variable and background gas density of every cell */
+  const double *tab_mu, *tab_D;
+  int tab_nc, tab_nx;
+  double tab_en_max;
+  const double *cprog, *Ngas;
 } or_col;
+
+#define OR_NA 6.02214076e23        /* Avogadro constant, 1/mol     */
+
+/* Bilinear interpolation of a [nc][nx] table with nodes c_k = k/(nc-1) and
+ * x_j = j en_max/(nx-1), at (c, x) clamped to the table. */
+double or_tab_lookup(const double* t, int nc, int nx, double en_max, double c, double x);
+static double tab_lookup(const double* t, int nc, int nx, double en_max, double c, double x) {
+  return or_tab_lookup(t, nc, nx, en_max, c, x);
+}
+double or_tab_lookup(const double* t, int nc, int nx, double en_max, double c, double x) {
+  double tc = c * (nc - 1), tx = x / en_max * (nx - 1);
+  if (tc < 0.0) tc = 0.0;
+  if (tc > nc - 1) tc = nc - 1;
+  if (tx < 0.0) tx = 0.0;
+  if (tx > nx - 1) tx = nx - 1;
+  int ic = (int)floor(tc), jx = (int)floor(tx);
+  if (ic > nc - 2) ic = nc - 2;
+  if (jx > nx - 2) jx = nx - 2;
+  double wc = tc - ic, wx = tx - jx;
+  const double* r0 = t + (size_t)ic * nx;
+  const double* r1 = r0 + nx;
+  return (1.0 - wc) * ((1.0 - wx) * r0[jx] + wx * r0[jx + 1]) +
+         wc * ((1.0 - wx) * r1[jx] + wx * r1[jx + 1]);
+}
+
+/* Electron mobility and diffusivity at the face between cells i and k
+ * (k = i + 1; k = i for an electrode face) where the potential gradient is G:
+ * constant mu and the mean of the cells' Einstein D, or the tables at the
+ * face means of c and N and E/N = |G| / N (Sec. 2.2). */
+static void face_transport(const or_col* c, int i, int k, double G, double* mu, double* D) {
+  if (!c->tab_mu) {
+    *mu = c->mu;
+    *D = k == i ? c->D[i] : 0.5 * (c->D[i] + c->D[k]);
+    return;
+  }
+  double cf = 0.5 * (c->cprog[i] + c->cprog[k]);
+  double Nf = 0.5 * (c->Ngas[i] + c->Ngas[k]);
+  double en = fabs(G) / Nf / 1e-21;
+  *mu = tab_lookup(c->tab_mu, c->tab_nc, c->tab_nx, c->tab_en_max, cf, en);
+  *D = tab_lookup(c->tab_D, c->tab_nc, c->tab_nx, c->tab_en_max, cf, en);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Bernoulli function B(x) = x / (e^x - 1) and its derivative.              */
@@ -152,11 +208,14 @@ static double dgrad_right(const or_col* c, const double* psi) {
 void or_residual_psi(const or_col* c, const double* ne, const double* psi,
                      double* Fe, double* Fp) {
   const int N = c->n;
-  const double h = c->h, dt = c->dt, mu = c->mu, g0 = grad0(c);
+  const double h = c->h, dt = c->dt, g0 = grad0(c);
   const double kap = OR_EPS0 * c->eps_r / OR_E;
   double dL = dgrad_left(c, psi), dR = dgrad_right(c, psi);
-  double vL = (c->U ? c->U[0] : 0.0) + mu * (g0 + dL);
-  double vR = (c->U ? c->U[N - 1] : 0.0) + mu * (g0 + dR);
+  double muL, muR, Dd;
+  face_transport(c, 0, 0, g0 + dL, &muL, &Dd);
+  face_transport(c, N - 1, N - 1, g0 + dR, &muR, &Dd);
+  double vL = (c->U ? c->U[0] : 0.0) + muL * (g0 + dL);
+  double vR = (c->U ? c->U[N - 1] : 0.0) + muR * (g0 + dR);
   double GamL, GamR;
   if (c->bc == OR_BC_ZERO_GRADIENT) {
     GamL = vL * ne[0];
@@ -172,9 +231,10 @@ void or_residual_psi(const or_col* c, const double* ne, const double* psi,
       gam_next = GamR;
       d_next = dR;
     } else {
-      double Df = 0.5 * (c->D[i] + c->D[i + 1]);
       d_next = (psi[i + 1] - psi[i]) / h;
-      double v = face_u(c, i) + mu * (g0 + d_next);
+      double muf, Df;
+      face_transport(c, i, i + 1, g0 + d_next, &muf, &Df);
+      double v = face_u(c, i) + muf * (g0 + d_next);
       double Pe = v * h / Df;
       gam_next = (Df / h) * (or_bern(-Pe) * ne[i] - or_bern(Pe) * ne[i + 1]);
     }
@@ -205,7 +265,7 @@ typedef struct { double *sub, *dia, *sup; } or_tri;
 void or_jacobian_col(const or_col* c, const double* ne, const double* phi,
                      or_tri A, or_tri B, or_tri L) {
   const int N = c->n;
-  const double h = c->h, dt = c->dt, mu = c->mu, r = dt / h;
+  const double h = c->h, dt = c->dt, r = dt / h;
   const double kap = OR_EPS0 * c->eps_r / OR_E;
   for (int i = 0; i < N; ++i) {
     A.sub[i] = A.sup[i] = B.sub[i] = B.sup[i] = L.sub[i] = L.sup[i] = 0.0;
@@ -215,13 +275,16 @@ void or_jacobian_col(const or_col* c, const double* ne, const double* phi,
   }
   /* interior faces i+1/2 */
   for (int i = 0; i + 1 < N; ++i) {
-    double Df = 0.5 * (c->D[i] + c->D[i + 1]);
-    double v = face_u(c, i) + mu * (phi[i + 1] - phi[i]) / h;
+    /* with transport tables mu and D are frozen at the current gradient: the
+       derivatives below are those of the flux with fixed coefficients */
+    double muf, Df;
+    face_transport(c, i, i + 1, (phi[i + 1] - phi[i]) / h, &muf, &Df);
+    double v = face_u(c, i) + muf * (phi[i + 1] - phi[i]) / h;
     double Pe = v * h / Df;
     double dG_dn0 = (Df / h) * or_bern(-Pe);
     double dG_dn1 = -(Df / h) * or_bern(Pe);
     /* dGam/dPe * dPe/dphi_{i+1}; dPe/dphi_{i+1} = mu / Df */
-    double dG_dp1 = (mu / h) * (-or_bern_deriv(-Pe) * ne[i] - or_bern_deriv(Pe) * ne[i + 1]);
+    double dG_dp1 = (muf / h) * (-or_bern_deriv(-Pe) * ne[i] - or_bern_deriv(Pe) * ne[i + 1]);
     double dG_dp0 = -dG_dp1;
     /* row i carries -r*Gam_{i+1/2}; row i+1 carries +r*Gam_{i+1/2} */
     A.dia[i] += -r * dG_dn0;  A.sup[i] += -r * dG_dn1;
@@ -235,12 +298,14 @@ void or_jacobian_col(const or_col* c, const double* ne, const double* phi,
   /* left electrode face: row 0 carries +r*GamL and -kap*GL/h */
   {
     double GL = (-8.0 * c->vl + 9.0 * phi[0] - phi[1]) / (3.0 * h);
-    double vL = (c->U ? c->U[0] : 0.0) + mu * GL;
+    double muL, Dd;
+    face_transport(c, 0, 0, GL, &muL, &Dd);
+    double vL = (c->U ? c->U[0] : 0.0) + muL * GL;
     int active = (c->bc == OR_BC_ZERO_GRADIENT) || vL < 0.0;
     if (active) {
       A.dia[0] += r * vL;
-      B.dia[0] += r * ne[0] * mu * (9.0 / (3.0 * h));
-      B.sup[0] += r * ne[0] * mu * (-1.0 / (3.0 * h));
+      B.dia[0] += r * ne[0] * muL * (9.0 / (3.0 * h));
+      B.sup[0] += r * ne[0] * muL * (-1.0 / (3.0 * h));
     }
     L.dia[0] += -kap / h * (9.0 / (3.0 * h));
     L.sup[0] += -kap / h * (-1.0 / (3.0 * h));
@@ -248,12 +313,14 @@ void or_jacobian_col(const or_col* c, const double* ne, const double* phi,
   /* right electrode face: row N-1 carries -r*GamR and +kap*GR/h */
   {
     double GR = (8.0 * c->vr - 9.0 * phi[N - 1] + phi[N - 2]) / (3.0 * h);
-    double vR = (c->U ? c->U[N - 1] : 0.0) + mu * GR;
+    double muR, Dd;
+    face_transport(c, N - 1, N - 1, GR, &muR, &Dd);
+    double vR = (c->U ? c->U[N - 1] : 0.0) + muR * GR;
     int active = (c->bc == OR_BC_ZERO_GRADIENT) || vR > 0.0;
     if (active) {
       A.dia[N - 1] += -r * vR;
-      B.dia[N - 1] += -r * ne[N - 1] * mu * (-9.0 / (3.0 * h));
-      B.sub[N - 1] += -r * ne[N - 1] * mu * (1.0 / (3.0 * h));
+      B.dia[N - 1] += -r * ne[N - 1] * muR * (-9.0 / (3.0 * h));
+      B.sub[N - 1] += -r * ne[N - 1] * muR * (1.0 / (3.0 * h));
     }
     L.dia[N - 1] += kap / h * (-9.0 / (3.0 * h));
     L.sub[N - 1] += kap / h * (1.0 / (3.0 * h));
@@ -1063,11 +1130,16 @@ typedef struct {
   const int* valence;
   const double* n_ion;          /* [n_species][cells] */
   const double *T, *u_adv, *i_re;
+  const double* rho;            /* [cells] gas density (transport tables only) */
 } or_batch;
 
 /* Per-column derived inputs: f_e, f_phi and D (Einstein relation). */
 static void build_col(const or_params* P, const or_batch* b, int64_t c, or_col* col,
-                      double* fe, double* fphi, double* D) {
+                      double* buf /* 5 n */) {
+  double *fe = buf, *fphi = buf + (b->col_off[c + 1] - b->col_off[c]);
+  double* D = fphi + (b->col_off[c + 1] - b->col_off[c]);
+  double* cprog = D + (b->col_off[c + 1] - b->col_off[c]);
+  double* Ngas = cprog + (b->col_off[c + 1] - b->col_off[c]);
   int64_t a = b->col_off[c], e = b->col_off[c + 1];
   int n = (int)(e - a);
   int64_t ncells = b->col_off[b->ncol];
@@ -1090,6 +1162,22 @@ static void build_col(const or_params* P, const or_batch* b, int64_t c, or_col* 
   col->fphi = fphi;
   col->D = D;
   col->U = b->u_adv ? b->u_adv + a : NULL;
+  col->tab_mu = col->tab_D = NULL;
+  col->cprog = col->Ngas = NULL;
+  if (P->transport == 1) {
+    for (int i = 0; i < n; ++i) {
+      double cp = (b->T[a + i] - P->T_in) / (P->T_max - P->T_in);
+      cprog[i] = cp < 0.0 ? 0.0 : (cp > 1.0 ? 1.0 : cp);
+      Ngas[i] = b->rho[a + i] * OR_NA / P->gas_molar_mass;
+    }
+    col->tab_mu = P->tab_mu;
+    col->tab_D = P->tab_D;
+    col->tab_nc = P->tab_nc;
+    col->tab_nx = P->tab_nx;
+    col->tab_en_max = P->tab_en_max;
+    col->cprog = cprog;
+    col->Ngas = Ngas;
+  }
 }
 
 void or_residual_batch(const or_params* P, const or_batch* b, const double* ne,
@@ -1097,9 +1185,9 @@ void or_residual_batch(const or_params* P, const or_batch* b, const double* ne,
   for (int64_t c = 0; c < b->ncol; ++c) {
     int n = (int)(b->col_off[c + 1] - b->col_off[c]);
     if (n < 2) continue;
-    double* tmp = (double*)malloc(sizeof(double) * 3 * n);
+    double* tmp = (double*)malloc(sizeof(double) * 5 * n);
     or_col col;
-    build_col(P, b, c, &col, tmp, tmp + n, tmp + 2 * n);
+    build_col(P, b, c, &col, tmp);
     int64_t a = b->col_off[c];
     or_residual_col(&col, ne + a, phi + a, Fe + a, Fp + a);
     free(tmp);
@@ -1113,9 +1201,9 @@ void or_jacobian_batch(const or_params* P, const or_batch* b, const double* ne,
   for (int64_t c = 0; c < b->ncol; ++c) {
     int n = (int)(b->col_off[c + 1] - b->col_off[c]);
     if (n < 2) continue;
-    double* tmp = (double*)malloc(sizeof(double) * 3 * n);
+    double* tmp = (double*)malloc(sizeof(double) * 5 * n);
     or_col col;
-    build_col(P, b, c, &col, tmp, tmp + n, tmp + 2 * n);
+    build_col(P, b, c, &col, tmp);
     int64_t a = b->col_off[c];
     or_tri A = {A3 + a, A3 + ncells + a, A3 + 2 * ncells + a};
     or_tri B = {B3 + a, B3 + ncells + a, B3 + 2 * ncells + a};
@@ -1130,11 +1218,11 @@ void or_prec_apply_col(const or_params* P, const or_batch* b, int64_t c, const d
                        const double* phi, const double* v1, const double* v2, double* x1,
                        double* x2, int* cycles /* precond 3: V-cycles used, or NULL */) {
   int n = (int)(b->col_off[c + 1] - b->col_off[c]);
-  double* tmp = (double*)malloc(sizeof(double) * 19 * n);
+  double* tmp = (double*)malloc(sizeof(double) * 21 * n);
   or_col col;
-  build_col(P, b, c, &col, tmp, tmp + n, tmp + 2 * n);
+  build_col(P, b, c, &col, tmp);
   int64_t a = b->col_off[c];
-  double* t = tmp + 3 * n;
+  double* t = tmp + 5 * n;
   or_tri A = {t, t + n, t + 2 * n}, B = {t + 3 * n, t + 4 * n, t + 5 * n},
          L = {t + 6 * n, t + 7 * n, t + 8 * n}, S = {t + 9 * n, t + 10 * n, t + 11 * n};
   or_jacobian_col(&col, ne + a, phi + a, A, B, L);
@@ -1178,9 +1266,9 @@ void or_solve_batch(const or_params* P, const or_batch* b, const double* ne_gues
       st.status = OR_BAD_INPUT;
       for (int i = 0; i < n; ++i) { ne_out[a + i] = b->ne_old[a + i]; phi_out[a + i] = b->phi_old[a + i]; }
     } else {
-      double* tmp = (double*)malloc(sizeof(double) * 3 * n);
+      double* tmp = (double*)malloc(sizeof(double) * 5 * n);
       or_col col;
-      build_col(P, b, c, &col, tmp, tmp + n, tmp + 2 * n);
+      build_col(P, b, c, &col, tmp);
       or_jfnk_col(P, &col, b->ne_old + a, b->phi_old + a,
                   ne_guess ? ne_guess + a : NULL, phi_guess ? phi_guess + a : NULL,
                   ne_out + a, phi_out + a, &st);
@@ -1353,10 +1441,10 @@ void or_current_batch(const or_params* P, const or_batch* b, const double* ne,
     int64_t f0 = a + c;
     for (int f = 0; f <= n; ++f) { j_pos[f0 + f] = 0.0; j_neg[f0 + f] = 0.0; }
     if (n < 2) continue;
-    double* tmp = (double*)malloc(sizeof(double) * 3 * n);
+    double* tmp = (double*)malloc(sizeof(double) * 5 * n);
     or_col col;
-    build_col(P, b, c, &col, tmp, tmp + n, tmp + 2 * n);
-    const double h = col.h, mu = col.mu;
+    build_col(P, b, c, &col, tmp);
+    const double h = col.h;
     const double* p = phi + a;
     const double* x = ne + a;
     const double* U = col.U;
@@ -1366,14 +1454,17 @@ void or_current_batch(const or_params* P, const or_batch* b, const double* ne,
     for (int f = 0; f <= n; ++f) {
       double gam;
       if (f == 0 || f == n) {
-        double v = f == 0 ? (U ? U[0] : 0.0) + mu * GL : (U ? U[n - 1] : 0.0) + mu * GR;
+        double mub, Db;
+        face_transport(&col, f == 0 ? 0 : n - 1, f == 0 ? 0 : n - 1, f == 0 ? GL : GR, &mub, &Db);
+        double v = f == 0 ? (U ? U[0] : 0.0) + mub * GL : (U ? U[n - 1] : 0.0) + mub * GR;
         double ned = f == 0 ? x[0] : x[n - 1];
         int out = f == 0 ? v < 0.0 : v > 0.0;
         gam = (col.bc == OR_BC_ZERO_GRADIENT || out) ? v * ned : 0.0;
       } else {
         int i = f - 1;
-        double Df = 0.5 * (col.D[i] + col.D[i + 1]);
-        double v = face_u(&col, i) + mu * (p[i + 1] - p[i]) / h;
+        double muf, Df;
+        face_transport(&col, i, i + 1, (p[i + 1] - p[i]) / h, &muf, &Df);
+        double v = face_u(&col, i) + muf * (p[i + 1] - p[i]) / h;
         double Pe = v * h / Df;
         gam = (Df / h) * (or_bern(-Pe) * x[i] - or_bern(Pe) * x[i + 1]);
       }

@@ -168,6 +168,38 @@ def uniform_batch(ncol: int, n: int, *, ne: float, n_ion: float, T: float, v_lef
 KAPPA_ION = 4e-3   # m^2/(V s): H3O+ mobility implied by the relaxation-time table (Sec. 4.4)
 
 
+def transport_table(nc: int = 21, nx: int = 161, en_max_td: float = 400.0, t_in: float = 300.0,
+                    t_max: float = 2000.0, mu_th: float = 0.4, e_mu: float = 20.0) -> dict:
+    """Synthetic electron transport tables over the progress variable c and the
+    reduced field E/N, standing in for the BOLSIG+ tables of the paper (not
+    available): the thermal mobility mu_th (1 + (c - 1/2)/4) at low field,
+    falling as 1/sqrt(1 + (E/N / e_mu)^2) with field heating; D = mu eps_k
+    with the characteristic energy eps_k = k_B T(c)/e + 0.02 (E/N)^2 / (30 +
+    E/N) V (E/N in Td), i.e. Einstein's relation at low field. Nodes: c_k =
+    k/(nc - 1), E/N_j = j en_max/(nx - 1) Td."""
+    kb_e = 1.380649e-23 / 1.602176634e-19
+    c = np.linspace(0.0, 1.0, nc)[:, None]
+    x = np.linspace(0.0, en_max_td, nx)[None, :]
+    T = t_in + c * (t_max - t_in)
+    mu = mu_th * (1.0 + 0.25 * (c - 0.5)) / np.sqrt(1.0 + (x / e_mu) ** 2)
+    eps_k = kb_e * T + 0.02 * x ** 2 / (30.0 + x)
+    return {"mu": np.ascontiguousarray(mu), "D": np.ascontiguousarray(mu * eps_k),
+            "en_max_td": en_max_td, "T_in": t_in, "T_max": t_max}
+
+
+def constant_transport_table(mobility: float = 0.4, nc: int = 11, nx: int = 5,
+                             en_max_td: float = 400.0, t_in: float = 300.0,
+                             t_max: float = 2000.0) -> dict:
+    """The constant-mobility model written as a table: mu = mobility and
+    Einstein D = mobility k_B T(c)/e, linear in c and independent of E/N."""
+    kb_e = 1.380649e-23 / 1.602176634e-19
+    c = np.linspace(0.0, 1.0, nc)[:, None]
+    T = t_in + c * (t_max - t_in)
+    mu = np.full((nc, nx), mobility)
+    return {"mu": mu, "D": mobility * kb_e * T * np.ones((1, nx)), "en_max_td": en_max_td,
+            "T_in": t_in, "T_max": t_max}
+
+
 def sdc_batch(ncol: int, seed: int, *, n_cells: int = 1024, cfl: float = 0.5,
               kappa_ion: float = KAPPA_ION) -> Batch:
     """Columns of the "ragged" profile family with a fixed cell count and a time
