@@ -93,6 +93,14 @@ extern "C" {
 #define SDCEF_MG_LINEAR 1    /* linear interpolation (1/2, 1/2), R = P^T, coarse
                                 operator R T P                                      */
 
+/* electron transport model (Sec. 2.2) */
+#define SDCEF_TRANSPORT_CONSTANT 0  /* constant mobility, Einstein diffusivity mu k_B T / e */
+#define SDCEF_TRANSPORT_TABLE 1     /* mu and D from tables over the progress variable
+                                       c = (T - T_in)/(T_max - T_in) and the reduced field
+                                       |E|/N (sdcef_set_transport_table); FP64 with the
+                                       exact, recast or no preconditioner; 128 threads per
+                                       column; needs batch->rho                          */
+
 /* provisional charged species between SDC iterations (sdcef_sdc_sweep) */
 #define SDCEF_ION_DRIFT_UPWIND 0  /* electric drift only, first-order upwind, explicit */
 #define SDCEF_ION_GODUNOV 1       /* the transport of Sec. 3.1 / Algorithm 1: effective-
@@ -136,6 +144,8 @@ typedef struct {
   int mg_transfer;    /* SDCEF_PREC_MG: SDCEF_MG_OPERATOR | SDCEF_MG_LINEAR       */
   int ion_scheme;     /* provisional ions of sdcef_sdc_sweep: SDCEF_ION_GODUNOV |
                          SDCEF_ION_DRIFT_UPWIND                                 */
+  int transport;      /* SDCEF_TRANSPORT_CONSTANT | SDCEF_TRANSPORT_TABLE         */
+  double gas_molar_mass; /* kg/mol; background gas number density N = rho N_A / W */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -184,8 +194,23 @@ typedef struct {
  * judged after 16 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
  * blocks (the optimum of Sec. 4.2), at most 50 V-cycles per block solve and
  * operator-dependent transfers; the paper's ion transport in the SDC sweep
- * (SDCEF_ION_GODUNOV). */
+ * (SDCEF_ION_GODUNOV); constant electron transport, gas molar mass 0.028 kg/mol. */
 void sdcef_default_params(sdcef_params* p);
+
+/* Electron transport tables for SDCEF_TRANSPORT_TABLE (Sec. 2.2: mobility
+ * and diffusion coefficient tabulated against the progress variable c and the
+ * reduced field |E|/N, interpolated during the solve). mu, D: HOST arrays
+ * [nc][nx], row k at c = k/(nc - 1), column j at E/N = j en_max_td/(nx - 1)
+ * Td (1 Td = 1e-21 V m^2), m^2/(V s) and m^2/s, finite and positive; c of a
+ * cell is (T - T_in)/(T_max - T_in) clamped to [0, 1]. Bilinear interpolation,
+ * clamped at the table edges; a face takes the means of its cells' c and N and
+ * E/N = |dphi/dx| / N at the face. The finite-difference Jacobian-vector
+ * product carries the field dependence; the preconditioner is built with the
+ * coefficients frozen at the current iterate. The tables are copied to the
+ * device (allocated here, replacing earlier ones). nc, nx >= 2, en_max_td > 0,
+ * T_max > T_in; SDCEF_ERR_INVALID otherwise. */
+int sdcef_set_transport_table(sdcef_ctx* ctx, int nc, int nx, double en_max_td, double T_in,
+                              double T_max, const double* mu, const double* D);
 
 /* Create a solver context. max_cols, max_cells and max_col_cells bound every
  * later batch (columns, total cells, cells of the longest column); the

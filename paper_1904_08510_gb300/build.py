@@ -69,9 +69,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd.append("-DSDCEF_WITH_ORDER")
         cmd += ["-c", os.path.join(CSRC, "kern_inst.cu"), "-o", obj]
         jobs.append((obj, cmd))
-    obj = os.path.join(BUILD, "kern_mg.o")
-    jobs.append((obj, [nvcc, *ARCH, *FLAGS, "-DSDCEF_MG", "-c", os.path.join(CSRC, "kern_inst.cu"),
-                       "-o", obj]))
+    for var in ("MG", "TAB"):
+        obj = os.path.join(BUILD, f"kern_{var.lower()}.o")
+        jobs.append((obj, [nvcc, *ARCH, *FLAGS, f"-DSDCEF_{var}", "-c",
+                           os.path.join(CSRC, "kern_inst.cu"), "-o", obj]))
     for src in ("sdcef.cu", "noalloc.cu", "mlp.cu"):
         obj = os.path.join(BUILD, src.replace(".cu", "_host.o"))
         jobs.append((obj, [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]))

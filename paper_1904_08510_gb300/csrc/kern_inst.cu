@@ -7,12 +7,18 @@
 #include "solver.cuh"
 
 namespace sdcef_impl {
-#ifdef SDCEF_MG
+#if defined(SDCEF_MG)
 // the multigrid-preconditioner kernel (FP64, kMgTPB threads per column)
 cudaError_t launch_mg(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
   return launch_mg_t(a, grid, smem, st);
 }
 int occupancy_mg(size_t smem) { return occupancy_mg_t(smem); }
+#elif defined(SDCEF_TAB)
+// the transport-table kernel (FP64, kMgTPB threads per column)
+cudaError_t launch_tab(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
+  return launch_tab_t(a, grid, smem, st);
+}
+int occupancy_tab(size_t smem) { return occupancy_tab_t(smem); }
 #else
 template cudaError_t launch_t<SDCEF_TPB, SDCEF_KR, SDCEF_PR>(const KArgs&, int, size_t, cudaStream_t);
 template int occupancy_t<SDCEF_TPB, SDCEF_KR, SDCEF_PR>(size_t);

@@ -69,6 +69,8 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
                                          void* stream) {
   int rc = validate_params(p);
   if (rc) return rc;
+  if (p->transport != SDCEF_TRANSPORT_CONSTANT)
+    return report_error(SDCEF_ERR_INVALID, "noalloc: transport tables need a context");
   if (!b) return report_error(SDCEF_ERR_INVALID, "noalloc: batch is NULL");
   if (b->ncol < 0) return report_error(SDCEF_ERR_INVALID, "noalloc: ncol < 0");
   if (b->ncol == 0) return SDCEF_SUCCESS;
@@ -158,7 +160,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
 
   cudaStream_t st = (cudaStream_t)stream;
   const size_t smem = smem_bytes_prec(prec, tpb, m);
-  const int per_sm = occupancy_prec(prec, tpb, smem, p->precond);
+  const int per_sm = occupancy_prec(prec, tpb, smem, p->precond, SDCEF_TRANSPORT_CONSTANT);
   const int grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, a.ncol, nslots});
   // the queue counter must start at zero; everything else a call reads it writes first
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);

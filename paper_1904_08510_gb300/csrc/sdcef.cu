@@ -42,12 +42,17 @@ struct sdcef_ctx {
   // host-call staging
   char* stage;
   size_t stage_bytes;
+  // electron transport tables (mu then D, [nc][nx] each), device
+  double* tab;
+  int tab_nc, tab_nx;
+  double tab_en_max, tab_T_in, tab_T_max;
 };
 
 namespace {
 
 int tpb_for(const sdcef_params& p, int max_col_cells) {
   if (p.precond == SDCEF_PREC_MG) return kMgTPB;   // the multigrid kernel's fixed width
+  if (p.transport == SDCEF_TRANSPORT_TABLE) return kMgTPB;   // the table kernel's
   if (p.threads_per_column) return p.threads_per_column;
   (void)max_col_cells;
   return 128;
@@ -82,6 +87,16 @@ int check_params(const sdcef_params* p, int m_cap) {
   }
   if (p->ion_scheme != SDCEF_ION_GODUNOV && p->ion_scheme != SDCEF_ION_DRIFT_UPWIND)
     return set_err(SDCEF_ERR_INVALID, "params: ion_scheme");
+  if (p->transport != SDCEF_TRANSPORT_CONSTANT && p->transport != SDCEF_TRANSPORT_TABLE)
+    return set_err(SDCEF_ERR_INVALID, "params: transport");
+  if (p->transport == SDCEF_TRANSPORT_TABLE) {
+    if (p->precision != SDCEF_FP64)
+      return set_err(SDCEF_ERR_INVALID, "params: transport tables need precision FP64");
+    if (p->precond == SDCEF_PREC_MG)
+      return set_err(SDCEF_ERR_INVALID, "params: transport tables with the multigrid preconditioner");
+    if (!(p->gas_molar_mass > 0.0) || !std::isfinite(p->gas_molar_mass))
+      return set_err(SDCEF_ERR_INVALID, "params: gas_molar_mass");
+  }
   if (p->bc_electron != SDCEF_BC_ABSORBING && p->bc_electron != SDCEF_BC_ZERO_GRADIENT)
     return set_err(SDCEF_ERR_INVALID, "params: bc_electron");
   int t = p->threads_per_column;
@@ -152,18 +167,29 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb) {
   a.p.mg_gS = p.mg_gamma_S;
   a.p.mg_maxc = p.mg_max_cycles;
   a.p.mg_transfer = p.mg_transfer;
+  a.p.transport = p.transport;
+  a.rho = b->rho;
+  a.tt.tab = ctx->tab;
+  a.tt.nc = ctx->tab_nc;
+  a.tt.nx = ctx->tab_nx;
+  a.tt.en_max_td = ctx->tab_en_max;
+  a.tt.T_in = ctx->tab_T_in;
+  a.tt.inv_dT = ctx->tab_T_max > ctx->tab_T_in ? 1.0 / (ctx->tab_T_max - ctx->tab_T_in) : 0.0;
+  a.tt.gas_W = p.gas_molar_mass;
   return a;
 }
 
 int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
   const int prec = ctx->p.precision;
+  if (ctx->p.transport == SDCEF_TRANSPORT_TABLE && (!ctx->tab || !a.rho))
+    return set_err(SDCEF_ERR_INVALID, "transport tables: no table set, or batch->rho is NULL");
   // restart length used by the iteration (planes are laid out for m_cap)
   const int m_run = ctx->p.restart_m;
   a.p.m = m_run;
   const size_t smem = smem_bytes_prec(prec, tpb, m_run);
   // slot layout must use the same m as the device code: recompute with m_run
   a.slot_bytes = slot_bytes_prec(prec, a.PL, m_run, tpb, ctx->p.precond);
-  int per_sm = occupancy_prec(prec, tpb, smem, ctx->p.precond);
+  int per_sm = occupancy_prec(prec, tpb, smem, ctx->p.precond, ctx->p.transport);
   int64_t slots_fit = (int64_t)(ctx->ws_bytes / a.slot_bytes);
   int grid = (int)std::min<int64_t>({(int64_t)per_sm * ctx->sms, a.ncol, slots_fit});
   if (grid < 1) return set_err(SDCEF_ERR_CAPACITY, "workspace too small for one column slot");
@@ -214,6 +240,8 @@ void sdcef_default_params(sdcef_params* p) {
   p->mg_max_cycles = 50;
   p->mg_transfer = SDCEF_MG_OPERATOR;
   p->ion_scheme = SDCEF_ION_GODUNOV;
+  p->transport = SDCEF_TRANSPORT_CONSTANT;
+  p->gas_molar_mass = 0.028;
   p->bc_electron = SDCEF_BC_ABSORBING;
   p->threads_per_column = 0;
   p->guess_newton_cap = 16;
@@ -283,7 +311,35 @@ int sdcef_destroy(sdcef_ctx* ctx) {
   cudaFree(ctx->queue);
   cudaFree(ctx->order);
   if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->tab) cudaFree(ctx->tab);
   delete ctx;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_set_transport_table(sdcef_ctx* ctx, int nc, int nx, double en_max_td, double T_in,
+                              double T_max, const double* mu, const double* D) {
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  if (nc < 2 || nx < 2 || nc > 4096 || nx > 65536 || !(en_max_td > 0.0) || !std::isfinite(en_max_td) ||
+      !std::isfinite(T_in) || !std::isfinite(T_max) || !(T_max > T_in) || !mu || !D)
+    return set_err(SDCEF_ERR_INVALID, "transport table: bad arguments");
+  const size_t n = (size_t)nc * nx;
+  for (size_t i = 0; i < n; ++i)
+    if (!(mu[i] > 0.0) || !(D[i] > 0.0) || !std::isfinite(mu[i]) || !std::isfinite(D[i]))
+      return set_err(SDCEF_ERR_INVALID, "transport table: entries must be finite and positive");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);   // no solve may still read the old table
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  if (ctx->tab) cudaFree(ctx->tab);
+  ctx->tab = nullptr;
+  e = cudaMalloc((void**)&ctx->tab, 2 * n * sizeof(double));
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
+  e = cudaMemcpy(ctx->tab, mu, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->tab + n, D, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  ctx->tab_nc = nc;
+  ctx->tab_nx = nx;
+  ctx->tab_en_max = en_max_td;
+  ctx->tab_T_in = T_in;
+  ctx->tab_T_max = T_max;
   return SDCEF_SUCCESS;
 }
 
@@ -452,6 +508,18 @@ int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
   a.kappa = kappa_ion;
   a.mu = ctx->p.mobility;
   a.bc = ctx->p.bc_electron;
+  if (ctx->p.transport == SDCEF_TRANSPORT_TABLE) {
+    if (!ctx->tab || !b->rho)
+      return set_err(SDCEF_ERR_INVALID, "current: transport tables need a table and batch->rho");
+    a.tt.tab = ctx->tab;
+    a.tt.nc = ctx->tab_nc;
+    a.tt.nx = ctx->tab_nx;
+    a.tt.en_max_td = ctx->tab_en_max;
+    a.tt.T_in = ctx->tab_T_in;
+    a.tt.inv_dT = 1.0 / (ctx->tab_T_max - ctx->tab_T_in);
+    a.tt.gas_W = ctx->p.gas_molar_mass;
+    a.rho = b->rho;
+  }
   cudaError_t e = launch_current(a, ctx->stream);
   if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
   ctx->launches = 1;

@@ -21,6 +21,7 @@ using namespace sdcef;
 constexpr double kQe = 1.602176634e-19;
 constexpr double kKb = 1.380649e-23;
 constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kNA = 6.02214076e23;
 // lambda_FD = eps_mach^(1/3) for IEEE double (Eq. jf_dfapprox)
 constexpr double kLambdaFD = 6.0554544523933395e-06;
 
@@ -35,9 +36,24 @@ struct DevParams {
   double guess_ratio;   // reject a supplied start with ||Fhat|| > ratio ||Fhat(X^n)|| (0 = never)
   double mg_gA, mg_gS;  // multigrid tolerances of the two blocks (<= 0: exact block solve)
   int mg_maxc, mg_transfer;
+  int transport;        // SDCEF_TRANSPORT_*
+};
+
+// Electron transport tables (SDCEF_TRANSPORT_TABLE): mu then D, each [nc][nx]
+// over c_k = k/(nc-1) and E/N_j = j en_max/(nx-1) Td.
+struct TransportTab {
+  const double* tab;
+  int nc, nx;
+  double en_max_td, T_in, inv_dT, gas_W;
 };
 
 enum { MODE_SOLVE = 0, MODE_RESIDUAL = 1, MODE_PRECOND = 2 };
+
+// Solver kernel variants (template parameter VAR): the base kernel, the one
+// carrying the multigrid preconditioner, and the one with field-dependent
+// electron transport from tables. Each is its own instantiation so that the
+// base kernel compiles without the others' code.
+enum { kVarBase = 0, kVarMG = 1, kVarTable = 2 };
 
 struct KArgs {
   int64_t ncol;
@@ -62,6 +78,9 @@ struct KArgs {
   // test modes: state X, residual-space vector r, outputs
   const double *x_ne, *x_phi, *r_e, *r_phi;
   double *o1, *o2;
+  // field-dependent transport
+  TransportTab tt;
+  const double* rho;
 };
 
 // FP64 planes of a slot
@@ -107,6 +126,9 @@ int occupancy_t(size_t smem);
 constexpr int kMgTPB = 128;
 cudaError_t launch_mg(const KArgs& a, int grid, size_t smem, cudaStream_t st);
 int occupancy_mg(size_t smem);
+// field-dependent transport: its own FP64 instantiation, kMgTPB threads per column
+cudaError_t launch_tab(const KArgs& a, int grid, size_t smem, cudaStream_t st);
+int occupancy_tab(size_t smem);
 
 // Precision modes as (Krylov type KR, preconditioner type PR):
 //   SDCEF_FP64 (double, double), SDCEF_MIXED (float, float),
@@ -147,12 +169,14 @@ inline int occupancy_tpb(int tpb, size_t smem) {
 inline cudaError_t launch_prec(int precision, int tpb, const KArgs& a, int grid, size_t smem,
                                cudaStream_t st) {
   if (a.p.precond == SDCEF_PREC_MG) return launch_mg(a, grid, smem, st);
+  if (a.p.transport == SDCEF_TRANSPORT_TABLE) return launch_tab(a, grid, smem, st);
   if (precision == SDCEF_MIXED) return launch_tpb<float, float>(tpb, a, grid, smem, st);
   if (precision == SDCEF_MIXED_DF) return launch_tpb<double, dfloat>(tpb, a, grid, smem, st);
   return launch_tpb<double, double>(tpb, a, grid, smem, st);
 }
-inline int occupancy_prec(int precision, int tpb, size_t smem, int precond) {
+inline int occupancy_prec(int precision, int tpb, size_t smem, int precond, int transport) {
   if (precond == SDCEF_PREC_MG) return occupancy_mg(smem);
+  if (transport == SDCEF_TRANSPORT_TABLE) return occupancy_tab(smem);
   if (precision == SDCEF_MIXED) return occupancy_tpb<float, float>(tpb, smem);
   if (precision == SDCEF_MIXED_DF) return occupancy_tpb<double, dfloat>(tpb, smem);
   return occupancy_tpb<double, double>(tpb, smem);
@@ -195,6 +219,8 @@ struct CurrentArgs {
   int nsp, bc;
   int val[SDCEF_MAX_SPECIES];
   double kappa, mu;
+  TransportTab tt;      // tt.tab null: constant mobility, Einstein D
+  const double* rho;
 };
 cudaError_t launch_current(const CurrentArgs& a, cudaStream_t st);
 // B(x) and B'(x) of the Scharfetter-Gummel flux, as the residual evaluates them.
@@ -311,6 +337,9 @@ struct ColShared {
   double kh2, m2kh2, m4kh2, kh2_43;
   double vald[SDCEF_MAX_SPECIES];       // ion valences as doubles
   int mgc;                              // V-cycles of this column's multigrid block solves
+  // transport tables: table coordinates of the electrode faces (c index, and
+  // the factor turning |G| into the E/N index) and their frozen mobilities
+  double tcL, sxL, tcR, sxR, muL[2], muR[2];
 };
 
 struct Geo {
@@ -353,6 +382,23 @@ __device__ Slot<TPB, KR, PR> make_slot(const KArgs& a, int slot) {
 
 __device__ __forceinline__ size_t ix(int j, int tid, int TPB) { return (size_t)j * TPB + tid; }
 
+// Bilinear interpolation of the mobility and diffusivity tables at table
+// coordinates (tc, tx) (fractional node indices), clamped to the table.
+__device__ __forceinline__ void tab_mu_d(const TransportTab& T, double tc, double tx, double* mu,
+                                         double* D) {
+  tc = fmin(fmax(tc, 0.0), (double)(T.nc - 1));
+  tx = fmin(fmax(tx, 0.0), (double)(T.nx - 1));
+  const int ic = min((int)tc, T.nc - 2), jx = min((int)tx, T.nx - 2);
+  const double wc = tc - ic, wx = tx - jx;
+  const double* r0 = T.tab + (size_t)ic * T.nx + jx;
+  const double* r1 = r0 + T.nx;
+  const size_t dofs = (size_t)T.nc * T.nx;
+  *mu = (1.0 - wc) * ((1.0 - wx) * __ldg(r0) + wx * __ldg(r0 + 1)) +
+        wc * ((1.0 - wx) * __ldg(r1) + wx * __ldg(r1 + 1));
+  *D = (1.0 - wc) * ((1.0 - wx) * __ldg(r0 + dofs) + wx * __ldg(r0 + dofs + 1)) +
+       wc * ((1.0 - wx) * __ldg(r1 + dofs) + wx * __ldg(r1 + dofs + 1));
+}
+
 // The multigrid region follows the slot's planes (SDCEF_PREC_MG only).
 template <int TPB, typename KR, typename PR>
 __device__ __forceinline__ MgArea mg_slot_area(const Slot<TPB, KR, PR>& S) {
@@ -369,7 +415,7 @@ __device__ __forceinline__ MgArea mg_slot_area(const Slot<TPB, KR, PR>& S) {
 // --------------------------------------------------------------------------
 enum { OUT_F = 0, OUT_JVP = 1 };
 
-template <int TPB, typename KR, typename PR>
+template <int TPB, typename KR, typename PR, int VAR>
 __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
                          const double* nb, const double* pb, const KR* dn, const KR* dp,
                          double cn, double cp, int out_mode, double* fe_o, double* fp_o, int fs,
@@ -415,7 +461,13 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
       // left electrode face: G_L - g0 = (9 psi_0 - psi_1) / (3h)
       double p1 = kt >= 2 ? st_p(1) : halo[1 * TPB + tid + 1];
       double dL = (9.0 * p_i - p1) * (ih * (1.0 / 3.0));
-      double vL = cs.ubl + mu * (g0 + dL);
+      double muL = mu;
+      if constexpr (VAR == kVarTable) {
+        double Dd;
+        tab_mu_d(a.tt, cs.tcL, fabs(g0 + dL) * cs.sxL, &muL, &Dd);
+        if (out_mode == OUT_F) cs.muL[fs] = muL;
+      }
+      double vL = cs.ubl + muL * (g0 + dL);
       bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0;
       gam_left = act ? vL * n_i : 0.0;
       d_left = dL;
@@ -428,20 +480,31 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         n_n = (j + 1 < kt) ? st_n(j + 1) : halo[0 * TPB + tid + 1];
         p_n = (j + 1 < kt) ? st_p(j + 1) : halo[1 * TPB + tid + 1];
         dd = (p_n - p_i) * ih;
-        // Pe = (u_f + mu (g0 + dpsi/dx)) h / D_f
-        const double Pe = fma(MUHD[ix(j, tid, TPB)], dd, PE0[ix(j, tid, TPB)]);
+        double Pe, dh, muf;
+        if constexpr (VAR == kVarTable) {
+          // mu, D from the tables at the face's c and E/N = |G| / N
+          const double G = g0 + dd;
+          double Df;
+          tab_mu_d(a.tt, DH[ix(j, tid, TPB)], fabs(G) * MUHD[ix(j, tid, TPB)], &muf, &Df);
+          Pe = fma(muf, G, PE0[ix(j, tid, TPB)]) * cs.h / Df;
+          dh = Df * ih;
+        } else {
+          // Pe = (u_f + mu (g0 + dpsi/dx)) h / D_f
+          Pe = fma(MUHD[ix(j, tid, TPB)], dd, PE0[ix(j, tid, TPB)]);
+          dh = DH[ix(j, tid, TPB)];
+          muf = mu;
+        }
         double aa = fabs(Pe), b, db = 0.0;
         if (out_mode == OUT_F) bern_pos<true>(aa, &b, &db);   // CTA-uniform branch
         else bern_pos<false>(aa, &b, &db);
         const bool pos = dbits(Pe) >= 0;   // sign bit clear
         const double Bp = pos ? b : aa + b, Bm = pos ? aa + b : b;   // B(Pe), B(-Pe)
-        const double dh = DH[ix(j, tid, TPB)];
         gam = dh * (Bm * n_i - Bp * n_n);
         if (out_mode == OUT_F) {
           const double dBp = pos ? db : -1.0 - db, dBm = pos ? -1.0 - db : db;
           // r dGam/dn_i, r dGam/dn_{i+1}, r dGam/dpsi_i, r dGam/dpsi_{i+1} (unscaled)
           double dg_n0 = dh * Bm, dg_n1 = -dh * Bp;
-          double dg_p1 = mu * ih * (-dBm * n_i - dBp * n_n);
+          double dg_p1 = muf * ih * (-dBm * n_i - dBp * n_n);
           face[0 * a.PL + ix(j, tid, TPB)] = r * dg_n0;
           face[1 * a.PL + ix(j, tid, TPB)] = r * dg_n1;
           face[2 * a.PL + ix(j, tid, TPB)] = -r * dg_p1;
@@ -451,7 +514,13 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         // right electrode face: G_R - g0 = (-9 psi_{N-1} + psi_{N-2}) / (3h)
         double pm = (j >= 1) ? st_p(j - 1) : halo[3 * TPB + tid - 1];
         dd = (-9.0 * p_i + pm) * (ih * (1.0 / 3.0));
-        double vR = cs.ubr + mu * (g0 + dd);
+        double muR = mu;
+        if constexpr (VAR == kVarTable) {
+          double Dd;
+          tab_mu_d(a.tt, cs.tcR, fabs(g0 + dd) * cs.sxR, &muR, &Dd);
+          if (out_mode == OUT_F) cs.muR[fs] = muR;
+        }
+        double vR = cs.ubr + muR * (g0 + dd);
         bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0;
         gam = act ? vR * n_i : 0.0;
         if (out_mode == OUT_F) cs.vR[fs] = vR;
@@ -540,7 +609,7 @@ struct RowJ {
   double As, Ad, Au, Bs, Bd, Bu, Ls, Ld, Lu, C;
 };
 
-template <int TPB, typename KR, typename PR>
+template <int TPB, typename KR, typename PR, int VAR>
 __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColShared& cs,
                                         const Slot<TPB, KR, PR>& S, int fs, int j,
                                         const double* lf /*left face (a0,a1,b0,b1)*/, double n_i,
@@ -563,10 +632,12 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
     R.Bu -= face[3 * a.PL + ix(j, g.tid, TPB)] * sb;
   } else {
     double vR = cs.vR[fs];
+    double muR = mu;
+    if constexpr (VAR == kVarTable) muR = cs.muR[fs];
     if (a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0) {
       R.Ad -= r * vR * sa;
-      R.Bd -= r * n_last * mu * (-3.0 * ih) * sb;
-      R.Bs -= r * n_last * mu * (ih * (1.0 / 3.0)) * sb;
+      R.Bd -= r * n_last * muR * (-3.0 * ih) * sb;
+      R.Bs -= r * n_last * muR * (ih * (1.0 / 3.0)) * sb;
     }
   }
   // left face (row i carries +r Gam_{i-1/2})
@@ -577,10 +648,12 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
     R.Bd += lf[3] * sb;
   } else {
     double vL = cs.vL[fs];
+    double muL = mu;
+    if constexpr (VAR == kVarTable) muL = cs.muL[fs];
     if (a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0) {
       R.Ad += r * vL * sa;
-      R.Bd += r * n_0 * mu * (3.0 * ih) * sb;
-      R.Bu += r * n_0 * mu * (-ih * (1.0 / 3.0)) * sb;
+      R.Bd += r * n_0 * muL * (3.0 * ih) * sb;
+      R.Bu += r * n_0 * muL * (-ih * (1.0 / 3.0)) * sb;
     }
   }
   // Poisson stencil with the second-order electrode closure
@@ -603,7 +676,7 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
 // --------------------------------------------------------------------------
 // Preconditioner: factorisation and application (scaled units).
 // --------------------------------------------------------------------------
-template <int TPB, typename KR, typename PR, bool MG>
+template <int TPB, typename KR, typename PR, int VAR>
 __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
                             int fs, PR* sh, double* halo, bool* bad) {
   const int tid = g.tid, kt = g.kt;
@@ -638,7 +711,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     auto rowf = [&](int j, Mat<2, PR>& M, Mat<2, PR>& D, Mat<2, PR>& U) {
       double lf[4];
       lface(j, lf);
-      RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
       M.a[0] = conv<PR>(R.As); M.a[1] = conv<PR>(R.Bs); M.a[2] = PR(0); M.a[3] = conv<PR>(R.Ls);
       D.a[0] = conv<PR>(R.Ad); D.a[1] = conv<PR>(R.Bd); D.a[2] = conv<PR>(R.C); D.a[3] = conv<PR>(R.Ld);
       U.a[0] = conv<PR>(R.Au); U.a[1] = conv<PR>(R.Bu); U.a[2] = PR(0); U.a[3] = conv<PR>(R.Lu);
@@ -655,7 +728,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     auto row1 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
       double lf[4];
       lface(j, lf);
-      RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
       M.a[0] = conv<PR>(R.As); D.a[0] = conv<PR>(R.Ad); U.a[0] = conv<PR>(R.Au);
       Bpl[0 * S.PL + ix(j, tid, TPB)] = conv<PR>(R.Bs);
       Bpl[1 * S.PL + ix(j, tid, TPB)] = conv<PR>(R.Bd);
@@ -665,14 +738,14 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     auto row2 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
       double lf[4];
       lface(j, lf);
-      RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
       M.a[0] = conv<PR>(R.Ls - rho * R.Bs);
       D.a[0] = conv<PR>(R.Ld - rho * R.Bd);
       U.a[0] = conv<PR>(R.Lu - rho * R.Bu);
     };
     part_factor<1, PR, TPB, false>(F2, S2, kt, tid, g.tact, row2, sh, bad);
   } else if (a.p.precond == SDCEF_PREC_MG) {
-    if constexpr (MG && std::is_same<KR, double>::value && std::is_same<PR, double>::value) {
+    if constexpr (VAR == kVarMG && std::is_same<KR, double>::value && std::is_same<PR, double>::value) {
       // level 0 of both blocks in natural row order (Ahat, S~hat = Lhat - rho Bhat),
       // Bhat kept for the matvec as in the recast form
       const MgArea M = mg_slot_area(S);
@@ -681,7 +754,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
       for (int j = 0; j < kt; ++j) {
         double lf[4];
         lface(j, lf);
-        RowJ R = jac_row<TPB, KR, PR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+        RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
         const int i = g.t0 + j;
         M.op[0].sub[i] = R.As;
         M.op[0].dia[i] = R.Ad;
@@ -765,7 +838,7 @@ __device__ __noinline__ int mg_solve(const KArgs& a, const Geo& g, const MgArea&
 
 // z = Mhat^{-1} r (scaled units); in/out are Krylov planes (2 components each).
 // Returns ||z||_2^2 (block-reduced) if want_norm.
-template <int TPB, typename KR, typename PR, bool MG>
+template <int TPB, typename KR, typename PR, int VAR>
 __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShared& cs,
                              const Slot<TPB, KR, PR>& S, KR* re, KR* rp, KR* ze, KR* zp, PR* sh,
                              double* red, bool want_norm) {
@@ -825,7 +898,7 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
     }
     for (int j = 0; j < kt; ++j) ze[ix(j, tid, TPB)] = ze[ix(j, tid, TPB)] - tpl[ix(j, tid, TPB)];
   } else if (a.p.precond == SDCEF_PREC_MG) {
-    if constexpr (MG && std::is_same<KR, double>::value && std::is_same<PR, double>::value) {
+    if constexpr (VAR == kVarMG && std::is_same<KR, double>::value && std::is_same<PR, double>::value) {
       // Eq. prec_recast as in the recast form, each block solve by V-cycles
       // (or exactly, where that block's tolerance is <= 0)
       const MgArea M = mg_slot_area(S);
@@ -895,7 +968,7 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
 // Column set-up: inputs into the slot, scaling, initial state.
 // Returns false if the column is rejected (BAD_INPUT).
 // --------------------------------------------------------------------------
-template <int TPB, typename KR, typename PR>
+template <int TPB, typename KR, typename PR, int VAR>
 __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
                              double* halo, double* red) {
   const int tid = threadIdx.x;
@@ -956,6 +1029,24 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
     double T = a.T[gi];
     if (dbits(T) <= 0 || nonfinite(T)) bad = 1;   // T <= 0 (incl. -0), NaN or Inf
     double D = mu * (kKb / kQe) * T;
+    if constexpr (VAR == kVarTable) {
+      // progress variable and gas number density in place of D
+      const double rh = a.rho[gi];
+      if (!(rh > 0.0) || nonfinite(rh)) bad = 1;
+      D = fmin(fmax((T - a.tt.T_in) * a.tt.inv_dT, 0.0), 1.0);
+      const double Ng = rh * (kNA / a.tt.gas_W);
+      MUHD[ix(j, tid, TPB)] = Ng;
+      if (j == 0) halo[2 * TPB + tid] = Ng;
+      const double sx = (double)(a.tt.nx - 1) / (a.tt.en_max_td * 1e-21 * Ng);
+      if (g.t0 + j == 0) {
+        cs.tcL = D * (a.tt.nc - 1);
+        cs.sxL = sx;
+      }
+      if (g.t0 + j == g.N - 1) {
+        cs.tcR = D * (a.tt.nc - 1);
+        cs.sxR = sx;
+      }
+    }
     if (j == 0) halo[tid] = D;
     if (a.u && j == 0) halo[TPB + tid] = a.u[gi];
     double neo = a.ne_old[gi], pho = a.phi_old[gi];
@@ -992,10 +1083,19 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
         double un = (j + 1 < g.kt) ? UF[ix(j + 1, tid, TPB)] : halo[TPB + tid + 1];
         uf = 0.5 * (UF[ix(j, tid, TPB)] + un);
       }
-      const double hd = cs.h / Df;
-      DH[ix(j, tid, TPB)] = Df * cs.inv_h;
-      MUHD[ix(j, tid, TPB)] = mu * hd;
-      UF[ix(j, tid, TPB)] = (uf + mu * cs.g0) * hd;
+      if constexpr (VAR == kVarTable) {
+        // table coordinates of the face: c index, |G| -> E/N index factor; face velocity
+        const double Nn = (j + 1 < g.kt) ? MUHD[ix(j + 1, tid, TPB)] : halo[2 * TPB + tid + 1];
+        const double Nf = 0.5 * (MUHD[ix(j, tid, TPB)] + Nn);
+        DH[ix(j, tid, TPB)] = Df * (a.tt.nc - 1);
+        MUHD[ix(j, tid, TPB)] = (double)(a.tt.nx - 1) / (a.tt.en_max_td * 1e-21 * Nf);
+        UF[ix(j, tid, TPB)] = uf;
+      } else {
+        const double hd = cs.h / Df;
+        DH[ix(j, tid, TPB)] = Df * cs.inv_h;
+        MUHD[ix(j, tid, TPB)] = mu * hd;
+        UF[ix(j, tid, TPB)] = (uf + mu * cs.g0) * hd;
+      }
     }
   }
   if (tid == 0) cs.ubl = a.u ? a.u[off] : 0.0;
@@ -1017,9 +1117,9 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
 // --------------------------------------------------------------------------
 // The persistent solver kernel.
 // --------------------------------------------------------------------------
-// MG = true: the instantiation that carries the multigrid preconditioner
-// (SDCEF_PREC_MG); the others compile without it.
-template <int TPB, typename KR, typename PR, bool MG>
+// VAR: kVarBase, kVarMG (the multigrid preconditioner, SDCEF_PREC_MG) or
+// kVarTable (transport tables, SDCEF_TRANSPORT_TABLE).
+template <int TPB, typename KR, typename PR, int VAR>
 __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ColShared cs;
@@ -1045,7 +1145,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     __syncthreads();
     if (cs.col < 0) break;
     Geo g;
-    bool ok = column_setup<TPB, KR, PR>(a, g, cs, S, halo, red);
+    bool ok = column_setup<TPB, KR, PR, VAR>(a, g, cs, S, halo, red);
     const int64_t col = cs.col;
     if (!ok) {
       if (tid == 0) {
@@ -1087,7 +1187,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       }
       if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; }
       __syncthreads();
-      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
@@ -1112,11 +1212,11 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         tp[ix(j, tid, TPB)] = a.phi_old[gi] - pref;
       }
       __syncthreads();
-      residual<TPB, KR, PR>(a, g, cs, S, tn, tp, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR, VAR>(a, g, cs, S, tn, tp, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
     } else {
       __syncthreads();
-      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
     }
     ++res_evals;
@@ -1150,7 +1250,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         }
       }
       __syncthreads();
-      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       ++res_evals;
     }
@@ -1159,7 +1259,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     bool bad = false;
 
     if (a.mode == MODE_PRECOND) {
-      prec_factor<TPB, KR, PR, MG>(a, g, cs, S, cur, sh, halo, &bad);
+      prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
       // r (physical) -> rhat = r / S_F -> z = Mhat^{-1} rhat -> x = S_X z
       KR* re = S.W(0);
       KR* rp = S.W(1);
@@ -1169,7 +1269,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         rp[ix(j, tid, TPB)] = (KR)(a.r_phi[gi] * cs.isFp);
       }
       __syncthreads();
-      prec_apply<TPB, KR, PR, MG>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
+      prec_apply<TPB, KR, PR, VAR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
         a.o1[gi] = (double)S.Z(0)[ix(j, tid, TPB)] * cs.sn;
@@ -1208,7 +1308,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       cur = 0;
       bad = false;
       __syncthreads();
-      residual<TPB, KR, PR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       ++res_evals;
       fninf = scaled_inf(norms);
@@ -1222,7 +1322,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       if (fninf < a.p.eps_F) { status = SDCEF_STATUS_OK; break; }
       if (l >= cap) { status = SDCEF_STATUS_MAX_NEWTON; break; }
       // preconditioner at X^(l) and ||S_X^{-1} X||_2 (X = (n, phi))
-      prec_factor<TPB, KR, PR, MG>(a, g, cs, S, cur, sh, halo, &bad);
+      prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
       {
         double s = 0.0;
         for (int j = 0; j < kt; ++j) {
@@ -1267,12 +1367,12 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         int kdim = 0;
         for (int jj = 0; jj < m && its < a.p.max_krylov; ++jj) {
           // z_jj = Mhat^{-1} V_jj (kept), w = Jhat z_jj
-          double zz = prec_apply<TPB, KR, PR, MG>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
+          double zz = prec_apply<TPB, KR, PR, VAR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
                                           S.ZK(jj, 1), sh, red, true);
           double zn = sqrt(zz);
           double eps = kLambdaFD * (kLambdaFD + cs.xnorm / zn);
           if (!(zn > 0.0)) eps = 1.0;
-          residual<TPB, KR, PR>(a, g, cs, S, NP, PP, S.ZK(jj, 0), S.ZK(jj, 1), eps * cs.sn,
+          residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, S.ZK(jj, 0), S.ZK(jj, 1), eps * cs.sn,
                             eps * cs.sp, OUT_JVP, nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1),
                             1.0 / eps, halo, red, norms);
           ++res_evals;
@@ -1371,7 +1471,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         block_reduce<TPB>(&dd, 1, false, red);
         double zn = sqrt(dd);
         double eps = (zn > 0.0) ? kLambdaFD * (kLambdaFD + cs.xnorm / zn) : 1.0;
-        residual<TPB, KR, PR>(a, g, cs, S, NP, PP, XHe, XHp, eps * cs.sn, eps * cs.sp, OUT_JVP,
+        residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, XHe, XHp, eps * cs.sn, eps * cs.sp, OUT_JVP,
                           nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1), 1.0 / eps, halo, red, norms);
         ++res_evals;
         ++its;
@@ -1402,7 +1502,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       const int nxt = 1 - cur;
       double tnorm[4];
       for (int t = 0; t <= a.p.max_ls; ++t) {
-        residual<TPB, KR, PR>(a, g, cs, S, NP, PP, XHe, XHp, lam * cs.sn, lam * cs.sp, OUT_F,
+        residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, XHe, XHp, lam * cs.sn, lam * cs.sp, OUT_F,
                           S.pd(PD_FE0 + 2 * nxt), S.pd(PD_FP0 + 2 * nxt), nxt, nullptr, nullptr,
                           nullptr, nullptr, 0, halo, red, tnorm);
         ++res_evals;
@@ -1653,15 +1753,37 @@ __global__ void current_kernel(CurrentArgs a) {
     const bool edge = (f == 0 || f == N);
     const int i = f - 1;   // interior face between cells i and i + 1
     double gam;            // electrons
+    // table coordinates (c index, |G| -> E/N index factor) of a face between cells i and k
+    auto tab_coord = [&](int i, int k, double* tc, double* sx) {
+      const double ci = fmin(fmax((T[i] - a.tt.T_in) * a.tt.inv_dT, 0.0), 1.0);
+      const double ck = fmin(fmax((T[k] - a.tt.T_in) * a.tt.inv_dT, 0.0), 1.0);
+      const double Nf = 0.5 * (a.rho[off + i] + a.rho[off + k]) * (kNA / a.tt.gas_W);
+      *tc = 0.5 * (ci + ck) * (a.tt.nc - 1);
+      *sx = (double)(a.tt.nx - 1) / (a.tt.en_max_td * 1e-21 * Nf);
+    };
     if (edge) {
-      const double v = (U ? U[f == 0 ? 0 : N - 1] : 0.0) + mu * (f == 0 ? GL : GR);
+      const int k = f == 0 ? 0 : N - 1;
+      const double G = f == 0 ? GL : GR;
+      double mub = mu;
+      if (a.tt.tab) {
+        double tc, sx, Dd;
+        tab_coord(k, k, &tc, &sx);
+        tab_mu_d(a.tt, tc, fabs(G) * sx, &mub, &Dd);
+      }
+      const double v = (U ? U[k] : 0.0) + mub * G;
       const double ned = f == 0 ? x[0] : x[N - 1];
       const bool out = f == 0 ? v < 0.0 : v > 0.0;
       gam = (a.bc == SDCEF_BC_ZERO_GRADIENT || out) ? v * ned : 0.0;
     } else {
-      const double Df = 0.5 * (mu * kbe * T[i] + mu * kbe * T[i + 1]);
+      double Df = 0.5 * (mu * kbe * T[i] + mu * kbe * T[i + 1]), muf = mu;
+      const double G = (p[i + 1] - p[i]) * ih;
+      if (a.tt.tab) {
+        double tc, sx;
+        tab_coord(i, i + 1, &tc, &sx);
+        tab_mu_d(a.tt, tc, fabs(G) * sx, &muf, &Df);
+      }
       const double uf = U ? 0.5 * (U[i] + U[i + 1]) : 0.0;
-      const double v = uf + mu * (p[i + 1] - p[i]) * ih;
+      const double v = uf + muf * G;
       const double Pe = v * h / Df;
       const double aa = fabs(Pe);
       double bb, dbb;
@@ -1713,7 +1835,7 @@ __global__ void bernoulli_kernel(const double* x, double* b, double* db, int64_t
 
 template <int TPB, typename KR, typename PR>
 cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
-  auto k = jfnk_kernel<TPB, KR, PR, false>;
+  auto k = jfnk_kernel<TPB, KR, PR, kVarBase>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, TPB, smem, st>>>(a);
@@ -1723,7 +1845,7 @@ cudaError_t launch_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
 template <int TPB, typename KR, typename PR>
 int occupancy_t(size_t smem) {
   int nb = 0;
-  auto k = jfnk_kernel<TPB, KR, PR, false>;
+  auto k = jfnk_kernel<TPB, KR, PR, kVarBase>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, TPB, smem) != cudaSuccess) return 1;
@@ -1733,7 +1855,7 @@ int occupancy_t(size_t smem) {
 #ifdef SDCEF_MG
 // The multigrid instantiation: FP64, kMgTPB threads per column.
 inline cudaError_t launch_mg_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
-  auto k = jfnk_kernel<kMgTPB, double, double, true>;
+  auto k = jfnk_kernel<kMgTPB, double, double, kVarMG>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, kMgTPB, smem, st>>>(a);
@@ -1741,13 +1863,31 @@ inline cudaError_t launch_mg_t(const KArgs& a, int grid, size_t smem, cudaStream
 }
 inline int occupancy_mg_t(size_t smem) {
   int nb = 0;
-  auto k = jfnk_kernel<kMgTPB, double, double, true>;
+  auto k = jfnk_kernel<kMgTPB, double, double, kVarMG>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kMgTPB, smem) != cudaSuccess) return 1;
   return nb < 1 ? 1 : nb;
 }
 #endif  // SDCEF_MG
+#ifdef SDCEF_TAB
+// The transport-table instantiation: FP64, kMgTPB threads per column.
+inline cudaError_t launch_tab_t(const KArgs& a, int grid, size_t smem, cudaStream_t st) {
+  auto k = jfnk_kernel<kMgTPB, double, double, kVarTable>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kMgTPB, smem, st>>>(a);
+  return cudaGetLastError();
+}
+inline int occupancy_tab_t(size_t smem) {
+  int nb = 0;
+  auto k = jfnk_kernel<kMgTPB, double, double, kVarTable>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kMgTPB, smem) != cudaSuccess) return 1;
+  return nb < 1 ? 1 : nb;
+}
+#endif  // SDCEF_TAB
 #endif  // SDCEF_KERNEL_TU
 
 }  // namespace sdcef_impl

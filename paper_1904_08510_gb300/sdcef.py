@@ -23,6 +23,7 @@ FP64, MIXED, MIXED_DF = 0, 1, 2
 PREC_EXACT, PREC_RECAST, PREC_NONE, PREC_MG = 0, 1, 2, 3
 MG_OPERATOR, MG_LINEAR = 0, 1
 ION_DRIFT_UPWIND, ION_GODUNOV = 0, 1
+TRANSPORT_CONSTANT, TRANSPORT_TABLE = 0, 1
 BC_ABSORBING, BC_ZERO_GRADIENT = 0, 1
 MAX_RESTART = 32
 MAX_SPECIES = 16
@@ -33,7 +34,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_precond_apply_batch", "sdcef_last_error", "sdcef_last_launch_count",
            "sdcef_solve_batch_noalloc", "sdcef_ion_update_batch", "sdcef_sdc_sweep",
            "sdcef_autotune", "sdcef_bernoulli_batch", "sdcef_current_batch",
-           "sdcef_ion_provisional_batch",
+           "sdcef_ion_provisional_batch", "sdcef_set_transport_table",
            "sdcef_mlp_create", "sdcef_mlp_destroy",
            "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
@@ -53,7 +54,8 @@ class Params(C.Structure):
                 ("bc_electron", C.c_int), ("threads_per_column", C.c_int),
                 ("guess_newton_cap", C.c_int), ("guess_reject_ratio", C.c_double),
                 ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
-                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int), ("ion_scheme", C.c_int)]
+                ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int), ("ion_scheme", C.c_int),
+                ("transport", C.c_int), ("gas_molar_mass", C.c_double)]
 
 
 class BatchC(C.Structure):
@@ -104,6 +106,8 @@ def lib():
         L.sdcef_ion_update_batch.argtypes = [vp, B, vp, C.c_double, vp]
         L.sdcef_current_batch.argtypes = [vp, B, vp, vp, C.c_double, vp, vp]
         L.sdcef_ion_provisional_batch.argtypes = [vp, B, vp, vp, C.c_double, vp, vp]
+        L.sdcef_set_transport_table.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double,
+                                                C.c_double, vp, vp]
         L.sdcef_sdc_sweep.argtypes = [vp, B, C.c_int, C.c_double, vp, R]
         L.sdcef_ion_update_batch.restype = C.c_int
         L.sdcef_autotune.argtypes = [vp, B, R, C.c_int, C.POINTER(C.c_int), vp]
@@ -310,6 +314,15 @@ class Solver:
         _check(lib().sdcef_current_batch(self.h, C.byref(bs), _ptr(ne), _ptr(phi),
                                          float(kappa_ion), _ptr(jp), _ptr(jn)))
         return jp, jn
+
+    def set_transport_table(self, table: dict):
+        """sdcef_set_transport_table from a dict with mu, D ([nc, nx] arrays),
+        en_max_td, T_in, T_max (workload.transport_table's format)."""
+        mu = np.ascontiguousarray(table["mu"], dtype=np.float64)
+        D = np.ascontiguousarray(table["D"], dtype=np.float64)
+        _check(lib().sdcef_set_transport_table(self.h, mu.shape[0], mu.shape[1],
+                                               float(table["en_max_td"]), float(table["T_in"]),
+                                               float(table["T_max"]), mu.ctypes.data, D.ctypes.data))
 
     def sweep_work(self, db: DeviceBatch):
         """Device scratch of sdcef_sdc_sweep for this context's ion scheme:
