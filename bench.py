@@ -588,7 +588,36 @@ def extras(args, S, b, db, solver, params, dev):
     ssolver.close()
     res["multigrid_block_solver"] = mg_study(S, dev)
     res["current_iv_sweep"] = iv_sweep(S, dev)
+    res["field_dependent_transport"] = transport_leg(S, b, db, dev)
     return res
+
+
+def transport_leg(S, b, db, dev):
+    """The headline workload with field-dependent electron transport (Sec. 2.2:
+    mobility and diffusivity from tables over the progress variable and E/N;
+    synthetic tables stand in for BOLSIG+) against constant transport."""
+    from paper_1904_08510_gb300.workload import transport_table
+    out = {"table": "workload.transport_table(): 21 x 161 nodes, E/N 0..400 Td"}
+    ref = None
+    for name, kw in (("constant", {}), ("table", dict(transport=S.TRANSPORT_TABLE))):
+        for m in (8, 30):
+            p = S.default_params(threads_per_column=128, restart_m=m, **kw)
+            sv = S.Solver(p, max_cols=b.ncol, max_cells=b.ncells, max_col_cells=int(b.lengths().max()))
+            if kw:
+                sv.set_transport_table(transport_table())
+            t, o = _timed(lambda: sv.solve(db), reps=2)
+            r = {"ms": 1e3 * t, "column_solves_per_s": b.ncol / t,
+                 "status_ok": int((o["status"] == 0).sum().item())}
+            r.update(_iterations(o))
+            if ref is None:
+                ref = o
+            elif kw:
+                ok = ((o["status"] == 0) & (ref["status"] == 0)).cpu().numpy()
+                e = _colerr(b, o["ne"].cpu().numpy(), ref["ne"].cpu().numpy())[ok]
+                r["root_change_vs_constant_ne"] = {"max": float(e.max()), "median": float(np.median(e))}
+            out[f"{name}_restart{m}"] = r
+            sv.close()
+    return out
 
 
 def iv_sweep(S, dev):
