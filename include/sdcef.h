@@ -295,8 +295,8 @@ int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const doubl
  * drift only. D: diffusion with D_m = kappa_ion k_B T / (|nu_m| e), no flux
  * through the electrodes. n^(k) = n_prev ([n_species][cells], NULL: n^n, the
  * first SDC iteration, where the correction vanishes). No reactions (the
- * columns carry no chemistry). n^n = batch->n_ion; scratch: [cells] device
- * doubles; n_ion_out: [n_species][cells] device (may not alias n^n or
+ * columns carry no chemistry). n^n = batch->n_ion; scratch: [n_species][cells]
+ * device doubles; n_ion_out: [n_species][cells] device (may not alias n^n or
  * n_prev). Enqueued on the context stream. */
 int sdcef_ion_provisional_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* phi,
                                 const double* n_prev, double kappa_ion, double* scratch,
@@ -326,7 +326,7 @@ int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* 
  * from sdcef_ion_provisional_batch (params ion_scheme SDCEF_ION_GODUNOV, with
  * the previous iteration's provisional ions as n^(k)) or from
  * sdcef_ion_update_batch (SDCEF_ION_DRIFT_UPWIND). n_ion_work is caller-owned
- * device scratch of (2 n_species + 1) x max_cells doubles (Godunov; max_cells
+ * device scratch of 3 n_species x max_cells doubles (Godunov; max_cells
  * of sdcef_create: the library does not read the cell count on the host) or
  * n_species x cells (drift-only). The results of the last iteration are
  * written to out; enqueued on the context stream with no allocation and no

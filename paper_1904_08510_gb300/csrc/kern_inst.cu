@@ -35,6 +35,10 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st) {
 }
 cudaError_t launch_ion_provisional(const IonProvArgs& a, cudaStream_t st) {
   ion_provisional_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t nthr = a.ncol * a.nsp;
+  ion_diffusion_kernel<<<(unsigned)((nthr + 127) / 128), 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_current(const CurrentArgs& a, cudaStream_t st) {

@@ -541,8 +541,8 @@ int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kapp
   const size_t plane = (size_t)b->n_species * (size_t)ctx->max_cells;
   for (int k = 0; k < k_max; ++k) {
     const double* phi_field = (k == 0) ? b->phi_old : out->phi_out;
-    // Godunov: provisional ions ping-pong between two halves of the work
-    // buffer (the previous iteration's are n^(k)); the Thomas scratch follows
+    // Godunov: provisional ions ping-pong between the first two thirds of the
+    // work buffer (the previous iteration's are n^(k)); the Thomas scratch follows
     double* prov = godunov ? n_ion_work + (size_t)(k & 1) * plane : n_ion_work;
     if (godunov)
       rc = sdcef_ion_provisional_batch(ctx, b, phi_field,

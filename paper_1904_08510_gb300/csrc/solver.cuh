@@ -1640,9 +1640,11 @@ __global__ void ion_update_kernel(IonArgs a) {
 // extrapolated by (1 -+ w dt/h)/2 times its monotonized-central limited
 // difference (zero in the end cells); electrodes pass the outgoing drift of
 // the edge cell only. D: Einstein diffusivity kappa k_B T_f / (|nu| e), no
-// flux through the electrodes. One CTA per column: the right-hand side with
-// thread-strided cells, then the tridiagonal solve by Thomas on one thread
-// (eliminated super-diagonal in scratch, right-hand side in place).
+// flux through the electrodes. ion_provisional_kernel forms the right-hand
+// side (one CTA per column, thread-strided cells); ion_diffusion_kernel then
+// solves (I - dt D) n~ = rhs by Thomas with one thread per (column, species),
+// so every column's elimination chain runs at once (eliminated
+// super-diagonal in scratch, right-hand side in place).
 __device__ __forceinline__ double mc_limited(double dm, double dp) {
   if (dm * dp <= 0.0) return 0.0;
   double m = fmin(2.0 * fabs(dm), 2.0 * fabs(dp));
@@ -1668,7 +1670,6 @@ __global__ void ion_provisional_kernel(IonProvArgs a) {
   const double* U = a.u ? a.u + off : nullptr;
   const double GL = (-8.0 * a.vl[c] + 9.0 * p[0] - p[1]) / (3.0 * h);
   const double GR = (8.0 * a.vr[c] - 9.0 * p[N - 1] + p[N - 2]) / (3.0 * h);
-  double* cp = a.scratch + off;
   for (int s = 0; s < a.nsp; ++s) {
     const double* n0 = a.n0 + (int64_t)s * cells + off;
     const double* nk = a.nk ? a.nk + (int64_t)s * cells + off : n0;
@@ -1700,22 +1701,45 @@ __global__ void ion_provisional_kernel(IonProvArgs a) {
                           Dl * (nk[i] - (i > 0 ? nk[i - 1] : nk[i]))) / (h * h);
       out[i] = n0[i] - (dt / h) * (flux(i + 1) - flux(i)) + 0.5 * dt * (dn0 - dnk);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sub = 0.0, sup = -dt * dface(1) / (h * h);
-      double piv = 1.0 - sub - sup;
-      cp[0] = sup / piv;
-      out[0] = out[0] / piv;
-      for (int i = 1; i < N; ++i) {
-        sub = -dt * dface(i) / (h * h);
-        sup = -dt * dface(i + 1) / (h * h);
-        piv = (1.0 - sub - sup) - sub * cp[i - 1];
-        cp[i] = sup / piv;
-        out[i] = (out[i] - sub * out[i - 1]) / piv;
-      }
-      for (int i = N - 2; i >= 0; --i) out[i] = out[i] - cp[i] * out[i + 1];
-    }
-    __syncthreads();
+  }
+}
+
+__global__ void ion_diffusion_kernel(IonProvArgs a) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.ncol * a.nsp) return;
+  const int64_t c = q / a.nsp;
+  const int s = (int)(q - c * a.nsp);
+  const int64_t off = a.col_off[c];
+  const int N = (int)(a.col_off[c + 1] - off);
+  if (N < 2) return;
+  const int64_t cells = a.col_off[a.ncol];
+  const double nu = (double)a.val[s];
+  const double Dc = nu != 0.0 ? a.kappa * kKb / (fabs(nu) * kQe) : 0.0;
+  const double h = a.length[c] / N, dt = a.dt[c];
+  const double* __restrict__ T = a.T + off;
+  double* __restrict__ out = a.n_out + (int64_t)s * cells + off;
+  double* __restrict__ cp = a.scratch + (int64_t)s * cells + off;
+  const double k = dt / (h * h);
+  // face diffusivities D_{i+1/2} = Dc (T_i + T_{i+1}) / 2; zero at the electrodes
+  double Tl = T[0], Tr = T[1];
+  double sub = 0.0, sup = -k * (Dc * 0.5 * (Tl + Tr));
+  double piv = 1.0 - sub - sup;
+  cp[0] = sup / piv;
+  double dprev = out[0] / piv;
+  out[0] = dprev;
+  for (int i = 1; i < N; ++i) {
+    sub = sup;                                  // the face shared with row i - 1
+    Tl = Tr;
+    sup = i + 1 < N ? -k * (Dc * 0.5 * (Tl + (Tr = T[i + 1]))) : 0.0;
+    piv = (1.0 - sub - sup) - sub * cp[i - 1];
+    cp[i] = sup / piv;
+    dprev = (out[i] - sub * dprev) / piv;
+    out[i] = dprev;
+  }
+  double xn = dprev;
+  for (int i = N - 2; i >= 0; --i) {
+    xn = out[i] - cp[i] * xn;
+    out[i] = xn;
   }
 }
 

@@ -326,10 +326,10 @@ class Solver:
 
     def sweep_work(self, db: DeviceBatch):
         """Device scratch of sdcef_sdc_sweep for this context's ion scheme:
-        (2 n_species + 1) x max_cells doubles (Godunov) or n_species x cells."""
+        3 n_species x max_cells doubles (Godunov) or n_species x cells."""
         import torch
         nsp = int(db.tensors["n_ion"].shape[0]) if db.tensors["n_ion"].dim() > 1 else 1
-        n = (2 * nsp + 1) * self.max_cells if self.params.ion_scheme == ION_GODUNOV else nsp * db.ncells
+        n = 3 * nsp * self.max_cells if self.params.ion_scheme == ION_GODUNOV else nsp * db.ncells
         return torch.empty(n, dtype=torch.float64, device=db.tensors["ne_old"].device)
 
     def ion_provisional(self, db: DeviceBatch, phi, n_prev=None, kappa_ion: float = 4e-3):
@@ -337,7 +337,7 @@ class Solver:
         transport; n_prev = the previous SDC iterate (None: n^n)."""
         import torch
         out = torch.empty_like(db.tensors["n_ion"])
-        scratch = torch.empty(db.ncells, dtype=torch.float64, device=phi.device)
+        scratch = torch.empty_like(db.tensors["n_ion"])
         bs = db.cstruct()
         _check(lib().sdcef_ion_provisional_batch(self.h, C.byref(bs), _ptr(phi), _ptr(n_prev),
                                                  float(kappa_ion), _ptr(scratch), _ptr(out)))
