@@ -29,22 +29,6 @@ cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int sh
   order_kernel<<<1, 1024, nbins * sizeof(int), st>>>(col_off, ncol, nbins, shift, order);
   return cudaGetLastError();
 }
-cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st) {
-  ion_update_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
-  return cudaGetLastError();
-}
-cudaError_t launch_ion_provisional(const IonProvArgs& a, cudaStream_t st) {
-  ion_provisional_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int64_t nthr = a.ncol * a.nsp;
-  ion_diffusion_kernel<<<(unsigned)((nthr + 127) / 128), 128, 0, st>>>(a);
-  return cudaGetLastError();
-}
-cudaError_t launch_current(const CurrentArgs& a, cudaStream_t st) {
-  current_kernel<<<(unsigned)a.ncol, 128, 0, st>>>(a);
-  return cudaGetLastError();
-}
 cudaError_t launch_bernoulli(const double* x, double* b, double* db, int64_t n, cudaStream_t st) {
   const int64_t blocks = (n + 255) / 256;
   bernoulli_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(x, b, db, n);

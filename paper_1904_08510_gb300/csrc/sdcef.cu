@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/sdcef.h"
+#include "fields.cuh"
 #include "solver.cuh"
 
 using namespace sdcef_impl;
@@ -511,13 +512,13 @@ int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
   if (ctx->p.transport == SDCEF_TRANSPORT_TABLE) {
     if (!ctx->tab || !b->rho)
       return set_err(SDCEF_ERR_INVALID, "current: transport tables need a table and batch->rho");
-    a.tt.tab = ctx->tab;
-    a.tt.nc = ctx->tab_nc;
-    a.tt.nx = ctx->tab_nx;
-    a.tt.en_max_td = ctx->tab_en_max;
-    a.tt.T_in = ctx->tab_T_in;
-    a.tt.inv_dT = 1.0 / (ctx->tab_T_max - ctx->tab_T_in);
-    a.tt.gas_W = ctx->p.gas_molar_mass;
+    a.tab = ctx->tab;
+    a.tnc = ctx->tab_nc;
+    a.tnx = ctx->tab_nx;
+    a.ten_max_td = ctx->tab_en_max;
+    a.tT_in = ctx->tab_T_in;
+    a.tinv_dT = 1.0 / (ctx->tab_T_max - ctx->tab_T_in);
+    a.tgas_W = ctx->p.gas_molar_mass;
     a.rho = b->rho;
   }
   cudaError_t e = launch_current(a, ctx->stream);
