@@ -393,6 +393,15 @@ int sdcef_mlp_destroy(sdcef_mlp* mlp);
 int sdcef_mlp_set_params(sdcef_mlp* mlp, const float* params_host);
 /* Copy the FP32 parameters to HOST memory. */
 int sdcef_mlp_get_params(sdcef_mlp* mlp, float* params_host);
+/* Training checkpoint: the FP32 parameters, the Adam moments m and v (each
+ * SDCEF_MLP_NPARAM floats, HOST memory) and the Adam step count. get copies
+ * them out (synchronises the stream); set restores them, so that training
+ * resumed from a checkpoint continues with the same update as an
+ * uninterrupted run. Not part of the paper (the learned guess is not in it). */
+int sdcef_mlp_get_state(sdcef_mlp* mlp, float* params_host, float* m_host, float* v_host,
+                        int64_t* step);
+int sdcef_mlp_set_state(sdcef_mlp* mlp, const float* params_host, const float* m_host,
+                        const float* v_host, int64_t step);
 /* Features of every cell of the batch into X_bf16 ([cells][32] bfloat16). */
 int sdcef_mlp_features(sdcef_mlp* mlp, const sdcef_batch* batch, void* X_bf16);
 /* Training targets y* ([cells][2] FP32) from converged (ne_star, phi_star). */

@@ -755,6 +755,36 @@ int sdcef_mlp_get_params(sdcef_mlp* h, float* params_host) {
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
 }
 
+int sdcef_mlp_get_state(sdcef_mlp* h, float* params_host, float* m_host, float* v_host,
+                        int64_t* step) {
+  if (!h || !params_host || !m_host || !v_host || !step)
+    return report_error(SDCEF_ERR_INVALID, "mlp_get_state: NULL");
+  cudaError_t e = cudaMemcpyAsync(params_host, h->p, kNParam * 4, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m_host, h->m, kNParam * 4, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v_host, h->v, kNParam * 4, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *step = h->step;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_mlp_set_state(sdcef_mlp* h, const float* params_host, const float* m_host,
+                        const float* v_host, int64_t step) {
+  if (!h || !params_host || !m_host || !v_host || step < 0 || step > 0x7fffffff)
+    return report_error(SDCEF_ERR_INVALID, "mlp_set_state: bad arguments");
+  cudaError_t e = cudaMemcpyAsync(h->p, params_host, kNParam * 4, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->m, m_host, kNParam * 4, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->v, v_host, kNParam * 4, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->g, 0, kNParam * 4, h->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  to_bf16_kernel<<<64, 256, 0, h->st>>>(h->p, h->w1, h->w2, h->w3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->step = (int)step;
+  return SDCEF_SUCCESS;
+}
+
 int sdcef_mlp_features(sdcef_mlp* h, const sdcef_batch* b, void* X_bf16) {
   if (!h || !X_bf16) return report_error(SDCEF_ERR_INVALID, "mlp_features: NULL");
   int rc = check_batch(b);

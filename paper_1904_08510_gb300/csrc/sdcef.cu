@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sdcef.h"
 #include "fields.cuh"
 #include "solver.cuh"
@@ -17,6 +19,13 @@
 using namespace sdcef_impl;
 
 namespace {
+
+// NVTX range over an entry point (host side; visible to profilers that
+// collect NVTX, free otherwise, and harmless inside a stream capture).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 thread_local std::string g_err;
 int set_err(int code, const std::string& m) {
   g_err = m;
@@ -347,6 +356,7 @@ int sdcef_set_transport_table(sdcef_ctx* ctx, int nc, int nx, double en_max_td, 
 int sdcef_last_launch_count(const sdcef_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out) {
+  Range range_("sdcef_solve_batch");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, true);
   if (rc) return rc;
@@ -368,6 +378,7 @@ int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* 
 
 int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out, int reps,
                    int* tpb_out, float* ms_out) {
+  Range range_("sdcef_autotune");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   if (reps < 1 || reps > 100) return set_err(SDCEF_ERR_INVALID, "autotune: reps out of range");
   const int cands[4] = {32, 64, 128, 256};
@@ -410,6 +421,7 @@ int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out
 }
 
 int sdcef_bernoulli_batch(sdcef_ctx* ctx, const double* x, double* b, double* db, int64_t n) {
+  Range range_("sdcef_bernoulli_batch");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   if (n < 0 || (n > 0 && (!x || !b || !db))) return set_err(SDCEF_ERR_INVALID, "bernoulli: bad arguments");
   if (n == 0) return SDCEF_SUCCESS;
@@ -420,6 +432,7 @@ int sdcef_bernoulli_batch(sdcef_ctx* ctx, const double* x, double* b, double* db
 
 int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* phi,
                            double kappa_ion, double* n_ion_out) {
+  Range range_("sdcef_ion_update_batch");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, false);
   if (rc) return rc;
@@ -448,6 +461,7 @@ int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* p
 int sdcef_ion_provisional_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* phi,
                                 const double* n_prev, double kappa_ion, double* scratch,
                                 double* n_ion_out) {
+  Range range_("sdcef_ion_provisional_batch");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, false);
   if (rc) return rc;
@@ -483,6 +497,7 @@ int sdcef_ion_provisional_batch(sdcef_ctx* ctx, const sdcef_batch* b, const doub
 
 int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
                         const double* phi, double kappa_ion, double* j_pos, double* j_neg) {
+  Range range_("sdcef_current_batch");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, false);
   if (rc) return rc;
@@ -529,6 +544,7 @@ int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
 
 int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kappa_ion,
                     double* n_ion_work, const sdcef_result* out) {
+  Range range_("sdcef_sdc_sweep");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, true);
   if (rc) return rc;
@@ -541,6 +557,7 @@ int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kapp
   // buffer stride from the context capacity: the cell count lives on the device
   const size_t plane = (size_t)b->n_species * (size_t)ctx->max_cells;
   for (int k = 0; k < k_max; ++k) {
+    Range it_("sdc iteration");
     const double* phi_field = (k == 0) ? b->phi_old : out->phi_out;
     // Godunov: provisional ions ping-pong between the first two thirds of the
     // work buffer (the previous iteration's are n^(k)); the Thomas scratch follows
@@ -568,6 +585,7 @@ int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kapp
 
 int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne, const double* phi,
                          double* F_e, double* F_phi) {
+  Range range_("sdcef_residual_batch");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, false);
   if (rc) return rc;
@@ -589,6 +607,7 @@ int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
 int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
                               const double* phi, const double* r_e, const double* r_phi,
                               double* x_e, double* x_phi, int* mg_cycles) {
+  Range range_("sdcef_precond_apply_batch");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, b, true);
   if (rc) return rc;
@@ -609,6 +628,7 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double
 }
 
 int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_result* ho) {
+  Range range_("sdcef_solve_batch_host");
   if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
   int rc = validate_batch(ctx, hb, true);
   if (rc) return rc;

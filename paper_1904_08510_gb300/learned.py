@@ -69,19 +69,48 @@ def generate(ncol: int, seed: int, *, kind="single", n_cells=256, n_range=None, 
     return torch.cat(Xs), torch.cat(Ts), sum(stats)
 
 
+def save_checkpoint(path, mlp, it, rng):
+    """Training checkpoint: parameters, Adam moments and step, the iteration
+    and the window generator's state."""
+    st = mlp.get_state()
+    np.savez(path, params=st["params"], adam_m=st["adam_m"], adam_v=st["adam_v"],
+             step=np.int64(st["step"]), it=np.int64(it),
+             rng=np.array(repr(rng.bit_generator.state)))
+
+
+def load_checkpoint(path):
+    import ast
+    with np.load(path) as z:
+        return ({"params": z["params"], "adam_m": z["adam_m"], "adam_v": z["adam_v"],
+                 "step": int(z["step"])}, int(z["it"]), ast.literal_eval(str(z["rng"])))
+
+
 def train(X, T, *, steps: int, batch: int = 32768, lr: float = 2e-3, lr_end: float = 1e-4,
-          seed: int = 0, params=None, log_every: int = 0):
+          seed: int = 0, params=None, log_every: int = 0, checkpoint=None, checkpoint_every=0,
+          resume=None):
     """Adam on contiguous random windows of (X, T); cosine learning-rate decay.
+    checkpoint / checkpoint_every: save a checkpoint every so many iterations;
+    resume: continue from a checkpoint (parameters, Adam state, iteration and
+    window sequence), reproducing the uninterrupted run's updates.
     Returns (mlp handle with the trained parameters, loss history)."""
     import torch
     rows = X.shape[0]
     batch = min(batch, rows)
     mlp = S.MLP(batch)
-    mlp.set_params(init_params(seed) if params is None else params)
     rng = np.random.default_rng(seed)
+    start = 0
+    if resume is not None:
+        state, start, rng_state = load_checkpoint(resume)
+        mlp.set_state(state)
+        rng.bit_generator.state = rng_state
+    else:
+        mlp.set_params(init_params(seed) if params is None else params)
     loss = torch.zeros(1, dtype=torch.float32, device=X.device)
     hist = []
-    for it in range(steps):
+    for it in range(start, steps):
+        if checkpoint and checkpoint_every and it > start and it % checkpoint_every == 0:
+            torch.cuda.synchronize()
+            save_checkpoint(checkpoint, mlp, it, rng)
         o = int(rng.integers(0, rows - batch + 1))
         a = lr_end + 0.5 * (lr - lr_end) * (1 + np.cos(np.pi * it / max(steps - 1, 1)))
         mlp.train_step(X[o:o + batch], T[o:o + batch], a, loss)

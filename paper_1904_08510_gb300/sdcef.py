@@ -38,7 +38,8 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_mlp_create", "sdcef_mlp_destroy",
            "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
-           "sdcef_mlp_guess", "sdcef_mlp_last_launch_count")
+           "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
+           "sdcef_mlp_set_state")
 MLP_NPARAM = 20994
 GUESS_NE, GUESS_PHI = 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -125,10 +126,13 @@ def lib():
         L.sdcef_mlp_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp]
         L.sdcef_mlp_guess.argtypes = [vp, B, i64, C.c_int, vp, vp]
         L.sdcef_mlp_last_launch_count.argtypes = [vp]
+        L.sdcef_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
+        L.sdcef_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
         for f in ("sdcef_mlp_create", "sdcef_mlp_destroy", "sdcef_mlp_set_params",
                   "sdcef_mlp_get_params", "sdcef_mlp_features", "sdcef_mlp_targets",
                   "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
-                  "sdcef_mlp_guess", "sdcef_mlp_last_launch_count"):
+                  "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
+                  "sdcef_mlp_set_state"):
             getattr(L, f).restype = C.c_int
         for f in ("sdcef_create", "sdcef_destroy", "sdcef_set_params", "sdcef_solve_batch",
                   "sdcef_solve_batch_host", "sdcef_residual_batch", "sdcef_precond_apply_batch",
@@ -437,6 +441,22 @@ class MLP:
         a = np.empty(MLP_NPARAM, dtype=np.float32)
         _check(lib().sdcef_mlp_get_params(self.h, a.ctypes.data))
         return a
+
+    def get_state(self) -> dict:
+        """Training checkpoint: parameters, Adam moments and step (host arrays)."""
+        p, m, v = (np.empty(MLP_NPARAM, dtype=np.float32) for _ in range(3))
+        step = C.c_int64(0)
+        _check(lib().sdcef_mlp_get_state(self.h, p.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                         C.byref(step)))
+        return {"params": p, "adam_m": m, "adam_v": v, "step": int(step.value)}
+
+    def set_state(self, state: dict):
+        """Restore a checkpoint taken by get_state."""
+        p, m, v = (np.ascontiguousarray(state[k], dtype=np.float32)
+                   for k in ("params", "adam_m", "adam_v"))
+        assert p.shape == m.shape == v.shape == (MLP_NPARAM,)
+        _check(lib().sdcef_mlp_set_state(self.h, p.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                         int(state["step"])))
 
     def launches(self) -> int:
         return int(lib().sdcef_mlp_last_launch_count(self.h))
