@@ -138,14 +138,34 @@ double or_tab_lookup(const double* t, int nc, int nx, double en_max, double c, d
          wc * ((1.0 - wx) * r1[jx] + wx * r1[jx + 1]);
 }
 
+/* d/dx of the bilinear interpolant at (c, x) (per Td): the slope of the
+ * table cell that tab_lookup interpolates in, zero where x is clamped. */
+static double tab_slope(const double* t, int nc, int nx, double en_max, double c, double x) {
+  double tx = x / en_max * (nx - 1);
+  if (tx < 0.0 || tx > nx - 1) return 0.0;
+  double tc = c * (nc - 1);
+  if (tc < 0.0) tc = 0.0;
+  if (tc > nc - 1) tc = nc - 1;
+  int ic = (int)floor(tc), jx = (int)floor(tx);
+  if (ic > nc - 2) ic = nc - 2;
+  if (jx > nx - 2) jx = nx - 2;
+  double wc = tc - ic;
+  const double* r0 = t + (size_t)ic * nx;
+  const double* r1 = r0 + nx;
+  return ((1.0 - wc) * (r0[jx + 1] - r0[jx]) + wc * (r1[jx + 1] - r1[jx])) * (nx - 1) / en_max;
+}
+
 /* Electron mobility and diffusivity at the face between cells i and k
  * (k = i + 1; k = i for an electrode face) where the potential gradient is G:
  * constant mu and the mean of the cells' Einstein D, or the tables at the
- * face means of c and N and E/N = |G| / N (Sec. 2.2). */
-static void face_transport(const or_col* c, int i, int k, double G, double* mu, double* D) {
+ * face means of c and N and E/N = |G| / N (Sec. 2.2). With dmu, dD non-NULL
+ * also their derivatives with respect to G (zero for constant transport). */
+static void face_transport_d(const or_col* c, int i, int k, double G, double* mu, double* D,
+                             double* dmu, double* dD) {
   if (!c->tab_mu) {
     *mu = c->mu;
     *D = k == i ? c->D[i] : 0.5 * (c->D[i] + c->D[k]);
+    if (dmu) { *dmu = 0.0; *dD = 0.0; }
     return;
   }
   double cf = 0.5 * (c->cprog[i] + c->cprog[k]);
@@ -153,6 +173,14 @@ static void face_transport(const or_col* c, int i, int k, double G, double* mu, 
   double en = fabs(G) / Nf / 1e-21;
   *mu = tab_lookup(c->tab_mu, c->tab_nc, c->tab_nx, c->tab_en_max, cf, en);
   *D = tab_lookup(c->tab_D, c->tab_nc, c->tab_nx, c->tab_en_max, cf, en);
+  if (dmu) {
+    double den = (G < 0.0 ? -1.0 : 1.0) / Nf / 1e-21;      /* d(E/N)/dG in Td */
+    *dmu = tab_slope(c->tab_mu, c->tab_nc, c->tab_nx, c->tab_en_max, cf, en) * den;
+    *dD = tab_slope(c->tab_D, c->tab_nc, c->tab_nx, c->tab_en_max, cf, en) * den;
+  }
+}
+static void face_transport(const or_col* c, int i, int k, double G, double* mu, double* D) {
+  face_transport_d(c, i, k, G, mu, D, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -275,16 +303,23 @@ void or_jacobian_col(const or_col* c, const double* ne, const double* phi,
   }
   /* interior faces i+1/2 */
   for (int i = 0; i + 1 < N; ++i) {
-    /* with transport tables mu and D are frozen at the current gradient: the
-       derivatives below are those of the flux with fixed coefficients */
-    double muf, Df;
-    face_transport(c, i, i + 1, (phi[i + 1] - phi[i]) / h, &muf, &Df);
-    double v = face_u(c, i) + muf * (phi[i + 1] - phi[i]) / h;
+    /* with transport tables mu and D depend on the face gradient G through
+       E/N: the flux derivative includes mu'(G) and D'(G) (the slopes of the
+       interpolant) */
+    double G = (phi[i + 1] - phi[i]) / h;
+    double muf, Df, dmu, dD;
+    face_transport_d(c, i, i + 1, G, &muf, &Df, &dmu, &dD);
+    double v = face_u(c, i) + muf * G;
     double Pe = v * h / Df;
     double dG_dn0 = (Df / h) * or_bern(-Pe);
     double dG_dn1 = -(Df / h) * or_bern(Pe);
-    /* dGam/dPe * dPe/dphi_{i+1}; dPe/dphi_{i+1} = mu / Df */
-    double dG_dp1 = (muf / h) * (-or_bern_deriv(-Pe) * ne[i] - or_bern_deriv(Pe) * ne[i + 1]);
+    /* dGam/dG = (D'/h)[B(-Pe) n_i - B(Pe) n_{i+1}]
+     *         + (D/h)[-B'(-Pe) n_i - B'(Pe) n_{i+1}] dPe/dG,
+     * dPe/dG = h ((mu + G mu') D - v D') / D^2; dG/dphi_{i+1} = 1/h */
+    double dPe = h * ((muf + G * dmu) * Df - v * dD) / (Df * Df);
+    double dGam = (dD / h) * (or_bern(-Pe) * ne[i] - or_bern(Pe) * ne[i + 1]) +
+                  (Df / h) * (-or_bern_deriv(-Pe) * ne[i] - or_bern_deriv(Pe) * ne[i + 1]) * dPe;
+    double dG_dp1 = dGam / h;
     double dG_dp0 = -dG_dp1;
     /* row i carries -r*Gam_{i+1/2}; row i+1 carries +r*Gam_{i+1/2} */
     A.dia[i] += -r * dG_dn0;  A.sup[i] += -r * dG_dn1;
@@ -298,14 +333,15 @@ void or_jacobian_col(const or_col* c, const double* ne, const double* phi,
   /* left electrode face: row 0 carries +r*GamL and -kap*GL/h */
   {
     double GL = (-8.0 * c->vl + 9.0 * phi[0] - phi[1]) / (3.0 * h);
-    double muL, Dd;
-    face_transport(c, 0, 0, GL, &muL, &Dd);
+    double muL, Dd, dmuL, dDd;
+    face_transport_d(c, 0, 0, GL, &muL, &Dd, &dmuL, &dDd);
     double vL = (c->U ? c->U[0] : 0.0) + muL * GL;
+    double dvL = muL + GL * dmuL;                  /* dv/dG at the electrode face */
     int active = (c->bc == OR_BC_ZERO_GRADIENT) || vL < 0.0;
     if (active) {
       A.dia[0] += r * vL;
-      B.dia[0] += r * ne[0] * muL * (9.0 / (3.0 * h));
-      B.sup[0] += r * ne[0] * muL * (-1.0 / (3.0 * h));
+      B.dia[0] += r * ne[0] * dvL * (9.0 / (3.0 * h));
+      B.sup[0] += r * ne[0] * dvL * (-1.0 / (3.0 * h));
     }
     L.dia[0] += -kap / h * (9.0 / (3.0 * h));
     L.sup[0] += -kap / h * (-1.0 / (3.0 * h));
@@ -313,14 +349,15 @@ void or_jacobian_col(const or_col* c, const double* ne, const double* phi,
   /* right electrode face: row N-1 carries -r*GamR and +kap*GR/h */
   {
     double GR = (8.0 * c->vr - 9.0 * phi[N - 1] + phi[N - 2]) / (3.0 * h);
-    double muR, Dd;
-    face_transport(c, N - 1, N - 1, GR, &muR, &Dd);
+    double muR, Dd, dmuR, dDd;
+    face_transport_d(c, N - 1, N - 1, GR, &muR, &Dd, &dmuR, &dDd);
     double vR = (c->U ? c->U[N - 1] : 0.0) + muR * GR;
+    double dvR = muR + GR * dmuR;
     int active = (c->bc == OR_BC_ZERO_GRADIENT) || vR > 0.0;
     if (active) {
       A.dia[N - 1] += -r * vR;
-      B.dia[N - 1] += -r * ne[N - 1] * muR * (-9.0 / (3.0 * h));
-      B.sub[N - 1] += -r * ne[N - 1] * muR * (1.0 / (3.0 * h));
+      B.dia[N - 1] += -r * ne[N - 1] * dvR * (-9.0 / (3.0 * h));
+      B.sub[N - 1] += -r * ne[N - 1] * dvR * (1.0 / (3.0 * h));
     }
     L.dia[N - 1] += kap / h * (-9.0 / (3.0 * h));
     L.sub[N - 1] += kap / h * (1.0 / (3.0 * h));

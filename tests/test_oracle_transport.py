@@ -84,3 +84,36 @@ def test_field_dependent_roots_satisfy_the_table_residual():
     # the field dependence changes the root (mobility falls with E/N)
     rc = O.solve(b, O.default_params(precond=O.PREC_EXACT))
     assert np.abs(r["ne"] - rc["ne"]).max() > 1e-4 * np.abs(rc["ne"]).max()
+
+
+def test_table_jacobian_matches_central_differences():
+    """The analytic Jacobian with transport tables carries the interpolant's
+    slopes mu'(G), D'(G): it matches central differences of the table residual
+    (steps small enough that no face crosses a table node)."""
+    b = make_batch("single", 1, 3, n_cells=14, dt=1e-7)
+    n = b.ncells
+    rng = np.random.default_rng(4)
+    ne = b.ne_old * (1 + 0.2 * rng.standard_normal(n)) + 1e14
+    phi = b.phi_old * 20.0 + 30.0 * rng.standard_normal(n)     # E/N of tens of Td
+    b.v_right = b.v_right * 20.0
+    P = O.default_params(table=transport_table())
+    A, B, L = O.jacobian_blocks(b, ne, phi, P)
+    d = lambda T: np.diag(T[1]) + np.diag(T[0][1:], -1) + np.diag(T[2][:-1], 1)
+    J = np.block([[d(A), d(B)], [-np.eye(n), d(L)]])
+    F = lambda X: np.concatenate(O.residual(b, X[:n], X[n:], P))
+    X = np.concatenate([ne, phi])
+    scale = np.concatenate([np.full(n, 1e16), np.full(n, 100.0)])
+    Jfd = np.zeros_like(J)
+    for j in range(2 * n):
+        h = 1e-8 * scale[j]
+        Xp, Xm = X.copy(), X.copy()
+        Xp[j] += h
+        Xm[j] -= h
+        Jfd[:, j] = (F(Xp) - F(Xm)) / (2 * h)
+    rowmax = np.abs(Jfd).max(axis=1, keepdims=True)
+    assert np.all(np.abs(J - Jfd) <= 1e-6 * rowmax)
+    # at these fields mu' G / mu is O(1) (the mobility falls with E/N over
+    # 20 Td), so a Jacobian with frozen coefficients would miss by far more
+    G = np.abs(np.diff(phi)) / (b.length[0] / n)
+    N = b.rho[0] * 6.02214076e23 / 0.028
+    assert np.median(G / N / 1e-21) > 10.0
