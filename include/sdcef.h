@@ -205,8 +205,8 @@ void sdcef_default_params(sdcef_params* p);
  * cell is (T - T_in)/(T_max - T_in) clamped to [0, 1]. Bilinear interpolation,
  * clamped at the table edges; a face takes the means of its cells' c and N and
  * E/N = |dphi/dx| / N at the face. The finite-difference Jacobian-vector
- * product carries the field dependence; the preconditioner is built with the
- * coefficients frozen at the current iterate. The tables are copied to the
+ * product carries the field dependence, and the preconditioner's analytic
+ * Jacobian includes the slopes of the interpolant in E/N. The tables are copied to the
  * device (allocated here, replacing earlier ones). nc, nx >= 2, en_max_td > 0,
  * T_max > T_in; SDCEF_ERR_INVALID otherwise. */
 int sdcef_set_transport_table(sdcef_ctx* ctx, int nc, int nx, double en_max_td, double T_in,

@@ -299,7 +299,7 @@ struct ColShared {
   double vald[SDCEF_MAX_SPECIES];       // ion valences as doubles
   int mgc;                              // V-cycles of this column's multigrid block solves
   // transport tables: table coordinates of the electrode faces (c index, and
-  // the factor turning |G| into the E/N index) and their frozen mobilities
+  // the factor turning |G| into the E/N index) and dv/dG = mu + G mu'(G) there
   double tcL, sxL, tcR, sxR, muL[2], muR[2];
 };
 
@@ -344,9 +344,12 @@ __device__ Slot<TPB, KR, PR> make_slot(const KArgs& a, int slot) {
 __device__ __forceinline__ size_t ix(int j, int tid, int TPB) { return (size_t)j * TPB + tid; }
 
 // Bilinear interpolation of the mobility and diffusivity tables at table
-// coordinates (tc, tx) (fractional node indices), clamped to the table.
+// coordinates (tc, tx) (fractional node indices), clamped to the table; with
+// dmu non-null also the slopes d/dtx of the interpolant (zero where tx is
+// clamped).
 __device__ __forceinline__ void tab_mu_d(const TransportTab& T, double tc, double tx, double* mu,
-                                         double* D) {
+                                         double* D, double* dmu = nullptr, double* dD = nullptr) {
+  const bool inside = tx >= 0.0 && tx <= (double)(T.nx - 1);
   tc = fmin(fmax(tc, 0.0), (double)(T.nc - 1));
   tx = fmin(fmax(tx, 0.0), (double)(T.nx - 1));
   const int ic = min((int)tc, T.nc - 2), jx = min((int)tx, T.nx - 2);
@@ -354,10 +357,15 @@ __device__ __forceinline__ void tab_mu_d(const TransportTab& T, double tc, doubl
   const double* r0 = T.tab + (size_t)ic * T.nx + jx;
   const double* r1 = r0 + T.nx;
   const size_t dofs = (size_t)T.nc * T.nx;
-  *mu = (1.0 - wc) * ((1.0 - wx) * __ldg(r0) + wx * __ldg(r0 + 1)) +
-        wc * ((1.0 - wx) * __ldg(r1) + wx * __ldg(r1 + 1));
-  *D = (1.0 - wc) * ((1.0 - wx) * __ldg(r0 + dofs) + wx * __ldg(r0 + dofs + 1)) +
-       wc * ((1.0 - wx) * __ldg(r1 + dofs) + wx * __ldg(r1 + dofs + 1));
+  const double m00 = __ldg(r0), m01 = __ldg(r0 + 1), m10 = __ldg(r1), m11 = __ldg(r1 + 1);
+  const double d00 = __ldg(r0 + dofs), d01 = __ldg(r0 + dofs + 1), d10 = __ldg(r1 + dofs),
+               d11 = __ldg(r1 + dofs + 1);
+  *mu = (1.0 - wc) * ((1.0 - wx) * m00 + wx * m01) + wc * ((1.0 - wx) * m10 + wx * m11);
+  *D = (1.0 - wc) * ((1.0 - wx) * d00 + wx * d01) + wc * ((1.0 - wx) * d10 + wx * d11);
+  if (dmu) {
+    *dmu = inside ? (1.0 - wc) * (m01 - m00) + wc * (m11 - m10) : 0.0;
+    *dD = inside ? (1.0 - wc) * (d01 - d00) + wc * (d11 - d10) : 0.0;
+  }
 }
 
 // The multigrid region follows the slot's planes (SDCEF_PREC_MG only).
@@ -424,9 +432,11 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
       double dL = (9.0 * p_i - p1) * (ih * (1.0 / 3.0));
       double muL = mu;
       if constexpr (VAR == kVarTable) {
-        double Dd;
-        tab_mu_d(a.tt, cs.tcL, fabs(g0 + dL) * cs.sxL, &muL, &Dd);
-        if (out_mode == OUT_F) cs.muL[fs] = muL;
+        double Dd, dmu_x, dDd;
+        const double G = g0 + dL;
+        tab_mu_d(a.tt, cs.tcL, fabs(G) * cs.sxL, &muL, &Dd, &dmu_x, &dDd);
+        // dv/dG = mu + G mu'(G) for the Jacobian row
+        if (out_mode == OUT_F) cs.muL[fs] = fma(G, dmu_x * (G < 0.0 ? -cs.sxL : cs.sxL), muL);
       }
       double vL = cs.ubl + muL * (g0 + dL);
       bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0;
@@ -442,11 +452,24 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         p_n = (j + 1 < kt) ? st_p(j + 1) : halo[1 * TPB + tid + 1];
         dd = (p_n - p_i) * ih;
         double Pe, dh, muf;
+        double dPe_dG = 0.0, dD_dG = 0.0;   // table mode, OUT_F: slopes of the interpolant
         if constexpr (VAR == kVarTable) {
           // mu, D from the tables at the face's c and E/N = |G| / N
           const double G = g0 + dd;
+          const double sx = MUHD[ix(j, tid, TPB)];
           double Df;
-          tab_mu_d(a.tt, DH[ix(j, tid, TPB)], fabs(G) * MUHD[ix(j, tid, TPB)], &muf, &Df);
+          if (out_mode == OUT_F) {
+            double dmu_x, dD_x;
+            tab_mu_d(a.tt, DH[ix(j, tid, TPB)], fabs(G) * sx, &muf, &Df, &dmu_x, &dD_x);
+            const double sg = G < 0.0 ? -sx : sx;   // d tx / dG
+            const double dmu = dmu_x * sg;
+            dD_dG = dD_x * sg;
+            const double v = fma(muf, G, PE0[ix(j, tid, TPB)]);
+            // dPe/dG = h ((mu + G mu') D - v D') / D^2
+            dPe_dG = cs.h * (fma(G, dmu, muf) * Df - v * dD_dG) / (Df * Df);
+          } else {
+            tab_mu_d(a.tt, DH[ix(j, tid, TPB)], fabs(G) * sx, &muf, &Df);
+          }
           Pe = fma(muf, G, PE0[ix(j, tid, TPB)]) * cs.h / Df;
           dh = Df * ih;
         } else {
@@ -465,7 +488,15 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
           const double dBp = pos ? db : -1.0 - db, dBm = pos ? -1.0 - db : db;
           // r dGam/dn_i, r dGam/dn_{i+1}, r dGam/dpsi_i, r dGam/dpsi_{i+1} (unscaled)
           double dg_n0 = dh * Bm, dg_n1 = -dh * Bp;
-          double dg_p1 = muf * ih * (-dBm * n_i - dBp * n_n);
+          double dg_p1;
+          if constexpr (VAR == kVarTable) {
+            // dGam/dG = (D'/h)(B(-Pe) n_i - B(Pe) n_{i+1}) + (D/h)(-B'(-Pe) n_i - B'(Pe) n_{i+1}) dPe/dG
+            const double dGam = dD_dG * ih * (Bm * n_i - Bp * n_n) +
+                                dh * (-dBm * n_i - dBp * n_n) * dPe_dG;
+            dg_p1 = ih * dGam;
+          } else {
+            dg_p1 = muf * ih * (-dBm * n_i - dBp * n_n);
+          }
           face[0 * a.PL + ix(j, tid, TPB)] = r * dg_n0;
           face[1 * a.PL + ix(j, tid, TPB)] = r * dg_n1;
           face[2 * a.PL + ix(j, tid, TPB)] = -r * dg_p1;
@@ -477,9 +508,10 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         dd = (-9.0 * p_i + pm) * (ih * (1.0 / 3.0));
         double muR = mu;
         if constexpr (VAR == kVarTable) {
-          double Dd;
-          tab_mu_d(a.tt, cs.tcR, fabs(g0 + dd) * cs.sxR, &muR, &Dd);
-          if (out_mode == OUT_F) cs.muR[fs] = muR;
+          double Dd, dmu_x, dDd;
+          const double G = g0 + dd;
+          tab_mu_d(a.tt, cs.tcR, fabs(G) * cs.sxR, &muR, &Dd, &dmu_x, &dDd);
+          if (out_mode == OUT_F) cs.muR[fs] = fma(G, dmu_x * (G < 0.0 ? -cs.sxR : cs.sxR), muR);
         }
         double vR = cs.ubr + muR * (g0 + dd);
         bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0;
