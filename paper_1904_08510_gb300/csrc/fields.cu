@@ -81,42 +81,52 @@ __global__ void ion_provisional_kernel(IonProvArgs a) {
     return;
   }
   const double h = a.length[c] / N, dt = a.dt[c];
+  const double ih = 1.0 / h, dtih = dt * ih, ih2 = ih * ih;
   const double* p = a.phi + off;
   const double* T = a.T + off;
   const double* U = a.u ? a.u + off : nullptr;
-  const double GL = (-8.0 * a.vl[c] + 9.0 * p[0] - p[1]) / (3.0 * h);
-  const double GR = (8.0 * a.vr[c] - 9.0 * p[N - 1] + p[N - 2]) / (3.0 * h);
+  const double GL = (-8.0 * a.vl[c] + 9.0 * p[0] - p[1]) * (ih * (1.0 / 3.0));
+  const double GR = (8.0 * a.vr[c] - 9.0 * p[N - 1] + p[N - 2]) * (ih * (1.0 / 3.0));
   for (int s = 0; s < a.nsp; ++s) {
     const double* n0 = a.n0 + (int64_t)s * cells + off;
     const double* nk = a.nk ? a.nk + (int64_t)s * cells + off : n0;
     double* out = a.n_out + (int64_t)s * cells + off;
+    // interior face fluxes F_{f}, f = 1..N-1, computed once each (scratch
+    // entry f - 1; the diffusion solve reuses the scratch afterwards)
+    double* Fi = a.scratch + (int64_t)s * cells + off;
     const double nu = (double)a.val[s];
+    const double nk_ = nu * a.kappa;
     const double Dc = nu != 0.0 ? a.kappa * kKb / (fabs(nu) * kQe) : 0.0;
     auto slope = [&](int i) {
       return (i == 0 || i == N - 1) ? 0.0 : mc_limited(n0[i] - n0[i - 1], n0[i + 1] - n0[i]);
     };
+    for (int f = 1 + threadIdx.x; f < N; f += blockDim.x) {
+      const int i = f - 1;
+      const double w = (U ? 0.5 * (U[i] + U[i + 1]) : 0.0) - nk_ * ((p[i + 1] - p[i]) * ih);
+      const double cfl = w * dtih;
+      const double nf = w >= 0.0 ? n0[i] + 0.5 * (1.0 - cfl) * slope(i)
+                                 : n0[i + 1] - 0.5 * (1.0 + cfl) * slope(i + 1);
+      Fi[i] = w * nf;
+    }
+    __syncthreads();
     auto flux = [&](int f) {
       if (f == 0 || f == N) {
-        const double w = (U ? U[f == 0 ? 0 : N - 1] : 0.0) + nu * a.kappa * (f == 0 ? -GL : -GR);
+        const double w = (U ? U[f == 0 ? 0 : N - 1] : 0.0) + nk_ * (f == 0 ? -GL : -GR);
         const bool out_ = f == 0 ? w < 0.0 : w > 0.0;
         return out_ ? w * (f == 0 ? n0[0] : n0[N - 1]) : 0.0;
       }
-      const int i = f - 1;
-      const double w = (U ? 0.5 * (U[i] + U[i + 1]) : 0.0) - nu * a.kappa * (p[i + 1] - p[i]) / h;
-      const double cfl = w * dt / h;
-      const double nf = w >= 0.0 ? n0[i] + 0.5 * (1.0 - cfl) * slope(i)
-                                 : n0[i + 1] - 0.5 * (1.0 + cfl) * slope(i + 1);
-      return w * nf;
+      return Fi[f - 1];
     };
     auto dface = [&](int f) { return (f == 0 || f == N) ? 0.0 : Dc * 0.5 * (T[f - 1] + T[f]); };
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       const double Dl = dface(i), Dr = dface(i + 1);
       const double dn0 = (Dr * ((i + 1 < N ? n0[i + 1] : n0[i]) - n0[i]) -
-                          Dl * (n0[i] - (i > 0 ? n0[i - 1] : n0[i]))) / (h * h);
+                          Dl * (n0[i] - (i > 0 ? n0[i - 1] : n0[i]))) * ih2;
       const double dnk = (Dr * ((i + 1 < N ? nk[i + 1] : nk[i]) - nk[i]) -
-                          Dl * (nk[i] - (i > 0 ? nk[i - 1] : nk[i]))) / (h * h);
-      out[i] = n0[i] - (dt / h) * (flux(i + 1) - flux(i)) + 0.5 * dt * (dn0 - dnk);
+                          Dl * (nk[i] - (i > 0 ? nk[i - 1] : nk[i]))) * ih2;
+      out[i] = n0[i] - dtih * (flux(i + 1) - flux(i)) + 0.5 * dt * (dn0 - dnk);
     }
+    __syncthreads();   // the next species writes its own scratch slice; keep passes ordered
   }
 }
 
@@ -136,20 +146,21 @@ __global__ void ion_diffusion_kernel(IonProvArgs a) {
   double* __restrict__ out = a.n_out + (int64_t)s * cells + off;
   double* __restrict__ cp = a.scratch + (int64_t)s * cells + off;
   const double k = dt / (h * h);
-  // face diffusivities D_{i+1/2} = Dc (T_i + T_{i+1}) / 2; zero at the electrodes
+  // face diffusivities D_{i+1/2} = Dc (T_i + T_{i+1}) / 2; zero at the
+  // electrodes; one reciprocal of the pivot per row
   double Tl = T[0], Tr = T[1];
   double sub = 0.0, sup = -k * (Dc * 0.5 * (Tl + Tr));
-  double piv = 1.0 - sub - sup;
-  cp[0] = sup / piv;
-  double dprev = out[0] / piv;
+  double rp = 1.0 / (1.0 - sub - sup);
+  cp[0] = sup * rp;
+  double dprev = out[0] * rp;
   out[0] = dprev;
   for (int i = 1; i < N; ++i) {
     sub = sup;                                  // the face shared with row i - 1
     Tl = Tr;
     sup = i + 1 < N ? -k * (Dc * 0.5 * (Tl + (Tr = T[i + 1]))) : 0.0;
-    piv = (1.0 - sub - sup) - sub * cp[i - 1];
-    cp[i] = sup / piv;
-    dprev = (out[i] - sub * dprev) / piv;
+    rp = 1.0 / ((1.0 - sub - sup) - sub * cp[i - 1]);
+    cp[i] = sup * rp;
+    dprev = (out[i] - sub * dprev) * rp;
     out[i] = dprev;
   }
   double xn = dprev;
