@@ -1,7 +1,8 @@
-// Learned Newton initial guess: feature extraction, a BF16 tensor-core GEMM
-// for training (mma.sync m16n8k16, FP32 accumulation) with fused bias/SiLU
-// epilogues, the MSE loss, backpropagation, Adam, and the fused inference
-// kernel on the tcgen05 tensor cores (mlp_tc.cuh) that assembles the guess. The network maps the
+// Learned Newton initial guess: feature extraction, a BF16 GEMM for training
+// on the tcgen05 tensor cores (FP32 accumulators in TMEM) with fused
+// bias/SiLU epilogues, the MSE loss, backpropagation, Adam, and the fused
+// inference kernel on the tcgen05 tensor cores (mlp_tc.cuh) that assembles
+// the guess. The network maps the
 // 5-cell stencil features of a cell to the scaled Newton increment
 // ((n* - n^n)/s_n, (phi* - phi^n)/s_phi); the JFNK of Algorithm 2 then starts
 // from X^n + S_X y instead of X^n and still decides convergence.
@@ -135,13 +136,31 @@ __global__ void feat_kernel(FeatArgs a) {
   }
 }
 
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
 // --------------------------------------------------------------------------
-// BF16 GEMM on the tensor cores: C[m][n] = sum_k A(m,k) B(k,n),
-// A(m,k) = transA ? A[k*lda+m] : A[m*lda+k], B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n].
-// 64x64 CTA tile, 32-deep K slab, 4 warps of 32x32, mma.sync m16n8k16.
-// Epilogues: 0 store/accumulate FP32 C; 1 Z = acc + bias (FP32, optional)
-// and H = silu(Z) (BF16); 2 dZ = acc * silu'(Zin) (BF16) with the column sums
-// of dZ added to colsum; 3 C = acc + bias (FP32).
+// Training GEMMs on the tcgen05 tensor cores: C[m][n] = sum_k A(m,k) B(k,n)
+// with A(m,k) = transA ? A[k*lda+m] : A[m*lda+k] and
+// B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n] (BF16), FP32 accumulators in TMEM.
+// Epilogues: 0 add C with atomics (split-K weight gradients); 1 Z = acc + bias
+// (FP32, optional) and H = silu(Z) (BF16); 2 dZ = acc * silu'(Zin) (BF16)
+// with the column sums of dZ added to colsum; 3 C = acc + bias (FP32).
+//
+// A CTA of 256 threads computes 128 rows of C (row m0 + r in TMEM lane r) by
+// all N <= 128 columns (the MMA's N is N rounded up to 16) over its share of
+// K, in slabs of up to 64 k held in two shared-memory buffers, so the threads
+// stage slab s + 1 while the tensor core multiplies slab s. Each operand is
+// staged in the K-major core-matrix layout of mlp_tc.cuh, zero outside the
+// matrix: a K-contiguous operand by 16-byte asynchronous copies (cp.async)
+// that land in core-matrix order, an operand whose rows are contiguous by the
+// same copies into a row-major buffer that ldmatrix.trans then transposes (two
+// consecutive k of one row per register). The epilogue runs on all 8 warps:
+// two per 32-lane quadrant of TMEM, each on half of the columns.
+// Every wait on an mbarrier is bounded; a CTA whose MMAs do not complete sets
+// the error word and writes NaN instead of its results.
 // --------------------------------------------------------------------------
 struct GemmArgs {
   int M, N, K;
@@ -150,8 +169,7 @@ struct GemmArgs {
   const __nv_bfloat16* B;
   int ldb, transB;
   float* C;
-  int ldc, atomic;
-  int kchunk;
+  int ldc;
   int epi;
   const float* bias;
   __nv_bfloat16* H;
@@ -161,120 +179,379 @@ struct GemmArgs {
   float* colsum;
 };
 
-constexpr int BM = 64, BN = 64, BK = 32, PADK = BK + 8;
+// the kernel's form: operand X(r, k) = X[r * sr + k * sk] with sr == 1 or sk == 1
+struct TcGemm {
+  int M, N, K, kchunk, epi;
+  const uint16_t* A;
+  int64_t sam, sak;
+  const uint16_t* B;
+  int64_t sbn, sbk;
+  float* C;
+  int64_t scm, scn;
+  const float* bias;
+  __nv_bfloat16* H;
+  int64_t ldh;
+  const float* Zin;
+  int64_t ldz;
+  float* colsum;
+  int* err;
+};
 
-__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+constexpr int kGemmThreads = 256;                           // two warps per TMEM lane quadrant
+constexpr int kSlabK = 64;                                  // k per slab
+constexpr uint32_t kOpBytes = 128 * kSlabK * 2;             // one operand slab
+__host__ __device__ constexpr uint32_t nat_pitch(int R) { return (uint32_t)(2 * R + 16); }
+__host__ __device__ constexpr uint32_t nat_bytes(int R) { return kSlabK * nat_pitch(R); }
+constexpr uint32_t kGemmSmemMax = 4 * kOpBytes + 2 * nat_bytes(128);
+constexpr int kZPitch = 36, kHPitch = 80;                   // epilogue staging pitches
+constexpr uint32_t kStageBytes = 32 * kZPitch * 4 + 32 * kHPitch;
+static_assert(kGemmThreads / 32 * kStageBytes <= 4 * kOpBytes, "staging tiles fit the operand buffers");
+
+__device__ __forceinline__ uint32_t pack_u16(uint16_t lo, uint16_t hi) {
+  return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 sA[BM][PADK];
-  __shared__ __align__(16) __nv_bfloat16 sB[BN][PADK];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kbeg = blockIdx.z * g.kchunk;
-  const int kend = min(g.K, kbeg + g.kchunk);
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float acc[2][4][4];
+// 16-byte asynchronous global -> shared copy; an invalid chunk is zero-filled
+// without reading global memory (the source then only names a valid address)
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::saddr(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// K-contiguous operand X(r, k) = X[r sr + k]: rows rbase.. rbase + R - 1 (valid
+// below rmax), k in [k0, k0 + 8 kc) (valid below kend). Item e fills bytes
+// [16 e, 16 e + 16) of S, i.e. core matrix e / 8, row e % 8: asynchronously
+// where the chunk's 8 k are all valid or all beyond the matrix, element by
+// element where it straddles the edge or the rows are not 16-byte aligned.
+__device__ __forceinline__ void stage_k(unsigned char* S, const uint16_t* X, int64_t sr, bool vec,
+                                        int64_t rbase, int64_t rmax, int R, int k0, int kend,
+                                        int kc, int tid) {
+  const int items = R * kc;
+#pragma unroll 4
+  for (int e = tid; e < items; e += kGemmThreads) {
+    const int grp = e / (8 * kc), w = e - grp * 8 * kc;
+    const int64_t gr = rbase + grp * 8 + (w & 7);
+    const int gk = k0 + (w >> 3) * 8;
+    const bool none = gr >= rmax || gk >= kend;
+    if (none || (vec && gk + 8 <= kend)) {
+      cp16(S + (size_t)e * 16, none ? (const void*)X : (const void*)(X + gr * sr + gk), !none);
+    } else {
+      uint16_t u[8];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    // load A tile -> sA[m][k], B tile -> sB[n][k]
-    for (int e = tid; e < BM * BK; e += 128) {
-      int mm, kk;
-      if (g.transA) { kk = e / BM; mm = e % BM; } else { mm = e / BK; kk = e % BK; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (gm < g.M && gk < kend)
-        v = g.transA ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
-      sA[mm][kk] = v;
+      for (int j = 0; j < 8; ++j) u[j] = (gk + j < kend) ? X[gr * sr + gk + j] : 0;
+      *reinterpret_cast<uint4*>(S + (size_t)e * 16) =
+          make_uint4(pack_u16(u[0], u[1]), pack_u16(u[2], u[3]), pack_u16(u[4], u[5]),
+                     pack_u16(u[6], u[7]));
     }
-    for (int e = tid; e < BN * BK; e += 128) {
-      int nn, kk;
-      if (g.transB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
-      const int gn = n0 + nn, gk = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (gn < g.N && gk < kend)
-        v = g.transB ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
-      sB[nn][kk] = v;
-    }
-    __syncthreads();
-    const int gr = lane >> 2, tc = (lane & 3) * 2;
-#pragma unroll
-    for (int ks = 0; ks < BK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + gr;
-        af[i][0] = *(const uint32_t*)&sA[r][ks + tc];
-        af[i][1] = *(const uint32_t*)&sA[r + 8][ks + tc];
-        af[i][2] = *(const uint32_t*)&sA[r][ks + tc + 8];
-        af[i][3] = *(const uint32_t*)&sA[r + 8][ks + tc + 8];
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + gr;
-        bfr[j][0] = *(const uint32_t*)&sB[c][ks + tc];
-        bfr[j][1] = *(const uint32_t*)&sB[c][ks + tc + 8];
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
-    }
-    __syncthreads();
   }
-  // epilogue
-  const int gr = lane >> 2, tc = (lane & 3) * 2;
-  float cs[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+}
+
+// row-contiguous operand X(r, k) = X[r + k sk]: copy the slab row-major into
+// nat (row k at k * pitch, 16 bytes = 8 consecutive r per item)
+__device__ __forceinline__ void stage_nat(unsigned char* nat, uint32_t pitch, const uint16_t* X,
+                                          int64_t sk, bool vec, int64_t rbase, int64_t rmax,
+                                          int R, int k0, int kend, int ks, int tid) {
+  const int rc = R >> 3, items = ks * rc;
+#pragma unroll 4
+  for (int e = tid; e < items; e += kGemmThreads) {
+    const int k = e / rc, c = e - k * rc;
+    const int64_t gr = rbase + c * 8, gk = k0 + k;
+    unsigned char* d = nat + (size_t)k * pitch + c * 16;
+    const bool none = gr >= rmax || gk >= kend;
+    if (none || (vec && gr + 8 <= rmax)) {
+      cp16(d, none ? (const void*)X : (const void*)(X + gk * sk + gr), !none);
+    } else {
+      uint16_t u[8];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 8; ++j) u[j] = (gr + j < rmax) ? X[gk * sk + gr + j] : 0;
+      *reinterpret_cast<uint4*>(d) = make_uint4(pack_u16(u[0], u[1]), pack_u16(u[2], u[3]),
+                                                pack_u16(u[4], u[5]), pack_u16(u[6], u[7]));
+    }
+  }
+}
+
+// nat (k rows, r contiguous) -> K-major core matrices. Core matrix i = c kc + kk
+// holds rows 8c.. of k 8kk..; ldmatrix.trans hands lane l the pair
+// (k = 8kk + 2 (l%4) + {0,1}, r = 8c + l/4), which sits at byte 4 l of it.
+__device__ __forceinline__ void nat_to_k(unsigned char* S, const unsigned char* nat,
+                                         uint32_t pitch, int R, int kc, int warp, int lane) {
+  const int mats = (R >> 3) * kc;   // a multiple of 4 (R >= 16, kc >= 2)
+  for (int g = warp; g * 4 < mats; g += kGemmThreads / 32) {
+    const int i = g * 4 + (lane >> 3);   // the matrix whose row address this lane gives
+    const int c = i / kc, kk = i - c * kc;
+    const uint32_t src = tc::saddr(nat + (size_t)(kk * 8 + (lane & 7)) * pitch + c * 16);
+    uint32_t r0, r1, r2, r3;
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(src));
+    uint32_t* d = reinterpret_cast<uint32_t*>(S + (size_t)g * 4 * 128) + lane;
+    d[0] = r0;
+    d[32] = r1;
+    d[64] = r2;
+    d[96] = r3;
+  }
+}
+
+// lane l ends with the sum over the warp of v[l]
+__device__ __forceinline__ float warp_colsum32(float* v, int lane) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int row = m0 + wm + i * 16 + gr + (q >> 1) * 8;
-        const int col = n0 + wn + j * 8 + tc + (q & 1);
-        if (row >= g.M || col >= g.N) continue;
-        float v = acc[i][j][q];
-        if (g.epi == 0) {
-          float* p = g.C + (size_t)row * g.ldc + col;
-          if (g.atomic) atomicAdd(p, v); else *p = v;
-        } else if (g.epi == 1) {
-          float z = v + g.bias[col];
-          if (g.C) g.C[(size_t)row * g.ldc + col] = z;
-          g.H[(size_t)row * g.ldh + col] = __float2bfloat16(silu(z));
-        } else if (g.epi == 2) {
-          float dz = v * silu_grad(g.Zin[(size_t)row * g.ldz + col]);
-          g.H[(size_t)row * g.ldh + col] = __float2bfloat16(dz);
-          cs[j][q & 1] += dz;
-        } else {
-          g.C[(size_t)row * g.ldc + col] = v + g.bias[col];
+    for (int j = 0; j < s; ++j) {
+      const float send = up ? v[j] : v[j + s];
+      const float keep = up ? v[j + s] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
+  extern __shared__ __align__(1024) unsigned char gsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ float sbias[128];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * 128;
+  if (g.epi == 1 || g.epi == 3)
+    for (int i = tid; i < g.N; i += kGemmThreads) sbias[i] = g.bias[i];
+  const int kbeg = blockIdx.y * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  const int Np = (g.N + 15) & ~15;
+  const bool amn = g.sak != 1, bmn = g.sbk != 1;
+  unsigned char* opA = gsm;
+  unsigned char* opB = gsm + 2 * kOpBytes;
+  unsigned char* natA = gsm + 4 * kOpBytes;
+  unsigned char* natB = natA + (amn ? nat_bytes(128) : 0);
+  const bool vecA = ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0) && (((amn ? g.sak : g.sam) & 7) == 0);
+  const bool vecB = ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0) && (((bmn ? g.sbk : g.sbn) & 7) == 0);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        tc::saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[1])) : "memory");
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tmem_base;
+  const uint32_t idesc = tc::idesc_bf16(128, Np);
+  const int nslab = (kend - kbeg + kSlabK - 1) / kSlabK;   // >= 1 (the host keeps kbeg < K)
+  // slabs in flight: two when both operands go straight to their buffers,
+  // one when a row-major copy (a single buffer per operand) is transposed
+  const int L = (amn || bmn) ? 1 : 2;
+  auto issue = [&](int s) {
+    const int b = s & 1, k0 = kbeg + s * kSlabK;
+    const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
+    if (!amn) stage_k(opA + b * kOpBytes, g.A, g.sam, vecA, m0, g.M, 128, k0, kend, kc, tid);
+    else stage_nat(natA, nat_pitch(128), g.A, g.sak, vecA, m0, g.M, 128, k0, kend, ks, tid);
+    if (!bmn) stage_k(opB + b * kOpBytes, g.B, g.sbn, vecB, 0, g.N, Np, k0, kend, kc, tid);
+    else stage_nat(natB, nat_pitch(Np), g.B, g.sbk, vecB, 0, g.N, Np, k0, kend, ks, tid);
+    cp_commit();
+  };
+  for (int j = 0; j < min(L, nslab); ++j) issue(j);
+  bool ok = true;
+  int last = -1;                                           // last slab whose MMAs were committed
+  for (int s = 0; s < nslab; ++s) {
+    const int b = s & 1, k0 = kbeg + s * kSlabK;
+    const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
+    if (L == 2 && s + 1 < nslab) cp_wait<1>();
+    else cp_wait<0>();
+    unsigned char* sA = opA + b * kOpBytes;
+    unsigned char* sB = opB + b * kOpBytes;
+    if (amn || bmn) {
+      __syncthreads();
+      if (amn) nat_to_k(sA, natA, nat_pitch(128), 128, kc, warp, lane);
+      if (bmn) nat_to_k(sB, natB, nat_pitch(Np), Np, kc, warp, lane);
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t aA = tc::saddr(sA), aB = tc::saddr(sB);
+      for (int kk = 0; kk < ks / 16; ++kk)
+        tc::mma(tm, tc::smem_desc(aA + kk * 256, 128, kc * 128),
+                tc::smem_desc(aB + kk * 256, 128, kc * 128), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+      tc::commit(tc::saddr(&mbar[b]));
+    }
+    last = s;
+    const int nxt = s + L;
+    if (nxt < nslab) {
+      // buffer nxt & 1 was last read by the MMAs of slab nxt - 2
+      if (nxt >= 2) {
+        const bool w = tc::wait_phase(tc::saddr(&mbar[nxt & 1]), ((nxt - 2) >> 1) & 1);
+        if (__syncthreads_or(!w)) {
+          ok = false;
+          break;
         }
       }
-  if (g.epi == 2) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        float v = cs[j][q];
-        // lanes sharing a column: same lane & 3
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        const int col = n0 + wn + j * 8 + tc + q;
-        if (gr == 0 && col < g.N) atomicAdd(&g.colsum[col], v);
-      }
+      issue(nxt);
+    }
   }
+  if (ok) {   // the last commit covers every MMA issued before it
+    const bool w = tc::wait_phase(tc::saddr(&mbar[last & 1]), (last >> 1) & 1);
+    ok = !__syncthreads_or(!w);
+  }
+  tc::fence_after();
+  // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (row m0 + 32 (w % 4)
+  // + lane) in columns 64 (w / 4) .. 64 (w / 4) + 63 ----
+  const int quad = warp & 3, half = warp >> 2;
+  const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
+  const int64_t row = m0 + quad * 32 + lane;
+  const bool live = row < g.M;
+  // the operand buffers are free now: each warp gets a staging tile of 32
+  // rows x 32 FP32 (pitch 36 floats) and 32 rows x 32 BF16 (pitch 80 B),
+  // pitches at which a quarter-warp's 16-byte accesses hit distinct banks
+  const int64_t rbase = m0 + quad * 32;
+  const int64_t rows_left = (int64_t)g.M - rbase;
+  const int nrows = rows_left <= 0 ? 0 : (rows_left < 32 ? (int)rows_left : 32);
+  float* zt = reinterpret_cast<float*>(gsm + warp * kStageBytes);
+  unsigned char* ht = gsm + warp * kStageBytes + 32 * kZPitch * 4;
+  const bool tiled =
+      (g.scm & 3) == 0 && (g.ldh & 7) == 0 && (g.ldz & 3) == 0 &&
+      ((reinterpret_cast<uintptr_t>(g.C) | reinterpret_cast<uintptr_t>(g.H) |
+        reinterpret_cast<uintptr_t>(g.Zin)) & 15) == 0;
+  for (int c0 = half * 64; c0 < min(Np, half * 64 + 64); c0 += 32) {
+    float v[32];
+    if (ok) {
+      tc::ld32(lane_addr + c0, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = __int_as_float(0x7fffffff);
+    }
+    const bool full = c0 + 32 <= g.N;
+    if (g.epi == 0) {
+      if (live) {
+        float* Cr = g.C + row * g.scm;
+        if (full && g.scn == 1 && ((reinterpret_cast<uintptr_t>(Cr + c0) & 15) == 0)) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            atomicAdd(reinterpret_cast<float4*>(Cr + c0 + 4 * q),
+                      make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < g.N) atomicAdd(Cr + (c0 + j) * g.scn, v[j]);
+        }
+      }
+    } else if (g.epi == 1) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += (c0 + j < g.N) ? sbias[c0 + j] : 0.0f;
+      if (full && tiled) {
+        // through the warp's staging tile, so that each store instruction
+        // writes whole rows: 4 rows x 128 B of Z, 8 rows x 64 B of H
+        if (g.C) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4*>(zt + lane * kZPitch + 4 * q) =
+                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(ht + lane * kHPitch + 16 * q) =
+              make_uint4(pack_bf16(silu(v[8 * q]), silu(v[8 * q + 1])),
+                         pack_bf16(silu(v[8 * q + 2]), silu(v[8 * q + 3])),
+                         pack_bf16(silu(v[8 * q + 4]), silu(v[8 * q + 5])),
+                         pack_bf16(silu(v[8 * q + 6]), silu(v[8 * q + 7])));
+        __syncwarp();
+        if (g.C) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int e = i * 32 + lane, r = e >> 3, c4 = e & 7;
+            if (r < nrows)
+              *reinterpret_cast<float4*>(g.C + (rbase + r) * g.scm + c0 + 4 * c4) =
+                  *reinterpret_cast<const float4*>(zt + r * kZPitch + 4 * c4);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = i * 32 + lane, r = e >> 2, p = e & 3;
+          if (r < nrows)
+            *reinterpret_cast<uint4*>(g.H + (rbase + r) * g.ldh + c0 + 8 * p) =
+                *reinterpret_cast<const uint4*>(ht + r * kHPitch + 16 * p);
+        }
+        __syncwarp();
+      } else if (live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < g.N) {
+            if (g.C) g.C[row * g.scm + c0 + j] = v[j];
+            g.H[row * g.ldh + c0 + j] = __float2bfloat16(silu(v[j]));
+          }
+      }
+    } else if (g.epi == 2) {
+      float z[32];
+      if (full && tiled) {
+        // Zin rows in with whole-row loads through the staging tile
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int e = i * 32 + lane, r = e >> 3, c4 = e & 7;
+          float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (r < nrows)
+            t = __ldg(reinterpret_cast<const float4*>(g.Zin + (rbase + r) * g.ldz + c0 + 4 * c4));
+          *reinterpret_cast<float4*>(zt + r * kZPitch + 4 * c4) = t;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 t = *reinterpret_cast<const float4*>(zt + lane * kZPitch + 4 * q);
+          z[4 * q] = t.x; z[4 * q + 1] = t.y; z[4 * q + 2] = t.z; z[4 * q + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) z[j] = (live && c0 + j < g.N) ? g.Zin[row * g.ldz + c0 + j] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = (live && c0 + j < g.N) ? v[j] * silu_grad(z[j]) : 0.0f;
+      if (full && tiled) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(ht + lane * kHPitch + 16 * q) =
+              make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                         pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = i * 32 + lane, r = e >> 2, p = e & 3;
+          if (r < nrows)
+            *reinterpret_cast<uint4*>(g.H + (rbase + r) * g.ldh + c0 + 8 * p) =
+                *reinterpret_cast<const uint4*>(ht + r * kHPitch + 16 * p);
+        }
+        __syncwarp();
+      } else if (live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < g.N) g.H[row * g.ldh + c0 + j] = __float2bfloat16(v[j]);
+      }
+      const float cs = warp_colsum32(v, lane);
+      if (c0 + lane < g.N) atomicAdd(&g.colsum[c0 + lane], cs);
+    } else {
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < g.N) g.C[row * g.scm + c0 + j] = v[j] + sbias[c0 + j];
+      }
+    }
+  }
+  if (!ok) {
+    cp_wait<0>();
+    if (tid == 0) atomicExch(g.err, 1);
+    // an MMA may still be in flight: one more bounded wait before TMEM is freed
+    if (last >= 0) tc::wait_phase(tc::saddr(&mbar[last & 1]), (last >> 1) & 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tm));
 }
 
 // --------------------------------------------------------------------------
@@ -290,11 +567,6 @@ struct GuessArgs {
   float* stage;                    // [cells][5] per-cell feature values (FP32)
   int* err;                        // set when a tensor-core wait times out
 };
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
 
 // TMEM lane -> bias + SiLU -> BF16 row of the next layer's A operand
 __device__ __forceinline__ void tc_epilogue(uint32_t taddr, const float* bias, unsigned char* A,
@@ -574,26 +846,46 @@ struct sdcef_mlp {
   __nv_bfloat16 *H1, *H2, *dY, *dZ2, *dZ1, *X;   // BF16 activations / features
   int step;
   int launches;
+  int sms;                              // multiprocessors of the device
 };
 
 namespace {
 
 int cuda_fail(cudaError_t e) { return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e)); }
 
-cudaError_t gemm(sdcef_mlp* h, GemmArgs g) {
+cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a) {
+  if (a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaSuccess;
+  TcGemm g;
+  memset(&g, 0, sizeof(g));
+  g.M = a.M; g.N = a.N; g.K = a.K; g.epi = a.epi;
+  g.A = reinterpret_cast<const uint16_t*>(a.A);
+  g.sam = a.transA ? 1 : a.lda; g.sak = a.transA ? a.lda : 1;
+  g.B = reinterpret_cast<const uint16_t*>(a.B);
+  g.sbn = a.transB ? a.ldb : 1; g.sbk = a.transB ? 1 : a.ldb;
+  g.C = a.C; g.scm = a.ldc; g.scn = 1;
+  g.bias = a.bias; g.H = a.H; g.ldh = a.ldh; g.Zin = a.Zin; g.ldz = a.ldz; g.colsum = a.colsum;
+  g.err = (int*)h->loss + 5;
+  if (g.epi == 0 && g.M < 64 && g.N > g.M) {
+    // C^T = B^T A^T: the long side of the product goes on the 128 TMEM lanes
+    std::swap(g.M, g.N); std::swap(g.A, g.B); std::swap(g.sam, g.sbn); std::swap(g.sak, g.sbk);
+    std::swap(g.scm, g.scn);
+  }
+  if (g.N > 128 || (g.sam != 1 && g.sak != 1) || (g.sbn != 1 && g.sbk != 1))
+    return cudaErrorInvalidValue;
+  const int tiles = (g.M + 127) / 128, Np = (g.N + 15) & ~15;
   int splits = 1;
-  g.kchunk = ((g.K + BK - 1) / BK) * BK;
-  if (g.epi == 0 && g.atomic) {
-    // split K across CTAs so that the long sample dimension fills the GPU
-    const int tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
-    splits = std::max(1, std::min(1024, 608 / std::max(tiles, 1)));
-    int kc = (g.K + splits - 1) / splits;
-    g.kchunk = ((kc + BK - 1) / BK) * BK;
+  g.kchunk = (g.K + kSlabK - 1) / kSlabK * kSlabK;
+  if (g.epi == 0) {
+    // split K (the sample dimension of the weight gradients) over about two
+    // CTAs per SM, at least two slabs each; partial sums meet in C by atomics
+    const int want = std::max(1, 2 * h->sms / tiles);
+    const int kc = (g.K + want - 1) / want;
+    g.kchunk = std::max((kc + kSlabK - 1) / kSlabK * kSlabK, 2 * kSlabK);
     splits = (g.K + g.kchunk - 1) / g.kchunk;
   }
+  const uint32_t smem = 4 * kOpBytes + (g.sak != 1 ? nat_bytes(128) : 0) + (g.sbk != 1 ? nat_bytes(Np) : 0);
   // M (the sample dimension of the layer GEMMs) on grid.x, whose limit is 2^31 - 1
-  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, splits);
-  gemm_bf16_kernel<<<grid, 128, 0, h->st>>>(g);
+  gemm_tc_kernel<<<dim3(tiles, splits), kGemmThreads, smem, h->st>>>(g);
   ++h->launches;
   return cudaGetLastError();
 }
@@ -638,7 +930,7 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64
   GemmArgs g = ga();
   g.M = kOut; g.N = kHid; g.K = (int)n;
   g.A = h->dY; g.lda = kOut; g.transA = 1; g.B = h->H2; g.ldb = kHid;
-  g.C = h->g + kOffW3; g.ldc = kHid; g.atomic = 1; g.epi = 0;
+  g.C = h->g + kOffW3; g.ldc = kHid; g.epi = 0;
   if ((e = gemm(h, g)) != cudaSuccess) return e;
   // dZ2 = (dY W3) * silu'(Z2); gb2 += colsum
   g = ga();
@@ -650,7 +942,7 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64
   g = ga();
   g.M = kHid; g.N = kHid; g.K = (int)n;
   g.A = h->dZ2; g.lda = kHid; g.transA = 1; g.B = h->H1; g.ldb = kHid;
-  g.C = h->g + kOffW2; g.ldc = kHid; g.atomic = 1;
+  g.C = h->g + kOffW2; g.ldc = kHid;
   if ((e = gemm(h, g)) != cudaSuccess) return e;
   // dZ1 = (dZ2 W2) * silu'(Z1); gb1 += colsum
   g = ga();
@@ -662,7 +954,7 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64
   g = ga();
   g.M = kHid; g.N = kIn; g.K = (int)n;
   g.A = h->dZ1; g.lda = kHid; g.transA = 1; g.B = X; g.ldb = kIn;
-  g.C = h->g + kOffW1; g.ldc = kIn; g.atomic = 1;
+  g.C = h->g + kOffW1; g.ldc = kIn;
   return gemm(h, g);
 }
 
@@ -702,6 +994,19 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
   memset(h, 0, sizeof(*h));
   h->max_rows = max_rows;
   h->st = (cudaStream_t)stream;
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kGemmSmemMax);
+    if (e != cudaSuccess) {
+      delete h;
+      return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+    }
+    h->sms = std::max(h->sms, 1);
+  }
   const size_t R = (size_t)max_rows;
   struct Alloc { void** p; size_t bytes; } al[] = {
       {(void**)&h->p, kNParam * 4}, {(void**)&h->g, kNParam * 4}, {(void**)&h->m, kNParam * 4},

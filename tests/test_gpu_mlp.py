@@ -76,7 +76,10 @@ def test_forward_matches_oracle_on_bf16_weights():
     assert np.linalg.norm(Y - Yr) <= 2e-2 * np.linalg.norm(Yr)
 
 
-@pytest.mark.parametrize("n", [37, 700])
+# 37 and 700 rows: one ragged 128-row tile and several; 20011 rows: the
+# weight gradients split their K = 20011 samples over ~150 CTAs of two
+# 64-sample slabs with a ragged last slab
+@pytest.mark.parametrize("n", [37, 700, 20011])
 def test_gradients_match_fp64_backprop(n):
     d = dev()
     flat, q = rounded_params(5)
