@@ -594,7 +594,51 @@ def extras(args, S, b, db, solver, params, dev):
     res["multigrid_block_solver"] = mg_study(S, dev)
     res["current_iv_sweep"] = iv_sweep(S, dev)
     res["field_dependent_transport"] = transport_leg(S, b, db, dev)
+    res["mlp_training"] = mlp_training_leg(S, dev)
     return res
+
+
+# algorithmic bytes per sample of one training step (each operand read once,
+# each result written once): forward 64 + 768 | 256 + 768 | 256 + 8, loss
+# 16 + 4, gW3 4 + 256, dZ2 4 + 512 + 256, gW2 256 + 256, dZ1 256 + 512 + 256,
+# gW1 256 + 64
+MLP_STEP_BYTES_PER_SAMPLE = 832 + 1024 + 264 + 20 + 260 + 772 + 512 + 1024 + 320
+MLP_STEP_FLOPS_PER_SAMPLE = 3 * 2 * (32 * 128 + 128 * 128 + 128 * 2)
+
+
+def mlp_training_leg(S, dev):
+    """One Adam step of the learned-guess network (forward, MSE, backward:
+    eight BF16 GEMMs on tcgen05 with fused epilogues, loss and Adam kernels)
+    on synthetic features, at the training batch and at a streaming size;
+    the epoch estimate is for the 51.2 M samples of 200k solves x 256 cells."""
+    import torch
+    peaks, peak_kind = load_peaks()
+    out = {}
+    rng = np.random.default_rng(12)
+    for n in (32768, 262144):
+        X = torch.as_tensor(rng.standard_normal((n, 32)), dtype=torch.float32)
+        X[:, 25:] = 0.0
+        X = X.to(torch.bfloat16).to(dev)
+        T = torch.as_tensor(rng.standard_normal((n, 2)), dtype=torch.float32, device=dev)
+        mlp = S.MLP(n)
+        mlp.set_params((0.05 * rng.standard_normal(S.MLP_NPARAM)).astype(np.float32))
+        reps = 10
+
+        def steps():
+            for _ in range(reps):
+                mlp.train_step(X, T, 1e-4)
+        t, _ = _timed(steps, reps=3)
+        t /= reps
+        gbs = MLP_STEP_BYTES_PER_SAMPLE * n / t / 1e9
+        out[f"batch_{n}"] = {
+            "us_per_step": 1e6 * t, "samples_per_s": n / t, "epoch_s_51_2M": 51.2e6 * t / n,
+            "launches_per_step": mlp.launches(),
+            "algorithmic": {"bytes_per_sample": MLP_STEP_BYTES_PER_SAMPLE,
+                            "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": gbs / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                            "tflops": MLP_STEP_FLOPS_PER_SAMPLE * n / t / 1e12}}
+        mlp.close()
+    return out
 
 
 def transport_leg(S, b, db, dev):

@@ -1,8 +1,9 @@
-// Learned Newton initial guess: feature extraction, a BF16 GEMM for training
-// on the tcgen05 tensor cores (FP32 accumulators in TMEM) with fused
-// bias/SiLU epilogues, the MSE loss, backpropagation, Adam, and the fused
-// inference kernel on the tcgen05 tensor cores (mlp_tc.cuh) that assembles
-// the guess. The network maps the
+// Learned Newton initial guess: feature extraction; training on the tcgen05
+// tensor cores (BF16 operands, FP32 accumulators in TMEM): the three-layer
+// forward fused in one kernel, the MSE loss, backpropagation through a BF16
+// GEMM with fused SiLU-derivative and split-K weight-gradient epilogues, and
+// Adam; and the fused inference kernel (mlp_tc.cuh) that assembles the
+// guess. The network maps the
 // 5-cell stencil features of a cell to the scaled Newton increment
 // ((n* - n^n)/s_n, (phi* - phi^n)/s_phi); the JFNK of Algorithm 2 then starts
 // from X^n + S_X y instead of X^n and still decides convergence.
@@ -145,9 +146,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // Training GEMMs on the tcgen05 tensor cores: C[m][n] = sum_k A(m,k) B(k,n)
 // with A(m,k) = transA ? A[k*lda+m] : A[m*lda+k] and
 // B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n] (BF16), FP32 accumulators in TMEM.
-// Epilogues: 0 add C with atomics (split-K weight gradients); 1 Z = acc + bias
-// (FP32, optional) and H = silu(Z) (BF16); 2 dZ = acc * silu'(Zin) (BF16)
-// with the column sums of dZ added to colsum; 3 C = acc + bias (FP32).
+// Epilogues: 0 add C with atomics (split-K weight gradients); 2 dZ = acc *
+// silu'(Zin) (BF16) with the column sums of dZ added to colsum (the forward
+// runs fused, fwd_tc_kernel below).
 //
 // A CTA of 256 threads computes 128 rows of C (row m0 + r in TMEM lane r) by
 // all N <= 128 columns (the MMA's N is N rounded up to 16) over its share of
@@ -171,7 +172,6 @@ struct GemmArgs {
   float* C;
   int ldc;
   int epi;
-  const float* bias;
   __nv_bfloat16* H;
   int ldh;
   const float* Zin;
@@ -188,7 +188,6 @@ struct TcGemm {
   int64_t sbn, sbk;
   float* C;
   int64_t scm, scn;
-  const float* bias;
   __nv_bfloat16* H;
   int64_t ldh;
   const float* Zin;
@@ -315,11 +314,8 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   extern __shared__ __align__(1024) unsigned char gsm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ float sbias[128];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
-  if (g.epi == 1 || g.epi == 3)
-    for (int i = tid; i < g.N; i += kGemmThreads) sbias[i] = g.bias[i];
   const int kbeg = blockIdx.y * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
   const int Np = (g.N + 15) & ~15;
   const bool amn = g.sak != 1, bmn = g.sbk != 1;
@@ -443,51 +439,6 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
             if (c0 + j < g.N) atomicAdd(Cr + (c0 + j) * g.scn, v[j]);
         }
       }
-    } else if (g.epi == 1) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] += (c0 + j < g.N) ? sbias[c0 + j] : 0.0f;
-      if (full && tiled) {
-        // through the warp's staging tile, so that each store instruction
-        // writes whole rows: 4 rows x 128 B of Z, 8 rows x 64 B of H
-        if (g.C) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            *reinterpret_cast<float4*>(zt + lane * kZPitch + 4 * q) =
-                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(ht + lane * kHPitch + 16 * q) =
-              make_uint4(pack_bf16(silu(v[8 * q]), silu(v[8 * q + 1])),
-                         pack_bf16(silu(v[8 * q + 2]), silu(v[8 * q + 3])),
-                         pack_bf16(silu(v[8 * q + 4]), silu(v[8 * q + 5])),
-                         pack_bf16(silu(v[8 * q + 6]), silu(v[8 * q + 7])));
-        __syncwarp();
-        if (g.C) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int e = i * 32 + lane, r = e >> 3, c4 = e & 7;
-            if (r < nrows)
-              *reinterpret_cast<float4*>(g.C + (rbase + r) * g.scm + c0 + 4 * c4) =
-                  *reinterpret_cast<const float4*>(zt + r * kZPitch + 4 * c4);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int e = i * 32 + lane, r = e >> 2, p = e & 3;
-          if (r < nrows)
-            *reinterpret_cast<uint4*>(g.H + (rbase + r) * g.ldh + c0 + 8 * p) =
-                *reinterpret_cast<const uint4*>(ht + r * kHPitch + 16 * p);
-        }
-        __syncwarp();
-      } else if (live) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < g.N) {
-            if (g.C) g.C[row * g.scm + c0 + j] = v[j];
-            g.H[row * g.ldh + c0 + j] = __float2bfloat16(silu(v[j]));
-          }
-      }
     } else if (g.epi == 2) {
       float z[32];
       if (full && tiled) {
@@ -534,12 +485,6 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
       }
       const float cs = warp_colsum32(v, lane);
       if (c0 + lane < g.N) atomicAdd(&g.colsum[c0 + lane], cs);
-    } else {
-      if (live) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < g.N) g.C[row * g.scm + c0 + j] = v[j] + sbias[c0 + j];
-      }
     }
   }
   if (!ok) {
@@ -547,6 +492,149 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
     if (tid == 0) atomicExch(g.err, 1);
     // an MMA may still be in flight: one more bounded wait before TMEM is freed
     if (last >= 0) tc::wait_phase(tc::saddr(&mbar[last & 1]), (last >> 1) & 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tm));
+}
+
+// --------------------------------------------------------------------------
+// Training forward, all three layers in one launch: a CTA of 256 threads
+// takes 128 rows of X, stages X and the BF16 weights in the K-major
+// core-matrix layout (cp.async), and chains the layers on the tensor core
+// through one 128-column TMEM accumulator. After each hidden layer the 8-warp
+// epilogue (two warps per TMEM lane quadrant, each on half of the columns)
+// adds the bias, writes Z (FP32, optional) and H = silu(Z) (BF16) to global
+// memory, and writes H into shared memory as the A operand of the next layer,
+// so H1 and H2 are not read back from global memory. Every wait on the
+// mbarrier is bounded; a CTA whose MMAs do not complete sets the error word
+// and writes NaN instead of its results.
+// --------------------------------------------------------------------------
+struct FwdArgs {
+  int64_t n;
+  const uint16_t* X;                  // [n][32] BF16
+  const uint16_t *w1, *w2, *w3;       // [128][32], [128][128], [2][128] BF16
+  const float* p;                     // FP32 parameters (biases)
+  float *Z1, *Z2;                     // [n][128] FP32, nullable
+  __nv_bfloat16 *H1, *H2;             // [n][128] BF16
+  float* Y;                           // [n][2] FP32
+  int* err;
+};
+
+constexpr uint32_t kFwW1 = kHid * kIn * 2, kFwW2 = kHid * kHid * 2, kFwW3 = 16 * kHid * 2,
+                   kFwX = 128 * kIn * 2, kFwH = 128 * kHid * 2;
+constexpr uint32_t kFwSmem = kFwW1 + kFwW2 + kFwW3 + kFwX + kFwH;
+
+__global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char gsm[];
+  unsigned char* sW1 = gsm;
+  unsigned char* sW2 = sW1 + kFwW1;
+  unsigned char* sW3 = sW2 + kFwW2;
+  unsigned char* sX = sW3 + kFwW3;
+  unsigned char* sH = sX + kFwX;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sb[2 * kHid + kOut];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * 128;
+  const bool vecX = (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
+  stage_k(sX, a.X, kIn, vecX, m0, a.n, 128, 0, kIn, kIn / 8, tid);
+  stage_k(sW1, a.w1, kIn, true, 0, kHid, kHid, 0, kIn, kIn / 8, tid);
+  stage_k(sW2, a.w2, kHid, true, 0, kHid, kHid, 0, kHid, kHid / 8, tid);
+  stage_k(sW3, a.w3, kHid, true, 0, kOut, 16, 0, kHid, kHid / 8, tid);   // rows 2..15 zero
+  cp_commit();
+  for (int i = tid; i < kHid; i += kGemmThreads) {
+    sb[i] = a.p[kOffB1 + i];
+    sb[kHid + i] = a.p[kOffB2 + i];
+  }
+  if (tid < kOut) sb[2 * kHid + tid] = a.p[kOffB3 + tid];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        tc::saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar)) : "memory");
+  cp_wait<0>();
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tmem_base, s_mbar = tc::saddr(&mbar);
+  const int quad = warp & 3, half = warp >> 2;
+  const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
+  const int r = quad * 32 + lane;                  // this thread's row of the tile (TMEM lane)
+  const int64_t row = m0 + r;
+  const bool live = row < a.n;
+  uint32_t phase = 0;
+  // one layer: the MMAs (K = 16 each) by thread 0, a bounded wait by all
+  auto layer = [&](const unsigned char* A, const unsigned char* B, int kc, uint32_t idesc) {
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t aA = tc::saddr(A), aB = tc::saddr(B);
+      for (int kk = 0; kk < kc / 2; ++kk)
+        tc::mma(tm, tc::smem_desc(aA + kk * 256, 128, kc * 128),
+                tc::smem_desc(aB + kk * 256, 128, kc * 128), idesc, kk > 0 ? 1u : 0u);
+      tc::commit(s_mbar);
+    }
+    const bool w = tc::wait_phase(s_mbar, phase);
+    phase ^= 1u;
+    const bool bad = __syncthreads_or(!w);
+    tc::fence_after();
+    return !bad;
+  };
+  // hidden-layer epilogue: Z = acc + bias, H = silu(Z) to global and to sH
+  auto hidden = [&](bool ok, const float* bias, float* Z, __nv_bfloat16* H) {
+#pragma unroll 1
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+      float v[32];
+      if (ok) {
+        tc::ld32(lane_addr + c0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __int_as_float(0x7fffffff);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += bias[c0 + j];
+      if (live && Z) {
+        float4* zp = reinterpret_cast<float4*>(Z + row * kHid + c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) zp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 hq = make_uint4(pack_bf16(silu(v[8 * q]), silu(v[8 * q + 1])),
+                                    pack_bf16(silu(v[8 * q + 2]), silu(v[8 * q + 3])),
+                                    pack_bf16(silu(v[8 * q + 4]), silu(v[8 * q + 5])),
+                                    pack_bf16(silu(v[8 * q + 6]), silu(v[8 * q + 7])));
+        if (live) *reinterpret_cast<uint4*>(H + row * kHid + c0 + 8 * q) = hq;
+        *reinterpret_cast<uint4*>(sH + tc::cm_off(r, c0 + 8 * q, kHid / 8)) = hq;
+      }
+    }
+    // sH complete (and the accumulator read) before the next layer's MMAs
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+  };
+  constexpr uint32_t kIdH = tc::idesc_bf16(128, 128), kIdO = tc::idesc_bf16(128, 16);
+  bool ok = layer(sX, sW1, kIn / 8, kIdH);
+  hidden(ok, sb, a.Z1, a.H1);
+  if (ok) ok = layer(sH, sW2, kHid / 8, kIdH);
+  hidden(ok, sb + kHid, a.Z2, a.H2);
+  if (ok) ok = layer(sH, sW3, kHid / 8, kIdO);
+  if (half == 0) {
+    float y[2] = {__int_as_float(0x7fffffff), __int_as_float(0x7fffffff)};
+    if (ok) tc::ld2(lane_addr, y);
+    if (live) {
+      a.Y[row * kOut] = y[0] + sb[2 * kHid];
+      a.Y[row * kOut + 1] = y[1] + sb[2 * kHid + 1];
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(a.err, 1);
+    // an MMA may still be in flight: one more bounded wait before TMEM is freed
+    tc::wait_phase(s_mbar, phase ^ 1u);
   }
   tc::fence_before();
   __syncthreads();
@@ -847,13 +935,15 @@ struct sdcef_mlp {
   int step;
   int launches;
   int sms;                              // multiprocessors of the device
+  cudaStream_t aux;                     // weight gradients beside the dZ chain
+  cudaEvent_t ev[4];
 };
 
 namespace {
 
 int cuda_fail(cudaError_t e) { return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e)); }
 
-cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a) {
+cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   if (a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaSuccess;
   TcGemm g;
   memset(&g, 0, sizeof(g));
@@ -863,7 +953,7 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a) {
   g.B = reinterpret_cast<const uint16_t*>(a.B);
   g.sbn = a.transB ? a.ldb : 1; g.sbk = a.transB ? 1 : a.ldb;
   g.C = a.C; g.scm = a.ldc; g.scn = 1;
-  g.bias = a.bias; g.H = a.H; g.ldh = a.ldh; g.Zin = a.Zin; g.ldz = a.ldz; g.colsum = a.colsum;
+  g.H = a.H; g.ldh = a.ldh; g.Zin = a.Zin; g.ldz = a.ldz; g.colsum = a.colsum;
   g.err = (int*)h->loss + 5;
   if (g.epi == 0 && g.M < 64 && g.N > g.M) {
     // C^T = B^T A^T: the long side of the product goes on the 128 TMEM lanes
@@ -885,7 +975,7 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a) {
   }
   const uint32_t smem = 4 * kOpBytes + (g.sak != 1 ? nat_bytes(128) : 0) + (g.sbk != 1 ? nat_bytes(Np) : 0);
   // M (the sample dimension of the layer GEMMs) on grid.x, whose limit is 2^31 - 1
-  gemm_tc_kernel<<<dim3(tiles, splits), kGemmThreads, smem, h->st>>>(g);
+  gemm_tc_kernel<<<dim3(tiles, splits), kGemmThreads, smem, st>>>(g);
   ++h->launches;
   return cudaGetLastError();
 }
@@ -898,25 +988,24 @@ GemmArgs ga() {
 
 // forward through the three layers for n rows of X; fills Z1, H1, Z2, H2, Y
 cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n, bool keep_z) {
-  GemmArgs g = ga();
-  g.M = (int)n; g.N = kHid; g.K = kIn;
-  g.A = X; g.lda = kIn; g.B = h->w1; g.ldb = kIn; g.transB = 1;
-  g.epi = 1; g.bias = h->p + kOffB1; g.C = keep_z ? h->Z1 : nullptr; g.ldc = kHid;
-  g.H = h->H1; g.ldh = kHid;
-  cudaError_t e = gemm(h, g);
-  if (e != cudaSuccess) return e;
-  g = ga();
-  g.M = (int)n; g.N = kHid; g.K = kHid;
-  g.A = h->H1; g.lda = kHid; g.B = h->w2; g.ldb = kHid; g.transB = 1;
-  g.epi = 1; g.bias = h->p + kOffB2; g.C = keep_z ? h->Z2 : nullptr; g.ldc = kHid;
-  g.H = h->H2; g.ldh = kHid;
-  e = gemm(h, g);
-  if (e != cudaSuccess) return e;
-  g = ga();
-  g.M = (int)n; g.N = kOut; g.K = kHid;
-  g.A = h->H2; g.lda = kHid; g.B = h->w3; g.ldb = kHid; g.transB = 1;
-  g.epi = 3; g.bias = h->p + kOffB3; g.C = h->Y; g.ldc = kOut;
-  return gemm(h, g);
+  if (n <= 0) return cudaSuccess;
+  FwdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.X = reinterpret_cast<const uint16_t*>(X);
+  a.w1 = reinterpret_cast<const uint16_t*>(h->w1);
+  a.w2 = reinterpret_cast<const uint16_t*>(h->w2);
+  a.w3 = reinterpret_cast<const uint16_t*>(h->w3);
+  a.p = h->p;
+  a.Z1 = keep_z ? h->Z1 : nullptr;
+  a.Z2 = keep_z ? h->Z2 : nullptr;
+  a.H1 = h->H1;
+  a.H2 = h->H2;
+  a.Y = h->Y;
+  a.err = (int*)h->loss + 5;
+  fwd_tc_kernel<<<(unsigned)((n + 127) / 128), kGemmThreads, kFwSmem, h->st>>>(a);
+  ++h->launches;
+  return cudaGetLastError();
 }
 
 // gradients of the mean-squared loss over n rows into h->g (accumulated)
@@ -926,36 +1015,45 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64
   ++h->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // the weight gradients (split-K over the samples) run on the auxiliary
+  // stream beside the dZ chain, each once its operands exist
+  auto fork = [&](int i) {
+    cudaError_t r = cudaEventRecord(h->ev[i], h->st);
+    return r == cudaSuccess ? cudaStreamWaitEvent(h->aux, h->ev[i], 0) : r;
+  };
   // gW3 = dY^T H2
   GemmArgs g = ga();
   g.M = kOut; g.N = kHid; g.K = (int)n;
   g.A = h->dY; g.lda = kOut; g.transA = 1; g.B = h->H2; g.ldb = kHid;
   g.C = h->g + kOffW3; g.ldc = kHid; g.epi = 0;
-  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  if ((e = fork(0)) != cudaSuccess || (e = gemm(h, g, h->aux)) != cudaSuccess) return e;
   // dZ2 = (dY W3) * silu'(Z2); gb2 += colsum
   g = ga();
   g.M = (int)n; g.N = kHid; g.K = kOut;
   g.A = h->dY; g.lda = kOut; g.B = h->w3; g.ldb = kHid;
   g.epi = 2; g.Zin = h->Z2; g.ldz = kHid; g.H = h->dZ2; g.ldh = kHid; g.colsum = h->g + kOffB2;
-  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
   // gW2 = dZ2^T H1
   g = ga();
   g.M = kHid; g.N = kHid; g.K = (int)n;
   g.A = h->dZ2; g.lda = kHid; g.transA = 1; g.B = h->H1; g.ldb = kHid;
   g.C = h->g + kOffW2; g.ldc = kHid;
-  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  if ((e = fork(1)) != cudaSuccess || (e = gemm(h, g, h->aux)) != cudaSuccess) return e;
   // dZ1 = (dZ2 W2) * silu'(Z1); gb1 += colsum
   g = ga();
   g.M = (int)n; g.N = kHid; g.K = kHid;
   g.A = h->dZ2; g.lda = kHid; g.B = h->w2; g.ldb = kHid;
   g.epi = 2; g.Zin = h->Z1; g.ldz = kHid; g.H = h->dZ1; g.ldh = kHid; g.colsum = h->g + kOffB1;
-  if ((e = gemm(h, g)) != cudaSuccess) return e;
+  if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
   // gW1 = dZ1^T X
   g = ga();
   g.M = kHid; g.N = kIn; g.K = (int)n;
   g.A = h->dZ1; g.lda = kHid; g.transA = 1; g.B = X; g.ldb = kIn;
   g.C = h->g + kOffW1; g.ldc = kIn;
-  return gemm(h, g);
+  if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
+  // join: the gradient is complete on the caller's stream
+  if ((e = cudaEventRecord(h->ev[2], h->aux)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(h->st, h->ev[2], 0);
 }
 
 FeatArgs feat_args(const sdcef_batch* b) {
@@ -1001,7 +1099,15 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kGemmSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kFwSmem);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
+      for (cudaEvent_t ev : h->ev) if (ev) cudaEventDestroy(ev);
+      if (h->aux) cudaStreamDestroy(h->aux);
       delete h;
       return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
     }
@@ -1020,6 +1126,8 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(*a.p, 0, a.bytes);
     if (e != cudaSuccess) {
       for (auto& b : al) if (*b.p) cudaFree(*b.p);
+      for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
+      cudaStreamDestroy(h->aux);
       delete h;
       return report_error(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
     }
@@ -1031,6 +1139,9 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
 int sdcef_mlp_destroy(sdcef_mlp* h) {
   if (!h) return SDCEF_SUCCESS;
   cudaStreamSynchronize(h->st);
+  cudaStreamSynchronize(h->aux);
+  for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
+  cudaStreamDestroy(h->aux);
   void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->Z1, h->Z2, h->Y, h->loss,
                 h->H1, h->H2, h->dY, h->dZ2, h->dZ1, h->X};
   for (void* p : ps) cudaFree(p);
