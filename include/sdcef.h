@@ -427,6 +427,11 @@ int sdcef_mlp_guess(sdcef_mlp* mlp, const sdcef_batch* batch, int64_t ncells, in
                     double* ne_guess, double* phi_guess);
 /* Kernel launches enqueued by the last forward / grad / train_step / guess call. */
 int sdcef_mlp_last_launch_count(const sdcef_mlp* mlp);
+/* Synchronises the stream and reports whether a tensor-core wait of an earlier
+ * forward / grad / train_step / guess call ran out (its kernels bound every
+ * wait; the affected rows were written as NaN): SDCEF_ERR_CUDA with a message
+ * if so, SDCEF_SUCCESS otherwise. Clears the condition. */
+int sdcef_mlp_check(sdcef_mlp* mlp);
 
 /* Message of the last error on this thread (static storage). */
 const char* sdcef_last_error(void);

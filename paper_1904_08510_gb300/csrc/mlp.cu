@@ -1298,7 +1298,7 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
   if (ncells * 5 > h->max_rows * (kIn / 2))
     return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
   g.stage = (float*)h->X;        // [cells][5] FP32 inside the [max_rows][32] BF16 buffer
-  cudaError_t e = cudaMemsetAsync(g.queue, 0, 2 * sizeof(int), h->st);
+  cudaError_t e = cudaMemsetAsync(g.queue, 0, sizeof(int), h->st);
   if (e != cudaSuccess) return cuda_fail(e);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1315,5 +1315,18 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
 }
 
 int sdcef_mlp_last_launch_count(const sdcef_mlp* h) { return h ? h->launches : 0; }
+
+int sdcef_mlp_check(sdcef_mlp* h) {
+  if (!h) return report_error(SDCEF_ERR_INVALID, "mlp_check: NULL");
+  int* word = (int*)h->loss + 5;
+  int flag = 0;
+  cudaError_t e = cudaStreamSynchronize(h->aux);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, word, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(word, 0, sizeof(int), h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return flag ? report_error(SDCEF_ERR_CUDA, "mlp: a tensor-core wait timed out (outputs set to NaN)")
+              : SDCEF_SUCCESS;
+}
 
 }  // extern "C"

@@ -39,7 +39,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
            "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
-           "sdcef_mlp_set_state")
+           "sdcef_mlp_set_state", "sdcef_mlp_check")
 MLP_NPARAM = 20994
 GUESS_NE, GUESS_PHI = 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -126,13 +126,14 @@ def lib():
         L.sdcef_mlp_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp]
         L.sdcef_mlp_guess.argtypes = [vp, B, i64, C.c_int, vp, vp]
         L.sdcef_mlp_last_launch_count.argtypes = [vp]
+        L.sdcef_mlp_check.argtypes = [vp]
         L.sdcef_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
         L.sdcef_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
         for f in ("sdcef_mlp_create", "sdcef_mlp_destroy", "sdcef_mlp_set_params",
                   "sdcef_mlp_get_params", "sdcef_mlp_features", "sdcef_mlp_targets",
                   "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
                   "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
-                  "sdcef_mlp_set_state"):
+                  "sdcef_mlp_set_state", "sdcef_mlp_check"):
             getattr(L, f).restype = C.c_int
         for f in ("sdcef_create", "sdcef_destroy", "sdcef_set_params", "sdcef_solve_batch",
                   "sdcef_solve_batch_host", "sdcef_residual_batch", "sdcef_precond_apply_batch",
@@ -460,6 +461,10 @@ class MLP:
 
     def launches(self) -> int:
         return int(lib().sdcef_mlp_last_launch_count(self.h))
+
+    def check(self):
+        """Raise if a tensor-core wait of an earlier call ran out (synchronises)."""
+        _check(lib().sdcef_mlp_check(self.h))
 
     def features(self, db: DeviceBatch):
         import torch

@@ -117,6 +117,7 @@ def test_adam_step_matches_oracle():
     X = torch.as_tensor(Xh, dtype=torch.float32, device=d).to(torch.bfloat16)
     T = torch.as_tensor(Th, dtype=torch.float32, device=d)
     mlp.train_step(X, T, 1e-3)
+    mlp.check()                       # no tensor-core wait ran out
     got = S.unpack_params(mlp.get_params())
     p0 = S.unpack_params(flat.astype(np.float64))
     # first Adam step moves every parameter with a non-negligible gradient by ~lr
