@@ -507,18 +507,28 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
 // epilogue (two warps per TMEM lane quadrant, each on half of the columns)
 // adds the bias, writes Z (FP32, optional) and H = silu(Z) (BF16) to global
 // memory, and writes H into shared memory as the A operand of the next layer,
-// so H1 and H2 are not read back from global memory. Every wait on the
-// mbarrier is bounded; a CTA whose MMAs do not complete sets the error word
-// and writes NaN instead of its results.
+// so H1 and H2 are not read back from global memory. The output layer
+// accumulates in TMEM columns of its own, so that in training the same
+// kernel goes on from Y to the loss against T (dY = (Y - T) / n, the loss and
+// the bias gradient of the output layer) and to the first backward product
+// dZ2 = (dY W3) * silu'(Z2), read straight from the layer-2 accumulator:
+// Z2 never goes to global memory. Every wait on the mbarrier is bounded; a
+// CTA whose MMAs do not complete sets the error word and writes NaN instead
+// of its results.
 // --------------------------------------------------------------------------
 struct FwdArgs {
   int64_t n;
   const uint16_t* X;                  // [n][32] BF16
   const uint16_t *w1, *w2, *w3;       // [128][32], [128][128], [2][128] BF16
   const float* p;                     // FP32 parameters (biases)
-  float *Z1, *Z2;                     // [n][128] FP32, nullable
+  float* Z1;                          // [n][128] FP32 (training)
   __nv_bfloat16 *H1, *H2;             // [n][128] BF16
-  float* Y;                           // [n][2] FP32
+  float* Y;                           // [n][2] FP32, nullable
+  // training (T != nullptr): the MSE loss and the first backward step
+  const float* T;                     // [n][2] FP32 targets
+  float inv_n;                        // 1 / n
+  __nv_bfloat16 *dY, *dZ2;            // [n][2], [n][128] BF16
+  float *loss, *gb2, *gb3;            // accumulated with atomics
   int* err;
 };
 
@@ -536,6 +546,9 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ float sb[2 * kHid + kOut];
+  __shared__ float sw3[kOut][kHid];   // the BF16 W3 as FP32 (dZ2 product)
+  __shared__ float sdy[128][kOut];    // the BF16-rounded dY of the tile's rows
+  __shared__ float sred[4][3];        // per-warp loss and output-bias partials
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
   const bool vecX = (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
@@ -549,8 +562,10 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
     sb[kHid + i] = a.p[kOffB2 + i];
   }
   if (tid < kOut) sb[2 * kHid + tid] = a.p[kOffB3 + tid];
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+  for (int i = tid; i < kOut * kHid; i += kGemmThreads)
+    sw3[i / kHid][i % kHid] = __uint_as_float((uint32_t)a.w3[i] << 16);
+  if (warp == 0) {   // columns 0..127: hidden layers; 128..143: output layer
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
         tc::saddr(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -569,12 +584,13 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   const bool live = row < a.n;
   uint32_t phase = 0;
   // one layer: the MMAs (K = 16 each) by thread 0, a bounded wait by all
-  auto layer = [&](const unsigned char* A, const unsigned char* B, int kc, uint32_t idesc) {
+  auto layer = [&](const unsigned char* A, const unsigned char* B, int kc, uint32_t idesc,
+                   uint32_t dcol) {
     if (tid == 0) {
       tc::fence_after();
       const uint32_t aA = tc::saddr(A), aB = tc::saddr(B);
       for (int kk = 0; kk < kc / 2; ++kk)
-        tc::mma(tm, tc::smem_desc(aA + kk * 256, 128, kc * 128),
+        tc::mma(tm + dcol, tc::smem_desc(aA + kk * 256, 128, kc * 128),
                 tc::smem_desc(aB + kk * 256, 128, kc * 128), idesc, kk > 0 ? 1u : 0u);
       tc::commit(s_mbar);
     }
@@ -618,17 +634,80 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
     __syncthreads();
   };
   constexpr uint32_t kIdH = tc::idesc_bf16(128, 128), kIdO = tc::idesc_bf16(128, 16);
-  bool ok = layer(sX, sW1, kIn / 8, kIdH);
+  bool ok = layer(sX, sW1, kIn / 8, kIdH, 0);
   hidden(ok, sb, a.Z1, a.H1);
-  if (ok) ok = layer(sH, sW2, kHid / 8, kIdH);
-  hidden(ok, sb + kHid, a.Z2, a.H2);
-  if (ok) ok = layer(sH, sW3, kHid / 8, kIdO);
+  if (ok) ok = layer(sH, sW2, kHid / 8, kIdH, 0);
+  hidden(ok, sb + kHid, nullptr, a.H2);   // Z2 stays in TMEM
+  if (ok) ok = layer(sH, sW3, kHid / 8, kIdO, 128);
+  const float qnan = __int_as_float(0x7fffffff);
   if (half == 0) {
-    float y[2] = {__int_as_float(0x7fffffff), __int_as_float(0x7fffffff)};
-    if (ok) tc::ld2(lane_addr, y);
-    if (live) {
-      a.Y[row * kOut] = y[0] + sb[2 * kHid];
-      a.Y[row * kOut + 1] = y[1] + sb[2 * kHid + 1];
+    float y[2] = {qnan, qnan};
+    if (ok) tc::ld2(lane_addr + 128, y);
+    y[0] += sb[2 * kHid];
+    y[1] += sb[2 * kHid + 1];
+    if (live && a.Y) {
+      a.Y[row * kOut] = y[0];
+      a.Y[row * kOut + 1] = y[1];
+    }
+    if (a.T) {
+      // MSE loss 1/(2n) sum |Y - T|^2: dY = (Y - T) / n in BF16 for the
+      // backward GEMMs, the output-layer bias gradient from the FP32 values
+      const float d0 = live ? y[0] - a.T[row * kOut] : 0.0f;
+      const float d1 = live ? y[1] - a.T[row * kOut + 1] : 0.0f;
+      const float e0 = d0 * a.inv_n, e1 = d1 * a.inv_n;
+      const __nv_bfloat16 q0 = __float2bfloat16(e0), q1 = __float2bfloat16(e1);
+      if (live) {
+        a.dY[row * kOut] = q0;
+        a.dY[row * kOut + 1] = q1;
+      }
+      sdy[r][0] = __bfloat162float(q0);
+      sdy[r][1] = __bfloat162float(q1);
+      float l = d0 * d0 + d1 * d1, g0 = e0, g1 = e1;
+      for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+      }
+      if (lane == 0) {
+        sred[quad][0] = l;
+        sred[quad][1] = g0;
+        sred[quad][2] = g1;
+      }
+    }
+  }
+  __syncthreads();
+  if (a.T) {
+    if (tid < 3) {
+      const float v = sred[0][tid] + sred[1][tid] + sred[2][tid] + sred[3][tid];
+      atomicAdd(tid == 0 ? a.loss : a.gb3 + (tid - 1), tid == 0 ? v * 0.5f * a.inv_n : v);
+    }
+    // dZ2 = (dY W3) * silu'(Z2), Z2 = layer-2 accumulator + b2; the column
+    // sums of dZ2 are the layer-2 bias gradient
+#pragma unroll 1
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+      float v[32];
+      if (ok) {
+        tc::ld32(lane_addr + c0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = qnan;
+      }
+      const float dy0 = sdy[r][0], dy1 = sdy[r][1];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        const float g = fmaf(dy1, sw3[1][c], dy0 * sw3[0][c]);
+        v[j] = live ? g * silu_grad(v[j] + sb[kHid + c]) : 0.0f;
+      }
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(a.dZ2 + row * kHid + c0 + 8 * q) =
+              make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                         pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+      }
+      const float cs = warp_colsum32(v, lane);
+      atomicAdd(&a.gb2[c0 + lane], cs);
     }
   }
   if (!ok) {
@@ -639,7 +718,7 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   tc::fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tm));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tm));
 }
 
 // --------------------------------------------------------------------------
@@ -865,34 +944,6 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
                  "n"(tc::kTmemCols));
 }
 
-// MSE loss: dY = 2 (Y - T) / (2 n) (BF16 for the backward GEMMs), loss and
-// the bias gradient of the output layer accumulated with atomics.
-__global__ void loss_kernel(const float* Y, const float* T, int64_t n, __nv_bfloat16* dY,
-                            float* loss, float* gb3) {
-  float l = 0.0f, g0 = 0.0f, g1 = 0.0f;
-  const float sc = 1.0f / (float)n;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    float d0 = Y[2 * s] - T[2 * s], d1 = Y[2 * s + 1] - T[2 * s + 1];
-    l += d0 * d0 + d1 * d1;
-    float e0 = d0 * sc, e1 = d1 * sc;   // 2 d / (2 n)
-    dY[2 * s] = __float2bfloat16(e0);
-    dY[2 * s + 1] = __float2bfloat16(e1);
-    g0 += e0;
-    g1 += e1;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    l += __shfl_xor_sync(0xffffffffu, l, o);
-    g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-    g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(loss, l * 0.5f * sc);
-    atomicAdd(&gb3[0], g0);
-    atomicAdd(&gb3[1], g1);
-  }
-}
-
 // Adam (Kingma & Ba 2015) with bias correction; refreshes the BF16 weight
 // copies and clears the gradient for the next step.
 __global__ void adam_kernel(float* p, float* g, float* m, float* v, int n, float lr, float b1,
@@ -930,13 +981,13 @@ struct sdcef_mlp {
   cudaStream_t st;
   float *p, *g, *m, *v;                 // FP32 parameters, gradients, Adam moments
   __nv_bfloat16 *w1, *w2, *w3;          // BF16 weight copies
-  float *Z1, *Z2, *Y, *loss;            // activations (FP32)
+  float *Z1, *Y, *loss;                 // activations (FP32)
   __nv_bfloat16 *H1, *H2, *dY, *dZ2, *dZ1, *X;   // BF16 activations / features
   int step;
   int launches;
   int sms;                              // multiprocessors of the device
   cudaStream_t aux;                     // weight gradients beside the dZ chain
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[2];
 };
 
 namespace {
@@ -987,7 +1038,10 @@ GemmArgs ga() {
 }
 
 // forward through the three layers for n rows of X; fills Z1, H1, Z2, H2, Y
-cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n, bool keep_z) {
+// forward through the three layers for n rows of X. Inference (T == nullptr):
+// Y (FP32 [n][2]) only. Training: Z1, H1, H2 for the backward GEMMs, and the
+// loss, dY, dZ2 and the bias gradients of layers 2 and 3 (into h->g).
+cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t n, float* Y) {
   if (n <= 0) return cudaSuccess;
   FwdArgs a;
   memset(&a, 0, sizeof(a));
@@ -997,48 +1051,45 @@ cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n, bool keep_z
   a.w2 = reinterpret_cast<const uint16_t*>(h->w2);
   a.w3 = reinterpret_cast<const uint16_t*>(h->w3);
   a.p = h->p;
-  a.Z1 = keep_z ? h->Z1 : nullptr;
-  a.Z2 = keep_z ? h->Z2 : nullptr;
   a.H1 = h->H1;
   a.H2 = h->H2;
-  a.Y = h->Y;
+  a.Y = Y;
+  if (T) {
+    a.Z1 = h->Z1;
+    a.T = T;
+    a.inv_n = 1.0f / (float)n;
+    a.dY = h->dY;
+    a.dZ2 = h->dZ2;
+    a.loss = h->loss;
+    a.gb2 = h->g + kOffB2;
+    a.gb3 = h->g + kOffB3;
+  }
   a.err = (int*)h->loss + 5;
   fwd_tc_kernel<<<(unsigned)((n + 127) / 128), kGemmThreads, kFwSmem, h->st>>>(a);
   ++h->launches;
   return cudaGetLastError();
 }
 
-// gradients of the mean-squared loss over n rows into h->g (accumulated)
-cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t n) {
-  int nb = (int)std::min<int64_t>(1216, (n + 255) / 256);
-  loss_kernel<<<std::max(nb, 1), 256, 0, h->st>>>(h->Y, T, n, h->dY, h->loss, h->g + kOffB3);
-  ++h->launches;
-  cudaError_t e = cudaGetLastError();
+// gradients of the mean-squared loss over n rows into h->g (accumulated),
+// after forward(.., T, ..) produced dY, dZ2 and the layer-2/3 bias gradients
+cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n) {
+  // the weight gradients of layers 3 and 2 (split-K over the samples) run on
+  // the auxiliary stream beside dZ1 and gW1
+  cudaError_t e = cudaEventRecord(h->ev[0], h->st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev[0], 0);
   if (e != cudaSuccess) return e;
-  // the weight gradients (split-K over the samples) run on the auxiliary
-  // stream beside the dZ chain, each once its operands exist
-  auto fork = [&](int i) {
-    cudaError_t r = cudaEventRecord(h->ev[i], h->st);
-    return r == cudaSuccess ? cudaStreamWaitEvent(h->aux, h->ev[i], 0) : r;
-  };
   // gW3 = dY^T H2
   GemmArgs g = ga();
   g.M = kOut; g.N = kHid; g.K = (int)n;
   g.A = h->dY; g.lda = kOut; g.transA = 1; g.B = h->H2; g.ldb = kHid;
   g.C = h->g + kOffW3; g.ldc = kHid; g.epi = 0;
-  if ((e = fork(0)) != cudaSuccess || (e = gemm(h, g, h->aux)) != cudaSuccess) return e;
-  // dZ2 = (dY W3) * silu'(Z2); gb2 += colsum
-  g = ga();
-  g.M = (int)n; g.N = kHid; g.K = kOut;
-  g.A = h->dY; g.lda = kOut; g.B = h->w3; g.ldb = kHid;
-  g.epi = 2; g.Zin = h->Z2; g.ldz = kHid; g.H = h->dZ2; g.ldh = kHid; g.colsum = h->g + kOffB2;
-  if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
+  if ((e = gemm(h, g, h->aux)) != cudaSuccess) return e;
   // gW2 = dZ2^T H1
   g = ga();
   g.M = kHid; g.N = kHid; g.K = (int)n;
   g.A = h->dZ2; g.lda = kHid; g.transA = 1; g.B = h->H1; g.ldb = kHid;
   g.C = h->g + kOffW2; g.ldc = kHid;
-  if ((e = fork(1)) != cudaSuccess || (e = gemm(h, g, h->aux)) != cudaSuccess) return e;
+  if ((e = gemm(h, g, h->aux)) != cudaSuccess) return e;
   // dZ1 = (dZ2 W2) * silu'(Z1); gb1 += colsum
   g = ga();
   g.M = (int)n; g.N = kHid; g.K = kHid;
@@ -1052,8 +1103,8 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64
   g.C = h->g + kOffW1; g.ldc = kIn;
   if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
   // join: the gradient is complete on the caller's stream
-  if ((e = cudaEventRecord(h->ev[2], h->aux)) != cudaSuccess) return e;
-  return cudaStreamWaitEvent(h->st, h->ev[2], 0);
+  if ((e = cudaEventRecord(h->ev[1], h->aux)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(h->st, h->ev[1], 0);
 }
 
 FeatArgs feat_args(const sdcef_batch* b) {
@@ -1103,7 +1154,7 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
       e = cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFwSmem);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
       e = cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
       for (cudaEvent_t ev : h->ev) if (ev) cudaEventDestroy(ev);
@@ -1117,7 +1168,7 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
   struct Alloc { void** p; size_t bytes; } al[] = {
       {(void**)&h->p, kNParam * 4}, {(void**)&h->g, kNParam * 4}, {(void**)&h->m, kNParam * 4},
       {(void**)&h->v, kNParam * 4}, {(void**)&h->w1, kHid * kIn * 2}, {(void**)&h->w2, kHid * kHid * 2},
-      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->Z1, R * kHid * 4}, {(void**)&h->Z2, R * kHid * 4},
+      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->Z1, R * kHid * 4},
       {(void**)&h->Y, R * kOut * 4}, {(void**)&h->loss, 64}, {(void**)&h->H1, R * kHid * 2},
       {(void**)&h->H2, R * kHid * 2}, {(void**)&h->dY, R * kOut * 2}, {(void**)&h->dZ2, R * kHid * 2},
       {(void**)&h->dZ1, R * kHid * 2}, {(void**)&h->X, R * kIn * 2}};
@@ -1142,7 +1193,7 @@ int sdcef_mlp_destroy(sdcef_mlp* h) {
   cudaStreamSynchronize(h->aux);
   for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
   cudaStreamDestroy(h->aux);
-  void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->Z1, h->Z2, h->Y, h->loss,
+  void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->Z1, h->Y, h->loss,
                 h->H1, h->H2, h->dY, h->dZ2, h->dZ1, h->X};
   for (void* p : ps) cudaFree(p);
   delete h;
@@ -1233,9 +1284,7 @@ int sdcef_mlp_forward(sdcef_mlp* h, const void* X_bf16, int64_t n, float* Y) {
   if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_forward: n exceeds max_rows");
   if (n == 0) return SDCEF_SUCCESS;
   h->launches = 0;
-  cudaError_t e = forward(h, (const __nv_bfloat16*)X_bf16, n, false);
-  if (e == cudaSuccess && Y)
-    e = cudaMemcpyAsync(Y, h->Y, (size_t)n * kOut * 4, cudaMemcpyDeviceToDevice, h->st);
+  cudaError_t e = forward(h, (const __nv_bfloat16*)X_bf16, nullptr, n, Y ? Y : h->Y);
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
 }
 
@@ -1246,8 +1295,8 @@ int sdcef_mlp_grad(sdcef_mlp* h, const void* X_bf16, const float* T, int64_t n, 
   h->launches = 0;
   cudaError_t e = cudaMemsetAsync(h->g, 0, kNParam * 4, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->loss, 0, 4, h->st);
-  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, n, true);
-  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, T, n);
+  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, T, n, nullptr);
+  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, n);
   if (e == cudaSuccess && grads)
     e = cudaMemcpyAsync(grads, h->g, kNParam * 4, cudaMemcpyDeviceToDevice, h->st);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, h->loss, 4, cudaMemcpyDeviceToDevice, h->st);
@@ -1262,8 +1311,8 @@ int sdcef_mlp_train_step(sdcef_mlp* h, const void* X_bf16, const float* T, int64
   if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_train_step: n exceeds max_rows");
   h->launches = 0;
   cudaError_t e = cudaMemsetAsync(h->loss, 0, 4, h->st);
-  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, n, true);
-  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, T, n);
+  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, T, n, nullptr);
+  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, n);
   if (e != cudaSuccess) return cuda_fail(e);
   h->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
