@@ -599,16 +599,16 @@ def extras(args, S, b, db, solver, params, dev):
 
 
 # algorithmic bytes per sample of one training step (each operand read once,
-# each result written once): forward 64 + 768 | 256 + 768 | 256 + 8, loss
-# 16 + 4, gW3 4 + 256, dZ2 4 + 512 + 256, gW2 256 + 256, dZ1 256 + 512 + 256,
-# gW1 256 + 64
-MLP_STEP_BYTES_PER_SAMPLE = 832 + 1024 + 264 + 20 + 260 + 772 + 512 + 1024 + 320
+# each result written once): forward + loss + dZ2 reads X 64 and T 8 and writes
+# Z1 512, H1 256, H2 256, dY 4, dZ2 256; gW3 4 + 256, gW2 256 + 256,
+# dZ1 256 + 512 + 256, gW1 256 + 64
+MLP_STEP_BYTES_PER_SAMPLE = 1356 + 260 + 512 + 1024 + 320
 MLP_STEP_FLOPS_PER_SAMPLE = 3 * 2 * (32 * 128 + 128 * 128 + 128 * 2)
 
 
 def mlp_training_leg(S, dev):
-    """One Adam step of the learned-guess network (forward, MSE, backward:
-    eight BF16 GEMMs on tcgen05 with fused epilogues, loss and Adam kernels)
+    """One Adam step of the learned-guess network (forward, MSE loss and dZ2 in
+    one tcgen05 kernel, four backward GEMMs on tcgen05, Adam)
     on synthetic features, at the training batch and at a streaming size;
     the epoch estimate is for the 51.2 M samples of 200k solves x 256 cells."""
     import torch
