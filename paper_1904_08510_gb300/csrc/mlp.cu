@@ -310,6 +310,9 @@ __device__ __forceinline__ float warp_colsum32(float* v, int lane) {
   return v[0];
 }
 
+// EPI: the epilogue (0 or 2); AMN / BMN: operand A / B has contiguous rows
+// (staged through the row-major copy and ldmatrix.trans) rather than contiguous k
+template <int EPI, bool AMN, bool BMN>
 __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   extern __shared__ __align__(1024) unsigned char gsm[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -318,10 +321,14 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   const int64_t m0 = (int64_t)blockIdx.x * 128;
   const int kbeg = blockIdx.y * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
   const int Np = (g.N + 15) & ~15;
-  const bool amn = g.sak != 1, bmn = g.sbk != 1;
+  constexpr bool amn = AMN, bmn = BMN;
+  // operand buffers: two per operand, except when both operands go through the
+  // row-major copies: then the copies carry the next slab and one buffer each
+  // (written after the previous slab's MMAs have finished) suffices
+  constexpr int NB = (AMN && BMN) ? 1 : 2;
   unsigned char* opA = gsm;
-  unsigned char* opB = gsm + 2 * kOpBytes;
-  unsigned char* natA = gsm + 4 * kOpBytes;
+  unsigned char* opB = gsm + NB * kOpBytes;
+  unsigned char* natA = gsm + 2 * NB * kOpBytes;
   unsigned char* natB = natA + (amn ? nat_bytes(128) : 0);
   const bool vecA = ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0) && (((amn ? g.sak : g.sam) & 7) == 0);
   const bool vecB = ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0) && (((bmn ? g.sbk : g.sbn) & 7) == 0);
@@ -343,9 +350,12 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   const int nslab = (kend - kbeg + kSlabK - 1) / kSlabK;   // >= 1 (the host keeps kbeg < K)
   // slabs in flight: two when both operands go straight to their buffers,
   // one when a row-major copy (a single buffer per operand) is transposed
-  const int L = (amn || bmn) ? 1 : 2;
+  constexpr int L = (amn || bmn) ? 1 : 2;
+  // the mbarrier that slab s's MMAs complete, and the parity of that completion
+  auto bar_of = [&](int s) { return tc::saddr(&mbar[NB == 2 ? (s & 1) : 0]); };
+  auto par_of = [&](int s) { return (uint32_t)(NB == 2 ? ((s >> 1) & 1) : (s & 1)); };
   auto issue = [&](int s) {
-    const int b = s & 1, k0 = kbeg + s * kSlabK;
+    const int b = NB == 2 ? (s & 1) : 0, k0 = kbeg + s * kSlabK;
     const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
     if (!amn) stage_k(opA + b * kOpBytes, g.A, g.sam, vecA, m0, g.M, 128, k0, kend, kc, tid);
     else stage_nat(natA, nat_pitch(128), g.A, g.sak, vecA, m0, g.M, 128, k0, kend, ks, tid);
@@ -357,7 +367,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   bool ok = true;
   int last = -1;                                           // last slab whose MMAs were committed
   for (int s = 0; s < nslab; ++s) {
-    const int b = s & 1, k0 = kbeg + s * kSlabK;
+    const int b = NB == 2 ? (s & 1) : 0, k0 = kbeg + s * kSlabK;
     const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
     if (L == 2 && s + 1 < nslab) cp_wait<1>();
     else cp_wait<0>();
@@ -365,6 +375,13 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
     unsigned char* sB = opB + b * kOpBytes;
     if (amn || bmn) {
       __syncthreads();
+      if (NB == 1 && s >= 1) {   // the single buffers: slab s - 1's MMAs have read them
+        const bool w = tc::wait_phase(bar_of(s - 1), par_of(s - 1));
+        if (__syncthreads_or(!w)) {
+          ok = false;
+          break;
+        }
+      }
       if (amn) nat_to_k(sA, natA, nat_pitch(128), 128, kc, warp, lane);
       if (bmn) nat_to_k(sB, natB, nat_pitch(Np), Np, kc, warp, lane);
     }
@@ -377,14 +394,14 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
       for (int kk = 0; kk < ks / 16; ++kk)
         tc::mma(tm, tc::smem_desc(aA + kk * 256, 128, kc * 128),
                 tc::smem_desc(aB + kk * 256, 128, kc * 128), idesc, (s > 0 || kk > 0) ? 1u : 0u);
-      tc::commit(tc::saddr(&mbar[b]));
+      tc::commit(bar_of(s));
     }
     last = s;
     const int nxt = s + L;
     if (nxt < nslab) {
-      // buffer nxt & 1 was last read by the MMAs of slab nxt - 2
-      if (nxt >= 2) {
-        const bool w = tc::wait_phase(tc::saddr(&mbar[nxt & 1]), ((nxt - 2) >> 1) & 1);
+      // with two buffers, buffer nxt & 1 was last read by the MMAs of slab nxt - 2
+      if (NB == 2 && nxt >= 2) {
+        const bool w = tc::wait_phase(bar_of(nxt - 2), par_of(nxt - 2));
         if (__syncthreads_or(!w)) {
           ok = false;
           break;
@@ -394,7 +411,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
     }
   }
   if (ok) {   // the last commit covers every MMA issued before it
-    const bool w = tc::wait_phase(tc::saddr(&mbar[last & 1]), (last >> 1) & 1);
+    const bool w = tc::wait_phase(bar_of(last), par_of(last));
     ok = !__syncthreads_or(!w);
   }
   tc::fence_after();
@@ -425,7 +442,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
       for (int j = 0; j < 32; ++j) v[j] = __int_as_float(0x7fffffff);
     }
     const bool full = c0 + 32 <= g.N;
-    if (g.epi == 0) {
+    if (EPI == 0) {
       if (live) {
         float* Cr = g.C + row * g.scm;
         if (full && g.scn == 1 && ((reinterpret_cast<uintptr_t>(Cr + c0) & 15) == 0)) {
@@ -439,7 +456,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
             if (c0 + j < g.N) atomicAdd(Cr + (c0 + j) * g.scn, v[j]);
         }
       }
-    } else if (g.epi == 2) {
+    } else {
       float z[32];
       if (full && tiled) {
         // Zin rows in with whole-row loads through the staging tile
@@ -491,7 +508,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
     cp_wait<0>();
     if (tid == 0) atomicExch(g.err, 1);
     // an MMA may still be in flight: one more bounded wait before TMEM is freed
-    if (last >= 0) tc::wait_phase(tc::saddr(&mbar[last & 1]), (last >> 1) & 1);
+    if (last >= 0) tc::wait_phase(bar_of(last), par_of(last));
   }
   tc::fence_before();
   __syncthreads();
@@ -1024,9 +1041,17 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
     g.kchunk = std::max((kc + kSlabK - 1) / kSlabK * kSlabK, 2 * kSlabK);
     splits = (g.K + g.kchunk - 1) / g.kchunk;
   }
-  const uint32_t smem = 4 * kOpBytes + (g.sak != 1 ? nat_bytes(128) : 0) + (g.sbk != 1 ? nat_bytes(Np) : 0);
+  const bool amn = g.sak != 1, bmn = g.sbk != 1;
+  const uint32_t smem = ((amn && bmn) ? 2 : 4) * kOpBytes + (amn ? nat_bytes(128) : 0) +
+                        (bmn ? nat_bytes(Np) : 0);
   // M (the sample dimension of the layer GEMMs) on grid.x, whose limit is 2^31 - 1
-  gemm_tc_kernel<<<dim3(tiles, splits), kGemmThreads, smem, st>>>(g);
+  const dim3 grid(tiles, splits);
+  if (g.epi == 0 && amn && bmn)
+    gemm_tc_kernel<0, true, true><<<grid, kGemmThreads, smem, st>>>(g);
+  else if (g.epi == 2 && !amn && bmn)
+    gemm_tc_kernel<2, false, true><<<grid, kGemmThreads, smem, st>>>(g);
+  else
+    return cudaErrorInvalidValue;   // a form the training step does not use
   ++h->launches;
   return cudaGetLastError();
 }
@@ -1148,8 +1173,11 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kGemmSmemMax);
+      e = cudaFuncSetAttribute(gemm_tc_kernel<0, true, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_tc_kernel<2, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmemMax);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFwSmem);
