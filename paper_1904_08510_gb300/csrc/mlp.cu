@@ -146,14 +146,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // Training GEMMs on the tcgen05 tensor cores: C[m][n] = sum_k A(m,k) B(k,n)
 // with A(m,k) = transA ? A[k*lda+m] : A[m*lda+k] and
 // B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n] (BF16), FP32 accumulators in TMEM.
-// Epilogues: 0 add C with atomics (split-K weight gradients); 2 dZ = acc *
-// silu'(Zin) (BF16) with the column sums of dZ added to colsum (the forward
-// runs fused, fwd_tc_kernel below).
+// Epilogues: kEpiAccumulate adds C with atomics (split-K weight gradients);
+// kEpiSiluGrad writes dZ = acc * silu'(Zin) (BF16) and adds the column sums of
+// dZ to colsum (the forward runs fused, fwd_tc_kernel below).
 //
 // A CTA of 256 threads computes 128 rows of C (row m0 + r in TMEM lane r) by
 // all N <= 128 columns (the MMA's N is N rounded up to 16) over its share of
-// K, in slabs of up to 64 k held in two shared-memory buffers, so the threads
-// stage slab s + 1 while the tensor core multiplies slab s. Each operand is
+// K, in slabs of up to 64 k, so that the threads stage slab s + 1 while the
+// tensor core multiplies slab s (two shared-memory buffers per operand, or
+// one when both operands go through the row-major copies, which then carry
+// the next slab). Each operand is
 // staged in the K-major core-matrix layout of mlp_tc.cuh, zero outside the
 // matrix: a K-contiguous operand by 16-byte asynchronous copies (cp.async)
 // that land in core-matrix order, an operand whose rows are contiguous by the
@@ -196,6 +198,7 @@ struct TcGemm {
   int* err;
 };
 
+constexpr int kEpiAccumulate = 0, kEpiSiluGrad = 2;         // GemmArgs::epi
 constexpr int kGemmThreads = 256;                           // two warps per TMEM lane quadrant
 constexpr int kSlabK = 64;                                  // k per slab
 constexpr uint32_t kOpBytes = 128 * kSlabK * 2;             // one operand slab
@@ -310,7 +313,7 @@ __device__ __forceinline__ float warp_colsum32(float* v, int lane) {
   return v[0];
 }
 
-// EPI: the epilogue (0 or 2); AMN / BMN: operand A / B has contiguous rows
+// EPI: the epilogue; AMN / BMN: operand A / B has contiguous rows
 // (staged through the row-major copy and ldmatrix.trans) rather than contiguous k
 template <int EPI, bool AMN, bool BMN>
 __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
       for (int j = 0; j < 32; ++j) v[j] = __int_as_float(0x7fffffff);
     }
     const bool full = c0 + 32 <= g.N;
-    if (EPI == 0) {
+    if (EPI == kEpiAccumulate) {
       if (live) {
         float* Cr = g.C + row * g.scm;
         if (full && g.scn == 1 && ((reinterpret_cast<uintptr_t>(Cr + c0) & 15) == 0)) {
@@ -1023,7 +1026,7 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   g.C = a.C; g.scm = a.ldc; g.scn = 1;
   g.H = a.H; g.ldh = a.ldh; g.Zin = a.Zin; g.ldz = a.ldz; g.colsum = a.colsum;
   g.err = (int*)h->loss + 5;
-  if (g.epi == 0 && g.M < 64 && g.N > g.M) {
+  if (g.epi == kEpiAccumulate && g.M < 64 && g.N > g.M) {
     // C^T = B^T A^T: the long side of the product goes on the 128 TMEM lanes
     std::swap(g.M, g.N); std::swap(g.A, g.B); std::swap(g.sam, g.sbn); std::swap(g.sak, g.sbk);
     std::swap(g.scm, g.scn);
@@ -1033,7 +1036,7 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   const int tiles = (g.M + 127) / 128, Np = (g.N + 15) & ~15;
   int splits = 1;
   g.kchunk = (g.K + kSlabK - 1) / kSlabK * kSlabK;
-  if (g.epi == 0) {
+  if (g.epi == kEpiAccumulate) {
     // split K (the sample dimension of the weight gradients) over about two
     // CTAs per SM, at least two slabs each; partial sums meet in C by atomics
     const int want = std::max(1, 2 * h->sms / tiles);
@@ -1046,10 +1049,10 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
                         (bmn ? nat_bytes(Np) : 0);
   // M (the sample dimension of the layer GEMMs) on grid.x, whose limit is 2^31 - 1
   const dim3 grid(tiles, splits);
-  if (g.epi == 0 && amn && bmn)
-    gemm_tc_kernel<0, true, true><<<grid, kGemmThreads, smem, st>>>(g);
-  else if (g.epi == 2 && !amn && bmn)
-    gemm_tc_kernel<2, false, true><<<grid, kGemmThreads, smem, st>>>(g);
+  if (g.epi == kEpiAccumulate && amn && bmn)
+    gemm_tc_kernel<kEpiAccumulate, true, true><<<grid, kGemmThreads, smem, st>>>(g);
+  else if (g.epi == kEpiSiluGrad && !amn && bmn)
+    gemm_tc_kernel<kEpiSiluGrad, false, true><<<grid, kGemmThreads, smem, st>>>(g);
   else
     return cudaErrorInvalidValue;   // a form the training step does not use
   ++h->launches;
@@ -1107,7 +1110,7 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n) {
   GemmArgs g = ga();
   g.M = kOut; g.N = kHid; g.K = (int)n;
   g.A = h->dY; g.lda = kOut; g.transA = 1; g.B = h->H2; g.ldb = kHid;
-  g.C = h->g + kOffW3; g.ldc = kHid; g.epi = 0;
+  g.C = h->g + kOffW3; g.ldc = kHid; g.epi = kEpiAccumulate;
   if ((e = gemm(h, g, h->aux)) != cudaSuccess) return e;
   // gW2 = dZ2^T H1
   g = ga();
@@ -1119,7 +1122,7 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n) {
   g = ga();
   g.M = (int)n; g.N = kHid; g.K = kHid;
   g.A = h->dZ2; g.lda = kHid; g.B = h->w2; g.ldb = kHid;
-  g.epi = 2; g.Zin = h->Z1; g.ldz = kHid; g.H = h->dZ1; g.ldh = kHid; g.colsum = h->g + kOffB1;
+  g.epi = kEpiSiluGrad; g.Zin = h->Z1; g.ldz = kHid; g.H = h->dZ1; g.ldh = kHid; g.colsum = h->g + kOffB1;
   if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
   // gW1 = dZ1^T X
   g = ga();
@@ -1173,10 +1176,10 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tc_kernel<0, true, true>,
+      e = cudaFuncSetAttribute(gemm_tc_kernel<kEpiAccumulate, true, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmemMax);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tc_kernel<2, false, true>,
+      e = cudaFuncSetAttribute(gemm_tc_kernel<kEpiSiluGrad, false, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmemMax);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
