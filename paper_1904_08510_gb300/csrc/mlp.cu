@@ -757,9 +757,9 @@ struct GuessArgs {
 
 // TMEM lane -> bias + SiLU -> BF16 row of the next layer's A operand
 __device__ __forceinline__ void tc_epilogue(uint32_t taddr, const float* bias, unsigned char* A,
-                                            int row) {
+                                            int row, int ch_begin) {
 #pragma unroll 1
-  for (int ch = 0; ch < 4; ++ch) {
+  for (int ch = ch_begin; ch < ch_begin + 2; ++ch) {
     float v[32];
     tc::ld32(taddr + ch * 32, v);
 #pragma unroll
@@ -775,7 +775,7 @@ __device__ __forceinline__ void tc_epilogue(uint32_t taddr, const float* bias, u
   }
 }
 
-__global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
+__global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArgs g) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* sW1 = tc_smem;
   unsigned char* sW2 = sW1 + tc::kW1Bytes;
@@ -783,21 +783,21 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
   float* sb = reinterpret_cast<float*>(sW3 + tc::kW3Bytes + 2 * tc::kABytes);   // b1, b2, b3
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ double red_s[2][4];
+  __shared__ double red_s[2][8];
   __shared__ int col_s[2];
   const FeatArgs& a = g.f;
   const int tid = threadIdx.x;
   // weights in the core-matrix layout; W3 padded with zero rows to N = 16
-  for (int e = tid; e < kHid * kIn; e += 256)
+  for (int e = tid; e < kHid * kIn; e += tc::kGuessThreads)
     *reinterpret_cast<__nv_bfloat16*>(sW1 + tc::cm_off(e / kIn, e % kIn, kIn / 8)) = g.w1[e];
-  for (int e = tid; e < kHid * kHid; e += 256)
+  for (int e = tid; e < kHid * kHid; e += tc::kGuessThreads)
     *reinterpret_cast<__nv_bfloat16*>(sW2 + tc::cm_off(e / kHid, e % kHid, kHid / 8)) = g.w2[e];
-  for (int e = tid; e < 16 * kHid; e += 256) {
+  for (int e = tid; e < 16 * kHid; e += tc::kGuessThreads) {
     const int n = e / kHid;
     *reinterpret_cast<__nv_bfloat16*>(sW3 + tc::cm_off(n, e % kHid, kHid / 8)) =
         n < kOut ? g.w3[e] : __float2bfloat16(0.0f);
   }
-  for (int e = tid; e < kHid; e += 256) {
+  for (int e = tid; e < kHid; e += tc::kGuessThreads) {
     sb[e] = g.p[kOffB1 + e];
     sb[kHid + e] = g.p[kOffB2 + e];
   }
@@ -816,15 +816,18 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  // ---- this warpgroup's worker ----
-  const int wg = tid >> 7, t = tid & 127, lane = t & 31, lw = t >> 5;
+  // ---- this worker (two warpgroups): warp lw of the worker reads TMEM lane
+  // quadrant lw % 4 (rows 32 (lw % 4) + lane of the tile) in column half lw / 4
+  const int wg = tid / tc::kWorkerThreads, t = tid % tc::kWorkerThreads, lane = t & 31, lw = t >> 5;
+  const int quad = lw & 3, half = lw >> 2, r = quad * 32 + lane;   // r: this thread's tile row
+  constexpr int W = tc::kWorkerThreads;
   const int barid = 1 + wg;                       // named barrier of the worker (0 is the CTA's)
   unsigned char* sA = sW3 + tc::kW3Bytes + wg * tc::kABytes;
   double* red = red_s[wg];
   const uint32_t s_mbar = tc::saddr(&mbar[wg]);
   const uint32_t tm = tmem_base;
   const uint32_t dcol = tm + 128u * (uint32_t)wg;                     // accumulator columns
-  const uint32_t lane_addr = dcol + ((uint32_t)(lw * 32) << 16);     // TMEM lane of row t
+  const uint32_t lane_addr = dcol + ((uint32_t)(quad * 32) << 16);   // TMEM lane of row r
   const uint32_t aA = tc::saddr(sA), aW1 = tc::saddr(sW1), aW2 = tc::saddr(sW2),
                  aW3 = tc::saddr(sW3);
   constexpr uint32_t kId1 = tc::idesc_bf16(128, 128), kId3 = tc::idesc_bf16(128, 16);
@@ -836,7 +839,7 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
   auto run_layer = [&](int layer) -> bool {
     tc::fence_async_smem();
     tc::fence_before();
-    tc::bar(barid, 128);
+    tc::bar(barid, W);
     if (t == 0) {
       tc::fence_after();
       if (layer == 1) {
@@ -856,14 +859,14 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
     }
     const bool ok = tc::wait_phase(s_mbar, phase);
     phase ^= 1u;
-    const bool bad = tc::bar_or(barid, 128, !ok);
+    const bool bad = tc::bar_or(barid, W, !ok);
     tc::fence_after();
     return !bad;
   };
   for (;;) {
-    tc::bar(barid, 128);
+    tc::bar(barid, W);
     if (t == 0) col_s[wg] = atomicAdd(g.queue, 1);
-    tc::bar(barid, 128);
+    tc::bar(barid, W);
     const int64_t c = col_s[wg];
     if (c >= a.ncol || failed) break;
     const int64_t off = a.col_off[c];
@@ -874,7 +877,7 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
       return q;
     };
     double mn = 0.0, mq = 0.0, mp = 0.0;
-    for (int i = t; i < N; i += 128) {
+    for (int i = t; i < N; i += W) {
       mn = fmax(mn, fabs(a.ne[off + i]));
       mq = fmax(mq, fabs(fphi(i)));
       mp = fmax(mp, fabs(a.phi[off + i]));
@@ -884,9 +887,10 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
       double v = mx[k];
       for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
       if (lane == 0) red[lw] = v;
-      tc::bar(barid, 128);
-      mx[k] = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
-      tc::bar(barid, 128);
+      tc::bar(barid, W);
+      mx[k] = fmax(fmax(fmax(red[0], red[1]), fmax(red[2], red[3])),
+                   fmax(fmax(red[4], red[5]), fmax(red[6], red[7])));
+      tc::bar(barid, W);
     }
     const double sn = fmax(fmax(mx[0], mx[1]), 1.0);
     const double sp = fmax(fmax(mx[2], fmax(fabs(a.v_left[c]), fabs(a.v_right[c]))), 1.0);
@@ -899,7 +903,7 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
     };
     // the five per-cell values of the features, staged once in FP32
     float* st = g.stage + off * 5;
-    for (int i = t; i < N; i += 128) {
+    for (int i = t; i < N; i += W) {
       const int kp = (i + 1 < N) ? i + 1 : N - 1;
       const int km = (i >= 1) ? i - 1 : 0;
       st[i * 5 + 0] = (float)(a.ne[off + i] * isn);
@@ -908,13 +912,14 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
       st[i * 5 + 3] = (float)(a.T[off + i] * (1.0 / 2000.0));
       st[i * 5 + 4] = (float)(-(a.phi[off + kp] - a.phi[off + km]) * 0.5 * isp);
     }
-    tc::bar(barid, 128);
+    tc::bar(barid, W);
     for (int r0 = 0; r0 < N; r0 += tc::kTile) {
-      // row t of A: the 25 stencil features of cell i (f = 5 o + q: quantity q
-      // of cell i + o - 2), zero-padded to K = 32
-      const int i = min(r0 + t, N - 1);
+      // row r of A: the 25 stencil features of cell i (f = 5 o + q: quantity q
+      // of cell i + o - 2), zero-padded to K = 32; the worker's two threads of
+      // row r build features 0..15 and 16..31
+      const int i = min(r0 + r, N - 1);
 #pragma unroll
-      for (int ch = 0; ch < kIn / 8; ++ch) {
+      for (int ch = 2 * half; ch < 2 * half + 2; ++ch) {
         float f8[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -926,21 +931,21 @@ __global__ void __launch_bounds__(256) guess_tc_kernel(GuessArgs g) {
         w.y = pack_bf16(f8[2], f8[3]);
         w.z = pack_bf16(f8[4], f8[5]);
         w.w = pack_bf16(f8[6], f8[7]);
-        *reinterpret_cast<uint4*>(sA + tc::cm_off(t, ch * 8, kIn / 8)) = w;
+        *reinterpret_cast<uint4*>(sA + tc::cm_off(r, ch * 8, kIn / 8)) = w;
       }
       bool ok = run_layer(1);
       if (ok) {
-        tc_epilogue(lane_addr, sb, sA, t);
+        tc_epilogue(lane_addr, sb, sA, r, 2 * half);
         ok = run_layer(2);
       }
       if (ok) {
-        tc_epilogue(lane_addr, sb + kHid, sA, t);
+        tc_epilogue(lane_addr, sb + kHid, sA, r, 2 * half);
         ok = run_layer(3);
       }
       float y[2] = {NAN, NAN};
-      if (ok) tc::ld2(lane_addr, y);
-      const int row = r0 + t;
-      if (row < N) {
+      if (ok && half == 0) tc::ld2(lane_addr, y);
+      const int row = r0 + r;
+      if (half == 0 && row < N) {
         const int64_t gi = off + row;
         const float yn = y[0] + sb[2 * kHid], yp = y[1] + sb[2 * kHid + 1];
         a.ne_g[gi] = a.ne[gi] + ((a.comps & 1) ? sn * (double)yn : (ok ? 0.0 : (double)NAN));
@@ -1388,7 +1393,7 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
   e = cudaFuncSetAttribute(guess_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc::kSmemBytes);
   if (e != cudaSuccess) return cuda_fail(e);
-  guess_tc_kernel<<<grid, 256, tc::kSmemBytes, h->st>>>(g);
+  guess_tc_kernel<<<grid, tc::kGuessThreads, tc::kSmemBytes, h->st>>>(g);
   ++h->launches;
   e = cudaGetLastError();
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);

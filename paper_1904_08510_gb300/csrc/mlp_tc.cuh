@@ -2,18 +2,19 @@
 // features -> 32x128 -> SiLU -> 128x128 -> SiLU -> 128x2 per cell, BF16
 // operands in shared memory, FP32 accumulators in tensor memory (TMEM).
 //
-// A CTA of 256 threads holds the weights once in shared memory and runs two
-// independent workers, one per 128-thread warpgroup: each takes columns from
-// a persistent queue and walks its column in tiles of 128 cells, with its own
-// A-operand buffer, its own 128 TMEM accumulator columns, its own mbarrier and
-// a named barrier of its 128 threads. Thread t of a worker builds row t of
-// the A operand, the worker's first thread issues the MMAs (M = 128, K = 16
-// each) and commits them to the worker's mbarrier, and after each layer thread
-// t reads TMEM lane t (= row t; warp w of the CTA reaches lanes 32 (w mod 4)..)
-// back with tcgen05.ld for the bias + SiLU epilogue, which writes the next
-// layer's A operand into the worker's buffer (the MMA that read it has
-// completed). Two workers per CTA and two CTAs per SM keep 16 warps and four
-// independent MMA chains resident per SM.
+// A CTA of 512 threads holds the weights once in shared memory and runs two
+// independent workers of 256 threads (two warpgroups) each: a worker takes
+// columns from a persistent queue and walks its column in tiles of 128 cells,
+// with its own A-operand buffer, its own 128 TMEM accumulator columns, its own
+// mbarrier and a named barrier of its 256 threads. Row r of a tile belongs to
+// two threads of the worker (warps w and w + 4 reach the same TMEM lane
+// quadrant w mod 4): each builds half of row r's features in the A operand,
+// the worker's first thread issues the MMAs (M = 128, K = 16 each) and
+// commits them to the worker's mbarrier, and after each layer each of the two
+// reads its half of TMEM lane r back with tcgen05.ld for the bias + SiLU
+// epilogue, which writes the next layer's A operand into the worker's buffer
+// (the MMA that read it has completed). Two CTAs per SM keep 32 warps and
+// four independent MMA chains resident per SM and fill its 512 TMEM columns.
 //
 // Shared-memory operand layout: K-major, no swizzle, in 8 x 16-byte core
 // matrices (8 rows x 8 BF16 of K): element (r, k) of a matrix with K/8 = kc
@@ -28,7 +29,9 @@
 
 namespace tc {
 
-constexpr int kTile = 128;              // rows per tile = threads = TMEM lanes
+constexpr int kTile = 128;              // rows per tile = TMEM lanes
+constexpr int kWorkerThreads = 256;     // two threads per row: two warps per TMEM lane quadrant
+constexpr int kGuessThreads = 2 * kWorkerThreads;
 constexpr uint32_t kTmemCols = 256;     // two workers: 128 accumulator columns each
 constexpr uint32_t kW1Bytes = 128 * 32 * 2, kW2Bytes = 128 * 128 * 2, kW3Bytes = 16 * 128 * 2,
                    kABytes = 128 * 128 * 2;
