@@ -11,6 +11,8 @@
 // Shapes: 32 (25 features, zero-padded) -> 128 -> 128 -> 2, SiLU activations.
 // Parameters (FP32 master copy, flat): W1[128][32], b1[128], W2[128][128],
 // b2[128], W3[2][128], b3[2]; BF16 copies of W1, W2, W3 feed the tensor cores.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -196,6 +198,7 @@ struct TcGemm {
   int64_t ldz;
   float* colsum;
   int* err;
+  int tmaA, tmaB;   // the operand's slabs come by TMA (tensor maps of the launch)
 };
 
 constexpr int kEpiAccumulate = 0, kEpiSiluGrad = 2;         // GemmArgs::epi
@@ -204,7 +207,7 @@ constexpr int kSlabK = 64;                                  // k per slab
 constexpr uint32_t kOpBytes = 128 * kSlabK * 2;             // one operand slab
 __host__ __device__ constexpr uint32_t nat_pitch(int R) { return (uint32_t)(2 * R + 16); }
 __host__ __device__ constexpr uint32_t nat_bytes(int R) { return kSlabK * nat_pitch(R); }
-constexpr uint32_t kGemmSmemMax = 4 * kOpBytes + 2 * nat_bytes(128);
+constexpr uint32_t kGemmSmemMax = 4 * kOpBytes + 2 * nat_bytes(128) + 1024;   // + alignment slack
 constexpr int kZPitch = 36, kHPitch = 80;                   // epilogue staging pitches
 constexpr uint32_t kStageBytes = 32 * kZPitch * 4 + 32 * kHPitch;
 static_assert(kGemmThreads / 32 * kStageBytes <= 4 * kOpBytes, "staging tiles fit the operand buffers");
@@ -276,6 +279,42 @@ __device__ __forceinline__ void stage_nat(unsigned char* nat, uint32_t pitch, co
   }
 }
 
+// TMA: a 64 x 64 BF16 box (64 k rows of 128 bytes) of a row-major operand
+// with 128-byte swizzle: the 16-byte chunk j of row k lands at chunk j ^ (k % 8)
+// of the row (the box's base is 1024-byte aligned). Completion on mbarrier mb.
+constexpr uint32_t kTmaBoxBytes = 64 * 128;
+__device__ __forceinline__ void tma_box(unsigned char* dst, const CUtensorMap* map, int x, int y,
+                                        uint32_t mb) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(tc::saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb)
+      : "memory");
+}
+
+// two swizzled boxes (r 0..63 and 64..127 of 64 k rows) -> K-major core matrices,
+// as nat_to_k: core matrix i = c kc + kk holds rows 8c.. of k 8kk..
+__device__ __forceinline__ void nat_sw_to_k(unsigned char* S, const unsigned char* nat, int kc,
+                                            int warp, int lane) {
+  const int mats = 16 * kc;
+  for (int g = warp; g * 4 < mats; g += kGemmThreads / 32) {
+    const int i = g * 4 + (lane >> 3);
+    const int c = i / kc, kk = i - c * kc;
+    const int k = kk * 8 + (lane & 7);
+    const uint32_t src =
+        tc::saddr(nat + (c >> 3) * kTmaBoxBytes + k * 128 + (((c & 7) ^ (k & 7)) << 4));
+    uint32_t r0, r1, r2, r3;
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(src));
+    uint32_t* d = reinterpret_cast<uint32_t*>(S + (size_t)g * 4 * 128) + lane;
+    d[0] = r0;
+    d[32] = r1;
+    d[64] = r2;
+    d[96] = r3;
+  }
+}
+
 // nat (k rows, r contiguous) -> K-major core matrices. Core matrix i = c kc + kk
 // holds rows 8c.. of k 8kk..; ldmatrix.trans hands lane l the pair
 // (k = 8kk + 2 (l%4) + {0,1}, r = 8c + l/4), which sits at byte 4 l of it.
@@ -316,9 +355,14 @@ __device__ __forceinline__ float warp_colsum32(float* v, int lane) {
 // EPI: the epilogue; AMN / BMN: operand A / B has contiguous rows
 // (staged through the row-major copy and ldmatrix.trans) rather than contiguous k
 template <int EPI, bool AMN, bool BMN>
-__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
-  extern __shared__ __align__(1024) unsigned char gsm[];
+__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
+                                                               const __grid_constant__ CUtensorMap tmA,
+                                                               const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ __align__(1024) unsigned char gsm_raw[];
+  // 1024-byte aligned base (the swizzled TMA boxes need it; the launch adds 1 KB)
+  unsigned char* gsm = gsm_raw + ((1024u - (tc::saddr(gsm_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t lbar;   // TMA slabs
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
@@ -332,7 +376,9 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   unsigned char* opA = gsm;
   unsigned char* opB = gsm + NB * kOpBytes;
   unsigned char* natA = gsm + 2 * NB * kOpBytes;
-  unsigned char* natB = natA + (amn ? nat_bytes(128) : 0);
+  unsigned char* natB = natA + (amn ? nat_bytes(128) : 0);   // 1024-aligned: 17408 = 17 KB
+  const bool tmaA = amn && g.tmaA, tmaB = bmn && g.tmaB;
+  const uint32_t l_bar = tc::saddr(&lbar);
   const bool vecA = ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0) && (((amn ? g.sak : g.sam) & 7) == 0);
   const bool vecB = ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0) && (((bmn ? g.sbk : g.sbn) & 7) == 0);
   if (warp == 0) {
@@ -343,6 +389,8 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[1])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(l_bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_async_smem();
   tc::fence_before();
@@ -360,10 +408,24 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   auto issue = [&](int s) {
     const int b = NB == 2 ? (s & 1) : 0, k0 = kbeg + s * kSlabK;
     const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
+    if ((tmaA || tmaB) && tid == 0) {
+      // two 64-row boxes per TMA operand (rows past the matrix arrive as zeros)
+      const uint32_t bytes = (tmaA ? 2 : 0) * kTmaBoxBytes + (tmaB ? 2 : 0) * kTmaBoxBytes;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(l_bar), "r"(bytes)
+                   : "memory");
+      if (tmaA) {
+        tma_box(natA, &tmA, (int)m0, k0, l_bar);
+        tma_box(natA + kTmaBoxBytes, &tmA, (int)m0 + 64, k0, l_bar);
+      }
+      if (tmaB) {
+        tma_box(natB, &tmB, 0, k0, l_bar);
+        tma_box(natB + kTmaBoxBytes, &tmB, 64, k0, l_bar);
+      }
+    }
     if (!amn) stage_k(opA + b * kOpBytes, g.A, g.sam, vecA, m0, g.M, 128, k0, kend, kc, tid);
-    else stage_nat(natA, nat_pitch(128), g.A, g.sak, vecA, m0, g.M, 128, k0, kend, ks, tid);
+    else if (!tmaA) stage_nat(natA, nat_pitch(128), g.A, g.sak, vecA, m0, g.M, 128, k0, kend, ks, tid);
     if (!bmn) stage_k(opB + b * kOpBytes, g.B, g.sbn, vecB, 0, g.N, Np, k0, kend, kc, tid);
-    else stage_nat(natB, nat_pitch(Np), g.B, g.sbk, vecB, 0, g.N, Np, k0, kend, ks, tid);
+    else if (!tmaB) stage_nat(natB, nat_pitch(Np), g.B, g.sbk, vecB, 0, g.N, Np, k0, kend, ks, tid);
     cp_commit();
   };
   for (int j = 0; j < min(L, nslab); ++j) issue(j);
@@ -377,6 +439,13 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
     unsigned char* sA = opA + b * kOpBytes;
     unsigned char* sB = opB + b * kOpBytes;
     if (amn || bmn) {
+      if (tmaA || tmaB) {   // slab s's boxes (one slab in flight: parity s & 1)
+        const bool w = tc::wait_phase(l_bar, (uint32_t)(s & 1));
+        if (__syncthreads_or(!w)) {
+          ok = false;
+          break;
+        }
+      }
       __syncthreads();
       if (NB == 1 && s >= 1) {   // the single buffers: slab s - 1's MMAs have read them
         const bool w = tc::wait_phase(bar_of(s - 1), par_of(s - 1));
@@ -385,8 +454,10 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
           break;
         }
       }
-      if (amn) nat_to_k(sA, natA, nat_pitch(128), 128, kc, warp, lane);
-      if (bmn) nat_to_k(sB, natB, nat_pitch(Np), Np, kc, warp, lane);
+      if (tmaA) nat_sw_to_k(sA, natA, kc, warp, lane);
+      else if (amn) nat_to_k(sA, natA, nat_pitch(128), 128, kc, warp, lane);
+      if (tmaB) nat_sw_to_k(sB, natB, kc, warp, lane);
+      else if (bmn) nat_to_k(sB, natB, nat_pitch(Np), Np, kc, warp, lane);
     }
     tc::fence_async_smem();
     tc::fence_before();
@@ -510,6 +581,8 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g) {
   if (!ok) {
     cp_wait<0>();
     if (tid == 0) atomicExch(g.err, 1);
+    // boxes of an issued slab may still be landing: a bounded wait
+    if ((tmaA || tmaB) && last + 1 < nslab) tc::wait_phase(l_bar, (uint32_t)((last + 1) & 1));
     // an MMA may still be in flight: one more bounded wait before TMEM is freed
     if (last >= 0) tc::wait_phase(bar_of(last), par_of(last));
   }
@@ -1019,6 +1092,28 @@ namespace {
 
 int cuda_fail(cudaError_t e) { return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e)); }
 
+// tensor map of a row-major BF16 operand (inner: values per k row, outer: k),
+// read in 64 x 64 boxes with 128-byte swizzle; false if it cannot be encoded
+// (the kernel then stages the operand with cp.async)
+bool tma_map(CUtensorMap* m, const uint16_t* base, int64_t inner, int64_t outer, int64_t row_bytes) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15) || outer < 1) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  const cuuint32_t box[2] = {64, 64}, estr[2] = {1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   if (a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaSuccess;
   TcGemm g;
@@ -1051,13 +1146,19 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   }
   const bool amn = g.sak != 1, bmn = g.sbk != 1;
   const uint32_t smem = ((amn && bmn) ? 2 : 4) * kOpBytes + (amn ? nat_bytes(128) : 0) +
-                        (bmn ? nat_bytes(Np) : 0);
+                        (bmn ? nat_bytes(Np) : 0) + 1024;
+  // row-major operands of 128 values per k row go by TMA (two swizzled 64 x 64 boxes per slab)
+  CUtensorMap mapA, mapB;
+  memset(&mapA, 0, sizeof(mapA));
+  memset(&mapB, 0, sizeof(mapB));
+  g.tmaA = amn && g.M == 128 && tma_map(&mapA, g.A, 128, g.K, g.sak * 2);
+  g.tmaB = bmn && g.N == 128 && tma_map(&mapB, g.B, 128, g.K, g.sbk * 2);
   // M (the sample dimension of the layer GEMMs) on grid.x, whose limit is 2^31 - 1
   const dim3 grid(tiles, splits);
   if (g.epi == kEpiAccumulate && amn && bmn)
-    gemm_tc_kernel<kEpiAccumulate, true, true><<<grid, kGemmThreads, smem, st>>>(g);
+    gemm_tc_kernel<kEpiAccumulate, true, true><<<grid, kGemmThreads, smem, st>>>(g, mapA, mapB);
   else if (g.epi == kEpiSiluGrad && !amn && bmn)
-    gemm_tc_kernel<kEpiSiluGrad, false, true><<<grid, kGemmThreads, smem, st>>>(g);
+    gemm_tc_kernel<kEpiSiluGrad, false, true><<<grid, kGemmThreads, smem, st>>>(g, mapA, mapB);
   else
     return cudaErrorInvalidValue;   // a form the training step does not use
   ++h->launches;
