@@ -207,7 +207,7 @@ constexpr int kSlabK = 64;                                  // k per slab
 constexpr uint32_t kOpBytes = 128 * kSlabK * 2;             // one operand slab
 __host__ __device__ constexpr uint32_t nat_pitch(int R) { return (uint32_t)(2 * R + 16); }
 __host__ __device__ constexpr uint32_t nat_bytes(int R) { return kSlabK * nat_pitch(R); }
-constexpr uint32_t kGemmSmemMax = 4 * kOpBytes + 2 * nat_bytes(128) + 1024;   // + alignment slack
+constexpr uint32_t kGemmSmemMax = 4 * kOpBytes + 4 * nat_bytes(128) + 1024;   // + alignment slack
 constexpr int kZPitch = 36, kHPitch = 80;                   // epilogue staging pitches
 constexpr uint32_t kStageBytes = 32 * kZPitch * 4 + 32 * kHPitch;
 static_assert(kGemmThreads / 32 * kStageBytes <= 4 * kOpBytes, "staging tiles fit the operand buffers");
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
   // 1024-byte aligned base (the swizzled TMA boxes need it; the launch adds 1 KB)
   unsigned char* gsm = gsm_raw + ((1024u - (tc::saddr(gsm_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ __align__(8) uint64_t lbar;   // TMA slabs
+  __shared__ __align__(8) uint64_t lbar[2];   // TMA slabs, one per row-major slot
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
@@ -375,10 +375,14 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
   constexpr int NB = (AMN && BMN) ? 1 : 2;
   unsigned char* opA = gsm;
   unsigned char* opB = gsm + NB * kOpBytes;
-  unsigned char* natA = gsm + 2 * NB * kOpBytes;
-  unsigned char* natB = natA + (amn ? nat_bytes(128) : 0);   // 1024-aligned: 17408 = 17 KB
+  // two slots of row-major copies per such operand, so that two slabs are in
+  // flight; every slot starts on a 1024-byte boundary (17408 = 17 KB)
+  constexpr uint32_t natA_sz = amn ? nat_bytes(128) : 0;
+  const uint32_t natB_sz = bmn ? nat_bytes(Np) : 0;
+  unsigned char* natA0 = gsm + 2 * NB * kOpBytes;
+  unsigned char* natB0 = natA0 + 2 * natA_sz;
   const bool tmaA = amn && g.tmaA, tmaB = bmn && g.tmaB;
-  const uint32_t l_bar = tc::saddr(&lbar);
+  auto l_bar = [&](int s) { return tc::saddr(&lbar[s & 1]); };
   const bool vecA = ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0) && (((amn ? g.sak : g.sam) & 7) == 0);
   const bool vecB = ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0) && (((bmn ? g.sbk : g.sbn) & 7) == 0);
   if (warp == 0) {
@@ -389,7 +393,8 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[1])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(l_bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&lbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&lbar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_async_smem();
@@ -399,27 +404,28 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
   const uint32_t tm = tmem_base;
   const uint32_t idesc = tc::idesc_bf16(128, Np);
   const int nslab = (kend - kbeg + kSlabK - 1) / kSlabK;   // >= 1 (the host keeps kbeg < K)
-  // slabs in flight: two when both operands go straight to their buffers,
-  // one when a row-major copy (a single buffer per operand) is transposed
-  constexpr int L = (amn || bmn) ? 1 : 2;
+  constexpr int L = 2;   // slabs in flight
   // the mbarrier that slab s's MMAs complete, and the parity of that completion
   auto bar_of = [&](int s) { return tc::saddr(&mbar[NB == 2 ? (s & 1) : 0]); };
   auto par_of = [&](int s) { return (uint32_t)(NB == 2 ? ((s >> 1) & 1) : (s & 1)); };
   auto issue = [&](int s) {
     const int b = NB == 2 ? (s & 1) : 0, k0 = kbeg + s * kSlabK;
     const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
+    unsigned char* natA = natA0 + (s & 1) * natA_sz;
+    unsigned char* natB = natB0 + (s & 1) * natB_sz;
     if ((tmaA || tmaB) && tid == 0) {
       // two 64-row boxes per TMA operand (rows past the matrix arrive as zeros)
       const uint32_t bytes = (tmaA ? 2 : 0) * kTmaBoxBytes + (tmaB ? 2 : 0) * kTmaBoxBytes;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(l_bar), "r"(bytes)
+      const uint32_t lb = l_bar(s);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lb), "r"(bytes)
                    : "memory");
       if (tmaA) {
-        tma_box(natA, &tmA, (int)m0, k0, l_bar);
-        tma_box(natA + kTmaBoxBytes, &tmA, (int)m0 + 64, k0, l_bar);
+        tma_box(natA, &tmA, (int)m0, k0, lb);
+        tma_box(natA + kTmaBoxBytes, &tmA, (int)m0 + 64, k0, lb);
       }
       if (tmaB) {
-        tma_box(natB, &tmB, 0, k0, l_bar);
-        tma_box(natB + kTmaBoxBytes, &tmB, 64, k0, l_bar);
+        tma_box(natB, &tmB, 0, k0, lb);
+        tma_box(natB + kTmaBoxBytes, &tmB, 64, k0, lb);
       }
     }
     if (!amn) stage_k(opA + b * kOpBytes, g.A, g.sam, vecA, m0, g.M, 128, k0, kend, kc, tid);
@@ -438,9 +444,11 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
     else cp_wait<0>();
     unsigned char* sA = opA + b * kOpBytes;
     unsigned char* sB = opB + b * kOpBytes;
+    unsigned char* natA = natA0 + (s & 1) * natA_sz;
+    unsigned char* natB = natB0 + (s & 1) * natB_sz;
     if (amn || bmn) {
-      if (tmaA || tmaB) {   // slab s's boxes (one slab in flight: parity s & 1)
-        const bool w = tc::wait_phase(l_bar, (uint32_t)(s & 1));
+      if (tmaA || tmaB) {   // slab s's boxes: completion (s >> 1) of its slot's mbarrier
+        const bool w = tc::wait_phase(l_bar(s), (uint32_t)((s >> 1) & 1));
         if (__syncthreads_or(!w)) {
           ok = false;
           break;
@@ -581,8 +589,10 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
   if (!ok) {
     cp_wait<0>();
     if (tid == 0) atomicExch(g.err, 1);
-    // boxes of an issued slab may still be landing: a bounded wait
-    if ((tmaA || tmaB) && last + 1 < nslab) tc::wait_phase(l_bar, (uint32_t)((last + 1) & 1));
+    // boxes of issued slabs may still be landing: bounded waits
+    if (tmaA || tmaB)
+      for (int q = last + 1; q < min(nslab, last + 1 + L); ++q)
+        tc::wait_phase(l_bar(q), (uint32_t)((q >> 1) & 1));
     // an MMA may still be in flight: one more bounded wait before TMEM is freed
     if (last >= 0) tc::wait_phase(bar_of(last), par_of(last));
   }
@@ -1145,8 +1155,8 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
     splits = (g.K + g.kchunk - 1) / g.kchunk;
   }
   const bool amn = g.sak != 1, bmn = g.sbk != 1;
-  const uint32_t smem = ((amn && bmn) ? 2 : 4) * kOpBytes + (amn ? nat_bytes(128) : 0) +
-                        (bmn ? nat_bytes(Np) : 0) + 1024;
+  const uint32_t smem = ((amn && bmn) ? 2 : 4) * kOpBytes + 2 * (amn ? nat_bytes(128) : 0) +
+                        2 * (bmn ? nat_bytes(Np) : 0) + 1024;
   // row-major operands of 128 values per k row go by TMA (two swizzled 64 x 64 boxes per slab)
   CUtensorMap mapA, mapB;
   memset(&mapA, 0, sizeof(mapA));
