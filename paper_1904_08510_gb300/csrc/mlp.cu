@@ -154,16 +154,18 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 //
 // A CTA of 256 threads computes 128 rows of C (row m0 + r in TMEM lane r) by
 // all N <= 128 columns (the MMA's N is N rounded up to 16) over its share of
-// K, in slabs of up to 64 k, so that the threads stage slab s + 1 while the
-// tensor core multiplies slab s (two shared-memory buffers per operand, or
-// one when both operands go through the row-major copies, which then carry
-// the next slab). Each operand is
-// staged in the K-major core-matrix layout of mlp_tc.cuh, zero outside the
-// matrix: a K-contiguous operand by 16-byte asynchronous copies (cp.async)
-// that land in core-matrix order, an operand whose rows are contiguous by the
-// same copies into a row-major buffer that ldmatrix.trans then transposes (two
-// consecutive k of one row per register). The epilogue runs on all 8 warps:
-// two per 32-lane quadrant of TMEM, each on half of the columns.
+// K, in slabs of up to 64 k, two of them in flight while the tensor core
+// multiplies the current one. Each operand is staged in the K-major
+// core-matrix layout of mlp_tc.cuh, zero outside the matrix: a K-contiguous
+// operand by 16-byte asynchronous copies (cp.async) that land in core-matrix
+// order (two buffers); an operand whose rows are contiguous into one of two
+// row-major slots, which ldmatrix.trans then transposes into the operand
+// buffer (one, or two when the other operand is K-contiguous) after the
+// previous slab's MMAs have read it. The row-major slots of operands with 128
+// values per row are filled by TMA (two 64 x 64 boxes with 128-byte swizzle,
+// completing on a per-slot mbarrier), narrower ones by cp.async. The
+// epilogue runs on all 8 warps: two per 32-lane quadrant of TMEM, each on
+// half of the columns.
 // Every wait on an mbarrier is bounded; a CTA whose MMAs do not complete sets
 // the error word and writes NaN instead of its results.
 // --------------------------------------------------------------------------
