@@ -37,22 +37,24 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
               kNParam = kOffB3 + kOut;
 static_assert(kNParam == SDCEF_MLP_NPARAM, "parameter count");
 
-// SiLU and its derivative with the hardware exponential and fast division (the
-// result feeds BF16 activations, whose rounding is far coarser).
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
-// Inference form: silu(z) = z/2 (1 + tanh(z/2)) with the hardware tanh
-// approximation (one special-function operation instead of an exponential and
-// a reciprocal; its ~2^-11 relative error is below the BF16 rounding of the
-// activation that follows).
+// SiLU and its derivative through the hardware tanh approximation:
+// silu(z) = z/2 (1 + tanh(z/2)), silu'(z) = s (1 + z (1 - s)) with the sigmoid
+// s = (1 + tanh(z/2)) / 2 -- one special-function operation each instead of an
+// exponential and a reciprocal. The ~2^-11 relative error of tanh.approx is
+// below the BF16 rounding of the activation or gradient that follows, and
+// training and inference evaluate the same activation.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x));
+  return t;
+}
 __device__ __forceinline__ float silu_fast(float z) {
   const float h = 0.5f * z;
-  float t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
-  return fmaf(h, t, h);
+  return fmaf(h, tanh_fast(h), h);
 }
 __device__ __forceinline__ float silu_grad(float z) {
-  float s = __fdividef(1.0f, 1.0f + __expf(-z));
-  return s * (1.0f + z * (1.0f - s));
+  const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+  return s * fmaf(z, 1.0f - s, 1.0f);
 }
 
 // --------------------------------------------------------------------------
@@ -725,10 +727,10 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const uint4 hq = make_uint4(pack_bf16(silu(v[8 * q]), silu(v[8 * q + 1])),
-                                    pack_bf16(silu(v[8 * q + 2]), silu(v[8 * q + 3])),
-                                    pack_bf16(silu(v[8 * q + 4]), silu(v[8 * q + 5])),
-                                    pack_bf16(silu(v[8 * q + 6]), silu(v[8 * q + 7])));
+        const uint4 hq = make_uint4(pack_bf16(silu_fast(v[8 * q]), silu_fast(v[8 * q + 1])),
+                                    pack_bf16(silu_fast(v[8 * q + 2]), silu_fast(v[8 * q + 3])),
+                                    pack_bf16(silu_fast(v[8 * q + 4]), silu_fast(v[8 * q + 5])),
+                                    pack_bf16(silu_fast(v[8 * q + 6]), silu_fast(v[8 * q + 7])));
         if (live) *reinterpret_cast<uint4*>(H + row * kHid + c0 + 8 * q) = hq;
         *reinterpret_cast<uint4*>(sH + tc::cm_off(r, c0 + 8 * q, kHid / 8)) = hq;
       }
