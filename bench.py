@@ -600,9 +600,9 @@ def extras(args, S, b, db, solver, params, dev):
 
 # algorithmic bytes per sample of one training step (each operand read once,
 # each result written once): forward + loss + dZ2 reads X 64 and T 8 and writes
-# Z1 512, H1 256, H2 256, dY 4, dZ2 256; gW3 4 + 256, gW2 256 + 256,
-# dZ1 256 + 512 + 256, gW1 256 + 64
-MLP_STEP_BYTES_PER_SAMPLE = 1356 + 260 + 512 + 1024 + 320
+# silu'(Z1) 256 (BF16), H1 256, H2 256, dY 4, dZ2 256; gW3 4 + 256,
+# gW2 256 + 256, dZ1 256 + 256 + 256, gW1 256 + 64
+MLP_STEP_BYTES_PER_SAMPLE = 1100 + 260 + 512 + 768 + 320
 MLP_STEP_FLOPS_PER_SAMPLE = 3 * 2 * (32 * 128 + 128 * 128 + 128 * 2)
 
 

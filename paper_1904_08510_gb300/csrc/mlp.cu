@@ -151,7 +151,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // with A(m,k) = transA ? A[k*lda+m] : A[m*lda+k] and
 // B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n] (BF16), FP32 accumulators in TMEM.
 // Epilogues: kEpiAccumulate adds C with atomics (split-K weight gradients);
-// kEpiSiluGrad writes dZ = acc * silu'(Zin) (BF16) and adds the column sums of
+// kEpiSiluGrad writes dZ = acc * G (BF16; G = silu'(Z) in BF16, stored by the
+// forward) and adds the column sums of
 // dZ to colsum (the forward runs fused, fwd_tc_kernel below).
 //
 // A CTA of 256 threads computes 128 rows of C (row m0 + r in TMEM lane r) by
@@ -182,8 +183,8 @@ struct GemmArgs {
   int epi;
   __nv_bfloat16* H;
   int ldh;
-  const float* Zin;
-  int ldz;
+  const __nv_bfloat16* Gin;
+  int ldgin;
   float* colsum;
 };
 
@@ -198,8 +199,8 @@ struct TcGemm {
   int64_t scm, scn;
   __nv_bfloat16* H;
   int64_t ldh;
-  const float* Zin;
-  int64_t ldz;
+  const __nv_bfloat16* Gin;
+  int64_t ldgin;
   float* colsum;
   int* err;
   int tmaA, tmaB;   // the operand's slabs come by TMA (tensor maps of the launch)
@@ -212,8 +213,8 @@ constexpr uint32_t kOpBytes = 128 * kSlabK * 2;             // one operand slab
 __host__ __device__ constexpr uint32_t nat_pitch(int R) { return (uint32_t)(2 * R + 16); }
 __host__ __device__ constexpr uint32_t nat_bytes(int R) { return kSlabK * nat_pitch(R); }
 constexpr uint32_t kGemmSmemMax = 4 * kOpBytes + 4 * nat_bytes(128) + 1024;   // + alignment slack
-constexpr int kZPitch = 36, kHPitch = 80;                   // epilogue staging pitches
-constexpr uint32_t kStageBytes = 32 * kZPitch * 4 + 32 * kHPitch;
+constexpr int kHPitch = 80;                                 // epilogue staging pitch (BF16 rows)
+constexpr uint32_t kStageBytes = 2 * 32 * kHPitch;
 static_assert(kGemmThreads / 32 * kStageBytes <= 4 * kOpBytes, "staging tiles fit the operand buffers");
 
 __device__ __forceinline__ uint32_t pack_u16(uint16_t lo, uint16_t hi) {
@@ -507,18 +508,17 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
   const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
   const int64_t row = m0 + quad * 32 + lane;
   const bool live = row < g.M;
-  // the operand buffers are free now: each warp gets a staging tile of 32
-  // rows x 32 FP32 (pitch 36 floats) and 32 rows x 32 BF16 (pitch 80 B),
-  // pitches at which a quarter-warp's 16-byte accesses hit distinct banks
+  // the operand buffers are free now: each warp gets two staging tiles of 32
+  // rows x 32 BF16 (pitch 80 B, at which a quarter-warp's 16-byte accesses hit
+  // distinct banks), one for G coming in and one for dZ going out
   const int64_t rbase = m0 + quad * 32;
   const int64_t rows_left = (int64_t)g.M - rbase;
   const int nrows = rows_left <= 0 ? 0 : (rows_left < 32 ? (int)rows_left : 32);
-  float* zt = reinterpret_cast<float*>(gsm + warp * kStageBytes);
-  unsigned char* ht = gsm + warp * kStageBytes + 32 * kZPitch * 4;
+  unsigned char* gt = gsm + warp * kStageBytes;
+  unsigned char* ht = gt + 32 * kHPitch;
   const bool tiled =
-      (g.scm & 3) == 0 && (g.ldh & 7) == 0 && (g.ldz & 3) == 0 &&
-      ((reinterpret_cast<uintptr_t>(g.C) | reinterpret_cast<uintptr_t>(g.H) |
-        reinterpret_cast<uintptr_t>(g.Zin)) & 15) == 0;
+      (g.ldh & 7) == 0 && (g.ldgin & 7) == 0 &&
+      ((reinterpret_cast<uintptr_t>(g.H) | reinterpret_cast<uintptr_t>(g.Gin)) & 15) == 0;
   for (int c0 = half * 64; c0 < min(Np, half * 64 + 64); c0 += 32) {
     float v[32];
     if (ok) {
@@ -543,29 +543,35 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
         }
       }
     } else {
-      float z[32];
+      float z[32];   // the multiplier G of this thread's row
       if (full && tiled) {
-        // Zin rows in with whole-row loads through the staging tile
+        // G rows in with whole-row loads (8 rows x 64 B per instruction) through the staging tile
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int e = i * 32 + lane, r = e >> 3, c4 = e & 7;
-          float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int i = 0; i < 4; ++i) {
+          const int e = i * 32 + lane, r = e >> 2, p = e & 3;
+          uint4 t = make_uint4(0, 0, 0, 0);
           if (r < nrows)
-            t = __ldg(reinterpret_cast<const float4*>(g.Zin + (rbase + r) * g.ldz + c0 + 4 * c4));
-          *reinterpret_cast<float4*>(zt + r * kZPitch + 4 * c4) = t;
+            t = __ldg(reinterpret_cast<const uint4*>(g.Gin + (rbase + r) * g.ldgin + c0 + 8 * p));
+          *reinterpret_cast<uint4*>(gt + r * kHPitch + 16 * p) = t;
         }
         __syncwarp();
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 t = *reinterpret_cast<const float4*>(zt + lane * kZPitch + 4 * q);
-          z[4 * q] = t.x; z[4 * q + 1] = t.y; z[4 * q + 2] = t.z; z[4 * q + 3] = t.w;
+        for (int q = 0; q < 4; ++q) {
+          const uint4 t = *reinterpret_cast<const uint4*>(gt + lane * kHPitch + 16 * q);
+          const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            z[8 * q + 2 * u] = __uint_as_float(w[u] << 16);
+            z[8 * q + 2 * u + 1] = __uint_as_float(w[u] & 0xffff0000u);
+          }
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) z[j] = (live && c0 + j < g.N) ? g.Zin[row * g.ldz + c0 + j] : 0.0f;
+        for (int j = 0; j < 32; ++j)
+          z[j] = (live && c0 + j < g.N) ? __bfloat162float(g.Gin[row * g.ldgin + c0 + j]) : 0.0f;
       }
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = (live && c0 + j < g.N) ? v[j] * silu_grad(z[j]) : 0.0f;
+      for (int j = 0; j < 32; ++j) v[j] = (live && c0 + j < g.N) ? v[j] * z[j] : 0.0f;
       if (full && tiled) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -612,8 +618,9 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
 // core-matrix layout (cp.async), and chains the layers on the tensor core
 // through one 128-column TMEM accumulator. After each hidden layer the 8-warp
 // epilogue (two warps per TMEM lane quadrant, each on half of the columns)
-// adds the bias, writes Z (FP32, optional) and H = silu(Z) (BF16) to global
-// memory, and writes H into shared memory as the A operand of the next layer,
+// adds the bias, writes H = silu(Z) (BF16) to global memory (and in training
+// silu'(Z1) in BF16, the factor of the layer-1 backward product, instead of
+// Z1), and writes H into shared memory as the A operand of the next layer,
 // so H1 and H2 are not read back from global memory. The output layer
 // accumulates in TMEM columns of its own, so that in training the same
 // kernel goes on from Y to the loss against T (dY = (Y - T) / n, the loss and
@@ -628,7 +635,7 @@ struct FwdArgs {
   const uint16_t* X;                  // [n][32] BF16
   const uint16_t *w1, *w2, *w3;       // [128][32], [128][128], [2][128] BF16
   const float* p;                     // FP32 parameters (biases)
-  float* Z1;                          // [n][128] FP32 (training)
+  __nv_bfloat16* G1;                  // [n][128] silu'(Z1) in BF16 (training)
   __nv_bfloat16 *H1, *H2;             // [n][128] BF16
   float* Y;                           // [n][2] FP32, nullable
   // training (T != nullptr): the MSE loss and the first backward step
@@ -707,8 +714,9 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
     tc::fence_after();
     return !bad;
   };
-  // hidden-layer epilogue: Z = acc + bias, H = silu(Z) to global and to sH
-  auto hidden = [&](bool ok, const float* bias, float* Z, __nv_bfloat16* H) {
+  // hidden-layer epilogue: Z = acc + bias, H = silu(Z) to global and to sH,
+  // and (training, layer 1) G = silu'(Z) for the backward pass
+  auto hidden = [&](bool ok, const float* bias, __nv_bfloat16* G, __nv_bfloat16* H) {
 #pragma unroll 1
     for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
       float v[32];
@@ -720,10 +728,14 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
       }
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] += bias[c0 + j];
-      if (live && Z) {
-        float4* zp = reinterpret_cast<float4*>(Z + row * kHid + c0);
+      if (live && G) {
+        uint4* gp = reinterpret_cast<uint4*>(G + row * kHid + c0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) zp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 4; ++q)
+          gp[q] = make_uint4(pack_bf16(silu_grad(v[8 * q]), silu_grad(v[8 * q + 1])),
+                             pack_bf16(silu_grad(v[8 * q + 2]), silu_grad(v[8 * q + 3])),
+                             pack_bf16(silu_grad(v[8 * q + 4]), silu_grad(v[8 * q + 5])),
+                             pack_bf16(silu_grad(v[8 * q + 6]), silu_grad(v[8 * q + 7])));
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -742,7 +754,7 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   };
   constexpr uint32_t kIdH = tc::idesc_bf16(128, 128), kIdO = tc::idesc_bf16(128, 16);
   bool ok = layer(sX, sW1, kIn / 8, kIdH, 0);
-  hidden(ok, sb, a.Z1, a.H1);
+  hidden(ok, sb, a.G1, a.H1);
   if (ok) ok = layer(sH, sW2, kHid / 8, kIdH, 0);
   hidden(ok, sb + kHid, nullptr, a.H2);   // Z2 stays in TMEM
   if (ok) ok = layer(sH, sW3, kHid / 8, kIdO, 128);
@@ -1093,8 +1105,8 @@ struct sdcef_mlp {
   cudaStream_t st;
   float *p, *g, *m, *v;                 // FP32 parameters, gradients, Adam moments
   __nv_bfloat16 *w1, *w2, *w3;          // BF16 weight copies
-  float *Z1, *Y, *loss;                 // activations (FP32)
-  __nv_bfloat16 *H1, *H2, *dY, *dZ2, *dZ1, *X;   // BF16 activations / features
+  float *Y, *loss;                      // output, loss (FP32)
+  __nv_bfloat16 *G1, *H1, *H2, *dY, *dZ2, *dZ1, *X;   // BF16 silu'(Z1), activations, features
   int step;
   int launches;
   int sms;                              // multiprocessors of the device
@@ -1138,7 +1150,7 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   g.B = reinterpret_cast<const uint16_t*>(a.B);
   g.sbn = a.transB ? a.ldb : 1; g.sbk = a.transB ? 1 : a.ldb;
   g.C = a.C; g.scm = a.ldc; g.scn = 1;
-  g.H = a.H; g.ldh = a.ldh; g.Zin = a.Zin; g.ldz = a.ldz; g.colsum = a.colsum;
+  g.H = a.H; g.ldh = a.ldh; g.Gin = a.Gin; g.ldgin = a.ldgin; g.colsum = a.colsum;
   g.err = (int*)h->loss + 5;
   if (g.epi == kEpiAccumulate && g.M < 64 && g.N > g.M) {
     // C^T = B^T A^T: the long side of the product goes on the 128 TMEM lanes
@@ -1185,9 +1197,8 @@ GemmArgs ga() {
   return g;
 }
 
-// forward through the three layers for n rows of X; fills Z1, H1, Z2, H2, Y
 // forward through the three layers for n rows of X. Inference (T == nullptr):
-// Y (FP32 [n][2]) only. Training: Z1, H1, H2 for the backward GEMMs, and the
+// Y (FP32 [n][2]) only. Training: silu'(Z1), H1, H2 for the backward GEMMs, and the
 // loss, dY, dZ2 and the bias gradients of layers 2 and 3 (into h->g).
 cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t n, float* Y) {
   if (n <= 0) return cudaSuccess;
@@ -1203,7 +1214,7 @@ cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_
   a.H2 = h->H2;
   a.Y = Y;
   if (T) {
-    a.Z1 = h->Z1;
+    a.G1 = h->G1;
     a.T = T;
     a.inv_n = 1.0f / (float)n;
     a.dY = h->dY;
@@ -1238,11 +1249,11 @@ cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n) {
   g.A = h->dZ2; g.lda = kHid; g.transA = 1; g.B = h->H1; g.ldb = kHid;
   g.C = h->g + kOffW2; g.ldc = kHid;
   if ((e = gemm(h, g, h->aux)) != cudaSuccess) return e;
-  // dZ1 = (dZ2 W2) * silu'(Z1); gb1 += colsum
+  // dZ1 = (dZ2 W2) * silu'(Z1), silu'(Z1) stored by the forward; gb1 += colsum
   g = ga();
   g.M = (int)n; g.N = kHid; g.K = kHid;
   g.A = h->dZ2; g.lda = kHid; g.B = h->w2; g.ldb = kHid;
-  g.epi = kEpiSiluGrad; g.Zin = h->Z1; g.ldz = kHid; g.H = h->dZ1; g.ldh = kHid; g.colsum = h->g + kOffB1;
+  g.epi = kEpiSiluGrad; g.Gin = h->G1; g.ldgin = kHid; g.H = h->dZ1; g.ldh = kHid; g.colsum = h->g + kOffB1;
   if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
   // gW1 = dZ1^T X
   g = ga();
@@ -1319,7 +1330,7 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
   struct Alloc { void** p; size_t bytes; } al[] = {
       {(void**)&h->p, kNParam * 4}, {(void**)&h->g, kNParam * 4}, {(void**)&h->m, kNParam * 4},
       {(void**)&h->v, kNParam * 4}, {(void**)&h->w1, kHid * kIn * 2}, {(void**)&h->w2, kHid * kHid * 2},
-      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->Z1, R * kHid * 4},
+      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->G1, R * kHid * 2},
       {(void**)&h->Y, R * kOut * 4}, {(void**)&h->loss, 64}, {(void**)&h->H1, R * kHid * 2},
       {(void**)&h->H2, R * kHid * 2}, {(void**)&h->dY, R * kOut * 2}, {(void**)&h->dZ2, R * kHid * 2},
       {(void**)&h->dZ1, R * kHid * 2}, {(void**)&h->X, R * kIn * 2}};
@@ -1344,7 +1355,7 @@ int sdcef_mlp_destroy(sdcef_mlp* h) {
   cudaStreamSynchronize(h->aux);
   for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
   cudaStreamDestroy(h->aux);
-  void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->Z1, h->Y, h->loss,
+  void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->G1, h->Y, h->loss,
                 h->H1, h->H2, h->dY, h->dZ2, h->dZ1, h->X};
   for (void* p : ps) cudaFree(p);
   delete h;
