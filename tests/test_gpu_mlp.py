@@ -61,11 +61,13 @@ def test_targets_and_guess_round_trip():
     np.testing.assert_allclose(T.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
 
 
-def test_forward_matches_oracle_on_bf16_weights():
+# 1000 rows: 8 tiles with a ragged last one; 40001: 313 tiles, more than the
+# 2 x 152 co-resident CTAs of the fused forward
+@pytest.mark.parametrize("n", [1000, 40001])
+def test_forward_matches_oracle_on_bf16_weights(n):
     d = dev()
     flat, q = rounded_params()
     rng = np.random.default_rng(1)
-    n = 1000
     Xh = M.bf16_round(rng.standard_normal((n, 32)))
     Xh[:, 25:] = 0.0
     mlp = S.MLP(n)
