@@ -80,8 +80,9 @@ def test_forward_matches_oracle_on_bf16_weights(n):
 
 # 37 and 700 rows: one ragged 128-row tile and several; 20011 rows: the
 # weight gradients split their K = 20011 samples over ~150 CTAs of two
-# 64-sample slabs with a ragged last slab
-@pytest.mark.parametrize("n", [37, 700, 20011])
+# 64-sample slabs with a ragged last slab; 40001 rows: three slabs per CTA,
+# so that a slab reuses a row-major slot (second completion of its mbarrier)
+@pytest.mark.parametrize("n", [37, 700, 20011, 40001])
 def test_gradients_match_fp64_backprop(n):
     d = dev()
     flat, q = rounded_params(5)
