@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int),
                 ("transport", C.c_int), ("tab_mu", C.c_void_p), ("tab_D", C.c_void_p),
                 ("tab_nc", C.c_int), ("tab_nx", C.c_int), ("tab_en_max", C.c_double),
-                ("T_in", C.c_double), ("T_max", C.c_double), ("gas_molar_mass", C.c_double)]
+                ("T_in", C.c_double), ("T_max", C.c_double), ("gas_molar_mass", C.c_double),
+                ("eps_E", C.c_double)]
 
 PREC_NONE, PREC_RECAST, PREC_EXACT, PREC_MG = 0, 1, 2, 3
 MG_OPERATOR, MG_LINEAR = 0, 1
@@ -59,7 +60,8 @@ class _Batch(C.Structure):
 
 
 def default_params(**kw) -> Params:
-    """Defaults: eps_F = 1e-10, gamma = 1e-4 (Table 1), mobility 0.4 m^2/(V s)
+    """Defaults: eps_F = 1e-10, error test eps_E = 5e-10 (see or_jfnk_col),
+    gamma = 1e-4 (Table 1), mobility 0.4 m^2/(V s)
     (Sec. 2.2), GMRES(30), 50 Newton steps, 200 Krylov iterations per step,
     20 line-search halvings, absorbing electrodes, recast Schur preconditioner;
     with precond=PREC_MG its blocks are solved by V-cycles to gamma_MG = 1e-4
@@ -68,7 +70,7 @@ def default_params(**kw) -> Params:
              restart_m=30, max_newton=50, max_krylov=200, max_linesearch=20,
              bc_electron=BC_ABSORBING, precond=PREC_RECAST, mg_gamma_A=1e-4, mg_gamma_S=1e-4,
              mg_max_cycles=100, mg_transfer=MG_OPERATOR, transport=TRANSPORT_CONSTANT,
-             gas_molar_mass=0.028, T_in=300.0, T_max=2000.0)
+             gas_molar_mass=0.028, T_in=300.0, T_max=2000.0, eps_E=5e-10)
     table = kw.pop("table", None)
     p.update(kw)
     P = Params(**p)

@@ -92,6 +92,7 @@ typedef struct {
   double tab_en_max;              /* Td (1 Td = 1e-21 V m^2) */
   double T_in, T_max;             /* c = (T - T_in) / (T_max - T_in), clamped to [0, 1] */
   double gas_molar_mass;          /* kg/mol: N = rho N_A / W */
+  double eps_E;         /* error test at the stop (see or_jfnk_col), 0 = off */
 } or_params;
 
 typedef struct {
@@ -115,6 +116,7 @@ typedef struct {
 } or_col;
 
 #define OR_NA 6.02214076e23        /* Avogadro constant, 1/mol     */
+#define OR_MAX_POLISH 2            /* Newton steps for the error test at most */
 
 /* Bilinear interpolation of a [nc][nx] table with nodes c_k = k/(nc-1) and
  * x_j = j en_max/(nx-1), at (c, x) clamped to the table. */
@@ -1013,6 +1015,24 @@ static double maxabs(int n, const double* a) {
   return m;
 }
 
+/* Preconditioner blocks of Eq. linear_nls at the iterate (ne, phi_ref + psi):
+ * A, B, L from the analytic Jacobian, S~ = L + C B = L - B (C = -I), and the
+ * multigrid hierarchies where the blocks are solved by V-cycles. phin is
+ * scratch for phi. */
+static void build_prec(const or_col* c, or_prec* pr, const double* ne, const double* psi,
+                       double* phin) {
+  const int n = c->n;
+  for (int i = 0; i < n; ++i) phin[i] = phi_ref(c, i) + psi[i];
+  or_jacobian_col(c, ne, phin, pr->A, pr->B, pr->L);
+  for (int i = 0; i < n; ++i) {
+    pr->S.sub[i] = pr->L.sub[i] - pr->B.sub[i];
+    pr->S.dia[i] = pr->L.dia[i] - pr->B.dia[i];
+    pr->S.sup[i] = pr->L.sup[i] - pr->B.sup[i];
+  }
+  if (pr->mgA) or_mg_setup(pr->mgA, pr->A.sub, pr->A.dia, pr->A.sup);
+  if (pr->mgS) or_mg_setup(pr->mgS, pr->S.sub, pr->S.dia, pr->S.sup);
+}
+
 void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
                  const double* phi_old, const double* ne0, const double* phi0,
                  double* ne, double* phi, or_stats* st) {
@@ -1081,20 +1101,40 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
   double fninf = scaled_norms(n, Fe, Fp, sFe, sFp, &fn2);
   st->first_res = fninf;
   st->status = OR_MAX_NEWTON;
+  int have_prec = 0;   /* preconditioner blocks built at an earlier iterate */
+  int polished = 0;    /* Newton steps taken for the error test */
   for (int l = 0;; ++l) {
     if (!isfinite(fninf)) { st->status = OR_NONFINITE; break; }
-    if (fninf < P->eps_F) { st->status = OR_OK; break; }
+    int polish = 0;    /* the residual test holds; this step serves the error test */
+    if (fninf < P->eps_F) {
+      /* Error test (eps_E > 0). Sec. 3.2 asks that the tolerances keep the
+       * nonlinear solution error small; the residual test bounds the error only
+       * through the conditioning of S_F^-1 J S_X, which is large for columns
+       * whose potential scale (a few volts) is small beside their space-charge
+       * scale. The Newton correction e = P^-1 F(X^(l)), with the preconditioner
+       * of the last Newton step (built at X^(l) if there was none; with the
+       * exact Schur form P = J), estimates the error of X^(l). The column stops
+       * when max|e_n| <= eps_E max|n| and max|e_phi| <= eps_E max|phi|;
+       * otherwise it takes one more Newton step. */
+      if (!(P->eps_E > 0.0) || l >= P->max_newton || polished >= OR_MAX_POLISH) {
+        st->status = OR_OK;
+        break;
+      }
+      if (!have_prec) {
+        build_prec(c, &J.prec, ne, psi, phin);
+        have_prec = 1;
+      }
+      for (int i = 0; i < n; ++i) { rhs[i] = Fe[i] / sFe; rhs[n + i] = Fp[i] / sFp; }
+      jf_prec(&J, rhs, dX);
+      double nmax = maxabs(n, ne), pmax = 0.0;
+      for (int i = 0; i < n; ++i) pmax = fmax(pmax, fabs(phi_ref(c, i) + psi[i]));
+      double en = sn * maxabs(n, dX), ep = sp * maxabs(n, dX + n);
+      if (en <= P->eps_E * nmax && ep <= P->eps_E * pmax) { st->status = OR_OK; break; }
+      polish = 1;
+    }
     if (l >= P->max_newton) { st->status = OR_MAX_NEWTON; break; }
     /* build the preconditioner blocks at X^(l) */
-    for (int i = 0; i < n; ++i) phin[i] = phi_ref(c, i) + psi[i];
-    or_jacobian_col(c, ne, phin, A, B, L);
-    for (int i = 0; i < n; ++i) {                 /* S~ = L + C B = L - B */
-      S.sub[i] = L.sub[i] - B.sub[i];
-      S.dia[i] = L.dia[i] - B.dia[i];
-      S.sup[i] = L.sup[i] - B.sup[i];
-    }
-    if (J.prec.mgA) or_mg_setup(J.prec.mgA, A.sub, A.dia, A.sup);
-    if (J.prec.mgS) or_mg_setup(J.prec.mgS, S.sub, S.dia, S.sup);
+    build_prec(c, &J.prec, ne, psi, phin);
     double xs = 0.0;
     for (int i = 0; i < n; ++i) xs += (ne[i] / sn) * (ne[i] / sn) + (phin[i] / sp) * (phin[i] / sp);
     J.xnorm = sqrt(xs);
@@ -1117,11 +1157,18 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
     }
     st->krylov_it += its;
     if (!conv) st->krylov_capped++;
-    /* backtracking line search */
+    have_prec = 1;
+    /* backtracking line search. A step taken for the error test tries lam = 1
+     * only and is also accepted if the new iterate still passes the residual
+     * test: near the rounding floor of F the sufficient decrease of the scaled
+     * 2-norm (dominated by the Poisson block's floor) can fail while the step
+     * still removes the error. If neither holds, the column keeps X^(l), which
+     * passed the residual test. */
     double lam = 1.0;
     int accepted = 0;
     double tr2 = 0.0, trinf = 0.0;
-    for (int t = 0; t <= P->max_linesearch; ++t) {
+    const int max_ls = polish ? 0 : P->max_linesearch;
+    for (int t = 0; t <= max_ls; ++t) {
       for (int i = 0; i < n; ++i) {
         trial_n[i] = ne[i] + lam * sn * dX[i];
         trial_p[i] = psi[i] + lam * sp * dX[n + i];
@@ -1129,12 +1176,14 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
       or_residual_psi(c, trial_n, trial_p, trial_Fe, trial_Fp);
       st->res_evals++;
       trinf = scaled_norms(n, trial_Fe, trial_Fp, sFe, sFp, &tr2);
-      if (isfinite(tr2) && tr2 <= (1.0 - P->ls_alpha * lam * (1.0 - P->gamma)) * fn2) {
+      if (isfinite(tr2) && (tr2 <= (1.0 - P->ls_alpha * lam * (1.0 - P->gamma)) * fn2 ||
+                            (polish && trinf < P->eps_F))) {
         accepted = 1;
         break;
       }
-      if (t < P->max_linesearch) { lam *= 0.5; st->ls_halvings++; }
+      if (t < max_ls) { lam *= 0.5; st->ls_halvings++; }
     }
+    if (!accepted && polish) { st->status = OR_OK; break; }
     if (!accepted) { st->status = conv ? OR_LINESEARCH_FAIL : OR_MAX_KRYLOV; break; }
     memcpy(ne, trial_n, sizeof(double) * n);
     memcpy(psi, trial_p, sizeof(double) * n);
@@ -1143,6 +1192,7 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
     fn2 = tr2;
     fninf = trinf;
     st->newton_it++;
+    polished += polish;
     if (P->eps_X > 0.0) {
       double st_inf = lam * maxabs(2 * n, dX);
       if (st_inf < P->eps_X && fninf >= P->eps_F) { st->status = OR_OK; break; }

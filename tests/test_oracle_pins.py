@@ -427,3 +427,26 @@ def test_ion_update_telescopes_with_absorbing_electrodes():
         wl, wr = -4e-3 * GL, -4e-3 * GR
         outflow = (max(wr, 0) * b.n_ion[0, s][-1] - min(wl, 0) * b.n_ion[0, s][0]) * dt / h
         assert np.sum(b.n_ion[0, s]) - np.sum(out[s]) == pytest.approx(outflow, rel=1e-9, abs=1e-9 * np.sum(b.n_ion[0, s]))
+
+
+def test_error_test_bounds_the_root_error():
+    """The error test at the stop (eps_E): on two low-voltage columns of the bench
+    workload (|V_R| of a few volts, where the scaled Jacobian is worst
+    conditioned) the residual test alone stops 7e-10 from the root of a dense
+    exact-Jacobian Newton solve (numpy), above eps_E = 5e-10; with the error
+    test the root error falls below eps_E, at the cost of one Newton step."""
+    full = make_batch("ragged", 4096, 2_000_000)
+    for c in (1459, 2068):
+        b = full.column(c)
+        n = b.ncells
+        assert abs(b.v_right[0]) < 10.0
+        X = _dense_newton(b, O.default_params(precond=2))
+        err = lambda r: max(np.abs(r["ne"] - X[:n]).max() / np.abs(X[:n]).max(),
+                            np.abs(r["phi"] - X[n:]).max() / np.abs(X[n:]).max())
+        off = O.solve(b, O.default_params(precond=2, eps_E=0.0))
+        on = O.solve(b, O.default_params(precond=2, eps_E=5e-10))
+        assert off["status"][0] == O.OK and on["status"][0] == O.OK
+        assert off["final_res"][0] < 1e-10 and on["final_res"][0] < 1e-10
+        assert err(off) > 5e-10
+        assert err(on) <= 5e-10
+        assert on["newton_it"][0] == off["newton_it"][0] + 1
