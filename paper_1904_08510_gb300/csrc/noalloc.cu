@@ -140,6 +140,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.max_col_cells = max_col_cells;
   a.p.eps_F = p->eps_F;
   a.p.eps_X = p->eps_X;
+  a.p.eps_E = p->eps_E;
   a.p.gamma = p->gamma;
   a.p.mu = p->mobility;
   a.p.ls_alpha = p->ls_alpha;

@@ -24,6 +24,8 @@ constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kNA = 6.02214076e23;
 // lambda_FD = eps_mach^(1/3) for IEEE double (Eq. jf_dfapprox)
 constexpr double kLambdaFD = 6.0554544523933395e-06;
+// Newton steps a column may take for the error test after the residual test holds
+constexpr int kMaxPolish = 2;
 
 
 // --------------------------------------------------------------------------
@@ -31,6 +33,7 @@ constexpr double kLambdaFD = 6.0554544523933395e-06;
 // --------------------------------------------------------------------------
 struct DevParams {
   double eps_F, eps_X, gamma, mu, ls_alpha, kap;   // kap = eps0 eps_r / e
+  double eps_E;         // error test at the stop (relative, per field); 0 = off
   int m, max_newton, max_krylov, max_ls, bc, precond;
   int guess_cap;   // Newton steps from a supplied start before restarting from X^n (0 = never)
   double guess_ratio;   // reject a supplied start with ||Fhat|| > ratio ||Fhat(X^n)|| (0 = never)
@@ -298,6 +301,9 @@ struct ColShared {
   double kh2, m2kh2, m4kh2, kh2_43;
   double vald[SDCEF_MAX_SPECIES];       // ion valences as doubles
   int mgc;                              // V-cycles of this column's multigrid block solves
+  // error test: factors of an earlier Newton step are in the slot; Newton steps
+  // taken for the error test; the current step is one of them
+  int have_prec, polished, polish;
   // transport tables: table coordinates of the electrode faces (c index, and
   // the factor turning |G| into the E/N index) and dv/dG = mu + G mu'(G) there
   double tcL, sxL, tcR, sxR, muL[2], muR[2];
@@ -1108,6 +1114,48 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
 }
 
 // --------------------------------------------------------------------------
+// Error test at the stop (eps_E > 0). Sec. 3.2 asks that the tolerances keep
+// the solution error of the nonlinear system small; the residual test bounds
+// that error only through the conditioning of S_F^-1 J S_X, which is large for
+// columns whose potential scale (a few volts) is small beside their space
+// charge. The Newton correction ehat = Mhat^-1 Fhat of the current factors (the
+// last Newton step's, with the exact Schur form P = J) estimates the scaled
+// error of the iterate. True if max|s_n ehat_n| <= eps_E max|n| and
+// max|s_phi ehat_phi| <= eps_E max|phi| over the column, or if the estimate is
+// not finite (no estimate: the residual test alone decides).
+// --------------------------------------------------------------------------
+template <int TPB, typename KR, typename PR, int VAR>
+__device__ __forceinline__ bool error_test(const KArgs& a, const Geo& g, ColShared& cs,
+                                        const Slot<TPB, KR, PR>& S, int cur, PR* sh,
+                                        double* red) {
+  const int tid = g.tid, kt = g.kt;
+  const double* Fe = S.pd(PD_FE0 + 2 * cur);
+  const double* Fp = S.pd(PD_FP0 + 2 * cur);
+  const double* NP = S.pd(PD_N);
+  const double* PP = S.pd(PD_PSI);
+  const double* PR_ = S.pd(PD_PREF);
+  KR* re = S.W(0);
+  KR* rp = S.W(1);
+  for (int j = 0; j < kt; ++j) {
+    re[ix(j, tid, TPB)] = (KR)(Fe[ix(j, tid, TPB)] * cs.isFe);
+    rp[ix(j, tid, TPB)] = (KR)(Fp[ix(j, tid, TPB)] * cs.isFp);
+  }
+  __syncthreads();
+  prec_apply<TPB, KR, PR, VAR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = 0; j < kt; ++j) {
+    v[0] = fmax(v[0], fabs((double)S.Z(0)[ix(j, tid, TPB)]));
+    v[1] = fmax(v[1], fabs((double)S.Z(1)[ix(j, tid, TPB)]));
+    v[2] = fmax(v[2], fabs(NP[ix(j, tid, TPB)]));
+    v[3] = fmax(v[3], fabs(PP[ix(j, tid, TPB)] + PR_[ix(j, tid, TPB)]));
+  }
+  block_reduce<TPB>(v, 4, true, red);
+  const double en = v[0] * cs.sn, ep = v[1] * cs.sp;
+  if (!(en <= 1.79e308) || !(ep <= 1.79e308)) return true;
+  return en <= a.p.eps_E * v[2] && ep <= a.p.eps_E * v[3];
+}
+
+// --------------------------------------------------------------------------
 // The persistent solver kernel.
 // --------------------------------------------------------------------------
 // VAR: kVarBase, kVarMG (the multigrid preconditioner, SDCEF_PREC_MG) or
@@ -1232,6 +1280,9 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       cs.m2kh2 = -2.0 * cs.kh2;
       cs.m4kh2 = -4.0 * cs.kh2;
       cs.kh2_43 = (4.0 / 3.0) * cs.kh2;
+      cs.have_prec = 0;
+      cs.polished = 0;
+      cs.polish = 0;
     }
     if (start_differs) {
       if (a.mode == MODE_PRECOND) {
@@ -1292,6 +1343,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     const int n_att = (guessed || reject) ? 2 : 1;
     for (int attempt = reject ? 1 : 0; attempt < n_att; ++attempt) {
     if (attempt == 1) {
+      if (tid == 0) cs.have_prec = 0;
       // restart from the plain start X^n
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
@@ -1312,10 +1364,29 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     status = SDCEF_STATUS_MAX_NEWTON;
     for (int l = 0;; ++l) {
       if (!(fninf <= 1.79e308)) { status = SDCEF_STATUS_NONFINITE; break; }
-      if (fninf < a.p.eps_F) { status = SDCEF_STATUS_OK; break; }
+      // cs.polish: this step is taken after the residual test held, for the
+      // error test (kept in shared memory: it is read again by the line search)
+      if (fninf < a.p.eps_F) {
+        if (!(a.p.eps_E > 0.0) || l >= cap || cs.polished >= kMaxPolish) {
+          status = SDCEF_STATUS_OK;
+          break;
+        }
+        if (!cs.have_prec) {   // no Newton step yet: factors at X^(l)
+          bool fbad = false;
+          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &fbad);
+        }
+        if (error_test<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, red)) {
+          status = SDCEF_STATUS_OK;
+          break;
+        }
+        if (tid == 0) cs.polish = 1;
+      } else if (tid == 0) {
+        cs.polish = 0;
+      }
       if (l >= cap) { status = SDCEF_STATUS_MAX_NEWTON; break; }
       // preconditioner at X^(l) and ||S_X^{-1} X||_2 (X = (n, phi))
       prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
+      if (tid == 0) cs.have_prec = 1;
       {
         double s = 0.0;
         for (int j = 0; j < kt; ++j) {
@@ -1490,22 +1561,31 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       if (bad) { status = SDCEF_STATUS_NONFINITE; break; }
       // delta-hat is in XH (sum of y_q Mhat^{-1} V_q over the cycles)
       // ---- backtracking line search ----------------------------------------
+      // A step taken for the error test tries lam = 1 only and is also accepted
+      // if the new iterate still passes the residual test (near the rounding
+      // floor of F the sufficient decrease of the scaled 2-norm, dominated by
+      // the Poisson block's floor, can fail while the step removes the error);
+      // otherwise the column keeps X^(l), which passed the residual test.
       double lam = 1.0;
       bool accepted = false;
       const int nxt = 1 - cur;
+      const bool polish = cs.polish != 0;
+      const int max_ls = polish ? 0 : a.p.max_ls;
       double tnorm[4];
-      for (int t = 0; t <= a.p.max_ls; ++t) {
+      for (int t = 0; t <= max_ls; ++t) {
         residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, XHe, XHp, lam * cs.sn, lam * cs.sp, OUT_F,
                           S.pd(PD_FE0 + 2 * nxt), S.pd(PD_FP0 + 2 * nxt), nxt, nullptr, nullptr,
                           nullptr, nullptr, 0, halo, red, tnorm);
         ++res_evals;
         double t2 = scaled_two(tnorm);
-        if (t2 <= 1.79e308 && t2 <= (1.0 - a.p.ls_alpha * lam * (1.0 - gam)) * fn2) {
+        if (t2 <= 1.79e308 && (t2 <= (1.0 - a.p.ls_alpha * lam * (1.0 - gam)) * fn2 ||
+                               (polish && scaled_inf(tnorm) < a.p.eps_F))) {
           accepted = true;
           break;
         }
-        if (t < a.p.max_ls) lam *= 0.5;
+        if (t < max_ls) lam *= 0.5;
       }
+      if (!accepted && polish) { status = SDCEF_STATUS_OK; break; }
       if (!accepted) {
         status = converged ? SDCEF_STATUS_LINESEARCH_FAIL : SDCEF_STATUS_MAX_KRYLOV;
         break;
@@ -1522,6 +1602,7 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       fninf = scaled_inf(tnorm);
       fn2 = scaled_two(tnorm);
       ++newton;
+      if (tid == 0) cs.polished += cs.polish;
       if (a.p.eps_X > 0.0) {
         block_reduce<TPB>(&smax, 1, true, red);
         if (lam * smax < a.p.eps_X && fninf >= a.p.eps_F) { status = SDCEF_STATUS_OK; break; }

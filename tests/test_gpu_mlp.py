@@ -2,8 +2,13 @@
 
 BF16 bar: features match the oracle rounded to bfloat16 to one BF16 ulp; the
 network output and every parameter gradient match the oracle evaluated on the
-same BF16-rounded weights and inputs to 2e-2 relative (BF16 activations and
-operands carry 8 significant bits; accumulation is FP32).
+same BF16-rounded weights and inputs element by element: |gpu - oracle| <=
+2e-2 x the max-norm of the oracle's output column or parameter tensor (BF16
+activations and operands carry 8 significant bits; accumulation is FP32). A
+numpy emulation of the kernels' rounding points stays below 7e-3 on these
+cases. The rows of the last, ragged 128-row tile are scaled up (inputs x3 for
+the forward pass, targets x300 for the gradients), so that a wrong or dropped
+last tile or split-K slab moves the compared values by far more than the bar.
 """
 import numpy as np
 import pytest
@@ -35,6 +40,20 @@ def rounded_params(seed=3):
     for k in ("W1", "W2", "W3"):
         q[k] = M.bf16_round(q[k])
     return flat, q
+
+
+def tail_rows(n):
+    """Rows of the last, ragged 128-row tile."""
+    return n - 128 * ((n - 1) // 128)
+
+
+def assert_elementwise(a, r, rel, what):
+    """|a - r| <= rel * max|r| for every element of each column (axis 0 scale)."""
+    a = np.atleast_2d(np.asarray(a, dtype=np.float64).T).T
+    r = np.atleast_2d(np.asarray(r, dtype=np.float64).T).T
+    scale = np.abs(r).max(axis=0)
+    err = np.abs(a - r) / np.maximum(scale, 1e-30)
+    assert err.max() <= rel, (what, float(err.max()), np.unravel_index(err.argmax(), err.shape))
 
 
 def test_features_match_oracle():
@@ -70,12 +89,13 @@ def test_forward_matches_oracle_on_bf16_weights(n):
     rng = np.random.default_rng(1)
     Xh = M.bf16_round(rng.standard_normal((n, 32)))
     Xh[:, 25:] = 0.0
+    Xh[-tail_rows(n):] *= 3.0          # the ragged last tile carries the largest outputs
     mlp = S.MLP(n)
     mlp.set_params(flat)
     X = torch.as_tensor(Xh, dtype=torch.float32, device=d).to(torch.bfloat16)
     Y = mlp.forward(X).cpu().numpy()
     Yr, _ = M.forward(q, Xh)
-    assert np.linalg.norm(Y - Yr) <= 2e-2 * np.linalg.norm(Yr)
+    assert_elementwise(Y, Yr, 2e-2, "Y")
 
 
 # 37 and 700 rows: one ragged 128-row tile and several; 20011 rows: the
@@ -90,6 +110,9 @@ def test_gradients_match_fp64_backprop(n):
     Xh = M.bf16_round(rng.standard_normal((n, 32)))
     Xh[:, 25:] = 0.0
     Th = rng.standard_normal((n, 2))
+    # the samples of the ragged last tile (and so of the last split-K slab)
+    # dominate every weight gradient: dropping them changes each by > 80 %
+    Th[-tail_rows(n):] *= 300.0
     mlp = S.MLP(n)
     mlp.set_params(flat)
     X = torch.as_tensor(Xh, dtype=torch.float32, device=d).to(torch.bfloat16)
@@ -104,7 +127,8 @@ def test_gradients_match_fp64_backprop(n):
         a, r = g[k], gr[k]
         if k == "W1":
             a, r = a[:, :25], r[:, :25]
-        assert np.linalg.norm(a - r) <= 2e-2 * np.linalg.norm(r), k
+        # one scale per tensor: the max-norm of the oracle's gradient
+        assert_elementwise(np.ravel(a), np.ravel(r), 2e-2, k)
 
 
 def test_adam_step_matches_oracle():
@@ -167,12 +191,15 @@ def test_fused_guess_matches_oracle_network(components):
     ne, phi = ne.cpu().numpy(), phi.cpu().numpy()
     Y, _ = M.forward(q, M.bf16_round(M.features(b)))
     sn, sp = M.column_scales(b)
+    yn = np.empty(b.ncells)
+    yp = np.empty(b.ncells)
     for c in range(b.ncol):
         s = slice(b.col_off[c], b.col_off[c + 1])
-        yn = (ne[s] - b.ne_old[s]) / sn[c]
-        assert np.linalg.norm(yn - Y[s, 0]) <= 2e-2 * np.linalg.norm(Y[s, 0]) + 1e-6
-        if components & S.GUESS_PHI:
-            yp = (phi[s] - b.phi_old[s]) / sp[c]
-            assert np.linalg.norm(yp - Y[s, 1]) <= 2e-2 * np.linalg.norm(Y[s, 1]) + 1e-6
-        else:
+        yn[s] = (ne[s] - b.ne_old[s]) / sn[c]
+        yp[s] = (phi[s] - b.phi_old[s]) / sp[c]
+        if not components & S.GUESS_PHI:
             assert np.array_equal(phi[s], b.phi_old[s])
+    # every cell of every column against the network's output scale
+    assert_elementwise(yn, Y[:, 0], 2e-2, "dn")
+    if components & S.GUESS_PHI:
+        assert_elementwise(yp, Y[:, 1], 2e-2, "dphi")
