@@ -178,8 +178,48 @@ def algorithmic_model(lengths, newton, krylov, res_evals, precond, kr_bytes):
     return float(np.sum(flop_cell * N)), float(np.sum(byte_cell * N))
 
 
-def cpu_baseline(batch, seconds, precond):
-    """The CPU oracle on a bounded prefix sample of the same workload."""
+def parity_sample(b, n_rand=54, seed=0):
+    """Columns compared with the oracle: the shortest, the longest, the eight
+    with the smallest |V_R| (the worst-conditioned scaled Jacobians) and a
+    seeded draw."""
+    lens = b.lengths()
+    cols = {int(np.argmin(lens)), int(np.argmax(lens))}
+    cols |= set(int(c) for c in np.argsort(np.abs(b.v_right))[:8])
+    rng = np.random.default_rng(seed)
+    cols |= set(int(c) for c in rng.choice(b.ncol, min(n_rand, b.ncol), replace=False))
+    return sorted(cols)
+
+
+def err_vs_oracle(parity):
+    """Max-norm relative error per column and field of each GPU leg against the
+    oracle's root converged to its rounding floor (eps_F = 1e-13, error test at
+    1e-14), on a sample of each batch's columns."""
+    import oracle as O
+    out = {}
+    for family, (b, legs) in parity.items():
+        cols = parity_sample(b)
+        sub = b.subset(cols)
+        ref = O.solve(sub, O.default_params(precond=2, eps_F=1e-13, max_linesearch=6, eps_E=1e-14))
+        ok = np.isin(ref["status"], [0, 3]) & (ref["final_res"] < 1e-10)
+        fam = {"columns": len(cols), "reference_ok": int(ok.sum())}
+        for leg, (ne, phi) in legs.items():
+            en, ep = [], []
+            for k, c in enumerate(cols):
+                if not ok[k]:
+                    continue
+                s = slice(int(b.col_off[c]), int(b.col_off[c + 1]))
+                r = slice(int(sub.col_off[k]), int(sub.col_off[k + 1]))
+                en.append(np.abs(ne[s] - ref["ne"][r]).max() / np.abs(ref["ne"][r]).max())
+                ep.append(np.abs(phi[s] - ref["phi"][r]).max() / np.abs(ref["phi"][r]).max())
+            fam[leg] = {"ne_max": float(np.max(en)), "phi_max": float(np.max(ep)),
+                        "ne_median": float(np.median(en)), "phi_median": float(np.median(ep))}
+        out[family] = fam
+    return out
+
+
+def cpu_baseline(batch, seconds, precond, parity=None):
+    """The CPU oracle on a bounded prefix sample of the same workload; with
+    parity, also the GPU legs' errors against the oracle's converged root."""
     import oracle as O
     P = O.default_params(precond=2 if precond == "exact" else 1,
                          restart_m=30 if precond == "recast" else 30)
@@ -199,8 +239,9 @@ def cpu_baseline(batch, seconds, precond):
     t0 = time.perf_counter()
     O.solve(batch.subset(range(m1)), P, threads=1)
     el1 = time.perf_counter() - t0
+    errs = err_vs_oracle(parity) if parity else None
     return {"value": m / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "value_1core": m1 / el1,
+            "value_1core": m1 / el1, "err_vs_oracle": errs,
             "sample": f"first {m} of {batch.ncol} columns ({int(sub.ncells)} cells), "
                       f"{el:.1f} s on {threads} threads, status OK {int((r['status'] == 0).sum())}/{m}; "
                       f"1 core: first {m1} columns, {el1:.2f} s"}
@@ -298,6 +339,9 @@ def main():
         barrier()
     ms = [a.elapsed_time(bb) for a, bb in ev]
     tot_ms = max_over_ranks(float(sum(ms)), device=dev)
+    # denominators of the ALU roofline, measured on this GPU after the timed region
+    fp64_peak = S.fma_peak_probe(S.FP64, 300)
+    fp32_peak = S.fma_peak_probe(S.MIXED, 12000)
     value = job_throughput(b.ncol, ws, args.steps, tot_ms / 1e3)
     st = out["status"].cpu().numpy()
     nw = out["newton_it"].cpu().numpy()
@@ -329,8 +373,10 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     extra = None
+    parity = {"headline": (b, {f"plain_{args.precision}": (out["ne"].cpu().numpy(),
+                                                         out["phi"].cpu().numpy())})}
     if not args.no_extras and ws == 1:
-        extra = extras(args, S, b, db, solver, params, dev)
+        extra = extras(args, S, b, db, solver, params, dev, parity)
     if rank != 0:
         return 0
     peaks, peak_kind = load_peaks()
@@ -338,13 +384,17 @@ def main():
     t_launch = tot_ms / args.steps / 1e3
     clocks = clk.summary()
     sm_clk = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    fp64_nominal = 152 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     achieved_tf = flops / t_launch / 1e12
     hbm_gbs = sbytes / t_launch / 1e9
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(b.ncells, tuned[0] if tuned else args.tpc),
                 "kernel": "jfnk_kernel (persistent solver)",
-                "peak_source": "FP64 FMA pipe, 2 DFMA/clk/SM x 152 SM x max SM clock",
+                "peak_source": "measured in this run: sdcef_fma_peak_probe, FP64 FMA chains on every SM, "
+                               "best of 5 CUDA-event timings",
+                "peak_nominal": {"value": fp64_nominal, "unit": "TFLOP/s",
+                                 "how": "2 DFMA/clk/SM x 152 SM x max SM clock"},
+                "fp32_fma_measured_tflops": fp32_peak,
                 "streaming_model": {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                     "frac": hbm_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind}}
     if roofline["traffic"] is not None:
@@ -354,7 +404,7 @@ def main():
                                 "frac": dram / peaks["hbm_gbs"], "peak_kind": peak_kind}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(b, args.cpu_seconds, args.precond)
+        cpu = cpu_baseline(b, args.cpu_seconds, args.precond, parity)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -367,6 +417,7 @@ def main():
                        "l2": "flushed between steps (256 MB write); inputs 5 x 8 B x cells > L2",
                        "parallelism": f"replicas x{ws}"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "err_vs_oracle": cpu["err_vs_oracle"] if cpu else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "comparisons": extra,
             "solve_stats": {"status_ok": int((st == 0).sum()), "ncol": int(b.ncol),
                             "status_hist": np.bincount(st, minlength=6).tolist(),
@@ -399,10 +450,12 @@ def _colerr(b, a, ref):
                      for s in (slice(b.col_off[c], b.col_off[c + 1]) for c in range(b.ncol))])
 
 
-def extras(args, S, b, db, solver, params, dev):
+def extras(args, S, b, db, solver, params, dev, parity):
     """The other configurations of the benchmark, reported beside the headline
     (not part of `value`): single column, unbatched comparator, mixed precision,
-    learned guess, SDC electric sweep."""
+    learned guess, SDC electric sweep. The learned legs' roots are added to
+    `parity` (family -> (batch, {leg: (ne, phi)})) for the comparison with the
+    oracle in the CPU-baseline leg."""
     import torch
     from paper_1904_08510_gb300 import learned as Lrn
     from paper_1904_08510_gb300.workload import make_batch, sdc_batch
@@ -487,9 +540,10 @@ def extras(args, S, b, db, solver, params, dev):
         gdb = db.with_guess(ne_g, ph_g)
         o_ref = solver.solve(db)
         legs = {}
-        for name, prec in (("headline_workload_learned", S.FP64),
-                           ("headline_workload_mixed_df_learned", S.MIXED_DF)):
-            sl = S.Solver(S.default_params(precision=prec, precond=params.precond, restart_m=8,
+        for name, prec, rm in (("headline_workload_learned", S.FP64, 8),
+                               ("headline_workload_mixed_df_learned", S.MIXED_DF, 8),
+                               ("headline_workload_mixed_learned", S.MIXED, 16)):
+            sl = S.Solver(S.default_params(precision=prec, precond=params.precond, restart_m=rm,
                                            threads_per_column=params.threads_per_column),
                           max_cols=b.ncol, max_cells=b.ncells, max_col_cells=int(b.lengths().max()))
             ol_ = sl.alloc_result(db)
@@ -504,7 +558,9 @@ def extras(args, S, b, db, solver, params, dev):
             res[name] = {"value": b.ncol / tl, "unit": "column-solves/s",
                          "status_ok": int((ol["status"] == 0).sum().item()), **_iterations(ol),
                          "err_vs_plain_fp64_ne": {"max": float(en.max()), "median": float(np.median(en))},
-                         "err_vs_plain_fp64_phi": {"max": float(ep.max()), "median": float(np.median(ep))}}
+                         "err_vs_plain_fp64_phi": {"max": float(ep.max()), "median": float(np.median(ep))},
+                         "err_vs_oracle": "see err_vs_oracle.headline." + name}
+            parity["headline"][1][name] = (ol["ne"].cpu().numpy(), ol["phi"].cpu().numpy())
             sl.close()
         res["headline_workload_plain_iterations"] = _iterations(o_ref)
         mlp.close()
@@ -525,6 +581,8 @@ def extras(args, S, b, db, solver, params, dev):
             mlp.guess(db4, ne_g, ph_g, components=S.GUESS_NE)
             return s4.solve(db4.with_guess(ne_g, ph_g), out4)
         tl, ol = _timed(learned)
+        parity["holdout"] = (b4, {"plain_fp64": (op["ne"].cpu().numpy(), op["phi"].cpu().numpy()),
+                                  "learned_fp64": (ol["ne"].cpu().numpy(), ol["phi"].cpu().numpy())})
         tg, _ = _timed(lambda: mlp.guess(db4, ne_g, ph_g, components=S.GUESS_NE))
         res["config4_learned_guess"] = {
             "columns": b4.ncol, "cells": "512-2048",

@@ -264,6 +264,17 @@ int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double*
  * SDCEF_ERR_INVALID for NULL arrays or n < 0. */
 int sdcef_bernoulli_batch(sdcef_ctx* ctx, const double* x, double* b, double* db, int64_t n);
 
+/* Measurement aid, not an operation of the paper: the FP64 (precision =
+ * SDCEF_FP64) or FP32 (SDCEF_MIXED) FMA throughput of this GPU, the
+ * denominator of the solver kernel's ALU roofline. Runs 8 independent FMA
+ * chains per thread, 16 FMAs per chain per loop trip, `iters` trips, on a grid
+ * of (SMs x resident blocks) x 256 threads on `stream` (a cudaStream_t, NULL =
+ * default), once as warm-up and 5 times timed with CUDA events; *tflops (HOST)
+ * receives the best rate in TFLOP/s (2 flops per FMA). Allocates a small output
+ * buffer and synchronises: not for use inside a stream capture. Returns
+ * SDCEF_ERR_INVALID for another precision, iters < 1 or tflops NULL. */
+int sdcef_fma_peak_probe(int precision, int iters, void* stream, double* tflops);
+
 /* Apply the configured preconditioner, built at X = (ne, phi), to the
  * residual-space vector (r_e, r_phi) in physical (unscaled) units:
  * x = P^-1 r with P^-1 from Eq. prec (SDCEF_PREC_EXACT: x = J^-1 r) or
@@ -365,9 +376,11 @@ int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* batch, int k_max, double 
  * columns run concurrently than with a context (as many slots as fit in the
  * array), so throughput is lower.
  *
- * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress, with the device current); make that first call
- * before any stream capture. Every call on a device shares the one array and
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so the entry point stays
+ * valid after cudaDeviceReset. The first call on a device may load the
+ * library's device code there; make that first call before any stream
+ * capture. Every call on a device shares the one array and
  * leaves its contents behind (the call itself zeroes the work-queue counter,
  * the only part that must start at zero): calls that overlap on the GPU, on
  * different streams or threads, race and give wrong results. Enqueued on
@@ -444,6 +457,16 @@ int sdcef_mlp_last_launch_count(const sdcef_mlp* mlp);
  * wait; the affected rows were written as NaN): SDCEF_ERR_CUDA with a message
  * if so, SDCEF_SUCCESS otherwise. Clears the condition. */
 int sdcef_mlp_check(sdcef_mlp* mlp);
+
+/* Failure-path test hook, not an operation of the paper: the number of polls
+ * of the main bounded mbarrier waits of this handle's tensor-core kernels
+ * (forward, grad, train_step, guess); polls < 0 restores the default (2^22).
+ * With polls = 0 every such wait gives up at once, as a wait that ran out would:
+ * the kernel sets the error word that sdcef_mlp_check reports, writes NaN for
+ * the rows it was computing and skips the rest of its work; its clean-up wait,
+ * which lets an issued MMA finish before the tensor memory is freed, keeps the
+ * default bound. Takes effect from the next call; no GPU work. */
+int sdcef_mlp_set_wait_polls(sdcef_mlp* mlp, int polls);
 
 /* Message of the last error on this thread (static storage). */
 const char* sdcef_last_error(void);

@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, f"kern_{var.lower()}.o")
         jobs.append((obj, [nvcc, *ARCH, *FLAGS, f"-DSDCEF_{var}", "-c",
                            os.path.join(CSRC, "kern_inst.cu"), "-o", obj]))
-    for src in ("sdcef.cu", "noalloc.cu", "mlp.cu", "fields.cu"):
+    for src in ("sdcef.cu", "noalloc.cu", "mlp.cu", "fields.cu", "probe.cu"):
         obj = os.path.join(BUILD, src.replace(".cu", "_host.o"))
         jobs.append((obj, [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]))
 

@@ -204,6 +204,7 @@ struct TcGemm {
   float* colsum;
   int* err;
   int tmaA, tmaB;   // the operand's slabs come by TMA (tensor maps of the launch)
+  int polls;        // polls of the main bounded waits (the clean-up waits use the default)
 };
 
 constexpr int kEpiAccumulate = 0, kEpiSiluGrad = 2;         // GemmArgs::epi
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
     unsigned char* natB = natB0 + (s & 1) * natB_sz;
     if (amn || bmn) {
       if (tmaA || tmaB) {   // slab s's boxes: completion (s >> 1) of its slot's mbarrier
-        const bool w = tc::wait_phase(l_bar(s), (uint32_t)((s >> 1) & 1));
+        const bool w = tc::wait_phase(l_bar(s), (uint32_t)((s >> 1) & 1), g.polls);
         if (__syncthreads_or(!w)) {
           ok = false;
           break;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
       }
       __syncthreads();
       if (NB == 1 && s >= 1) {   // the single buffers: slab s - 1's MMAs have read them
-        const bool w = tc::wait_phase(bar_of(s - 1), par_of(s - 1));
+        const bool w = tc::wait_phase(bar_of(s - 1), par_of(s - 1), g.polls);
         if (__syncthreads_or(!w)) {
           ok = false;
           break;
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
     if (nxt < nslab) {
       // with two buffers, buffer nxt & 1 was last read by the MMAs of slab nxt - 2
       if (NB == 2 && nxt >= 2) {
-        const bool w = tc::wait_phase(bar_of(nxt - 2), par_of(nxt - 2));
+        const bool w = tc::wait_phase(bar_of(nxt - 2), par_of(nxt - 2), g.polls);
         if (__syncthreads_or(!w)) {
           ok = false;
           break;
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
     }
   }
   if (ok) {   // the last commit covers every MMA issued before it
-    const bool w = tc::wait_phase(bar_of(last), par_of(last));
+    const bool w = tc::wait_phase(bar_of(last), par_of(last), g.polls);
     ok = !__syncthreads_or(!w);
   }
   tc::fence_after();
@@ -644,6 +645,7 @@ struct FwdArgs {
   __nv_bfloat16 *dY, *dZ2;            // [n][2], [n][128] BF16
   float *loss, *gb2, *gb3;            // accumulated with atomics
   int* err;
+  int polls;                          // polls of the layer waits (clean-up: the default)
 };
 
 constexpr uint32_t kFwW1 = kHid * kIn * 2, kFwW2 = kHid * kHid * 2, kFwW3 = 16 * kHid * 2,
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
                 tc::smem_desc(aB + kk * 256, 128, kc * 128), idesc, kk > 0 ? 1u : 0u);
       tc::commit(s_mbar);
     }
-    const bool w = tc::wait_phase(s_mbar, phase);
+    const bool w = tc::wait_phase(s_mbar, phase, a.polls);
     phase ^= 1u;
     const bool bad = __syncthreads_or(!w);
     tc::fence_after();
@@ -852,6 +854,7 @@ struct GuessArgs {
   int* queue;
   float* stage;                    // [cells][5] per-cell feature values (FP32)
   int* err;                        // set when a tensor-core wait times out
+  int polls;                       // polls of the layer waits (clean-up: the default)
 };
 
 // TMEM lane -> bias + SiLU -> BF16 row of the next layer's A operand
@@ -956,7 +959,7 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
       }
       tc::commit(s_mbar);
     }
-    const bool ok = tc::wait_phase(s_mbar, phase);
+    const bool ok = tc::wait_phase(s_mbar, phase, g.polls);
     phase ^= 1u;
     const bool bad = tc::bar_or(barid, W, !ok);
     tc::fence_after();
@@ -1112,6 +1115,7 @@ struct sdcef_mlp {
   int sms;                              // multiprocessors of the device
   cudaStream_t aux;                     // weight gradients beside the dZ chain
   cudaEvent_t ev[2];
+  int polls;                            // polls of the kernels' main bounded waits
 };
 
 namespace {
@@ -1152,6 +1156,7 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   g.C = a.C; g.scm = a.ldc; g.scn = 1;
   g.H = a.H; g.ldh = a.ldh; g.Gin = a.Gin; g.ldgin = a.ldgin; g.colsum = a.colsum;
   g.err = (int*)h->loss + 5;
+  g.polls = h->polls;
   if (g.epi == kEpiAccumulate && g.M < 64 && g.N > g.M) {
     // C^T = B^T A^T: the long side of the product goes on the 128 TMEM lanes
     std::swap(g.M, g.N); std::swap(g.A, g.B); std::swap(g.sam, g.sbn); std::swap(g.sak, g.sbk);
@@ -1224,6 +1229,7 @@ cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_
     a.gb3 = h->g + kOffB3;
   }
   a.err = (int*)h->loss + 5;
+  a.polls = h->polls;
   fwd_tc_kernel<<<(unsigned)((n + 127) / 128), kGemmThreads, kFwSmem, h->st>>>(a);
   ++h->launches;
   return cudaGetLastError();
@@ -1301,6 +1307,7 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
   sdcef_mlp* h = new sdcef_mlp();
   memset(h, 0, sizeof(*h));
   h->max_rows = max_rows;
+  h->polls = tc::kWaitPolls;
   h->st = (cudaStream_t)stream;
   {
     int dev = 0;
@@ -1506,6 +1513,7 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
   g.w3 = h->w3;
   g.queue = (int*)h->loss + 4;   // spare words of the loss buffer
   g.err = (int*)h->loss + 5;
+  g.polls = h->polls;
   if (ncells * 5 > h->max_rows * (kIn / 2))
     return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
   g.stage = (float*)h->X;        // [cells][5] FP32 inside the [max_rows][32] BF16 buffer
@@ -1526,6 +1534,12 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
 }
 
 int sdcef_mlp_last_launch_count(const sdcef_mlp* h) { return h ? h->launches : 0; }
+
+int sdcef_mlp_set_wait_polls(sdcef_mlp* h, int polls) {
+  if (!h) return report_error(SDCEF_ERR_INVALID, "mlp_set_wait_polls: NULL");
+  h->polls = polls < 0 ? tc::kWaitPolls : polls;
+  return SDCEF_SUCCESS;
+}
 
 int sdcef_mlp_check(sdcef_mlp* h) {
   if (!h) return report_error(SDCEF_ERR_INVALID, "mlp_check: NULL");

@@ -73,9 +73,13 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
       : "memory");
 }
 
-// bounded wait for the completion of phase `parity`; false on timeout
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+// default number of polls of a bounded wait
+constexpr int kWaitPolls = 1 << 22;
+
+// bounded wait for the completion of phase `parity`: at most `polls` polls;
+// false on timeout (polls = 0 gives up at once: the failure path's test)
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, int polls = kWaitPolls) {
+  for (int it = 0; it < polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"

@@ -12,7 +12,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/sdcef.h"
 #include "solver.cuh"
@@ -33,34 +32,23 @@ constexpr size_t kHeaderAligned = (kHeaderBytes + 255) & ~(size_t)255;
 // a device address; the device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_scratch[SDCEF_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-int g_sms[kMaxDevices] = {0};
-
-// Device address of the scratch array on the current device (set-up on the
-// first call per device, with that device current).
+// Device address of the scratch array on the current device and its SM count,
+// looked up on every call (neither allocates): an address kept from an earlier
+// call would go stale after cudaDeviceReset or a new primary context.
 int scratch_for_current_device(unsigned char** ptr, int* sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return report_error(SDCEF_ERR_INVALID, "noalloc: device index out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
-    int n = 0;
-    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
-    g_addr[dev] = p;
-    g_sms[dev] = n;
-  }
-  *ptr = (unsigned char*)g_addr[dev];
-  *sms = g_sms[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  int n = 0;
+  e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  *ptr = (unsigned char*)p;
+  *sms = n;
   return SDCEF_SUCCESS;
 }
-
 
 }  // namespace
 

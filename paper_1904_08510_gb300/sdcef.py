@@ -39,7 +39,8 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_mlp_set_params", "sdcef_mlp_get_params", "sdcef_mlp_features",
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
            "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
-           "sdcef_mlp_set_state", "sdcef_mlp_check")
+           "sdcef_mlp_set_state", "sdcef_mlp_check", "sdcef_fma_peak_probe",
+           "sdcef_mlp_set_wait_polls")
 MLP_NPARAM = 20994
 GUESS_NE, GUESS_PHI = 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -114,6 +115,8 @@ def lib():
         L.sdcef_autotune.argtypes = [vp, B, R, C.c_int, C.POINTER(C.c_int), vp]
         L.sdcef_autotune.restype = C.c_int
         L.sdcef_sdc_sweep.restype = C.c_int
+        L.sdcef_fma_peak_probe.argtypes = [C.c_int, C.c_int, vp, C.POINTER(C.c_double)]
+        L.sdcef_fma_peak_probe.restype = C.c_int
         i64 = C.c_int64
         L.sdcef_mlp_create.argtypes = [C.POINTER(vp), i64, vp]
         L.sdcef_mlp_destroy.argtypes = [vp]
@@ -127,13 +130,14 @@ def lib():
         L.sdcef_mlp_guess.argtypes = [vp, B, i64, C.c_int, vp, vp]
         L.sdcef_mlp_last_launch_count.argtypes = [vp]
         L.sdcef_mlp_check.argtypes = [vp]
+        L.sdcef_mlp_set_wait_polls.argtypes = [vp, C.c_int]
         L.sdcef_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
         L.sdcef_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
         for f in ("sdcef_mlp_create", "sdcef_mlp_destroy", "sdcef_mlp_set_params",
                   "sdcef_mlp_get_params", "sdcef_mlp_features", "sdcef_mlp_targets",
                   "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
                   "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
-                  "sdcef_mlp_set_state", "sdcef_mlp_check"):
+                  "sdcef_mlp_set_state", "sdcef_mlp_check", "sdcef_mlp_set_wait_polls"):
             getattr(L, f).restype = C.c_int
         for f in ("sdcef_create", "sdcef_destroy", "sdcef_set_params", "sdcef_solve_batch",
                   "sdcef_solve_batch_host", "sdcef_residual_batch", "sdcef_precond_apply_batch",
@@ -394,6 +398,18 @@ class Solver:
         return (xe, xp, cyc) if return_cycles else (xe, xp)
 
 
+def fma_peak_probe(precision: int = FP64, iters: int = 300, stream=None) -> float:
+    """sdcef_fma_peak_probe: measured FMA throughput (TFLOP/s) of this GPU in FP64
+    (precision=FP64) or FP32 (precision=MIXED); synchronises."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    t = C.c_double(0.0)
+    _check(lib().sdcef_fma_peak_probe(int(precision), int(iters), C.c_void_p(stream.cuda_stream),
+                                      C.byref(t)))
+    return float(t.value)
+
+
 def solve_noalloc(params: Params, db: DeviceBatch, out: dict, max_col_cells: int, stream=None):
     """sdcef_solve_batch_noalloc: the solve without a context, its workspace in the
     library's fixed device scratch array (for callers that cannot allocate)."""
@@ -465,6 +481,11 @@ class MLP:
     def check(self):
         """Raise if a tensor-core wait of an earlier call ran out (synchronises)."""
         _check(lib().sdcef_mlp_check(self.h))
+
+    def set_wait_polls(self, polls: int):
+        """Polls of the kernels' main bounded waits (test hook; < 0 = default,
+        0 = every such wait gives up at once)."""
+        _check(lib().sdcef_mlp_set_wait_polls(self.h, int(polls)))
 
     def features(self, db: DeviceBatch):
         import torch

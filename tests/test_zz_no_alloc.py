@@ -72,3 +72,52 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     with pytest.raises(S.SdcefError) as e:
         S.solve_noalloc(S.default_params(), db, out, S.NOALLOC_MAX_COL_CELLS + 1)
     assert e.value.code == S.ERR_CAPACITY
+
+
+def test_noalloc_reports_a_column_longer_than_max_col_cells():
+    """max_col_cells comes from the caller here, so the kernel's own length check
+    is the only guard on the slot size: a longer column is BAD_INPUT and the
+    others still match the context solve."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = "cuda:0"
+    b = make_batch("ragged", 12, 6060, n_range=(64, 400))
+    lens = b.lengths()
+    long_col = int(np.argmax(lens))
+    mcc = int(np.sort(lens)[-2])            # every column fits but the longest
+    assert lens[long_col] > mcc
+    p = S.default_params()
+    ref_solver = S.Solver(p, max_cols=b.ncol, max_cells=b.ncells, max_col_cells=int(lens.max()))
+    db = S.DeviceBatch.from_host(b, d)
+    ref = {k: v.cpu().numpy() for k, v in ref_solver.solve(db).items()}
+    out = ref_solver.alloc_result(db)
+    S.solve_noalloc(p, db, out, mcc)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    others = np.arange(b.ncol) != long_col
+    assert got["status"][long_col] == S.STATUS_BAD_INPUT
+    assert (got["status"][others] == S.STATUS_OK).all()
+    assert _colerr(b, got["ne"], ref["ne"])[others].max() <= 1e-9
+    assert _colerr(b, got["phi"], ref["phi"])[others].max() <= 1e-9
+    ref_solver.close()
+
+
+def test_noalloc_single_column_matches_context_solve():
+    """One column: the path that launches no column-order kernel."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = "cuda:0"
+    b = make_batch("ragged", 1, 777, n_range=(300, 900))
+    p = S.default_params()
+    n = int(b.ncells)
+    ref_solver = S.Solver(p, max_cols=1, max_cells=n, max_col_cells=n)
+    db = S.DeviceBatch.from_host(b, d)
+    ref = {k: v.cpu().numpy() for k, v in ref_solver.solve(db).items()}
+    out = ref_solver.alloc_result(db)
+    S.solve_noalloc(p, db, out, n)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    assert got["status"][0] == S.STATUS_OK and ref["status"][0] == S.STATUS_OK
+    assert got["newton_it"][0] == ref["newton_it"][0]
+    assert np.array_equal(got["ne"], ref["ne"]) and np.array_equal(got["phi"], ref["phi"])
+    ref_solver.close()
