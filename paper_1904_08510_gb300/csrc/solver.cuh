@@ -88,13 +88,21 @@ struct KArgs {
 
 // FP64 planes of a slot
 enum {
-  // PD_MUHD: mu h / D_f per face; PD_PE0: (u_f + mu g0) h / D_f, the face Peclet number
-  // at dpsi/dx = 0, so that Pe = PD_PE0 + PD_MUHD dpsi/dx is one FMA
+  // PD_MUHD: mu / D_f per face; PD_PE0: (u_f + mu g0) h / D_f, the face Peclet number
+  // at dpsi/dx = 0, so that Pe = PD_PE0 + PD_MUHD (psi_{i+1} - psi_i) is one FMA
+  // (the transport-table kernel keeps its E/N index factor in PD_MUHD instead)
   PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_MUHD, PD_PE0, PD_PREF,
   PD_FACE0,               // 4 planes: face derivative set 0 (a0, a1, b0, b1), scaled
   PD_FACE1 = PD_FACE0 + 4,
-  PD_COUNT = PD_FACE1 + 4
+  // state (n, psi) of set 1; set 0 is PD_N, PD_PSI. The state of set s is the
+  // X whose residual is in (PD_FE0, PD_FP0) + 2 s and whose face derivatives are
+  // face set s, so a line-search trial writes its state into the other set and
+  // accepting it only switches sets.
+  PD_N1 = PD_FACE1 + 4, PD_PSI1,
+  PD_COUNT
 };
+__device__ __forceinline__ int pd_n(int set) { return set ? PD_N1 : PD_N; }
+__device__ __forceinline__ int pd_psi(int set) { return set ? PD_PSI1 : PD_PSI; }
 // Krylov planes (type KR): V[(m+1)*2], W[2], Z[2], XH[2], T[2], ZK[m*2]
 // Preconditioner planes (type PR): 20 factor planes + 2 scratch planes for the
 // forward/backward sweeps of a solve; per-thread scalars (type PR).
@@ -234,34 +242,32 @@ constexpr long long kBits1em3 = 0x3F50624DD2F1A9FCLL;   // bit pattern of 1e-3
 
 // e^a - 1 for a >= 1e-3 (+inf for a >= 709 and for NaN), FP64, after the
 // table-driven method of P. T. P. Tang (ACM TOMS 15, 1989, for exp; ACM TOMS
-// 18, 1992, for expm1):
-//   k = round(64 a / ln 2) = 64 M + j,  r = a - k ln2/64 (|r| <= ln2/128),
-//   e^a = 2^M 2^(j/64) e^r,  e^r - 1 = p(r) = r + r^2 (1/2 + r/6 + r^2/24
-//   + r^3/120 + r^4/720)  (Taylor; truncation below 3e-20 on |r| <= ln2/128),
-//   e^a - 1 = (2^M T_hi - 1) + 2^M (T_lo + T_hi p),  2^(j/64) = T_hi + T_lo.
-// k comes from the shifter trick (a * 64/ln2 + 1.5 2^52 rounds to an integer
+// 18, 1992, for expm1), with a table of 1024 entries:
+//   k = round(1024 a / ln 2) = 1024 M + j,  r = a - k ln2/1024 (|r| <= ln2/2048),
+//   e^a = 2^M 2^(j/1024) e^r,  e^r - 1 = p(r) = r + r^2 (1/2 + r/6 + r^2/24)
+//   (Taylor; truncation below 4e-20 on |r| <= ln2/2048),
+//   e^a - 1 = (2^M T_hi - 1) + 2^M (T_lo + T_hi p),  2^(j/1024) = T_hi + T_lo.
+// k comes from the shifter trick (a * 1024/ln2 + 1.5 2^52 rounds to an integer
 // held in the low bits) and 2^M from the exponent bits, so the whole
-// evaluation is 13 FP64 operations (CUDA's expm1 measured ~18 FP64-pipe
-// instructions). Error below 1.4 ulp over [1e-3, 709] against a long-double
-// reference; for a in [709, inf) the Bernoulli function underflows
-// (a / (e^a - 1) < 1e-305) and +inf gives B = 0.
+// evaluation is 11 FP64 operations; the 16 KB table is read through L1. For a
+// in [709, inf) the Bernoulli function underflows (a / (e^a - 1) < 1e-305) and
+// +inf gives B = 0.
 __device__ __forceinline__ double expm1_pos(double a) {
   constexpr long long kBits709 = 0x4086280000000000LL;   // bit pattern of 709.0
   if (dbits(a) >= kBits709) return __longlong_as_double(0x7FF0000000000000LL);
   constexpr double kShift = 0x1.8p52;
+  constexpr int kMask = (1 << kExpTabBits) - 1;
   const double t = fma(a, kExpInvL, kShift);
   const int k = __double2loint(t);
   const double kd = t - kShift;
   double r = fma(-kd, kExpL1, a);
   r = fma(-kd, kExpL2, r);
-  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  q = fma(q, r, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(q, r, 0.5);
   const double p = fma(r * r, q, r);
-  const double2 T = __ldg(&kExp2Tab[k & 63]);
+  const double2 T = __ldg(&kExp2Tab[k & kMask]);
   const double u = fma(T.x, p, T.y);
-  const double s = __longlong_as_double((long long)((k >> 6) + 1023) << 52);
+  const double s = __longlong_as_double((long long)((k >> kExpTabBits) + 1023) << 52);
   return fma(s, u, fma(s, T.x, -1.0));
 }
 
@@ -395,10 +401,16 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
                          const double* nb, const double* pb, const KR* dn, const KR* dp,
                          double cn, double cp, int out_mode, double* fe_o, double* fp_o, int fs,
                          const double* fe_ref, const double* fp_ref, KR* we, KR* wp, double ieps,
-                         double* halo, double* red, double* norms) {
+                         double* halo, double* red, double* norms, double* n_o = nullptr,
+                         double* p_o = nullptr) {
   const int tid = g.tid, kt = g.kt, N = g.N;
   const double ih = cs.inv_h, dt = cs.dt, g0 = cs.g0, mu = a.p.mu, kap = a.p.kap;
   const double r = dt * ih;
+  // face differences dd: psi_{i+1} - psi_i (RAW, 1/h folded into PD_MUHD and the
+  // Poisson constant), or the gradient dpsi/dx for the transport-table kernel
+  constexpr bool RAW = VAR != kVarTable;
+  const double dsc = RAW ? 1.0 : ih;              // dd -> dd as the kernel keeps it
+  const double kpo = RAW ? kap * ih * ih : kap * ih;   // Poisson: kpo (dd_{i+1/2} - dd_{i-1/2})
   const double ie_e = ieps * cs.isFe, ie_p = ieps * cs.isFp;   // JVP output scaling
   const double* FEX = S.pd(PD_FEX);
   const double* FPHI = S.pd(PD_FPHI);
@@ -435,16 +447,17 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
     if (g.t0 == 0) {
       // left electrode face: G_L - g0 = (9 psi_0 - psi_1) / (3h)
       double p1 = kt >= 2 ? st_p(1) : halo[1 * TPB + tid + 1];
-      double dL = (9.0 * p_i - p1) * (ih * (1.0 / 3.0));
+      double dL = (9.0 * p_i - p1) * (dsc * (1.0 / 3.0));
+      const double GL = g0 + (RAW ? dL * ih : dL);
       double muL = mu;
       if constexpr (VAR == kVarTable) {
         double Dd, dmu_x, dDd;
-        const double G = g0 + dL;
+        const double G = GL;
         tab_mu_d(a.tt, cs.tcL, fabs(G) * cs.sxL, &muL, &Dd, &dmu_x, &dDd);
         // dv/dG = mu + G mu'(G) for the Jacobian row
         if (out_mode == OUT_F) cs.muL[fs] = fma(G, dmu_x * (G < 0.0 ? -cs.sxL : cs.sxL), muL);
       }
-      double vL = cs.ubl + muL * (g0 + dL);
+      double vL = cs.ubl + muL * GL;
       bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vL < 0.0;
       gam_left = act ? vL * n_i : 0.0;
       d_left = dL;
@@ -452,11 +465,15 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
     }
     for (int j = 0; j < kt; ++j) {
       const int i = g.t0 + j;
+      if (n_o) {   // the evaluated state, kept for the line search's accepted trial
+        n_o[ix(j, tid, TPB)] = n_i;
+        p_o[ix(j, tid, TPB)] = p_i;
+      }
       double n_n, p_n, gam, dd;
       if (i < N - 1) {
         n_n = (j + 1 < kt) ? st_n(j + 1) : halo[0 * TPB + tid + 1];
         p_n = (j + 1 < kt) ? st_p(j + 1) : halo[1 * TPB + tid + 1];
-        dd = (p_n - p_i) * ih;
+        dd = (p_n - p_i) * dsc;
         double Pe, dh, muf;
         double dPe_dG = 0.0, dD_dG = 0.0;   // table mode, OUT_F: slopes of the interpolant
         if constexpr (VAR == kVarTable) {
@@ -479,7 +496,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
           Pe = fma(muf, G, PE0[ix(j, tid, TPB)]) * cs.h / Df;
           dh = Df * ih;
         } else {
-          // Pe = (u_f + mu (g0 + dpsi/dx)) h / D_f
+          // Pe = (u_f + mu (g0 + dpsi/dx)) h / D_f = PE0 + (mu / D_f) (psi_{i+1} - psi_i)
           Pe = fma(MUHD[ix(j, tid, TPB)], dd, PE0[ix(j, tid, TPB)]);
           dh = DH[ix(j, tid, TPB)];
           muf = mu;
@@ -511,15 +528,16 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
       } else {
         // right electrode face: G_R - g0 = (-9 psi_{N-1} + psi_{N-2}) / (3h)
         double pm = (j >= 1) ? st_p(j - 1) : halo[3 * TPB + tid - 1];
-        dd = (-9.0 * p_i + pm) * (ih * (1.0 / 3.0));
+        dd = (-9.0 * p_i + pm) * (dsc * (1.0 / 3.0));
+        const double GR = g0 + (RAW ? dd * ih : dd);
         double muR = mu;
         if constexpr (VAR == kVarTable) {
           double Dd, dmu_x, dDd;
-          const double G = g0 + dd;
+          const double G = GR;
           tab_mu_d(a.tt, cs.tcR, fabs(G) * cs.sxR, &muR, &Dd, &dmu_x, &dDd);
           if (out_mode == OUT_F) cs.muR[fs] = fma(G, dmu_x * (G < 0.0 ? -cs.sxR : cs.sxR), muR);
         }
-        double vR = cs.ubr + muR * (g0 + dd);
+        double vR = cs.ubr + muR * GR;
         bool act = a.p.bc == SDCEF_BC_ZERO_GRADIENT || vR > 0.0;
         gam = act ? vR * n_i : 0.0;
         if (out_mode == OUT_F) cs.vR[fs] = vR;
@@ -530,12 +548,12 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
       double Fe, Fp;
       if (j == 0) {
         Fe = -n_i + fex - r * gam;     // + r * gam_left later
-        Fp = -n_i + fph + kap * ih * dd;
+        Fp = -n_i + fph + kpo * dd;
         pend_e = Fe;
         pend_p = Fp;
       } else {
         Fe = -n_i + fex - r * (gam - gam_prev);
-        Fp = -n_i + fph + kap * ih * (dd - d_prev);
+        Fp = -n_i + fph + kpo * (dd - d_prev);
         if (out_mode == OUT_F) {
           fe_o[ix(j, tid, TPB)] = Fe;
           fp_o[ix(j, tid, TPB)] = Fp;
@@ -568,7 +586,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
       d_left = halo[1 * TPB + tid - 1];
     }
     double Fe = pend_e + r * gam_left;
-    double Fp = pend_p - kap * ih * d_left;
+    double Fp = pend_p - kpo * d_left;
     if (out_mode == OUT_F) {
       fe_o[ix(0, tid, TPB)] = Fe;
       fp_o[ix(0, tid, TPB)] = Fp;
@@ -691,7 +709,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
 #pragma unroll
     for (int q = 0; q < 4; ++q) lf0[q] = halo[q * TPB + tid - 1];
   }
-  const double* NP = S.pd(PD_N);
+  const double* NP = S.pd(pd_n(fs));
   const double n0 = (g.t0 == 0 && kt > 0) ? NP[ix(0, tid, TPB)] : 0.0;
   const double nlast = (kt > 0 && g.t0 + kt == g.N) ? NP[ix(kt - 1, tid, TPB)] : 0.0;
   const double* face = S.pd(PD_FACE0 + 4 * fs);
@@ -1092,7 +1110,7 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
       } else {
         const double hd = cs.h / Df;
         DH[ix(j, tid, TPB)] = Df * cs.inv_h;
-        MUHD[ix(j, tid, TPB)] = mu * hd;
+        MUHD[ix(j, tid, TPB)] = mu / Df;
         UF[ix(j, tid, TPB)] = (uf + mu * cs.g0) * hd;
       }
     }
@@ -1131,8 +1149,8 @@ __device__ __forceinline__ bool error_test(const KArgs& a, const Geo& g, ColShar
   const int tid = g.tid, kt = g.kt;
   const double* Fe = S.pd(PD_FE0 + 2 * cur);
   const double* Fp = S.pd(PD_FP0 + 2 * cur);
-  const double* NP = S.pd(PD_N);
-  const double* PP = S.pd(PD_PSI);
+  const double* NP = S.pd(pd_n(cur));
+  const double* PP = S.pd(pd_psi(cur));
   const double* PR_ = S.pd(PD_PREF);
   KR* re = S.W(0);
   KR* rp = S.W(1);
@@ -1344,16 +1362,16 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     for (int attempt = reject ? 1 : 0; attempt < n_att; ++attempt) {
     if (attempt == 1) {
       if (tid == 0) cs.have_prec = 0;
-      // restart from the plain start X^n
+      // restart from the plain start X^n (state set 0)
       for (int j = 0; j < kt; ++j) {
         const int64_t gi = off + g.t0 + j;
-        NP[ix(j, tid, TPB)] = a.ne_old[gi];
-        PP[ix(j, tid, TPB)] = a.phi_old[gi] - S.pd(PD_PREF)[ix(j, tid, TPB)];
+        S.pd(PD_N)[ix(j, tid, TPB)] = a.ne_old[gi];
+        S.pd(PD_PSI)[ix(j, tid, TPB)] = a.phi_old[gi] - S.pd(PD_PREF)[ix(j, tid, TPB)];
       }
       cur = 0;
       bad = false;
       __syncthreads();
-      residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
+      residual<TPB, KR, PR, VAR>(a, g, cs, S, S.pd(pd_n(cur)), S.pd(pd_psi(cur)), nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       ++res_evals;
       fninf = scaled_inf(norms);
@@ -1391,8 +1409,8 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         double s = 0.0;
         for (int j = 0; j < kt; ++j) {
           const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
-          double xn = NP[ix(j, tid, TPB)] * cs.isn;
-          double xp = (PP[ix(j, tid, TPB)] + pref) * cs.isp;
+          double xn = S.pd(pd_n(cur))[ix(j, tid, TPB)] * cs.isn;
+          double xp = (S.pd(pd_psi(cur))[ix(j, tid, TPB)] + pref) * cs.isp;
           s += xn * xn + xp * xp;
         }
         double v[2] = {s, bad ? 1.0 : 0.0};
@@ -1408,7 +1426,13 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       // the final preconditioner application.
       KR* XHe = S.XH(0);
       KR* XHp = S.XH(1);
-      for (int j = 0; j < kt; ++j) { XHe[ix(j, tid, TPB)] = KR(0); XHp[ix(j, tid, TPB)] = KR(0); }
+      // the correction is dcoef * (DXe, DXp): y_0 z_0 in place when one Krylov
+      // vector sufficed in the first cycle (the common case with the exact
+      // preconditioner), else the sum accumulated in XH
+      const KR* DXe = XHe;
+      const KR* DXp = XHp;
+      double dcoef = 1.0;
+      bool first_cycle = true;
       double beta = fn2;                 // ||Fhat||_2
       const double beta0 = fn2;
       int its = 0;
@@ -1436,15 +1460,18 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           double zn = sqrt(zz);
           double eps = kLambdaFD * (kLambdaFD + cs.xnorm / zn);
           if (!(zn > 0.0)) eps = 1.0;
-          residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, S.ZK(jj, 0), S.ZK(jj, 1), eps * cs.sn,
+          residual<TPB, KR, PR, VAR>(a, g, cs, S, S.pd(pd_n(cur)), S.pd(pd_psi(cur)), S.ZK(jj, 0), S.ZK(jj, 1), eps * cs.sn,
                             eps * cs.sp, OUT_JVP, nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1),
                             1.0 / eps, halo, red, norms);
           ++res_evals;
           ++its;
-          // CGS with one re-orthogonalisation
+          // CGS with one re-orthogonalisation. Pass 1: d = V^T w, w -= V d. Pass 2
+          // reduces d2 = V^T w together with ||w||^2: the re-orthogonalised vector
+          // has ||w - V d2||^2 = ||w||^2 - ||d2||^2 (V has orthonormal columns, and
+          // after pass 1 d2 is small beside w), and its update below writes
+          // V_{jj+1} = (w - V d2) / hn directly.
           double hcur[34];
-          for (int q = 0; q <= jj; ++q) hcur[q] = 0.0;
-          for (int pass = 0; pass < 2; ++pass) {
+          {
             double d[34];
             for (int q = 0; q <= jj; ++q) d[q] = 0.0;
             for (int j = 0; j < kt; ++j) {
@@ -1463,15 +1490,24 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
               S.W(0)[ix(j, tid, TPB)] = (KR)we;
               S.W(1)[ix(j, tid, TPB)] = (KR)wp;
             }
-            for (int q = 0; q <= jj; ++q) hcur[q] += d[q];
+            for (int q = 0; q <= jj; ++q) hcur[q] = d[q];
           }
-          double wn = 0.0;
+          double d2[35];
+          for (int q = 0; q <= jj + 1; ++q) d2[q] = 0.0;
           for (int j = 0; j < kt; ++j) {
             double we = S.W(0)[ix(j, tid, TPB)], wp = S.W(1)[ix(j, tid, TPB)];
-            wn += we * we + wp * wp;
+            for (int q = 0; q <= jj; ++q)
+              d2[q] += (double)S.V(q, 0)[ix(j, tid, TPB)] * we +
+                       (double)S.V(q, 1)[ix(j, tid, TPB)] * wp;
+            d2[jj + 1] += we * we + wp * wp;
           }
-          block_reduce<TPB>(&wn, 1, false, red);
-          double hn = sqrt(wn);
+          block_reduce<TPB>(d2, jj + 2, false, red);
+          double s2 = 0.0;
+          for (int q = 0; q <= jj; ++q) {
+            s2 += d2[q] * d2[q];
+            hcur[q] += d2[q];
+          }
+          const double hn = sqrt(fmax(d2[jj + 1] - s2, 0.0));
           if (tid == 0) {
             for (int q = 0; q <= jj; ++q) Hm[q * m + jj] = hcur[q];
             Hm[(jj + 1) * m + jj] = hn;
@@ -1481,9 +1517,10 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
               Hm[(q + 1) * m + jj] = -sn_[q] * x0 + cs_[q] * x1;
             }
             double x0 = Hm[jj * m + jj], x1 = Hm[(jj + 1) * m + jj];
-            double rho = hypot(x0, x1);
-            cs_[jj] = rho == 0.0 ? 1.0 : x0 / rho;
-            sn_[jj] = rho == 0.0 ? 0.0 : x1 / rho;
+            const double rho = sqrt(fma(x0, x0, x1 * x1));
+            const double irho = 1.0 / rho;
+            cs_[jj] = rho == 0.0 ? 1.0 : x0 * irho;
+            sn_[jj] = rho == 0.0 ? 0.0 : x1 * irho;
             Hm[jj * m + jj] = rho;
             Hm[(jj + 1) * m + jj] = 0.0;
             gv[jj + 1] = -sn_[jj] * gv[jj];
@@ -1498,10 +1535,16 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           if (cv == 2) { bad = true; break; }
           if (cv) { converged = true; break; }
           if (jj + 1 < m) {
+            // pass 2's update and the normalisation: V_{jj+1} = (w - V d2) / hn
             const double ihn = 1.0 / hn;
             for (int j = 0; j < kt; ++j) {
-              S.V(jj + 1, 0)[ix(j, tid, TPB)] = (KR)((double)S.W(0)[ix(j, tid, TPB)] * ihn);
-              S.V(jj + 1, 1)[ix(j, tid, TPB)] = (KR)((double)S.W(1)[ix(j, tid, TPB)] * ihn);
+              double we = S.W(0)[ix(j, tid, TPB)], wp = S.W(1)[ix(j, tid, TPB)];
+              for (int q = 0; q <= jj; ++q) {
+                we -= d2[q] * (double)S.V(q, 0)[ix(j, tid, TPB)];
+                wp -= d2[q] * (double)S.V(q, 1)[ix(j, tid, TPB)];
+              }
+              S.V(jj + 1, 0)[ix(j, tid, TPB)] = (KR)(we * ihn);
+              S.V(jj + 1, 1)[ix(j, tid, TPB)] = (KR)(wp * ihn);
             }
           }
           __syncthreads();
@@ -1518,9 +1561,17 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         __syncthreads();
         // ||delta-hat||^2 is needed only by a restart (its FD epsilon)
         const bool restart = !(converged || its >= a.p.max_krylov);
+        if (first_cycle && !restart && kdim == 1) {
+          DXe = S.ZK(0, 0);
+          DXp = S.ZK(0, 1);
+          dcoef = yv[0];
+          first_cycle = false;
+          break;
+        }
         double dd = 0.0;
         for (int j = 0; j < kt; ++j) {
-          double xe = XHe[ix(j, tid, TPB)], xp = XHp[ix(j, tid, TPB)];
+          double xe = first_cycle ? 0.0 : (double)XHe[ix(j, tid, TPB)];
+          double xp = first_cycle ? 0.0 : (double)XHp[ix(j, tid, TPB)];
           for (int q = 0; q < kdim; ++q) {
             xe += yv[q] * (double)S.ZK(q, 0)[ix(j, tid, TPB)];
             xp += yv[q] * (double)S.ZK(q, 1)[ix(j, tid, TPB)];
@@ -1529,13 +1580,14 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           XHp[ix(j, tid, TPB)] = (KR)xp;
           if (restart) dd += xe * xe + xp * xp;
         }
+        first_cycle = false;
         __syncthreads();
         if (!restart) break;
         // restart: r = -Fhat - Jhat delta-hat
         block_reduce<TPB>(&dd, 1, false, red);
         double zn = sqrt(dd);
         double eps = (zn > 0.0) ? kLambdaFD * (kLambdaFD + cs.xnorm / zn) : 1.0;
-        residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, XHe, XHp, eps * cs.sn, eps * cs.sp, OUT_JVP,
+        residual<TPB, KR, PR, VAR>(a, g, cs, S, S.pd(pd_n(cur)), S.pd(pd_psi(cur)), XHe, XHp, eps * cs.sn, eps * cs.sp, OUT_JVP,
                           nullptr, nullptr, 0, Fe, Fp, S.W(0), S.W(1), 1.0 / eps, halo, red, norms);
         ++res_evals;
         ++its;
@@ -1559,6 +1611,10 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       }
       krylov += its;
       if (bad) { status = SDCEF_STATUS_NONFINITE; break; }
+      if (first_cycle) {   // no GMRES cycle ran (Fhat = 0): a zero correction
+        for (int j = 0; j < kt; ++j) { XHe[ix(j, tid, TPB)] = KR(0); XHp[ix(j, tid, TPB)] = KR(0); }
+        __syncthreads();
+      }
       // delta-hat is in XH (sum of y_q Mhat^{-1} V_q over the cycles)
       // ---- backtracking line search ----------------------------------------
       // A step taken for the error test tries lam = 1 only and is also accepted
@@ -1573,9 +1629,11 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
       const int max_ls = polish ? 0 : a.p.max_ls;
       double tnorm[4];
       for (int t = 0; t <= max_ls; ++t) {
-        residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, XHe, XHp, lam * cs.sn, lam * cs.sp, OUT_F,
+        residual<TPB, KR, PR, VAR>(a, g, cs, S, S.pd(pd_n(cur)), S.pd(pd_psi(cur)), DXe, DXp, lam * dcoef * cs.sn,
+                          lam * dcoef * cs.sp, OUT_F,
                           S.pd(PD_FE0 + 2 * nxt), S.pd(PD_FP0 + 2 * nxt), nxt, nullptr, nullptr,
-                          nullptr, nullptr, 0, halo, red, tnorm);
+                          nullptr, nullptr, 0, halo, red, tnorm, S.pd(pd_n(nxt)),
+                          S.pd(pd_psi(nxt)));
         ++res_evals;
         double t2 = scaled_two(tnorm);
         if (t2 <= 1.79e308 && (t2 <= (1.0 - a.p.ls_alpha * lam * (1.0 - gam)) * fn2 ||
@@ -1590,14 +1648,14 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
         status = converged ? SDCEF_STATUS_LINESEARCH_FAIL : SDCEF_STATUS_MAX_KRYLOV;
         break;
       }
-      // X += lam S_X delta-hat; step size for the eps_X test
+      // X += lam S_X delta-hat: the accepted trial's state is in set nxt;
+      // the step size for the eps_X test
       double smax = 0.0;
-      for (int j = 0; j < kt; ++j) {
-        double dn = (double)XHe[ix(j, tid, TPB)], dp = (double)XHp[ix(j, tid, TPB)];
-        NP[ix(j, tid, TPB)] = fma(lam * cs.sn, dn, NP[ix(j, tid, TPB)]);
-        PP[ix(j, tid, TPB)] = fma(lam * cs.sp, dp, PP[ix(j, tid, TPB)]);
-        if (a.p.eps_X > 0.0) smax = fmax(smax, fmax(fabs(dn), fabs(dp)));
-      }
+      if (a.p.eps_X > 0.0)
+        for (int j = 0; j < kt; ++j) {
+          double dn = (double)DXe[ix(j, tid, TPB)], dp = (double)DXp[ix(j, tid, TPB)];
+          smax = fmax(smax, fabs(dcoef) * fmax(fabs(dn), fabs(dp)));
+        }
       cur = nxt;
       fninf = scaled_inf(tnorm);
       fn2 = scaled_two(tnorm);
@@ -1616,8 +1674,8 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
     for (int j = 0; j < kt; ++j) {
       const int64_t gi = off + g.t0 + j;
       const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
-      a.ne_out[gi] = NP[ix(j, tid, TPB)];
-      a.phi_out[gi] = pref + PP[ix(j, tid, TPB)];
+      a.ne_out[gi] = S.pd(pd_n(cur))[ix(j, tid, TPB)];
+      a.phi_out[gi] = pref + S.pd(pd_psi(cur))[ix(j, tid, TPB)];
     }
     if (tid == 0) {
       if (a.status) a.status[col] = status;
