@@ -491,7 +491,8 @@ __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, in
 // rhs). sh must hold 3 * TPB * NB values of R. UT as for part_factor.
 template <int NB, typename R, typename IO, int TPB, bool UT>
 __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* rhs,
-                           IO* const* out, R* const* scr, int kt, int tid, int tact, R* sh) {
+                           IO* const* out, R* const* scr, int kt, int tid, int tact, R* sh,
+                           double* nrm2 = nullptr) {
   using FI = FIdx<NB>;
   const int m = kt - 1;
   auto ldin = [&](int j) {
@@ -510,9 +511,16 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* 
 #pragma unroll
     for (int k = 0; k < NB; ++k) scr[k][(size_t)j * TPB + tid] = v.a[k];
   };
+  // stores a row of the solution; with nrm2, also adds the squares of the
+  // stored values (this thread's part of ||out||_2^2)
+  double acc = 0.0;
   auto stout = [&](int j, const Vec<NB, R>& v) {
 #pragma unroll
-    for (int k = 0; k < NB; ++k) out[k][(size_t)j * TPB + tid] = conv<IO>(v.a[k]);
+    for (int k = 0; k < NB; ++k) {
+      const IO o = conv<IO>(v.a[k]);
+      out[k][(size_t)j * TPB + tid] = o;
+      if (nrm2) acc = fma((double)o, (double)o, acc);
+    }
   };
   Vec<NB, R> yfirst = vzero<NB, R>(), ylast = vzero<NB, R>(), rsep = vzero<NB, R>();
   if (kt > 0) {
@@ -565,6 +573,7 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* 
     }
     stout(m, xsep);
   }
+  if (nrm2) *nrm2 = acc;
   __syncthreads();   // the caller may reuse sh
 }
 

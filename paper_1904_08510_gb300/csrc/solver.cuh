@@ -92,13 +92,15 @@ enum {
   // at dpsi/dx = 0, so that Pe = PD_PE0 + PD_MUHD (psi_{i+1} - psi_i) is one FMA
   // (the transport-table kernel keeps its E/N index factor in PD_MUHD instead)
   PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_MUHD, PD_PE0, PD_PREF,
-  PD_FACE0,               // 4 planes: face derivative set 0 (a0, a1, b0, b1), scaled
-  PD_FACE1 = PD_FACE0 + 4,
+  // 3 planes per set: r dGam/dn_i, r dGam/dn_{i+1} and r dGam/dpsi_{i+1}
+  // (= -r dGam/dpsi_i) of face i+1/2, unscaled
+  PD_FACE0,
+  PD_FACE1 = PD_FACE0 + 3,
   // state (n, psi) of set 1; set 0 is PD_N, PD_PSI. The state of set s is the
   // X whose residual is in (PD_FE0, PD_FP0) + 2 s and whose face derivatives are
   // face set s, so a line-search trial writes its state into the other set and
   // accepting it only switches sets.
-  PD_N1 = PD_FACE1 + 4, PD_PSI1,
+  PD_N1 = PD_FACE1 + 3, PD_PSI1,
   PD_COUNT
 };
 __device__ __forceinline__ int pd_n(int set) { return set ? PD_N1 : PD_N; }
@@ -417,7 +419,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
   const double* DH = S.pd(PD_DH);
   const double* MUHD = S.pd(PD_MUHD);
   const double* PE0 = S.pd(PD_PE0);
-  double* face = S.pd(PD_FACE0 + 4 * fs);
+  double* face = S.pd(PD_FACE0 + 3 * fs);
   auto st_n = [&](int j) {
     double v = nb[ix(j, tid, TPB)];
     if (dn) v = fma(cn, (double)dn[ix(j, tid, TPB)], v);
@@ -522,8 +524,7 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
           }
           face[0 * a.PL + ix(j, tid, TPB)] = r * dg_n0;
           face[1 * a.PL + ix(j, tid, TPB)] = r * dg_n1;
-          face[2 * a.PL + ix(j, tid, TPB)] = -r * dg_p1;
-          face[3 * a.PL + ix(j, tid, TPB)] = r * dg_p1;
+          face[2 * a.PL + ix(j, tid, TPB)] = r * dg_p1;
         }
       } else {
         // right electrode face: G_R - g0 = (-9 psi_{N-1} + psi_{N-2}) / (3h)
@@ -629,10 +630,10 @@ struct RowJ {
 template <int TPB, typename KR, typename PR, int VAR>
 __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColShared& cs,
                                         const Slot<TPB, KR, PR>& S, int fs, int j,
-                                        const double* lf /*left face (a0,a1,b0,b1)*/, double n_i,
+                                        const double* lf /*left face's 3 derivatives*/, double n_i,
                                         double n_0, double n_last) {
   (void)n_i;
-  const double* face = S.pd(PD_FACE0 + 4 * fs);
+  const double* face = S.pd(PD_FACE0 + 3 * fs);
   const int i = g.t0 + j, N = g.N;
   const double ih = cs.inv_h, r = cs.dt * ih, mu = a.p.mu;
   RowJ R;
@@ -645,8 +646,9 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   if (i < N - 1) {
     R.Ad -= face[0 * a.PL + ix(j, g.tid, TPB)] * sa;
     R.Au -= face[1 * a.PL + ix(j, g.tid, TPB)] * sa;
-    R.Bd -= face[2 * a.PL + ix(j, g.tid, TPB)] * sb;
-    R.Bu -= face[3 * a.PL + ix(j, g.tid, TPB)] * sb;
+    const double t = face[2 * a.PL + ix(j, g.tid, TPB)] * sb;   // dGam/dpsi_i = -dGam/dpsi_{i+1}
+    R.Bd += t;
+    R.Bu -= t;
   } else {
     double vR = cs.vR[fs];
     double muR = mu;
@@ -661,8 +663,9 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   if (i > 0) {
     R.As += lf[0] * sa;
     R.Ad += lf[1] * sa;
-    R.Bs += lf[2] * sb;
-    R.Bd += lf[3] * sb;
+    const double t = lf[2] * sb;
+    R.Bs -= t;
+    R.Bd += t;
   } else {
     double vL = cs.vL[fs];
     double muL = mu;
@@ -699,34 +702,34 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
   const int tid = g.tid, kt = g.kt;
   // left-face derivatives of each thread's first row = previous thread's last face
   if (kt > 0) {
-    const double* face = S.pd(PD_FACE0 + 4 * fs);
+    const double* face = S.pd(PD_FACE0 + 3 * fs);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) halo[q * TPB + tid] = face[q * a.PL + ix(kt - 1, tid, TPB)];
+    for (int q = 0; q < 3; ++q) halo[q * TPB + tid] = face[q * a.PL + ix(kt - 1, tid, TPB)];
   }
   __syncthreads();
-  double lf0[4] = {0, 0, 0, 0};
+  double lf0[3] = {0, 0, 0};
   if (kt > 0 && tid > 0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) lf0[q] = halo[q * TPB + tid - 1];
+    for (int q = 0; q < 3; ++q) lf0[q] = halo[q * TPB + tid - 1];
   }
   const double* NP = S.pd(pd_n(fs));
   const double n0 = (g.t0 == 0 && kt > 0) ? NP[ix(0, tid, TPB)] : 0.0;
   const double nlast = (kt > 0 && g.t0 + kt == g.N) ? NP[ix(kt - 1, tid, TPB)] : 0.0;
-  const double* face = S.pd(PD_FACE0 + 4 * fs);
+  const double* face = S.pd(PD_FACE0 + 3 * fs);
   auto lface = [&](int j, double* lf) {
     if (j == 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) lf[q] = lf0[q];
+      for (int q = 0; q < 3; ++q) lf[q] = lf0[q];
     } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) lf[q] = face[q * a.PL + ix(j - 1, tid, TPB)];
+      for (int q = 0; q < 3; ++q) lf[q] = face[q * a.PL + ix(j - 1, tid, TPB)];
     }
   };
   if (a.p.precond == SDCEF_PREC_EXACT) {
     Planes<2, PR, TPB> F{S.f, S.PL};
     Scal<2, PR, TPB> Sc{S.s};
     auto rowf = [&](int j, Mat<2, PR>& M, Mat<2, PR>& D, Mat<2, PR>& U) {
-      double lf[4];
+      double lf[3];
       lface(j, lf);
       RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
       M.a[0] = conv<PR>(R.As); M.a[1] = conv<PR>(R.Bs); M.a[2] = PR(0); M.a[3] = conv<PR>(R.Ls);
@@ -743,7 +746,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     Scal<1, PR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
     const double rho = cs.r_rho;
     auto row1 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
-      double lf[4];
+      double lf[3];
       lface(j, lf);
       RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
       M.a[0] = conv<PR>(R.As); D.a[0] = conv<PR>(R.Ad); U.a[0] = conv<PR>(R.Au);
@@ -753,7 +756,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     };
     part_factor<1, PR, TPB, false>(F1, S1, kt, tid, g.tact, row1, sh, bad);
     auto row2 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
-      double lf[4];
+      double lf[3];
       lface(j, lf);
       RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
       M.a[0] = conv<PR>(R.Ls - rho * R.Bs);
@@ -769,7 +772,7 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
       PR* Bpl = S.f + 10 * S.PL;
       const double rho = cs.r_rho;
       for (int j = 0; j < kt; ++j) {
-        double lf[4];
+        double lf[3];
         lface(j, lf);
         RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
         const int i = g.t0 + j;
@@ -860,13 +863,17 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
                              const Slot<TPB, KR, PR>& S, KR* re, KR* rp, KR* ze, KR* zp, PR* sh,
                              double* red, bool want_norm) {
   const int tid = g.tid, kt = g.kt;
+  double s = 0.0;                 // this thread's part of ||z||_2^2 (want_norm)
+  bool have_s = false;
   if (a.p.precond == SDCEF_PREC_EXACT) {
     Planes<2, PR, TPB> F{S.f, S.PL};
     Scal<2, PR, TPB> Sc{S.s};
     KR* rin[2] = {re, rp};
     KR* out[2] = {ze, zp};
     PR* scr[2] = {S.f + (size_t)kScrPlane * S.PL, S.f + (size_t)(kScrPlane + 1) * S.PL};
-    part_solve<2, PR, KR, TPB, true>(F, Sc, rin, out, scr, kt, tid, g.tact, sh);
+    part_solve<2, PR, KR, TPB, true>(F, Sc, rin, out, scr, kt, tid, g.tact, sh,
+                                     want_norm ? &s : nullptr);
+    have_s = true;
   } else if (a.p.precond == SDCEF_PREC_RECAST) {
     Planes<1, PR, TPB> F1{S.f, S.PL};
     Planes<1, PR, TPB> F2{S.f + 5 * S.PL, S.PL};
@@ -968,11 +975,11 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
   }
   double nz = 0.0;
   if (want_norm) {
-    double s = 0.0;
-    for (int j = 0; j < kt; ++j) {
-      double x = ze[ix(j, tid, TPB)], y = zp[ix(j, tid, TPB)];
-      s += x * x + y * y;
-    }
+    if (!have_s)
+      for (int j = 0; j < kt; ++j) {
+        double x = ze[ix(j, tid, TPB)], y = zp[ix(j, tid, TPB)];
+        s += x * x + y * y;
+      }
     block_reduce<TPB>(&s, 1, false, red);
     nz = s;
   } else {
@@ -1179,7 +1186,7 @@ __device__ __forceinline__ bool error_test(const KArgs& a, const Geo& g, ColShar
 // VAR: kVarBase, kVarMG (the multigrid preconditioner, SDCEF_PREC_MG) or
 // kVarTable (transport tables, SDCEF_TRANSPORT_TABLE).
 template <int TPB, typename KR, typename PR, int VAR>
-__global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
+__global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_kernel(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ColShared cs;
   constexpr int NW = TPB / 32;
@@ -1470,6 +1477,45 @@ __global__ void __launch_bounds__(TPB) jfnk_kernel(KArgs a) {
           // has ||w - V d2||^2 = ||w||^2 - ||d2||^2 (V has orthonormal columns, and
           // after pass 1 d2 is small beside w), and its update below writes
           // V_{jj+1} = (w - V d2) / hn directly.
+          // First basis vector: CGS2 in closed form from one pass. With d0 = V0.w,
+          // the second pass gives d2 = d0 (1 - |V0|^2), so h = d0 + d2 and
+          // |w - h V0|^2 = |w|^2 - 2 h d0 + h^2 |V0|^2. The subtraction cancels as
+          // w nears span(V0) but errs by at most a few ulp of |w|^2, i.e. by
+          // ~1e-8 |w| in hn, far below the gamma = 1e-4 test; if this step
+          // converges (the common case with the exact preconditioner) V_1 is not
+          // needed, else the explicit passes below run.
+          if (jj == 0) {
+            double v3[3] = {0.0, 0.0, 0.0};
+            for (int j = 0; j < kt; ++j) {
+              const double we = S.W(0)[ix(j, tid, TPB)], wp = S.W(1)[ix(j, tid, TPB)];
+              const double ve = S.V(0, 0)[ix(j, tid, TPB)], vp = S.V(0, 1)[ix(j, tid, TPB)];
+              v3[0] = fma(ve, we, fma(vp, wp, v3[0]));
+              v3[1] = fma(we, we, fma(wp, wp, v3[1]));
+              v3[2] = fma(ve, ve, fma(vp, vp, v3[2]));
+            }
+            block_reduce<TPB>(v3, 3, false, red);
+            const double d0 = v3[0];
+            const double h = fma(d0, 1.0 - v3[2], d0);
+            const double hn0 = sqrt(fmax(fma(h * v3[2], h, fma(-2.0 * h, d0, v3[1])), 0.0));
+            // the rotation and residual estimate exactly as the Givens step below
+            const double rho = sqrt(fma(h, h, hn0 * hn0));
+            const double sn0 = rho == 0.0 ? 0.0 : hn0 * (1.0 / rho);
+            const double est = fabs(-sn0 * gv[0]);
+            if (est <= gam * beta0 && hn0 > 0.0 && isfinite(est)) {
+              if (tid == 0) {
+                Hm[0] = rho;
+                Hm[m] = 0.0;
+                cs_[0] = h * (1.0 / rho);
+                sn_[0] = sn0;
+                gv[1] = -sn0 * gv[0];
+                gv[0] = cs_[0] * gv[0];
+              }
+              __syncthreads();
+              kdim = 1;
+              converged = true;
+              break;
+            }
+          }
           double hcur[34];
           {
             double d[34];
