@@ -340,8 +340,8 @@ def main():
     ms = [a.elapsed_time(bb) for a, bb in ev]
     tot_ms = max_over_ranks(float(sum(ms)), device=dev)
     # denominators of the ALU roofline, measured on this GPU after the timed region
-    fp64_peak = S.fma_peak_probe(S.FP64, 300)
-    fp32_peak = S.fma_peak_probe(S.MIXED, 12000)
+    fp64_peak = S.fma_peak_probe(S.FP64, 100)
+    fp32_peak = S.fma_peak_probe(S.MIXED, 4000)
     value = job_throughput(b.ncol, ws, args.steps, tot_ms / 1e3)
     st = out["status"].cpu().numpy()
     nw = out["newton_it"].cpu().numpy()
