@@ -264,6 +264,19 @@ int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double*
  * SDCEF_ERR_INVALID for NULL arrays or n < 0. */
 int sdcef_bernoulli_batch(sdcef_ctx* ctx, const double* x, double* b, double* db, int64_t n);
 
+/* Bounds-checking build (the library compiled with -DSDCEF_CHECKS; not an
+ * operation of the paper: the stand-in for a device memory checker). In that
+ * build every plane, level, shared-memory and global index the kernels form is
+ * tested before use; a failing test records its site number (a code of
+ * csrc/checks.cuh) in the check word of the context or MLP handle, the first
+ * failure winning, and the access is redirected inside its array; nothing
+ * traps. sdcef_checks_compiled returns 1 in that build, 0 otherwise.
+ * sdcef_check_word / sdcef_mlp_check_word synchronise the stream, store the
+ * word in *word (HOST; 0 = no failed test) and clear it; in the normal build
+ * the word stays 0. They return SDCEF_ERR_INVALID for NULL arguments. */
+int sdcef_checks_compiled(void);
+int sdcef_check_word(sdcef_ctx* ctx, unsigned* word);
+
 /* Measurement aid, not an operation of the paper: the FP64 (precision =
  * SDCEF_FP64) or FP32 (SDCEF_MIXED) FMA throughput of this GPU, the
  * denominator of the solver kernel's ALU roofline. Runs 8 independent FMA
@@ -467,6 +480,10 @@ int sdcef_mlp_check(sdcef_mlp* mlp);
  * which lets an issued MMA finish before the tensor memory is freed, keeps the
  * default bound. Takes effect from the next call; no GPU work. */
 int sdcef_mlp_set_wait_polls(sdcef_mlp* mlp, int polls);
+
+/* The MLP handle's check word of the bounds-checking build (see
+ * sdcef_check_word). */
+int sdcef_mlp_check_word(sdcef_mlp* mlp, unsigned* word);
 
 /* Message of the last error on this thread (static storage). */
 const char* sdcef_last_error(void);

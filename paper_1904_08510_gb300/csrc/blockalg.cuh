@@ -30,6 +30,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "checks.cuh"
 #include "dfloat.cuh"
 
 namespace sdcef {
@@ -166,20 +167,33 @@ __device__ __forceinline__ Mat<2, R> minv(const Mat<2, R>& x, bool* bad) {
   return r;
 }
 
+template <int NB> struct FIdx;
+
 // Plane storage: a plane holds one value per (row j, thread t) at j*TPB + t.
 template <int NB, typename R, int TPB>
 struct Planes {
   R* p;
   size_t PL;   // elements per plane
+  // checked element offset of block (k0, row j, thread t): k0 .. k0 + NB^2 - 1
+  // must be factor planes and j * TPB + t an element of a plane
+  __device__ __forceinline__ size_t at(int k0, int j, int t) const {
+    if (!SDCEF_CHECK(k0 >= 0 && k0 + NB * NB <= FIdx<NB>::NPLANES && j >= 0 && t >= 0 &&
+                         t < TPB && (size_t)j * TPB + t < PL,
+                     sdcef_chk::kFacPlane))
+      return 0;
+    return (size_t)k0 * PL + (size_t)j * TPB + t;
+  }
   __device__ __forceinline__ Mat<NB, R> ldm(int k0, int j, int t) const {
     Mat<NB, R> m;
+    const size_t o = at(k0, j, t);
 #pragma unroll
-    for (int k = 0; k < NB * NB; ++k) m.a[k] = p[(size_t)(k0 + k) * PL + (size_t)j * TPB + t];
+    for (int k = 0; k < NB * NB; ++k) m.a[k] = p[o + (size_t)k * PL];
     return m;
   }
   __device__ __forceinline__ void stm(int k0, int j, int t, const Mat<NB, R>& m) const {
+    const size_t o = at(k0, j, t);
 #pragma unroll
-    for (int k = 0; k < NB * NB; ++k) p[(size_t)(k0 + k) * PL + (size_t)j * TPB + t] = m.a[k];
+    for (int k = 0; k < NB * NB; ++k) p[o + (size_t)k * PL] = m.a[k];
   }
 };
 
@@ -187,15 +201,23 @@ struct Planes {
 template <int NB, typename R, int TPB>
 struct Scal {
   R* p;
+  __device__ __forceinline__ int at(int k0, int t) const {
+    if (!SDCEF_CHECK(k0 >= 0 && k0 + NB * NB <= FIdx<NB>::NSCAL && t >= 0 && t < TPB,
+                     sdcef_chk::kScal))
+      return 0;
+    return k0 * TPB + t;
+  }
   __device__ __forceinline__ Mat<NB, R> ldm(int k0, int t) const {
     Mat<NB, R> m;
+    const int o = at(k0, t);
 #pragma unroll
-    for (int k = 0; k < NB * NB; ++k) m.a[k] = p[(k0 + k) * TPB + t];
+    for (int k = 0; k < NB * NB; ++k) m.a[k] = p[o + k * TPB];
     return m;
   }
   __device__ __forceinline__ void stm(int k0, int t, const Mat<NB, R>& m) const {
+    const int o = at(k0, t);
 #pragma unroll
-    for (int k = 0; k < NB * NB; ++k) p[(k0 + k) * TPB + t] = m.a[k];
+    for (int k = 0; k < NB * NB; ++k) p[o + k * TPB] = m.a[k];
   }
 };
 
@@ -241,13 +263,19 @@ __device__ void red_factor(Scal<NB, R, TPB> S, int tid, int T, const Mat<NB, R>&
   R* sA = sh;
   R* sB = sh + NN * TPB;
   R* sC = sh + 2 * NN * TPB;
+  auto row = [&](int i) {   // a row of the shared reduced system
+    if (!SDCEF_CHECK(i >= 0 && i < TPB, sdcef_chk::kRedRow)) i = 0;
+    return i;
+  };
   auto ld = [&](const R* b, int i) {
     Mat<NB, R> m;
+    i = row(i);
 #pragma unroll
     for (int k = 0; k < NN; ++k) m.a[k] = b[k * TPB + i];
     return m;
   };
   auto st = [&](R* b, int i, const Mat<NB, R>& m) {
+    i = row(i);
 #pragma unroll
     for (int k = 0; k < NN; ++k) b[k * TPB + i] = m.a[k];
   };
@@ -340,15 +368,23 @@ __device__ void red_solve(Scal<NB, R, TPB> S, int tid, int T, const Vec<NB, R>& 
   using FI = FIdx<NB>;
   constexpr int NN = NB * NB;
   // level l occupies sr[o_l + k * n_l + i], o_l = NB * (T + T/2 + ... ) before it
+  // the levels occupy at most NB (T + T/2 + ...) < 2 NB TPB values of sr
+  auto el = [&](int o, int n, int i) {
+    if (!SDCEF_CHECK(o >= 0 && i >= 0 && i < n && o + NB * n <= 2 * NB * TPB, sdcef_chk::kRedRow))
+      return 0;
+    return o + i;
+  };
   auto ld = [&](int o, int n, int i) {
     Vec<NB, R> v;
+    const int e = el(o, n, i);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) v.a[k] = sr[o + k * n + i];
+    for (int k = 0; k < NB; ++k) v.a[k] = sr[e + k * n];
     return v;
   };
   auto st = [&](int o, int n, int i, const Vec<NB, R>& v) {
+    const int e = el(o, n, i);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) sr[o + k * n + i] = v.a[k];
+    for (int k = 0; k < NB; ++k) sr[e + k * n] = v.a[k];
   };
   if (tid < T) st(0, T, tid, rb);
   __syncthreads();
@@ -495,30 +531,41 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* 
                            double* nrm2 = nullptr) {
   using FI = FIdx<NB>;
   const int m = kt - 1;
+  // element of row j of this thread in a right-hand side, scratch or output plane
+  auto el = [&](int j) {
+    if (!SDCEF_CHECK(j >= 0 && tid >= 0 && tid < TPB && (size_t)j * TPB + tid < F.PL,
+                     sdcef_chk::kScr))
+      return (size_t)0;
+    return (size_t)j * TPB + tid;
+  };
   auto ldin = [&](int j) {
     Vec<NB, R> v;
+    const size_t e = el(j);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) v.a[k] = conv<R>(rhs[k][(size_t)j * TPB + tid]);
+    for (int k = 0; k < NB; ++k) v.a[k] = conv<R>(rhs[k][e]);
     return v;
   };
   auto lds = [&](int j) {
     Vec<NB, R> v;
+    const size_t e = el(j);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) v.a[k] = scr[k][(size_t)j * TPB + tid];
+    for (int k = 0; k < NB; ++k) v.a[k] = scr[k][e];
     return v;
   };
   auto sts = [&](int j, const Vec<NB, R>& v) {
+    const size_t e = el(j);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) scr[k][(size_t)j * TPB + tid] = v.a[k];
+    for (int k = 0; k < NB; ++k) scr[k][e] = v.a[k];
   };
   // stores a row of the solution; with nrm2, also adds the squares of the
   // stored values (this thread's part of ||out||_2^2)
   double acc = 0.0;
   auto stout = [&](int j, const Vec<NB, R>& v) {
+    const size_t e = el(j);
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
       const IO o = conv<IO>(v.a[k]);
-      out[k][(size_t)j * TPB + tid] = o;
+      out[k][e] = o;
       if (nrm2) acc = fma((double)o, (double)o, acc);
     }
   };

@@ -9,6 +9,12 @@
 
 namespace sdcef_impl {
 
+// The cells [off, off + N) of column c lie inside the batch's cells (checked
+// build: records the site and reports the column as empty otherwise).
+__device__ __forceinline__ bool col_in_batch(unsigned* chk, int64_t off, int64_t N, int64_t cells) {
+  return SDCEF_CHECK_W(chk, off >= 0 && N >= 0 && off + N <= cells, sdcef_chk::kIonCell);
+}
+
 // n~_i = n_i - (dt/h) (Phi_{i+1/2} - Phi_{i-1/2}), Phi = w n_upwind with the
 // drift velocity w = nu kappa E at the face (E = -dphi/dx; the electrode faces
 // use the second-order one-sided gradient); electrodes absorb outgoing ions
@@ -20,6 +26,7 @@ __global__ void ion_update_kernel(IonArgs a) {
   const int N = (int)(a.col_off[c + 1] - off);
   if (N < 2) return;
   const int64_t cells = a.col_off[a.ncol];
+  if (!col_in_batch(a.chk, off, N, cells)) return;
   const double h = a.length[c] / N, ih = 1.0 / h, r = a.dt[c] * ih;
   const double* p = a.phi + off;
   const double GL = (-8.0 * a.vl[c] + 9.0 * p[0] - p[1]) * (ih * (1.0 / 3.0));
@@ -74,6 +81,7 @@ __global__ void ion_provisional_kernel(IonProvArgs a) {
   const int64_t off = a.col_off[c];
   const int N = (int)(a.col_off[c + 1] - off);
   const int64_t cells = a.col_off[a.ncol];
+  if (!col_in_batch(a.chk, off, N, cells)) return;
   if (N < 2) {
     for (int s = 0; s < a.nsp; ++s)
       for (int i = threadIdx.x; i < N; i += blockDim.x)
@@ -139,6 +147,7 @@ __global__ void ion_diffusion_kernel(IonProvArgs a) {
   const int N = (int)(a.col_off[c + 1] - off);
   if (N < 2) return;
   const int64_t cells = a.col_off[a.ncol];
+  if (!col_in_batch(a.chk, off, N, cells)) return;
   const double nu = (double)a.val[s];
   const double Dc = nu != 0.0 ? a.kappa * kKb / (fabs(nu) * kQe) : 0.0;
   const double h = a.length[c] / N, dt = a.dt[c];
@@ -183,6 +192,7 @@ __global__ void current_kernel(CurrentArgs a) {
   const int64_t off = a.col_off[c];
   const int N = (int)(a.col_off[c + 1] - off);
   const int64_t f0 = off + c;
+  if (!col_in_batch(a.chk, off, N, a.col_off[a.ncol])) return;
   if (N < 2) {
     for (int f = threadIdx.x; f <= N; f += blockDim.x) {
       a.jp[f0 + f] = 0.0;

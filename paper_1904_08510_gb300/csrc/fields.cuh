@@ -19,6 +19,7 @@ struct IonArgs {
   int nsp;
   int val[SDCEF_MAX_SPECIES];
   double kappa;
+  unsigned* chk;   // check word of the bounds-checking build (may be null)
 };
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t st);
 
@@ -32,6 +33,7 @@ struct IonProvArgs {
   int nsp;
   int val[SDCEF_MAX_SPECIES];
   double kappa;
+  unsigned* chk;   // check word of the bounds-checking build (may be null)
 };
 cudaError_t launch_ion_provisional(const IonProvArgs& a, cudaStream_t st);
 
@@ -48,6 +50,7 @@ struct CurrentArgs {
   int tnc, tnx;
   double ten_max_td, tT_in, tinv_dT, tgas_W;
   const double* rho;
+  unsigned* chk;   // check word of the bounds-checking build (may be null)
 };
 cudaError_t launch_current(const CurrentArgs& a, cudaStream_t st);
 // B(x) and B'(x) of the Scharfetter-Gummel flux, as the residual evaluates them.

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/sdcef.h"
+#include "checks.cuh"
 
 namespace sdcef_impl {
 
@@ -40,10 +41,12 @@ __host__ __device__ inline size_t mg_region_doubles(size_t PL) { return 21 * PL;
 
 struct MgOp {
   double *sub, *dia, *sup, *dinv;
+  size_t cap;   // elements of each level array (all levels of the block)
 };
 struct MgArea {
   MgOp op[2];
   double *x, *b, *xp;
+  size_t cap;   // elements of x and b (all levels)
 };
 
 __device__ inline MgArea mg_area(double* base, size_t PL) {
@@ -53,10 +56,12 @@ __device__ inline MgArea mg_area(double* base, size_t PL) {
     m.op[k].dia = base + (size_t)(8 * k + 2) * PL;
     m.op[k].sup = base + (size_t)(8 * k + 4) * PL;
     m.op[k].dinv = base + (size_t)(8 * k + 6) * PL;
+    m.op[k].cap = 2 * PL;
   }
   m.x = base + 16 * PL;
   m.b = base + 18 * PL;
   m.xp = base + 20 * PL;
+  m.cap = 2 * PL;
   return m;
 }
 
@@ -83,6 +88,8 @@ struct MgLev {
 };
 
 __device__ inline MgLev mg_lev(const MgOp& T, int off, int n) {
+  if (!SDCEF_CHECK(off >= 0 && n >= 0 && (size_t)off + n <= T.cap, sdcef_chk::kMgLevel))
+    off = n = 0;
   return MgLev{T.sub + off, T.dia + off, T.sup + off, T.dinv + off, n};
 }
 
@@ -130,6 +137,11 @@ __device__ __noinline__ void mg_build(const MgOp& T, int N, int transfer, bool* 
   int o = 0;
   for (int l = 0;; ++l) {
     const int n = N >> l;
+    // this level and the next coarser one inside the level arrays
+    if (!SDCEF_CHECK((size_t)o + n + (N >> (l + 1)) <= T.cap, sdcef_chk::kMgLevel)) {
+      ok = false;
+      break;
+    }
     for (int i = threadIdx.x; i < n; i += TPB) {
       const double d = T.dia[o + i];
       ok = ok && (d != 0.0) && isfinite(d);
@@ -181,6 +193,8 @@ __device__ __noinline__ void mg_vcycle(const MgOp& T, int N, double* X, double* 
   int o = 0, l = 0;
   for (; l + 1 < nlev; ++l) {
     const int n = N >> l, nc = N >> (l + 1), oc = o + n;
+    // the vectors X, B of this level and the next share the operator's offsets
+    if (!SDCEF_CHECK((size_t)oc + nc <= T.cap, sdcef_chk::kMgLevel)) return;
     const MgLev F = mg_lev(T, o, n);
     double* x = X + o;
     const double* b = B + o;

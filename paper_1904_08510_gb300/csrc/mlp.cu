@@ -22,6 +22,7 @@
 #include <string>
 
 #include "../../include/sdcef.h"
+#include "checks.cuh"
 #include "mlp_tc.cuh"
 
 namespace sdcef_impl {
@@ -72,6 +73,7 @@ struct FeatArgs {
   float* Tgt;           // [cells][2]
   const float* Y;       // [cells][2] network output (guess mode)
   double *ne_g, *phi_g;
+  unsigned* chk;        // check word of the bounds-checking build (may be null)
   int mode;             // 0 features, 1 targets, 2 guess
   int comps;            // guess: bit 0 applies the n_e increment, bit 1 the phi increment
 };
@@ -94,6 +96,7 @@ __global__ void feat_kernel(FeatArgs a) {
   const int64_t off = a.col_off[c];
   const int N = (int)(a.col_off[c + 1] - off);
   const int64_t cells = a.col_off[a.ncol];
+  if (!SDCEF_CHECK_W(a.chk, off >= 0 && N >= 0 && off + N <= cells, sdcef_chk::kMlpRow)) return;
   auto fphi = [&](int i) {
     double q = 0.0;
     for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * cells + off + i];
@@ -205,6 +208,7 @@ struct TcGemm {
   int* err;
   int tmaA, tmaB;   // the operand's slabs come by TMA (tensor maps of the launch)
   int polls;        // polls of the main bounded waits (the clean-up waits use the default)
+  unsigned* chk;    // check word of the bounds-checking build (may be null)
 };
 
 constexpr int kEpiAccumulate = 0, kEpiSiluGrad = 2;         // GemmArgs::epi
@@ -373,6 +377,12 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
   const int kbeg = blockIdx.y * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  // the CTA's rows and its share of K inside the matrices (before any
+  // barrier, tensor-memory allocation or copy)
+  if (!SDCEF_CHECK_W(g.chk, m0 < g.M && kbeg >= 0 && kbeg < kend && kend <= g.K &&
+                                g.N >= 1 && g.N <= 128,
+                     sdcef_chk::kMlpRow))
+    return;
   const int Np = (g.N + 15) & ~15;
   constexpr bool amn = AMN, bmn = BMN;
   // operand buffers: two per operand, except when both operands go through the
@@ -646,6 +656,7 @@ struct FwdArgs {
   float *loss, *gb2, *gb3;            // accumulated with atomics
   int* err;
   int polls;                          // polls of the layer waits (clean-up: the default)
+  unsigned* chk;                      // check word of the bounds-checking build (may be null)
 };
 
 constexpr uint32_t kFwW1 = kHid * kIn * 2, kFwW2 = kHid * kHid * 2, kFwW3 = 16 * kHid * 2,
@@ -667,6 +678,8 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   __shared__ float sred[4][3];        // per-warp loss and output-bias partials
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
+  // the CTA's rows inside the batch (before any barrier or allocation)
+  if (!SDCEF_CHECK_W(a.chk, m0 < a.n, sdcef_chk::kMlpRow)) return;
   const bool vecX = (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
   stage_k(sX, a.X, kIn, vecX, m0, a.n, 128, 0, kIn, kIn / 8, tid);
   stage_k(sW1, a.w1, kIn, true, 0, kHid, kHid, 0, kIn, kIn / 8, tid);
@@ -853,6 +866,7 @@ struct GuessArgs {
   const __nv_bfloat16 *w1, *w2, *w3;
   int* queue;
   float* stage;                    // [cells][5] per-cell feature values (FP32)
+  int64_t stage_cap;               // floats the stage buffer holds
   int* err;                        // set when a tensor-core wait times out
   int polls;                       // polls of the layer waits (clean-up: the default)
 };
@@ -973,6 +987,12 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
     if (c >= a.ncol || failed) break;
     const int64_t off = a.col_off[c];
     const int N = (int)(a.col_off[c + 1] - off);
+    // the column inside the batch and its staged features inside the stage
+    // buffer (uniform over the worker: a failed column is skipped by all)
+    if (!SDCEF_CHECK_W(a.chk, off >= 0 && N >= 0 && off + N <= cells &&
+                                  (off + N) * 5 <= g.stage_cap,
+                       sdcef_chk::kMlpStage))
+      continue;
     auto fphi = [&](int i) {
       double q = 0.0;
       for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * cells + off + i];
@@ -1033,7 +1053,9 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
         w.y = pack_bf16(f8[2], f8[3]);
         w.z = pack_bf16(f8[4], f8[5]);
         w.w = pack_bf16(f8[6], f8[7]);
-        *reinterpret_cast<uint4*>(sA + tc::cm_off(r, ch * 8, kIn / 8)) = w;
+        uint32_t ao = tc::cm_off(r, ch * 8, kIn / 8);
+        if (!SDCEF_CHECK_W(a.chk, ao + 16 <= tc::kABytes, sdcef_chk::kMlpSmem)) ao = 0;
+        *reinterpret_cast<uint4*>(sA + ao) = w;
       }
       bool ok = run_layer(1);
       if (ok) {
@@ -1119,6 +1141,11 @@ struct sdcef_mlp {
 };
 
 namespace {
+// check word of the bounds-checking build: a spare word of the loss buffer
+unsigned* mlp_chk(sdcef_mlp* h) { return reinterpret_cast<unsigned*>(h->loss) + 6; }
+}  // namespace
+
+namespace {
 
 int cuda_fail(cudaError_t e) { return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e)); }
 
@@ -1157,6 +1184,7 @@ cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
   g.H = a.H; g.ldh = a.ldh; g.Gin = a.Gin; g.ldgin = a.ldgin; g.colsum = a.colsum;
   g.err = (int*)h->loss + 5;
   g.polls = h->polls;
+  g.chk = mlp_chk(h);
   if (g.epi == kEpiAccumulate && g.M < 64 && g.N > g.M) {
     // C^T = B^T A^T: the long side of the product goes on the 128 TMEM lanes
     std::swap(g.M, g.N); std::swap(g.A, g.B); std::swap(g.sam, g.sbn); std::swap(g.sak, g.sbk);
@@ -1230,6 +1258,7 @@ cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_
   }
   a.err = (int*)h->loss + 5;
   a.polls = h->polls;
+  a.chk = mlp_chk(h);
   fwd_tc_kernel<<<(unsigned)((n + 127) / 128), kGemmThreads, kFwSmem, h->st>>>(a);
   ++h->launches;
   return cudaGetLastError();
@@ -1426,6 +1455,7 @@ int sdcef_mlp_features(sdcef_mlp* h, const sdcef_batch* b, void* X_bf16) {
   int rc = check_batch(b);
   if (rc || b->ncol == 0) return rc;
   FeatArgs a = feat_args(b);
+  a.chk = mlp_chk(h);
   a.X = (__nv_bfloat16*)X_bf16;
   a.mode = 0;
   feat_kernel<<<(unsigned)b->ncol, 128, 0, h->st>>>(a);
@@ -1439,6 +1469,7 @@ int sdcef_mlp_targets(sdcef_mlp* h, const sdcef_batch* b, const double* ne_star,
   int rc = check_batch(b);
   if (rc || b->ncol == 0) return rc;
   FeatArgs a = feat_args(b);
+  a.chk = mlp_chk(h);
   a.ne_star = ne_star;
   a.phi_star = phi_star;
   a.Tgt = targets;
@@ -1504,6 +1535,7 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
   GuessArgs g;
   memset(&g, 0, sizeof(g));
   g.f = feat_args(b);
+  g.f.chk = mlp_chk(h);
   g.f.comps = components;
   g.f.ne_g = ne_guess;
   g.f.phi_g = phi_guess;
@@ -1517,6 +1549,7 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
   if (ncells * 5 > h->max_rows * (kIn / 2))
     return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
   g.stage = (float*)h->X;        // [cells][5] FP32 inside the [max_rows][32] BF16 buffer
+  g.stage_cap = h->max_rows * (kIn / 2);
   cudaError_t e = cudaMemsetAsync(g.queue, 0, sizeof(int), h->st);
   if (e != cudaSuccess) return cuda_fail(e);
   int dev = 0, sms = 0;
@@ -1534,6 +1567,18 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
 }
 
 int sdcef_mlp_last_launch_count(const sdcef_mlp* h) { return h ? h->launches : 0; }
+
+int sdcef_mlp_check_word(sdcef_mlp* h, unsigned* word) {
+  if (!h || !word) return report_error(SDCEF_ERR_INVALID, "mlp_check_word: NULL argument");
+  unsigned w = 0;
+  cudaError_t e = cudaStreamSynchronize(h->aux);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&w, mlp_chk(h), sizeof(unsigned), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mlp_chk(h), 0, sizeof(unsigned), h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *word = w;
+  return SDCEF_SUCCESS;
+}
 
 int sdcef_mlp_set_wait_polls(sdcef_mlp* h, int polls) {
   if (!h) return report_error(SDCEF_ERR_INVALID, "mlp_set_wait_polls: NULL");

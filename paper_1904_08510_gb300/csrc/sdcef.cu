@@ -46,7 +46,7 @@ struct sdcef_ctx {
   char* ws;
   size_t ws_bytes;
   int nslots;
-  int* queue;     // 1 int
+  int* queue;     // 4 ints: [0] work-queue counter, [3] check word of the bounds-checking build
   int* order;     // max_cols ints
   int launches;
   // host-call staging
@@ -134,9 +134,12 @@ int validate_batch(const sdcef_ctx* ctx, const sdcef_batch* b, bool need_solve_i
 }
 
 // Fill kernel args shared by all modes.
+unsigned* check_word(sdcef_ctx* ctx) { return reinterpret_cast<unsigned*>(ctx->queue + 3); }
+
 KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb) {
   KArgs a;
   memset(&a, 0, sizeof(a));
+  a.chk = check_word(ctx);
   a.ncol = b->ncol;
   a.col_off = b->col_off;
   a.length = b->length;
@@ -298,6 +301,7 @@ int sdcef_create(sdcef_ctx** out, const sdcef_params* p, int64_t max_cols, int64
   c->ws_bytes = best * (size_t)nslots;
   e = cudaMalloc((void**)&c->ws, c->ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->queue, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(c->queue, 0, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->order, sizeof(int) * (size_t)max_cols);
   if (e != cudaSuccess) {
     if (c->ws) cudaFree(c->ws);
@@ -358,6 +362,26 @@ int sdcef_set_transport_table(sdcef_ctx* ctx, int nc, int nx, double en_max_td, 
 }
 
 int sdcef_last_launch_count(const sdcef_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int sdcef_checks_compiled(void) {
+#ifdef SDCEF_CHECKS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int sdcef_check_word(sdcef_ctx* ctx, unsigned* word) {
+  if (!ctx || !word) return set_err(SDCEF_ERR_INVALID, "check_word: NULL argument");
+  unsigned w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, check_word(ctx), sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(check_word(ctx), 0, sizeof(unsigned), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  *word = w;
+  return SDCEF_SUCCESS;
+}
 
 int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out) {
   Range range_("sdcef_solve_batch");
@@ -457,6 +481,7 @@ int sdcef_ion_update_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* p
   a.nsp = b->n_species;
   for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
   a.kappa = kappa_ion;
+  a.chk = check_word(ctx);
   cudaError_t e = launch_ion_update(a, ctx->stream);
   if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
   return SDCEF_SUCCESS;
@@ -494,6 +519,7 @@ int sdcef_ion_provisional_batch(sdcef_ctx* ctx, const sdcef_batch* b, const doub
   a.nsp = b->n_species;
   for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
   a.kappa = kappa_ion;
+  a.chk = check_word(ctx);
   cudaError_t e = launch_ion_provisional(a, ctx->stream);
   if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
   return SDCEF_SUCCESS;
@@ -526,6 +552,7 @@ int sdcef_current_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double* ne,
   a.nsp = b->n_species;
   for (int s = 0; s < b->n_species; ++s) a.val[s] = b->valence[s];
   a.kappa = kappa_ion;
+  a.chk = check_word(ctx);
   a.mu = ctx->p.mobility;
   a.bc = ctx->p.bc_electron;
   if (ctx->p.transport == SDCEF_TRANSPORT_TABLE) {

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "../../include/sdcef.h"
+#include "checks.cuh"
 #include "blockalg.cuh"
 #include "expm1_table.cuh"
 #include "mg.cuh"
@@ -84,6 +85,7 @@ struct KArgs {
   // field-dependent transport
   TransportTab tt;
   const double* rho;
+  unsigned* chk;      // check word of the bounds-checking build (may be null)
 };
 
 // FP64 planes of a slot
@@ -208,6 +210,7 @@ template <int TPB>
 __device__ __forceinline__ void block_reduce(double* v, int nv, bool is_max, double* red) {
   constexpr int NW = TPB / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (!SDCEF_CHECK(nv >= 0 && nv <= 40, sdcef_chk::kRed)) nv = 0;
   for (int k = 0; k < nv; ++k) {
     double x = v[k];
 #pragma unroll
@@ -329,14 +332,28 @@ struct Slot {
   PR* s;        // per-thread scalars
   size_t PL;
   int m;
-  __device__ double* pd(int i) const { return d + (size_t)i * PL; }
-  __device__ KR* V(int i, int comp) const { return k + (size_t)(2 * i + comp) * PL; }
-  __device__ KR* W(int comp) const { return k + (size_t)(2 * (m + 1) + comp) * PL; }
-  __device__ KR* Z(int comp) const { return k + (size_t)(2 * (m + 1) + 2 + comp) * PL; }
-  __device__ KR* XH(int comp) const { return k + (size_t)(2 * (m + 1) + 4 + comp) * PL; }
-  __device__ KR* T(int comp) const { return k + (size_t)(2 * (m + 1) + 6 + comp) * PL; }
+  __device__ double* pd(int i) const {
+    if (!SDCEF_CHECK(i >= 0 && i < PD_COUNT, sdcef_chk::kPlane)) i = 0;
+    return d + (size_t)i * PL;
+  }
+  __device__ KR* V(int i, int comp) const {
+    if (!SDCEF_CHECK(i >= 0 && i <= m && (comp == 0 || comp == 1), sdcef_chk::kKrylov)) i = comp = 0;
+    return k + (size_t)(2 * i + comp) * PL;
+  }
+  __device__ KR* W(int comp) const { return k + (size_t)(2 * (m + 1) + cmp(comp)) * PL; }
+  __device__ KR* Z(int comp) const { return k + (size_t)(2 * (m + 1) + 2 + cmp(comp)) * PL; }
+  __device__ KR* XH(int comp) const { return k + (size_t)(2 * (m + 1) + 4 + cmp(comp)) * PL; }
+  __device__ KR* T(int comp) const { return k + (size_t)(2 * (m + 1) + 6 + cmp(comp)) * PL; }
+  // a component number, 0 (n) or 1 (psi)
+  __device__ static int cmp(int comp) {
+    if (!SDCEF_CHECK(comp == 0 || comp == 1, sdcef_chk::kKrylov)) comp = 0;
+    return comp;
+  }
   // Mhat^{-1} V_i of the current GMRES cycle (flexible-GMRES storage)
-  __device__ KR* ZK(int i, int comp) const { return k + (size_t)(2 * (m + 1) + 8 + 2 * i + comp) * PL; }
+  __device__ KR* ZK(int i, int comp) const {
+    if (!SDCEF_CHECK(i >= 0 && i < m && (comp == 0 || comp == 1), sdcef_chk::kZk)) i = comp = 0;
+    return k + (size_t)(2 * (m + 1) + 8 + 2 * i + comp) * PL;
+  }
 };
 
 template <int TPB, typename KR, typename PR>
@@ -355,7 +372,23 @@ __device__ Slot<TPB, KR, PR> make_slot(const KArgs& a, int slot) {
   return s;
 }
 
-__device__ __forceinline__ size_t ix(int j, int tid, int TPB) { return (size_t)j * TPB + tid; }
+// Element of row j of thread tid in a slot plane (every plane holds kmax * TPB
+// elements).
+__device__ __forceinline__ size_t ix(int j, int tid, int TPB) {
+#ifdef SDCEF_CHECKS
+  if (!SDCEF_CHECK(j >= 0 && j < sdcef_chk::s_kmax && tid >= 0 && tid < TPB, sdcef_chk::kIx))
+    j = tid = 0;
+#endif
+  return (size_t)j * TPB + tid;
+}
+
+// Global index of row j of this thread inside the column [off, off + N).
+__device__ __forceinline__ int64_t cell_ix(int64_t off, const Geo& g, int j) {
+#ifdef SDCEF_CHECKS
+  if (!SDCEF_CHECK(j >= 0 && g.t0 + j < g.N, sdcef_chk::kCell)) return off;
+#endif
+  return off + g.t0 + j;
+}
 
 // Bilinear interpolation of the mobility and diffusivity tables at table
 // coordinates (tc, tx) (fractional node indices), clamped to the table; with
@@ -1049,7 +1082,7 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
   long long m_n = 0, m_fphi = 0, m_phi = 0, m_fe = 0;
   // D at this thread's first cell, for the neighbour's last face
   for (int j = 0; j < g.kt; ++j) {
-    const int64_t gi = off + g.t0 + j;
+    const int64_t gi = cell_ix(off, g, j);
     double T = a.T[gi];
     if (dbits(T) <= 0 || nonfinite(T)) bad = 1;   // T <= 0 (incl. -0), NaN or Inf
     double D = mu * (kKb / kQe) * T;
@@ -1201,12 +1234,20 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
   double* hv = yv + m;                                      // m+2 scratch
   PR* sh = (PR*)(hv + m + 2);                               // 12 * TPB (PCR / exchange)
   const int tid = threadIdx.x;
+#ifdef SDCEF_CHECKS
+  if (tid == 0) {
+    sdcef_chk::s_word = a.chk;
+    sdcef_chk::s_kmax = a.kmax;
+  }
+  __syncthreads();
+#endif
   Slot<TPB, KR, PR> S = make_slot<TPB, KR, PR>(a, blockIdx.x);
 
   for (;;) {
     if (tid == 0) {
       int q = atomicAdd(a.queue, 1);
       cs.col = (q < a.ncol) ? (a.order ? a.order[q] : q) : -1;
+      if (q < a.ncol && !SDCEF_CHECK(cs.col >= 0 && cs.col < a.ncol, sdcef_chk::kCol)) cs.col = -1;
     }
     __syncthreads();
     if (cs.col < 0) break;
@@ -1246,7 +1287,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
     // ---- test modes -------------------------------------------------------
     if (a.mode == MODE_RESIDUAL) {
       for (int j = 0; j < kt; ++j) {
-        const int64_t gi = off + g.t0 + j;
+        const int64_t gi = cell_ix(off, g, j);
         const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
         NP[ix(j, tid, TPB)] = a.x_ne[gi];
         PP[ix(j, tid, TPB)] = a.x_phi[gi] - pref;
@@ -1256,7 +1297,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       for (int j = 0; j < kt; ++j) {
-        const int64_t gi = off + g.t0 + j;
+        const int64_t gi = cell_ix(off, g, j);
         a.o1[gi] = S.pd(PD_FE0)[ix(j, tid, TPB)];
         a.o2[gi] = S.pd(PD_FP0)[ix(j, tid, TPB)];
       }
@@ -1272,7 +1313,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       double* tn = S.pd(PD_FE1);
       double* tp = S.pd(PD_FP1);
       for (int j = 0; j < kt; ++j) {
-        const int64_t gi = off + g.t0 + j;
+        const int64_t gi = cell_ix(off, g, j);
         const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
         tn[ix(j, tid, TPB)] = a.ne_old[gi];
         tp[ix(j, tid, TPB)] = a.phi_old[gi] - pref;
@@ -1312,7 +1353,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
     if (start_differs) {
       if (a.mode == MODE_PRECOND) {
         for (int j = 0; j < kt; ++j) {
-          const int64_t gi = off + g.t0 + j;
+          const int64_t gi = cell_ix(off, g, j);
           const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
           NP[ix(j, tid, TPB)] = a.x_ne[gi];
           PP[ix(j, tid, TPB)] = a.x_phi[gi] - pref;
@@ -1333,14 +1374,14 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       KR* re = S.W(0);
       KR* rp = S.W(1);
       for (int j = 0; j < kt; ++j) {
-        const int64_t gi = off + g.t0 + j;
+        const int64_t gi = cell_ix(off, g, j);
         re[ix(j, tid, TPB)] = (KR)(a.r_e[gi] * cs.isFe);
         rp[ix(j, tid, TPB)] = (KR)(a.r_phi[gi] * cs.isFp);
       }
       __syncthreads();
       prec_apply<TPB, KR, PR, VAR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
       for (int j = 0; j < kt; ++j) {
-        const int64_t gi = off + g.t0 + j;
+        const int64_t gi = cell_ix(off, g, j);
         a.o1[gi] = (double)S.Z(0)[ix(j, tid, TPB)] * cs.sn;
         a.o2[gi] = (double)S.Z(1)[ix(j, tid, TPB)] * cs.sp;
       }
@@ -1371,7 +1412,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       if (tid == 0) cs.have_prec = 0;
       // restart from the plain start X^n (state set 0)
       for (int j = 0; j < kt; ++j) {
-        const int64_t gi = off + g.t0 + j;
+        const int64_t gi = cell_ix(off, g, j);
         S.pd(PD_N)[ix(j, tid, TPB)] = a.ne_old[gi];
         S.pd(PD_PSI)[ix(j, tid, TPB)] = a.phi_old[gi] - S.pd(PD_PREF)[ix(j, tid, TPB)];
       }
@@ -1461,6 +1502,8 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
         __syncthreads();
         int kdim = 0;
         for (int jj = 0; jj < m && its < a.p.max_krylov; ++jj) {
+          // the Arnoldi scratch below holds jj + 2 <= 34 values
+          if (!SDCEF_CHECK(jj + 2 <= 34, sdcef_chk::kHess)) { bad = true; break; }
           // z_jj = Mhat^{-1} V_jj (kept), w = Jhat z_jj
           double zz = prec_apply<TPB, KR, PR, VAR>(a, g, cs, S, S.V(jj, 0), S.V(jj, 1), S.ZK(jj, 0),
                                           S.ZK(jj, 1), sh, red, true);
@@ -1718,7 +1761,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
     }   // attempts
     // ---- outputs ----------------------------------------------------------
     for (int j = 0; j < kt; ++j) {
-      const int64_t gi = off + g.t0 + j;
+      const int64_t gi = cell_ix(off, g, j);
       const double pref = S.pd(PD_PREF)[ix(j, tid, TPB)];
       a.ne_out[gi] = S.pd(pd_n(cur))[ix(j, tid, TPB)];
       a.phi_out[gi] = pref + S.pd(pd_psi(cur))[ix(j, tid, TPB)];

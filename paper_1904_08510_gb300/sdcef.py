@@ -13,7 +13,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsdcef.so")
+# SDCEF_LIB selects another build of the library (the bounds-checking one in
+# _build_checks/ for its tests); default: the in-tree _build/libsdcef.so
+LIB_PATH = os.environ.get("SDCEF_LIB") or os.path.join(_HERE, "_build", "libsdcef.so")
 
 SUCCESS = 0
 ERR_INVALID, ERR_CUDA, ERR_CAPACITY, ERR_NOMEM = -1, -2, -3, -4
@@ -40,7 +42,8 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_mlp_targets", "sdcef_mlp_forward", "sdcef_mlp_grad", "sdcef_mlp_train_step",
            "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
            "sdcef_mlp_set_state", "sdcef_mlp_check", "sdcef_fma_peak_probe",
-           "sdcef_mlp_set_wait_polls")
+           "sdcef_mlp_set_wait_polls", "sdcef_checks_compiled", "sdcef_check_word",
+           "sdcef_mlp_check_word")
 MLP_NPARAM = 20994
 GUESS_NE, GUESS_PHI = 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -131,6 +134,12 @@ def lib():
         L.sdcef_mlp_last_launch_count.argtypes = [vp]
         L.sdcef_mlp_check.argtypes = [vp]
         L.sdcef_mlp_set_wait_polls.argtypes = [vp, C.c_int]
+        L.sdcef_checks_compiled.argtypes = []
+        L.sdcef_checks_compiled.restype = C.c_int
+        L.sdcef_check_word.argtypes = [vp, C.POINTER(C.c_uint)]
+        L.sdcef_check_word.restype = C.c_int
+        L.sdcef_mlp_check_word.argtypes = [vp, C.POINTER(C.c_uint)]
+        L.sdcef_mlp_check_word.restype = C.c_int
         L.sdcef_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
         L.sdcef_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
         for f in ("sdcef_mlp_create", "sdcef_mlp_destroy", "sdcef_mlp_set_params",
@@ -241,6 +250,13 @@ class Solver:
 
     def launches(self) -> int:
         return int(lib().sdcef_last_launch_count(self.h))
+
+    def check_word(self) -> int:
+        """sdcef_check_word: the bounds-checking build's failed-check site (0 = none);
+        synchronises and clears it."""
+        w = C.c_uint(0)
+        _check(lib().sdcef_check_word(self.h, C.byref(w)))
+        return int(w.value)
 
     def alloc_result(self, db: DeviceBatch):
         import torch
@@ -481,6 +497,12 @@ class MLP:
     def check(self):
         """Raise if a tensor-core wait of an earlier call ran out (synchronises)."""
         _check(lib().sdcef_mlp_check(self.h))
+
+    def check_word(self) -> int:
+        """sdcef_mlp_check_word (see Solver.check_word)."""
+        w = C.c_uint(0)
+        _check(lib().sdcef_mlp_check_word(self.h, C.byref(w)))
+        return int(w.value)
 
     def set_wait_polls(self, polls: int):
         """Polls of the kernels' main bounded waits (test hook; < 0 = default,

@@ -48,3 +48,11 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(S, "_lib", None)
     with pytest.raises(RuntimeError):
         S.lib()
+
+
+def test_default_build_carries_no_bounds_checks(libpath):
+    """The in-tree library is the production build; the bounds-checking one is
+    built separately (build(checks=True)) and loaded through SDCEF_LIB."""
+    assert S.lib().sdcef_checks_compiled() == 0
+    p = S.default_params()
+    assert p.eps_E == 5e-10
