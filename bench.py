@@ -614,14 +614,27 @@ def extras(args, S, b, db, solver, params, dev, parity):
         "column_solves_per_s_graph": 4 * sb.ncol / tg,
         "status_ok_last_iteration": int((sst == 0).sum()),
         "newton_mean_last_iteration": float(sout["newton_it"].float().mean().item())}
-    # the same sweep with the double-float preconditioner and the learned Newton
-    # start of the first SDC iteration: guess kernel + 4 solves in one CUDA graph
-    if os.path.exists(Lrn.WEIGHTS):
+    # the same sweep with the double-float preconditioner, without and with the
+    # learned Newton start of the first SDC iteration (the network trained on
+    # that iteration's solves, learned.py --family sweep): guess kernel + 4
+    # solves in one CUDA graph
+    wpath = Lrn.WEIGHTS_SWEEP if os.path.exists(Lrn.WEIGHTS_SWEEP) else Lrn.WEIGHTS
+    if os.path.exists(wpath):
         pdf = S.default_params(precision=S.MIXED_DF, restart_m=8,
                                threads_per_column=params.threads_per_column)
         dsolver = S.Solver(pdf, max_cols=sb.ncol, max_cells=sb.ncells, max_col_cells=1024, stream=st_)
+        dout0 = dsolver.alloc_result(sdb)
+        with torch.cuda.stream(st_):
+            g1 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g1, stream=st_):
+                dsolver.sdc_sweep(sdb, 4, work=work, out=dout0)
+            tdg, _ = _timed(lambda: g1.replay(), reps=2)
+        res["config5_sdc_sweep_mixed_df"] = {
+            "ms_per_sweep_graph": 1e3 * tdg, "column_solves_per_s_graph": 4 * sb.ncol / tdg,
+            "speedup_vs_fp64_graph": tg / tdg,
+            "status_ok_last_iteration": int((dout0["status"] == 0).sum().item())}
         mlp5 = S.MLP(sb.ncells, stream=st_)
-        mlp5.set_params(Lrn.load())
+        mlp5.set_params(Lrn.load(wpath))
         g_ne = torch.empty(sb.ncells, dtype=torch.float64, device=dev)
         g_ph = torch.empty_like(g_ne)
         gdb = sdb.with_guess(g_ne, g_ph)
@@ -640,6 +653,7 @@ def extras(args, S, b, db, solver, params, dev, parity):
         en = _colerr(sb, dout["ne"].cpu().numpy(), sout["ne"].cpu().numpy())[okc]
         ep = _colerr(sb, dout["phi"].cpu().numpy(), sout["phi"].cpu().numpy())[okc]
         res["config5_sdc_sweep_mixed_df_learned"] = {
+            "weights": os.path.basename(wpath),
             "ms_per_sweep_eager": 1e3 * tme, "ms_per_sweep_graph": 1e3 * tmg,
             "column_solves_per_s_graph": 4 * sb.ncol / tmg, "speedup_vs_fp64_graph": tg / tmg,
             "status_ok_last_iteration": int((dout["status"] == 0).sum().item()),
@@ -648,6 +662,11 @@ def extras(args, S, b, db, solver, params, dev, parity):
             "err_vs_fp64_sweep_phi": {"max": float(ep.max()), "median": float(np.median(ep))}}
         mlp5.close()
         dsolver.close()
+        # the first SDC iteration alone (the one the learned start applies to):
+        # Newton / GMRES iterations and time with and without it, FP64
+        res["config5_first_iteration_learned"] = {
+            "weights": os.path.basename(wpath), "columns": sb.ncol, "cells_per_column": 1024,
+            **Lrn.evaluate_sweep(Lrn.load(wpath), sb.ncol, 5_000_000, n_cells=1024, device=dev)}
     ssolver.close()
     res["multigrid_block_solver"] = mg_study(S, dev)
     res["current_iv_sweep"] = iv_sweep(S, dev)

@@ -17,11 +17,12 @@ import time
 import numpy as np
 
 from . import sdcef as S
-from .workload import make_batch
+from .workload import make_batch, sdc_batch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "data", "mlp_weights.npz")                 # single-flame family
 WEIGHTS_RAGGED = os.path.join(HERE, "data", "mlp_weights_ragged.npz")   # ragged (bench) family
+WEIGHTS_SWEEP = os.path.join(HERE, "data", "mlp_weights_sweep.npz")     # first SDC iteration
 
 
 def init_params(seed=0):
@@ -42,7 +43,12 @@ def generate(ncol: int, seed: int, *, kind="single", n_cells=256, n_range=None, 
     """Solve ncol seeded columns of profile family `kind` on the GPU; return
     (features bf16 [cells,32], targets f32 [cells,2]) device tensors and the
     number of converged solves. For kind="ragged" the cell counts follow the
-    family's own draw unless n_range is given."""
+    family's own draw unless n_range is given. kind="sweep": the first SDC
+    iteration of the MISDC electric sweep (Algorithm 1) on workload.sdc_batch
+    columns of n_cells cells at the ion-CFL step: the features are those of X^n
+    with the ion densities n^n (what the guess sees before the sweep), the
+    target is the root of the implicit solve with the provisional ions of the
+    first iteration."""
     import torch
     Xs, Ts, stats = [], [], []
     mlp = S.MLP(1, )
@@ -50,13 +56,20 @@ def generate(ncol: int, seed: int, *, kind="single", n_cells=256, n_range=None, 
         n = min(chunk, ncol - c0)
         if kind == "ragged":
             b = make_batch("ragged", n, seed + c0, n_range=n_range)
+        elif kind == "sweep":
+            b = sdc_batch(n, seed + c0, n_cells=n_cells)
         else:
             b = make_batch("single", n, seed + c0, n_cells=None if n_range else n_cells,
                            n_range=n_range)
         db = S.DeviceBatch.from_host(b, device)
         solver = S.Solver(S.default_params(eps_F=eps_F), max_cols=n, max_cells=b.ncells,
                           max_col_cells=int(b.lengths().max()))
-        out = solver.solve(db)
+        if kind == "sweep":
+            ions = solver.ion_provisional(db, db.tensors["phi_old"])
+            out = solver.solve(S.DeviceBatch(db.ncol, db.ncells, dict(db.tensors, n_ion=ions),
+                                             db.valence))
+        else:
+            out = solver.solve(db)
         X = mlp.features(db)
         T = mlp.targets(db, out["ne"], out["phi"])
         ok = out["status"] == S.STATUS_OK
@@ -161,6 +174,47 @@ def evaluate(params, ncol: int, seed: int, *, kind="single", n_range=(512, 2048)
     return b, res
 
 
+def evaluate_sweep(params, ncol: int, seed: int, *, n_cells=1024, device="cuda:0", reps=3,
+                   components=1):
+    """The MISDC electric sweep's first SDC iteration (workload.sdc_batch columns)
+    with and without the learned start: Newton and GMRES iterations and time of
+    that iteration (guess kernel included)."""
+    import torch
+    b = sdc_batch(ncol, seed, n_cells=n_cells)
+    db = S.DeviceBatch.from_host(b, device)
+    solver = S.Solver(S.default_params(), max_cols=b.ncol, max_cells=b.ncells,
+                      max_col_cells=n_cells)
+    work = solver.sweep_work(db)
+    out = solver.alloc_result(db)
+    mlp = S.MLP(b.ncells)
+    mlp.set_params(params)
+    ne_g = torch.empty(b.ncells, dtype=torch.float64, device=device)
+    ph_g = torch.empty_like(ne_g)
+    gdb = db.with_guess(ne_g, ph_g)
+    res = {}
+    for name in ("plain", "learned"):
+        def one():
+            if name == "learned":
+                mlp.guess(db, ne_g, ph_g, components=components)
+                return solver.sdc_sweep(gdb, 1, work=work, out=out)
+            return solver.sdc_sweep(db, 1, work=work, out=out)
+        one()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            o = one()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        res[name] = dict(ms=float(np.median(times)), status_ok=int((o["status"] == 0).sum().item()),
+                         newton_mean=float(o["newton_it"].float().mean().item()),
+                         krylov_mean=float(o["krylov_it"].float().mean().item()))
+    solver.close()
+    mlp.close()
+    return res
+
+
 def save(params, path=WEIGHTS, meta=None):
     os.makedirs(os.path.dirname(path), exist_ok=True)
     np.savez(path, params=np.asarray(params, dtype=np.float32), meta=np.array(repr(meta or {})))
@@ -184,13 +238,17 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--train-cells", default="256",
                     help="cells per training column: an integer, or lo:hi for U{lo..hi}")
-    ap.add_argument("--family", default="single", choices=["single", "ragged"],
-                    help="profile family of the training and evaluation columns")
+    ap.add_argument("--family", default="single", choices=["single", "ragged", "sweep"],
+                    help="profile family of the training and evaluation columns (sweep: the "
+                         "first SDC iteration of the electric sweep, 1024-cell columns)")
     args = ap.parse_args()
     t0 = time.perf_counter()
     if args.family == "ragged":
         # training seeds 3e6 + i, disjoint from the evaluation / benchmark seeds 2e6 + i
         X, T, nok = generate(args.ncol, 3_000_000, kind="ragged")
+    elif args.family == "sweep":
+        # training seeds 6e6 + i, disjoint from the sweep benchmark's 5e6 + i
+        X, T, nok = generate(args.ncol, 6_000_000, kind="sweep", n_cells=1024)
     elif ":" in args.train_cells:
         lo, hi = (int(v) for v in args.train_cells.split(":"))
         X, T, nok = generate(args.ncol, 1_000_000, n_range=(lo, hi))
@@ -202,14 +260,17 @@ def main():
     params = mlp.get_params()
     save(params, args.out, dict(ncol=args.ncol, steps=args.steps, batch=args.batch, lr=args.lr,
                                 train_cells=args.train_cells, family=args.family))
-    b, res = evaluate(params, args.eval_ncol, 2_000_000, kind=args.family,
-                      n_range=None if args.family == "ragged" else (512, 2048),
-                      variants=(("learned_ne", 1), ("learned_ne_phi", 3)))
+    if args.family == "sweep":
+        ev = {f"components_{c}": evaluate_sweep(params, args.eval_ncol, 5_000_000, components=c)
+              for c in (1, 3)}
+    else:
+        b, res = evaluate(params, args.eval_ncol, 2_000_000, kind=args.family,
+                          n_range=None if args.family == "ragged" else (512, 2048),
+                          variants=(("learned_ne", 1), ("learned_ne_phi", 3)))
+        ev = {k: {kk: vv for kk, vv in v.items() if kk not in ("ne", "phi")} for k, v in res.items()}
     summary = dict(family=args.family, train_columns=args.ncol, train_cells=args.train_cells,
                    train_samples=int(X.shape[0]), converged=nok,
-                   data_s=t1 - t0, train_s=t2 - t1, loss=hist,
-                   eval={k: {kk: vv for kk, vv in v.items() if kk not in ("ne", "phi")}
-                         for k, v in res.items()})
+                   data_s=t1 - t0, train_s=t2 - t1, loss=hist, eval=ev)
     print(json.dumps(summary))
 
 
