@@ -851,7 +851,8 @@ def mg_study(S, dev):
         dbq = S.DeviceBatch.from_host(bq, dev)
         row = {"dv_V": dv, "dt_s": dtq}
         for name, pc in (("recast", S.PREC_RECAST), ("none", S.PREC_NONE)):
-            p = S.default_params(precond=pc, restart_m=32, max_newton=1, max_krylov=cap)
+            p = S.default_params(precond=pc, restart_m=32, max_newton=1, max_krylov=cap,
+                                 stall_ratio=0.0)
             sv = S.Solver(p, max_cols=bq.ncol, max_cells=bq.ncells, max_col_cells=512)
             o = sv.solve(dbq)
             torch.cuda.synchronize()

@@ -158,6 +158,13 @@ typedef struct {
                          takes up to 2 more Newton steps (full steps, accepted on
                          sufficient decrease or if the residual test still holds;
                          a rejected one ends the solve at X). Default 5e-10.    */
+  double stall_ratio; /* a GMRES restart cycle whose recomputed linear residual
+                         exceeds stall_ratio times the residual at its start
+                         ends the GMRES solve of that Newton step with the
+                         correction reached (stagnation, e.g. at the attainable
+                         accuracy of FP32 Krylov vectors); 0 = never. In [0, 1);
+                         default 0.9. The paper states no GMRES cap; this and
+                         max_krylov are safeguards of this implementation.     */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -198,7 +205,8 @@ typedef struct {
                          (SDCEF_PREC_MG; 0 otherwise)                         */
 } sdcef_result;
 
-/* Fill p with the defaults: eps_F 1e-10, eps_X 0, eps_E 5e-10, gamma 1e-4 (Table 1),
+/* Fill p with the defaults: eps_F 1e-10, eps_X 0, eps_E 5e-10, stall_ratio 0.9,
+ * gamma 1e-4 (Table 1),
  * mobility 0.4 (Sec. 2.2), ls_alpha 1e-4, eps_r 1, restart 8, 50 Newton
  * steps, 200 Krylov iterations per step, 20 halvings, FP64, exact Schur
  * preconditioner, absorbing electrodes, automatic threads per column, and a

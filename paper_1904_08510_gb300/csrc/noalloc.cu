@@ -129,6 +129,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.p.eps_F = p->eps_F;
   a.p.eps_X = p->eps_X;
   a.p.eps_E = p->eps_E;
+  a.p.stall = p->stall_ratio > 0.0 ? p->stall_ratio : 2.0;
   a.p.gamma = p->gamma;
   a.p.mu = p->mobility;
   a.p.ls_alpha = p->ls_alpha;

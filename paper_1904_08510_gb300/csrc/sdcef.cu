@@ -73,9 +73,10 @@ int check_params(const sdcef_params* p, int m_cap) {
   if (!p) return set_err(SDCEF_ERR_INVALID, "params is NULL");
   if (!(p->eps_F > 0.0) || !(p->gamma > 0.0 && p->gamma < 1.0) || !(p->mobility > 0.0) ||
       !(p->ls_alpha >= 0.0 && p->ls_alpha < 1.0) || !(p->eps_r > 0.0) || !(p->eps_X >= 0.0) ||
-      !(p->eps_E >= 0.0) || !std::isfinite(p->eps_E))
+      !(p->eps_E >= 0.0) || !std::isfinite(p->eps_E) ||
+      !(p->stall_ratio >= 0.0 && p->stall_ratio < 1.0))
     return set_err(SDCEF_ERR_INVALID,
-                   "params: eps_F, eps_X, eps_E, gamma, mobility, ls_alpha, eps_r out of range");
+                   "params: eps_F, eps_X, eps_E, stall_ratio, gamma, mobility, ls_alpha, eps_r out of range");
   if (p->restart_m < 1 || p->restart_m > SDCEF_MAX_RESTART || (m_cap > 0 && p->restart_m > m_cap))
     return set_err(SDCEF_ERR_INVALID, "params: restart_m out of range");
   if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0 || p->guess_newton_cap < 0 ||
@@ -167,6 +168,7 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb) {
   a.p.eps_F = p.eps_F;
   a.p.eps_X = p.eps_X;
   a.p.eps_E = p.eps_E;
+  a.p.stall = p.stall_ratio > 0.0 ? p.stall_ratio : 2.0;
   a.p.gamma = p.gamma;
   a.p.mu = p.mobility;
   a.p.ls_alpha = p.ls_alpha;
@@ -242,6 +244,7 @@ void sdcef_default_params(sdcef_params* p) {
   p->eps_F = 1e-10;
   p->eps_X = 0.0;
   p->eps_E = 5e-10;
+  p->stall_ratio = 0.9;
   p->gamma = 1e-4;
   p->mobility = 0.4;
   p->ls_alpha = 1e-4;

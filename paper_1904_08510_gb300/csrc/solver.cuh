@@ -35,6 +35,7 @@ constexpr int kMaxPolish = 2;
 struct DevParams {
   double eps_F, eps_X, gamma, mu, ls_alpha, kap;   // kap = eps0 eps_r / e
   double eps_E;         // error test at the stop (relative, per field); 0 = off
+  double stall;         // GMRES restart-cycle stagnation ratio (> 1: never)
   int m, max_newton, max_krylov, max_ls, bc, precond;
   int guess_cap;   // Newton steps from a supplied start before restarting from X^n (0 = never)
   double guess_ratio;   // reject a supplied start with ||Fhat|| > ratio ||Fhat(X^n)|| (0 = never)
@@ -1495,6 +1496,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       }
       __syncthreads();
       while (!converged && its < a.p.max_krylov) {
+        const double beta_cycle = beta;   // residual at the start of this cycle
         if (tid == 0) {
           for (int q = 0; q <= m; ++q) gv[q] = 0.0;
           gv[0] = beta;
@@ -1691,6 +1693,12 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
         block_reduce<TPB>(&rs, 1, false, red);
         beta = sqrt(rs);
         if (beta <= gam * beta0) { converged = true; break; }
+        // stagnation: a full cycle that leaves more than stall_ratio of its
+        // starting true residual ends the solve with the correction reached
+        // (the line search still judges the step); GMRES(m) stalls this way
+        // near the attainable accuracy of FP32 Krylov vectors on
+        // ill-conditioned columns
+        if (beta > a.p.stall * beta_cycle) break;
         const double ib = 1.0 / beta;
         for (int j = 0; j < kt; ++j) {
           S.V(0, 0)[ix(j, tid, TPB)] = (KR)((double)S.W(0)[ix(j, tid, TPB)] * ib);

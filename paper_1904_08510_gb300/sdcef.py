@@ -60,7 +60,8 @@ class Params(C.Structure):
                 ("guess_newton_cap", C.c_int), ("guess_reject_ratio", C.c_double),
                 ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
                 ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int), ("ion_scheme", C.c_int),
-                ("transport", C.c_int), ("gas_molar_mass", C.c_double), ("eps_E", C.c_double)]
+                ("transport", C.c_int), ("gas_molar_mass", C.c_double), ("eps_E", C.c_double),
+                ("stall_ratio", C.c_double)]
 
 
 class BatchC(C.Structure):
