@@ -478,14 +478,22 @@ __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, in
       Plast = Pn;
       Qlast = Qn;
       F.stm(FI::Q, m - 1, tid, Qn);
-      for (int j = m - 2; j >= 0; --j) {
-        const Mat<NB, R> Cp = F.ldm(FI::CP, j, tid);
-        const Mat<NB, R> Pj = mprod<-1, true, false, false>(F.ldm(FI::P, j, tid), Cp, Pn);
-        const Mat<NB, R> Qj = mprod<-1, false, false, false>(Cp, Cp, Qn);
-        F.stm(FI::P, j, tid, Pj);
-        F.stm(FI::Q, j, tid, Qj);
-        Pn = Pj;
-        Qn = Qj;
+      if (m >= 2) {
+        // row j - 1's operands are loaded before row j is computed and stored
+        Mat<NB, R> Cn = F.ldm(FI::CP, m - 2, tid), Pgn = F.ldm(FI::P, m - 2, tid);
+        for (int j = m - 2; j >= 0; --j) {
+          const Mat<NB, R> Cp = Cn, Pg = Pgn;
+          if (j >= 1) {
+            Cn = F.ldm(FI::CP, j - 1, tid);
+            Pgn = F.ldm(FI::P, j - 1, tid);
+          }
+          const Mat<NB, R> Pj = mprod<-1, true, false, false>(Pg, Cp, Pn);
+          const Mat<NB, R> Qj = mprod<-1, false, false, false>(Cp, Cp, Qn);
+          F.stm(FI::P, j, tid, Pj);
+          F.stm(FI::Q, j, tid, Qj);
+          Pn = Pj;
+          Qn = Qj;
+        }
       }
       Pfirst = Pn;
       Qfirst = Qn;
@@ -569,23 +577,45 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* 
       if (nrm2) acc = fma((double)o, (double)o, acc);
     }
   };
+  // Each sweep loads the operands of its next row before it computes and
+  // stores the current one (rows differ, so no store can change a loaded value),
+  // so that the loads of one row overlap the arithmetic of the previous row.
   Vec<NB, R> yfirst = vzero<NB, R>(), ylast = vzero<NB, R>(), rsep = vzero<NB, R>();
   if (kt > 0) {
     rsep = ldin(m);
     Vec<NB, R> g = vzero<NB, R>();
-    for (int j = 0; j < m; ++j) {
-      Vec<NB, R> gn = mvec(F.ldm(FI::WINV, j, tid), ldin(j));
-      if (j > 0) gn = vprod<-1, true, false>(gn, F.ldm(FI::G, j, tid), g);
-      sts(j, gn);
-      g = gn;
-    }
     if (m > 0) {
+      Mat<NB, R> Wn = F.ldm(FI::WINV, 0, tid), Gn = mzero<NB, R>();
+      Vec<NB, R> rn = ldin(0);
+      for (int j = 0; j < m; ++j) {
+        const Mat<NB, R> Wc = Wn, Gc = Gn;
+        const Vec<NB, R> rc = rn;
+        if (j + 1 < m) {
+          Wn = F.ldm(FI::WINV, j + 1, tid);
+          Gn = F.ldm(FI::G, j + 1, tid);
+          rn = ldin(j + 1);
+        }
+        Vec<NB, R> gn = mvec(Wc, rc);
+        if (j > 0) gn = vprod<-1, true, false>(gn, Gc, g);
+        sts(j, gn);
+        g = gn;
+      }
       Vec<NB, R> yn = g;
       ylast = yn;
-      for (int j = m - 2; j >= 0; --j) {
-        const Vec<NB, R> yj = vprod<-1, true, false>(lds(j), F.ldm(FI::CP, j, tid), yn);
-        sts(j, yj);
-        yn = yj;
+      if (m >= 2) {
+        Mat<NB, R> Cn = F.ldm(FI::CP, m - 2, tid);
+        Vec<NB, R> sn = lds(m - 2);
+        for (int j = m - 2; j >= 0; --j) {
+          const Mat<NB, R> Cc = Cn;
+          const Vec<NB, R> sc = sn;
+          if (j >= 1) {
+            Cn = F.ldm(FI::CP, j - 1, tid);
+            sn = lds(j - 1);
+          }
+          const Vec<NB, R> yj = vprod<-1, true, false>(sc, Cc, yn);
+          sts(j, yj);
+          yn = yj;
+        }
       }
       yfirst = yn;
     }
@@ -613,10 +643,21 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* 
 #pragma unroll
       for (int k = 0; k < NB; ++k) xl.a[k] = sr[k * tact + tid - 1];
     }
-    for (int j = 0; j < m; ++j) {
-      Vec<NB, R> xj = vprod<1, true, false>(lds(j), F.ldm(FI::P, j, tid), xl);
-      xj = vprod<1, true, false>(xj, F.ldm(FI::Q, j, tid), xsep);
-      stout(j, xj);
+    if (m > 0) {
+      Mat<NB, R> Pn = F.ldm(FI::P, 0, tid), Qn = F.ldm(FI::Q, 0, tid);
+      Vec<NB, R> sn = lds(0);
+      for (int j = 0; j < m; ++j) {
+        const Mat<NB, R> Pc = Pn, Qc = Qn;
+        const Vec<NB, R> sc = sn;
+        if (j + 1 < m) {
+          Pn = F.ldm(FI::P, j + 1, tid);
+          Qn = F.ldm(FI::Q, j + 1, tid);
+          sn = lds(j + 1);
+        }
+        Vec<NB, R> xj = vprod<1, true, false>(sc, Pc, xl);
+        xj = vprod<1, true, false>(xj, Qc, xsep);
+        stout(j, xj);
+      }
     }
     stout(m, xsep);
   }

@@ -95,8 +95,8 @@ enum {
   // at dpsi/dx = 0, so that Pe = PD_PE0 + PD_MUHD (psi_{i+1} - psi_i) is one FMA
   // (the transport-table kernel keeps its E/N index factor in PD_MUHD instead)
   PD_N = 0, PD_PSI, PD_FE0, PD_FP0, PD_FE1, PD_FP1, PD_FEX, PD_FPHI, PD_DH, PD_MUHD, PD_PE0, PD_PREF,
-  // 3 planes per set: r dGam/dn_i, r dGam/dn_{i+1} and r dGam/dpsi_{i+1}
-  // (= -r dGam/dpsi_i) of face i+1/2, unscaled
+  // 3 planes per set: r dGam/dn_i, r dGam/dn_{i+1} (times s_n / s_Fe) and
+  // r dGam/dpsi_{i+1} (= -r dGam/dpsi_i, times s_psi / s_Fe) of face i+1/2
   PD_FACE0,
   PD_FACE1 = PD_FACE0 + 3,
   // state (n, psi) of set 1; set 0 is PD_N, PD_PSI. The state of set s is the
@@ -442,6 +442,9 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
   const int tid = g.tid, kt = g.kt, N = g.N;
   const double ih = cs.inv_h, dt = cs.dt, g0 = cs.g0, mu = a.p.mu, kap = a.p.kap;
   const double r = dt * ih;
+  // the face derivatives are stored in the Jacobian's scaled units: the n
+  // derivatives times r s_n / s_Fe, the psi derivative times r s_psi / s_Fe
+  const double ra = r * cs.r_a, rbi = r * cs.r_b * ih, rbm = rbi * mu;
   // face differences dd: psi_{i+1} - psi_i (RAW, 1/h folded into PD_MUHD and the
   // Poisson constant), or the gradient dpsi/dx for the transport-table kernel
   constexpr bool RAW = VAR != kVarTable;
@@ -545,20 +548,20 @@ __device__ __noinline__ void residual(const KArgs& a, const Geo& g, ColShared& c
         gam = dh * (Bm * n_i - Bp * n_n);
         if (out_mode == OUT_F) {
           const double dBp = pos ? db : -1.0 - db, dBm = pos ? -1.0 - db : db;
-          // r dGam/dn_i, r dGam/dn_{i+1}, r dGam/dpsi_i, r dGam/dpsi_{i+1} (unscaled)
-          double dg_n0 = dh * Bm, dg_n1 = -dh * Bp;
+          // scaled r dGam/dn_i, r dGam/dn_{i+1} and r dGam/dpsi_{i+1}
+          const double rdh = ra * dh;
           double dg_p1;
           if constexpr (VAR == kVarTable) {
             // dGam/dG = (D'/h)(B(-Pe) n_i - B(Pe) n_{i+1}) + (D/h)(-B'(-Pe) n_i - B'(Pe) n_{i+1}) dPe/dG
             const double dGam = dD_dG * ih * (Bm * n_i - Bp * n_n) +
                                 dh * (-dBm * n_i - dBp * n_n) * dPe_dG;
-            dg_p1 = ih * dGam;
+            dg_p1 = rbi * dGam;
           } else {
-            dg_p1 = muf * ih * (-dBm * n_i - dBp * n_n);
+            dg_p1 = rbm * (-dBm * n_i - dBp * n_n);
           }
-          face[0 * a.PL + ix(j, tid, TPB)] = r * dg_n0;
-          face[1 * a.PL + ix(j, tid, TPB)] = r * dg_n1;
-          face[2 * a.PL + ix(j, tid, TPB)] = r * dg_p1;
+          face[0 * a.PL + ix(j, tid, TPB)] = rdh * Bm;
+          face[1 * a.PL + ix(j, tid, TPB)] = -rdh * Bp;
+          face[2 * a.PL + ix(j, tid, TPB)] = dg_p1;
         }
       } else {
         // right electrode face: G_R - g0 = (-9 psi_{N-1} + psi_{N-2}) / (3h)
@@ -664,10 +667,9 @@ struct RowJ {
 template <int TPB, typename KR, typename PR, int VAR>
 __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColShared& cs,
                                         const Slot<TPB, KR, PR>& S, int fs, int j,
-                                        const double* lf /*left face's 3 derivatives*/, double n_i,
+                                        const double* lf /*left face's 3 derivatives*/,
+                                        const double* rf /*right face's 3 derivatives*/,
                                         double n_0, double n_last) {
-  (void)n_i;
-  const double* face = S.pd(PD_FACE0 + 3 * fs);
   const int i = g.t0 + j, N = g.N;
   const double ih = cs.inv_h, r = cs.dt * ih, mu = a.p.mu;
   RowJ R;
@@ -678,9 +680,9 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   R.C = -cs.r_c;
   // right face (row i carries -r Gam_{i+1/2})
   if (i < N - 1) {
-    R.Ad -= face[0 * a.PL + ix(j, g.tid, TPB)] * sa;
-    R.Au -= face[1 * a.PL + ix(j, g.tid, TPB)] * sa;
-    const double t = face[2 * a.PL + ix(j, g.tid, TPB)] * sb;   // dGam/dpsi_i = -dGam/dpsi_{i+1}
+    R.Ad -= rf[0];
+    R.Au -= rf[1];
+    const double t = rf[2];   // dGam/dpsi_i = -dGam/dpsi_{i+1}
     R.Bd += t;
     R.Bu -= t;
   } else {
@@ -695,9 +697,9 @@ __device__ __forceinline__ RowJ jac_row(const KArgs& a, const Geo& g, const ColS
   }
   // left face (row i carries +r Gam_{i-1/2})
   if (i > 0) {
-    R.As += lf[0] * sa;
-    R.Ad += lf[1] * sa;
-    const double t = lf[2] * sb;
+    R.As += lf[0];
+    R.Ad += lf[1];
+    const double t = lf[2];
     R.Bs -= t;
     R.Bd += t;
   } else {
@@ -750,22 +752,35 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
   const double n0 = (g.t0 == 0 && kt > 0) ? NP[ix(0, tid, TPB)] : 0.0;
   const double nlast = (kt > 0 && g.t0 + kt == g.N) ? NP[ix(kt - 1, tid, TPB)] : 0.0;
   const double* face = S.pd(PD_FACE0 + 3 * fs);
-  auto lface = [&](int j, double* lf) {
+  // the left and right faces' derivatives of row j; rows come in order, so the
+  // right face of row j - 1 is carried over as the left face of row j
+  double cf[3] = {0.0, 0.0, 0.0};
+  int cj = -2;
+  auto faces = [&](int j, double* lf, double* rf) {
     if (j == 0) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) lf[q] = lf0[q];
+    } else if (j == cj + 1) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) lf[q] = cf[q];
     } else {
 #pragma unroll
       for (int q = 0; q < 3; ++q) lf[q] = face[q * a.PL + ix(j - 1, tid, TPB)];
     }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      rf[q] = face[q * a.PL + ix(j, tid, TPB)];
+      cf[q] = rf[q];
+    }
+    cj = j;
   };
   if (a.p.precond == SDCEF_PREC_EXACT) {
     Planes<2, PR, TPB> F{S.f, S.PL};
     Scal<2, PR, TPB> Sc{S.s};
     auto rowf = [&](int j, Mat<2, PR>& M, Mat<2, PR>& D, Mat<2, PR>& U) {
-      double lf[3];
-      lface(j, lf);
-      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      double lf[3], rf[3];
+      faces(j, lf, rf);
+      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, rf, n0, nlast);
       M.a[0] = conv<PR>(R.As); M.a[1] = conv<PR>(R.Bs); M.a[2] = PR(0); M.a[3] = conv<PR>(R.Ls);
       D.a[0] = conv<PR>(R.Ad); D.a[1] = conv<PR>(R.Bd); D.a[2] = conv<PR>(R.C); D.a[3] = conv<PR>(R.Ld);
       U.a[0] = conv<PR>(R.Au); U.a[1] = conv<PR>(R.Bu); U.a[2] = PR(0); U.a[3] = conv<PR>(R.Lu);
@@ -780,9 +795,9 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     Scal<1, PR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
     const double rho = cs.r_rho;
     auto row1 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
-      double lf[3];
-      lface(j, lf);
-      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      double lf[3], rf[3];
+      faces(j, lf, rf);
+      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, rf, n0, nlast);
       M.a[0] = conv<PR>(R.As); D.a[0] = conv<PR>(R.Ad); U.a[0] = conv<PR>(R.Au);
       Bpl[0 * S.PL + ix(j, tid, TPB)] = conv<PR>(R.Bs);
       Bpl[1 * S.PL + ix(j, tid, TPB)] = conv<PR>(R.Bd);
@@ -790,9 +805,9 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
     };
     part_factor<1, PR, TPB, false>(F1, S1, kt, tid, g.tact, row1, sh, bad);
     auto row2 = [&](int j, Mat<1, PR>& M, Mat<1, PR>& D, Mat<1, PR>& U) {
-      double lf[3];
-      lface(j, lf);
-      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+      double lf[3], rf[3];
+      faces(j, lf, rf);
+      RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, rf, n0, nlast);
       M.a[0] = conv<PR>(R.Ls - rho * R.Bs);
       D.a[0] = conv<PR>(R.Ld - rho * R.Bd);
       U.a[0] = conv<PR>(R.Lu - rho * R.Bu);
@@ -806,9 +821,9 @@ __device__ __noinline__ void prec_factor(const KArgs& a, const Geo& g, ColShared
       PR* Bpl = S.f + 10 * S.PL;
       const double rho = cs.r_rho;
       for (int j = 0; j < kt; ++j) {
-        double lf[3];
-        lface(j, lf);
-        RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, 0.0, n0, nlast);
+        double lf[3], rf[3];
+        faces(j, lf, rf);
+        RowJ R = jac_row<TPB, KR, PR, VAR>(a, g, cs, S, fs, j, lf, rf, n0, nlast);
         const int i = g.t0 + j;
         M.op[0].sub[i] = R.As;
         M.op[0].dia[i] = R.Ad;
@@ -1309,7 +1324,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
     // scaling: typical values at the plain start X^n (Eq. newton_sc, Algorithm 2
     // first line), whatever the Newton start is
     const bool start_differs = (a.mode == MODE_PRECOND) || a.ne_g || a.phi_g;
-    if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; }
+    if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; cs.r_a = 1.0; cs.r_b = 1.0; }
     if (start_differs) {
       double* tn = S.pd(PD_FE1);
       double* tp = S.pd(PD_FP1);
@@ -1364,6 +1379,16 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);
       ++res_evals;
+    } else {
+      // the face derivatives at X^n were stored before the scales were known
+      __syncthreads();
+      const double fa = cs.r_a, fb = cs.r_b;
+      double* f0 = S.pd(PD_FACE0);
+      for (int j = 0; j < kt; ++j) {
+        f0[0 * a.PL + ix(j, tid, TPB)] *= fa;
+        f0[1 * a.PL + ix(j, tid, TPB)] *= fa;
+        f0[2 * a.PL + ix(j, tid, TPB)] *= fb;
+      }
     }
     __syncthreads();
     int cur = 0;   // current F / face set
