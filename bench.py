@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tpc", type=int, default=0, help="threads per column (0 = library default)")
+    ap.add_argument("--krylov-on-chip", type=int, default=-1, choices=[-1, 0, 1],
+                    help="Krylov vectors in the solver kernel's spare shared memory (1), all in "
+                         "the workspace slot (0), or picked by the autotuner (-1)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the unbatched / learned / SDC-sweep comparison legs")
     ap.add_argument("--sdc-ncol", type=int, default=16384)
@@ -131,13 +134,14 @@ def kernel_digest():
     """Digest of the solver kernel sources (ties an ncu capture to the code it measured)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("solver.cuh", "blockalg.cuh", "dfloat.cuh", "mg.cuh", "expm1_table.cuh", "kern_inst.cu"):
+    for f in ("solver.cuh", "blockalg.cuh", "checks.cuh", "dfloat.cuh", "mg.cuh", "expm1_table.cuh",
+              "kern_inst.cu"):
         with open(os.path.join(ROOT, "paper_1904_08510_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(ncells, tpc):
+def ncu_traffic(ncells, tpc, on_chip):
     """DRAM bytes per launch of the solver kernel from the committed ncu summary, if it
     was taken on the current kernel sources and launch shape (else None), scaled to
     this batch's cells."""
@@ -147,7 +151,8 @@ def ncu_traffic(ncells, tpc):
             c = json.load(f)
     except Exception:
         return None
-    if c.get("kernel_digest") != kernel_digest() or int(c.get("threads_per_column", -1)) != tpc:
+    if (c.get("kernel_digest") != kernel_digest() or int(c.get("threads_per_column", -1)) != tpc
+            or int(c.get("krylov_on_chip", 0)) != on_chip):
         return None
     return float(c["dram_bytes_per_launch"]) * ncells / float(c["cells"])
 
@@ -305,13 +310,18 @@ def main():
     prec = {"fp64": S.FP64, "mixed": S.MIXED, "mixed_df": S.MIXED_DF}[args.precision]
     pc = S.PREC_EXACT if args.precond == "exact" else S.PREC_RECAST
     params = S.default_params(precision=prec, precond=pc, threads_per_column=args.tpc,
-                              restart_m=30 if pc == S.PREC_RECAST else (16 if prec == S.MIXED else 8))
+                              restart_m=30 if pc == S.PREC_RECAST else (16 if prec == S.MIXED else 8),
+                              krylov_on_chip=max(args.krylov_on_chip, 0))
     solver = S.Solver(params, max_cols=b.ncol, max_cells=b.ncells,
                       max_col_cells=int(lengths.max()))
     db = S.DeviceBatch.from_host(b, dev)
     tuned = None
     if args.tpc == 0:
         tuned = solver.autotune(db, reps=1)   # before warm-up and timing
+    tuned_oc = None
+    if args.krylov_on_chip < 0:
+        tuned_oc = solver.autotune_on_chip(db, reps=2)
+    on_chip = int(solver.params.krylov_on_chip)
     out = solver.alloc_result(db)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -388,7 +398,8 @@ def main():
     achieved_tf = flops / t_launch / 1e12
     hbm_gbs = sbytes / t_launch / 1e9
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(b.ncells, tuned[0] if tuned else args.tpc),
+                "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(b.ncells, tuned[0] if tuned else args.tpc,
+                                                       on_chip),
                 "kernel": "jfnk_kernel (persistent solver)",
                 "peak_source": "measured in this run: sdcef_fma_peak_probe, FP64 FMA chains on every SM, "
                                "best of 5 CUDA-event timings",
@@ -413,6 +424,8 @@ def main():
             "config": {"workload": WORKLOAD, "ncol": b.ncol, "cells": int(b.ncells),
                        "precision": args.precision, "precond": args.precond, "eps_F": 1e-10,
                        "threads_per_column": (tuned[0] if tuned else args.tpc),
+                       "krylov_on_chip": on_chip,
+                       "krylov_on_chip_ms": (tuned_oc[1] if tuned_oc else None),
                        "autotune_ms": (tuned[1] if tuned else None),
                        "l2": "flushed between steps (256 MB write); inputs 5 x 8 B x cells > L2",
                        "parallelism": f"replicas x{ws}"},

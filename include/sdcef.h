@@ -165,6 +165,16 @@ typedef struct {
                          accuracy of FP32 Krylov vectors); 0 = never. In [0, 1);
                          default 0.9. The paper states no GMRES cap; this and
                          max_krylov are safeguards of this implementation.     */
+  int krylov_on_chip; /* 1: the Krylov vectors of a column (Algorithm 2's
+                         GMRES: w, v_0, z_0 = P^-1 v_0, the error test's
+                         correction, the correction sum, then v_i, z_i in order)
+                         that fit in the shared memory the solver kernel leaves
+                         unused at its occupancy live there for the whole solve
+                         of that column, the others in its workspace slot;
+                         0 (default): all in the slot. Results are bit-identical
+                         either way; the shared memory is taken from the L1
+                         cache, so which is faster depends on the batch:
+                         sdcef_autotune_on_chip measures it.                    */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -206,6 +216,7 @@ typedef struct {
 } sdcef_result;
 
 /* Fill p with the defaults: eps_F 1e-10, eps_X 0, eps_E 5e-10, stall_ratio 0.9,
+ * Krylov vectors in the slot (krylov_on_chip 0),
  * gamma 1e-4 (Table 1),
  * mobility 0.4 (Sec. 2.2), ls_alpha 1e-4, eps_r 1, restart 8, 50 Newton
  * steps, 200 Krylov iterations per step, 20 halvings, FP64, exact Schur
@@ -315,6 +326,14 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const do
  * paper (the paper solves one 1D problem at a time). */
 int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef_result* out, int reps,
                    int* tpb_out, float* ms_out);
+
+/* Autotuner for the Krylov storage: times sdcef_solve_batch on this batch with
+ * krylov_on_chip 0 and 1 at the context's threads per column (one warm-up and
+ * `reps` timed solves each), keeps the faster in the context's parameters and
+ * returns it in *on_chip_out (ms_out, if not NULL, receives the 2 mean times,
+ * slot first). Synchronises the stream; call it before any stream capture. */
+int sdcef_autotune_on_chip(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef_result* out,
+                           int reps, int* on_chip_out, float* ms_out);
 
 /* Provisional charged species of an SDC iteration: the electric-drift part of
  * the provisional rho Y~ that Algorithm 1 hands to the electric solve (the

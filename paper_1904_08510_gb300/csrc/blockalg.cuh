@@ -146,18 +146,35 @@ __device__ __forceinline__ bool bad_pivot(float det, float inv) {
   const int d = __float_as_int(det), v = __float_as_int(inv);
   return (d & 0x7FFFFFFF) == 0 || (v & 0x7F800000) == 0x7F800000;
 }
+// Reciprocal of a pivot. FP64: the hardware's approximate reciprocal y
+// (relative error ~1e-6) refined by one Newton-Raphson step that keeps the
+// second-order term, y (1 + e + e^2) with e = 1 - x y (the series
+// 1/x = y / (1 - e) cut after e^2), so the error is the seed's cubed, below
+// rounding. A zero, subnormal or non-finite x gives a non-finite result, which
+// the pivot check flags. Other types divide.
+template <typename R>
+__device__ __forceinline__ R recip(R x) {
+  return R(1) / x;
+}
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
 // Inverse; *bad is set when the pivot is zero or the inverse not finite.
 template <typename R>
 __device__ __forceinline__ Mat<1, R> minv(const Mat<1, R>& x, bool* bad) {
   Mat<1, R> r;
-  r.a[0] = R(1) / x.a[0];
+  r.a[0] = recip(x.a[0]);
   if (bad_pivot(x.a[0], r.a[0])) *bad = true;
   return r;
 }
 template <typename R>
 __device__ __forceinline__ Mat<2, R> minv(const Mat<2, R>& x, bool* bad) {
   const R det = fma(x.a[0], x.a[3], -(x.a[1] * x.a[2]));
-  const R id = R(1) / det;
+  const R id = recip(det);
   Mat<2, R> r;
   r.a[0] = x.a[3] * id;
   r.a[1] = -x.a[1] * id;

@@ -149,8 +149,10 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.mode = MODE_SOLVE;
 
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t smem = smem_bytes_prec(prec, tpb, m);
+  size_t smem = smem_bytes_prec(prec, tpb, m);
   const int per_sm = occupancy_prec(prec, tpb, smem, p->precond, SDCEF_TRANSPORT_CONSTANT);
+  if (p->krylov_on_chip)
+    smem = krylov_arena(prec, tpb, smem, per_sm, p->precond, SDCEF_TRANSPORT_CONSTANT, &a);
   const int grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, a.ncol, nslots});
   // the queue counter must start at zero; everything else a call reads it writes first
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);

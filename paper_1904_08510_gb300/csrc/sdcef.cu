@@ -77,6 +77,8 @@ int check_params(const sdcef_params* p, int m_cap) {
       !(p->stall_ratio >= 0.0 && p->stall_ratio < 1.0))
     return set_err(SDCEF_ERR_INVALID,
                    "params: eps_F, eps_X, eps_E, stall_ratio, gamma, mobility, ls_alpha, eps_r out of range");
+  if (p->krylov_on_chip != 0 && p->krylov_on_chip != 1)
+    return set_err(SDCEF_ERR_INVALID, "params: krylov_on_chip must be 0 or 1");
   if (p->restart_m < 1 || p->restart_m > SDCEF_MAX_RESTART || (m_cap > 0 && p->restart_m > m_cap))
     return set_err(SDCEF_ERR_INVALID, "params: restart_m out of range");
   if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0 || p->guess_newton_cap < 0 ||
@@ -204,10 +206,12 @@ int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
   // restart length used by the iteration (planes are laid out for m_cap)
   const int m_run = ctx->p.restart_m;
   a.p.m = m_run;
-  const size_t smem = smem_bytes_prec(prec, tpb, m_run);
+  size_t smem = smem_bytes_prec(prec, tpb, m_run);
   // slot layout must use the same m as the device code: recompute with m_run
   a.slot_bytes = slot_bytes_prec(prec, a.PL, m_run, tpb, ctx->p.precond);
   int per_sm = occupancy_prec(prec, tpb, smem, ctx->p.precond, ctx->p.transport);
+  if (ctx->p.krylov_on_chip)
+    smem = krylov_arena(prec, tpb, smem, per_sm, ctx->p.precond, ctx->p.transport, &a);
   int64_t slots_fit = (int64_t)(ctx->ws_bytes / a.slot_bytes);
   int grid = (int)std::min<int64_t>({(int64_t)per_sm * ctx->sms, a.ncol, slots_fit});
   if (grid < 1) return set_err(SDCEF_ERR_CAPACITY, "workspace too small for one column slot");
@@ -245,6 +249,7 @@ void sdcef_default_params(sdcef_params* p) {
   p->eps_X = 0.0;
   p->eps_E = 5e-10;
   p->stall_ratio = 0.9;
+  p->krylov_on_chip = 0;
   p->gamma = 1e-4;
   p->mobility = 0.4;
   p->ls_alpha = 1e-4;
@@ -448,6 +453,42 @@ int sdcef_autotune(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out
   if (rc) return rc;
   ctx->p.threads_per_column = best;
   if (tpb_out) *tpb_out = best;
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_autotune_on_chip(sdcef_ctx* ctx, const sdcef_batch* b, const sdcef_result* out,
+                           int reps, int* on_chip_out, float* ms_out) {
+  Range range_("sdcef_autotune_on_chip");
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  if (reps < 1 || reps > 100) return set_err(SDCEF_ERR_INVALID, "autotune: reps out of range");
+  const sdcef_params saved = ctx->p;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  float t[2] = {0.0f, 0.0f};
+  int rc = SDCEF_SUCCESS;
+  for (int oc = 0; oc < 2 && rc == SDCEF_SUCCESS; ++oc) {
+    ctx->p.krylov_on_chip = oc;
+    rc = sdcef_solve_batch(ctx, b, out);   // warm-up
+    for (int r = 0; r < reps && rc == SDCEF_SUCCESS; ++r) {
+      e = cudaEventRecord(e0, ctx->stream);
+      if (e == cudaSuccess) rc = sdcef_solve_batch(ctx, b, out);
+      if (e == cudaSuccess && rc == SDCEF_SUCCESS) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess && rc == SDCEF_SUCCESS) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess && rc == SDCEF_SUCCESS) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) rc = set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+      t[oc] += ms / reps;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->p = saved;
+  if (rc) return rc;
+  ctx->p.krylov_on_chip = t[1] < t[0] ? 1 : 0;
+  if (on_chip_out) *on_chip_out = ctx->p.krylov_on_chip;
+  if (ms_out) { ms_out[0] = t[0]; ms_out[1] = t[1]; }
   return SDCEF_SUCCESS;
 }
 

@@ -6,6 +6,7 @@
 // translation unit per (threads per column, Krylov precision).
 #pragma once
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -80,6 +81,9 @@ struct KArgs {
   const int* order;
   DevParams p;
   int mode;
+  // on-chip Krylov planes: byte offset and size of their region in the dynamic
+  // shared memory (size 0: every Krylov plane is in the slot)
+  unsigned arena_off, arena_bytes;
   // test modes: state X, residual-space vector r, outputs
   const double *x_ne, *x_phi, *r_e, *r_phi;
   double *o1, *o2;
@@ -197,6 +201,37 @@ inline int occupancy_prec(int precision, int tpb, size_t smem, int precond, int 
   if (precision == SDCEF_MIXED_DF) return occupancy_tpb<double, dfloat>(tpb, smem);
   return occupancy_tpb<double, double>(tpb, smem);
 }
+// Region for on-chip Krylov planes: the shared memory an SM has left when
+// per_sm CTAs of the kernel (registers decide per_sm) each hold smem bytes,
+// split evenly between them, so that the region does not lower the occupancy.
+// Sets a->arena_off / arena_bytes and returns the launch's dynamic shared
+// memory (smem when no region fits).
+inline size_t krylov_arena(int precision, int tpb, size_t smem, int per_sm, int precond,
+                           int transport, KArgs* a) {
+  a->arena_off = 0;
+  a->arena_bytes = 0;
+  int dev = 0, per_sm_bytes = 0, reserved = 0, optin = 0;
+  if (per_sm < 1 || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return smem;
+  const size_t off = (smem + 255) & ~(size_t)255;
+  long long avail = std::min<long long>((long long)per_sm_bytes / per_sm - reserved, optin);
+  avail = (avail - (long long)off) & ~255LL;
+  // the kernel's static shared memory also counts: step down until the
+  // occupancy holds
+  for (; avail >= 4096; avail -= 256) {
+    if (occupancy_prec(precision, tpb, off + (size_t)avail, precond, transport) >= per_sm) {
+      a->arena_off = (unsigned)off;
+      a->arena_bytes = (unsigned)avail;
+      return off + (size_t)avail;
+    }
+  }
+  return smem;
+}
 #endif  // SDCEF_KERNEL_TU
 cudaError_t launch_order(const int64_t* col_off, int64_t ncol, int nbins, int shift, int* order,
                          cudaStream_t st);
@@ -278,6 +313,18 @@ __device__ __forceinline__ double expm1_pos(double a) {
 }
 
 // DERIV = false skips B'(a): the finite-difference JVP needs fluxes only.
+// 1/E for E >= 1e-3: the hardware's approximate reciprocal y (relative error
+// ~1e-6) refined by one Newton-Raphson step that keeps the second-order term,
+// y (1 + e + e^2) with e = 1 - E y (the series 1/E = y / (1 - e) cut after e^2),
+// so the result's error is the seed's cubed, below rounding. E = +inf (a >= 709)
+// gives 0, as 1/E does.
+__device__ __forceinline__ double rcp_pos(double E) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(E));
+  const double e = fma(-E, y, 1.0);
+  const double r = fma(y, fma(e, e, e), y);
+  return dbits(E) >= 0x7FF0000000000000LL ? 0.0 : r;
+}
 template <bool DERIV>
 __device__ __forceinline__ void bern_pos(double a, double* b, double* db) {
   if (dbits(a) < kBits1em3) {
@@ -286,7 +333,7 @@ __device__ __forceinline__ void bern_pos(double a, double* b, double* db) {
     if (DERIV) *db = -0.5 + a * (1.0 / 6.0) - a * a2 * (1.0 / 180.0);
   } else {
     double E = expm1_pos(a);
-    double iE = 1.0 / E;
+    double iE = rcp_pos(E);
     *b = a * iE;
     if (DERIV) *db = (1.0 - a - *b) * iE;
   }
@@ -325,6 +372,11 @@ struct Geo {
   int tid, kt, t0, N, K, tact;
 };
 
+// Component pointers of the running column's Krylov pairs, by slot position
+// (set per column by krylov_table).
+constexpr int kMaxKPairs = 2 * SDCEF_MAX_RESTART + 5;
+static __shared__ void* s_kptr[2 * kMaxKPairs];
+
 template <int TPB, typename KR, typename PR>
 struct Slot {
   double* d;    // FP64 planes
@@ -337,14 +389,19 @@ struct Slot {
     if (!SDCEF_CHECK(i >= 0 && i < PD_COUNT, sdcef_chk::kPlane)) i = 0;
     return d + (size_t)i * PL;
   }
+  // Krylov pairs by slot position: V_0..V_m, W, Z, XH, T, ZK_0..ZK_{m-1}; the
+  // component pointers come from the column's table (on chip or in the slot)
+  __device__ KR* kp(int pos, int comp) const {
+    return static_cast<KR*>(s_kptr[2 * pos + comp]);
+  }
   __device__ KR* V(int i, int comp) const {
     if (!SDCEF_CHECK(i >= 0 && i <= m && (comp == 0 || comp == 1), sdcef_chk::kKrylov)) i = comp = 0;
-    return k + (size_t)(2 * i + comp) * PL;
+    return kp(i, comp);
   }
-  __device__ KR* W(int comp) const { return k + (size_t)(2 * (m + 1) + cmp(comp)) * PL; }
-  __device__ KR* Z(int comp) const { return k + (size_t)(2 * (m + 1) + 2 + cmp(comp)) * PL; }
-  __device__ KR* XH(int comp) const { return k + (size_t)(2 * (m + 1) + 4 + cmp(comp)) * PL; }
-  __device__ KR* T(int comp) const { return k + (size_t)(2 * (m + 1) + 6 + cmp(comp)) * PL; }
+  __device__ KR* W(int comp) const { return kp(m + 1, cmp(comp)); }
+  __device__ KR* Z(int comp) const { return kp(m + 2, cmp(comp)); }
+  __device__ KR* XH(int comp) const { return kp(m + 3, cmp(comp)); }
+  __device__ KR* T(int comp) const { return kp(m + 4, cmp(comp)); }
   // a component number, 0 (n) or 1 (psi)
   __device__ static int cmp(int comp) {
     if (!SDCEF_CHECK(comp == 0 || comp == 1, sdcef_chk::kKrylov)) comp = 0;
@@ -353,7 +410,7 @@ struct Slot {
   // Mhat^{-1} V_i of the current GMRES cycle (flexible-GMRES storage)
   __device__ KR* ZK(int i, int comp) const {
     if (!SDCEF_CHECK(i >= 0 && i < m && (comp == 0 || comp == 1), sdcef_chk::kZk)) i = comp = 0;
-    return k + (size_t)(2 * (m + 1) + 8 + 2 * i + comp) * PL;
+    return kp(m + 5 + i, comp);
   }
 };
 
@@ -1041,6 +1098,34 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
 // Column set-up: inputs into the slot, scaling, initial state.
 // Returns false if the column is rejected (BAD_INPUT).
 // --------------------------------------------------------------------------
+// Krylov pointer table of the column. Pairs go on chip in the order W, V_0,
+// ZK_0, Z, XH, V_1, ZK_1, ..., V_{m-1}, ZK_{m-1}, V_m, T (the vectors of a
+// one-iteration GMRES solve and of the error test first) while they fit the
+// region, a plane there holding the column's K * TPB elements; the others stay
+// at their slot planes. All threads call it after column_setup.
+template <int TPB, typename KR, typename PR>
+__device__ void krylov_table(const KArgs& a, const Geo& g, const Slot<TPB, KR, PR>& S,
+                             unsigned char* smem_raw) {
+  const int m = S.m, npair = 2 * m + 5;
+  const size_t PLs = (size_t)g.K * TPB;
+  const int nks = (int)min((size_t)npair, (size_t)a.arena_bytes / (2 * PLs * sizeof(KR)));
+  KR* ks = reinterpret_cast<KR*>(smem_raw + a.arena_off);
+  for (int e = g.tid; e < 2 * npair; e += TPB) {
+    const int pos = e >> 1, comp = e & 1;
+    int r;   // on-chip rank of slot position pos
+    if (pos == 0) r = 1;                        // V_0
+    else if (pos <= m) r = 2 * pos + 3;         // V_1 .. V_m
+    else if (pos == m + 1) r = 0;               // W
+    else if (pos == m + 2) r = 3;               // Z
+    else if (pos == m + 3) r = 4;               // XH
+    else if (pos == m + 4) r = 2 * m + 4;       // T
+    else r = pos == m + 5 ? 2 : 2 * (pos - m - 5) + 4;   // ZK_i
+    s_kptr[e] = r < nks ? static_cast<void*>(ks + (size_t)(2 * r + comp) * PLs)
+                        : static_cast<void*>(S.k + (size_t)(2 * pos + comp) * S.PL);
+  }
+  __syncthreads();
+}
+
 template <int TPB, typename KR, typename PR, int VAR>
 __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs, const Slot<TPB, KR, PR>& S,
                              double* halo, double* red) {
@@ -1293,6 +1378,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       __syncthreads();
       continue;
     }
+    krylov_table<TPB, KR, PR>(a, g, S, smem_raw);
     const int kt = g.kt;
     const int64_t off = cs.off;
     double* NP = S.pd(PD_N);
@@ -1308,7 +1394,7 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
         NP[ix(j, tid, TPB)] = a.x_ne[gi];
         PP[ix(j, tid, TPB)] = a.x_phi[gi] - pref;
       }
-      if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; }
+      if (tid == 0) { cs.sFe = 1.0; cs.sFp = 1.0; cs.r_a = 1.0; cs.r_b = 1.0; }
       __syncthreads();
       residual<TPB, KR, PR, VAR>(a, g, cs, S, NP, PP, nullptr, nullptr, 0, 0, OUT_F, S.pd(PD_FE0),
                         S.pd(PD_FP0), 0, nullptr, nullptr, nullptr, nullptr, 0, halo, red, norms);

@@ -43,7 +43,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
            "sdcef_mlp_set_state", "sdcef_mlp_check", "sdcef_fma_peak_probe",
            "sdcef_mlp_set_wait_polls", "sdcef_checks_compiled", "sdcef_check_word",
-           "sdcef_mlp_check_word")
+           "sdcef_mlp_check_word", "sdcef_autotune_on_chip")
 MLP_NPARAM = 20994
 GUESS_NE, GUESS_PHI = 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -61,7 +61,7 @@ class Params(C.Structure):
                 ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
                 ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int), ("ion_scheme", C.c_int),
                 ("transport", C.c_int), ("gas_molar_mass", C.c_double), ("eps_E", C.c_double),
-                ("stall_ratio", C.c_double)]
+                ("stall_ratio", C.c_double), ("krylov_on_chip", C.c_int)]
 
 
 class BatchC(C.Structure):
@@ -118,6 +118,8 @@ def lib():
         L.sdcef_ion_update_batch.restype = C.c_int
         L.sdcef_autotune.argtypes = [vp, B, R, C.c_int, C.POINTER(C.c_int), vp]
         L.sdcef_autotune.restype = C.c_int
+        L.sdcef_autotune_on_chip.argtypes = [vp, B, R, C.c_int, C.POINTER(C.c_int), vp]
+        L.sdcef_autotune_on_chip.restype = C.c_int
         L.sdcef_sdc_sweep.restype = C.c_int
         L.sdcef_fma_peak_probe.argtypes = [C.c_int, C.c_int, vp, C.POINTER(C.c_double)]
         L.sdcef_fma_peak_probe.restype = C.c_int
@@ -321,6 +323,19 @@ class Solver:
                                     C.cast(ms, C.c_void_p)))
         self.params.threads_per_column = tpb.value
         return tpb.value, {t: float(m) for t, m in zip((32, 64, 128, 256), ms)}
+
+    def autotune_on_chip(self, db: DeviceBatch, reps: int = 2):
+        """sdcef_autotune_on_chip: Krylov vectors in shared memory or in the slot,
+        whichever solves this batch faster; returns (choice, {0: ms, 1: ms})."""
+        out = self.alloc_result(db)
+        bs = db.cstruct()
+        rs = ResultC(_ptr(out["ne"]), _ptr(out["phi"]), None, None, None, None, None)
+        oc = C.c_int(0)
+        ms = (C.c_float * 2)()
+        _check(lib().sdcef_autotune_on_chip(self.h, C.byref(bs), C.byref(rs), int(reps),
+                                            C.byref(oc), C.cast(ms, C.c_void_p)))
+        self.params.krylov_on_chip = oc.value
+        return oc.value, {0: float(ms[0]), 1: float(ms[1])}
 
     def ion_update(self, db: DeviceBatch, phi, kappa_ion: float = 4e-3):
         import torch
