@@ -151,10 +151,12 @@ def ncu_traffic(ncells, tpc, on_chip):
             c = json.load(f)
     except Exception:
         return None
-    if (c.get("kernel_digest") != kernel_digest() or int(c.get("threads_per_column", -1)) != tpc
-            or int(c.get("krylov_on_chip", 0)) != on_chip):
+    if c.get("kernel_digest") != kernel_digest() or int(c.get("threads_per_column", -1)) != tpc:
         return None
-    return float(c["dram_bytes_per_launch"]) * ncells / float(c["cells"])
+    cap = c.get("captures", {}).get(str(int(on_chip)))
+    if not cap:
+        return None
+    return float(cap["dram_bytes_per_launch"]) * ncells / float(c["cells"])
 
 
 def algorithmic_model(lengths, newton, krylov, res_evals, precond, kr_bytes):
