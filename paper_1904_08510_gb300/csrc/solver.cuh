@@ -1301,13 +1301,21 @@ __device__ __forceinline__ bool error_test(const KArgs& a, const Geo& g, ColShar
   }
   __syncthreads();
   prec_apply<TPB, KR, PR, VAR>(a, g, cs, S, re, rp, S.Z(0), S.Z(1), sh, red, false);
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  // maxima of |.| on the bit patterns (integer pipe): non-negative doubles
+  // order as their patterns; a NaN counts as 0, as fmax would ignore it
+  auto absb = [](double x) {
+    const long long b = dbits(x) & 0x7FFFFFFFFFFFFFFFLL;
+    return b > 0x7FF0000000000000LL ? 0LL : b;
+  };
+  long long m[4] = {0, 0, 0, 0};
   for (int j = 0; j < kt; ++j) {
-    v[0] = fmax(v[0], fabs((double)S.Z(0)[ix(j, tid, TPB)]));
-    v[1] = fmax(v[1], fabs((double)S.Z(1)[ix(j, tid, TPB)]));
-    v[2] = fmax(v[2], fabs(NP[ix(j, tid, TPB)]));
-    v[3] = fmax(v[3], fabs(PP[ix(j, tid, TPB)] + PR_[ix(j, tid, TPB)]));
+    m[0] = max(m[0], absb((double)S.Z(0)[ix(j, tid, TPB)]));
+    m[1] = max(m[1], absb((double)S.Z(1)[ix(j, tid, TPB)]));
+    m[2] = max(m[2], absb(NP[ix(j, tid, TPB)]));
+    m[3] = max(m[3], absb(PP[ix(j, tid, TPB)] + PR_[ix(j, tid, TPB)]));
   }
+  double v[4];
+  for (int q = 0; q < 4; ++q) v[q] = __longlong_as_double(m[q]);
   block_reduce<TPB>(v, 4, true, red);
   const double en = v[0] * cs.sn, ep = v[1] * cs.sp;
   if (!(en <= 1.79e308) || !(ep <= 1.79e308)) return true;
