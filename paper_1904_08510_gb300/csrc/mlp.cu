@@ -1,9 +1,9 @@
 // Learned Newton initial guess: feature extraction; training on the tcgen05
-// tensor cores (BF16 operands, FP32 accumulators in TMEM): the three-layer
-// forward fused in one kernel, the MSE loss, backpropagation through a BF16
-// GEMM with fused SiLU-derivative and split-K weight-gradient epilogues, and
-// Adam; and the fused inference kernel (mlp_tc.cuh) that assembles the
-// guess. The network maps the
+// tensor cores (BF16 operands, FP32 accumulators in TMEM): forward, MSE loss
+// and backpropagation fused in one persistent kernel whose weight gradients
+// accumulate in TMEM, and Adam over the kernel's per-CTA partial gradients;
+// the inference forward; and the fused inference kernel (mlp_tc.cuh) that
+// assembles the guess. The network maps the
 // 5-cell stencil features of a cell to the scaled Newton increment
 // ((n* - n^n)/s_n, (phi* - phi^n)/s_phi); the JFNK of Algorithm 2 then starts
 // from X^n + S_X y instead of X^n and still decides convergence.
@@ -11,8 +11,6 @@
 // Shapes: 32 (25 features, zero-padded) -> 128 -> 128 -> 2, SiLU activations.
 // Parameters (FP32 master copy, flat): W1[128][32], b1[128], W2[128][128],
 // b2[128], W3[2][128], b3[2]; BF16 copies of W1, W2, W3 feed the tensor cores.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -150,81 +148,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // --------------------------------------------------------------------------
-// Training GEMMs on the tcgen05 tensor cores: C[m][n] = sum_k A(m,k) B(k,n)
-// with A(m,k) = transA ? A[k*lda+m] : A[m*lda+k] and
-// B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n] (BF16), FP32 accumulators in TMEM.
-// Epilogues: kEpiAccumulate adds C with atomics (split-K weight gradients);
-// kEpiSiluGrad writes dZ = acc * G (BF16; G = silu'(Z) in BF16, stored by the
-// forward) and adds the column sums of
-// dZ to colsum (the forward runs fused, fwd_tc_kernel below).
-//
-// A CTA of 256 threads computes 128 rows of C (row m0 + r in TMEM lane r) by
-// all N <= 128 columns (the MMA's N is N rounded up to 16) over its share of
-// K, in slabs of up to 64 k, two of them in flight while the tensor core
-// multiplies the current one. Each operand is staged in the K-major
-// core-matrix layout of mlp_tc.cuh, zero outside the matrix: a K-contiguous
-// operand by 16-byte asynchronous copies (cp.async) that land in core-matrix
-// order (two buffers); an operand whose rows are contiguous into one of two
-// row-major slots, which ldmatrix.trans then transposes into the operand
-// buffer (one, or two when the other operand is K-contiguous) after the
-// previous slab's MMAs have read it. The row-major slots of operands with 128
-// values per row are filled by TMA (two 64 x 64 boxes with 128-byte swizzle,
-// completing on a per-slot mbarrier), narrower ones by cp.async. The
-// epilogue runs on all 8 warps: two per 32-lane quadrant of TMEM, each on
-// half of the columns.
-// Every wait on an mbarrier is bounded; a CTA whose MMAs do not complete sets
-// the error word and writes NaN instead of its results.
+// Helpers of the tensor-core training kernels: operand staging in the K-major
+// core-matrix layout of mlp_tc.cuh (16-byte asynchronous copies) and the
+// column sums of an epilogue's values over a warp.
 // --------------------------------------------------------------------------
-struct GemmArgs {
-  int M, N, K;
-  const __nv_bfloat16* A;
-  int lda, transA;
-  const __nv_bfloat16* B;
-  int ldb, transB;
-  float* C;
-  int ldc;
-  int epi;
-  __nv_bfloat16* H;
-  int ldh;
-  const __nv_bfloat16* Gin;
-  int ldgin;
-  float* colsum;
-};
-
-// the kernel's form: operand X(r, k) = X[r * sr + k * sk] with sr == 1 or sk == 1
-struct TcGemm {
-  int M, N, K, kchunk, epi;
-  const uint16_t* A;
-  int64_t sam, sak;
-  const uint16_t* B;
-  int64_t sbn, sbk;
-  float* C;
-  int64_t scm, scn;
-  __nv_bfloat16* H;
-  int64_t ldh;
-  const __nv_bfloat16* Gin;
-  int64_t ldgin;
-  float* colsum;
-  int* err;
-  int tmaA, tmaB;   // the operand's slabs come by TMA (tensor maps of the launch)
-  int polls;        // polls of the main bounded waits (the clean-up waits use the default)
-  unsigned* chk;    // check word of the bounds-checking build (may be null)
-};
-
-constexpr int kEpiAccumulate = 0, kEpiSiluGrad = 2;         // GemmArgs::epi
-constexpr int kGemmThreads = 256;                           // two warps per TMEM lane quadrant
-constexpr int kSlabK = 64;                                  // k per slab
-constexpr uint32_t kOpBytes = 128 * kSlabK * 2;             // one operand slab
-__host__ __device__ constexpr uint32_t nat_pitch(int R) { return (uint32_t)(2 * R + 16); }
-__host__ __device__ constexpr uint32_t nat_bytes(int R) { return kSlabK * nat_pitch(R); }
-constexpr uint32_t kGemmSmemMax = 4 * kOpBytes + 4 * nat_bytes(128) + 1024;   // + alignment slack
-constexpr int kHPitch = 80;                                 // epilogue staging pitch (BF16 rows)
-constexpr uint32_t kStageBytes = 2 * 32 * kHPitch;
-static_assert(kGemmThreads / 32 * kStageBytes <= 4 * kOpBytes, "staging tiles fit the operand buffers");
+constexpr int kGemmThreads = 256;   // two warps per TMEM lane quadrant
 
 __device__ __forceinline__ uint32_t pack_u16(uint16_t lo, uint16_t hi) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
+
 
 // 16-byte asynchronous global -> shared copy; an invalid chunk is zero-filled
 // without reading global memory (the source then only names a valid address)
@@ -233,6 +166,8 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
                "r"(valid ? 16 : 0)
                : "memory");
 }
+
+
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -265,87 +200,6 @@ __device__ __forceinline__ void stage_k(unsigned char* S, const uint16_t* X, int
   }
 }
 
-// row-contiguous operand X(r, k) = X[r + k sk]: copy the slab row-major into
-// nat (row k at k * pitch, 16 bytes = 8 consecutive r per item)
-__device__ __forceinline__ void stage_nat(unsigned char* nat, uint32_t pitch, const uint16_t* X,
-                                          int64_t sk, bool vec, int64_t rbase, int64_t rmax,
-                                          int R, int k0, int kend, int ks, int tid) {
-  const int rc = R >> 3, items = ks * rc;
-#pragma unroll 4
-  for (int e = tid; e < items; e += kGemmThreads) {
-    const int k = e / rc, c = e - k * rc;
-    const int64_t gr = rbase + c * 8, gk = k0 + k;
-    unsigned char* d = nat + (size_t)k * pitch + c * 16;
-    const bool none = gr >= rmax || gk >= kend;
-    if (none || (vec && gr + 8 <= rmax)) {
-      cp16(d, none ? (const void*)X : (const void*)(X + gk * sk + gr), !none);
-    } else {
-      uint16_t u[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) u[j] = (gr + j < rmax) ? X[gk * sk + gr + j] : 0;
-      *reinterpret_cast<uint4*>(d) = make_uint4(pack_u16(u[0], u[1]), pack_u16(u[2], u[3]),
-                                                pack_u16(u[4], u[5]), pack_u16(u[6], u[7]));
-    }
-  }
-}
-
-// TMA: a 64 x 64 BF16 box (64 k rows of 128 bytes) of a row-major operand
-// with 128-byte swizzle: the 16-byte chunk j of row k lands at chunk j ^ (k % 8)
-// of the row (the box's base is 1024-byte aligned). Completion on mbarrier mb.
-constexpr uint32_t kTmaBoxBytes = 64 * 128;
-__device__ __forceinline__ void tma_box(unsigned char* dst, const CUtensorMap* map, int x, int y,
-                                        uint32_t mb) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(tc::saddr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb)
-      : "memory");
-}
-
-// two swizzled boxes (r 0..63 and 64..127 of 64 k rows) -> K-major core matrices,
-// as nat_to_k: core matrix i = c kc + kk holds rows 8c.. of k 8kk..
-__device__ __forceinline__ void nat_sw_to_k(unsigned char* S, const unsigned char* nat, int kc,
-                                            int warp, int lane) {
-  const int mats = 16 * kc;
-  for (int g = warp; g * 4 < mats; g += kGemmThreads / 32) {
-    const int i = g * 4 + (lane >> 3);
-    const int c = i / kc, kk = i - c * kc;
-    const int k = kk * 8 + (lane & 7);
-    const uint32_t src =
-        tc::saddr(nat + (c >> 3) * kTmaBoxBytes + k * 128 + (((c & 7) ^ (k & 7)) << 4));
-    uint32_t r0, r1, r2, r3;
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(src));
-    uint32_t* d = reinterpret_cast<uint32_t*>(S + (size_t)g * 4 * 128) + lane;
-    d[0] = r0;
-    d[32] = r1;
-    d[64] = r2;
-    d[96] = r3;
-  }
-}
-
-// nat (k rows, r contiguous) -> K-major core matrices. Core matrix i = c kc + kk
-// holds rows 8c.. of k 8kk..; ldmatrix.trans hands lane l the pair
-// (k = 8kk + 2 (l%4) + {0,1}, r = 8c + l/4), which sits at byte 4 l of it.
-__device__ __forceinline__ void nat_to_k(unsigned char* S, const unsigned char* nat,
-                                         uint32_t pitch, int R, int kc, int warp, int lane) {
-  const int mats = (R >> 3) * kc;   // a multiple of 4 (R >= 16, kc >= 2)
-  for (int g = warp; g * 4 < mats; g += kGemmThreads / 32) {
-    const int i = g * 4 + (lane >> 3);   // the matrix whose row address this lane gives
-    const int c = i / kc, kk = i - c * kc;
-    const uint32_t src = tc::saddr(nat + (size_t)(kk * 8 + (lane & 7)) * pitch + c * 16);
-    uint32_t r0, r1, r2, r3;
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(src));
-    uint32_t* d = reinterpret_cast<uint32_t*>(S + (size_t)g * 4 * 128) + lane;
-    d[0] = r0;
-    d[32] = r1;
-    d[64] = r2;
-    d[96] = r3;
-  }
-}
 
 // lane l ends with the sum over the warp of v[l]
 __device__ __forceinline__ float warp_colsum32(float* v, int lane) {
@@ -362,298 +216,24 @@ __device__ __forceinline__ float warp_colsum32(float* v, int lane) {
   return v[0];
 }
 
-// EPI: the epilogue; AMN / BMN: operand A / B has contiguous rows
-// (staged through the row-major copy and ldmatrix.trans) rather than contiguous k
-template <int EPI, bool AMN, bool BMN>
-__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(TcGemm g,
-                                                               const __grid_constant__ CUtensorMap tmA,
-                                                               const __grid_constant__ CUtensorMap tmB) {
-  extern __shared__ __align__(1024) unsigned char gsm_raw[];
-  // 1024-byte aligned base (the swizzled TMA boxes need it; the launch adds 1 KB)
-  unsigned char* gsm = gsm_raw + ((1024u - (tc::saddr(gsm_raw) & 1023u)) & 1023u);
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ __align__(8) uint64_t lbar[2];   // TMA slabs, one per row-major slot
-  __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * 128;
-  const int kbeg = blockIdx.y * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
-  // the CTA's rows and its share of K inside the matrices (before any
-  // barrier, tensor-memory allocation or copy)
-  if (!SDCEF_CHECK_W(g.chk, m0 < g.M && kbeg >= 0 && kbeg < kend && kend <= g.K &&
-                                g.N >= 1 && g.N <= 128,
-                     sdcef_chk::kMlpRow))
-    return;
-  const int Np = (g.N + 15) & ~15;
-  constexpr bool amn = AMN, bmn = BMN;
-  // operand buffers: two per operand, except when both operands go through the
-  // row-major copies: then the copies carry the next slab and one buffer each
-  // (written after the previous slab's MMAs have finished) suffices
-  constexpr int NB = (AMN && BMN) ? 1 : 2;
-  unsigned char* opA = gsm;
-  unsigned char* opB = gsm + NB * kOpBytes;
-  // two slots of row-major copies per such operand, so that two slabs are in
-  // flight; every slot starts on a 1024-byte boundary (17408 = 17 KB)
-  constexpr uint32_t natA_sz = amn ? nat_bytes(128) : 0;
-  const uint32_t natB_sz = bmn ? nat_bytes(Np) : 0;
-  unsigned char* natA0 = gsm + 2 * NB * kOpBytes;
-  unsigned char* natB0 = natA0 + 2 * natA_sz;
-  const bool tmaA = amn && g.tmaA, tmaB = bmn && g.tmaB;
-  auto l_bar = [&](int s) { return tc::saddr(&lbar[s & 1]); };
-  const bool vecA = ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0) && (((amn ? g.sak : g.sam) & 7) == 0);
-  const bool vecB = ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0) && (((bmn ? g.sbk : g.sbn) & 7) == 0);
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-        tc::saddr(&tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[1])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&lbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&lbar[1])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc::fence_async_smem();
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tm = tmem_base;
-  const uint32_t idesc = tc::idesc_bf16(128, Np);
-  const int nslab = (kend - kbeg + kSlabK - 1) / kSlabK;   // >= 1 (the host keeps kbeg < K)
-  constexpr int L = 2;   // slabs in flight
-  // the mbarrier that slab s's MMAs complete, and the parity of that completion
-  auto bar_of = [&](int s) { return tc::saddr(&mbar[NB == 2 ? (s & 1) : 0]); };
-  auto par_of = [&](int s) { return (uint32_t)(NB == 2 ? ((s >> 1) & 1) : (s & 1)); };
-  auto issue = [&](int s) {
-    const int b = NB == 2 ? (s & 1) : 0, k0 = kbeg + s * kSlabK;
-    const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
-    unsigned char* natA = natA0 + (s & 1) * natA_sz;
-    unsigned char* natB = natB0 + (s & 1) * natB_sz;
-    if ((tmaA || tmaB) && tid == 0) {
-      // two 64-row boxes per TMA operand (rows past the matrix arrive as zeros)
-      const uint32_t bytes = (tmaA ? 2 : 0) * kTmaBoxBytes + (tmaB ? 2 : 0) * kTmaBoxBytes;
-      const uint32_t lb = l_bar(s);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lb), "r"(bytes)
-                   : "memory");
-      if (tmaA) {
-        tma_box(natA, &tmA, (int)m0, k0, lb);
-        tma_box(natA + kTmaBoxBytes, &tmA, (int)m0 + 64, k0, lb);
-      }
-      if (tmaB) {
-        tma_box(natB, &tmB, 0, k0, lb);
-        tma_box(natB + kTmaBoxBytes, &tmB, 64, k0, lb);
-      }
-    }
-    if (!amn) stage_k(opA + b * kOpBytes, g.A, g.sam, vecA, m0, g.M, 128, k0, kend, kc, tid);
-    else if (!tmaA) stage_nat(natA, nat_pitch(128), g.A, g.sak, vecA, m0, g.M, 128, k0, kend, ks, tid);
-    if (!bmn) stage_k(opB + b * kOpBytes, g.B, g.sbn, vecB, 0, g.N, Np, k0, kend, kc, tid);
-    else if (!tmaB) stage_nat(natB, nat_pitch(Np), g.B, g.sbk, vecB, 0, g.N, Np, k0, kend, ks, tid);
-    cp_commit();
-  };
-  for (int j = 0; j < min(L, nslab); ++j) issue(j);
-  bool ok = true;
-  int last = -1;                                           // last slab whose MMAs were committed
-  for (int s = 0; s < nslab; ++s) {
-    const int b = NB == 2 ? (s & 1) : 0, k0 = kbeg + s * kSlabK;
-    const int ks = min(kSlabK, (kend - k0 + 15) & ~15), kc = ks >> 3;
-    if (L == 2 && s + 1 < nslab) cp_wait<1>();
-    else cp_wait<0>();
-    unsigned char* sA = opA + b * kOpBytes;
-    unsigned char* sB = opB + b * kOpBytes;
-    unsigned char* natA = natA0 + (s & 1) * natA_sz;
-    unsigned char* natB = natB0 + (s & 1) * natB_sz;
-    if (amn || bmn) {
-      if (tmaA || tmaB) {   // slab s's boxes: completion (s >> 1) of its slot's mbarrier
-        const bool w = tc::wait_phase(l_bar(s), (uint32_t)((s >> 1) & 1), g.polls);
-        if (__syncthreads_or(!w)) {
-          ok = false;
-          break;
-        }
-      }
-      __syncthreads();
-      if (NB == 1 && s >= 1) {   // the single buffers: slab s - 1's MMAs have read them
-        const bool w = tc::wait_phase(bar_of(s - 1), par_of(s - 1), g.polls);
-        if (__syncthreads_or(!w)) {
-          ok = false;
-          break;
-        }
-      }
-      if (tmaA) nat_sw_to_k(sA, natA, kc, warp, lane);
-      else if (amn) nat_to_k(sA, natA, nat_pitch(128), 128, kc, warp, lane);
-      if (tmaB) nat_sw_to_k(sB, natB, kc, warp, lane);
-      else if (bmn) nat_to_k(sB, natB, nat_pitch(Np), Np, kc, warp, lane);
-    }
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t aA = tc::saddr(sA), aB = tc::saddr(sB);
-      for (int kk = 0; kk < ks / 16; ++kk)
-        tc::mma(tm, tc::smem_desc(aA + kk * 256, 128, kc * 128),
-                tc::smem_desc(aB + kk * 256, 128, kc * 128), idesc, (s > 0 || kk > 0) ? 1u : 0u);
-      tc::commit(bar_of(s));
-    }
-    last = s;
-    const int nxt = s + L;
-    if (nxt < nslab) {
-      // with two buffers, buffer nxt & 1 was last read by the MMAs of slab nxt - 2
-      if (NB == 2 && nxt >= 2) {
-        const bool w = tc::wait_phase(bar_of(nxt - 2), par_of(nxt - 2), g.polls);
-        if (__syncthreads_or(!w)) {
-          ok = false;
-          break;
-        }
-      }
-      issue(nxt);
-    }
-  }
-  if (ok) {   // the last commit covers every MMA issued before it
-    const bool w = tc::wait_phase(bar_of(last), par_of(last), g.polls);
-    ok = !__syncthreads_or(!w);
-  }
-  tc::fence_after();
-  // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (row m0 + 32 (w % 4)
-  // + lane) in columns 64 (w / 4) .. 64 (w / 4) + 63 ----
-  const int quad = warp & 3, half = warp >> 2;
-  const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
-  const int64_t row = m0 + quad * 32 + lane;
-  const bool live = row < g.M;
-  // the operand buffers are free now: each warp gets two staging tiles of 32
-  // rows x 32 BF16 (pitch 80 B, at which a quarter-warp's 16-byte accesses hit
-  // distinct banks), one for G coming in and one for dZ going out
-  const int64_t rbase = m0 + quad * 32;
-  const int64_t rows_left = (int64_t)g.M - rbase;
-  const int nrows = rows_left <= 0 ? 0 : (rows_left < 32 ? (int)rows_left : 32);
-  unsigned char* gt = gsm + warp * kStageBytes;
-  unsigned char* ht = gt + 32 * kHPitch;
-  const bool tiled =
-      (g.ldh & 7) == 0 && (g.ldgin & 7) == 0 &&
-      ((reinterpret_cast<uintptr_t>(g.H) | reinterpret_cast<uintptr_t>(g.Gin)) & 15) == 0;
-  for (int c0 = half * 64; c0 < min(Np, half * 64 + 64); c0 += 32) {
-    float v[32];
-    if (ok) {
-      tc::ld32(lane_addr + c0, v);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = __int_as_float(0x7fffffff);
-    }
-    const bool full = c0 + 32 <= g.N;
-    if (EPI == kEpiAccumulate) {
-      if (live) {
-        float* Cr = g.C + row * g.scm;
-        if (full && g.scn == 1 && ((reinterpret_cast<uintptr_t>(Cr + c0) & 15) == 0)) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            atomicAdd(reinterpret_cast<float4*>(Cr + c0 + 4 * q),
-                      make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (c0 + j < g.N) atomicAdd(Cr + (c0 + j) * g.scn, v[j]);
-        }
-      }
-    } else {
-      float z[32];   // the multiplier G of this thread's row
-      if (full && tiled) {
-        // G rows in with whole-row loads (8 rows x 64 B per instruction) through the staging tile
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int e = i * 32 + lane, r = e >> 2, p = e & 3;
-          uint4 t = make_uint4(0, 0, 0, 0);
-          if (r < nrows)
-            t = __ldg(reinterpret_cast<const uint4*>(g.Gin + (rbase + r) * g.ldgin + c0 + 8 * p));
-          *reinterpret_cast<uint4*>(gt + r * kHPitch + 16 * p) = t;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint4 t = *reinterpret_cast<const uint4*>(gt + lane * kHPitch + 16 * q);
-          const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            z[8 * q + 2 * u] = __uint_as_float(w[u] << 16);
-            z[8 * q + 2 * u + 1] = __uint_as_float(w[u] & 0xffff0000u);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          z[j] = (live && c0 + j < g.N) ? __bfloat162float(g.Gin[row * g.ldgin + c0 + j]) : 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = (live && c0 + j < g.N) ? v[j] * z[j] : 0.0f;
-      if (full && tiled) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(ht + lane * kHPitch + 16 * q) =
-              make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
-                         pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int e = i * 32 + lane, r = e >> 2, p = e & 3;
-          if (r < nrows)
-            *reinterpret_cast<uint4*>(g.H + (rbase + r) * g.ldh + c0 + 8 * p) =
-                *reinterpret_cast<const uint4*>(ht + r * kHPitch + 16 * p);
-        }
-        __syncwarp();
-      } else if (live) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < g.N) g.H[row * g.ldh + c0 + j] = __float2bfloat16(v[j]);
-      }
-      const float cs = warp_colsum32(v, lane);
-      if (c0 + lane < g.N) atomicAdd(&g.colsum[c0 + lane], cs);
-    }
-  }
-  if (!ok) {
-    cp_wait<0>();
-    if (tid == 0) atomicExch(g.err, 1);
-    // boxes of issued slabs may still be landing: bounded waits
-    if (tmaA || tmaB)
-      for (int q = last + 1; q < min(nslab, last + 1 + L); ++q)
-        tc::wait_phase(l_bar(q), (uint32_t)((q >> 1) & 1));
-    // an MMA may still be in flight: one more bounded wait before TMEM is freed
-    if (last >= 0) tc::wait_phase(bar_of(last), par_of(last));
-  }
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tm));
-}
-
 // --------------------------------------------------------------------------
-// Training forward, all three layers in one launch: a CTA of 256 threads
+// Inference forward, all three layers in one launch: a CTA of 256 threads
 // takes 128 rows of X, stages X and the BF16 weights in the K-major
 // core-matrix layout (cp.async), and chains the layers on the tensor core
 // through one 128-column TMEM accumulator. After each hidden layer the 8-warp
 // epilogue (two warps per TMEM lane quadrant, each on half of the columns)
-// adds the bias, writes H = silu(Z) (BF16) to global memory (and in training
-// silu'(Z1) in BF16, the factor of the layer-1 backward product, instead of
-// Z1), and writes H into shared memory as the A operand of the next layer,
-// so H1 and H2 are not read back from global memory. The output layer
-// accumulates in TMEM columns of its own, so that in training the same
-// kernel goes on from Y to the loss against T (dY = (Y - T) / n, the loss and
-// the bias gradient of the output layer) and to the first backward product
-// dZ2 = (dY W3) * silu'(Z2), read straight from the layer-2 accumulator:
-// Z2 never goes to global memory. Every wait on the mbarrier is bounded; a
-// CTA whose MMAs do not complete sets the error word and writes NaN instead
-// of its results.
+// adds the bias and writes H = silu(Z) (BF16) into shared memory as the A
+// operand of the next layer; the output layer accumulates in TMEM columns of
+// its own and Y (FP32) is the only result written. Every wait on the mbarrier
+// is bounded; a CTA whose MMAs do not complete sets the error word and writes
+// NaN instead of its results.
 // --------------------------------------------------------------------------
 struct FwdArgs {
   int64_t n;
   const uint16_t* X;                  // [n][32] BF16
   const uint16_t *w1, *w2, *w3;       // [128][32], [128][128], [2][128] BF16
   const float* p;                     // FP32 parameters (biases)
-  __nv_bfloat16* G1;                  // [n][128] silu'(Z1) in BF16 (training)
-  __nv_bfloat16 *H1, *H2;             // [n][128] BF16
-  float* Y;                           // [n][2] FP32, nullable
-  // training (T != nullptr): the MSE loss and the first backward step
-  const float* T;                     // [n][2] FP32 targets
-  float inv_n;                        // 1 / n
-  __nv_bfloat16 *dY, *dZ2;            // [n][2], [n][128] BF16
-  float *loss, *gb2, *gb3;            // accumulated with atomics
+  float* Y;                           // [n][2] FP32
   int* err;
   int polls;                          // polls of the layer waits (clean-up: the default)
   unsigned* chk;                      // check word of the bounds-checking build (may be null)
@@ -673,9 +253,6 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ float sb[2 * kHid + kOut];
-  __shared__ float sw3[kOut][kHid];   // the BF16 W3 as FP32 (dZ2 product)
-  __shared__ float sdy[128][kOut];    // the BF16-rounded dY of the tile's rows
-  __shared__ float sred[4][3];        // per-warp loss and output-bias partials
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
   // the CTA's rows inside the batch (before any barrier or allocation)
@@ -691,8 +268,6 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
     sb[kHid + i] = a.p[kOffB2 + i];
   }
   if (tid < kOut) sb[2 * kHid + tid] = a.p[kOffB3 + tid];
-  for (int i = tid; i < kOut * kHid; i += kGemmThreads)
-    sw3[i / kHid][i % kHid] = __uint_as_float((uint32_t)a.w3[i] << 16);
   if (warp == 0) {   // columns 0..127: hidden layers; 128..143: output layer
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
         tc::saddr(&tmem_base)));
@@ -729,9 +304,8 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
     tc::fence_after();
     return !bad;
   };
-  // hidden-layer epilogue: Z = acc + bias, H = silu(Z) to global and to sH,
-  // and (training, layer 1) G = silu'(Z) for the backward pass
-  auto hidden = [&](bool ok, const float* bias, __nv_bfloat16* G, __nv_bfloat16* H) {
+  // hidden-layer epilogue: H = silu(acc + bias) into sH
+  auto hidden = [&](bool ok, const float* bias) {
 #pragma unroll 1
     for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
       float v[32];
@@ -743,24 +317,13 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
       }
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] += bias[c0 + j];
-      if (live && G) {
-        uint4* gp = reinterpret_cast<uint4*>(G + row * kHid + c0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          gp[q] = make_uint4(pack_bf16(silu_grad(v[8 * q]), silu_grad(v[8 * q + 1])),
-                             pack_bf16(silu_grad(v[8 * q + 2]), silu_grad(v[8 * q + 3])),
-                             pack_bf16(silu_grad(v[8 * q + 4]), silu_grad(v[8 * q + 5])),
-                             pack_bf16(silu_grad(v[8 * q + 6]), silu_grad(v[8 * q + 7])));
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 hq = make_uint4(pack_bf16(silu_fast(v[8 * q]), silu_fast(v[8 * q + 1])),
-                                    pack_bf16(silu_fast(v[8 * q + 2]), silu_fast(v[8 * q + 3])),
-                                    pack_bf16(silu_fast(v[8 * q + 4]), silu_fast(v[8 * q + 5])),
-                                    pack_bf16(silu_fast(v[8 * q + 6]), silu_fast(v[8 * q + 7])));
-        if (live) *reinterpret_cast<uint4*>(H + row * kHid + c0 + 8 * q) = hq;
-        *reinterpret_cast<uint4*>(sH + tc::cm_off(r, c0 + 8 * q, kHid / 8)) = hq;
-      }
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sH + tc::cm_off(r, c0 + 8 * q, kHid / 8)) =
+            make_uint4(pack_bf16(silu_fast(v[8 * q]), silu_fast(v[8 * q + 1])),
+                       pack_bf16(silu_fast(v[8 * q + 2]), silu_fast(v[8 * q + 3])),
+                       pack_bf16(silu_fast(v[8 * q + 4]), silu_fast(v[8 * q + 5])),
+                       pack_bf16(silu_fast(v[8 * q + 6]), silu_fast(v[8 * q + 7])));
     }
     // sH complete (and the accumulator read) before the next layer's MMAs
     tc::fence_async_smem();
@@ -769,79 +332,17 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   };
   constexpr uint32_t kIdH = tc::idesc_bf16(128, 128), kIdO = tc::idesc_bf16(128, 16);
   bool ok = layer(sX, sW1, kIn / 8, kIdH, 0);
-  hidden(ok, sb, a.G1, a.H1);
+  hidden(ok, sb);
   if (ok) ok = layer(sH, sW2, kHid / 8, kIdH, 0);
-  hidden(ok, sb + kHid, nullptr, a.H2);   // Z2 stays in TMEM
+  hidden(ok, sb + kHid);
   if (ok) ok = layer(sH, sW3, kHid / 8, kIdO, 128);
-  const float qnan = __int_as_float(0x7fffffff);
   if (half == 0) {
+    const float qnan = __int_as_float(0x7fffffff);
     float y[2] = {qnan, qnan};
     if (ok) tc::ld2(lane_addr + 128, y);
-    y[0] += sb[2 * kHid];
-    y[1] += sb[2 * kHid + 1];
-    if (live && a.Y) {
-      a.Y[row * kOut] = y[0];
-      a.Y[row * kOut + 1] = y[1];
-    }
-    if (a.T) {
-      // MSE loss 1/(2n) sum |Y - T|^2: dY = (Y - T) / n in BF16 for the
-      // backward GEMMs, the output-layer bias gradient from the FP32 values
-      const float d0 = live ? y[0] - a.T[row * kOut] : 0.0f;
-      const float d1 = live ? y[1] - a.T[row * kOut + 1] : 0.0f;
-      const float e0 = d0 * a.inv_n, e1 = d1 * a.inv_n;
-      const __nv_bfloat16 q0 = __float2bfloat16(e0), q1 = __float2bfloat16(e1);
-      if (live) {
-        a.dY[row * kOut] = q0;
-        a.dY[row * kOut + 1] = q1;
-      }
-      sdy[r][0] = __bfloat162float(q0);
-      sdy[r][1] = __bfloat162float(q1);
-      float l = d0 * d0 + d1 * d1, g0 = e0, g1 = e1;
-      for (int o = 16; o > 0; o >>= 1) {
-        l += __shfl_xor_sync(0xffffffffu, l, o);
-        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-      }
-      if (lane == 0) {
-        sred[quad][0] = l;
-        sred[quad][1] = g0;
-        sred[quad][2] = g1;
-      }
-    }
-  }
-  __syncthreads();
-  if (a.T) {
-    if (tid < 3) {
-      const float v = sred[0][tid] + sred[1][tid] + sred[2][tid] + sred[3][tid];
-      atomicAdd(tid == 0 ? a.loss : a.gb3 + (tid - 1), tid == 0 ? v * 0.5f * a.inv_n : v);
-    }
-    // dZ2 = (dY W3) * silu'(Z2), Z2 = layer-2 accumulator + b2; the column
-    // sums of dZ2 are the layer-2 bias gradient
-#pragma unroll 1
-    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
-      float v[32];
-      if (ok) {
-        tc::ld32(lane_addr + c0, v);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = qnan;
-      }
-      const float dy0 = sdy[r][0], dy1 = sdy[r][1];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        const float g = fmaf(dy1, sw3[1][c], dy0 * sw3[0][c]);
-        v[j] = live ? g * silu_grad(v[j] + sb[kHid + c]) : 0.0f;
-      }
-      if (live) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(a.dZ2 + row * kHid + c0 + 8 * q) =
-              make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
-                         pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-      }
-      const float cs = warp_colsum32(v, lane);
-      atomicAdd(&a.gb2[c0 + lane], cs);
+    if (live) {
+      a.Y[row * kOut] = y[0] + sb[2 * kHid];
+      a.Y[row * kOut + 1] = y[1] + sb[2 * kHid + 1];
     }
   }
   if (!ok) {
@@ -853,6 +354,385 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tm));
+}
+
+// --------------------------------------------------------------------------
+// Training step, forward and backward fused in one persistent kernel. A CTA of
+// 256 threads (two warps per TMEM lane quadrant, each on half of the columns)
+// walks tiles of 128 samples; for each it chains on the tensor core
+//   Z1 = X W1^T, Z2 = H1 W2^T, Y = H2 W3^T            (forward, K-major operands)
+//   dH1 = dZ2 W2                                        (W2 read MN-major)
+//   gW2 += dZ2^T H1, gW3^T += H2^T dY, gW1 += dZ1^T X    (contraction over the
+//                                                        tile's samples: both
+//                                                        operands MN-major)
+// with H = silu(Z + b), dY = (Y - T) / n, dZ2 = (dY W3) * silu'(Z2 + b2) and
+// dZ1 = dH1 * silu'(Z1 + b1). Every operand stays in shared memory in the one
+// core-matrix layout its producer writes ([sample][unit], 16-byte chunks of 8
+// units): read K-major by the next layer and MN-major (transposed) by the
+// weight gradients, so nothing is transposed and no activation leaves the
+// chip. The weight gradients accumulate in TMEM across the CTA's tiles, the
+// bias gradients and the loss in shared memory; at the end the CTA writes one
+// partial gradient vector (parameter order, then the loss) that the Adam or
+// reduction kernel sums over the CTAs. Every mbarrier wait is bounded; a CTA
+// whose MMAs do not complete sets the error word, writes NaN as its partial
+// and frees its TMEM after one more bounded wait.
+// --------------------------------------------------------------------------
+constexpr int kPart = kNParam + 2;   // partial: gradient, loss, one pad (16-byte rows)
+static_assert(kPart % 4 == 0, "partials in 16-byte rows");
+
+struct TrainArgs {
+  int64_t n;
+  int ntiles;
+  const uint16_t* X;                  // [n][32] BF16
+  const uint16_t *w1, *w2, *w3;       // [128][32], [128][128], [2][128] BF16
+  const float* p;                     // FP32 parameters (biases)
+  const float* T;                     // [n][2] FP32 targets
+  float inv_n;                        // 1 / n
+  float* part;                        // [gridDim.x][kPart]
+  int* err;
+  int polls;                          // polls of the main waits (clean-up: the default)
+  unsigned* chk;                      // check word of the bounds-checking build (may be null)
+};
+
+constexpr uint32_t kTrW1 = kHid * kIn * 2, kTrW2 = kHid * kHid * 2, kTrW3 = 16 * kHid * 2,
+                   kTrX = 128 * kIn * 2, kTrA = 128 * kHid * 2, kTrDY = 128 * 16 * 2;
+constexpr uint32_t kTrOffW2 = kTrW1, kTrOffW3 = kTrOffW2 + kTrW2, kTrOffX = kTrOffW3 + kTrW3,
+                   kTrOffH1 = kTrOffX + 2 * kTrX, kTrOffH2 = kTrOffH1 + kTrA,
+                   kTrOffDZ2 = kTrOffH2 + kTrA, kTrOffDY = kTrOffDZ2 + kTrA,
+                   kTrSmem = kTrOffDY + kTrDY;
+// TMEM columns: Z1; Z2, then dH1; gW2; gW1; Y; gW3^T
+constexpr uint32_t kCZ1 = 0, kCZ2 = 128, kCG2 = 256, kCG1 = 384, kCY = 416, kCG3 = 448;
+// instruction-descriptor bits: A / B read MN-major (transposed)
+constexpr uint32_t kTransA = 1u << 15, kTransB = 1u << 16;
+
+__global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* sW1 = tsm;
+  unsigned char* sW2 = tsm + kTrOffW2;
+  unsigned char* sW3 = tsm + kTrOffW3;
+  unsigned char* sX0 = tsm + kTrOffX;
+  unsigned char* sH1 = tsm + kTrOffH1;
+  unsigned char* sH2 = tsm + kTrOffH2;   // also dZ1, once H2 is consumed
+  unsigned char* sDZ2 = tsm + kTrOffDZ2;
+  unsigned char* sDY = tsm + kTrOffDY;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sb[2 * kHid + kOut];
+  __shared__ float sw3[kOut][kHid];   // the BF16 W3 as FP32 (the dY W3 product)
+  __shared__ float sdy[128][kOut];    // the BF16-rounded dY of the tile's rows
+  __shared__ float sg1[kHid], sg2[kHid], sacc[4];   // bias gradients; loss, gb3
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cta = blockIdx.x, G = gridDim.x;
+  // a CTA without a tile (the host sizes the grid so that there is none)
+  // contributes a zero partial
+  if (cta >= a.ntiles) {
+    (void)SDCEF_CHECK_W(a.chk, false, sdcef_chk::kMlpRow);
+    for (int i = tid; i < kPart; i += kGemmThreads) a.part[(size_t)cta * kPart + i] = 0.0f;
+    return;
+  }
+  const bool vecX = (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
+  auto sX = [&](int t) { return sX0 + (size_t)((t / G) & 1) * kTrX; };
+  stage_k(sX(cta), a.X, kIn, vecX, (int64_t)cta * 128, a.n, 128, 0, kIn, kIn / 8, tid);
+  stage_k(sW1, a.w1, kIn, true, 0, kHid, kHid, 0, kIn, kIn / 8, tid);
+  stage_k(sW2, a.w2, kHid, true, 0, kHid, kHid, 0, kHid, kHid / 8, tid);
+  stage_k(sW3, a.w3, kHid, true, 0, kOut, 16, 0, kHid, kHid / 8, tid);   // rows 2..15 zero
+  cp_commit();
+  for (int i = tid; i < (int)(kTrDY / 16); i += kGemmThreads)
+    reinterpret_cast<uint4*>(sDY)[i] = make_uint4(0u, 0u, 0u, 0u);   // o = 2..15 stay zero
+  for (int i = tid; i < kHid; i += kGemmThreads) {
+    sb[i] = a.p[kOffB1 + i];
+    sb[kHid + i] = a.p[kOffB2 + i];
+    sg1[i] = 0.0f;
+    sg2[i] = 0.0f;
+  }
+  if (tid < kOut) sb[2 * kHid + tid] = a.p[kOffB3 + tid];
+  if (tid < 4) sacc[tid] = 0.0f;
+  for (int i = tid; i < kOut * kHid; i += kGemmThreads)
+    sw3[i / kHid][i % kHid] = __uint_as_float((uint32_t)a.w3[i] << 16);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        tc::saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar)) : "memory");
+  cp_wait<0>();
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tmem_base, s_mbar = tc::saddr(&mbar);
+  const int quad = warp & 3, half = warp >> 2;
+  const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
+  const int r = quad * 32 + lane;   // this thread's row of a tile (TMEM lane)
+  const float qnan = __int_as_float(0x7fffffff);
+  uint32_t phase = 0;
+  bool ok = true;
+  // bounded wait for the last commit, by all threads; false once any thread gave up
+  auto wait_all = [&]() {
+    const bool w = tc::wait_phase(s_mbar, phase, a.polls);
+    phase ^= 1u;
+    const bool bad = __syncthreads_or(!w);
+    tc::fence_after();
+    return !bad;
+  };
+  // K-major operand [rows][kc chunks]: K-step kk (16 values) starts 256 bytes on
+  auto kdesc = [](const unsigned char* s, int kk, int kc) {
+    return tc::smem_desc(tc::saddr(s) + kk * 256, 128, kc * 128);
+  };
+  // the same storage read MN-major, K = its rows (the samples): K-step kk
+  // starts 2 core-matrix rows (2 kc 128 bytes) on; the leading offset steps
+  // along K, the stride offset along M / N (8 units, 128 bytes)
+  auto mdesc = [](const unsigned char* s, int kk, int kc) {
+    return tc::smem_desc(tc::saddr(s) + kk * 256 * kc, kc * 128, 128);
+  };
+  constexpr uint32_t kIdH = tc::idesc_bf16(128, 128), kIdO = tc::idesc_bf16(128, 16),
+                     kIdG1 = tc::idesc_bf16(128, 32) | kTransA | kTransB,
+                     kIdG2 = kIdH | kTransA | kTransB, kIdG3 = kIdO | kTransA | kTransB,
+                     kIdDH = kIdH | kTransB;
+  // layer 1 of the first tile
+  if (tid == 0) {
+    tc::fence_after();
+    for (int kk = 0; kk < kIn / 16; ++kk)
+      tc::mma(tm + kCZ1, kdesc(sX(cta), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
+    tc::commit(s_mbar);
+  }
+  bool first = true;
+#pragma unroll 1
+  for (int t = cta; t < a.ntiles && ok; t += G) {
+    const int64_t m0 = (int64_t)t * 128, row = m0 + r;
+    const bool live = row < a.n;
+    ok = wait_all();   // layer 1 (and the previous tile's gW1) done
+    if (!ok) break;
+    // the next tile's X into the other buffer (its last reader, gW1 two tiles
+    // back, has completed)
+    const int tn = t + G;
+    if (tn < a.ntiles) {
+      stage_k(sX(tn), a.X, kIn, vecX, (int64_t)tn * 128, a.n, 128, 0, kIn, kIn / 8, tid);
+      cp_commit();
+    }
+    // hidden layer: H = silu(acc + bias) into the next layer's operand
+    auto hidden = [&](uint32_t col, const float* bias, unsigned char* H) {
+#pragma unroll 1
+      for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+        float v[32];
+        tc::ld32(lane_addr + col + c0, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = c0 + 8 * q;
+          *reinterpret_cast<uint4*>(H + tc::cm_off(r, c, kHid / 8)) = make_uint4(
+              pack_bf16(silu_fast(v[8 * q] + bias[c]), silu_fast(v[8 * q + 1] + bias[c + 1])),
+              pack_bf16(silu_fast(v[8 * q + 2] + bias[c + 2]), silu_fast(v[8 * q + 3] + bias[c + 3])),
+              pack_bf16(silu_fast(v[8 * q + 4] + bias[c + 4]), silu_fast(v[8 * q + 5] + bias[c + 5])),
+              pack_bf16(silu_fast(v[8 * q + 6] + bias[c + 6]), silu_fast(v[8 * q + 7] + bias[c + 7])));
+        }
+      }
+      tc::fence_async_smem();
+      tc::fence_before();
+      __syncthreads();
+    };
+    hidden(kCZ1, sb, sH1);   // Z1 stays in TMEM for dZ1
+    if (tid == 0) {
+      tc::fence_after();
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        tc::mma(tm + kCZ2, kdesc(sH1, kk, kHid / 8), kdesc(sW2, kk, kHid / 8), kIdH, kk > 0);
+      tc::commit(s_mbar);
+    }
+    if (!(ok = wait_all())) break;
+    hidden(kCZ2, sb + kHid, sH2);   // Z2 stays in TMEM for dZ2
+    if (tid == 0) {
+      tc::fence_after();
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        tc::mma(tm + kCY, kdesc(sH2, kk, kHid / 8), kdesc(sW3, kk, kHid / 8), kIdO, kk > 0);
+      tc::commit(s_mbar);
+    }
+    if (!(ok = wait_all())) break;
+    // output layer, loss and dY = (Y - T) / n (BF16) into the dY operand
+    if (half == 0) {
+      float y[2];
+      tc::ld2(lane_addr + kCY, y);
+      const float d0 = live ? y[0] + sb[2 * kHid] - a.T[row * kOut] : 0.0f;
+      const float d1 = live ? y[1] + sb[2 * kHid + 1] - a.T[row * kOut + 1] : 0.0f;
+      const float e0 = d0 * a.inv_n, e1 = d1 * a.inv_n;
+      const __nv_bfloat16 q0 = __float2bfloat16(e0), q1 = __float2bfloat16(e1);
+      sdy[r][0] = __bfloat162float(q0);
+      sdy[r][1] = __bfloat162float(q1);
+      *reinterpret_cast<uint4*>(sDY + tc::cm_off(r, 0, 2)) =
+          make_uint4((uint32_t)__bfloat16_as_ushort(q0) | ((uint32_t)__bfloat16_as_ushort(q1) << 16),
+                     0u, 0u, 0u);
+      float l = d0 * d0 + d1 * d1, g0 = e0, g1 = e1;
+      for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&sacc[0], l);
+        atomicAdd(&sacc[1], g0);
+        atomicAdd(&sacc[2], g1);
+      }
+    }
+    __syncthreads();
+    // dZ2 = (dY W3) * silu'(Z2 + b2) into its operand; gb2 += column sums
+#pragma unroll 1
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+      float v[32];
+      tc::ld32(lane_addr + kCZ2 + c0, v);
+      const float dy0 = sdy[r][0], dy1 = sdy[r][1];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        const float g = fmaf(dy1, sw3[1][c], dy0 * sw3[0][c]);
+        v[j] = live ? g * silu_grad(v[j] + sb[kHid + c]) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sDZ2 + tc::cm_off(r, c0 + 8 * q, kHid / 8)) =
+            make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                       pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+      atomicAdd(&sg2[c0 + lane], warp_colsum32(v, lane));
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    // dH1 = dZ2 W2 (over Z2); gW2 += dZ2^T H1; gW3^T += H2^T dY
+    if (tid == 0) {
+      tc::fence_after();
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        tc::mma(tm + kCZ2, kdesc(sDZ2, kk, kHid / 8), mdesc(sW2, kk, kHid / 8), kIdDH, kk > 0);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+        tc::mma(tm + kCG2, mdesc(sDZ2, kk, kHid / 8), mdesc(sH1, kk, kHid / 8), kIdG2, acc);
+        tc::mma(tm + kCG3, mdesc(sH2, kk, kHid / 8), mdesc(sDY, kk, 2), kIdG3, acc);
+      }
+      tc::commit(s_mbar);
+    }
+    if (!(ok = wait_all())) break;
+    // dZ1 = dH1 * silu'(Z1 + b1) into the H2 buffer; gb1 += column sums
+    unsigned char* sDZ1 = sH2;
+#pragma unroll 1
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+      float v[32], z[32];
+      tc::ld32(lane_addr + kCZ2 + c0, v);
+      tc::ld32(lane_addr + kCZ1 + c0, z);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = live ? v[j] * silu_grad(z[j] + sb[c0 + j]) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sDZ1 + tc::cm_off(r, c0 + 8 * q, kHid / 8)) =
+            make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                       pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+      atomicAdd(&sg1[c0 + lane], warp_colsum32(v, lane));
+    }
+    if (tn < a.ntiles) cp_wait<0>();   // the next tile's X has landed
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    // gW1 += dZ1^T X; then the next tile's layer 1 (the same commit covers both)
+    if (tid == 0) {
+      tc::fence_after();
+      for (int kk = 0; kk < 128 / 16; ++kk)
+        tc::mma(tm + kCG1, mdesc(sDZ1, kk, kHid / 8), mdesc(sX(t), kk, kIn / 8), kIdG1,
+                (first && kk == 0) ? 0u : 1u);
+      if (tn < a.ntiles)
+        for (int kk = 0; kk < kIn / 16; ++kk)
+          tc::mma(tm + kCZ1, kdesc(sX(tn), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
+      tc::commit(s_mbar);
+    }
+    first = false;
+  }
+  // the last commit (the last tile's gW1) is still to be waited for
+  if (ok) ok = wait_all();
+  float* part = a.part + (size_t)cta * kPart;
+  if (ok) {
+    // gW2 [c][h]: TMEM lane c, column h; gW1 [h][f]: lane h, column f;
+    // gW3 [o][c]: lane c, column o
+#pragma unroll 1
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+      float v[32];
+      tc::ld32(lane_addr + kCG2 + c0, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4*>(part + kOffW2 + r * kHid + c0 + 4 * q) =
+            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    {
+      float v[32];
+      tc::ld32(lane_addr + kCG1, v);   // both halves read; half 0 stores
+      if (half == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(part + kOffW1 + r * kIn + 4 * q) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      float y[2];
+      tc::ld2(lane_addr + kCG3, y);
+      if (half == 1) {
+        part[kOffW3 + r] = y[0];
+        part[kOffW3 + kHid + r] = y[1];
+      }
+    }
+    if (tid < kHid) {
+      part[kOffB1 + tid] = sg1[tid];
+      part[kOffB2 + tid] = sg2[tid];
+    }
+    if (tid == 0) {
+      part[kOffB3] = sacc[1];
+      part[kOffB3 + 1] = sacc[2];
+      part[kNParam] = sacc[0] * 0.5f * a.inv_n;
+      part[kNParam + 1] = 0.0f;
+    }
+  } else {
+    if (tid == 0) atomicExch(a.err, 1);
+    for (int i = tid; i < kPart; i += kGemmThreads) part[i] = qnan;
+    // an MMA may still be in flight: one more bounded wait (the parity of the
+    // commit that was not seen to complete) before TMEM is freed
+    tc::wait_phase(s_mbar, phase ^ 1u);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tm));
+}
+
+// Sum of the CTAs' partials: 32 parameters per block of 256 threads, each of
+// the 8 row groups of a parameter summing every 8th partial. ADAM: the Adam
+// update (and the BF16 weight copies); otherwise g = the gradient. The loss
+// (entry kNParam) goes to *loss.
+template <bool ADAM>
+__global__ void __launch_bounds__(256) part_reduce_kernel(const float* part, int nparts, float* g,
+                                                          float* loss, float* p, float* m, float* v,
+                                                          float lr, float b1, float b2, float eps,
+                                                          float c1, float c2, __nv_bfloat16* w1,
+                                                          __nv_bfloat16* w2, __nv_bfloat16* w3) {
+  __shared__ float s[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + tx;
+  float acc = 0.0f;
+  if (i < kNParam + 1)
+    for (int b = ty; b < nparts; b += 8) acc += part[(size_t)b * kPart + i];
+  s[ty][tx] = acc;
+  __syncthreads();
+  if (ty != 0 || i > kNParam) return;
+  float gi = 0.0f;
+  for (int q = 0; q < 8; ++q) gi += s[q][tx];
+  if (i == kNParam) {
+    *loss = gi;
+    return;
+  }
+  if (!ADAM) {
+    g[i] = gi;
+    return;
+  }
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  p[i] = pi;
+  if (i >= kOffW1 && i < kOffB1) w1[i - kOffW1] = __float2bfloat16(pi);
+  else if (i >= kOffW2 && i < kOffB2) w2[i - kOffW2] = __float2bfloat16(pi);
+  else if (i >= kOffW3 && i < kOffB3) w3[i - kOffW3] = __float2bfloat16(pi);
 }
 
 // --------------------------------------------------------------------------
@@ -1093,26 +973,6 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
                  "n"(tc::kTmemCols));
 }
 
-// Adam (Kingma & Ba 2015) with bias correction; refreshes the BF16 weight
-// copies and clears the gradient for the next step.
-__global__ void adam_kernel(float* p, float* g, float* m, float* v, int n, float lr, float b1,
-                            float b2, float eps, float c1, float c2, __nv_bfloat16* w1,
-                            __nv_bfloat16* w2, __nv_bfloat16* w3) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float gi = g[i];
-    float mi = b1 * m[i] + (1.0f - b1) * gi;
-    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    p[i] = pi;
-    g[i] = 0.0f;
-    if (i >= kOffW1 && i < kOffB1) w1[i - kOffW1] = __float2bfloat16(pi);
-    else if (i >= kOffW2 && i < kOffB2) w2[i - kOffW2] = __float2bfloat16(pi);
-    else if (i >= kOffW3 && i < kOffB3) w3[i - kOffW3] = __float2bfloat16(pi);
-  }
-}
-
 __global__ void to_bf16_kernel(const float* p, __nv_bfloat16* w1, __nv_bfloat16* w2,
                                __nv_bfloat16* w3) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNParam; i += gridDim.x * blockDim.x) {
@@ -1131,12 +991,11 @@ struct sdcef_mlp {
   float *p, *g, *m, *v;                 // FP32 parameters, gradients, Adam moments
   __nv_bfloat16 *w1, *w2, *w3;          // BF16 weight copies
   float *Y, *loss;                      // output, loss (FP32)
-  __nv_bfloat16 *G1, *H1, *H2, *dY, *dZ2, *dZ1, *X;   // BF16 silu'(Z1), activations, features
+  float* part;                          // [sms][kPart] per-CTA partials of the training kernel
+  __nv_bfloat16* X;                     // [max_rows][32] staging area of the guess
   int step;
   int launches;
   int sms;                              // multiprocessors of the device
-  cudaStream_t aux;                     // weight gradients beside the dZ chain
-  cudaEvent_t ev[2];
   int polls;                            // polls of the kernels' main bounded waits
 };
 
@@ -1149,91 +1008,8 @@ namespace {
 
 int cuda_fail(cudaError_t e) { return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e)); }
 
-// tensor map of a row-major BF16 operand (inner: values per k row, outer: k),
-// read in 64 x 64 boxes with 128-byte swizzle; false if it cannot be encoded
-// (the kernel then stages the operand with cp.async)
-bool tma_map(CUtensorMap* m, const uint16_t* base, int64_t inner, int64_t outer, int64_t row_bytes) {
-  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      fn = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }();
-  if (!encode || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15) || outer < 1) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-  const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
-  const cuuint32_t box[2] = {64, 64}, estr[2] = {1, 1};
-  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides,
-                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-cudaError_t gemm(sdcef_mlp* h, const GemmArgs& a, cudaStream_t st) {
-  if (a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaSuccess;
-  TcGemm g;
-  memset(&g, 0, sizeof(g));
-  g.M = a.M; g.N = a.N; g.K = a.K; g.epi = a.epi;
-  g.A = reinterpret_cast<const uint16_t*>(a.A);
-  g.sam = a.transA ? 1 : a.lda; g.sak = a.transA ? a.lda : 1;
-  g.B = reinterpret_cast<const uint16_t*>(a.B);
-  g.sbn = a.transB ? a.ldb : 1; g.sbk = a.transB ? 1 : a.ldb;
-  g.C = a.C; g.scm = a.ldc; g.scn = 1;
-  g.H = a.H; g.ldh = a.ldh; g.Gin = a.Gin; g.ldgin = a.ldgin; g.colsum = a.colsum;
-  g.err = (int*)h->loss + 5;
-  g.polls = h->polls;
-  g.chk = mlp_chk(h);
-  if (g.epi == kEpiAccumulate && g.M < 64 && g.N > g.M) {
-    // C^T = B^T A^T: the long side of the product goes on the 128 TMEM lanes
-    std::swap(g.M, g.N); std::swap(g.A, g.B); std::swap(g.sam, g.sbn); std::swap(g.sak, g.sbk);
-    std::swap(g.scm, g.scn);
-  }
-  if (g.N > 128 || (g.sam != 1 && g.sak != 1) || (g.sbn != 1 && g.sbk != 1))
-    return cudaErrorInvalidValue;
-  const int tiles = (g.M + 127) / 128, Np = (g.N + 15) & ~15;
-  int splits = 1;
-  g.kchunk = (g.K + kSlabK - 1) / kSlabK * kSlabK;
-  if (g.epi == kEpiAccumulate) {
-    // split K (the sample dimension of the weight gradients) over about two
-    // CTAs per SM, at least two slabs each; partial sums meet in C by atomics
-    const int want = std::max(1, 2 * h->sms / tiles);
-    const int kc = (g.K + want - 1) / want;
-    g.kchunk = std::max((kc + kSlabK - 1) / kSlabK * kSlabK, 2 * kSlabK);
-    splits = (g.K + g.kchunk - 1) / g.kchunk;
-  }
-  const bool amn = g.sak != 1, bmn = g.sbk != 1;
-  const uint32_t smem = ((amn && bmn) ? 2 : 4) * kOpBytes + 2 * (amn ? nat_bytes(128) : 0) +
-                        2 * (bmn ? nat_bytes(Np) : 0) + 1024;
-  // row-major operands of 128 values per k row go by TMA (two swizzled 64 x 64 boxes per slab)
-  CUtensorMap mapA, mapB;
-  memset(&mapA, 0, sizeof(mapA));
-  memset(&mapB, 0, sizeof(mapB));
-  g.tmaA = amn && g.M == 128 && tma_map(&mapA, g.A, 128, g.K, g.sak * 2);
-  g.tmaB = bmn && g.N == 128 && tma_map(&mapB, g.B, 128, g.K, g.sbk * 2);
-  // M (the sample dimension of the layer GEMMs) on grid.x, whose limit is 2^31 - 1
-  const dim3 grid(tiles, splits);
-  if (g.epi == kEpiAccumulate && amn && bmn)
-    gemm_tc_kernel<kEpiAccumulate, true, true><<<grid, kGemmThreads, smem, st>>>(g, mapA, mapB);
-  else if (g.epi == kEpiSiluGrad && !amn && bmn)
-    gemm_tc_kernel<kEpiSiluGrad, false, true><<<grid, kGemmThreads, smem, st>>>(g, mapA, mapB);
-  else
-    return cudaErrorInvalidValue;   // a form the training step does not use
-  ++h->launches;
-  return cudaGetLastError();
-}
-
-GemmArgs ga() {
-  GemmArgs g;
-  memset(&g, 0, sizeof(g));
-  return g;
-}
-
-// forward through the three layers for n rows of X. Inference (T == nullptr):
-// Y (FP32 [n][2]) only. Training: silu'(Z1), H1, H2 for the backward GEMMs, and the
-// loss, dY, dZ2 and the bias gradients of layers 2 and 3 (into h->g).
-cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t n, float* Y) {
+// forward through the three layers for n rows of X: Y (FP32 [n][2])
+cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n, float* Y) {
   if (n <= 0) return cudaSuccess;
   FwdArgs a;
   memset(&a, 0, sizeof(a));
@@ -1243,19 +1019,7 @@ cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_
   a.w2 = reinterpret_cast<const uint16_t*>(h->w2);
   a.w3 = reinterpret_cast<const uint16_t*>(h->w3);
   a.p = h->p;
-  a.H1 = h->H1;
-  a.H2 = h->H2;
   a.Y = Y;
-  if (T) {
-    a.G1 = h->G1;
-    a.T = T;
-    a.inv_n = 1.0f / (float)n;
-    a.dY = h->dY;
-    a.dZ2 = h->dZ2;
-    a.loss = h->loss;
-    a.gb2 = h->g + kOffB2;
-    a.gb3 = h->g + kOffB3;
-  }
   a.err = (int*)h->loss + 5;
   a.polls = h->polls;
   a.chk = mlp_chk(h);
@@ -1264,41 +1028,49 @@ cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_
   return cudaGetLastError();
 }
 
-// gradients of the mean-squared loss over n rows into h->g (accumulated),
-// after forward(.., T, ..) produced dY, dZ2 and the layer-2/3 bias gradients
-cudaError_t backward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n) {
-  // the weight gradients of layers 3 and 2 (split-K over the samples) run on
-  // the auxiliary stream beside dZ1 and gW1
-  cudaError_t e = cudaEventRecord(h->ev[0], h->st);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev[0], 0);
+// forward, loss and backward over n rows (train_tc_kernel), then the sum of
+// the CTAs' partials: the Adam step (adam) or the gradient into h->g; the loss
+// into h->loss[0]. The grid spreads the 128-row tiles evenly over at most one
+// CTA per multiprocessor.
+cudaError_t train(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t n, bool adam,
+                  float lr) {
+  const int64_t ntiles = (n + 127) / 128;
+  const int64_t per = (ntiles + h->sms - 1) / h->sms;
+  const int grid = (int)((ntiles + per - 1) / per);
+  TrainArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.ntiles = (int)ntiles;
+  a.X = reinterpret_cast<const uint16_t*>(X);
+  a.w1 = reinterpret_cast<const uint16_t*>(h->w1);
+  a.w2 = reinterpret_cast<const uint16_t*>(h->w2);
+  a.w3 = reinterpret_cast<const uint16_t*>(h->w3);
+  a.p = h->p;
+  a.T = T;
+  a.inv_n = 1.0f / (float)n;
+  a.part = h->part;
+  a.err = (int*)h->loss + 5;
+  a.polls = h->polls;
+  a.chk = mlp_chk(h);
+  train_tc_kernel<<<grid, kGemmThreads, kTrSmem, h->st>>>(a);
+  ++h->launches;
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // gW3 = dY^T H2
-  GemmArgs g = ga();
-  g.M = kOut; g.N = kHid; g.K = (int)n;
-  g.A = h->dY; g.lda = kOut; g.transA = 1; g.B = h->H2; g.ldb = kHid;
-  g.C = h->g + kOffW3; g.ldc = kHid; g.epi = kEpiAccumulate;
-  if ((e = gemm(h, g, h->aux)) != cudaSuccess) return e;
-  // gW2 = dZ2^T H1
-  g = ga();
-  g.M = kHid; g.N = kHid; g.K = (int)n;
-  g.A = h->dZ2; g.lda = kHid; g.transA = 1; g.B = h->H1; g.ldb = kHid;
-  g.C = h->g + kOffW2; g.ldc = kHid;
-  if ((e = gemm(h, g, h->aux)) != cudaSuccess) return e;
-  // dZ1 = (dZ2 W2) * silu'(Z1), silu'(Z1) stored by the forward; gb1 += colsum
-  g = ga();
-  g.M = (int)n; g.N = kHid; g.K = kHid;
-  g.A = h->dZ2; g.lda = kHid; g.B = h->w2; g.ldb = kHid;
-  g.epi = kEpiSiluGrad; g.Gin = h->G1; g.ldgin = kHid; g.H = h->dZ1; g.ldh = kHid; g.colsum = h->g + kOffB1;
-  if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
-  // gW1 = dZ1^T X
-  g = ga();
-  g.M = kHid; g.N = kIn; g.K = (int)n;
-  g.A = h->dZ1; g.lda = kHid; g.transA = 1; g.B = X; g.ldb = kIn;
-  g.C = h->g + kOffW1; g.ldc = kIn;
-  if ((e = gemm(h, g, h->st)) != cudaSuccess) return e;
-  // join: the gradient is complete on the caller's stream
-  if ((e = cudaEventRecord(h->ev[1], h->aux)) != cudaSuccess) return e;
-  return cudaStreamWaitEvent(h->st, h->ev[1], 0);
+  const unsigned blocks = (unsigned)((kNParam + 1 + 31) / 32);
+  if (adam) {
+    h->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)h->step), c2 = 1.0f - powf(b2, (float)h->step);
+    part_reduce_kernel<true><<<blocks, 256, 0, h->st>>>(h->part, grid, h->g, h->loss, h->p, h->m,
+                                                         h->v, lr, b1, b2, 1e-8f, c1, c2, h->w1,
+                                                         h->w2, h->w3);
+  } else {
+    part_reduce_kernel<false><<<blocks, 256, 0, h->st>>>(h->part, grid, h->g, h->loss, nullptr,
+                                                          nullptr, nullptr, 0.0f, 0.0f, 0.0f, 0.0f,
+                                                          0.0f, 0.0f, nullptr, nullptr, nullptr);
+  }
+  ++h->launches;
+  return cudaGetLastError();
 }
 
 FeatArgs feat_args(const sdcef_batch* b) {
@@ -1343,20 +1115,12 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tc_kernel<kEpiAccumulate, true, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmemMax);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tc_kernel<kEpiSiluGrad, false, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmemMax);
-    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFwSmem);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
-      e = cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTrSmem);
     if (e != cudaSuccess) {
-      for (cudaEvent_t ev : h->ev) if (ev) cudaEventDestroy(ev);
-      if (h->aux) cudaStreamDestroy(h->aux);
       delete h;
       return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e));
     }
@@ -1366,17 +1130,13 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
   struct Alloc { void** p; size_t bytes; } al[] = {
       {(void**)&h->p, kNParam * 4}, {(void**)&h->g, kNParam * 4}, {(void**)&h->m, kNParam * 4},
       {(void**)&h->v, kNParam * 4}, {(void**)&h->w1, kHid * kIn * 2}, {(void**)&h->w2, kHid * kHid * 2},
-      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->G1, R * kHid * 2},
-      {(void**)&h->Y, R * kOut * 4}, {(void**)&h->loss, 64}, {(void**)&h->H1, R * kHid * 2},
-      {(void**)&h->H2, R * kHid * 2}, {(void**)&h->dY, R * kOut * 2}, {(void**)&h->dZ2, R * kHid * 2},
-      {(void**)&h->dZ1, R * kHid * 2}, {(void**)&h->X, R * kIn * 2}};
+      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->Y, R * kOut * 4}, {(void**)&h->loss, 64},
+      {(void**)&h->part, (size_t)h->sms * kPart * 4}, {(void**)&h->X, R * kIn * 2}};
   for (auto& a : al) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
     if (e == cudaSuccess) e = cudaMemset(*a.p, 0, a.bytes);
     if (e != cudaSuccess) {
       for (auto& b : al) if (*b.p) cudaFree(*b.p);
-      for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
-      cudaStreamDestroy(h->aux);
       delete h;
       return report_error(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
     }
@@ -1388,11 +1148,7 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
 int sdcef_mlp_destroy(sdcef_mlp* h) {
   if (!h) return SDCEF_SUCCESS;
   cudaStreamSynchronize(h->st);
-  cudaStreamSynchronize(h->aux);
-  for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
-  cudaStreamDestroy(h->aux);
-  void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->G1, h->Y, h->loss,
-                h->H1, h->H2, h->dY, h->dZ2, h->dZ1, h->X};
+  void* ps[] = {h->p, h->g, h->m, h->v, h->w1, h->w2, h->w3, h->Y, h->loss, h->part, h->X};
   for (void* p : ps) cudaFree(p);
   delete h;
   return SDCEF_SUCCESS;
@@ -1484,7 +1240,7 @@ int sdcef_mlp_forward(sdcef_mlp* h, const void* X_bf16, int64_t n, float* Y) {
   if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_forward: n exceeds max_rows");
   if (n == 0) return SDCEF_SUCCESS;
   h->launches = 0;
-  cudaError_t e = forward(h, (const __nv_bfloat16*)X_bf16, nullptr, n, Y ? Y : h->Y);
+  cudaError_t e = forward(h, (const __nv_bfloat16*)X_bf16, n, Y ? Y : h->Y);
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
 }
 
@@ -1493,14 +1249,10 @@ int sdcef_mlp_grad(sdcef_mlp* h, const void* X_bf16, const float* T, int64_t n, 
   if (!h || !X_bf16 || !T || n < 1) return report_error(SDCEF_ERR_INVALID, "mlp_grad: bad arguments");
   if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_grad: n exceeds max_rows");
   h->launches = 0;
-  cudaError_t e = cudaMemsetAsync(h->g, 0, kNParam * 4, h->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->loss, 0, 4, h->st);
-  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, T, n, nullptr);
-  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, n);
+  cudaError_t e = train(h, (const __nv_bfloat16*)X_bf16, T, n, false, 0.0f);
   if (e == cudaSuccess && grads)
     e = cudaMemcpyAsync(grads, h->g, kNParam * 4, cudaMemcpyDeviceToDevice, h->st);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, h->loss, 4, cudaMemcpyDeviceToDevice, h->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->g, 0, kNParam * 4, h->st);
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
 }
 
@@ -1510,17 +1262,8 @@ int sdcef_mlp_train_step(sdcef_mlp* h, const void* X_bf16, const float* T, int64
     return report_error(SDCEF_ERR_INVALID, "mlp_train_step: bad arguments");
   if (n > h->max_rows) return report_error(SDCEF_ERR_CAPACITY, "mlp_train_step: n exceeds max_rows");
   h->launches = 0;
-  cudaError_t e = cudaMemsetAsync(h->loss, 0, 4, h->st);
-  if (e == cudaSuccess) e = forward(h, (const __nv_bfloat16*)X_bf16, T, n, nullptr);
-  if (e == cudaSuccess) e = backward(h, (const __nv_bfloat16*)X_bf16, n);
+  cudaError_t e = train(h, (const __nv_bfloat16*)X_bf16, T, n, true, lr);
   if (e != cudaSuccess) return cuda_fail(e);
-  h->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.0f - powf(b1, (float)h->step), c2 = 1.0f - powf(b2, (float)h->step);
-  adam_kernel<<<64, 256, 0, h->st>>>(h->p, h->g, h->m, h->v, kNParam, lr, b1, b2, 1e-8f, c1, c2,
-                                      h->w1, h->w2, h->w3);
-  ++h->launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   if (loss) e = cudaMemcpyAsync(loss, h->loss, 4, cudaMemcpyDeviceToDevice, h->st);
   return e == cudaSuccess ? SDCEF_SUCCESS : cuda_fail(e);
 }
@@ -1571,8 +1314,7 @@ int sdcef_mlp_last_launch_count(const sdcef_mlp* h) { return h ? h->launches : 0
 int sdcef_mlp_check_word(sdcef_mlp* h, unsigned* word) {
   if (!h || !word) return report_error(SDCEF_ERR_INVALID, "mlp_check_word: NULL argument");
   unsigned w = 0;
-  cudaError_t e = cudaStreamSynchronize(h->aux);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&w, mlp_chk(h), sizeof(unsigned), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaMemcpyAsync(&w, mlp_chk(h), sizeof(unsigned), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(mlp_chk(h), 0, sizeof(unsigned), h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -1590,8 +1332,7 @@ int sdcef_mlp_check(sdcef_mlp* h) {
   if (!h) return report_error(SDCEF_ERR_INVALID, "mlp_check: NULL");
   int* word = (int*)h->loss + 5;
   int flag = 0;
-  cudaError_t e = cudaStreamSynchronize(h->aux);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, word, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaMemcpyAsync(&flag, word, sizeof(int), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(word, 0, sizeof(int), h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return cuda_fail(e);
