@@ -38,10 +38,11 @@ static_assert(kNParam == SDCEF_MLP_NPARAM, "parameter count");
 
 // SiLU and its derivative through the hardware tanh approximation:
 // silu(z) = z/2 (1 + tanh(z/2)), silu'(z) = s (1 + z (1 - s)) with the sigmoid
-// s = (1 + tanh(z/2)) / 2 -- one special-function operation each instead of an
-// exponential and a reciprocal. The ~2^-11 relative error of tanh.approx is
-// below the BF16 rounding of the activation or gradient that follows, and
-// training and inference evaluate the same activation.
+// s = (1 + tanh(z/2)) / 2 -- one special-function operation for both instead
+// of an exponential and a reciprocal (the training kernel forms them together).
+// The ~2^-11 relative error of tanh.approx is below the BF16 rounding of the
+// activation or gradient that follows, and training and inference evaluate
+// the same activation.
 __device__ __forceinline__ float tanh_fast(float x) {
   float t;
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x));
@@ -50,10 +51,6 @@ __device__ __forceinline__ float tanh_fast(float x) {
 __device__ __forceinline__ float silu_fast(float z) {
   const float h = 0.5f * z;
   return fmaf(h, tanh_fast(h), h);
-}
-__device__ __forceinline__ float silu_grad(float z) {
-  const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
-  return s * fmaf(z, 1.0f - s, 1.0f);
 }
 
 // --------------------------------------------------------------------------
@@ -148,16 +145,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // --------------------------------------------------------------------------
-// Helpers of the tensor-core training kernels: operand staging in the K-major
-// core-matrix layout of mlp_tc.cuh (16-byte asynchronous copies) and the
-// column sums of an epilogue's values over a warp.
+// Helpers of the tensor-core kernels: operand staging in the K-major
+// core-matrix layout of mlp_tc.cuh (16-byte asynchronous copies).
 // --------------------------------------------------------------------------
 constexpr int kGemmThreads = 256;   // two warps per TMEM lane quadrant
 
 __device__ __forceinline__ uint32_t pack_u16(uint16_t lo, uint16_t hi) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
-
 
 // 16-byte asynchronous global -> shared copy; an invalid chunk is zero-filled
 // without reading global memory (the source then only names a valid address)
@@ -177,12 +172,13 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // [16 e, 16 e + 16) of S, i.e. core matrix e / 8, row e % 8: asynchronously
 // where the chunk's 8 k are all valid or all beyond the matrix, element by
 // element where it straddles the edge or the rows are not 16-byte aligned.
+template <int NT = kGemmThreads>
 __device__ __forceinline__ void stage_k(unsigned char* S, const uint16_t* X, int64_t sr, bool vec,
                                         int64_t rbase, int64_t rmax, int R, int k0, int kend,
                                         int kc, int tid) {
   const int items = R * kc;
 #pragma unroll 4
-  for (int e = tid; e < items; e += kGemmThreads) {
+  for (int e = tid; e < items; e += NT) {
     const int grp = e / (8 * kc), w = e - grp * 8 * kc;
     const int64_t gr = rbase + grp * 8 + (w & 7);
     const int gk = k0 + (w >> 3) * 8;
@@ -200,21 +196,6 @@ __device__ __forceinline__ void stage_k(unsigned char* S, const uint16_t* X, int
   }
 }
 
-
-// lane l ends with the sum over the warp of v[l]
-__device__ __forceinline__ float warp_colsum32(float* v, int lane) {
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool up = (lane & s) != 0;
-#pragma unroll
-    for (int j = 0; j < s; ++j) {
-      const float send = up ? v[j] : v[j + s];
-      const float keep = up ? v[j + s] : v[j];
-      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-    }
-  }
-  return v[0];
-}
 
 // --------------------------------------------------------------------------
 // Inference forward, all three layers in one launch: a CTA of 256 threads
@@ -358,27 +339,31 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
 
 // --------------------------------------------------------------------------
 // Training step, forward and backward fused in one persistent kernel. A CTA of
-// 256 threads (two warps per TMEM lane quadrant, each on half of the columns)
+// 512 threads (four warps per TMEM lane quadrant, each on 32 of the columns)
 // walks tiles of 128 samples; for each it chains on the tensor core
 //   Z1 = X W1^T, Z2 = H1 W2^T, Y = H2 W3^T            (forward, K-major operands)
 //   dH1 = dZ2 W2                                        (W2 read MN-major)
-//   gW2 += dZ2^T H1, gW3^T += H2^T dY, gW1 += dZ1^T X    (contraction over the
+//   gW2 += dZ2^T H1, gW3^T += H2^T dY, gW1 += dZ1^T X,
+//   gb2 += dZ2^T 1, gb1 += dZ1^T 1                      (contraction over the
 //                                                        tile's samples: both
 //                                                        operands MN-major)
 // with H = silu(Z + b), dY = (Y - T) / n, dZ2 = (dY W3) * silu'(Z2 + b2) and
-// dZ1 = dH1 * silu'(Z1 + b1). Every operand stays in shared memory in the one
-// core-matrix layout its producer writes ([sample][unit], 16-byte chunks of 8
-// units): read K-major by the next layer and MN-major (transposed) by the
-// weight gradients, so nothing is transposed and no activation leaves the
-// chip. The weight gradients accumulate in TMEM across the CTA's tiles, the
-// bias gradients and the loss in shared memory; at the end the CTA writes one
-// partial gradient vector (parameter order, then the loss) that the Adam or
-// reduction kernel sums over the CTAs. Every mbarrier wait is bounded; a CTA
-// whose MMAs do not complete sets the error word, writes NaN as its partial
-// and frees its TMEM after one more bounded wait.
+// dZ1 = dH1 * silu'(Z1 + b1); the hidden-layer epilogues store silu' (BF16)
+// beside H from the same tanh, and the backward epilogues turn it into dZ in
+// place. Every operand stays in shared memory in the one core-matrix layout
+// its producer writes ([sample][unit], 16-byte chunks of 8 units): read
+// K-major by the next layer and MN-major (transposed) by the weight and bias
+// gradients, so nothing is transposed and no activation leaves the chip. The
+// weight and bias gradients accumulate in TMEM across the CTA's tiles, the
+// loss and gb3 in shared memory; at the end the CTA writes one partial
+// gradient vector (parameter order, then the loss) that the Adam or reduction
+// kernel sums over the CTAs. Every mbarrier wait is bounded; a CTA whose MMAs
+// do not complete sets the error word, writes NaN as its partial and frees its
+// TMEM after one more bounded wait.
 // --------------------------------------------------------------------------
 constexpr int kPart = kNParam + 2;   // partial: gradient, loss, one pad (16-byte rows)
 static_assert(kPart % 4 == 0, "partials in 16-byte rows");
+constexpr int kTrThreads = 512;      // four warps per TMEM lane quadrant
 
 struct TrainArgs {
   int64_t n;
@@ -395,59 +380,67 @@ struct TrainArgs {
 };
 
 constexpr uint32_t kTrW1 = kHid * kIn * 2, kTrW2 = kHid * kHid * 2, kTrW3 = 16 * kHid * 2,
-                   kTrX = 128 * kIn * 2, kTrA = 128 * kHid * 2, kTrDY = 128 * 16 * 2;
+                   kTrX = 128 * kIn * 2, kTrA = 128 * kHid * 2, kTrN16 = 128 * 16 * 2;
+// buffers: W1, W2, W3, X (two), H1, H2, G1 (silu'(Z1), then dZ1), G2 (silu'(Z2),
+// then dZ2), dY, ones
 constexpr uint32_t kTrOffW2 = kTrW1, kTrOffW3 = kTrOffW2 + kTrW2, kTrOffX = kTrOffW3 + kTrW3,
                    kTrOffH1 = kTrOffX + 2 * kTrX, kTrOffH2 = kTrOffH1 + kTrA,
-                   kTrOffDZ2 = kTrOffH2 + kTrA, kTrOffDY = kTrOffDZ2 + kTrA,
-                   kTrSmem = kTrOffDY + kTrDY;
-// TMEM columns: Z1; Z2, then dH1; gW2; gW1; Y; gW3^T
-constexpr uint32_t kCZ1 = 0, kCZ2 = 128, kCG2 = 256, kCG1 = 384, kCY = 416, kCG3 = 448;
+                   kTrOffG1 = kTrOffH2 + kTrA, kTrOffG2 = kTrOffG1 + kTrA,
+                   kTrOffDY = kTrOffG2 + kTrA, kTrOffOne = kTrOffDY + kTrN16,
+                   kTrSmem = kTrOffOne + kTrN16;
+// TMEM columns: Z1; Z2, then dH1; gW2; gW1; Y; gW3^T; gb2; gb1
+constexpr uint32_t kCZ1 = 0, kCZ2 = 128, kCG2 = 256, kCG1 = 384, kCY = 416, kCG3 = 432,
+                   kCB2 = 448, kCB1 = 464;
 // instruction-descriptor bits: A / B read MN-major (transposed)
 constexpr uint32_t kTransA = 1u << 15, kTransB = 1u << 16;
 
-__global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) {
+__global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* sW1 = tsm;
   unsigned char* sW2 = tsm + kTrOffW2;
   unsigned char* sW3 = tsm + kTrOffW3;
   unsigned char* sX0 = tsm + kTrOffX;
   unsigned char* sH1 = tsm + kTrOffH1;
-  unsigned char* sH2 = tsm + kTrOffH2;   // also dZ1, once H2 is consumed
-  unsigned char* sDZ2 = tsm + kTrOffDZ2;
+  unsigned char* sH2 = tsm + kTrOffH2;
+  unsigned char* sG1 = tsm + kTrOffG1;   // silu'(Z1 + b1), then dZ1 in place
+  unsigned char* sG2 = tsm + kTrOffG2;   // silu'(Z2 + b2), then dZ2 in place
   unsigned char* sDY = tsm + kTrOffDY;
+  unsigned char* sOne = tsm + kTrOffOne;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ float sb[2 * kHid + kOut];
   __shared__ float sw3[kOut][kHid];   // the BF16 W3 as FP32 (the dY W3 product)
   __shared__ float sdy[128][kOut];    // the BF16-rounded dY of the tile's rows
-  __shared__ float sg1[kHid], sg2[kHid], sacc[4];   // bias gradients; loss, gb3
+  __shared__ float sacc[4];           // loss, gb3
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x, G = gridDim.x;
   // a CTA without a tile (the host sizes the grid so that there is none)
   // contributes a zero partial
   if (cta >= a.ntiles) {
     (void)SDCEF_CHECK_W(a.chk, false, sdcef_chk::kMlpRow);
-    for (int i = tid; i < kPart; i += kGemmThreads) a.part[(size_t)cta * kPart + i] = 0.0f;
+    for (int i = tid; i < kPart; i += kTrThreads) a.part[(size_t)cta * kPart + i] = 0.0f;
     return;
   }
   const bool vecX = (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
   auto sX = [&](int t) { return sX0 + (size_t)((t / G) & 1) * kTrX; };
-  stage_k(sX(cta), a.X, kIn, vecX, (int64_t)cta * 128, a.n, 128, 0, kIn, kIn / 8, tid);
-  stage_k(sW1, a.w1, kIn, true, 0, kHid, kHid, 0, kIn, kIn / 8, tid);
-  stage_k(sW2, a.w2, kHid, true, 0, kHid, kHid, 0, kHid, kHid / 8, tid);
-  stage_k(sW3, a.w3, kHid, true, 0, kOut, 16, 0, kHid, kHid / 8, tid);   // rows 2..15 zero
+  stage_k<kTrThreads>(sX(cta), a.X, kIn, vecX, (int64_t)cta * 128, a.n, 128, 0, kIn, kIn / 8, tid);
+  stage_k<kTrThreads>(sW1, a.w1, kIn, true, 0, kHid, kHid, 0, kIn, kIn / 8, tid);
+  stage_k<kTrThreads>(sW2, a.w2, kHid, true, 0, kHid, kHid, 0, kHid, kHid / 8, tid);
+  stage_k<kTrThreads>(sW3, a.w3, kHid, true, 0, kOut, 16, 0, kHid, kHid / 8, tid);   // rows 2..15 zero
   cp_commit();
-  for (int i = tid; i < (int)(kTrDY / 16); i += kGemmThreads)
-    reinterpret_cast<uint4*>(sDY)[i] = make_uint4(0u, 0u, 0u, 0u);   // o = 2..15 stay zero
-  for (int i = tid; i < kHid; i += kGemmThreads) {
+  // dY (units 2..15 stay zero) and the ones operand (unit 0 one, the rest zero),
+  // [sample][16] in the core-matrix layout
+  for (int i = tid; i < (int)(kTrN16 / 16); i += kTrThreads) {
+    reinterpret_cast<uint4*>(sDY)[i] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(sOne)[i] = make_uint4((i & 8) ? 0u : 0x3F80u, 0u, 0u, 0u);
+  }
+  for (int i = tid; i < kHid; i += kTrThreads) {
     sb[i] = a.p[kOffB1 + i];
     sb[kHid + i] = a.p[kOffB2 + i];
-    sg1[i] = 0.0f;
-    sg2[i] = 0.0f;
   }
   if (tid < kOut) sb[2 * kHid + tid] = a.p[kOffB3 + tid];
   if (tid < 4) sacc[tid] = 0.0f;
-  for (int i = tid; i < kOut * kHid; i += kGemmThreads)
+  for (int i = tid; i < kOut * kHid; i += kTrThreads)
     sw3[i / kHid][i % kHid] = __uint_as_float((uint32_t)a.w3[i] << 16);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -462,9 +455,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
   __syncthreads();
   tc::fence_after();
   const uint32_t tm = tmem_base, s_mbar = tc::saddr(&mbar);
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, part4 = warp >> 2;   // lane quadrant; 32-column group
   const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
   const int r = quad * 32 + lane;   // this thread's row of a tile (TMEM lane)
+  const int c0 = part4 * 32;        // this thread's 32 columns of a 128-column result
   const float qnan = __int_as_float(0x7fffffff);
   uint32_t phase = 0;
   bool ok = true;
@@ -488,7 +482,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
   };
   constexpr uint32_t kIdH = tc::idesc_bf16(128, 128), kIdO = tc::idesc_bf16(128, 16),
                      kIdG1 = tc::idesc_bf16(128, 32) | kTransA | kTransB,
-                     kIdG2 = kIdH | kTransA | kTransB, kIdG3 = kIdO | kTransA | kTransB,
+                     kIdG2 = kIdH | kTransA | kTransB, kIdG16 = kIdO | kTransA | kTransB,
                      kIdDH = kIdH | kTransB;
   // layer 1 of the first tile
   if (tid == 0) {
@@ -497,41 +491,58 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
       tc::mma(tm + kCZ1, kdesc(sX(cta), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
     tc::commit(s_mbar);
   }
+  // hidden-layer epilogue: with t = tanh((acc + bias) / 2), H = silu and
+  // G = silu' (sigmoid s = (1 + t) / 2, silu' = s (1 + z (1 - s))) into their operands
+  auto hidden = [&](uint32_t col, const float* bias, unsigned char* H, unsigned char* Gd) {
+    float v[32];
+    tc::ld32(lane_addr + col + c0, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float h[8], g[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float z = v[8 * q + j] + bias[c0 + 8 * q + j];
+        const float hz = 0.5f * z, t = tanh_fast(hz);
+        const float sg = fmaf(0.5f, t, 0.5f);
+        h[j] = fmaf(hz, t, hz);
+        g[j] = sg * fmaf(z, 1.0f - sg, 1.0f);
+      }
+      const uint32_t off = tc::cm_off(r, c0 + 8 * q, kHid / 8);
+      *reinterpret_cast<uint4*>(H + off) =
+          make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
+                     pack_bf16(h[6], h[7]));
+      *reinterpret_cast<uint4*>(Gd + off) =
+          make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+                     pack_bf16(g[6], g[7]));
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+  };
+  // 8 BF16 of an operand chunk <-> FP32
+  auto unpack8 = [](const uint4& u, float* f) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      f[2 * j] = __uint_as_float(w[j] << 16);
+      f[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
+    }
+  };
   bool first = true;
 #pragma unroll 1
   for (int t = cta; t < a.ntiles && ok; t += G) {
-    const int64_t m0 = (int64_t)t * 128, row = m0 + r;
+    const int64_t row = (int64_t)t * 128 + r;
     const bool live = row < a.n;
-    ok = wait_all();   // layer 1 (and the previous tile's gW1) done
+    ok = wait_all();   // layer 1 (and the previous tile's gW1, gb1) done
     if (!ok) break;
     // the next tile's X into the other buffer (its last reader, gW1 two tiles
     // back, has completed)
     const int tn = t + G;
     if (tn < a.ntiles) {
-      stage_k(sX(tn), a.X, kIn, vecX, (int64_t)tn * 128, a.n, 128, 0, kIn, kIn / 8, tid);
+      stage_k<kTrThreads>(sX(tn), a.X, kIn, vecX, (int64_t)tn * 128, a.n, 128, 0, kIn, kIn / 8, tid);
       cp_commit();
     }
-    // hidden layer: H = silu(acc + bias) into the next layer's operand
-    auto hidden = [&](uint32_t col, const float* bias, unsigned char* H) {
-#pragma unroll 1
-      for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
-        float v[32];
-        tc::ld32(lane_addr + col + c0, v);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = c0 + 8 * q;
-          *reinterpret_cast<uint4*>(H + tc::cm_off(r, c, kHid / 8)) = make_uint4(
-              pack_bf16(silu_fast(v[8 * q] + bias[c]), silu_fast(v[8 * q + 1] + bias[c + 1])),
-              pack_bf16(silu_fast(v[8 * q + 2] + bias[c + 2]), silu_fast(v[8 * q + 3] + bias[c + 3])),
-              pack_bf16(silu_fast(v[8 * q + 4] + bias[c + 4]), silu_fast(v[8 * q + 5] + bias[c + 5])),
-              pack_bf16(silu_fast(v[8 * q + 6] + bias[c + 6]), silu_fast(v[8 * q + 7] + bias[c + 7])));
-        }
-      }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-    };
-    hidden(kCZ1, sb, sH1);   // Z1 stays in TMEM for dZ1
+    hidden(kCZ1, sb, sH1, sG1);
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
@@ -539,7 +550,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
       tc::commit(s_mbar);
     }
     if (!(ok = wait_all())) break;
-    hidden(kCZ2, sb + kHid, sH2);   // Z2 stays in TMEM for dZ2
+    hidden(kCZ2, sb + kHid, sH2, sG2);
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
     }
     if (!(ok = wait_all())) break;
     // output layer, loss and dY = (Y - T) / n (BF16) into the dY operand
-    if (half == 0) {
+    if (part4 == 0) {
       float y[2];
       tc::ld2(lane_addr + kCY, y);
       const float d0 = live ? y[0] + sb[2 * kHid] - a.T[row * kOut] : 0.0f;
@@ -573,67 +584,65 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
       }
     }
     __syncthreads();
-    // dZ2 = (dY W3) * silu'(Z2 + b2) into its operand; gb2 += column sums
-#pragma unroll 1
-    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
-      float v[32];
-      tc::ld32(lane_addr + kCZ2 + c0, v);
-      const float dy0 = sdy[r][0], dy1 = sdy[r][1];
+    // dZ2 = (dY W3) * silu'(Z2 + b2), in place of silu'
+    {
+      const float dy0 = live ? sdy[r][0] : 0.0f, dy1 = live ? sdy[r][1] : 0.0f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        const float g = fmaf(dy1, sw3[1][c], dy0 * sw3[0][c]);
-        v[j] = live ? g * silu_grad(v[j] + sb[kHid + c]) : 0.0f;
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + 8 * q;
+        uint4* pp = reinterpret_cast<uint4*>(sG2 + tc::cm_off(r, c, kHid / 8));
+        float g[8];
+        unpack8(*pp, g);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) g[j] *= fmaf(dy1, sw3[1][c + j], dy0 * sw3[0][c + j]);
+        *pp = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+                         pack_bf16(g[6], g[7]));
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(sDZ2 + tc::cm_off(r, c0 + 8 * q, kHid / 8)) =
-            make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
-                       pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-      atomicAdd(&sg2[c0 + lane], warp_colsum32(v, lane));
     }
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
-    // dH1 = dZ2 W2 (over Z2); gW2 += dZ2^T H1; gW3^T += H2^T dY
+    // dH1 = dZ2 W2 (over Z2); gW2 += dZ2^T H1; gW3^T += H2^T dY; gb2 += dZ2^T 1
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
-        tc::mma(tm + kCZ2, kdesc(sDZ2, kk, kHid / 8), mdesc(sW2, kk, kHid / 8), kIdDH, kk > 0);
+        tc::mma(tm + kCZ2, kdesc(sG2, kk, kHid / 8), mdesc(sW2, kk, kHid / 8), kIdDH, kk > 0);
       for (int kk = 0; kk < 128 / 16; ++kk) {
         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-        tc::mma(tm + kCG2, mdesc(sDZ2, kk, kHid / 8), mdesc(sH1, kk, kHid / 8), kIdG2, acc);
-        tc::mma(tm + kCG3, mdesc(sH2, kk, kHid / 8), mdesc(sDY, kk, 2), kIdG3, acc);
+        tc::mma(tm + kCG2, mdesc(sG2, kk, kHid / 8), mdesc(sH1, kk, kHid / 8), kIdG2, acc);
+        tc::mma(tm + kCG3, mdesc(sH2, kk, kHid / 8), mdesc(sDY, kk, 2), kIdG16, acc);
+        tc::mma(tm + kCB2, mdesc(sG2, kk, kHid / 8), mdesc(sOne, kk, 2), kIdG16, acc);
       }
       tc::commit(s_mbar);
     }
     if (!(ok = wait_all())) break;
-    // dZ1 = dH1 * silu'(Z1 + b1) into the H2 buffer; gb1 += column sums
-    unsigned char* sDZ1 = sH2;
-#pragma unroll 1
-    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
-      float v[32], z[32];
+    // dZ1 = dH1 * silu'(Z1 + b1), in place of silu'
+    {
+      float v[32];
       tc::ld32(lane_addr + kCZ2 + c0, v);
-      tc::ld32(lane_addr + kCZ1 + c0, z);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = live ? v[j] * silu_grad(z[j] + sb[c0 + j]) : 0.0f;
+      for (int q = 0; q < 4; ++q) {
+        uint4* pp = reinterpret_cast<uint4*>(sG1 + tc::cm_off(r, c0 + 8 * q, kHid / 8));
+        float g[8];
+        unpack8(*pp, g);
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(sDZ1 + tc::cm_off(r, c0 + 8 * q, kHid / 8)) =
-            make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
-                       pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-      atomicAdd(&sg1[c0 + lane], warp_colsum32(v, lane));
+        for (int j = 0; j < 8; ++j) g[j] = live ? g[j] * v[8 * q + j] : 0.0f;
+        *pp = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+                         pack_bf16(g[6], g[7]));
+      }
     }
     if (tn < a.ntiles) cp_wait<0>();   // the next tile's X has landed
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
-    // gW1 += dZ1^T X; then the next tile's layer 1 (the same commit covers both)
+    // gW1 += dZ1^T X; gb1 += dZ1^T 1; then the next tile's layer 1 (one commit)
     if (tid == 0) {
       tc::fence_after();
-      for (int kk = 0; kk < 128 / 16; ++kk)
-        tc::mma(tm + kCG1, mdesc(sDZ1, kk, kHid / 8), mdesc(sX(t), kk, kIn / 8), kIdG1,
-                (first && kk == 0) ? 0u : 1u);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+        tc::mma(tm + kCG1, mdesc(sG1, kk, kHid / 8), mdesc(sX(t), kk, kIn / 8), kIdG1, acc);
+        tc::mma(tm + kCB1, mdesc(sG1, kk, kHid / 8), mdesc(sOne, kk, 2), kIdG16, acc);
+      }
       if (tn < a.ntiles)
         for (int kk = 0; kk < kIn / 16; ++kk)
           tc::mma(tm + kCZ1, kdesc(sX(tn), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
@@ -641,14 +650,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
     }
     first = false;
   }
-  // the last commit (the last tile's gW1) is still to be waited for
+  // the last commit (the last tile's gW1, gb1) is still to be waited for
   if (ok) ok = wait_all();
   float* part = a.part + (size_t)cta * kPart;
   if (ok) {
     // gW2 [c][h]: TMEM lane c, column h; gW1 [h][f]: lane h, column f;
-    // gW3 [o][c]: lane c, column o
-#pragma unroll 1
-    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+    // gW3 [o][c]: lane c, column o; gb2, gb1: lane c (h), column 0
+    {
       float v[32];
       tc::ld32(lane_addr + kCG2 + c0, v);
 #pragma unroll
@@ -656,25 +664,26 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
         *reinterpret_cast<float4*>(part + kOffW2 + r * kHid + c0 + 4 * q) =
             make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
-    {
+    if (part4 == 0) {
       float v[32];
-      tc::ld32(lane_addr + kCG1, v);   // both halves read; half 0 stores
-      if (half == 0) {
+      tc::ld32(lane_addr + kCG1, v);
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<float4*>(part + kOffW1 + r * kIn + 4 * q) =
-              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4*>(part + kOffW1 + r * kIn + 4 * q) =
+            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (part4 == 1) {
       float y[2];
       tc::ld2(lane_addr + kCG3, y);
-      if (half == 1) {
-        part[kOffW3 + r] = y[0];
-        part[kOffW3 + kHid + r] = y[1];
-      }
-    }
-    if (tid < kHid) {
-      part[kOffB1 + tid] = sg1[tid];
-      part[kOffB2 + tid] = sg2[tid];
+      part[kOffW3 + r] = y[0];
+      part[kOffW3 + kHid + r] = y[1];
+    } else if (part4 == 2) {
+      float y[2];
+      tc::ld2(lane_addr + kCB2, y);
+      part[kOffB2 + r] = y[0];
+    } else {
+      float y[2];
+      tc::ld2(lane_addr + kCB1, y);
+      part[kOffB1 + r] = y[0];
     }
     if (tid == 0) {
       part[kOffB3] = sacc[1];
@@ -684,7 +693,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) train_tc_kernel(TrainArgs a) 
     }
   } else {
     if (tid == 0) atomicExch(a.err, 1);
-    for (int i = tid; i < kPart; i += kGemmThreads) part[i] = qnan;
+    for (int i = tid; i < kPart; i += kTrThreads) part[i] = qnan;
     // an MMA may still be in flight: one more bounded wait (the parity of the
     // commit that was not seen to complete) before TMEM is freed
     tc::wait_phase(s_mbar, phase ^ 1u);
@@ -1052,7 +1061,7 @@ cudaError_t train(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t 
   a.err = (int*)h->loss + 5;
   a.polls = h->polls;
   a.chk = mlp_chk(h);
-  train_tc_kernel<<<grid, kGemmThreads, kTrSmem, h->st>>>(a);
+  train_tc_kernel<<<grid, kTrThreads, kTrSmem, h->st>>>(a);
   ++h->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
