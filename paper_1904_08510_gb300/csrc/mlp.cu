@@ -406,11 +406,14 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   unsigned char* sG2 = tsm + kTrOffG2;   // silu'(Z2 + b2), then dZ2 in place
   unsigned char* sDY = tsm + kTrOffDY;
   unsigned char* sOne = tsm + kTrOffOne;
-  __shared__ __align__(8) uint64_t mbar;
+  // mbar[0]: the layers and gW1 / gb1; mbar[1]: dH1; mbar[2]: gW2, gW3, gb2,
+  // so that the dZ1 epilogue runs while the weight-gradient MMAs do. A
+  // barrier never has more than one commit that is not waited for: a parity
+  // wait cannot tell a phase from the one two later
+  __shared__ __align__(8) uint64_t mbar[3];
   __shared__ uint32_t tmem_base;
   __shared__ float sb[2 * kHid + kOut];
   __shared__ float sw3[kOut][kHid];   // the BF16 W3 as FP32 (the dY W3 product)
-  __shared__ float sdy[128][kOut];    // the BF16-rounded dY of the tile's rows
   __shared__ float sacc[4];           // loss, gb3
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x, G = gridDim.x;
@@ -447,27 +450,37 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
         tc::saddr(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0)
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar)) : "memory");
+  if (tid < 3)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[tid])) : "memory");
   cp_wait<0>();
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tm = tmem_base, s_mbar = tc::saddr(&mbar);
+  const uint32_t tm = tmem_base,
+                 s_bar[3] = {tc::saddr(&mbar[0]), tc::saddr(&mbar[1]), tc::saddr(&mbar[2])};
   const int quad = warp & 3, part4 = warp >> 2;   // lane quadrant; 32-column group
   const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
   const int r = quad * 32 + lane;   // this thread's row of a tile (TMEM lane)
   const int c0 = part4 * 32;        // this thread's 32 columns of a 128-column result
   const float qnan = __int_as_float(0x7fffffff);
-  uint32_t phase = 0;
+  // commits issued and waited for on each mbarrier (every thread counts them
+  // alike); phases complete in issue order, each is waited for in turn
+  uint32_t issued[3] = {0u, 0u, 0u}, waited[3] = {0u, 0u, 0u};
+  int failed = -1;   // the barrier of a wait that gave up
   bool ok = true;
-  // bounded wait for the last commit, by all threads; false once any thread gave up
-  auto wait_all = [&]() {
-    const bool w = tc::wait_phase(s_mbar, phase, a.polls);
-    phase ^= 1u;
+  auto commit = [&](int b) {
+    if (tid == 0) tc::commit(s_bar[b]);
+    ++issued[b];
+  };
+  // bounded wait for the oldest unwaited commit of barrier b, by all threads;
+  // false once any thread gave up
+  auto wait_bar = [&](int b) {
+    const bool w = tc::wait_phase(s_bar[b], waited[b] & 1u, a.polls);
+    ++waited[b];
     const bool bad = __syncthreads_or(!w);
     tc::fence_after();
+    if (bad) failed = b;
     return !bad;
   };
   // K-major operand [rows][kc chunks]: K-step kk (16 values) starts 256 bytes on
@@ -489,8 +502,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
     tc::fence_after();
     for (int kk = 0; kk < kIn / 16; ++kk)
       tc::mma(tm + kCZ1, kdesc(sX(cta), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
-    tc::commit(s_mbar);
   }
+  commit(0);
   // hidden-layer epilogue: with t = tanh((acc + bias) / 2), H = silu and
   // G = silu' (sigmoid s = (1 + t) / 2, silu' = s (1 + z (1 - s))) into their operands
   auto hidden = [&](uint32_t col, const float* bias, unsigned char* H, unsigned char* Gd) {
@@ -533,8 +546,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   for (int t = cta; t < a.ntiles && ok; t += G) {
     const int64_t row = (int64_t)t * 128 + r;
     const bool live = row < a.n;
-    ok = wait_all();   // layer 1 (and the previous tile's gW1, gb1) done
-    if (!ok) break;
+    // this row's targets, loaded while the MMAs run
+    const float t0 = live ? a.T[row * kOut] : 0.0f, t1 = live ? a.T[row * kOut + 1] : 0.0f;
+    // the previous tile's weight gradients, then its gW1 / gb1 and this tile's layer 1
+    if (!first && !(ok = wait_bar(2))) break;
+    if (!(ok = wait_bar(0))) break;
     // the next tile's X into the other buffer (its last reader, gW1 two tiles
     // back, has completed)
     const int tn = t + G;
@@ -547,76 +563,81 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
         tc::mma(tm + kCZ2, kdesc(sH1, kk, kHid / 8), kdesc(sW2, kk, kHid / 8), kIdH, kk > 0);
-      tc::commit(s_mbar);
     }
-    if (!(ok = wait_all())) break;
+    commit(0);
+    if (!(ok = wait_bar(0))) break;
     hidden(kCZ2, sb + kHid, sH2, sG2);
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
         tc::mma(tm + kCY, kdesc(sH2, kk, kHid / 8), kdesc(sW3, kk, kHid / 8), kIdO, kk > 0);
-      tc::commit(s_mbar);
     }
-    if (!(ok = wait_all())) break;
-    // output layer, loss and dY = (Y - T) / n (BF16) into the dY operand
-    if (part4 == 0) {
+    commit(0);
+    if (!(ok = wait_bar(0))) break;
+    // output layer and dY = (Y - T) / n (BF16), by every thread for its row;
+    // the first column group writes the dY operand and sums the loss and gb3
+    float dy0, dy1;
+    {
       float y[2];
       tc::ld2(lane_addr + kCY, y);
-      const float d0 = live ? y[0] + sb[2 * kHid] - a.T[row * kOut] : 0.0f;
-      const float d1 = live ? y[1] + sb[2 * kHid + 1] - a.T[row * kOut + 1] : 0.0f;
+      const float d0 = live ? y[0] + sb[2 * kHid] - t0 : 0.0f;
+      const float d1 = live ? y[1] + sb[2 * kHid + 1] - t1 : 0.0f;
       const float e0 = d0 * a.inv_n, e1 = d1 * a.inv_n;
       const __nv_bfloat16 q0 = __float2bfloat16(e0), q1 = __float2bfloat16(e1);
-      sdy[r][0] = __bfloat162float(q0);
-      sdy[r][1] = __bfloat162float(q1);
-      *reinterpret_cast<uint4*>(sDY + tc::cm_off(r, 0, 2)) =
-          make_uint4((uint32_t)__bfloat16_as_ushort(q0) | ((uint32_t)__bfloat16_as_ushort(q1) << 16),
-                     0u, 0u, 0u);
-      float l = d0 * d0 + d1 * d1, g0 = e0, g1 = e1;
-      for (int o = 16; o > 0; o >>= 1) {
-        l += __shfl_xor_sync(0xffffffffu, l, o);
-        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-      }
-      if (lane == 0) {
-        atomicAdd(&sacc[0], l);
-        atomicAdd(&sacc[1], g0);
-        atomicAdd(&sacc[2], g1);
+      dy0 = __bfloat162float(q0);
+      dy1 = __bfloat162float(q1);
+      if (part4 == 0) {
+        *reinterpret_cast<uint4*>(sDY + tc::cm_off(r, 0, 2)) =
+            make_uint4((uint32_t)__bfloat16_as_ushort(q0) | ((uint32_t)__bfloat16_as_ushort(q1) << 16),
+                       0u, 0u, 0u);
+        float l = d0 * d0 + d1 * d1, g0 = e0, g1 = e1;
+        for (int o = 16; o > 0; o >>= 1) {
+          l += __shfl_xor_sync(0xffffffffu, l, o);
+          g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+          g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+        }
+        if (lane == 0) {
+          atomicAdd(&sacc[0], l);
+          atomicAdd(&sacc[1], g0);
+          atomicAdd(&sacc[2], g1);
+        }
       }
     }
-    __syncthreads();
     // dZ2 = (dY W3) * silu'(Z2 + b2), in place of silu'
-    {
-      const float dy0 = live ? sdy[r][0] : 0.0f, dy1 = live ? sdy[r][1] : 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = c0 + 8 * q;
-        uint4* pp = reinterpret_cast<uint4*>(sG2 + tc::cm_off(r, c, kHid / 8));
-        float g[8];
-        unpack8(*pp, g);
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + 8 * q;
+      uint4* pp = reinterpret_cast<uint4*>(sG2 + tc::cm_off(r, c, kHid / 8));
+      float g[8];
+      unpack8(*pp, g);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) g[j] *= fmaf(dy1, sw3[1][c + j], dy0 * sw3[0][c + j]);
-        *pp = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
-                         pack_bf16(g[6], g[7]));
-      }
+      for (int j = 0; j < 8; ++j) g[j] *= fmaf(dy1, sw3[1][c + j], dy0 * sw3[0][c + j]);
+      *pp = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+                       pack_bf16(g[6], g[7]));
     }
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
-    // dH1 = dZ2 W2 (over Z2); gW2 += dZ2^T H1; gW3^T += H2^T dY; gb2 += dZ2^T 1
+    // dH1 = dZ2 W2 (over Z2; barrier 1), then gW2 += dZ2^T H1, gW3^T += H2^T dY,
+    // gb2 += dZ2^T 1 (barrier 2, waited for before the next tile's epilogues)
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
         tc::mma(tm + kCZ2, kdesc(sG2, kk, kHid / 8), mdesc(sW2, kk, kHid / 8), kIdDH, kk > 0);
+    }
+    commit(1);
+    if (tid == 0) {
       for (int kk = 0; kk < 128 / 16; ++kk) {
         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
         tc::mma(tm + kCG2, mdesc(sG2, kk, kHid / 8), mdesc(sH1, kk, kHid / 8), kIdG2, acc);
         tc::mma(tm + kCG3, mdesc(sH2, kk, kHid / 8), mdesc(sDY, kk, 2), kIdG16, acc);
         tc::mma(tm + kCB2, mdesc(sG2, kk, kHid / 8), mdesc(sOne, kk, 2), kIdG16, acc);
       }
-      tc::commit(s_mbar);
     }
-    if (!(ok = wait_all())) break;
-    // dZ1 = dH1 * silu'(Z1 + b1), in place of silu'
+    commit(2);
+    if (!(ok = wait_bar(1))) break;
+    // dZ1 = dH1 * silu'(Z1 + b1), in place of silu' (the weight-gradient MMAs
+    // read neither)
     {
       float v[32];
       tc::ld32(lane_addr + kCZ2 + c0, v);
@@ -646,12 +667,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
       if (tn < a.ntiles)
         for (int kk = 0; kk < kIn / 16; ++kk)
           tc::mma(tm + kCZ1, kdesc(sX(tn), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
-      tc::commit(s_mbar);
     }
+    commit(0);
     first = false;
   }
-  // the last commit (the last tile's gW1, gb1) is still to be waited for
-  if (ok) ok = wait_all();
+  // the last tile's weight gradients and gW1 / gb1 are still to be waited for
+  if (ok && waited[2] < issued[2]) ok = wait_bar(2);
+  if (ok && waited[0] < issued[0]) ok = wait_bar(0);
   float* part = a.part + (size_t)cta * kPart;
   if (ok) {
     // gW2 [c][h]: TMEM lane c, column h; gW1 [h][f]: lane h, column f;
@@ -694,9 +716,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   } else {
     if (tid == 0) atomicExch(a.err, 1);
     for (int i = tid; i < kPart; i += kTrThreads) part[i] = qnan;
-    // an MMA may still be in flight: one more bounded wait (the parity of the
-    // commit that was not seen to complete) before TMEM is freed
-    tc::wait_phase(s_mbar, phase ^ 1u);
+    // MMAs may still be in flight: bounded waits, in order, for every commit
+    // not seen to complete (the one a wait gave up on included) before TMEM is freed
+    for (int b = 0; b < 3; ++b)
+      for (uint32_t w = waited[b] - (b == failed ? 1u : 0u); w < issued[b]; ++w)
+        tc::wait_phase(s_bar[b], w & 1u);
   }
   tc::fence_before();
   __syncthreads();
