@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kGemmThreads) fwd_tc_kernel(FwdArgs a) {
 // weight and bias gradients accumulate in TMEM across the CTA's tiles, the
 // loss and gb3 in shared memory; at the end the CTA writes one partial
 // gradient vector (parameter order, then the loss) that the Adam or reduction
-// kernel sums over the CTAs. Every mbarrier wait is bounded; a CTA whose MMAs
+// kernel sums over the CTAs in a fixed order, so that a step is deterministic. Every mbarrier wait is bounded; a CTA whose MMAs
 // do not complete sets the error word, writes NaN as its partial and frees its
 // TMEM after one more bounded wait.
 // --------------------------------------------------------------------------
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   __shared__ uint32_t tmem_base;
   __shared__ float sb[2 * kHid + kOut];
   __shared__ float sw3[kOut][kHid];   // the BF16 W3 as FP32 (the dY W3 product)
-  __shared__ float sacc[4];           // loss, gb3
+  __shared__ float sacc[4][3];        // per lane quadrant: loss, gb3 (one writer each)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x, G = gridDim.x;
   // a CTA without a tile (the host sizes the grid so that there is none)
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
     sb[kHid + i] = a.p[kOffB2 + i];
   }
   if (tid < kOut) sb[2 * kHid + tid] = a.p[kOffB3 + tid];
-  if (tid < 4) sacc[tid] = 0.0f;
+  if (tid < 12) sacc[tid / 3][tid % 3] = 0.0f;
   for (int i = tid; i < kOut * kHid; i += kTrThreads)
     sw3[i / kHid][i % kHid] = __uint_as_float((uint32_t)a.w3[i] << 16);
   if (warp == 0) {
@@ -596,10 +596,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
           g0 += __shfl_xor_sync(0xffffffffu, g0, o);
           g1 += __shfl_xor_sync(0xffffffffu, g1, o);
         }
-        if (lane == 0) {
-          atomicAdd(&sacc[0], l);
-          atomicAdd(&sacc[1], g0);
-          atomicAdd(&sacc[2], g1);
+        if (lane == 0) {   // the quadrant's one writer: a fixed summation order
+          sacc[quad][0] += l;
+          sacc[quad][1] += g0;
+          sacc[quad][2] += g1;
         }
       }
     }
@@ -708,9 +708,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
       part[kOffB1 + r] = y[0];
     }
     if (tid == 0) {
-      part[kOffB3] = sacc[1];
-      part[kOffB3 + 1] = sacc[2];
-      part[kNParam] = sacc[0] * 0.5f * a.inv_n;
+      float v[3];
+      for (int k = 0; k < 3; ++k) v[k] = (sacc[0][k] + sacc[1][k]) + (sacc[2][k] + sacc[3][k]);
+      part[kOffB3] = v[1];
+      part[kOffB3 + 1] = v[2];
+      part[kNParam] = v[0] * 0.5f * a.inv_n;
       part[kNParam + 1] = 0.0f;
     }
   } else {

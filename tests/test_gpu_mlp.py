@@ -8,7 +8,7 @@ activations and operands carry 8 significant bits; accumulation is FP32). A
 numpy emulation of the kernels' rounding points stays below 7e-3 on these
 cases. The rows of the last, ragged 128-row tile are scaled up (inputs x3 for
 the forward pass, targets x300 for the gradients), so that a wrong or dropped
-last tile or split-K slab moves the compared values by far more than the bar.
+last tile moves the compared values by far more than the bar.
 """
 import numpy as np
 import pytest
@@ -98,10 +98,10 @@ def test_forward_matches_oracle_on_bf16_weights(n):
     assert_elementwise(Y, Yr, 2e-2, "Y")
 
 
-# 37 and 700 rows: one ragged 128-row tile and several; 20011 rows: the
-# weight gradients split their K = 20011 samples over ~150 CTAs of two
-# 64-sample slabs with a ragged last slab; 40001 rows: three slabs per CTA,
-# so that a slab reuses a row-major slot (second completion of its mbarrier)
+# 37 and 700 rows: one ragged 128-row tile and several; 20011 rows: 157 tiles,
+# two per CTA of the persistent training kernel, the last one ragged; 40001
+# rows: three tiles per CTA, so that each CTA accumulates its weight and bias
+# gradients in TMEM across tiles and reuses both of its X buffers
 @pytest.mark.parametrize("n", [37, 700, 20011, 40001])
 def test_gradients_match_fp64_backprop(n):
     d = dev()
@@ -110,8 +110,8 @@ def test_gradients_match_fp64_backprop(n):
     Xh = M.bf16_round(rng.standard_normal((n, 32)))
     Xh[:, 25:] = 0.0
     Th = rng.standard_normal((n, 2))
-    # the samples of the ragged last tile (and so of the last split-K slab)
-    # dominate every weight gradient: dropping them changes each by > 80 %
+    # the samples of the ragged last tile dominate every weight gradient:
+    # dropping them changes each by > 80 %
     Th[-tail_rows(n):] *= 300.0
     mlp = S.MLP(n)
     mlp.set_params(flat)

@@ -1,9 +1,10 @@
 """Failure path of the tensor-core kernels' bounded waits.
 
-Every mbarrier wait of the tcgen05 kernels (guess, forward, gradient GEMMs) is
-bounded; a wait that runs out makes the kernel set an error word, write NaN for
-the rows it was computing, skip the rest of its work and, after one more
-bounded wait that lets an issued MMA finish, free its tensor memory. The poll
+Every mbarrier wait of the tcgen05 kernels (guess, inference forward, fused
+training step) is bounded; a wait that runs out makes the kernel set an error
+word, write NaN for the rows (or the partial gradient) it was computing, skip
+the rest of its work and, after bounded waits that let issued MMAs finish,
+free its tensor memory. The poll
 count of the main waits is a handle setting; at 0 every such wait gives up at
 once, exactly as one that ran out, with no GPU fault and no hang. The test
 drives that path and checks that the context stays usable: with the default
@@ -79,7 +80,6 @@ def test_wait_that_runs_out_sets_error_and_nan_then_recovers():
     g2, _ = mlp.grad(X, T)
     mlp.check()                       # the error word was cleared by the last check
     assert np.array_equal(ne2.cpu().numpy(), ne0)
-    g2 = g2.cpu().numpy()
-    # split-K weight gradients accumulate with atomics: equal up to summation order
-    assert np.abs(g2 - g0).max() <= 1e-5 * np.abs(g0).max()
+    # the training step sums its partial gradients in a fixed order: bit-identical
+    assert np.array_equal(g2.cpu().numpy(), g0)
     mlp.close()
