@@ -744,8 +744,17 @@ __global__ void __launch_bounds__(256) part_reduce_kernel(const float* part, int
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + tx;
   float acc = 0.0f;
-  if (i < kNParam + 1)
-    for (int b = ty; b < nparts; b += 8) acc += part[(size_t)b * kPart + i];
+  if (i < kNParam + 1) {
+    // four independent loads in flight per thread; the order of the sums is fixed
+    float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int b = ty;
+    for (; b + 24 < nparts; b += 32) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] += part[(size_t)(b + 8 * u) * kPart + i];
+    }
+    for (; b < nparts; b += 8) q[0] += part[(size_t)b * kPart + i];
+    acc = (q[0] + q[1]) + (q[2] + q[3]);
+  }
   s[ty][tx] = acc;
   __syncthreads();
   if (ty != 0 || i > kNParam) return;
