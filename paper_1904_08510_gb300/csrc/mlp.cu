@@ -11,6 +11,8 @@
 // Shapes: 32 (25 features, zero-padded) -> 128 -> 128 -> 2, SiLU activations.
 // Parameters (FP32 master copy, flat): W1[128][32], b1[128], W2[128][128],
 // b2[128], W3[2][128], b3[2]; BF16 copies of W1, W2, W3 feed the tensor cores.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -197,6 +199,53 @@ __device__ __forceinline__ void stage_k(unsigned char* S, const uint16_t* X, int
 }
 
 
+// Chunk-major core-matrix layout of a tile of R rows (the training kernel's X
+// and weights): the 8-value chunk c of row r (values 8c .. 8c + 7) at byte
+// c R 16 + r 16, so chunk c of all R rows is one 16 R-byte block. A K-major
+// descriptor steps along K by R 16 bytes (leading offset) and along the rows by
+// 128 bytes (stride offset); read MN-major, K runs along the rows (leading
+// offset 128) and M / N along the chunks (stride offset R 16). This is the
+// layout a TMA box of 8 values x R rows writes (one box per chunk).
+//
+// Staging into it by 16-byte asynchronous copies (when the tensor-map copy is
+// not available): rows rbase .. rbase + R - 1 (zero at and beyond rmax), kc
+// chunks of 8 values of X(r, k) = X[r sr + k].
+template <int NT>
+__device__ __forceinline__ void stage_cm(unsigned char* S, const uint16_t* X, int64_t sr, bool vec,
+                                         int64_t rbase, int64_t rmax, int R, int kc, int tid) {
+  for (int e = tid; e < R * kc; e += NT) {
+    const int c = e / R, r = e - c * R;
+    const int64_t gr = rbase + r;
+    const bool none = gr >= rmax;
+    if (none || vec) {
+      cp16(S + (size_t)e * 16, none ? (const void*)X : (const void*)(X + gr * sr + 8 * c), !none);
+    } else {
+      uint16_t u[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) u[j] = X[gr * sr + 8 * c + j];
+      *reinterpret_cast<uint4*>(S + (size_t)e * 16) =
+          make_uint4(pack_u16(u[0], u[1]), pack_u16(u[2], u[3]), pack_u16(u[4], u[5]),
+                     pack_u16(u[6], u[7]));
+    }
+  }
+}
+
+// TMA: one box of 8 BF16 values (x: the first value, a multiple of 8) by the
+// map's box rows (y: the first row) into dst, completing on mbarrier mb; rows
+// beyond the matrix arrive as zeros.
+__device__ __forceinline__ void tma_box(unsigned char* dst, const CUtensorMap* map, int x, int y,
+                                        uint32_t mb) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(tc::saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb)
+      : "memory");
+}
+__device__ __forceinline__ void expect_tx(uint32_t mb, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+               : "memory");
+}
+
 // --------------------------------------------------------------------------
 // Inference forward, all three layers in one launch: a CTA of 256 threads
 // takes 128 rows of X, stages X and the BF16 weights in the K-major
@@ -377,6 +426,7 @@ struct TrainArgs {
   int* err;
   int polls;                          // polls of the main waits (clean-up: the default)
   unsigned* chk;                      // check word of the bounds-checking build (may be null)
+  int tma;                            // 1: X and the weights by TMA (tensor maps of the launch)
 };
 
 constexpr uint32_t kTrW1 = kHid * kIn * 2, kTrW2 = kHid * kHid * 2, kTrW3 = 16 * kHid * 2,
@@ -394,7 +444,10 @@ constexpr uint32_t kCZ1 = 0, kCZ2 = 128, kCG2 = 256, kCG1 = 384, kCY = 416, kCG3
 // instruction-descriptor bits: A / B read MN-major (transposed)
 constexpr uint32_t kTransA = 1u << 15, kTransB = 1u << 16;
 
-__global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
+__global__ void __launch_bounds__(kTrThreads, 1)
+    train_tc_kernel(TrainArgs a, const __grid_constant__ CUtensorMap mX,
+                    const __grid_constant__ CUtensorMap mW1, const __grid_constant__ CUtensorMap mW2,
+                    const __grid_constant__ CUtensorMap mW3) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* sW1 = tsm;
   unsigned char* sW2 = tsm + kTrOffW2;
@@ -407,10 +460,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   unsigned char* sDY = tsm + kTrOffDY;
   unsigned char* sOne = tsm + kTrOffOne;
   // mbar[0]: the layers and gW1 / gb1; mbar[1]: dH1; mbar[2]: gW2, gW3, gb2,
-  // so that the dZ1 epilogue runs while the weight-gradient MMAs do. A
-  // barrier never has more than one commit that is not waited for: a parity
-  // wait cannot tell a phase from the one two later
-  __shared__ __align__(8) uint64_t mbar[3];
+  // so that the dZ1 epilogue runs while the weight-gradient MMAs do; mbar[3]:
+  // the TMA copies. A barrier never has more than one arrival that is not
+  // waited for: a parity wait cannot tell a phase from the one two later
+  __shared__ __align__(8) uint64_t mbar[4];
   __shared__ uint32_t tmem_base;
   __shared__ float sb[2 * kHid + kOut];
   __shared__ float sw3[kOut][kHid];   // the BF16 W3 as FP32 (the dY W3 product)
@@ -426,11 +479,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   }
   const bool vecX = (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
   auto sX = [&](int t) { return sX0 + (size_t)((t / G) & 1) * kTrX; };
-  stage_k<kTrThreads>(sX(cta), a.X, kIn, vecX, (int64_t)cta * 128, a.n, 128, 0, kIn, kIn / 8, tid);
-  stage_k<kTrThreads>(sW1, a.w1, kIn, true, 0, kHid, kHid, 0, kIn, kIn / 8, tid);
-  stage_k<kTrThreads>(sW2, a.w2, kHid, true, 0, kHid, kHid, 0, kHid, kHid / 8, tid);
-  stage_k<kTrThreads>(sW3, a.w3, kHid, true, 0, kOut, 16, 0, kHid, kHid / 8, tid);   // rows 2..15 zero
-  cp_commit();
+  // X and the weights in the chunk-major layout: by TMA once the barriers
+  // exist (below), else by asynchronous copies here
+  if (!a.tma) {
+    stage_cm<kTrThreads>(sX(cta), a.X, kIn, vecX, (int64_t)cta * 128, a.n, 128, kIn / 8, tid);
+    stage_cm<kTrThreads>(sW1, a.w1, kIn, true, 0, kHid, 128, kIn / 8, tid);
+    stage_cm<kTrThreads>(sW2, a.w2, kHid, true, 0, kHid, 128, kHid / 8, tid);
+    stage_cm<kTrThreads>(sW3, a.w3, kHid, true, 0, kOut, 16, kHid / 8, tid);   // rows 2..15 zero
+    cp_commit();
+  }
   // dY (units 2..15 stay zero) and the ones operand (unit 0 one, the rest zero),
   // [sample][16] in the core-matrix layout
   for (int i = tid; i < (int)(kTrN16 / 16); i += kTrThreads) {
@@ -450,15 +507,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
         tc::saddr(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid < 3)
+  if (tid < 4)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[tid])) : "memory");
   cp_wait<0>();
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tm = tmem_base,
-                 s_bar[3] = {tc::saddr(&mbar[0]), tc::saddr(&mbar[1]), tc::saddr(&mbar[2])};
+  const uint32_t tm = tmem_base, s_bar[4] = {tc::saddr(&mbar[0]), tc::saddr(&mbar[1]),
+                                             tc::saddr(&mbar[2]), tc::saddr(&mbar[3])};
   const int quad = warp & 3, part4 = warp >> 2;   // lane quadrant; 32-column group
   const uint32_t lane_addr = tm + ((uint32_t)(quad * 32) << 16);
   const int r = quad * 32 + lane;   // this thread's row of a tile (TMEM lane)
@@ -466,7 +523,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   const float qnan = __int_as_float(0x7fffffff);
   // commits issued and waited for on each mbarrier (every thread counts them
   // alike); phases complete in issue order, each is waited for in turn
-  uint32_t issued[3] = {0u, 0u, 0u}, waited[3] = {0u, 0u, 0u};
+  uint32_t issued[4] = {0u, 0u, 0u, 0u}, waited[4] = {0u, 0u, 0u, 0u};
   int failed = -1;   // the barrier of a wait that gave up
   bool ok = true;
   auto commit = [&](int b) {
@@ -487,6 +544,21 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
   auto kdesc = [](const unsigned char* s, int kk, int kc) {
     return tc::smem_desc(tc::saddr(s) + kk * 256, 128, kc * 128);
   };
+  // chunk-major tile of R rows (X, the weights), read K-major or MN-major
+  auto ckdesc = [](const unsigned char* s, int kk, int R) {
+    return tc::smem_desc(tc::saddr(s) + kk * 2 * R * 16, R * 16, 128);
+  };
+  auto cmdesc = [](const unsigned char* s, int kk, int R) {
+    return tc::smem_desc(tc::saddr(s) + kk * 256, 128, R * 16);
+  };
+  // X of tile t by TMA: one box of 8 values x 128 rows per chunk
+  auto tma_x = [&](int t) {
+    if (tid == 0) {
+      expect_tx(s_bar[3], kTrX);
+      for (int c = 0; c < kIn / 8; ++c) tma_box(sX(t) + c * 2048, &mX, 8 * c, t * 128, s_bar[3]);
+    }
+    ++issued[3];
+  };
   // the same storage read MN-major, K = its rows (the samples): K-step kk
   // starts 2 core-matrix rows (2 kc 128 bytes) on; the leading offset steps
   // along K, the stride offset along M / N (8 units, 128 bytes)
@@ -497,13 +569,28 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
                      kIdG1 = tc::idesc_bf16(128, 32) | kTransA | kTransB,
                      kIdG2 = kIdH | kTransA | kTransB, kIdG16 = kIdO | kTransA | kTransB,
                      kIdDH = kIdH | kTransB;
-  // layer 1 of the first tile
-  if (tid == 0) {
-    tc::fence_after();
-    for (int kk = 0; kk < kIn / 16; ++kk)
-      tc::mma(tm + kCZ1, kdesc(sX(cta), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
+  if (a.tma) {
+    // the weights (W3 as its 16-row zero-padded copy) and the first X tile
+    if (tid == 0) {
+      expect_tx(s_bar[3], kTrW1 + kTrW2 + kTrW3 + kTrX);
+      for (int c = 0; c < kIn / 8; ++c) tma_box(sW1 + c * 2048, &mW1, 8 * c, 0, s_bar[3]);
+      for (int c = 0; c < kHid / 8; ++c) tma_box(sW2 + c * 2048, &mW2, 8 * c, 0, s_bar[3]);
+      for (int c = 0; c < kHid / 8; ++c) tma_box(sW3 + c * 256, &mW3, 8 * c, 0, s_bar[3]);
+      for (int c = 0; c < kIn / 8; ++c)
+        tma_box(sX(cta) + c * 2048, &mX, 8 * c, cta * 128, s_bar[3]);
+    }
+    ++issued[3];
+    ok = wait_bar(3);
   }
-  commit(0);
+  // layer 1 of the first tile
+  if (ok) {
+    if (tid == 0) {
+      tc::fence_after();
+      for (int kk = 0; kk < kIn / 16; ++kk)
+        tc::mma(tm + kCZ1, ckdesc(sX(cta), kk, 128), ckdesc(sW1, kk, 128), kIdH, kk > 0);
+    }
+    commit(0);
+  }
   // hidden-layer epilogue: with t = tanh((acc + bias) / 2), H = silu and
   // G = silu' (sigmoid s = (1 + t) / 2, silu' = s (1 + z (1 - s))) into their operands
   auto hidden = [&](uint32_t col, const float* bias, unsigned char* H, unsigned char* Gd) {
@@ -555,14 +642,18 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
     // back, has completed)
     const int tn = t + G;
     if (tn < a.ntiles) {
-      stage_k<kTrThreads>(sX(tn), a.X, kIn, vecX, (int64_t)tn * 128, a.n, 128, 0, kIn, kIn / 8, tid);
-      cp_commit();
+      if (a.tma) {
+        tma_x(tn);
+      } else {
+        stage_cm<kTrThreads>(sX(tn), a.X, kIn, vecX, (int64_t)tn * 128, a.n, 128, kIn / 8, tid);
+        cp_commit();
+      }
     }
     hidden(kCZ1, sb, sH1, sG1);
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
-        tc::mma(tm + kCZ2, kdesc(sH1, kk, kHid / 8), kdesc(sW2, kk, kHid / 8), kIdH, kk > 0);
+        tc::mma(tm + kCZ2, kdesc(sH1, kk, kHid / 8), ckdesc(sW2, kk, 128), kIdH, kk > 0);
     }
     commit(0);
     if (!(ok = wait_bar(0))) break;
@@ -570,7 +661,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
-        tc::mma(tm + kCY, kdesc(sH2, kk, kHid / 8), kdesc(sW3, kk, kHid / 8), kIdO, kk > 0);
+        tc::mma(tm + kCY, kdesc(sH2, kk, kHid / 8), ckdesc(sW3, kk, 16), kIdO, kk > 0);
     }
     commit(0);
     if (!(ok = wait_bar(0))) break;
@@ -623,7 +714,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
     if (tid == 0) {
       tc::fence_after();
       for (int kk = 0; kk < kHid / 16; ++kk)
-        tc::mma(tm + kCZ2, kdesc(sG2, kk, kHid / 8), mdesc(sW2, kk, kHid / 8), kIdDH, kk > 0);
+        tc::mma(tm + kCZ2, kdesc(sG2, kk, kHid / 8), cmdesc(sW2, kk, 128), kIdDH, kk > 0);
     }
     commit(1);
     if (tid == 0) {
@@ -652,7 +743,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
                          pack_bf16(g[6], g[7]));
       }
     }
-    if (tn < a.ntiles) cp_wait<0>();   // the next tile's X has landed
+    if (tn < a.ntiles) {   // the next tile's X has landed
+      if (a.tma) {
+        if (!(ok = wait_bar(3))) break;
+      } else {
+        cp_wait<0>();
+      }
+    }
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
@@ -661,12 +758,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
       tc::fence_after();
       for (int kk = 0; kk < 128 / 16; ++kk) {
         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-        tc::mma(tm + kCG1, mdesc(sG1, kk, kHid / 8), mdesc(sX(t), kk, kIn / 8), kIdG1, acc);
+        tc::mma(tm + kCG1, mdesc(sG1, kk, kHid / 8), cmdesc(sX(t), kk, 128), kIdG1, acc);
         tc::mma(tm + kCB1, mdesc(sG1, kk, kHid / 8), mdesc(sOne, kk, 2), kIdG16, acc);
       }
       if (tn < a.ntiles)
         for (int kk = 0; kk < kIn / 16; ++kk)
-          tc::mma(tm + kCZ1, kdesc(sX(tn), kk, kIn / 8), kdesc(sW1, kk, kIn / 8), kIdH, kk > 0);
+          tc::mma(tm + kCZ1, ckdesc(sX(tn), kk, 128), ckdesc(sW1, kk, 128), kIdH, kk > 0);
     }
     commit(0);
     first = false;
@@ -720,7 +817,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tc_kernel(TrainArgs a) {
     for (int i = tid; i < kPart; i += kTrThreads) part[i] = qnan;
     // MMAs may still be in flight: bounded waits, in order, for every commit
     // not seen to complete (the one a wait gave up on included) before TMEM is freed
-    for (int b = 0; b < 3; ++b)
+    for (int b = 0; b < 4; ++b)
       for (uint32_t w = waited[b] - (b == failed ? 1u : 0u); w < issued[b]; ++w)
         tc::wait_phase(s_bar[b], w & 1u);
   }
@@ -1033,7 +1130,9 @@ struct sdcef_mlp {
   int64_t max_rows;
   cudaStream_t st;
   float *p, *g, *m, *v;                 // FP32 parameters, gradients, Adam moments
-  __nv_bfloat16 *w1, *w2, *w3;          // BF16 weight copies
+  __nv_bfloat16 *w1, *w2, *w3;          // BF16 weight copies (W3 zero-padded to 16 rows)
+  CUtensorMap mw[3];                    // tensor maps of W1, W2, W3 (TMA boxes of 8 values)
+  int tma_w;                            // the weight maps could be encoded
   float *Y, *loss;                      // output, loss (FP32)
   float* part;                          // [sms][kPart] per-CTA partials of the training kernel
   __nv_bfloat16* X;                     // [max_rows][32] staging area of the guess
@@ -1051,6 +1150,33 @@ unsigned* mlp_chk(sdcef_mlp* h) { return reinterpret_cast<unsigned*>(h->loss) + 
 namespace {
 
 int cuda_fail(cudaError_t e) { return report_error(SDCEF_ERR_CUDA, cudaGetErrorString(e)); }
+
+// Tensor map of a row-major BF16 matrix [rows][cols], read in boxes of 8
+// values (16 bytes) x box_rows rows: box c of a tile lands as box_rows 16-byte
+// rows, the chunk-major layout of the training kernel; rows beyond the matrix
+// arrive as zeros. False if it cannot be encoded (the kernel then stages by
+// cp.async).
+bool tma_rows(CUtensorMap* m, const void* base, int64_t rows, int cols, int box_rows) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  memset(m, 0, sizeof(*m));
+  if (!encode || (reinterpret_cast<uintptr_t>(base) & 15) || ((cols * 2) & 15) || rows < 1 ||
+      cols % 8)
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {8, (cuuint32_t)box_rows}, estr[2] = {1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // forward through the three layers for n rows of X: Y (FP32 [n][2])
 cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n, float* Y) {
@@ -1096,7 +1222,9 @@ cudaError_t train(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t 
   a.err = (int*)h->loss + 5;
   a.polls = h->polls;
   a.chk = mlp_chk(h);
-  train_tc_kernel<<<grid, kTrThreads, kTrSmem, h->st>>>(a);
+  CUtensorMap mx;
+  a.tma = (h->tma_w && tma_rows(&mx, X, n, kIn, 128)) ? 1 : 0;
+  train_tc_kernel<<<grid, kTrThreads, kTrSmem, h->st>>>(a, mx, h->mw[0], h->mw[1], h->mw[2]);
   ++h->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1174,7 +1302,7 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
   struct Alloc { void** p; size_t bytes; } al[] = {
       {(void**)&h->p, kNParam * 4}, {(void**)&h->g, kNParam * 4}, {(void**)&h->m, kNParam * 4},
       {(void**)&h->v, kNParam * 4}, {(void**)&h->w1, kHid * kIn * 2}, {(void**)&h->w2, kHid * kHid * 2},
-      {(void**)&h->w3, kOut * kHid * 2}, {(void**)&h->Y, R * kOut * 4}, {(void**)&h->loss, 64},
+      {(void**)&h->w3, 16 * kHid * 2}, {(void**)&h->Y, R * kOut * 4}, {(void**)&h->loss, 64},
       {(void**)&h->part, (size_t)h->sms * kPart * 4}, {(void**)&h->X, R * kIn * 2}};
   for (auto& a : al) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -1185,6 +1313,8 @@ int sdcef_mlp_create(sdcef_mlp** out, int64_t max_rows, void* stream) {
       return report_error(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
     }
   }
+  h->tma_w = tma_rows(&h->mw[0], h->w1, kHid, kIn, 128) && tma_rows(&h->mw[1], h->w2, kHid, kHid, 128) &&
+             tma_rows(&h->mw[2], h->w3, 16, kHid, 16);
   *out = h;
   return SDCEF_SUCCESS;
 }
