@@ -28,6 +28,7 @@
 // of the 2x2 off-diagonal blocks of Eq. linear_nls is zero because
 // dF_phi/dn is diagonal) and every multiply-accumulate is one FMA chain.
 #pragma once
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "checks.cuh"
@@ -186,31 +187,55 @@ __device__ __forceinline__ Mat<2, R> minv(const Mat<2, R>& x, bool* bad) {
 
 template <int NB> struct FIdx;
 
-// Plane storage: a plane holds one value per (row j, thread t) at j*TPB + t.
+// Factor storage: NB x NB blocks, one per (row j, thread t), in groups of
+// NB^2 planes: the block of group k0 for row j of thread t holds its NB^2
+// values contiguously at k0 PL + (j TPB + t) NB^2, so that a warp reads a row's
+// blocks as one contiguous run and a 2 x 2 block of 8-byte values is two
+// 16-byte loads (a block smaller than 16 bytes is read value by value).
 template <int NB, typename R, int TPB>
 struct Planes {
   R* p;
   size_t PL;   // elements per plane
+  static constexpr int NN = NB * NB;
+  static constexpr bool kVec = (NN * sizeof(R)) % 16 == 0 && sizeof(Mat<NB, R>) == NN * sizeof(R);
   // checked element offset of block (k0, row j, thread t): k0 .. k0 + NB^2 - 1
   // must be factor planes and j * TPB + t an element of a plane
   __device__ __forceinline__ size_t at(int k0, int j, int t) const {
-    if (!SDCEF_CHECK(k0 >= 0 && k0 + NB * NB <= FIdx<NB>::NPLANES && j >= 0 && t >= 0 &&
+    if (!SDCEF_CHECK(k0 >= 0 && k0 + NN <= FIdx<NB>::NPLANES && j >= 0 && t >= 0 &&
                          t < TPB && (size_t)j * TPB + t < PL,
                      sdcef_chk::kFacPlane))
       return 0;
-    return (size_t)k0 * PL + (size_t)j * TPB + t;
+    return (size_t)k0 * PL + ((size_t)j * TPB + t) * NN;
   }
   __device__ __forceinline__ Mat<NB, R> ldm(int k0, int j, int t) const {
     Mat<NB, R> m;
     const size_t o = at(k0, j, t);
+    if constexpr (kVec) {
+      constexpr int NV = NN * sizeof(R) / 16;
+      const uint4* s = reinterpret_cast<const uint4*>(p + o);
+      uint4 u[NV];
 #pragma unroll
-    for (int k = 0; k < NB * NB; ++k) m.a[k] = p[o + (size_t)k * PL];
+      for (int i = 0; i < NV; ++i) u[i] = s[i];
+      memcpy(&m, u, sizeof(m));
+    } else {
+#pragma unroll
+      for (int k = 0; k < NN; ++k) m.a[k] = p[o + k];
+    }
     return m;
   }
   __device__ __forceinline__ void stm(int k0, int j, int t, const Mat<NB, R>& m) const {
     const size_t o = at(k0, j, t);
+    if constexpr (kVec) {
+      constexpr int NV = NN * sizeof(R) / 16;
+      uint4 u[NV];
+      memcpy(u, &m, sizeof(m));
+      uint4* d = reinterpret_cast<uint4*>(p + o);
 #pragma unroll
-    for (int k = 0; k < NB * NB; ++k) p[o + (size_t)k * PL] = m.a[k];
+      for (int i = 0; i < NV; ++i) d[i] = u[i];
+    } else {
+#pragma unroll
+      for (int k = 0; k < NN; ++k) p[o + k] = m.a[k];
+    }
   }
 };
 
