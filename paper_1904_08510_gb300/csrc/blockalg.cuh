@@ -572,12 +572,14 @@ __device__ void part_factor(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, int kt, in
 }
 
 // Solve with the factors of part_factor. rhs and out are NB planes each of the
-// caller's type IO (row j of thread t at j*TPB + t); scr are NB planes of R
-// for the intermediate sweeps (scr may alias out when IO is R; out may alias
-// rhs). sh must hold 3 * TPB * NB values of R. UT as for part_factor.
+// caller's type IO (row j of thread t at j*TPB + t; out may alias rhs); scr is
+// the scratch of the intermediate sweeps, NB planes of R holding the NB values
+// of row j of thread t contiguously at (j TPB + t) NB (one 16-byte access where
+// they fill 16 bytes). sh must hold 3 * TPB * NB values of R. UT as for
+// part_factor.
 template <int NB, typename R, typename IO, int TPB, bool UT>
 __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* rhs,
-                           IO* const* out, R* const* scr, int kt, int tid, int tact, R* sh,
+                           IO* const* out, R* scr, int kt, int tid, int tact, R* sh,
                            double* nrm2 = nullptr) {
   using FI = FIdx<NB>;
   const int m = kt - 1;
@@ -595,17 +597,29 @@ __device__ void part_solve(Planes<NB, R, TPB> F, Scal<NB, R, TPB> S, IO* const* 
     for (int k = 0; k < NB; ++k) v.a[k] = conv<R>(rhs[k][e]);
     return v;
   };
+  constexpr bool kVecS = NB * sizeof(R) == 16 && sizeof(Vec<NB, R>) == 16;
   auto lds = [&](int j) {
     Vec<NB, R> v;
-    const size_t e = el(j);
+    const size_t e = el(j) * NB;
+    if constexpr (kVecS) {
+      const uint4 u = *reinterpret_cast<const uint4*>(scr + e);
+      memcpy(&v, &u, sizeof(v));
+    } else {
 #pragma unroll
-    for (int k = 0; k < NB; ++k) v.a[k] = scr[k][e];
+      for (int k = 0; k < NB; ++k) v.a[k] = scr[e + k];
+    }
     return v;
   };
   auto sts = [&](int j, const Vec<NB, R>& v) {
-    const size_t e = el(j);
+    const size_t e = el(j) * NB;
+    if constexpr (kVecS) {
+      uint4 u;
+      memcpy(&u, &v, sizeof(v));
+      *reinterpret_cast<uint4*>(scr + e) = u;
+    } else {
 #pragma unroll
-    for (int k = 0; k < NB; ++k) scr[k][e] = v.a[k];
+      for (int k = 0; k < NB; ++k) scr[e + k] = v.a[k];
+    }
   };
   // stores a row of the solution; with nrm2, also adds the squares of the
   // stored values (this thread's part of ||out||_2^2)

@@ -976,7 +976,7 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
     Scal<2, PR, TPB> Sc{S.s};
     KR* rin[2] = {re, rp};
     KR* out[2] = {ze, zp};
-    PR* scr[2] = {S.f + (size_t)kScrPlane * S.PL, S.f + (size_t)(kScrPlane + 1) * S.PL};
+    PR* scr = S.f + (size_t)kScrPlane * S.PL;   // two planes, a row's pair contiguous
     part_solve<2, PR, KR, TPB, true>(F, Sc, rin, out, scr, kt, tid, g.tact, sh,
                                      want_norm ? &s : nullptr);
     have_s = true;
@@ -984,7 +984,7 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
     Planes<1, PR, TPB> F1{S.f, S.PL};
     Planes<1, PR, TPB> F2{S.f + 5 * S.PL, S.PL};
     const PR* Bpl = S.f + 10 * S.PL;
-    PR* scr[1] = {S.f + (size_t)kScrPlane * S.PL};
+    PR* scr = S.f + (size_t)kScrPlane * S.PL;
     Scal<1, PR, TPB> S1{S.s};
     Scal<1, PR, TPB> S2{S.s + FIdx<1>::NSCAL * TPB};
     const KR cfac = (KR)cs.r_c;   // -Chat
@@ -1033,7 +1033,7 @@ __device__ __noinline__ double prec_apply(const KArgs& a, const Geo& g, ColShare
       // (or exactly, where that block's tolerance is <= 0)
       const MgArea M = mg_slot_area(S);
       const PR* Bpl = S.f + 10 * S.PL;
-      PR* scr[1] = {S.f + (size_t)kScrPlane * S.PL};
+      PR* scr = S.f + (size_t)kScrPlane * S.PL;
       auto blk_solve = [&](int blk, KR* rin_, KR* out_) {
         if ((blk == 0 ? a.p.mg_gA : a.p.mg_gS) > 0.0) {
           const int k = mg_solve<TPB>(a, g, M, blk, rin_, out_, red);
