@@ -470,6 +470,9 @@ __global__ void __launch_bounds__(kTrThreads, 1)
   __shared__ float sacc[4][3];        // per lane quadrant: loss, gb3 (one writer each)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x, G = gridDim.x;
+  // launched early behind the previous kernel of the stream (programmatic
+  // dependent launch): nothing that kernel writes is read before it completes
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   // a CTA without a tile (the host sizes the grid so that there is none)
   // contributes a zero partial
   if (cta >= a.ntiles) {
@@ -821,6 +824,9 @@ __global__ void __launch_bounds__(kTrThreads, 1)
       for (uint32_t w = waited[b] - (b == failed ? 1u : 0u); w < issued[b]; ++w)
         tc::wait_phase(s_bar[b], w & 1u);
   }
+  // the partial is written: the summing kernel may launch (it still waits for
+  // this grid to complete before it reads)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   tc::fence_before();
   __syncthreads();
   if (warp == 0)
@@ -840,6 +846,7 @@ __global__ void __launch_bounds__(256) part_reduce_kernel(const float* part, int
   __shared__ float s[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + tx;
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // the training kernel has completed
   float acc = 0.0f;
   if (i < kNParam + 1) {
     // four independent loads in flight per thread; the order of the sums is fixed
@@ -1198,6 +1205,30 @@ cudaError_t forward(sdcef_mlp* h, const __nv_bfloat16* X, int64_t n, float* Y) {
   return cudaGetLastError();
 }
 
+// A launch that may start while the previous kernel of the stream finishes
+// (programmatic dependent launch; the kernel waits for it with
+// griddepcontrol.wait before it reads that kernel's results). Falls back to a
+// plain launch where the attribute is refused.
+template <typename... KT, typename... AT>
+cudaError_t launch_early(void (*k)(KT...), unsigned grid, unsigned block, size_t smem,
+                         cudaStream_t st, AT... args) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k, args...) == cudaSuccess) return cudaSuccess;
+  (void)cudaGetLastError();
+  k<<<grid, block, smem, st>>>(args...);
+  return cudaGetLastError();
+}
+
 // forward, loss and backward over n rows (train_tc_kernel), then the sum of
 // the CTAs' partials: the Adam step (adam) or the gradient into h->g; the loss
 // into h->loss[0]. The grid spreads the 128-row tiles evenly over at most one
@@ -1224,25 +1255,26 @@ cudaError_t train(sdcef_mlp* h, const __nv_bfloat16* X, const float* T, int64_t 
   a.chk = mlp_chk(h);
   CUtensorMap mx;
   a.tma = (h->tma_w && tma_rows(&mx, X, n, kIn, 128)) ? 1 : 0;
-  train_tc_kernel<<<grid, kTrThreads, kTrSmem, h->st>>>(a, mx, h->mw[0], h->mw[1], h->mw[2]);
+  cudaError_t e = launch_early(train_tc_kernel, (unsigned)grid, kTrThreads, kTrSmem, h->st, a, mx,
+                               h->mw[0], h->mw[1], h->mw[2]);
   ++h->launches;
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((kNParam + 1 + 31) / 32);
   if (adam) {
     h->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)h->step), c2 = 1.0f - powf(b2, (float)h->step);
-    part_reduce_kernel<true><<<blocks, 256, 0, h->st>>>(h->part, grid, h->g, h->loss, h->p, h->m,
-                                                         h->v, lr, b1, b2, 1e-8f, c1, c2, h->w1,
-                                                         h->w2, h->w3);
+    e = launch_early(part_reduce_kernel<true>, blocks, 256, 0, h->st, (const float*)h->part, grid,
+                     h->g, h->loss, h->p, h->m, h->v, lr, b1, b2, 1e-8f, c1, c2, h->w1, h->w2,
+                     h->w3);
   } else {
-    part_reduce_kernel<false><<<blocks, 256, 0, h->st>>>(h->part, grid, h->g, h->loss, nullptr,
-                                                          nullptr, nullptr, 0.0f, 0.0f, 0.0f, 0.0f,
-                                                          0.0f, 0.0f, nullptr, nullptr, nullptr);
+    e = launch_early(part_reduce_kernel<false>, blocks, 256, 0, h->st, (const float*)h->part, grid,
+                     h->g, h->loss, (float*)nullptr, (float*)nullptr, (float*)nullptr, 0.0f, 0.0f,
+                     0.0f, 0.0f, 0.0f, 0.0f, (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr,
+                     (__nv_bfloat16*)nullptr);
   }
   ++h->launches;
-  return cudaGetLastError();
+  return e;
 }
 
 FeatArgs feat_args(const sdcef_batch* b) {
