@@ -470,16 +470,32 @@ __global__ void __launch_bounds__(kTrThreads, 1)
   __shared__ float sacc[4][3];        // per lane quadrant: loss, gb3 (one writer each)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x, G = gridDim.x;
-  // launched early behind the previous kernel of the stream (programmatic
-  // dependent launch): nothing that kernel writes is read before it completes
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  // a CTA without a tile (the host sizes the grid so that there is none)
-  // contributes a zero partial
+  // The kernel may be launched early behind the previous kernel of the stream
+  // (programmatic dependent launch): until griddepcontrol.wait it touches only
+  // its own shared and tensor memory, nothing that kernel reads or writes.
+  // A CTA without a tile (the host sizes the grid so that there is none)
+  // contributes a zero partial.
   if (cta >= a.ntiles) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     (void)SDCEF_CHECK_W(a.chk, false, sdcef_chk::kMlpRow);
     for (int i = tid; i < kPart; i += kTrThreads) a.part[(size_t)cta * kPart + i] = 0.0f;
     return;
   }
+  // dY (units 2..15 stay zero) and the ones operand (unit 0 one, the rest zero),
+  // [sample][16] in the core-matrix layout; TMEM; the barriers
+  for (int i = tid; i < (int)(kTrN16 / 16); i += kTrThreads) {
+    reinterpret_cast<uint4*>(sDY)[i] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(sOne)[i] = make_uint4((i & 8) ? 0u : 0x3F80u, 0u, 0u, 0u);
+  }
+  if (tid < 12) sacc[tid / 3][tid % 3] = 0.0f;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        tc::saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid < 4)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[tid])) : "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const bool vecX = (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
   auto sX = [&](int t) { return sX0 + (size_t)((t / G) & 1) * kTrX; };
   // X and the weights in the chunk-major layout: by TMA once the barriers
@@ -491,27 +507,13 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     stage_cm<kTrThreads>(sW3, a.w3, kHid, true, 0, kOut, 16, kHid / 8, tid);   // rows 2..15 zero
     cp_commit();
   }
-  // dY (units 2..15 stay zero) and the ones operand (unit 0 one, the rest zero),
-  // [sample][16] in the core-matrix layout
-  for (int i = tid; i < (int)(kTrN16 / 16); i += kTrThreads) {
-    reinterpret_cast<uint4*>(sDY)[i] = make_uint4(0u, 0u, 0u, 0u);
-    reinterpret_cast<uint4*>(sOne)[i] = make_uint4((i & 8) ? 0u : 0x3F80u, 0u, 0u, 0u);
-  }
   for (int i = tid; i < kHid; i += kTrThreads) {
     sb[i] = a.p[kOffB1 + i];
     sb[kHid + i] = a.p[kOffB2 + i];
   }
   if (tid < kOut) sb[2 * kHid + tid] = a.p[kOffB3 + tid];
-  if (tid < 12) sacc[tid / 3][tid % 3] = 0.0f;
   for (int i = tid; i < kOut * kHid; i += kTrThreads)
     sw3[i / kHid][i % kHid] = __uint_as_float((uint32_t)a.w3[i] << 16);
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-        tc::saddr(&tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid < 4)
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[tid])) : "memory");
   cp_wait<0>();
   tc::fence_async_smem();
   tc::fence_before();
@@ -847,6 +849,8 @@ __global__ void __launch_bounds__(256) part_reduce_kernel(const float* part, int
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + tx;
   asm volatile("griddepcontrol.wait;" ::: "memory");   // the training kernel has completed
+  // the next training step may launch; it waits for this kernel before it reads
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   float acc = 0.0f;
   if (i < kNParam + 1) {
     // four independent loads in flight per thread; the order of the sums is fixed
