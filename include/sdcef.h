@@ -270,6 +270,18 @@ int sdcef_solve_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef_resu
  * solves, copies the results back and synchronises the stream. */
 int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* batch, const sdcef_result* out);
 
+/* Solve nbatch batches given in host memory, one after another, with the
+ * copies overlapping the solves: the inputs of batch k + 1 go to the device
+ * and the results of batch k - 1 come back while batch k is solved (two
+ * staging halves owned by the context, one copy stream each way). batches[k]
+ * and out[k] follow the rules of sdcef_solve_batch_host; every batch fits the
+ * context (max_cols, max_cells, max_col_cells). Returns when all results are in
+ * host memory; on an error the batches not yet solved are not solved. Host
+ * buffers should be pinned for the copies to overlap. Not part of the paper:
+ * the serving form of the batched solve. */
+int sdcef_solve_batches_host(sdcef_ctx* ctx, int nbatch, const sdcef_batch* batches,
+                             const sdcef_result* out);
+
 /* Evaluate the residual F(X) of Eq. nls at X = (ne, phi) for every column
  * (device pointers, [cells] each). Enqueued on the context stream. */
 int sdcef_residual_batch(sdcef_ctx* ctx, const sdcef_batch* batch, const double* ne,

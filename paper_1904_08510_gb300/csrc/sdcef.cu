@@ -52,6 +52,11 @@ struct sdcef_ctx {
   // host-call staging
   char* stage;
   size_t stage_bytes;
+  // double-buffered host calls: copy streams (host to device, device to host)
+  // and, per staging half, inputs staged / solved / half free again
+  cudaStream_t cs[2];
+  cudaEvent_t ev_in[2], ev_done[2], ev_free[2];
+  bool pipe;
   // electron transport tables (mu then D, [nc][nx] each), device
   double* tab;
   int tab_nc, tab_nx;
@@ -338,6 +343,15 @@ int sdcef_destroy(sdcef_ctx* ctx) {
   cudaFree(ctx->order);
   if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->tab) cudaFree(ctx->tab);
+  if (ctx->pipe) {
+    for (int i = 0; i < 2; ++i) {
+      cudaStreamSynchronize(ctx->cs[i]);
+      cudaStreamDestroy(ctx->cs[i]);
+      cudaEventDestroy(ctx->ev_in[i]);
+      cudaEventDestroy(ctx->ev_done[i]);
+      cudaEventDestroy(ctx->ev_free[i]);
+    }
+  }
   delete ctx;
   return SDCEF_SUCCESS;
 }
@@ -702,111 +716,230 @@ int sdcef_precond_apply_batch(sdcef_ctx* ctx, const sdcef_batch* b, const double
   return run(ctx, a, tpb);
 }
 
-int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_result* ho) {
-  Range range_("sdcef_solve_batch_host");
-  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
-  int rc = validate_batch(ctx, hb, true);
-  if (rc) return rc;
-  if (!ho || !ho->ne_out || !ho->phi_out) return set_err(SDCEF_ERR_INVALID, "result: ne_out / phi_out is NULL");
-  const int64_t ncol = hb->ncol;
-  if (ncol == 0) return SDCEF_SUCCESS;
-  const int64_t cells = hb->col_off[ncol];
-  if (cells > ctx->max_cells || cells < 0) return set_err(SDCEF_ERR_CAPACITY, "batch: cells exceed max_cells");
-  const int nsp = hb->n_species;
-  // staging layout (bytes)
-  struct Item { const void* src; void* dst_host; size_t bytes; };
+}  // extern "C"
+
+namespace {
+
+// Layout of one host batch in a device staging area: inputs, then results
+// (byte offsets, each 256-byte aligned).
+struct Stage {
+  size_t off, len, dt, vl, vr, ne, ph, ion, T, u, ir, ng, pg, neo, pho, st, nt, kt, re, fr, mg;
+  size_t need;
+};
+
+Stage stage_layout(const sdcef_batch* hb) {
+  Stage L;
   size_t need = 0;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int64_t ncol = hb->ncol, cells = hb->col_off[ncol];
   const size_t c8 = (size_t)cells * 8, n8 = (size_t)ncol * 8, n4 = (size_t)ncol * 4;
-  size_t o_off = need; need += al((size_t)(ncol + 1) * 8);
-  size_t o_len = need; need += al(n8);
-  size_t o_dt = need; need += al(n8);
-  size_t o_vl = need; need += al(n8);
-  size_t o_vr = need; need += al(n8);
-  size_t o_ne = need; need += al(c8);
-  size_t o_ph = need; need += al(c8);
-  size_t o_ion = need; need += al(c8 * (size_t)std::max(nsp, 1));
-  size_t o_T = need; need += al(c8);
-  size_t o_u = need; if (hb->u_adv) need += al(c8);
-  size_t o_ir = need; if (hb->i_re) need += al(c8);
-  size_t o_ng = need; if (hb->ne_guess) need += al(c8);
-  size_t o_pg = need; if (hb->phi_guess) need += al(c8);
-  size_t o_neo = need; need += al(c8);
-  size_t o_pho = need; need += al(c8);
-  size_t o_st = need; need += al(n4);
-  size_t o_nt = need; need += al(n4);
-  size_t o_kt = need; need += al(n4);
-  size_t o_re = need; need += al(n4);
-  size_t o_fr = need; need += al(n8);
-  size_t o_mg = need; need += al(n4);
-  if (need > ctx->stage_bytes) {
-    if (ctx->stage) cudaFree(ctx->stage);
-    ctx->stage = nullptr;
-    ctx->stage_bytes = 0;
-    // sized for the context capacity so later calls never reallocate
-    size_t cap = need * 2;
-    cudaError_t e = cudaMalloc((void**)&ctx->stage, cap);
-    if (e != cudaSuccess) return set_err(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
-    ctx->stage_bytes = cap;
-  }
-  char* d = ctx->stage;
-  cudaStream_t st = ctx->stream;
+  const int nsp = hb->n_species;
+  L.off = need; need += al((size_t)(ncol + 1) * 8);
+  L.len = need; need += al(n8);
+  L.dt = need; need += al(n8);
+  L.vl = need; need += al(n8);
+  L.vr = need; need += al(n8);
+  L.ne = need; need += al(c8);
+  L.ph = need; need += al(c8);
+  L.ion = need; need += al(c8 * (size_t)std::max(nsp, 1));
+  L.T = need; need += al(c8);
+  L.u = need; if (hb->u_adv) need += al(c8);
+  L.ir = need; if (hb->i_re) need += al(c8);
+  L.ng = need; if (hb->ne_guess) need += al(c8);
+  L.pg = need; if (hb->phi_guess) need += al(c8);
+  L.neo = need; need += al(c8);
+  L.pho = need; need += al(c8);
+  L.st = need; need += al(n4);
+  L.nt = need; need += al(n4);
+  L.kt = need; need += al(n4);
+  L.re = need; need += al(n4);
+  L.fr = need; need += al(n8);
+  L.mg = need; need += al(n4);
+  L.need = need;
+  return L;
+}
+
+// host -> staging copies of the batch's inputs on stream st
+cudaError_t stage_in(const Stage& L, char* d, const sdcef_batch* hb, cudaStream_t st) {
+  const int64_t ncol = hb->ncol, cells = hb->col_off[ncol];
+  const size_t c8 = (size_t)cells * 8, n8 = (size_t)ncol * 8;
   auto h2d = [&](size_t o, const void* src, size_t bytes) {
     return cudaMemcpyAsync(d + o, src, bytes, cudaMemcpyHostToDevice, st);
   };
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = h2d(o_off, hb->col_off, (size_t)(ncol + 1) * 8);
-  if (e == cudaSuccess) e = h2d(o_len, hb->length, n8);
-  if (e == cudaSuccess) e = h2d(o_dt, hb->dt, n8);
-  if (e == cudaSuccess) e = h2d(o_vl, hb->v_left, n8);
-  if (e == cudaSuccess) e = h2d(o_vr, hb->v_right, n8);
-  if (e == cudaSuccess) e = h2d(o_ne, hb->ne_old, c8);
-  if (e == cudaSuccess) e = h2d(o_ph, hb->phi_old, c8);
-  if (e == cudaSuccess && nsp > 0) e = h2d(o_ion, hb->n_ion, c8 * nsp);
-  if (e == cudaSuccess) e = h2d(o_T, hb->T, c8);
-  if (e == cudaSuccess && hb->u_adv) e = h2d(o_u, hb->u_adv, c8);
-  if (e == cudaSuccess && hb->i_re) e = h2d(o_ir, hb->i_re, c8);
-  if (e == cudaSuccess && hb->ne_guess) e = h2d(o_ng, hb->ne_guess, c8);
-  if (e == cudaSuccess && hb->phi_guess) e = h2d(o_pg, hb->phi_guess, c8);
-  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
-  sdcef_batch db = *hb;
-  db.col_off = (const int64_t*)(d + o_off);
-  db.length = (const double*)(d + o_len);
-  db.dt = (const double*)(d + o_dt);
-  db.v_left = (const double*)(d + o_vl);
-  db.v_right = (const double*)(d + o_vr);
-  db.ne_old = (const double*)(d + o_ne);
-  db.phi_old = (const double*)(d + o_ph);
-  db.n_ion = nsp > 0 ? (const double*)(d + o_ion) : nullptr;
-  db.T = (const double*)(d + o_T);
-  db.rho = nullptr;
-  db.u_adv = hb->u_adv ? (const double*)(d + o_u) : nullptr;
-  db.i_re = hb->i_re ? (const double*)(d + o_ir) : nullptr;
-  db.ne_guess = hb->ne_guess ? (const double*)(d + o_ng) : nullptr;
-  db.phi_guess = hb->phi_guess ? (const double*)(d + o_pg) : nullptr;
-  sdcef_result dr;
-  dr.ne_out = (double*)(d + o_neo);
-  dr.phi_out = (double*)(d + o_pho);
-  dr.status = (int*)(d + o_st);
-  dr.newton_it = (int*)(d + o_nt);
-  dr.krylov_it = (int*)(d + o_kt);
-  dr.res_evals = (int*)(d + o_re);
-  dr.final_res = (double*)(d + o_fr);
-  dr.mg_cycles = (int*)(d + o_mg);
-  rc = sdcef_solve_batch(ctx, &db, &dr);
-  if (rc) return rc;
+  cudaError_t e = h2d(L.off, hb->col_off, (size_t)(ncol + 1) * 8);
+  if (e == cudaSuccess) e = h2d(L.len, hb->length, n8);
+  if (e == cudaSuccess) e = h2d(L.dt, hb->dt, n8);
+  if (e == cudaSuccess) e = h2d(L.vl, hb->v_left, n8);
+  if (e == cudaSuccess) e = h2d(L.vr, hb->v_right, n8);
+  if (e == cudaSuccess) e = h2d(L.ne, hb->ne_old, c8);
+  if (e == cudaSuccess) e = h2d(L.ph, hb->phi_old, c8);
+  if (e == cudaSuccess && hb->n_species > 0) e = h2d(L.ion, hb->n_ion, c8 * hb->n_species);
+  if (e == cudaSuccess) e = h2d(L.T, hb->T, c8);
+  if (e == cudaSuccess && hb->u_adv) e = h2d(L.u, hb->u_adv, c8);
+  if (e == cudaSuccess && hb->i_re) e = h2d(L.ir, hb->i_re, c8);
+  if (e == cudaSuccess && hb->ne_guess) e = h2d(L.ng, hb->ne_guess, c8);
+  if (e == cudaSuccess && hb->phi_guess) e = h2d(L.pg, hb->phi_guess, c8);
+  return e;
+}
+
+// the device views of the staged batch and of its result slots
+void stage_views(const Stage& L, char* d, const sdcef_batch* hb, sdcef_batch* db,
+                 sdcef_result* dr) {
+  *db = *hb;
+  db->col_off = (const int64_t*)(d + L.off);
+  db->length = (const double*)(d + L.len);
+  db->dt = (const double*)(d + L.dt);
+  db->v_left = (const double*)(d + L.vl);
+  db->v_right = (const double*)(d + L.vr);
+  db->ne_old = (const double*)(d + L.ne);
+  db->phi_old = (const double*)(d + L.ph);
+  db->n_ion = hb->n_species > 0 ? (const double*)(d + L.ion) : nullptr;
+  db->T = (const double*)(d + L.T);
+  db->rho = nullptr;
+  db->u_adv = hb->u_adv ? (const double*)(d + L.u) : nullptr;
+  db->i_re = hb->i_re ? (const double*)(d + L.ir) : nullptr;
+  db->ne_guess = hb->ne_guess ? (const double*)(d + L.ng) : nullptr;
+  db->phi_guess = hb->phi_guess ? (const double*)(d + L.pg) : nullptr;
+  dr->ne_out = (double*)(d + L.neo);
+  dr->phi_out = (double*)(d + L.pho);
+  dr->status = (int*)(d + L.st);
+  dr->newton_it = (int*)(d + L.nt);
+  dr->krylov_it = (int*)(d + L.kt);
+  dr->res_evals = (int*)(d + L.re);
+  dr->final_res = (double*)(d + L.fr);
+  dr->mg_cycles = (int*)(d + L.mg);
+}
+
+// staging -> host copies of the results the caller asked for, on stream st
+cudaError_t stage_out(const Stage& L, char* d, const sdcef_batch* hb, const sdcef_result* ho,
+                      cudaStream_t st) {
+  const int64_t ncol = hb->ncol, cells = hb->col_off[ncol];
+  const size_t c8 = (size_t)cells * 8, n8 = (size_t)ncol * 8, n4 = (size_t)ncol * 4;
   auto d2h = [&](void* dst, size_t o, size_t bytes) {
     return dst ? cudaMemcpyAsync(dst, d + o, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
   };
-  e = d2h(ho->ne_out, o_neo, c8);
-  if (e == cudaSuccess) e = d2h(ho->phi_out, o_pho, c8);
-  if (e == cudaSuccess) e = d2h(ho->status, o_st, n4);
-  if (e == cudaSuccess) e = d2h(ho->newton_it, o_nt, n4);
-  if (e == cudaSuccess) e = d2h(ho->krylov_it, o_kt, n4);
-  if (e == cudaSuccess) e = d2h(ho->res_evals, o_re, n4);
-  if (e == cudaSuccess) e = d2h(ho->final_res, o_fr, n8);
-  if (e == cudaSuccess) e = d2h(ho->mg_cycles, o_mg, n4);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaError_t e = d2h(ho->ne_out, L.neo, c8);
+  if (e == cudaSuccess) e = d2h(ho->phi_out, L.pho, c8);
+  if (e == cudaSuccess) e = d2h(ho->status, L.st, n4);
+  if (e == cudaSuccess) e = d2h(ho->newton_it, L.nt, n4);
+  if (e == cudaSuccess) e = d2h(ho->krylov_it, L.kt, n4);
+  if (e == cudaSuccess) e = d2h(ho->res_evals, L.re, n4);
+  if (e == cudaSuccess) e = d2h(ho->final_res, L.fr, n8);
+  if (e == cudaSuccess) e = d2h(ho->mg_cycles, L.mg, n4);
+  return e;
+}
+
+// the host batch is solvable by this context and the result pointers are usable
+int check_host_batch(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_result* ho) {
+  int rc = validate_batch(ctx, hb, true);
+  if (rc) return rc;
+  if (!ho || !ho->ne_out || !ho->phi_out)
+    return set_err(SDCEF_ERR_INVALID, "result: ne_out / phi_out is NULL");
+  const int64_t cells = hb->ncol > 0 ? hb->col_off[hb->ncol] : 0;
+  if (cells > ctx->max_cells || cells < 0)
+    return set_err(SDCEF_ERR_CAPACITY, "batch: cells exceed max_cells");
+  return SDCEF_SUCCESS;
+}
+
+// staging area of at least `bytes`; grown to twice the request so that
+// later calls do not reallocate
+int stage_reserve(sdcef_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->stage_bytes) return SDCEF_SUCCESS;
+  if (ctx->stage) {
+    cudaError_t e = cudaDeviceSynchronize();   // no copy or solve may still use the old area
+    if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+    cudaFree(ctx->stage);
+  }
+  ctx->stage = nullptr;
+  ctx->stage_bytes = 0;
+  cudaError_t e = cudaMalloc((void**)&ctx->stage, bytes * 2);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_NOMEM, cudaGetErrorString(e));
+  ctx->stage_bytes = bytes * 2;
+  return SDCEF_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdcef_solve_batch_host(sdcef_ctx* ctx, const sdcef_batch* hb, const sdcef_result* ho) {
+  Range range_("sdcef_solve_batch_host");
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  int rc = check_host_batch(ctx, hb, ho);
+  if (rc) return rc;
+  if (hb->ncol == 0) return SDCEF_SUCCESS;
+  const Stage L = stage_layout(hb);
+  if ((rc = stage_reserve(ctx, L.need))) return rc;
+  char* d = ctx->stage;
+  cudaError_t e = stage_in(L, d, hb, ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  sdcef_batch db;
+  sdcef_result dr;
+  stage_views(L, d, hb, &db, &dr);
+  rc = sdcef_solve_batch(ctx, &db, &dr);
+  if (rc) return rc;
+  e = stage_out(L, d, hb, ho, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+  return SDCEF_SUCCESS;
+}
+
+int sdcef_solve_batches_host(sdcef_ctx* ctx, int nbatch, const sdcef_batch* hbs,
+                             const sdcef_result* hos) {
+  Range range_("sdcef_solve_batches_host");
+  if (!ctx) return set_err(SDCEF_ERR_INVALID, "ctx is NULL");
+  if (nbatch < 0 || (nbatch > 0 && (!hbs || !hos)))
+    return set_err(SDCEF_ERR_INVALID, "batches: nbatch < 0 or NULL arrays");
+  size_t half = 0;
+  for (int k = 0; k < nbatch; ++k) {
+    int rc = check_host_batch(ctx, &hbs[k], &hos[k]);
+    if (rc) return rc;
+    if (hbs[k].ncol > 0) half = std::max(half, (stage_layout(&hbs[k]).need + 255) & ~(size_t)255);
+  }
+  if (half == 0) return SDCEF_SUCCESS;
+  int rc = stage_reserve(ctx, 2 * half);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->pipe) {
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaStreamCreateWithFlags(&ctx->cs[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_free[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+    ctx->pipe = true;
+  }
+  // copies start after the work already enqueued on the context stream
+  e = cudaEventRecord(ctx->ev_free[0], ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_free[1], ctx->stream);
+  for (int k = 0; k < nbatch && e == cudaSuccess; ++k) {
+    const sdcef_batch* hb = &hbs[k];
+    if (hb->ncol == 0) continue;
+    const int h = k & 1;
+    char* d = ctx->stage + (size_t)h * half;
+    const Stage L = stage_layout(hb);
+    // inputs of batch k once this half's previous batch has been solved and read back
+    e = cudaStreamWaitEvent(ctx->cs[0], ctx->ev_free[h], 0);
+    if (e == cudaSuccess) e = stage_in(L, d, hb, ctx->cs[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in[h], ctx->cs[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_in[h], 0);
+    if (e != cudaSuccess) break;
+    sdcef_batch db;
+    sdcef_result dr;
+    stage_views(L, d, hb, &db, &dr);
+    if ((rc = sdcef_solve_batch(ctx, &db, &dr))) break;
+    e = cudaEventRecord(ctx->ev_done[h], ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cs[1], ctx->ev_done[h], 0);
+    if (e == cudaSuccess) e = stage_out(L, d, hb, &hos[k], ctx->cs[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_free[h], ctx->cs[1]);
+  }
+  // every copy and solve has finished before the call returns (also on an error)
+  cudaError_t e2 = cudaStreamSynchronize(ctx->cs[0]);
+  cudaError_t e3 = cudaStreamSynchronize(ctx->stream);
+  cudaError_t e4 = cudaStreamSynchronize(ctx->cs[1]);
+  if (rc) return rc;
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
   if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
   return SDCEF_SUCCESS;
 }

@@ -43,7 +43,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_mlp_guess", "sdcef_mlp_last_launch_count", "sdcef_mlp_get_state",
            "sdcef_mlp_set_state", "sdcef_mlp_check", "sdcef_fma_peak_probe",
            "sdcef_mlp_set_wait_polls", "sdcef_checks_compiled", "sdcef_check_word",
-           "sdcef_mlp_check_word", "sdcef_autotune_on_chip")
+           "sdcef_mlp_check_word", "sdcef_autotune_on_chip", "sdcef_solve_batches_host")
 MLP_NPARAM = 20994
 GUESS_NE, GUESS_PHI = 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -101,6 +101,8 @@ def lib():
         L.sdcef_set_params.argtypes = [vp, P]
         L.sdcef_solve_batch.argtypes = [vp, B, R]
         L.sdcef_solve_batch_host.argtypes = [vp, B, R]
+        L.sdcef_solve_batches_host.argtypes = [vp, C.c_int, vp, vp]
+        L.sdcef_solve_batches_host.restype = C.c_int
         L.sdcef_residual_batch.argtypes = [vp, B, vp, vp, vp, vp]
         L.sdcef_bernoulli_batch.argtypes = [vp, vp, vp, vp, C.c_int64]
         L.sdcef_bernoulli_batch.restype = C.c_int
@@ -283,10 +285,10 @@ class Solver:
         _check(lib().sdcef_solve_batch(self.h, C.byref(bs), C.byref(rs)))
         return out
 
-    def solve_host(self, b, out: dict | None = None, guess=None) -> dict:
-        """sdcef_solve_batch_host: numpy (or pinned torch) host arrays in and out."""
-        keep = []
-
+    @staticmethod
+    def _host_structs(b, out, guess, keep):
+        """BatchC / ResultC of host arrays (numpy or pinned torch); the arrays
+        that back the pointers are appended to keep."""
         def h(a, dt=np.float64):
             if a is None:
                 return None
@@ -297,6 +299,7 @@ class Solver:
             keep.append(arr)
             return arr.ctypes.data
         val = np.ascontiguousarray(b.valence, dtype=np.int32)
+        keep.append(val)
         bs = BatchC(b.ncol, h(b.col_off, np.int64), h(b.length), h(b.dt), h(b.v_left),
                     h(b.v_right), h(b.ne_old), h(b.phi_old), int(val.shape[0]), val.ctypes.data,
                     h(np.atleast_2d(b.n_ion) if not hasattr(b.n_ion, "data_ptr") else b.n_ion),
@@ -309,8 +312,26 @@ class Solver:
                        final_res=np.empty(b.ncol))
         rs = ResultC(*[h(out[k], None) if k in out else None for k in
                        ("ne", "phi", "status", "newton_it", "krylov_it", "res_evals", "final_res")])
+        return bs, rs, out
+
+    def solve_host(self, b, out: dict | None = None, guess=None) -> dict:
+        """sdcef_solve_batch_host: numpy (or pinned torch) host arrays in and out."""
+        keep = []
+        bs, rs, out = self._host_structs(b, out, guess, keep)
         _check(lib().sdcef_solve_batch_host(self.h, C.byref(bs), C.byref(rs)))
         return out
+
+    def solve_host_many(self, batches, outs=None) -> list:
+        """sdcef_solve_batches_host: several host batches, the copies of the next
+        and previous batch overlapping each solve; returns the result dicts."""
+        keep = []
+        outs = outs if outs is not None else [None] * len(batches)
+        structs = [self._host_structs(b, o, None, keep) for b, o in zip(batches, outs)]
+        barr = (BatchC * len(structs))(*[st[0] for st in structs])
+        rarr = (ResultC * len(structs))(*[st[1] for st in structs])
+        _check(lib().sdcef_solve_batches_host(self.h, len(structs), C.cast(barr, C.c_void_p),
+                                              C.cast(rarr, C.c_void_p)))
+        return [st[2] for st in structs]
 
     def autotune(self, db: DeviceBatch, reps: int = 2):
         """sdcef_autotune: pick threads per column for this batch by timing."""

@@ -398,6 +398,30 @@ def test_host_entry_point_matches_device_entry_point():
     assert np.array_equal(out_h["status"], out_d["status"].cpu().numpy())
 
 
+def test_pipelined_host_batches_match_one_call_per_batch():
+    """sdcef_solve_batches_host overlaps the copies of neighbouring batches
+    with each solve; every batch's results equal those of its own call."""
+    dev()
+    bs = [make_batch("ragged", 7, 70, n_range=(64, 400)),
+          make_batch("ragged", 0, 71),
+          make_batch("ragged", 12, 72, n_range=(32, 500)),
+          make_batch("ragged", 3, 73, n_range=(200, 260)),
+          make_batch("ragged", 9, 74, n_range=(64, 128))]
+    s = S.Solver(S.default_params(), max_cols=12, max_cells=max(b.ncells for b in bs),
+                 max_col_cells=500)
+    many = s.solve_host_many(bs)
+    for b, got in zip(bs, many):
+        if b.ncol == 0:
+            continue
+        ref = s.solve_host(b)
+        for k in ("ne", "phi", "status", "newton_it", "krylov_it", "final_res"):
+            assert np.array_equal(got[k], ref[k]), k
+    # a batch the context cannot hold fails the whole call before any copy
+    big = make_batch("ragged", 13, 75, n_range=(64, 128))
+    with pytest.raises(S.SdcefError):
+        s.solve_host_many([bs[0], big])
+
+
 def test_outputs_may_alias_inputs():
     d = dev()
     b = make_batch("ragged", 5, 90, n_range=(64, 300))
