@@ -11,12 +11,27 @@ Algorithm 2 by a predicted one, and the JFNK still converges every solve):
       n_e^n / s_n, phi^n / s_phi, f_phi / s_n, T / 2000 K, E h / s_phi,
   with E h = -(phi_{k+1} - phi_{k-1}) / 2 (mirrored neighbours) and the
   per-column scales s_n, s_phi of Eq. newton_sc taken at X^n; 25 values in
-  stencil-major order, zero-padded to 32.
+  stencil-major order, followed by seven values of the column context:
+      25: x_i / L = (i + 1/2) / N               (cell position)
+      26: log10(s_n / 1 m^-3) - 16               (density level)
+      27: (V_R - V_L) / 1000 V                   (applied voltage)
+      28: (log2 N - 10) / 2                      (resolution)
+      29: log10(dt / 1 s) + 5                    (time step)
+      30: asinh(phi_ion,i / s_phi)
+      31: asinh(E_ion,i L / s_phi)
+  where phi_ion is the potential of the ion charge alone: the root of the
+  Poisson residual F_phi (Sec. 2, Eq. nls) with n_e = 0 and both electrodes
+  at 0 V (eps_r = 1), and E_ion,i = -(G_{i-1/2} + G_{i+1/2}) / 2 the mean of
+  its two face gradients (electrode faces by the residual's one-sided
+  formulas). A column of one cell has no Poisson system: 30, 31 are 0.
 
   network: y = W3 silu(W2 silu(W1 x + b1) + b2) + b3, 32 -> 128 -> 128 -> 2,
   silu(z) = z / (1 + e^{-z}).
 
-  guess: n_e = n_e^n + s_n y_0, phi = phi^n + s_phi y_1.
+  guess (components, a bit set): bit 0 adds the n_e increment s_n y_0; bit 1
+  adds the potential increment s_phi y_1; bit 2 instead takes as potential the
+  root of F_phi at the guessed n_e (the potential consistent with the guessed
+  charge, eps_r = 1; columns of one cell keep phi^n).
 
   training target: y* = ((n_e* - n_e^n) / s_n, (phi* - phi^n) / s_phi) from
   converged solves, loss = mean over samples and both outputs of (y - y*)^2,
@@ -26,11 +41,15 @@ from __future__ import annotations
 
 import numpy as np
 
-NF = 25
+NF = 25          # stencil features
+NF_CTX = 7       # column-context features (slots 25..31)
 NF_PAD = 32
 HIDDEN = 128
 NOUT = 2
 T_SCALE = 2000.0
+E_CHARGE = 1.602176634e-19      # C (CODATA 2018)
+EPS0 = 8.8541878128e-12         # F/m
+KAPPA = EPS0 / E_CHARGE         # eps_0 eps_r / e with eps_r = 1
 
 
 def column_scales(batch):
@@ -43,6 +62,48 @@ def column_scales(batch):
         sn[c] = max(np.abs(batch.ne_old[s]).max(), np.abs(fphi[s]).max(), 1.0)
         sp[c] = max(np.abs(batch.phi_old[s]).max(), abs(batch.v_left[c]), abs(batch.v_right[c]), 1.0)
     return sn, sp
+
+
+def poisson_potential(n_minus_f, h, v_left, v_right):
+    """Cell potentials phi [N] (N >= 2) with F_phi = -n + f + kappa (G_{i+1/2} -
+    G_{i-1/2}) / h = 0 for every cell, given n - f [N] (m^-3): interior face
+    gradients (phi_{i+1} - phi_i) / h, electrode faces (9 phi_0 - phi_1 - 8 V_L)
+    / (3h) and (8 V_R - 9 phi_{N-1} + phi_{N-2}) / (3h). A banded solve of the
+    N tridiagonal rows written out from those faces."""
+    from scipy.linalg import solve_banded
+    N = n_minus_f.shape[0]
+    k = KAPPA / (h * h)
+    ab = np.zeros((3, N))            # ab[0, j+1] = A[j, j+1], ab[1, j] = A[j, j], ab[2, j] = A[j+1, j]
+    rhs = np.asarray(n_minus_f, dtype=np.float64).copy()
+    ab[1, :] = -2.0 * k
+    ab[0, 1:] = k
+    ab[2, :-1] = k
+    # row 0: kappa/h [(phi_1 - phi_0)/h - (9 phi_0 - phi_1 - 8 V_L)/(3h)]
+    ab[1, 0] = -4.0 * k
+    ab[0, 1] = 4.0 / 3.0 * k
+    rhs[0] -= 8.0 / 3.0 * k * v_left
+    # row N-1: kappa/h [(8 V_R - 9 phi_{N-1} + phi_{N-2})/(3h) - (phi_{N-1} - phi_{N-2})/h]
+    ab[1, N - 1] = -4.0 * k
+    ab[2, N - 2] = 4.0 / 3.0 * k
+    rhs[N - 1] -= 8.0 / 3.0 * k * v_right
+    return solve_banded((1, 1), ab, rhs)
+
+
+def face_gradients(phi, h, v_left, v_right):
+    """G_{-1/2}, G_{1/2}, ..., G_{N-1/2} of the Poisson residual (N + 1 faces)."""
+    G = np.empty(phi.shape[0] + 1)
+    G[1:-1] = np.diff(phi) / h
+    G[0] = (9.0 * phi[0] - phi[1] - 8.0 * v_left) / (3.0 * h)
+    G[-1] = (8.0 * v_right - 9.0 * phi[-1] + phi[-2]) / (3.0 * h)
+    return G
+
+
+def ion_field(q, h):
+    """(phi_ion, E_ion) of a column: the potential of the ion charge f (n_e = 0,
+    electrodes at 0 V) and the mean of each cell's two face gradients, negated."""
+    phi = poisson_potential(-np.asarray(q, dtype=np.float64), h, 0.0, 0.0)
+    G = face_gradients(phi, h, 0.0, 0.0)
+    return phi, -0.5 * (G[:-1] + G[1:])
 
 
 def features(batch):
@@ -68,6 +129,16 @@ def features(batch):
             X[a:b, base + 2] = q[k] / sn[c]
             X[a:b, base + 3] = T[k] / T_SCALE
             X[a:b, base + 4] = -(phi[kp] - phi[km]) / 2.0 / sp[c]
+        L = batch.length[c]
+        X[a:b, 25] = (i + 0.5) / N
+        X[a:b, 26] = np.log10(sn[c]) - 16.0
+        X[a:b, 27] = (batch.v_right[c] - batch.v_left[c]) / 1000.0
+        X[a:b, 28] = (np.log2(N) - 10.0) / 2.0
+        X[a:b, 29] = np.log10(batch.dt[c]) + 5.0
+        if N >= 2:
+            pi, ei = ion_field(q, L / N)
+            X[a:b, 30] = np.arcsinh(pi / sp[c])
+            X[a:b, 31] = np.arcsinh(ei * L / sp[c])
     return X
 
 
@@ -81,14 +152,22 @@ def targets(batch, ne_star, phi_star):
     return Y
 
 
-def guess(batch, Y):
+def guess(batch, Y, components=3):
     sn, sp = column_scales(batch)
     ne = batch.ne_old.copy()
     phi = batch.phi_old.copy()
+    fphi = (batch.valence[:, None] * np.atleast_2d(batch.n_ion)).sum(axis=0)
     for c in range(batch.ncol):
         s = slice(batch.col_off[c], batch.col_off[c + 1])
-        ne[s] += sn[c] * Y[s, 0]
-        phi[s] += sp[c] * Y[s, 1]
+        N = s.stop - s.start
+        if components & 1:
+            ne[s] += sn[c] * Y[s, 0]
+        if components & 4:
+            if N >= 2:
+                phi[s] = poisson_potential(ne[s] - fphi[s], batch.length[c] / N,
+                                           batch.v_left[c], batch.v_right[c])
+        elif components & 2:
+            phi[s] += sp[c] * Y[s, 1]
     return ne, phi
 
 
