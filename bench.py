@@ -31,6 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "column-solves/s at rel. residual 1e-10 (batched/learned vs plain JFNK); HBM %"
+# the learned Newton start: the predicted n_e increment and the potential of
+# the guessed charge (root of the Poisson residual at that n_e)
+LEARNED_START = 5
 UNIT = "column-solves/s"
 WORKLOAD = "4096 ragged columns, 128-2048 cells, L=1cm, dt=1e-5s, V_R~U(-500,500)V"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -579,7 +582,7 @@ def extras(args, S, b, db, solver, params, dev, parity):
             ol_ = sl.alloc_result(db)
 
             def learned(sl=sl, ol_=ol_):
-                mlp.guess(db, ne_g, ph_g, components=S.GUESS_NE)
+                mlp.guess(db, ne_g, ph_g, components=LEARNED_START)
                 return sl.solve(gdb, ol_)
             tl, ol = _timed(learned)
             okc = ((o_ref["status"] == 0) & (ol["status"] == 0)).cpu().numpy()
@@ -608,12 +611,12 @@ def extras(args, S, b, db, solver, params, dev, parity):
         tp, op = _timed(lambda: s4.solve(db4))
 
         def learned():
-            mlp.guess(db4, ne_g, ph_g, components=S.GUESS_NE)
+            mlp.guess(db4, ne_g, ph_g, components=LEARNED_START)
             return s4.solve(db4.with_guess(ne_g, ph_g), out4)
         tl, ol = _timed(learned)
         parity["holdout"] = (b4, {"plain_fp64": (op["ne"].cpu().numpy(), op["phi"].cpu().numpy()),
                                   "learned_fp64": (ol["ne"].cpu().numpy(), ol["phi"].cpu().numpy())})
-        tg, _ = _timed(lambda: mlp.guess(db4, ne_g, ph_g, components=S.GUESS_NE))
+        tg, _ = _timed(lambda: mlp.guess(db4, ne_g, ph_g, components=LEARNED_START))
         res["config4_learned_guess"] = {
             "columns": b4.ncol, "cells": "512-2048",
             "plain": {"value": b4.ncol / tp, **_iterations(op),
@@ -621,7 +624,8 @@ def extras(args, S, b, db, solver, params, dev, parity):
             "learned": {"value": b4.ncol / tl, **_iterations(ol),
                         "status_ok": int((ol["status"] == 0).sum().item()),
                         "guess_kernel_ms": 1e3 * tg},
-            "unit": "column-solves/s", "components": "n_e increment"}
+            "unit": "column-solves/s",
+            "components": "n_e increment; potential of the guessed charge (root of F_phi)"}
         mlp.close()
         s4.close()
     # config 5: SDC electric sweep, k_max = 4 solves per MISDC step, ion-CFL step, CUDA graph
@@ -671,7 +675,7 @@ def extras(args, S, b, db, solver, params, dev, parity):
         dout = dsolver.alloc_result(sdb)
 
         def mixed_learned():
-            mlp5.guess(sdb, g_ne, g_ph, components=S.GUESS_NE)
+            mlp5.guess(sdb, g_ne, g_ph, components=LEARNED_START)
             return dsolver.sdc_sweep(gdb, 4, work=work, out=dout)
         with torch.cuda.stream(st_):
             tme, _ = _timed(mixed_learned, reps=2)

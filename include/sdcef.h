@@ -222,7 +222,7 @@ typedef struct {
  * steps, 200 Krylov iterations per step, 20 halvings, FP64, exact Schur
  * preconditioner, absorbing electrodes, automatic threads per column, and a
  * supplied start rejected if its residual is over 30x the plain start's and
- * judged after 16 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
+ * judged after 5 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
  * blocks (the optimum of Sec. 4.2), at most 50 V-cycles per block solve and
  * operator-dependent transfers; the paper's ion transport in the SDC sweep
  * (SDCEF_ION_GODUNOV); constant electron transport, gas molar mass 0.028 kg/mol. */
@@ -445,14 +445,21 @@ int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batch* batch,
 
 /* ---------------------------------------------------------------------------
  * Learned Newton initial guess. Not part of the paper: a small MLP predicts,
- * from local stencil features of the plain start X^n, the scaled increment to
- * the converged solution; Algorithm 2 then starts from X^n + S_X y and still
- * decides convergence with its own residual test, so the guess changes only
- * the iteration count, never the accepted root.
- *   features of cell i: for stencil offsets -2..2 (indices mirrored at the
- *   column ends) n_e^n/s_n, phi^n/s_phi, f_phi/s_n, T/2000 K, E h/s_phi with
- *   E h = -(phi_{k+1} - phi_{k-1})/2; 25 values zero-padded to 32, BF16,
- *   row-major [cells][32]; s_n, s_phi are the per-column scales of Eq. newton_sc.
+ * from stencil and column features of the plain start X^n, the scaled
+ * increment to the converged solution; Algorithm 2 then starts from the guess
+ * and still decides convergence with its own residual test, so the guess
+ * changes only the iteration count, never the accepted root.
+ *   features of cell i (BF16, row-major [cells][32]; s_n, s_phi are the
+ *   per-column scales of Eq. newton_sc):
+ *   0..24: for stencil offsets -2..2 (indices mirrored at the column ends)
+ *     n_e^n/s_n, phi^n/s_phi, f_phi/s_n, T/2000 K, E h/s_phi with
+ *     E h = -(phi_{k+1} - phi_{k-1})/2;
+ *   25..31, the column context: (i + 1/2)/N, log10(s_n / 1 m^-3) - 16,
+ *     (V_R - V_L)/1000 V, (log2 N - 10)/2, log10(dt / 1 s) + 5,
+ *     asinh(phi_ion,i/s_phi), asinh(E_ion,i L/s_phi), where phi_ion is the
+ *     root of the Poisson residual F_phi (Sec. 2) with n_e = 0, electrodes at
+ *     0 V and eps_r = 1 (the potential of the ion charge alone) and E_ion,i is
+ *     minus the mean of its two face gradients at cell i (0 for N = 1).
  *   network: y = W3 silu(W2 silu(W1 x + b1) + b2) + b3 (32 -> 128 -> 128 -> 2),
  *   BF16 weights and activations on the tensor cores, FP32 accumulation.
  *   parameters: FP32 flat array of SDCEF_MLP_NPARAM values, in order
@@ -493,13 +500,19 @@ int sdcef_mlp_grad(sdcef_mlp* mlp, const void* X_bf16, const float* targets, int
 /* One Adam step on n rows with learning rate lr; loss [1] FP32 device (may be NULL). */
 int sdcef_mlp_train_step(sdcef_mlp* mlp, const void* X_bf16, const float* targets, int64_t n,
                          float lr, float* loss);
-/* Newton start for every cell of the batch: features, network, and
- * X^n + S_X y written to ne_guess / phi_guess ([cells] FP64). ncells is the
- * batch's total cell count (<= max_rows). components selects which predicted
- * increments are applied (SDCEF_GUESS_NE | SDCEF_GUESS_PHI); an increment not
- * selected leaves that field at its plain start value. */
+/* Newton start for every cell of the batch: features, network, and the
+ * start written to ne_guess / phi_guess ([cells] FP64). ncells is the
+ * batch's total cell count (<= max_rows). components is a bit set:
+ *   SDCEF_GUESS_NE: n_e = n_e^n + s_n y_0 (else n_e^n);
+ *   SDCEF_GUESS_PHI: phi = phi^n + s_phi y_1 (else phi^n);
+ *   SDCEF_GUESS_PHI_POISSON: phi = the root of the Poisson residual F_phi at
+ *     the start's n_e (the potential consistent with the guessed charge;
+ *     eps_r = 1, electrodes at V_L, V_R); it takes precedence over
+ *     SDCEF_GUESS_PHI. Columns of one cell keep phi^n.
+ * Returns SDCEF_ERR_INVALID for components outside 0..7. */
 #define SDCEF_GUESS_NE 1
 #define SDCEF_GUESS_PHI 2
+#define SDCEF_GUESS_PHI_POISSON 4
 int sdcef_mlp_guess(sdcef_mlp* mlp, const sdcef_batch* batch, int64_t ncells, int components,
                     double* ne_guess, double* phi_guess);
 /* Kernel launches enqueued by the last forward / grad / train_step / guess call. */

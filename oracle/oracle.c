@@ -117,6 +117,8 @@ typedef struct {
 
 #define OR_NA 6.02214076e23        /* Avogadro constant, 1/mol     */
 #define OR_MAX_POLISH 2            /* Newton steps for the error test at most */
+#define OR_ERR_MARGIN 10.0         /* a stale-factor error estimate within this factor
+                                      of the bar is re-taken with factors at X^(l) */
 
 /* Bilinear interpolation of a [nc][nx] table with nodes c_k = k/(nc-1) and
  * x_j = j en_max/(nx-1), at (c, x) clamped to the table. */
@@ -1102,6 +1104,8 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
   st->first_res = fninf;
   st->status = OR_MAX_NEWTON;
   int have_prec = 0;   /* preconditioner blocks built at an earlier iterate */
+  int prec_cur = 0;    /* ... and those blocks were built at the current iterate */
+  const int from_guess = ne0 != NULL || phi0 != NULL;   /* a supplied start */
   int polished = 0;    /* Newton steps taken for the error test */
   for (int l = 0;; ++l) {
     if (!isfinite(fninf)) { st->status = OR_NONFINITE; break; }
@@ -1115,7 +1119,12 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
        * of the last Newton step (built at X^(l) if there was none; with the
        * exact Schur form P = J), estimates the error of X^(l). The column stops
        * when max|e_n| <= eps_E max|n| and max|e_phi| <= eps_E max|phi|;
-       * otherwise it takes one more Newton step. */
+       * otherwise it takes one more Newton step. Blocks built at the previous
+       * iterate misjudge the error by the change of J over the last step; from
+       * the plain start the last step is small and the estimate matches the
+       * true error, but a supplied (learned) start can end with a large step:
+       * there an estimate that passes within a factor OR_ERR_MARGIN of the bar
+       * is taken again with blocks built at X^(l). */
       if (!(P->eps_E > 0.0) || l >= P->max_newton || polished >= OR_MAX_POLISH) {
         st->status = OR_OK;
         break;
@@ -1123,12 +1132,24 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
       if (!have_prec) {
         build_prec(c, &J.prec, ne, psi, phin);
         have_prec = 1;
+        prec_cur = 1;
       }
-      for (int i = 0; i < n; ++i) { rhs[i] = Fe[i] / sFe; rhs[n + i] = Fp[i] / sFp; }
-      jf_prec(&J, rhs, dX);
       double nmax = maxabs(n, ne), pmax = 0.0;
       for (int i = 0; i < n; ++i) pmax = fmax(pmax, fabs(phi_ref(c, i) + psi[i]));
-      double en = sn * maxabs(n, dX), ep = sp * maxabs(n, dX + n);
+      double en = 0.0, ep = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < n; ++i) { rhs[i] = Fe[i] / sFe; rhs[n + i] = Fp[i] / sFp; }
+        jf_prec(&J, rhs, dX);
+        en = sn * maxabs(n, dX);
+        ep = sp * maxabs(n, dX + n);
+        const int marginal = en > P->eps_E / OR_ERR_MARGIN * nmax ||
+                             ep > P->eps_E / OR_ERR_MARGIN * pmax;
+        if (!from_guess || prec_cur || !marginal ||
+            !(en <= P->eps_E * nmax && ep <= P->eps_E * pmax))
+          break;
+        build_prec(c, &J.prec, ne, psi, phin);
+        prec_cur = 1;
+      }
       if (en <= P->eps_E * nmax && ep <= P->eps_E * pmax) { st->status = OR_OK; break; }
       polish = 1;
     }
@@ -1193,6 +1214,7 @@ void or_jfnk_col(const or_params* P, const or_col* c, const double* ne_old,
     fninf = trinf;
     st->newton_it++;
     polished += polish;
+    prec_cur = 0;
     if (P->eps_X > 0.0) {
       double st_inf = lam * maxabs(2 * n, dX);
       if (st_inf < P->eps_X && fninf >= P->eps_F) { st->status = OR_OK; break; }

@@ -4,11 +4,13 @@
 // accumulate in TMEM, and Adam over the kernel's per-CTA partial gradients;
 // the inference forward; and the fused inference kernel (mlp_tc.cuh) that
 // assembles the guess. The network maps the
-// 5-cell stencil features of a cell to the scaled Newton increment
-// ((n* - n^n)/s_n, (phi* - phi^n)/s_phi); the JFNK of Algorithm 2 then starts
-// from X^n + S_X y instead of X^n and still decides convergence.
+// 5-cell stencil features and the column context of a cell to the scaled
+// Newton increment ((n* - n^n)/s_n, (phi* - phi^n)/s_phi); the JFNK of
+// Algorithm 2 then starts from the guess instead of X^n and still decides
+// convergence. The guess may take as potential the root of the Poisson
+// residual at the guessed electron density (poisson_column).
 //
-// Shapes: 32 (25 features, zero-padded) -> 128 -> 128 -> 2, SiLU activations.
+// Shapes: 32 (25 stencil + 7 column features) -> 128 -> 128 -> 2, SiLU activations.
 // Parameters (FP32 master copy, flat): W1[128][32], b1[128], W2[128][128],
 // b2[128], W3[2][128], b3[2]; BF16 copies of W1, W2, W3 feed the tensor cores.
 #include <cuda.h>
@@ -20,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "../../include/sdcef.h"
 #include "checks.cuh"
@@ -61,18 +64,17 @@ __device__ __forceinline__ float silu_fast(float z) {
 struct FeatArgs {
   int64_t ncol;
   const int64_t* col_off;
-  const double *v_left, *v_right, *ne, *phi, *n_ion, *T;
+  const double *length, *dt, *v_left, *v_right, *ne, *phi, *n_ion, *T;
   int nsp;
   int val[SDCEF_MAX_SPECIES];
   __nv_bfloat16* X;     // [cells][32]
   // optional targets / guess
   const double *ne_star, *phi_star;
   float* Tgt;           // [cells][2]
-  const float* Y;       // [cells][2] network output (guess mode)
   double *ne_g, *phi_g;
   unsigned* chk;        // check word of the bounds-checking build (may be null)
-  int mode;             // 0 features, 1 targets, 2 guess
-  int comps;            // guess: bit 0 applies the n_e increment, bit 1 the phi increment
+  int mode;             // 0 features, 1 targets
+  int comps;            // guess: bit 0 n_e increment, bit 1 phi increment, bit 2 Poisson phi
 };
 
 __device__ __forceinline__ double block_max(double v, double* sh) {
@@ -86,6 +88,151 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return r;
 }
 
+// eps_0 / e (eps_r = 1), the Poisson constant of the column features and of
+// the Poisson start (CODATA 2018 values)
+constexpr double kKapGuess = 8.8541878128e-12 / 1.602176634e-19;
+
+// Exclusive prefix sum of v over threads t = 0..W-1 (W a multiple of 32, at
+// most 32 warps), all of which call it; *total gets the sum over all threads
+// (the same value, summed in the same order, on every thread). red holds W/32
+// doubles of shared memory; bar() synchronises the W threads.
+template <class Bar>
+__device__ __forceinline__ double excl_scan(double v, int t, int W, double* red, Bar bar,
+                                            double* total) {
+  const int lane = t & 31, w = t >> 5, nw = W >> 5;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  double ex = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) ex = 0.0;
+  if (lane == 31) red[w] = x;
+  bar();
+  double base = 0.0, tot = 0.0;
+  for (int q = 0; q < nw; ++q) {
+    const double r = red[q];
+    if (q < w) base += r;
+    tot += r;
+  }
+  bar();
+  *total = tot;
+  return base + ex;
+}
+
+// Root of the Poisson residual of one column (N >= 2 cells),
+//   F_phi,i = -n_i + f_i + kappa (G_{i+1/2} - G_{i-1/2}) / h = 0,
+// interior faces G = (phi_{i+1} - phi_i)/h, electrode faces
+// G_{-1/2} = (9 phi_0 - phi_1 - 8 V_L)/(3h), G_{N-1/2} = (8 V_R - 9 phi_{N-1} + phi_{N-2})/(3h),
+// for the cell sources s_i = (h^2/kappa)(n_i - f_i), by two prefix sums instead
+// of a tridiagonal solve: with the face differences D_i = h G_{i+1/2}, row i
+// reads D_i - D_{i-1} = s_i, so D_i = D_{-1} + S_i (S_i = s_0 + ... + s_i) and
+// phi_i = phi_0 + i D_{-1} + T_i (T_i = S_0 + ... + S_{i-1}); the two electrode
+// faces give phi_0 = V_L + D_{-1}/2 + S_0/8 and
+//   D_{-1} = (8 (V_R - V_L) - S_0 - 8 T_{N-1} - S_{N-2} - 3 S_{N-1}) / (8 N).
+// Thread t of W takes a contiguous run of cells; src(i) is s_i (called twice
+// per cell and once more for cells 0 and N-1); emit(i, phi_i, S_{i-1}, S_i, D_{-1})
+// per cell. Every thread of the W calls it.
+template <class Src, class Emit, class Bar>
+__device__ __forceinline__ void poisson_column(int N, double vl, double vr, int t, int W,
+                                               double* red, Bar bar, Src src, Emit emit) {
+  const int run = (N + W - 1) / W;
+  const int lo = min(t * run, N), hi = min(lo + run, N);
+  double sig = 0.0, tau = 0.0;
+  for (int k = lo; k < hi; ++k) {
+    sig += src(k);
+    tau += sig;
+  }
+  double s_tot, t_tot;
+  const double s_before = excl_scan(sig, t, W, red, bar, &s_tot);
+  const double t_before = excl_scan((double)(hi - lo) * s_before + tau, t, W, red, bar, &t_tot);
+  const double S0 = src(0), SN1 = s_tot, SN2 = s_tot - src(N - 1), TN1 = t_tot - s_tot;
+  const double D = (8.0 * (vr - vl) - S0 - 8.0 * TN1 - SN2 - 3.0 * SN1) / (8.0 * N);
+  const double p0 = vl + 0.5 * D + 0.125 * S0;
+  double S = s_before, T = t_before, pk = fma((double)lo, D, p0);   // pk = phi_0 + k D_{-1}
+  for (int k = lo; k < hi; ++k) {
+    const double Sn = S + src(k);
+    emit(k, pk + T, S, Sn, D);
+    T += Sn;
+    S = Sn;
+    pk += D;
+  }
+}
+
+// Column-context features 26..29 of a column (once per column, in FP64, so
+// that a feature that is 0, as log10(dt) + 5 at dt = 1e-5 s, stays near 0).
+struct ColCtx {
+  float f[4];
+};
+__device__ __forceinline__ ColCtx col_context(double sn, int N, double vl, double vr, double dt) {
+  ColCtx c;
+  c.f[0] = (float)(log10(sn) - 16.0);
+  c.f[1] = (float)((vr - vl) * 1e-3);
+  c.f[2] = (float)((log2((double)N) - 10.0) * 0.5);
+  c.f[3] = (float)(log10(dt) + 5.0);
+  return c;
+}
+
+// Feature 25: the cell position x_i / L = (i + 1/2) / N.
+__device__ __forceinline__ float ctx_pos(int i, int N) {
+  return ((float)i + 0.5f) / (float)N;
+}
+
+// Features 30, 31 of cell i from the ion potential phi_i = phi_ion,i and the
+// face sums of poisson_column: E_ion,i = -(D_{i-1} + D_i) / (2h) (the sum of
+// face differences in FP64, where the field changes sign; the scaling and
+// the asinh in FP32, the features being rounded to BF16).
+__device__ __forceinline__ void ion_features(double phi_i, double S_prev, double S_i, double D,
+                                             float L2h_isp, float isp, float* f30, float* f31) {
+  *f30 = asinhf((float)phi_i * isp);
+  *f31 = asinhf(-(float)(2.0 * D + S_prev + S_i) * L2h_isp);
+}
+
+// f_phi = sum_s nu_s n_s of batch cell gi (one unit cation: the density itself)
+__device__ __forceinline__ double fphi_cell(const FeatArgs& a, int64_t cells, int64_t gi) {
+  if (a.nsp == 1 && a.val[0] == 1) return a.n_ion[gi];
+  double q = 0.0;
+  for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * cells + gi];
+  return q;
+}
+
+// |x| as an ordered bit pattern (non-negative doubles order as their patterns,
+// so maxima run on the integer pipe); a NaN counts as 0, as fmax ignores it
+__device__ __forceinline__ long long abs_bits(double x) {
+  const long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+  return b > 0x7FF0000000000000LL ? 0LL : b;
+}
+
+// Per-thread maxima of |n_e|, |f_phi|, |phi| of a column over cells t, t+W, ...
+__device__ __forceinline__ void col_maxima(const FeatArgs& a, int64_t cells, int64_t off, int N,
+                                           int t, int W, double* m) {
+  long long mn = 0, mq = 0, mp = 0;
+  for (int i = t; i < N; i += W) {
+    mn = max(mn, abs_bits(a.ne[off + i]));
+    mq = max(mq, abs_bits(fphi_cell(a, cells, off + i)));
+    mp = max(mp, abs_bits(a.phi[off + i]));
+  }
+  m[0] = __longlong_as_double(mn);
+  m[1] = __longlong_as_double(mq);
+  m[2] = __longlong_as_double(mp);
+}
+
+// The five per-cell quantities of the stencil features of cell i (FP32):
+// n_e/s_n, phi/s_phi, f_phi/s_n, T/2000 K and E h/s_phi = -(phi_{i+1} -
+// phi_{i-1}) / (2 s_phi) with mirrored neighbours; each value is rounded to
+// FP32 and scaled in FP32 (the neighbour difference is taken in FP64).
+__device__ __forceinline__ void cell_quantities(const FeatArgs& a, int64_t cells, int64_t off, int N,
+                                                int i, float isn, float isp, float* v) {
+  const int kp = (i + 1 < N) ? i + 1 : N - 1;
+  const int km = (i >= 1) ? i - 1 : 0;
+  v[0] = (float)a.ne[off + i] * isn;
+  v[1] = (float)a.phi[off + i] * isp;
+  v[2] = (float)fphi_cell(a, cells, off + i) * isn;
+  v[3] = (float)a.T[off + i] * (1.0f / 2000.0f);
+  v[4] = (float)(a.phi[off + kp] - a.phi[off + km]) * (-0.5f * isp);
+}
+
 __global__ void feat_kernel(FeatArgs a) {
   __shared__ double sh[32];
   const int64_t c = blockIdx.x;
@@ -94,51 +241,57 @@ __global__ void feat_kernel(FeatArgs a) {
   const int N = (int)(a.col_off[c + 1] - off);
   const int64_t cells = a.col_off[a.ncol];
   if (!SDCEF_CHECK_W(a.chk, off >= 0 && N >= 0 && off + N <= cells, sdcef_chk::kMlpRow)) return;
-  auto fphi = [&](int i) {
-    double q = 0.0;
-    for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * cells + off + i];
-    return q;
-  };
-  double mn = 0.0, mq = 0.0, mp = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    mn = fmax(mn, fabs(a.ne[off + i]));
-    mq = fmax(mq, fabs(fphi(i)));
-    mp = fmax(mp, fabs(a.phi[off + i]));
-  }
-  mn = block_max(mn, sh);
-  mq = block_max(mq, sh);
-  mp = block_max(mp, sh);
+  double m[3];
+  col_maxima(a, cells, off, N, (int)threadIdx.x, (int)blockDim.x, m);
+  const double mn = block_max(m[0], sh), mq = block_max(m[1], sh), mp = block_max(m[2], sh);
   const double sn = fmax(fmax(mn, mq), 1.0);
   const double sp = fmax(fmax(mp, fmax(fabs(a.v_left[c]), fabs(a.v_right[c]))), 1.0);
-  const double isn = 1.0 / sn, isp = 1.0 / sp;
   if (N < 1) return;
+  if (a.mode == 1) {
+    const double isn = 1.0 / sn, isp = 1.0 / sp;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const int64_t gi = off + i;
+      a.Tgt[gi * 2 + 0] = (float)((a.ne_star[gi] - a.ne[gi]) * isn);
+      a.Tgt[gi * 2 + 1] = (float)((a.phi_star[gi] - a.phi[gi]) * isp);
+    }
+    return;
+  }
+  const float isn = (float)(1.0 / sn), isp = (float)(1.0 / sp);
   auto mir = [&](int j) {
     if (j < 0) j = -j - 1;
     if (j >= N) j = 2 * N - 1 - j;
     return min(max(j, 0), N - 1);
   };
+  const ColCtx cx = col_context(sn, N, a.v_left[c], a.v_right[c], a.dt[c]);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const int64_t gi = off + i;
-    if (a.mode == 0) {
-      __nv_bfloat16* x = a.X + gi * kIn;
-      for (int o = -2; o <= 2; ++o) {
-        int k = mir(i + o), kp = mir(k + 1), km = mir(k - 1);
-        int base = 5 * (o + 2);
-        x[base + 0] = __float2bfloat16((float)(a.ne[off + k] * isn));
-        x[base + 1] = __float2bfloat16((float)(a.phi[off + k] * isp));
-        x[base + 2] = __float2bfloat16((float)(fphi(k) * isn));
-        x[base + 3] = __float2bfloat16((float)(a.T[off + k] * (1.0 / 2000.0)));
-        x[base + 4] = __float2bfloat16((float)(-(a.phi[off + kp] - a.phi[off + km]) * 0.5 * isp));
-      }
-      for (int f = kFeat; f < kIn; ++f) x[f] = __float2bfloat16(0.0f);
-    } else if (a.mode == 1) {
-      a.Tgt[gi * 2 + 0] = (float)((a.ne_star[gi] - a.ne[gi]) * isn);
-      a.Tgt[gi * 2 + 1] = (float)((a.phi_star[gi] - a.phi[gi]) * isp);
-    } else {
-      a.ne_g[gi] = a.ne[gi] + ((a.comps & 1) ? sn * (double)a.Y[gi * 2 + 0] : 0.0);
-      a.phi_g[gi] = a.phi[gi] + ((a.comps & 2) ? sp * (double)a.Y[gi * 2 + 1] : 0.0);
+    __nv_bfloat16* x = a.X + (off + i) * kIn;
+    for (int o = -2; o <= 2; ++o) {
+      float v[5];
+      cell_quantities(a, cells, off, N, mir(i + o), isn, isp, v);
+      for (int q = 0; q < 5; ++q) x[5 * (o + 2) + q] = __float2bfloat16(v[q]);
+    }
+    x[kFeat] = __float2bfloat16(ctx_pos(i, N));
+    for (int q = 0; q < 4; ++q) x[kFeat + 1 + q] = __float2bfloat16(cx.f[q]);
+    if (N < 2) {
+      x[kFeat + 5] = __float2bfloat16(0.0f);
+      x[kFeat + 6] = __float2bfloat16(0.0f);
     }
   }
+  if (N < 2) return;
+  // features 30, 31: the potential and field of the ion charge alone
+  __syncthreads();   // sh is free again (last read by block_max)
+  const double L = a.length[c], hk = (L / N) * (L / N) / kKapGuess;
+  const float L2h_isp = 0.5f * (float)N * isp;
+  poisson_column(
+      N, 0.0, 0.0, (int)threadIdx.x, (int)blockDim.x, sh, [] { __syncthreads(); },
+      [&](int i) { return -hk * fphi_cell(a, cells, off + i); },
+      [&](int i, double phi_i, double S_prev, double S_i, double D) {
+        float f30, f31;
+        ion_features(phi_i, S_prev, S_i, D, L2h_isp, isp, &f30, &f31);
+        __nv_bfloat16* x = a.X + (off + i) * kIn;
+        x[kFeat + 5] = __float2bfloat16(f30);
+        x[kFeat + 6] = __float2bfloat16(f31);
+      });
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -892,12 +1045,15 @@ __global__ void __launch_bounds__(256) part_reduce_kernel(const float* part, int
 // the tcgen05 tensor cores (BF16 operands in shared memory, FP32 accumulators
 // in tensor memory); the kernel's organisation is described in mlp_tc.cuh.
 // --------------------------------------------------------------------------
+// per cell of the stage: the 5 stencil quantities, then features 30 and 31
+constexpr int kStageW = 7;
+
 struct GuessArgs {
   FeatArgs f;
   const float* p;                  // FP32 parameters (biases read from here)
   const __nv_bfloat16 *w1, *w2, *w3;
   int* queue;
-  float* stage;                    // [cells][5] per-cell feature values (FP32)
+  float* stage;                    // [cells][kStageW] per-cell values (FP32)
   int64_t stage_cap;               // floats the stage buffer holds
   int* err;                        // set when a tensor-core wait times out
   int polls;                       // polls of the layer waits (clean-up: the default)
@@ -933,6 +1089,7 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
   __shared__ uint32_t tmem_base;
   __shared__ double red_s[2][8];
   __shared__ int col_s[2];
+  __shared__ float cx_s[2][4];     // features 26..29 of each worker's column
   const FeatArgs& a = g.f;
   const int tid = threadIdx.x;
   // weights in the core-matrix layout; W3 padded with zero rows to N = 16
@@ -1022,21 +1179,11 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
     // the column inside the batch and its staged features inside the stage
     // buffer (uniform over the worker: a failed column is skipped by all)
     if (!SDCEF_CHECK_W(a.chk, off >= 0 && N >= 0 && off + N <= cells &&
-                                  (off + N) * 5 <= g.stage_cap,
+                                  (off + N) * kStageW <= g.stage_cap,
                        sdcef_chk::kMlpStage))
       continue;
-    auto fphi = [&](int i) {
-      double q = 0.0;
-      for (int s = 0; s < a.nsp; ++s) q += (double)a.val[s] * a.n_ion[(int64_t)s * cells + off + i];
-      return q;
-    };
-    double mn = 0.0, mq = 0.0, mp = 0.0;
-    for (int i = t; i < N; i += W) {
-      mn = fmax(mn, fabs(a.ne[off + i]));
-      mq = fmax(mq, fabs(fphi(i)));
-      mp = fmax(mp, fabs(a.phi[off + i]));
-    }
-    double mx[3] = {mn, mq, mp};
+    double mx[3];
+    col_maxima(a, cells, off, N, t, W, mx);
     for (int k = 0; k < 3; ++k) {
       double v = mx[k];
       for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -1048,37 +1195,56 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
     }
     const double sn = fmax(fmax(mx[0], mx[1]), 1.0);
     const double sp = fmax(fmax(mx[2], fmax(fabs(a.v_left[c]), fabs(a.v_right[c]))), 1.0);
-    const double isn = 1.0 / sn, isp = 1.0 / sp;
     if (N < 1) continue;
+    const float isn = (float)(1.0 / sn), isp = (float)(1.0 / sp);
+    // the five per-cell quantities of the stencil features and features 30, 31
+    // (ion potential and field, poisson_column), staged once in FP32
+    float* st = g.stage + off * kStageW;
+    if (t == 0) {
+      const ColCtx cx = col_context(sn, N, a.v_left[c], a.v_right[c], a.dt[c]);
+      for (int q = 0; q < 4; ++q) cx_s[wg][q] = cx.f[q];
+    }
+    auto wbar = [&] { tc::bar(barid, W); };
+    for (int i = t; i < N; i += W) {
+      float v[5];
+      cell_quantities(a, cells, off, N, i, isn, isp, v);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) st[i * kStageW + q] = v[q];
+      if (N < 2) st[i * kStageW + 5] = st[i * kStageW + 6] = 0.0f;
+    }
+    if (N >= 2) {
+      const double L = a.length[c], hk = (L / N) * (L / N) / kKapGuess;
+      const float L2h_isp = 0.5f * (float)N * isp;
+      poisson_column(
+          N, 0.0, 0.0, t, W, red, wbar, [&](int i) { return -hk * fphi_cell(a, cells, off + i); },
+          [&](int i, double phi_i, double S_prev, double S_i, double D) {
+            ion_features(phi_i, S_prev, S_i, D, L2h_isp, isp, &st[i * kStageW + 5],
+                         &st[i * kStageW + 6]);
+          });
+    }
+    tc::bar(barid, W);
     auto mir = [&](int j) {
       if (j < 0) j = -j - 1;
       if (j >= N) j = 2 * N - 1 - j;
       return min(max(j, 0), N - 1);
     };
-    // the five per-cell values of the features, staged once in FP32
-    float* st = g.stage + off * 5;
-    for (int i = t; i < N; i += W) {
-      const int kp = (i + 1 < N) ? i + 1 : N - 1;
-      const int km = (i >= 1) ? i - 1 : 0;
-      st[i * 5 + 0] = (float)(a.ne[off + i] * isn);
-      st[i * 5 + 1] = (float)(a.phi[off + i] * isp);
-      st[i * 5 + 2] = (float)(fphi(i) * isn);
-      st[i * 5 + 3] = (float)(a.T[off + i] * (1.0 / 2000.0));
-      st[i * 5 + 4] = (float)(-(a.phi[off + kp] - a.phi[off + km]) * 0.5 * isp);
-    }
-    tc::bar(barid, W);
-    for (int r0 = 0; r0 < N; r0 += tc::kTile) {
-      // row r of A: the 25 stencil features of cell i (f = 5 o + q: quantity q
-      // of cell i + o - 2), zero-padded to K = 32; the worker's two threads of
-      // row r build features 0..15 and 16..31
-      const int i = min(r0 + r, N - 1);
+    // row r of A: the 25 stencil features of cell i (f = 5 o + q: quantity q
+    // of cell i + o - 2) and the 7 of the column context; thread half H of row
+    // r builds features 16 H .. 16 H + 15 (the feature index is a compile-time
+    // constant in each instance)
+    auto build_row = [&](int i, auto hc) {
+      constexpr int H = decltype(hc)::value;
 #pragma unroll
-      for (int ch = 2 * half; ch < 2 * half + 2; ++ch) {
+      for (int cl = 0; cl < 2; ++cl) {
+        const int ch = 2 * H + cl;
         float f8[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int f = ch * 8 + u;
-          f8[u] = f < kFeat ? st[mir(i + f / 5 - 2) * 5 + f % 5] : 0.0f;
+          if (f < kFeat) f8[u] = st[mir(i + f / 5 - 2) * kStageW + f % 5];
+          else if (f == kFeat) f8[u] = ctx_pos(i, N);
+          else if (f < kFeat + 5) f8[u] = cx_s[wg][f - kFeat - 1];
+          else f8[u] = st[i * kStageW + (f - kFeat)];
         }
         uint4 w;
         w.x = pack_bf16(f8[0], f8[1]);
@@ -1089,6 +1255,12 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
         if (!SDCEF_CHECK_W(a.chk, ao + 16 <= tc::kABytes, sdcef_chk::kMlpSmem)) ao = 0;
         *reinterpret_cast<uint4*>(sA + ao) = w;
       }
+    };
+    const bool poisson = (a.comps & 4) && N >= 2;
+    for (int r0 = 0; r0 < N; r0 += tc::kTile) {
+      const int i = min(r0 + r, N - 1);
+      if (half == 0) build_row(i, std::integral_constant<int, 0>{});
+      else build_row(i, std::integral_constant<int, 1>{});
       bool ok = run_layer(1);
       if (ok) {
         tc_epilogue(lane_addr, sb, sA, r, 2 * half);
@@ -1105,7 +1277,8 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
         const int64_t gi = off + row;
         const float yn = y[0] + sb[2 * kHid], yp = y[1] + sb[2 * kHid + 1];
         a.ne_g[gi] = a.ne[gi] + ((a.comps & 1) ? sn * (double)yn : (ok ? 0.0 : (double)NAN));
-        a.phi_g[gi] = a.phi[gi] + ((a.comps & 2) ? sp * (double)yp : 0.0);
+        if (!poisson)
+          a.phi_g[gi] = a.phi[gi] + ((a.comps & 6) == 2 ? sp * (double)yp : 0.0);
       }
       // the next tile's layer 1 overwrites these TMEM columns after the barrier
       tc::fence_before();
@@ -1116,6 +1289,16 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
         tc::wait_phase(s_mbar, phase ^ 1u);
         break;
       }
+    }
+    // the potential at the guessed n_e: root of the Poisson residual
+    // (uniform over the worker: failed and poisson are)
+    if (poisson && !failed) {
+      tc::bar(barid, W);   // every n_e of the column written
+      const double L = a.length[c], hk = (L / N) * (L / N) / kKapGuess;
+      poisson_column(
+          N, a.v_left[c], a.v_right[c], t, W, red, wbar,
+          [&](int i) { return hk * (a.ne_g[off + i] - fphi_cell(a, cells, off + i)); },
+          [&](int i, double phi_i, double, double, double) { a.phi_g[off + i] = phi_i; });
     }
   }
   tc::fence_before();
@@ -1286,6 +1469,8 @@ FeatArgs feat_args(const sdcef_batch* b) {
   memset(&a, 0, sizeof(a));
   a.ncol = b->ncol;
   a.col_off = b->col_off;
+  a.length = b->length;
+  a.dt = b->dt;
   a.v_left = b->v_left;
   a.v_right = b->v_right;
   a.ne = b->ne_old;
@@ -1480,7 +1665,7 @@ int sdcef_mlp_train_step(sdcef_mlp* h, const void* X_bf16, const float* T, int64
 
 int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int components,
                     double* ne_guess, double* phi_guess) {
-  if (!h || !ne_guess || !phi_guess || ncells < 0 || components < 0 || components > 3)
+  if (!h || !ne_guess || !phi_guess || ncells < 0 || components < 0 || components > 7)
     return report_error(SDCEF_ERR_INVALID, "mlp_guess: bad arguments");
   int rc = check_batch(b);
   if (rc || b->ncol == 0) return rc;
@@ -1499,9 +1684,9 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
   g.queue = (int*)h->loss + 4;   // spare words of the loss buffer
   g.err = (int*)h->loss + 5;
   g.polls = h->polls;
-  if (ncells * 5 > h->max_rows * (kIn / 2))
+  if (ncells > h->max_rows || ncells * kStageW > h->max_rows * (kIn / 2))
     return report_error(SDCEF_ERR_CAPACITY, "mlp_guess: ncells exceeds max_rows");
-  g.stage = (float*)h->X;        // [cells][5] FP32 inside the [max_rows][32] BF16 buffer
+  g.stage = (float*)h->X;        // [cells][kStageW] FP32 inside the [max_rows][32] BF16 buffer
   g.stage_cap = h->max_rows * (kIn / 2);
   cudaError_t e = cudaMemsetAsync(g.queue, 0, sizeof(int), h->st);
   if (e != cudaSuccess) return cuda_fail(e);

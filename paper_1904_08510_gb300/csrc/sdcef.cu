@@ -274,7 +274,7 @@ void sdcef_default_params(sdcef_params* p) {
   p->gas_molar_mass = 0.028;
   p->bc_electron = SDCEF_BC_ABSORBING;
   p->threads_per_column = 0;
-  p->guess_newton_cap = 16;
+  p->guess_newton_cap = 5;
   p->guess_reject_ratio = 30.0;
 }
 

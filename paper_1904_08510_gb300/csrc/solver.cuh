@@ -28,6 +28,7 @@ constexpr double kNA = 6.02214076e23;
 constexpr double kLambdaFD = 6.0554544523933395e-06;
 // Newton steps a column may take for the error test after the residual test holds
 constexpr int kMaxPolish = 2;
+constexpr double kErrMargin = 10.0;   // error_test: a pass this close to the bar is re-taken
 
 
 // --------------------------------------------------------------------------
@@ -362,7 +363,7 @@ struct ColShared {
   int mgc;                              // V-cycles of this column's multigrid block solves
   // error test: factors of an earlier Newton step are in the slot; Newton steps
   // taken for the error test; the current step is one of them
-  int have_prec, polished, polish;
+  int have_prec, polished;
   // transport tables: table coordinates of the electrode faces (c index, and
   // the factor turning |G| into the E/N index) and dv/dG = mu + G mu'(G) there
   double tcL, sxL, tcR, sxR, muL[2], muR[2];
@@ -1281,10 +1282,14 @@ __device__ __noinline__ bool column_setup(const KArgs& a, Geo& g, ColShared& cs,
 // last Newton step's, with the exact Schur form P = J) estimates the scaled
 // error of the iterate. True if max|s_n ehat_n| <= eps_E max|n| and
 // max|s_phi ehat_phi| <= eps_E max|phi| over the column, or if the estimate is
-// not finite (no estimate: the residual test alone decides).
+// not finite (no estimate: the residual test alone decides). Returns 0 (fails),
+// 1 (passes) or 2 (passes within a factor kErrMargin of the bar: from a
+// supplied start an estimate on factors of the previous iterate is then taken
+// again at X^(l), since the change of J over a large last step, as a learned
+// start can end with, can misjudge it; from X^n the last step is small).
 // --------------------------------------------------------------------------
 template <int TPB, typename KR, typename PR, int VAR>
-__device__ __forceinline__ bool error_test(const KArgs& a, const Geo& g, ColShared& cs,
+__device__ __noinline__ int error_test(const KArgs& a, const Geo& g, ColShared& cs,
                                         const Slot<TPB, KR, PR>& S, int cur, PR* sh,
                                         double* red) {
   const int tid = g.tid, kt = g.kt;
@@ -1318,8 +1323,10 @@ __device__ __forceinline__ bool error_test(const KArgs& a, const Geo& g, ColShar
   for (int q = 0; q < 4; ++q) v[q] = __longlong_as_double(m[q]);
   block_reduce<TPB>(v, 4, true, red);
   const double en = v[0] * cs.sn, ep = v[1] * cs.sp;
-  if (!(en <= 1.79e308) || !(ep <= 1.79e308)) return true;
-  return en <= a.p.eps_E * v[2] && ep <= a.p.eps_E * v[3];
+  if (!(en <= 1.79e308) || !(ep <= 1.79e308)) return 1;
+  if (!(en <= a.p.eps_E * v[2] && ep <= a.p.eps_E * v[3])) return 0;
+  const double lo = a.p.eps_E * (1.0 / kErrMargin);
+  return (en > lo * v[2] || ep > lo * v[3]) ? 2 : 1;
 }
 
 // --------------------------------------------------------------------------
@@ -1458,7 +1465,6 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       cs.kh2_43 = (4.0 / 3.0) * cs.kh2;
       cs.have_prec = 0;
       cs.polished = 0;
-      cs.polish = 0;
     }
     if (start_differs) {
       if (a.mode == MODE_PRECOND) {
@@ -1548,30 +1554,47 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
     const int cap = (guessed && attempt == 0) ? min(a.p.guess_cap, a.p.max_newton)
                                               : a.p.max_newton - newton;
     status = SDCEF_STATUS_MAX_NEWTON;
+    bool prec_cur = false;   // the factors were built at the current iterate (CTA-uniform)
+    bool pbad = false;       // and their pivot check
+    bool polish = false;     // this step serves the error test (CTA-uniform)
+    const bool from_guess = supplied && attempt == 0;   // the start is the supplied one
     for (int l = 0;; ++l) {
       if (!(fninf <= 1.79e308)) { status = SDCEF_STATUS_NONFINITE; break; }
-      // cs.polish: this step is taken after the residual test held, for the
-      // error test (kept in shared memory: it is read again by the line search)
+      // polish: this step is taken after the residual test held, for the
+      // error test (the line search reads it again). The error test and its polish steps are bounded by the Newton budget,
+      // not by the cap of a supplied start: a start that passes the residual
+      // test within the cap is judged like any other.
       if (fninf < a.p.eps_F) {
-        if (!(a.p.eps_E > 0.0) || l >= cap || cs.polished >= kMaxPolish) {
+        if (!(a.p.eps_E > 0.0) || newton >= a.p.max_newton || cs.polished >= kMaxPolish) {
           status = SDCEF_STATUS_OK;
           break;
         }
         if (!cs.have_prec) {   // no Newton step yet: factors at X^(l)
-          bool fbad = false;
-          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &fbad);
+          pbad = false;
+          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &pbad);
+          prec_cur = true;
         }
-        if (error_test<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, red)) {
+        int et;
+        for (;;) {   // a marginal pass on the last step's factors is taken again at X^(l)
+          et = error_test<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, red);
+          if (et != 2 || prec_cur || !from_guess) break;
+          pbad = false;
+          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &pbad);
+          prec_cur = true;
+        }
+        if (et != 0) {
           status = SDCEF_STATUS_OK;
           break;
         }
-        if (tid == 0) cs.polish = 1;
-      } else if (tid == 0) {
-        cs.polish = 0;
+        polish = true;
+      } else {
+        polish = false;
       }
-      if (l >= cap) { status = SDCEF_STATUS_MAX_NEWTON; break; }
-      // preconditioner at X^(l) and ||S_X^{-1} X||_2 (X = (n, phi))
-      prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
+      if (l >= cap && !polish) { status = SDCEF_STATUS_MAX_NEWTON; break; }
+      // preconditioner at X^(l) (unless the error test built it there) and
+      // ||S_X^{-1} X||_2 (X = (n, phi))
+      if (!prec_cur) prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
+      else bad = bad || pbad;
       if (tid == 0) cs.have_prec = 1;
       {
         double s = 0.0;
@@ -1841,7 +1864,6 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       double lam = 1.0;
       bool accepted = false;
       const int nxt = 1 - cur;
-      const bool polish = cs.polish != 0;
       const int max_ls = polish ? 0 : a.p.max_ls;
       double tnorm[4];
       for (int t = 0; t <= max_ls; ++t) {
@@ -1876,7 +1898,8 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       fninf = scaled_inf(tnorm);
       fn2 = scaled_two(tnorm);
       ++newton;
-      if (tid == 0) cs.polished += cs.polish;
+      prec_cur = false;
+      if (tid == 0) cs.polished += polish ? 1 : 0;
       if (a.p.eps_X > 0.0) {
         block_reduce<TPB>(&smax, 1, true, red);
         if (lam * smax < a.p.eps_X && fninf >= a.p.eps_F) { status = SDCEF_STATUS_OK; break; }

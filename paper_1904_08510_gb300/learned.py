@@ -135,10 +135,11 @@ def train(X, T, *, steps: int, batch: int = 32768, lr: float = 2e-3, lr_end: flo
 
 
 def evaluate(params, ncol: int, seed: int, *, kind="single", n_range=(512, 2048), device="cuda:0",
-             reps=3, variants=(("learned", 1),)):
+             reps=3, variants=(("learned", 5),)):
     """Held-out solves with and without the learned guess (FP64 batched JFNK).
     variants: (name, components) pairs; components = 1 applies the predicted
-    n_e increment only, 3 applies n_e and phi."""
+    n_e increment only, 3 applies n_e and phi, 5 the n_e increment with the
+    potential of the guessed charge (root of the Poisson residual)."""
     import torch
     b = make_batch(kind, ncol, seed, n_range=n_range)
     db = S.DeviceBatch.from_host(b, device)
@@ -175,7 +176,7 @@ def evaluate(params, ncol: int, seed: int, *, kind="single", n_range=(512, 2048)
 
 
 def evaluate_sweep(params, ncol: int, seed: int, *, n_cells=1024, device="cuda:0", reps=3,
-                   components=1):
+                   components=5):
     """The MISDC electric sweep's first SDC iteration (workload.sdc_batch columns)
     with and without the learned start: Newton and GMRES iterations and time of
     that iteration (guess kernel included)."""
@@ -262,11 +263,11 @@ def main():
                                 train_cells=args.train_cells, family=args.family))
     if args.family == "sweep":
         ev = {f"components_{c}": evaluate_sweep(params, args.eval_ncol, 5_000_000, components=c)
-              for c in (1, 3)}
+              for c in (1, 5)}
     else:
         b, res = evaluate(params, args.eval_ncol, 2_000_000, kind=args.family,
                           n_range=None if args.family == "ragged" else (512, 2048),
-                          variants=(("learned_ne", 1), ("learned_ne_phi", 3)))
+                          variants=(("learned_ne", 1), ("learned_ne_poisson_phi", 5)))
         ev = {k: {kk: vv for kk, vv in v.items() if kk not in ("ne", "phi")} for k, v in res.items()}
     summary = dict(family=args.family, train_columns=args.ncol, train_cells=args.train_cells,
                    train_samples=int(X.shape[0]), converged=nok,

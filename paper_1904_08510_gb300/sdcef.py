@@ -45,7 +45,7 @@ EXPORTS = ("sdcef_default_params", "sdcef_create", "sdcef_destroy", "sdcef_set_p
            "sdcef_mlp_set_wait_polls", "sdcef_checks_compiled", "sdcef_check_word",
            "sdcef_mlp_check_word", "sdcef_autotune_on_chip", "sdcef_solve_batches_host")
 MLP_NPARAM = 20994
-GUESS_NE, GUESS_PHI = 1, 2
+GUESS_NE, GUESS_PHI, GUESS_PHI_POISSON = 1, 2, 4
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NOALLOC_MAX_COLS = 65536
 NOALLOC_MAX_COL_CELLS = 4096

@@ -1,7 +1,8 @@
 """The learned-start solve against the oracle's converged root.
 
 The path under test is a learned Newton start (the BF16 network's n_e
-increment, tcgen05 inference kernel) followed by the batched solve at the
+increment and the potential of the guessed charge, tcgen05 inference kernel)
+followed by the batched solve at the
 bench tolerance ||S_F^-1 F||_inf < 1e-10 with the error test of the stop
 (eps_E = 5e-10, the default), in FP64, with the double-float preconditioner
 and with the FP32 Krylov solve and preconditioner. The plain start (X^n) is
@@ -80,7 +81,7 @@ def test_learned_start_matches_converged_oracle_root(family):
     db = S.DeviceBatch.from_host(b, d)
     mlp = S.MLP(b.ncells)
     mlp.set_params(Lrn.load(weights))
-    ne_g, ph_g = mlp.guess(db, components=S.GUESS_NE)
+    ne_g, ph_g = mlp.guess(db, components=S.GUESS_NE | S.GUESS_PHI_POISSON)
     mlp.check()
     gdb = db.with_guess(ne_g, ph_g)
     lmax = int(b.lengths().max())
