@@ -1555,7 +1555,6 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
                                               : a.p.max_newton - newton;
     status = SDCEF_STATUS_MAX_NEWTON;
     bool prec_cur = false;   // the factors were built at the current iterate (CTA-uniform)
-    bool pbad = false;       // and their pivot check
     bool polish = false;     // this step serves the error test (CTA-uniform)
     const bool from_guess = supplied && attempt == 0;   // the start is the supplied one
     for (int l = 0;; ++l) {
@@ -1569,17 +1568,17 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
           status = SDCEF_STATUS_OK;
           break;
         }
+        // (a bad pivot leaves a non-finite estimate, which passes: the residual
+        // test then decides; a polish step reports it through bad)
         if (!cs.have_prec) {   // no Newton step yet: factors at X^(l)
-          pbad = false;
-          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &pbad);
+          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
           prec_cur = true;
         }
         int et;
         for (;;) {   // a marginal pass on the last step's factors is taken again at X^(l)
           et = error_test<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, red);
           if (et != 2 || prec_cur || !from_guess) break;
-          pbad = false;
-          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &pbad);
+          prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
           prec_cur = true;
         }
         if (et != 0) {
@@ -1594,7 +1593,6 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
       // preconditioner at X^(l) (unless the error test built it there) and
       // ||S_X^{-1} X||_2 (X = (n, phi))
       if (!prec_cur) prec_factor<TPB, KR, PR, VAR>(a, g, cs, S, cur, sh, halo, &bad);
-      else bad = bad || pbad;
       if (tid == 0) cs.have_prec = 1;
       {
         double s = 0.0;
