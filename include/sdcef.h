@@ -175,6 +175,12 @@ typedef struct {
                          either way; the shared memory is taken from the L1
                          cache, so which is faster depends on the batch:
                          sdcef_autotune_on_chip measures it.                    */
+  double guess_progress; /* a supplied start whose Newton step leaves the scaled
+                         residual max-norm above this fraction of the previous
+                         step's (while the residual test does not hold) is
+                         judged to wander and restarts from X^n, as after
+                         guess_newton_cap steps (which must be > 0); 0 = never.
+                         In [0, 1].                                             */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32
@@ -221,8 +227,9 @@ typedef struct {
  * mobility 0.4 (Sec. 2.2), ls_alpha 1e-4, eps_r 1, restart 8, 50 Newton
  * steps, 200 Krylov iterations per step, 20 halvings, FP64, exact Schur
  * preconditioner, absorbing electrodes, automatic threads per column, and a
- * supplied start rejected if its residual is over 30x the plain start's and
- * judged after 5 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
+ * supplied start rejected if its residual is over 30x the plain start's,
+ * restarted from X^n after a step that leaves its residual above 0.3x the
+ * previous one and judged after 8 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
  * blocks (the optimum of Sec. 4.2), at most 50 V-cycles per block solve and
  * operator-dependent transfers; the paper's ion transport in the SDC sweep
  * (SDCEF_ION_GODUNOV); constant electron transport, gas molar mass 0.028 kg/mol. */

@@ -142,6 +142,7 @@ extern "C" int sdcef_solve_batch_noalloc(const sdcef_params* p, const sdcef_batc
   a.p.precond = p->precond;
   a.p.guess_cap = p->guess_newton_cap;
   a.p.guess_ratio = p->guess_reject_ratio;
+  a.p.guess_prog = p->guess_progress;
   a.p.mg_gA = p->mg_gamma_A;
   a.p.mg_gS = p->mg_gamma_S;
   a.p.mg_maxc = p->mg_max_cycles;

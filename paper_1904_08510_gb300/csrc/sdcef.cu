@@ -87,7 +87,7 @@ int check_params(const sdcef_params* p, int m_cap) {
   if (p->restart_m < 1 || p->restart_m > SDCEF_MAX_RESTART || (m_cap > 0 && p->restart_m > m_cap))
     return set_err(SDCEF_ERR_INVALID, "params: restart_m out of range");
   if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0 || p->guess_newton_cap < 0 ||
-      !(p->guess_reject_ratio >= 0.0))
+      !(p->guess_reject_ratio >= 0.0) || !(p->guess_progress >= 0.0 && p->guess_progress <= 1.0))
     return set_err(SDCEF_ERR_INVALID, "params: iteration caps out of range");
   if (p->precision != SDCEF_FP64 && p->precision != SDCEF_MIXED && p->precision != SDCEF_MIXED_DF)
     return set_err(SDCEF_ERR_INVALID, "params: precision");
@@ -188,6 +188,7 @@ KArgs base_args(sdcef_ctx* ctx, const sdcef_batch* b, int tpb) {
   a.p.precond = p.precond;
   a.p.guess_cap = p.guess_newton_cap;
   a.p.guess_ratio = p.guess_reject_ratio;
+  a.p.guess_prog = p.guess_progress;
   a.p.mg_gA = p.mg_gamma_A;
   a.p.mg_gS = p.mg_gamma_S;
   a.p.mg_maxc = p.mg_max_cycles;
@@ -274,8 +275,9 @@ void sdcef_default_params(sdcef_params* p) {
   p->gas_molar_mass = 0.028;
   p->bc_electron = SDCEF_BC_ABSORBING;
   p->threads_per_column = 0;
-  p->guess_newton_cap = 5;
+  p->guess_newton_cap = 8;
   p->guess_reject_ratio = 30.0;
+  p->guess_progress = 0.3;
 }
 
 const char* sdcef_last_error(void) { return g_err.c_str(); }

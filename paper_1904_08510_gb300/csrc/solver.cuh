@@ -41,6 +41,7 @@ struct DevParams {
   int m, max_newton, max_krylov, max_ls, bc, precond;
   int guess_cap;   // Newton steps from a supplied start before restarting from X^n (0 = never)
   double guess_ratio;   // reject a supplied start with ||Fhat|| > ratio ||Fhat(X^n)|| (0 = never)
+  double guess_prog;    // restart a supplied start whose step keeps ||Fhat||_inf above this fraction (0 = never)
   double mg_gA, mg_gS;  // multigrid tolerances of the two blocks (<= 0: exact block solve)
   int mg_maxc, mg_transfer;
   int transport;        // SDCEF_TRANSPORT_*
@@ -1893,11 +1894,20 @@ __global__ void __launch_bounds__(TPB, VAR == kVarBase ? 512 / TPB : 1) jfnk_ker
           smax = fmax(smax, fabs(dcoef) * fmax(fabs(dn), fabs(dp)));
         }
       cur = nxt;
+      const double fprev = fninf;
       fninf = scaled_inf(tnorm);
       fn2 = scaled_two(tnorm);
       ++newton;
       prec_cur = false;
       if (tid == 0) cs.polished += polish ? 1 : 0;
+      // a supplied start whose step keeps the residual above guess_prog times
+      // the previous one wanders: restart from X^n (CTA-uniform)
+      if (guessed && attempt == 0 && a.p.guess_prog > 0.0 && !(fninf < a.p.eps_F) &&
+          fninf > a.p.guess_prog * fprev) {
+        __syncthreads();
+        status = SDCEF_STATUS_MAX_NEWTON;
+        break;
+      }
       if (a.p.eps_X > 0.0) {
         block_reduce<TPB>(&smax, 1, true, red);
         if (lam * smax < a.p.eps_X && fninf >= a.p.eps_F) { status = SDCEF_STATUS_OK; break; }

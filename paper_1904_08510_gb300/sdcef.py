@@ -61,7 +61,8 @@ class Params(C.Structure):
                 ("mg_gamma_A", C.c_double), ("mg_gamma_S", C.c_double),
                 ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int), ("ion_scheme", C.c_int),
                 ("transport", C.c_int), ("gas_molar_mass", C.c_double), ("eps_E", C.c_double),
-                ("stall_ratio", C.c_double), ("krylov_on_chip", C.c_int)]
+                ("stall_ratio", C.c_double), ("krylov_on_chip", C.c_int),
+                ("guess_progress", C.c_double)]
 
 
 class BatchC(C.Structure):

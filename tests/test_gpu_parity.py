@@ -454,10 +454,11 @@ def test_autotune_picks_a_candidate_and_keeps_results():
 
 def test_bad_guess_is_judged_and_replaced_by_plain_start():
     """A start far from the root (rough noise in n_e and phi) fails Newton. The
-    solver judges a supplied start twice: its residual against the plain
-    start's before the first step (guess_reject_ratio) and its progress after
-    guess_newton_cap steps; either judge alone brings the column back to X^n,
-    and it converges to the same root as the plain solve."""
+    solver judges a supplied start three times: its residual against the plain
+    start's before the first step (guess_reject_ratio), the residual reduction
+    of each step (guess_progress) and its convergence within guess_newton_cap
+    steps; each judge alone brings the column back to X^n, and it converges to
+    the same root as the plain solve."""
     d = dev()
     b = make_batch("single", 6, 77, n_cells=300)
     rng = np.random.default_rng(9)
@@ -469,12 +470,19 @@ def test_bad_guess_is_judged_and_replaced_by_plain_start():
                                  max_newton=20), dict(precond=2), guess=(g_ne, g_phi))
     ratio_only, _ = _solve_both(b, dict(eps_F=1e-12, guess_newton_cap=0), dict(precond=2),
                                 guess=(g_ne, g_phi))
-    cap_only, _ = _solve_both(b, dict(eps_F=1e-12, guess_reject_ratio=0.0), dict(precond=2),
-                              guess=(g_ne, g_phi))
+    cap_only, _ = _solve_both(b, dict(eps_F=1e-12, guess_reject_ratio=0.0, guess_progress=0.0),
+                              dict(precond=2), guess=(g_ne, g_phi))
+    # the progress judge alone: a wandering step sends the column back to X^n
+    # long before a cap of 40 steps
+    prog_only, _ = _solve_both(b, dict(eps_F=1e-12, guess_reject_ratio=0.0, guess_newton_cap=40,
+                                       guess_progress=0.3), dict(precond=2), guess=(g_ne, g_phi))
     assert (plain["status"] == S.STATUS_OK).all()
     assert (judged["status"] == S.STATUS_OK).all()
     assert (raw["status"] != S.STATUS_OK).any()
     assert (ratio_only["status"] == S.STATUS_OK).all()   # rejected before the first step
     assert (cap_only["status"] == S.STATUS_OK).all()     # restarted after the cap
+    assert (prog_only["status"] == S.STATUS_OK).all()    # restarted after a wandering step
+    assert prog_only["newton_it"].max() < 40 + plain["newton_it"].max()
+    assert colerr(b, prog_only["ne"], plain["ne"]).max() <= 1e-9
     assert colerr(b, judged["ne"], plain["ne"]).max() <= 1e-9
     assert colerr(b, judged["phi"], plain["phi"]).max() <= 1e-9
