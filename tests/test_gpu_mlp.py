@@ -74,6 +74,39 @@ def test_features_match_oracle(n_range):
     mlp.close()
 
 
+def test_features_and_poisson_start_with_two_species_and_varied_steps():
+    """The general charge f_phi = sum nu_s n_s (a cation and a 5 % anion) and
+    per-column time steps and electrode potentials: features against the
+    oracle (one BF16 ulp), and the Poisson start against the oracle's banded
+    solve of F_phi = 0 with the kernel's own n_e (1e-9)."""
+    d = dev()
+    b = make_batch("ragged", 7, 57, n_range=(2, 400))
+    rng = np.random.default_rng(4)
+    b.n_ion = np.vstack([b.n_ion, 0.05 * b.n_ion * np.abs(rng.standard_normal(b.ncells))])
+    b.valence = np.array([1, -1], dtype=np.int32)
+    b.dt = 10.0 ** rng.uniform(-7, -4, b.ncol)
+    b.v_left = rng.uniform(-50, 50, b.ncol)
+    db = S.DeviceBatch.from_host(b, d)
+    mlp = S.MLP(b.ncells)
+    X = mlp.features(db).float().cpu().numpy()
+    ref = M.bf16_round(M.features(b))
+    tol = 2.0 ** -7 * np.abs(ref) + 1e-30
+    tol[:, 25:] += 1e-6
+    assert np.all(np.abs(X - ref) <= tol), np.argwhere(np.abs(X - ref) > tol)[:5]
+    flat, _ = rounded_params(17)
+    mlp.set_params(flat)
+    ne, phi = mlp.guess(db, components=S.GUESS_NE | S.GUESS_PHI_POISSON)
+    mlp.check()
+    ne, phi = ne.cpu().numpy(), phi.cpu().numpy()
+    f = (b.valence[:, None] * b.n_ion).sum(axis=0)
+    for c in range(b.ncol):
+        sl = slice(b.col_off[c], b.col_off[c + 1])
+        N = sl.stop - sl.start
+        pr = M.poisson_potential(ne[sl] - f[sl], b.length[c] / N, b.v_left[c], b.v_right[c])
+        assert np.abs(phi[sl] - pr).max() <= 1e-9 * np.abs(pr).max(), c
+    mlp.close()
+
+
 def test_targets_and_guess_round_trip():
     d = dev()
     b = make_batch("ragged", 4, 8, n_range=(20, 200))
