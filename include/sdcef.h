@@ -181,6 +181,11 @@ typedef struct {
                          judged to wander and restarts from X^n, as after
                          guess_newton_cap steps (which must be > 0); 0 = never.
                          In [0, 1].                                             */
+  int sdc_poisson_start; /* sdcef_sdc_sweep, iterations k >= 2: 1 (default) starts
+                         from the previous iterate's n_e with the potential of
+                         its charge under the new provisional ions (the root of
+                         F_phi, which is linear in phi); 0 starts from the
+                         previous iterate as it is. The root is the same.      */
 } sdcef_params;
 
 #define SDCEF_MAX_RESTART 32

@@ -294,6 +294,27 @@ __global__ void feat_kernel(FeatArgs a) {
       });
 }
 
+// Potential of the given electron density: for every column of two or more
+// cells, phi = the root of the Poisson residual at n_e = a.ne with the ion
+// densities a.n_ion (kappa = eps_0 eps_r / e), written to phi_out; columns of
+// one cell are left as they are. One CTA per column (grid-stride over columns).
+__global__ void poisson_start_kernel(FeatArgs a, double kappa, double* phi_out) {
+  __shared__ double red[32];
+  const int64_t cells = a.col_off[a.ncol];
+  for (int64_t c = blockIdx.x; c < a.ncol; c += gridDim.x) {
+    const int64_t off = a.col_off[c];
+    const int N = (int)(a.col_off[c + 1] - off);
+    if (!SDCEF_CHECK_W(a.chk, off >= 0 && N >= 0 && off + N <= cells, sdcef_chk::kMlpRow)) continue;
+    if (N < 2) continue;
+    const double L = a.length[c], hk = (L / N) * (L / N) / kappa;
+    poisson_column(
+        N, a.v_left[c], a.v_right[c], (int)threadIdx.x, (int)blockDim.x, red,
+        [] { __syncthreads(); },
+        [&](int i) { return hk * (a.ne[off + i] - fphi_cell(a, cells, off + i)); },
+        [&](int i, double phi_i, double, double, double) { phi_out[off + i] = phi_i; });
+  }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -1705,6 +1726,30 @@ int sdcef_mlp_guess(sdcef_mlp* h, const sdcef_batch* b, int64_t ncells, int comp
 }
 
 int sdcef_mlp_last_launch_count(const sdcef_mlp* h) { return h ? h->launches : 0; }
+
+}  // extern "C"
+
+namespace sdcef_impl {
+// The potential consistent with an electron density (poisson_start_kernel),
+// enqueued on st: batch geometry, electrode potentials and valences from b,
+// ion densities n_ion ([n_species][cells], device), n_e ne (device); phi_out
+// (device) may alias nothing the kernel reads. The SDC sweep starts its later
+// iterations from it.
+cudaError_t launch_poisson_start(const sdcef_batch* b, const double* ne, const double* n_ion,
+                                 double kappa, double* phi_out, cudaStream_t st) {
+  FeatArgs a = feat_args(b);
+  a.ne = ne;
+  a.n_ion = n_ion;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(b->ncol, (int64_t)std::max(sms, 1) * 8);
+  poisson_start_kernel<<<grid, 256, 0, st>>>(a, kappa, phi_out);
+  return cudaGetLastError();
+}
+}  // namespace sdcef_impl
+
+extern "C" {
 
 int sdcef_mlp_check_word(sdcef_mlp* h, unsigned* word) {
   if (!h || !word) return report_error(SDCEF_ERR_INVALID, "mlp_check_word: NULL argument");

@@ -84,6 +84,8 @@ int check_params(const sdcef_params* p, int m_cap) {
                    "params: eps_F, eps_X, eps_E, stall_ratio, gamma, mobility, ls_alpha, eps_r out of range");
   if (p->krylov_on_chip != 0 && p->krylov_on_chip != 1)
     return set_err(SDCEF_ERR_INVALID, "params: krylov_on_chip must be 0 or 1");
+  if (p->sdc_poisson_start != 0 && p->sdc_poisson_start != 1)
+    return set_err(SDCEF_ERR_INVALID, "params: sdc_poisson_start must be 0 or 1");
   if (p->restart_m < 1 || p->restart_m > SDCEF_MAX_RESTART || (m_cap > 0 && p->restart_m > m_cap))
     return set_err(SDCEF_ERR_INVALID, "params: restart_m out of range");
   if (p->max_newton < 0 || p->max_krylov < 1 || p->max_linesearch < 0 || p->guess_newton_cap < 0 ||
@@ -244,6 +246,9 @@ int run(sdcef_ctx* ctx, KArgs& a, int tpb) {
 // Shared with the allocation-free entry point (noalloc.cu).
 namespace sdcef_impl {
 int report_error(int code, const char* msg) { return set_err(code, msg); }
+// mlp.cu: the potential of a given electron density (root of F_phi) per column
+cudaError_t launch_poisson_start(const sdcef_batch* b, const double* ne, const double* n_ion,
+                                 double kappa, double* phi_out, cudaStream_t st);
 int validate_params(const sdcef_params* p) { return check_params(p, 0); }
 }  // namespace sdcef_impl
 
@@ -278,6 +283,7 @@ void sdcef_default_params(sdcef_params* p) {
   p->guess_newton_cap = 8;
   p->guess_reject_ratio = 30.0;
   p->guess_progress = 0.3;
+  p->sdc_poisson_start = 1;
 }
 
 const char* sdcef_last_error(void) { return g_err.c_str(); }
@@ -662,13 +668,23 @@ int sdcef_sdc_sweep(sdcef_ctx* ctx, const sdcef_batch* b, int k_max, double kapp
     if (rc) return rc;
     sdcef_batch bk = *b;
     bk.n_ion = b->n_species > 0 ? prov : b->n_ion;
+    int extra = 0;
     if (k > 0) {
       bk.ne_guess = out->ne_out;
       bk.phi_guess = out->phi_out;
+      if (ctx->p.sdc_poisson_start) {
+        // the previous iterate's potential is that of its own charge: re-solve
+        // F_phi = 0 for the new provisional ions (in place: it reads n_e only)
+        cudaError_t e = sdcef_impl::launch_poisson_start(&bk, out->ne_out, bk.n_ion,
+                                                         kEps0 * ctx->p.eps_r / kQe,
+                                                         out->phi_out, ctx->stream);
+        if (e != cudaSuccess) return set_err(SDCEF_ERR_CUDA, cudaGetErrorString(e));
+        extra = 1;
+      }
     }
     rc = sdcef_solve_batch(ctx, &bk, out);
     if (rc) return rc;
-    launches += ctx->launches + (b->n_species > 0 ? 1 : 0);
+    launches += ctx->launches + (b->n_species > 0 ? 1 : 0) + extra;
   }
   ctx->launches = launches;
   return SDCEF_SUCCESS;

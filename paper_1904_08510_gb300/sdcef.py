@@ -62,7 +62,7 @@ class Params(C.Structure):
                 ("mg_max_cycles", C.c_int), ("mg_transfer", C.c_int), ("ion_scheme", C.c_int),
                 ("transport", C.c_int), ("gas_molar_mass", C.c_double), ("eps_E", C.c_double),
                 ("stall_ratio", C.c_double), ("krylov_on_chip", C.c_int),
-                ("guess_progress", C.c_double)]
+                ("guess_progress", C.c_double), ("sdc_poisson_start", C.c_int)]
 
 
 class BatchC(C.Structure):

@@ -84,6 +84,30 @@ def test_sdc_sweep_matches_oracle(precond, precision, scheme):
     assert colerr(b, out["phi"].cpu().numpy(), phi_r).max() <= 1e-9
 
 
+def test_sdc_poisson_start_keeps_the_roots_and_saves_gmres():
+    """Iterations k >= 2 start from the previous n_e with the potential of its
+    charge under the new provisional ions (sdc_poisson_start = 1, the default)
+    or from the previous iterate as it is (0): the same roots (the oracle's
+    sweep at 1e-9), fewer GMRES iterations in the last SDC iteration."""
+    d = dev()
+    b = sdc_batch(64, 778, n_cells=512)
+    db = S.DeviceBatch.from_host(b, d)
+    outs = {}
+    for ps in (0, 1):
+        s = S.Solver(S.default_params(eps_F=1e-12, sdc_poisson_start=ps), max_cols=b.ncol,
+                     max_cells=b.ncells, max_col_cells=512)
+        o = s.sdc_sweep(db, k_max=4)
+        torch.cuda.synchronize()
+        outs[ps] = {k: v.cpu().numpy() for k, v in o.items()}
+        assert (outs[ps]["status"] == S.STATUS_OK).all()
+        s.close()
+    ne_r, phi_r, hist = O.sdc_sweep(b, 4, 4e-3, O.default_params(precond=2, eps_F=1e-12))
+    for ps in (0, 1):
+        assert colerr(b, outs[ps]["ne"], ne_r).max() <= 1e-9
+        assert colerr(b, outs[ps]["phi"], phi_r).max() <= 1e-9
+    assert outs[1]["krylov_it"].mean() <= outs[0]["krylov_it"].mean()
+
+
 @pytest.mark.parametrize("precision", [S.FP64, S.MIXED_DF])
 def test_sdc_sweep_graph_replay_matches_eager(precision):
     d = dev()
