@@ -15,6 +15,9 @@
 // epilogue, which writes the next layer's A operand into the worker's buffer
 // (the MMA that read it has completed). Two CTAs per SM keep 32 warps and
 // four independent MMA chains resident per SM and fill its 512 TMEM columns.
+// Before its tiles the worker stages the column's per-cell quantities and the
+// ion-field features (two prefix sums); after them, for the Poisson start, it
+// solves for the potential of the guessed charge (two more).
 //
 // Shared-memory operand layout: K-major, no swizzle, in 8 x 16-byte core
 // matrices (8 rows x 8 BF16 of K): element (r, k) of a matrix with K/8 = kc

@@ -26,7 +26,8 @@ WEIGHTS_SWEEP = os.path.join(HERE, "data", "mlp_weights_sweep.npz")     # first 
 
 
 def init_params(seed=0):
-    """He-style initial parameters, flat FP32 in the order of the C ABI."""
+    """He-style initial parameters, flat FP32 in the order of the C ABI; the
+    weights of the 7 column-context inputs start at 0 (training brings them in)."""
     rng = np.random.default_rng(seed)
     p = dict(W1=rng.standard_normal((128, 32)) * np.sqrt(2.0 / 25),
              b1=np.zeros(128),
