@@ -420,6 +420,10 @@ def test_pipelined_host_batches_match_one_call_per_batch():
     big = make_batch("ragged", 13, 75, n_range=(64, 128))
     with pytest.raises(S.SdcefError):
         s.solve_host_many([bs[0], big])
+    assert s.solve_host_many([]) == []
+    # one batch through the pipelined call equals the single-batch call
+    one = s.solve_host_many([bs[2]])[0]
+    assert np.array_equal(one["ne"], s.solve_host(bs[2])["ne"])
 
 
 def test_outputs_may_alias_inputs():
