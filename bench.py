@@ -457,6 +457,19 @@ def main():
                             "newton_mean": float(nw.mean()), "krylov_mean": float(kr.mean()),
                             "res_evals_mean": float(re.mean()), "final_res_max": float(fr.max()),
                             "step_ms": ms}}
+    if extra and "headline_workload_learned" in extra:
+        # the learned start on this batch, beside the plain batched solve above
+        # (the network, the guess kernel and the solve; details in comparisons)
+        lw, ld = extra["headline_workload_learned"], extra.get("headline_workload_mixed_df_learned", {})
+        line["learned_start"] = {
+            "value": lw["value"], "unit": UNIT, "vs_plain_batched": lw["value"] / value,
+            "mixed_df_value": ld.get("value"),
+            "newton_per_column": [float(nw.mean()), lw.get("newton_mean")],
+            "gmres_per_column": [float(kr.mean()), lw.get("krylov_mean")],
+            "status_ok": lw.get("status_ok"),
+            "note": "FP64 solve from the learned start (n_e from the network, phi the root of the "
+                    "Poisson residual at that n_e), timed including the guess kernel; "
+                    "iterations as [plain, learned]"}
     print(json.dumps(line))
     return 0
 
