@@ -237,7 +237,9 @@ typedef struct {
  * previous one and judged after 8 Newton steps; for SDCEF_PREC_MG, gamma_MG = 1e-4 on both
  * blocks (the optimum of Sec. 4.2), at most 50 V-cycles per block solve and
  * operator-dependent transfers; the paper's ion transport in the SDC sweep
- * (SDCEF_ION_GODUNOV); constant electron transport, gas molar mass 0.028 kg/mol. */
+ * (SDCEF_ION_GODUNOV), whose later iterations start from the potential of the
+ * previous charge under the new ions (sdc_poisson_start 1); constant electron
+ * transport, gas molar mass 0.028 kg/mol. */
 void sdcef_default_params(sdcef_params* p);
 
 /* Electron transport tables for SDCEF_TRANSPORT_TABLE (Sec. 2.2: mobility
