@@ -96,23 +96,22 @@ constexpr double kKapGuess = 8.8541878128e-12 / 1.602176634e-19;
 // most 32 warps), all of which call it; *total gets the sum over all threads
 // (the same value, summed in the same order, on every thread). red holds W/32
 // doubles of shared memory; bar() synchronises the W threads.
-template <class Bar>
-__device__ __forceinline__ double excl_scan(double v, int t, int W, double* red, Bar bar,
-                                            double* total) {
+template <typename T, class Bar>
+__device__ __forceinline__ T excl_scan(T v, int t, int W, T* red, Bar bar, T* total) {
   const int lane = t & 31, w = t >> 5, nw = W >> 5;
-  double x = v;
+  T x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    const T y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  double ex = __shfl_up_sync(0xffffffffu, x, 1);
-  if (lane == 0) ex = 0.0;
+  T ex = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) ex = T(0);
   if (lane == 31) red[w] = x;
   bar();
-  double base = 0.0, tot = 0.0;
+  T base = T(0), tot = T(0);
   for (int q = 0; q < nw; ++q) {
-    const double r = red[q];
+    const T r = red[q];
     if (q < w) base += r;
     tot += r;
   }
@@ -133,26 +132,28 @@ __device__ __forceinline__ double excl_scan(double v, int t, int W, double* red,
 //   D_{-1} = (8 (V_R - V_L) - S_0 - 8 T_{N-1} - S_{N-2} - 3 S_{N-1}) / (8 N).
 // Thread t of W takes a contiguous run of cells; src(i) is s_i (called twice
 // per cell and once more for cells 0 and N-1); emit(i, phi_i, S_{i-1}, S_i, D_{-1})
-// per cell. Every thread of the W calls it.
-template <class Src, class Emit, class Bar>
-__device__ __forceinline__ void poisson_column(int N, double vl, double vr, int t, int W,
-                                               double* red, Bar bar, Src src, Emit emit) {
+// per cell. Every thread of the W calls it. R is the arithmetic type: double for
+// a potential that starts Newton, float for the ion-field features (their
+// sources share one sign for cations only, and the features are rounded to BF16).
+template <typename R, class Src, class Emit, class Bar>
+__device__ __forceinline__ void poisson_column(int N, R vl, R vr, int t, int W, R* red, Bar bar,
+                                               Src src, Emit emit) {
   const int run = (N + W - 1) / W;
   const int lo = min(t * run, N), hi = min(lo + run, N);
-  double sig = 0.0, tau = 0.0;
+  R sig = R(0), tau = R(0);
   for (int k = lo; k < hi; ++k) {
     sig += src(k);
     tau += sig;
   }
-  double s_tot, t_tot;
-  const double s_before = excl_scan(sig, t, W, red, bar, &s_tot);
-  const double t_before = excl_scan((double)(hi - lo) * s_before + tau, t, W, red, bar, &t_tot);
-  const double S0 = src(0), SN1 = s_tot, SN2 = s_tot - src(N - 1), TN1 = t_tot - s_tot;
-  const double D = (8.0 * (vr - vl) - S0 - 8.0 * TN1 - SN2 - 3.0 * SN1) / (8.0 * N);
-  const double p0 = vl + 0.5 * D + 0.125 * S0;
-  double S = s_before, T = t_before, pk = fma((double)lo, D, p0);   // pk = phi_0 + k D_{-1}
+  R s_tot, t_tot;
+  const R s_before = excl_scan<R>(sig, t, W, red, bar, &s_tot);
+  const R t_before = excl_scan<R>(R(hi - lo) * s_before + tau, t, W, red, bar, &t_tot);
+  const R S0 = src(0), SN1 = s_tot, SN2 = s_tot - src(N - 1), TN1 = t_tot - s_tot;
+  const R D = (R(8) * (vr - vl) - S0 - R(8) * TN1 - SN2 - R(3) * SN1) / (R(8) * R(N));
+  const R p0 = vl + R(0.5) * D + R(0.125) * S0;
+  R S = s_before, T = t_before, pk = fma(R(lo), D, p0);   // pk = phi_0 + k D_{-1}
   for (int k = lo; k < hi; ++k) {
-    const double Sn = S + src(k);
+    const R Sn = S + src(k);
     emit(k, pk + T, S, Sn, D);
     T += Sn;
     S = Sn;
@@ -180,13 +181,12 @@ __device__ __forceinline__ float ctx_pos(int i, int N) {
 }
 
 // Features 30, 31 of cell i from the ion potential phi_i = phi_ion,i and the
-// face sums of poisson_column: E_ion,i = -(D_{i-1} + D_i) / (2h) (the sum of
-// face differences in FP64, where the field changes sign; the scaling and
-// the asinh in FP32, the features being rounded to BF16).
-__device__ __forceinline__ void ion_features(double phi_i, double S_prev, double S_i, double D,
+// face sums of poisson_column: E_ion,i = -(D_{i-1} + D_i) / (2h), in FP32 (the
+// features are rounded to BF16).
+__device__ __forceinline__ void ion_features(float phi_i, float S_prev, float S_i, float D,
                                              float L2h_isp, float isp, float* f30, float* f31) {
-  *f30 = asinhf((float)phi_i * isp);
-  *f31 = asinhf(-(float)(2.0 * D + S_prev + S_i) * L2h_isp);
+  *f30 = asinhf(phi_i * isp);
+  *f31 = asinhf(-(2.0f * D + S_prev + S_i) * L2h_isp);
 }
 
 // f_phi = sum_s nu_s n_s of batch cell gi (one unit cation: the density itself)
@@ -280,12 +280,16 @@ __global__ void feat_kernel(FeatArgs a) {
   if (N < 2) return;
   // features 30, 31: the potential and field of the ion charge alone
   __syncthreads();   // sh is free again (last read by block_max)
-  const double L = a.length[c], hk = (L / N) * (L / N) / kKapGuess;
+  // sources -(h^2/kappa) f_i = -(h^2 s_n/kappa) (f_i/s_n), the second factor
+  // being the staged FP32 quantity of the stencil features
+  const double L = a.length[c];
+  const float hks = (float)((L / N) * (L / N) / kKapGuess * sn);
   const float L2h_isp = 0.5f * (float)N * isp;
-  poisson_column(
-      N, 0.0, 0.0, (int)threadIdx.x, (int)blockDim.x, sh, [] { __syncthreads(); },
-      [&](int i) { return -hk * fphi_cell(a, cells, off + i); },
-      [&](int i, double phi_i, double S_prev, double S_i, double D) {
+  poisson_column<float>(
+      N, 0.0f, 0.0f, (int)threadIdx.x, (int)blockDim.x, reinterpret_cast<float*>(sh),
+      [] { __syncthreads(); },
+      [&](int i) { return -hks * ((float)fphi_cell(a, cells, off + i) * isn); },
+      [&](int i, float phi_i, float S_prev, float S_i, float D) {
         float f30, f31;
         ion_features(phi_i, S_prev, S_i, D, L2h_isp, isp, &f30, &f31);
         __nv_bfloat16* x = a.X + (off + i) * kIn;
@@ -1234,11 +1238,14 @@ __global__ void __launch_bounds__(tc::kGuessThreads, 2) guess_tc_kernel(GuessArg
       if (N < 2) st[i * kStageW + 5] = st[i * kStageW + 6] = 0.0f;
     }
     if (N >= 2) {
-      const double L = a.length[c], hk = (L / N) * (L / N) / kKapGuess;
+      tc::bar(barid, W);   // the staged quantities of every cell of the column
+      const double L = a.length[c];
+      const float hks = (float)((L / N) * (L / N) / kKapGuess * sn);
       const float L2h_isp = 0.5f * (float)N * isp;
-      poisson_column(
-          N, 0.0, 0.0, t, W, red, wbar, [&](int i) { return -hk * fphi_cell(a, cells, off + i); },
-          [&](int i, double phi_i, double S_prev, double S_i, double D) {
+      poisson_column<float>(
+          N, 0.0f, 0.0f, t, W, reinterpret_cast<float*>(red), wbar,
+          [&](int i) { return -hks * st[i * kStageW + 2]; },
+          [&](int i, float phi_i, float S_prev, float S_i, float D) {
             ion_features(phi_i, S_prev, S_i, D, L2h_isp, isp, &st[i * kStageW + 5],
                          &st[i * kStageW + 6]);
           });

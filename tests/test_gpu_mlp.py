@@ -58,10 +58,12 @@ def assert_elementwise(a, r, rel, what):
 @pytest.mark.parametrize("n_range", [(3, 300), (1, 4)])
 def test_features_match_oracle(n_range):
     """One BF16 ulp. The ion potential and field (features 30, 31) come from
-    prefix sums on the GPU and a banded solve in the oracle; where the field
-    changes sign the two FP64 roundings can differ in sign of a value near 0;
-    log10(dt) + 5 is 0 up to rounding at dt = 1e-5 s: hence an absolute floor
-    of 1e-6 on the context features."""
+    FP32 prefix sums on the GPU and an FP64 banded solve in the oracle: near the
+    electrodes, where the potential tends to 0, and where the field changes
+    sign they differ by the FP32 rounding of the sums (relative 1e-6 of the
+    column's largest terms), hence an absolute floor of 1e-4 on those two (a
+    BF16 ulp of a feature of order 1 is 4e-3); log10(dt) + 5 is 0 up to
+    rounding at dt = 1e-5 s: an absolute floor of 1e-6 on the context features."""
     d = dev()
     b = make_batch("ragged", 5, 31, n_range=n_range)
     db = S.DeviceBatch.from_host(b, d)
@@ -70,6 +72,7 @@ def test_features_match_oracle(n_range):
     ref = M.bf16_round(M.features(b))
     tol = 2.0 ** -7 * np.abs(ref) + 1e-30
     tol[:, 25:] += 1e-6   # context features that are 0 up to rounding (log10(dt) + 5)
+    tol[:, 30:] += 1e-4   # the ion field from FP32 prefix sums
     assert np.all(np.abs(X - ref) <= tol), np.argwhere(np.abs(X - ref) > tol)[:5]
     mlp.close()
 
@@ -92,6 +95,7 @@ def test_features_and_poisson_start_with_two_species_and_varied_steps():
     ref = M.bf16_round(M.features(b))
     tol = 2.0 ** -7 * np.abs(ref) + 1e-30
     tol[:, 25:] += 1e-6
+    tol[:, 30:] += 1e-4
     assert np.all(np.abs(X - ref) <= tol), np.argwhere(np.abs(X - ref) > tol)[:5]
     flat, _ = rounded_params(17)
     mlp.set_params(flat)
