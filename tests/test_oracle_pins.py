@@ -450,3 +450,29 @@ def test_error_test_bounds_the_root_error():
         assert err(off) > 5e-10
         assert err(on) <= 5e-10
         assert on["newton_it"][0] == off["newton_it"][0] + 1
+
+
+def test_supplied_start_stops_within_the_error_bar():
+    """From a supplied start (the converged root with a smooth relative n_e
+    error of 1-5 % and the potential of that charge, as a learned start is
+    built) the oracle's solve stops within eps_E = 5e-10 of the dense
+    exact-Jacobian Newton root on the two low-voltage columns of the bench
+    workload, the error test being taken on fresh factors when the estimate on
+    the last step's factors is within a factor 10 of the bar."""
+    from oracle import mlp as M
+    full = make_batch("ragged", 4096, 2_000_000)
+    for c in (1459, 2068):
+        b = full.column(c)
+        n = b.ncells
+        X = _dense_newton(b, O.default_params(precond=2))
+        x = (np.arange(n) + 0.5) / n
+        for amp in (1e-2, 5e-2):
+            for k in (1, 3):
+                ne0 = X[:n] * (1 + amp * np.sin(k * np.pi * x))
+                phi0 = M.poisson_potential(ne0 - b.n_ion[0], b.length[0] / n, b.v_left[0],
+                                           b.v_right[0])
+                r = O.solve(b, O.default_params(precond=2, eps_E=5e-10), guess=(ne0, phi0))
+                assert r["status"][0] == O.OK
+                e = max(np.abs(r["ne"] - X[:n]).max() / np.abs(X[:n]).max(),
+                        np.abs(r["phi"] - X[n:]).max() / np.abs(X[n:]).max())
+                assert e <= 5e-10, (c, amp, k, e)
