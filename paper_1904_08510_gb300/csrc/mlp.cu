@@ -95,7 +95,7 @@ constexpr double kKapGuess = 8.8541878128e-12 / 1.602176634e-19;
 // Exclusive prefix sum of v over threads t = 0..W-1 (W a multiple of 32, at
 // most 32 warps), all of which call it; *total gets the sum over all threads
 // (the same value, summed in the same order, on every thread). red holds W/32
-// doubles of shared memory; bar() synchronises the W threads.
+// values of type T in shared memory; bar() synchronises the W threads.
 template <typename T, class Bar>
 __device__ __forceinline__ T excl_scan(T v, int t, int W, T* red, Bar bar, T* total) {
   const int lane = t & 31, w = t >> 5, nw = W >> 5;
