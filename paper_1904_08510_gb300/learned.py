@@ -232,18 +232,28 @@ def main():
     import argparse
     import json
     ap = argparse.ArgumentParser()
-    ap.add_argument("--ncol", type=int, default=200_000)
-    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--ncol", type=int, default=None,
+                    help="training columns (default: 400k single, 600k ragged, 262144 sweep, "
+                         "the sets of the shipped networks)")
+    ap.add_argument("--steps", type=int, default=480_000)
     ap.add_argument("--batch", type=int, default=32768)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--eval-ncol", type=int, default=4096)
-    ap.add_argument("--out", default=WEIGHTS)
-    ap.add_argument("--train-cells", default="256",
+    ap.add_argument("--eval-ncol", type=int, default=None,
+                    help="held-out columns (default: 4096; 16384 for the sweep family)")
+    ap.add_argument("--out", default=None,
+                    help="weights file (default: the family's file under data/)")
+    ap.add_argument("--train-cells", default="512:2048",
                     help="cells per training column: an integer, or lo:hi for U{lo..hi}")
     ap.add_argument("--family", default="single", choices=["single", "ragged", "sweep"],
                     help="profile family of the training and evaluation columns (sweep: the "
                          "first SDC iteration of the electric sweep, 1024-cell columns)")
     args = ap.parse_args()
+    if args.ncol is None:
+        args.ncol = {"single": 400_000, "ragged": 600_000, "sweep": 262_144}[args.family]
+    if args.eval_ncol is None:
+        args.eval_ncol = 16384 if args.family == "sweep" else 4096
+    if args.out is None:
+        args.out = {"single": WEIGHTS, "ragged": WEIGHTS_RAGGED, "sweep": WEIGHTS_SWEEP}[args.family]
     t0 = time.perf_counter()
     if args.family == "ragged":
         # training seeds 3e6 + i, disjoint from the evaluation / benchmark seeds 2e6 + i
